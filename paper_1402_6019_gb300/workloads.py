@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs shared by the CUDA path and its checker.
+
+This module holds no arithmetic of the method: it only draws density fields.  Both the library
+(tests, bench) and the oracle take their initial densities from here, so no random number is
+ever drawn on either side of the comparison.
+
+Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014), used as a counter-based generator: draw i of stream `seed` is the
+SplitMix64 output mix(seed + (i + 1) * 0x9E3779B97F4A7C15).  It is written out here so the
+streams are identical on every machine and numpy version.
+
+The workloads stand in for the paper's emulsions (Sec. IV: A-rich droplets at rho ~ 1.2 in a
+B-rich matrix and vice versa, Fig. 4) and for the single-component tests of Secs. II-III.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Draws offset .. offset+n-1 of SplitMix64 stream `seed` (uint64)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of each draw."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def noise_field(nx: int, nz: int, seed: int, mean: float = 1.0, amp: float = 0.01,
+                n_species: int = 1) -> np.ndarray:
+    """rho [n_species, nz, nx] = mean + U(-amp, amp), one independent draw per site."""
+    u = uniform(seed, n_species * nz * nx).reshape(n_species, nz, nx)
+    return mean + amp * (2.0 * u - 1.0)
+
+
+def disk_packing(nx: int, nz: int, fraction: float, seed: int, r_mean: float = 12.0,
+                 r_spread: float = 3.0, rho_in: float = 1.2, rho_out: float = 0.05,
+                 periodic_z: bool = True, max_disks: int = 1_000_000):
+    """Two-species density fields of a random polydisperse disk packing.
+
+    Disks with uniform radius in [r_mean - r_spread, r_mean + r_spread] and uniform centres are
+    added one at a time (overlap allowed) until the covered area reaches `fraction`; random
+    sequential addition without overlap jams near 0.55, below the packings asked for.  Inside a
+    disk (rho_A, rho_B) = (rho_in, rho_out), outside (rho_out, rho_in).  Periodic in x; in z
+    periodic, or clipped by walls.  Returns (rho [2, nz, nx], achieved covered fraction).
+    """
+    if not (0.0 <= fraction < 1.0):
+        raise ValueError("fraction must be in [0, 1)")
+    covered = np.zeros((nz, nx), dtype=bool)
+    xs = np.arange(nx, dtype=np.float64)
+    zs = np.arange(nz, dtype=np.float64)
+    target = fraction * nx * nz
+    k = 0
+    while covered.sum() < target and k < max_disks:
+        u = uniform(seed, 3, offset=3 * k)
+        cx, cz = u[0] * nx, u[1] * nz
+        r = r_mean + r_spread * (2.0 * u[2] - 1.0)
+        dx = np.abs(xs - cx)
+        dx = np.minimum(dx, nx - dx)
+        dz = np.abs(zs - cz)
+        if periodic_z:
+            dz = np.minimum(dz, nz - dz)
+        covered |= (dz[:, None] ** 2 + dx[None, :] ** 2) <= r * r
+        k += 1
+    rho = np.empty((2, nz, nx))
+    rho[0] = np.where(covered, rho_in, rho_out)
+    rho[1] = np.where(covered, rho_out, rho_in)
+    return rho, float(covered.mean())
+
+
+# Normalisation of the interaction weights: Appendix B's tables satisfy sum W c c = 1, while
+# Eq. BULK (P_b = c_s^2 rho + c_s^2 (G1 + G2) psi^2 / 2) implies sum W c c = c_s^2.  The paper's
+# couplings only give stable phases near its printed densities under the latter, so every
+# interaction weight is scaled by c_s^2 = 1/3.
+WEIGHT_NORM = 1.0 / 3.0
+
+# Couplings of the paper's emulsion (Sec. IV): G_AA = (-9.0, 8.1), G_BB = (-8.0, 7.1),
+# psi = 1 - exp(-rho/0.83).  The 1024^2 workload uses G_AB = 0.405; the paper's flow runs 0.587.
+EMULSION_PARAMS = dict(tau=(1.0, 1.0), G1=(-9.0, -8.0), G2=(8.1, 7.1), G_AB=0.405,
+                       psi_form=0, rho0=(0.83, 0.83), weight_norm=WEIGHT_NORM)
+
+# Single-component frustrated couplings of Secs. III-IV with psi = 1 - exp(-rho).
+SINGLE_PARAMS = dict(tau=(1.0, 1.0), G1=(-9.0, -9.0), G2=(8.1, 8.1), psi_form=0,
+                     rho0=(1.0, 1.0), weight_norm=WEIGHT_NORM)
+
+# Phase-separating single-component couplings of the thin-film test (Sec. III, Fig. 3).
+FILM_PARAMS = dict(tau=(1.0, 1.0), G1=(-20.4, -20.4), G2=(16.0, 16.0), psi_form=0,
+                   rho0=(1.0, 1.0), weight_norm=WEIGHT_NORM)
+
+
+def workload(name: str, seed: int = 1402):
+    """Named workloads: returns dict(nx, nz, n_species, z_boundary, params, rho, note)."""
+    if name == "single_128":
+        rho = noise_field(128, 128, seed)
+        return dict(nx=128, nz=128, n_species=1, z_boundary=0, params=dict(SINGLE_PARAMS),
+                    rho=rho, note="128x128 periodic, rho = 1 + U(-0.01, 0.01)")
+    if name == "emulsion_1024":
+        rho, frac = disk_packing(1024, 1024, 0.8, seed)
+        return dict(nx=1024, nz=1024, n_species=2, z_boundary=0, params=dict(EMULSION_PARAMS),
+                    rho=rho, note=f"1024x1024 periodic disk packing, covered {frac:.3f}")
+    if name.startswith("emulsion_"):
+        n = int(name.split("_")[1])
+        rho, frac = disk_packing(n, n, 0.8, seed)
+        return dict(nx=n, nz=n, n_species=2, z_boundary=0, params=dict(EMULSION_PARAMS),
+                    rho=rho, note=f"{n}x{n} periodic disk packing, covered {frac:.3f}")
+    if name in ("channel_couette", "channel_poiseuille"):
+        rho, frac = disk_packing(2048, 256, 0.85, seed, periodic_z=False)
+        p = dict(EMULSION_PARAMS)
+        if name == "channel_couette":
+            p["wall_u"] = (-0.01, 0.01)
+        else:
+            p["body_force"] = 1e-6
+        return dict(nx=2048, nz=256, n_species=2, z_boundary=1, params=p, rho=rho,
+                    note=f"2048x256 walled channel, packing {frac:.3f}")
+    raise KeyError(name)
