@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the multirange Shan-Chen lattice Boltzmann step on GB300.
+
+One "step" is one pass of the whole hot path over the lattice: density and pseudopotential,
+two-belt + cross + body force, shifted-velocity BGK collision, streaming with walls, and the
+observables of the collided state (mass, momentum, profiles, pressure tensor, surface tension,
+wall stress, fluidity) reduced in FP64 -- i.e. lbm_step with sampling every step.
+
+Default workload: the two-component A/B emulsion on a 1024 x 1024 periodic lattice, FP32
+populations stored as deviations, FP64 reductions (disk packing at fraction 0.8, radii
+12 +- 3, G_AA = (-9.0, 8.1), G_BB = (-8.0, 7.1), G_AB = 0.405, rho0 = 0.83).
+
+Metric: MLUPS (million lattice-site updates per second, whole job).  Between timed steps a
+buffer larger than L2 is written (cold L2 for every step); each step is bracketed by CUDA events
+on the library's stream.  The step kernel is additionally timed alone (lbm_profile) for the
+roofline line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SITE = {("fp32", 2): 144, ("fp64", 2): 288, ("fp32", 1): 72, ("fp64", 1): 144}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="emulsion_1024")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--rows-per-warp", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic(kernel_src_hash, workload, precision):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when
+    the summary is for another source of the kernel or another workload."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(f"{workload}/{precision}")
+    if not e or e.get("kernel_source_sha1") != kernel_src_hash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in ("lbm_fused.cu", "lbm_core.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1402_6019_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def cpu_baseline(w, seconds=12.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
+    whole oracle steps (step + observables, like the GPU step) on a 256 x 256 lattice cut from
+    the same workload, until `seconds` of wall time have passed."""
+    import oracle
+
+    oracle.build()
+    n = 256
+    rho = np.ascontiguousarray(w["rho"][:, :n, :n])
+    ref = oracle.RefLattice(n, n, w["n_species"], w["z_boundary"], **w["params"])
+    ref.set_fields(rho)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        ref.step(1)
+        ref.observables()
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n * n * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{k} oracle steps (step + observables) on a {n}x{n} cut of the workload, "
+                      f"{dt:.1f} s wall, OpenMP threads={cores}"}
+
+
+def run_reference(a, w):
+    """--impl reference: the FP64 oracle timed on the host cores on a bounded sample of the
+    workload (a 256 x 256 cut): W warm-up steps then K timed steps, each = oracle step +
+    observables, MLUPS over the sample's sites."""
+    import oracle
+
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    oracle.build()
+    n = 256
+    rho = np.ascontiguousarray(w["rho"][:, :n, :n])
+    ref = oracle.RefLattice(n, n, w["n_species"], w["z_boundary"], **w["params"])
+    ref.set_fields(rho)
+    for _ in range(a.warmup):
+        ref.step(1)
+        ref.observables()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        ref.step(1)
+        ref.observables()
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n * n * a.steps / dt / 1e6
+    sample = f"{a.steps} timed oracle steps (step + observables) on a {n}x{n} cut of {a.workload}"
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": a.workload, "sample": f"{n}x{n}"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    a = _args()
+    from paper_1402_6019_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    w = W.workload(a.workload, seed=1402 + rank)
+    if a.impl == "reference":
+        return run_reference(a, w)
+
+    import torch
+
+    from paper_1402_6019_gb300 import lbm as L
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+
+        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    nx, nz, ns = w["nx"], w["nz"], w["n_species"]
+    sites = nx * nz
+    prec = L.LBM_FP32 if a.precision == "fp32" else L.LBM_FP64
+    # a non-default stream: the library runs on it, and the events below are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=L.LBM_KERNEL_FUSED, device=local,
+                    stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, **w["params"])
+    lat.set_fields(w["rho"])
+    lat.set_observe(1)  # every step reduces the observables of the state it collides
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(a.warmup):
+        flush.fill_(1.0)
+        lat.step(1)
+    lat.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    L.lbm_profile(lat.h, True)
+    launches0 = lat.launches
+    barrier()
+    with Clocks(local) as clk:
+        for k in range(a.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            lat.step(1)
+            ends[k].record(stream)
+        barrier()
+    launches = lat.launches - launches0
+    step_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    kern_ms, kern_n = L.lbm_profile_read(lat.h)
+    L.lbm_profile(lat.h, False)
+    lat.synchronize()
+    if dist:
+        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    ms_per_step = step_ms / a.steps
+    value = sites * world / (ms_per_step * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (the fused step kernel)
+    bps = BYTES_PER_SITE[(a.precision, ns)]
+    kern_avg_ms = kern_ms / max(kern_n, 1)
+    achieved = bps * sites / (kern_avg_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic(kernel_source_hash(), a.workload, a.precision)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "lbm::k_fused<T, 2, M_WRITE|M_OBS>", "kernel_ms": round(kern_avg_ms, 5),
+                "algorithmic_bytes_per_site": bps}
+
+    # end to end through the public API with host buffers: upload the fields from pinned host
+    # memory, then per step lbm_step + lbm_averages (D2H of the step's observables)
+    e2e = None
+    if a.e2e_steps > 0:
+        rho_pin = torch.from_numpy(np.ascontiguousarray(w["rho"])).pin_memory()
+        rho_np = rho_pin.numpy()
+        o, prof = lat._obs_struct()
+        barrier()
+        t0 = time.perf_counter()
+        lat.set_fields(rho_np)
+        lat.set_observe(1)
+        for _ in range(a.e2e_steps):
+            lat.step(1)
+            L.lbm_averages(lat.h, o, True)
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        obs_bytes = (16 + 5 * nz + 2 * nx) * 8
+        e2e = {"value": round(sites * world * a.e2e_steps / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(rho_np.nbytes // a.e2e_steps), "d2h_bytes_per_step": obs_bytes,
+               "steps": a.e2e_steps}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "nx": nx, "nz": nz, "n_species": ns,
+                   "precision": a.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MiB write)", "observables": "every step",
+                   "rows_per_warp": lat.desc.rows_per_warp},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * lbm.h -- C ABI of liblbm.so, the GB300 (sm_103a) implementation of the time step of the
+ * two-belt ("frustrated") multirange Shan-Chen lattice Boltzmann model for non-ideal fluids
+ * and A/B emulsions of Sbragaglia, Benzi, Bernaschi and Succi, "The emergence of
+ * supramolecular forces from lattice kinetic models of non ideal fluids: applications to the
+ * rheology of soft glassy materials" (arXiv:1402.6019).
+ *
+ * Conventions for every call:
+ *  - Return value: LBM_OK (0) or a positive LBM_E* code.  No call throws and no call aborts
+ *    the process.  lbm_last_error() gives a one-line description of the last failure on
+ *    that context.
+ *  - Lattice: x (stream-flow, periodic) is the fastest index, z (cross-flow) the slower one,
+ *    as in Sec. IV.  Host arrays are C-contiguous FP64 in the layouts stated per call.
+ *  - Memory: host arrays passed in are copied before the call returns; host arrays passed
+ *    out are written before it returns.  "where" = LBM_DEVICE means the pointer is CUDA
+ *    device memory on the context's device, read or written on the context's stream and
+ *    owned by the caller.  The library owns all device memory it allocates and frees it in
+ *    lbm_destroy.
+ *  - Streams: calls that launch work enqueue it on the context's stream and return without
+ *    waiting, except where a call says it synchronises.
+ *  - A context is bound to one device and one stream and is not thread-safe.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+/* status codes */
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* bad argument; nothing was changed                          */
+    LBM_ECUDA = 2,      /* a CUDA call failed (no device, launch error, ...)           */
+    LBM_ENOMEM = 3,     /* device or host allocation failed                            */
+    LBM_ENONFINITE = 4, /* the state holds a density that is <= 0, NaN or Inf           */
+    LBM_ETIMEOUT = 5    /* a bounded device-side wait gave up                          */
+};
+
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };            /* storage + arithmetic of the populations  */
+enum { LBM_PERIODIC = 0, LBM_BOUNCEBACK = 1 };  /* boundary in z (x is always periodic)     */
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_FUSED = 1, LBM_KERNEL_TWO_PASS = 2 };
+enum { LBM_PSI_EXP = 0, LBM_PSI_RHO = 1 };
+enum { LBM_WEIGHTS_PAPER = 0, LBM_WEIGHTS_CHEM09 = 1 };
+enum { LBM_WALL_MIRROR = 0, LBM_WALL_ZERO = 1 };
+enum { LBM_HOST = 0, LBM_DEVICE = 1 };
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Lattice and execution description, fixed for the life of a context. */
+typedef struct {
+    int nx, nz;          /* lattice size, 1 <= nx, nz <= 65536, nx * nz <= 2^30          */
+    int n_species;       /* 1 (Secs. II-III) or 2 (the A/B emulsion of Sec. IV)          */
+    int precision;       /* LBM_FP64, or LBM_FP32: populations stored and relaxed in FP32
+                            as deviations f_l - W_l rho_ref from the rest weights           */
+    int z_boundary;      /* LBM_PERIODIC or LBM_BOUNCEBACK (walls at z = -1/2, nz - 1/2)  */
+    int kernel;          /* LBM_KERNEL_AUTO / _FUSED (one pass per step) / _TWO_PASS      */
+    int device;          /* CUDA device ordinal                                          */
+    void *stream;        /* cudaStream_t to run on; NULL = a stream owned by the context  */
+    int rows_per_warp;   /* fused kernel: rows of one strip swept by a warp; 0 = auto     */
+} lbm_desc;
+
+/* Model parameters (Eq. LB, Eq. FORCE, Sec. IV).  Species index 0 = A, 1 = B. */
+typedef struct {
+    double tau[2];       /* BGK relaxation time (Eq. LB), > 1/2                          */
+    double G1[2];        /* short-range (attractive, < 0) coupling of Eq. FORCE            */
+    double G2[2];        /* mid-range (repulsive, > 0) coupling of Eq. FORCE               */
+    double G_AB;         /* A-B cross repulsion of Sec. IV                                */
+    int psi_form;        /* LBM_PSI_EXP: psi = 1 - exp(-rho/rho0) (Sec. IV); LBM_PSI_RHO  */
+    double rho0[2];      /* rho0 of the exponential pseudopotential, > 0                  */
+    int weight_preset;   /* LBM_WEIGHTS_PAPER: attraction on |c|^2 <= 4 (l = 1..12),
+                            repulsion on |c|^2 <= 8 (l = 1..24), both 6th-order isotropic
+                            (Eq. FORCE); LBM_WEIGHTS_CHEM09: attraction on the first belt    */
+    double weight_norm;  /* scale of every interaction weight: the tables of Appendix B
+                            have sum W c c = 1; Eq. BULK corresponds to 1/3               */
+    double body_force;   /* acceleration g along x: F_s += rho_s g (Sec. IV drive)        */
+    double wall_u[2];    /* x-velocity of the bottom and top walls (Sec. IV Couette)      */
+    int psi_wall;        /* psi and rho in the two ghost rows beyond a wall: mirror image
+                            of the fluid (LBM_WALL_MIRROR) or zero (LBM_WALL_ZERO)          */
+    double rho_ref[2];   /* LBM_FP32 only: reference density of the stored deviations;
+                            < 0 selects the mean density given to lbm_set_fields            */
+} lbm_params;
+
+/* Observables of one state (Secs. III-IV), FP64.  Profile pointers are caller-owned host
+   arrays or NULL to skip. */
+typedef struct {
+    double mass[2];        /* sum over sites of rho_s                                      */
+    double momentum[2];    /* sum over sites and species of j_s + F_s / 2                  */
+    double gamma;          /* sum over x of the z-average of P_xx - P_zz (Eq. DIS1): the
+                              surface tension of interfaces normal to x                     */
+    double wall_force[2];  /* x-momentum given per step and unit length to the bottom and
+                              top wall by bounce-back (zero without walls)                  */
+    int nonfinite;         /* 1 if a density <= 0, NaN or Inf was met                      */
+    long long step;        /* steps taken since lbm_set_fields                             */
+    long long samples;     /* lbm_averages: number of states averaged                      */
+    double *ux_z;          /* [nz] x-average of the barycentric velocity u_x               */
+    double *rho_z;         /* [n_species][nz] x-average of rho_s                          */
+    double *sxz_z;         /* [nz] x-average of the shear stress S_xz                      */
+    double *fluid_z;       /* [nz] fluidity (d ux_z / dz) / sxz_z (Eq. fluidity)            */
+    double *ps_x;          /* [nx] z-average of P_xx - P_zz                                */
+    double *pxx_x;         /* [nx] z-average of the normal pressure P_xx (Sec. III)        */
+} lbm_obs;
+
+/* Create a context: validates d, selects d->device, allocates the double-buffered
+   populations and the reduction buffers.  *out is NULL on failure. */
+int lbm_create(lbm_ctx **out, const lbm_desc *d);
+
+/* Check a description without touching any GPU (LBM_OK or LBM_EINVAL). */
+int lbm_validate_desc(const lbm_desc *d);
+/* Check parameters for a context with n_species species without touching any GPU. */
+int lbm_validate_params(const lbm_params *p, int n_species);
+/* Fill d and p with the defaults (1 species, FP64, periodic; tau = 1, weight_norm = 1/3). */
+void lbm_default_desc(lbm_desc *d);
+void lbm_default_params(lbm_params *p);
+
+/* Set the model parameters (Eq. LB tau, Eq. FORCE G1/G2 and weights, Sec. IV G_AB, psi
+   form, drives).  Takes effect from the next step. */
+int lbm_set_params(lbm_ctx *c, const lbm_params *p);
+
+/* Initial state: populations at the equilibrium of Sec. II for the given densities
+   rho [n_species][nz][nx] (every value > 0 and finite) and velocity u [2][nz][nx] (NULL:
+   u = 0).  Resets the step counter and the time averages.  Synchronises the stream. */
+int lbm_set_fields(lbm_ctx *c, const double *rho, const double *u, int where);
+
+/* Read the state.  Any pointer may be NULL.  rho [n_species][nz][nx]; u [2][nz][nx], the
+   barycentric velocity (sum_s j_s + F_s/2) / sum_s rho_s; f [n_species][9][nz][nx], the
+   populations after streaming (FP64; FP32 deviations are converted).  Synchronises. */
+int lbm_get_fields(lbm_ctx *c, double *rho, double *u, double *f, int where);
+
+/* Advance nsteps >= 0 time steps (Eq. LB with the force of Eq. FORCE applied by the shifted
+   velocity of Sec. II, then streaming with the walls of Sec. IV).  Asynchronous.  While
+   sampling is on (lbm_set_observe), every k-th step also accumulates the observables of
+   the state it collides into FP64 time sums on the device. */
+int lbm_step(lbm_ctx *c, int nsteps);
+
+/* Sampling of time averages: every k >= 1 steps, or 0 = off.  Resets the sums. */
+int lbm_set_observe(lbm_ctx *c, int every);
+
+/* Observables of the current state.  Synchronises the stream. */
+int lbm_observables(lbm_ctx *c, lbm_obs *out);
+
+/* Time averages of the observables sampled since the last reset (out->samples of them);
+   reset != 0 clears the sums afterwards.  Synchronises the stream. */
+int lbm_averages(lbm_ctx *c, lbm_obs *out, int reset);
+
+/* Wait for the context's stream; reports LBM_ENONFINITE if a step met a bad density. */
+int lbm_synchronize(lbm_ctx *c);
+
+/* Number of kernels the context has launched so far (all kinds). */
+long long lbm_launch_count(const lbm_ctx *c);
+
+/* Kernel timing: while enabled (enable != 0), every launch of the step kernel made by
+   lbm_step is bracketed by CUDA events on the context's stream (CUDA-graph replay is off),
+   and lbm_profile_read returns the summed event time in milliseconds and the number of
+   launches timed since profiling was enabled.  lbm_profile_read synchronises. */
+int lbm_profile(lbm_ctx *c, int enable);
+int lbm_profile_read(lbm_ctx *c, double *step_kernel_ms, long long *launches);
+
+/* One-line description of the last failure on c (or of the last lbm_create failure when
+   c is NULL).  Valid until the next call on c. */
+const char *lbm_last_error(const lbm_ctx *c);
+
+/* Free the context and everything it allocated (NULL is ignored). */
+void lbm_destroy(lbm_ctx *c);
+
+/* LBM_ABI_VERSION of the library. */
+int lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,573 @@
+// lbm_api.cu -- the C ABI of liblbm.so (declared in include/lbm.h).
+//
+// Owns the device buffers of one simulation, turns lbm_params into the per-step constant
+// tables of the kernels, and enqueues the kernels on the context's stream.  Every entry
+// point returns a status; nothing throws across the ABI.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_consts.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_desc d{};
+    lbm_params p{};
+    int pitch = 0;
+    long long plane = 0;
+    size_t esize = 0;  // bytes per stored population value
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nsm = 0;
+    SweepGeom geom{};
+    GhostGeom ghost{};
+    int kernel = LBM_KERNEL_FUSED;  // resolved
+    int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
+    double* part_row = nullptr;
+    double* part_col = nullptr;
+    double* row_sum = nullptr;
+    double* col_sum = nullptr;
+    unsigned* ticket = nullptr;
+    int* flag = nullptr;
+    double* out = nullptr;
+    double* avg = nullptr;
+    double* staging = nullptr;  // (ns + 2) * n doubles
+    double* fexport = nullptr;  // ns * 9 * n doubles
+    void* gfield = nullptr;     // two-pass ghost fields
+    double* host_out = nullptr; // pinned
+    StepConst<float> c32{};
+    StepConst<double> c64{};
+    double rho_ref[2] = {0.0, 0.0};
+    bool have_params = false, have_fields = false;
+    int observe_every = 0;
+    long long step = 0;
+    long long launches = 0;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][observe]
+    int graph_steps = 16;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;  // pairs around step-kernel launches
+    size_t ev_used = 0;
+    std::string err;
+};
+
+static std::string g_create_error;
+
+static int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+    } while (0)
+
+static void refresh_const(lbm_ctx* c) {
+    fill_step_const<float>(c->c32, c->p, c->d.nx, c->d.nz, c->pitch, c->plane, c->d.n_species, c->d.z_boundary,
+                           c->rho_ref);
+    fill_step_const<double>(c->c64, c->p, c->d.nx, c->d.nz, c->pitch, c->plane, c->d.n_species, c->d.z_boundary,
+                            c->rho_ref);
+}
+
+static void drop_graphs(lbm_ctx* c) {
+    for (auto& pr : c->graph)
+        for (auto& g : pr)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
+
+// ---------------------------------------------------------------------------------------
+// Validation (host only)
+// ---------------------------------------------------------------------------------------
+extern "C" void lbm_default_desc(lbm_desc* d) {
+    if (!d) return;
+    memset(d, 0, sizeof *d);
+    d->nx = d->nz = 64;
+    d->n_species = 1;
+    d->precision = LBM_FP64;
+    d->z_boundary = LBM_PERIODIC;
+    d->kernel = LBM_KERNEL_AUTO;
+}
+
+extern "C" void lbm_default_params(lbm_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->tau[0] = p->tau[1] = 1.0;
+    p->rho0[0] = p->rho0[1] = 1.0;
+    p->weight_norm = 1.0 / 3.0;
+    p->rho_ref[0] = p->rho_ref[1] = -1.0;
+}
+
+static int check_desc(lbm_ctx* c, const lbm_desc* d) {
+    if (!d) return fail(c, LBM_EINVAL, "desc is NULL");
+    if (d->nx < 1 || d->nz < 1 || d->nx > 65536 || d->nz > 65536)
+        return fail(c, LBM_EINVAL, "nx, nz must be in [1, 65536] (got %d x %d)", d->nx, d->nz);
+    if ((long long)d->nx * d->nz > (1LL << 30)) return fail(c, LBM_EINVAL, "nx * nz exceeds 2^30");
+    if (d->n_species != 1 && d->n_species != 2) return fail(c, LBM_EINVAL, "n_species must be 1 or 2");
+    if (d->precision != LBM_FP64 && d->precision != LBM_FP32) return fail(c, LBM_EINVAL, "unknown precision");
+    if (d->z_boundary != LBM_PERIODIC && d->z_boundary != LBM_BOUNCEBACK)
+        return fail(c, LBM_EINVAL, "unknown z boundary");
+    if (d->kernel < LBM_KERNEL_AUTO || d->kernel > LBM_KERNEL_TWO_PASS) return fail(c, LBM_EINVAL, "unknown kernel");
+    if (d->rows_per_warp < 0 || d->rows_per_warp > 65536) return fail(c, LBM_EINVAL, "rows_per_warp out of range");
+    if (d->device < 0) return fail(c, LBM_EINVAL, "negative device ordinal");
+    return LBM_OK;
+}
+
+static int check_params(lbm_ctx* c, const lbm_params* p, int ns) {
+    if (!p) return fail(c, LBM_EINVAL, "params is NULL");
+    for (int s = 0; s < ns; ++s) {
+        if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) return fail(c, LBM_EINVAL, "tau[%d] must be > 1/2", s);
+        if (!std::isfinite(p->G1[s]) || !std::isfinite(p->G2[s])) return fail(c, LBM_EINVAL, "G1/G2 not finite");
+        if (p->psi_form == LBM_PSI_EXP && !(p->rho0[s] > 0.0 && std::isfinite(p->rho0[s])))
+            return fail(c, LBM_EINVAL, "rho0[%d] must be > 0", s);
+        if (!std::isfinite(p->rho_ref[s])) return fail(c, LBM_EINVAL, "rho_ref not finite");
+    }
+    if (p->psi_form != LBM_PSI_EXP && p->psi_form != LBM_PSI_RHO) return fail(c, LBM_EINVAL, "unknown psi form");
+    if (p->weight_preset != LBM_WEIGHTS_PAPER && p->weight_preset != LBM_WEIGHTS_CHEM09)
+        return fail(c, LBM_EINVAL, "unknown weight preset");
+    if (p->psi_wall != LBM_WALL_MIRROR && p->psi_wall != LBM_WALL_ZERO) return fail(c, LBM_EINVAL, "unknown psi_wall");
+    if (!(p->weight_norm > 0.0) || !std::isfinite(p->weight_norm)) return fail(c, LBM_EINVAL, "weight_norm must be > 0");
+    if (!std::isfinite(p->G_AB) || !std::isfinite(p->body_force) || !std::isfinite(p->wall_u[0]) ||
+        !std::isfinite(p->wall_u[1]))
+        return fail(c, LBM_EINVAL, "G_AB, body_force, wall_u must be finite");
+    return LBM_OK;
+}
+
+extern "C" int lbm_validate_desc(const lbm_desc* d) { return check_desc(nullptr, d); }
+extern "C" int lbm_validate_params(const lbm_params* p, int n_species) {
+    if (n_species != 1 && n_species != 2) return fail(nullptr, LBM_EINVAL, "n_species must be 1 or 2");
+    return check_params(nullptr, p, n_species);
+}
+
+// ---------------------------------------------------------------------------------------
+// Creation
+// ---------------------------------------------------------------------------------------
+static void release(lbm_ctx* c) {
+    if (!c) return;
+    if (c->d.device >= 0) cudaSetDevice(c->d.device);
+    drop_graphs(c);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    void* ptrs[] = {c->f[0], c->f[1], c->part_row, c->part_col, c->row_sum, c->col_sum, c->ticket,
+                    c->flag, c->out,  c->avg,  c->staging,  c->fexport,  c->gfield};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->host_out) cudaFreeHost(c->host_out);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+static int choose_hz(const lbm_ctx* c) {
+    if (c->d.rows_per_warp > 0) return c->d.rows_per_warp < c->d.nz ? c->d.rows_per_warp : c->d.nz;
+    const long long strips = (c->d.nx + STRIP_W - 1) / STRIP_W;
+    const long long target = (long long)(c->nsm > 0 ? c->nsm : 152) * 16;  // warps in flight
+    long long hz = (c->d.nz * strips + target - 1) / target;
+    if (hz < 8) hz = 8;
+    if (hz > c->d.nz) hz = c->d.nz;
+    return (int)hz;
+}
+
+extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_desc(nullptr, d);
+    if (rc) return rc;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    c->d = *d;
+    lbm_default_params(&c->p);
+    auto bail = [&](int code) {
+        g_create_error = c->err;
+        release(c);
+        delete c;
+        return code;
+    };
+#define CKC(call)                                                                                          \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            return bail(fail(c, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", #call, \
+                             cudaGetErrorString(e_)));                                                     \
+    } while (0)
+    int ndev = 0;
+    CKC(cudaGetDeviceCount(&ndev));
+    if (d->device >= ndev) return bail(fail(c, LBM_EINVAL, "device %d not present (%d devices)", d->device, ndev));
+    CKC(cudaSetDevice(d->device));
+    cudaDeviceProp prop;
+    CKC(cudaGetDeviceProperties(&prop, d->device));
+    c->nsm = prop.multiProcessorCount;
+    if (d->stream) {
+        c->stream = (cudaStream_t)d->stream;
+    } else {
+        CKC(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    const int nx = d->nx, nz = d->nz, ns = d->n_species;
+    c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+    c->pitch = (nx + 31) / 32 * 32;
+    c->plane = (long long)nz * c->pitch;
+    c->kernel = d->kernel == LBM_KERNEL_TWO_PASS ? LBM_KERNEL_TWO_PASS : LBM_KERNEL_FUSED;
+    const size_t fbytes = (size_t)ns * 9 * c->plane * c->esize;
+    CKC(cudaMalloc(&c->f[0], fbytes));
+    CKC(cudaMalloc(&c->f[1], fbytes));
+    CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->stream));
+    CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->stream));
+    // fused geometry and partial-sum groups
+    c->geom.nstrips = (nx + STRIP_W - 1) / STRIP_W;
+    c->geom.hz = choose_hz(c);
+    c->geom.nchunks = (nz + c->geom.hz - 1) / c->geom.hz;
+    const int tx = (nx + TPX - 1) / TPX, tz = (nz + TPZ - 1) / TPZ;
+    const long long rows_parts = std::max(c->geom.nstrips, tx);
+    const long long col_parts = std::max(c->geom.nchunks, tz);
+    CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * sizeof(double)));
+    CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * sizeof(double)));
+    CKC(cudaMalloc(&c->row_sum, (size_t)nz * NQR * sizeof(double)));
+    CKC(cudaMalloc(&c->col_sum, (size_t)nx * NQC * sizeof(double)));
+    CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
+    CKC(cudaMalloc(&c->flag, sizeof(int)));
+    const size_t olen = (size_t)obs_len(nx, nz) * sizeof(double);
+    CKC(cudaMalloc(&c->out, olen));
+    CKC(cudaMalloc(&c->avg, olen));
+    CKC(cudaMalloc(&c->staging, (size_t)(ns + 2) * nx * nz * sizeof(double)));
+    CKC(cudaMallocHost(&c->host_out, olen));
+    CKC(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->stream));
+    CKC(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CKC(cudaMemsetAsync(c->avg, 0, olen, c->stream));
+    if (c->kernel == LBM_KERNEL_TWO_PASS) {
+        c->ghost.gpitch = (nx + 2 * GX + 3) / 4 * 4;
+        c->ghost.gplane = (long long)(nz + 4) * c->ghost.gpitch;
+        CKC(cudaMalloc(&c->gfield, (size_t)2 * ns * c->ghost.gplane * c->esize));
+        CKC(cudaMemsetAsync(c->gfield, 0, (size_t)2 * ns * c->ghost.gplane * c->esize, c->stream));
+    }
+    CKC(cudaStreamSynchronize(c->stream));
+#undef CKC
+    refresh_const(c);
+    *out = c;
+    return LBM_OK;
+}
+
+extern "C" void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release(c);
+    delete c;
+}
+
+extern "C" int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
+    if (!c) return LBM_EINVAL;
+    int rc = check_params(c, p, c->d.n_species);
+    if (rc) return rc;
+    c->p = *p;
+    c->have_params = true;
+    refresh_const(c);
+    drop_graphs(c);
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Step kernels
+// ---------------------------------------------------------------------------------------
+static ObsPtrs obs_ptrs(const lbm_ctx* c) {
+    ObsPtrs O;
+    O.part_row = c->part_row;
+    O.part_col = c->part_col;
+    O.fields = c->staging;
+    O.flag = c->flag;
+    return O;
+}
+
+// One pass of the step kernel over the state in f[cur] (mode: M_WRITE into f[cur^1],
+// M_OBS partial sums, M_FIELDS per-site fields), plus the reduction when M_OBS.
+static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool accumulate) {
+    const ObsPtrs O = obs_ptrs(c);
+    cudaError_t e;
+    const bool timed = c->profiling && (mode & M_WRITE);
+    if (timed) {
+        if (c->ev_used + 2 > c->ev.size()) {
+            for (int k = 0; k < 64; ++k) {
+                cudaEvent_t ev;
+                e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return e;
+                c->ev.push_back(ev);
+            }
+        }
+        e = cudaEventRecord(c->ev[c->ev_used], c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (c->d.precision == LBM_FP64)
+        e = launch_fused<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64,
+                                 c->geom, O, c->stream);
+    else
+        e = launch_fused<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32,
+                                c->geom, O, c->stream);
+    c->launches += 1;
+    if (e != cudaSuccess) return e;
+    if (timed) {
+        e = cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+        if (e != cudaSuccess) return e;
+        c->ev_used += 2;
+    }
+    if (reduce) {
+        e = launch_reduce(O, c->geom.nstrips, c->geom.nchunks, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
+                          c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
+        c->launches += 1;
+    }
+    return e;
+}
+
+static bool observe_now(const lbm_ctx* c, long long step) {
+    return c->observe_every > 0 && step % c->observe_every == 0;
+}
+
+extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c || nsteps < 0) return c ? fail(c, LBM_EINVAL, "nsteps < 0") : LBM_EINVAL;
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    int left = nsteps;
+    const int G = c->graph_steps;
+    const bool graphable = !c->profiling && (c->observe_every == 0 || c->observe_every == 1);
+    while (left > 0) {
+        if (graphable && left >= G) {
+            const int ob = c->observe_every == 1 ? 1 : 0;
+            cudaGraphExec_t& ge = c->graph[c->cur][ob];
+            if (!ge) {
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                const long long saved = c->launches;
+                cudaError_t e = cudaSuccess;
+                for (int i = 0; i < G && e == cudaSuccess; ++i)
+                    e = enqueue_pass(c, (c->cur + i) & 1, M_WRITE | (ob ? M_OBS : 0), ob, ob);
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                c->launches = saved;
+                CK(e);
+                CK(e2);
+                e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                CK(e);
+            }
+            CK(cudaGraphLaunch(ge, c->stream));
+            c->launches += (long long)G * (ob ? 2 : 1);
+            c->step += G;  // G is even: the parity of cur is unchanged
+            left -= G;
+            continue;
+        }
+        const bool ob = observe_now(c, c->step);
+        CK(enqueue_pass(c, c->cur, M_WRITE | (ob ? M_OBS : 0), ob, ob));
+        c->cur ^= 1;
+        c->step += 1;
+        left -= 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_observe(lbm_ctx* c, int every) {
+    if (!c) return LBM_EINVAL;
+    if (every < 0) return fail(c, LBM_EINVAL, "every must be >= 0");
+    CK(cudaSetDevice(c->d.device));
+    c->observe_every = every;
+    CK(cudaMemsetAsync(c->avg, 0, (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double), c->stream));
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fields
+// ---------------------------------------------------------------------------------------
+extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, int where) {
+    if (!c) return LBM_EINVAL;
+    if (!rho) return fail(c, LBM_EINVAL, "rho is NULL");
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
+    CK(cudaSetDevice(c->d.device));
+    const int ns = c->d.n_species;
+    const long long n = (long long)c->d.nx * c->d.nz;
+    // validation and the reference densities need the values on the host
+    std::vector<double> h;
+    const double* hr = rho;
+    if (where == LBM_DEVICE) {
+        h.resize((size_t)ns * n);
+        CK(cudaMemcpyAsync(h.data(), rho, (size_t)ns * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        hr = h.data();
+    }
+    for (int s = 0; s < ns; ++s) {
+        double sum = 0.0;
+        for (long long i = 0; i < n; ++i) {
+            const double v = hr[s * n + i];
+            if (!(v > 0.0) || !std::isfinite(v)) return fail(c, LBM_EINVAL, "rho[%d][%lld] = %g is not > 0", s, i, v);
+            sum += v;
+        }
+        c->rho_ref[s] = c->d.precision == LBM_FP64 ? 0.0 : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : sum / n);
+    }
+    const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(c->staging, rho, (size_t)ns * n * sizeof(double), kind, c->stream));
+    const double* du = nullptr;
+    if (u) {
+        CK(cudaMemcpyAsync(c->staging + ns * n, u, (size_t)2 * n * sizeof(double), kind, c->stream));
+        du = c->staging + ns * n;
+    }
+    refresh_const(c);
+    drop_graphs(c);
+    c->cur = 0;
+    if (c->d.precision == LBM_FP64)
+        CK(launch_init<double>(ns, (double*)c->f[0], c->staging, du, c->c64, c->stream));
+    else
+        CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->stream));
+    c->launches += 1;
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->avg, 0, (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = 0;
+    c->have_fields = true;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int where) {
+    if (!c) return LBM_EINVAL;
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
+    CK(cudaSetDevice(c->d.device));
+    const int ns = c->d.n_species;
+    const long long n = (long long)c->d.nx * c->d.nz;
+    const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (rho || u) {
+        CK(enqueue_pass(c, c->cur, M_FIELDS, false, false));
+        if (rho) CK(cudaMemcpyAsync(rho, c->staging, (size_t)ns * n * sizeof(double), kind, c->stream));
+        if (u) CK(cudaMemcpyAsync(u, c->staging + ns * n, (size_t)2 * n * sizeof(double), kind, c->stream));
+    }
+    if (f) {
+        if (!c->fexport) CK(cudaMalloc(&c->fexport, (size_t)ns * 9 * n * sizeof(double)));
+        if (c->d.precision == LBM_FP64)
+            CK(launch_export<double>(ns, (const double*)c->f[c->cur], c->fexport, c->c64, c->stream));
+        else
+            CK(launch_export<float>(ns, (const float*)c->f[c->cur], c->fexport, c->c32, c->stream));
+        c->launches += 1;
+        CK(cudaMemcpyAsync(f, c->fexport, (size_t)ns * 9 * n * sizeof(double), kind, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Observables
+// ---------------------------------------------------------------------------------------
+static void unpack(const lbm_ctx* c, const double* buf, lbm_obs* o, double scale) {
+    const int nx = c->d.nx, nz = c->d.nz, ns = c->d.n_species;
+    o->mass[0] = buf[O_MASS] * scale;
+    o->mass[1] = ns == 2 ? buf[O_MASS + 1] * scale : 0.0;
+    o->momentum[0] = buf[O_MOM] * scale;
+    o->momentum[1] = buf[O_MOM + 1] * scale;
+    o->gamma = buf[O_GAMMA] * scale;
+    o->wall_force[0] = buf[O_WALL] * scale;
+    o->wall_force[1] = buf[O_WALL + 1] * scale;
+    o->nonfinite = buf[O_BAD] != 0.0;
+    o->step = c->step;
+    const double* ux = buf + O_PROF;
+    const double* rz = ux + nz;
+    const double* sx = rz + 2LL * nz;
+    const double* fl = sx + nz;
+    const double* ps = fl + nz;
+    const double* px = ps + nx;
+    for (int z = 0; z < nz; ++z) {
+        if (o->ux_z) o->ux_z[z] = ux[z] * scale;
+        if (o->sxz_z) o->sxz_z[z] = sx[z] * scale;
+        if (o->fluid_z) o->fluid_z[z] = fl[z] * scale;
+        if (o->rho_z)
+            for (int s = 0; s < ns; ++s) o->rho_z[s * nz + z] = rz[s * nz + z] * scale;
+    }
+    for (int x = 0; x < nx; ++x) {
+        if (o->ps_x) o->ps_x[x] = ps[x] * scale;
+        if (o->pxx_x) o->pxx_x[x] = px[x] * scale;
+    }
+}
+
+extern "C" int lbm_observables(lbm_ctx* c, lbm_obs* o) {
+    if (!c) return LBM_EINVAL;
+    if (!o) return fail(c, LBM_EINVAL, "out is NULL");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    CK(enqueue_pass(c, c->cur, M_OBS, true, false));
+    const size_t olen = (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double);
+    CK(cudaMemcpyAsync(c->host_out, c->out, olen, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    unpack(c, c->host_out, o, 1.0);
+    o->samples = 1;
+    return o->nonfinite ? fail(c, LBM_ENONFINITE, "state holds a density <= 0, NaN or Inf") : LBM_OK;
+}
+
+extern "C" int lbm_averages(lbm_ctx* c, lbm_obs* o, int reset) {
+    if (!c) return LBM_EINVAL;
+    if (!o) return fail(c, LBM_EINVAL, "out is NULL");
+    CK(cudaSetDevice(c->d.device));
+    const size_t olen = (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double);
+    CK(cudaMemcpyAsync(c->host_out, c->avg, olen, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double n = c->host_out[O_COUNT];
+    unpack(c, c->host_out, o, n > 0 ? 1.0 / n : 0.0);
+    o->nonfinite = c->host_out[O_BAD] != 0.0;
+    o->samples = (long long)n;
+    if (reset) CK(cudaMemsetAsync(c->avg, 0, olen, c->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_synchronize(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    CK(cudaSetDevice(c->d.device));
+    CK(cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 1) return fail(c, LBM_ENONFINITE, "a step met a density <= 0, NaN or Inf");
+    return LBM_OK;
+}
+
+extern "C" long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : -1; }
+
+extern "C" int lbm_profile(lbm_ctx* c, int enable) {
+    if (!c) return LBM_EINVAL;
+    CK(cudaSetDevice(c->d.device));
+    CK(cudaStreamSynchronize(c->stream));
+    c->profiling = enable != 0;
+    c->ev_used = 0;
+    return LBM_OK;
+}
+
+extern "C" int lbm_profile_read(lbm_ctx* c, double* ms, long long* n) {
+    if (!c) return LBM_EINVAL;
+    CK(cudaSetDevice(c->d.device));
+    CK(cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (n) *n = (long long)(c->ev_used / 2);
+    return LBM_OK;
+}
+
+extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+extern "C" int lbm_abi_version(void) { return LBM_ABI_VERSION; }

@@ -1,0 +1,288 @@
+// lbm_core.cuh -- per-site arithmetic of the multirange Shan-Chen lattice Boltzmann step
+// (Sbragaglia, Benzi, Bernaschi, Succi, arXiv:1402.6019), shared by every step kernel.
+//
+// Everything here is __host__ __device__ and free of CUDA intrinsics so the same arithmetic
+// can be compiled for the host.  Kernels gather the neighbourhood values (by warp shuffles
+// or from shared memory) and call these functions.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define LBM_HD __host__ __device__ __forceinline__
+#else
+#define LBM_HD inline
+#endif
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------------------
+// Lattice.  D2Q9 velocities in the order c0 = (0,0), c1 = (1,0), c2 = (0,1), c3 = (-1,0),
+// c4 = (0,-1), c5 = (1,1), c6 = (-1,1), c7 = (-1,-1), c8 = (1,-1): c1..c8 are also the
+// first interaction belt, and Appendix A's pair terms (c13 = c5 - c3 = c1 - c7, ...) hold.
+// ---------------------------------------------------------------------------------------
+LBM_HD constexpr int cx(int l) { return l == 1 || l == 5 || l == 8 ? 1 : (l == 3 || l == 6 || l == 7 ? -1 : 0); }
+LBM_HD constexpr int cz(int l) { return l == 2 || l == 5 || l == 6 ? 1 : (l == 4 || l == 7 || l == 8 ? -1 : 0); }
+LBM_HD constexpr int opp(int l) { return l == 0 ? 0 : (l <= 4 ? (l + 1) % 4 + 1 : (l - 5 + 2) % 4 + 5); }
+// rest weights of D2Q9: 4/9, 1/9 (axis), 1/36 (diagonal)
+template <typename T> LBM_HD constexpr T wlb(int l) { return l == 0 ? T(4) / T(9) : (l <= 4 ? T(1) / T(9) : T(1) / T(36)); }
+
+// Per-step constants, passed to kernels by value (they live in the kernel-parameter
+// constant bank).  Force tables are indexed by the neighbour offset (dz + 2) * 5 + dx + 2.
+template <typename T>
+struct StepConst {
+    int nx, nz, pitch, ns;
+    int zbc;        // 0 periodic, 1 bounce-back walls
+    int psi_form;   // 0 psi = 1 - exp(-rho/rho0), 1 psi = rho
+    int psi_wall;   // 0 mirror, 1 zero
+    int pad0;
+    long long plane;          // elements of one population plane (nz * pitch)
+    T omega[2], tau[2], rho_ref[2], inv_rho0[2], rho0[2];
+    T g;                      // body acceleration along x
+    T wall_u[2];              // bottom, top wall velocity (x)
+    T kx[2][25], kz[2][25];   // K_s(|c|^2) c for the intra-species force
+    T sq[2][9];               // App. A shell prefactors x K_s by |c|^2
+    T kcx[9], kcz[9];         // G_AB w8(|c|^2) c for the cross force, (dz+1)*3 + dx+1
+    T sc[3];                  // G_AB w8(|c|^2) / 2 for the cross stress, by |c|^2 = 1, 2
+    T kin[2];                 // (tau_s - 1/2)^2 of the Sec. III stress
+};
+
+// Pseudopotential of Sec. IV, psi = 1 - exp(-rho/rho0) (or psi = rho).  FP32 uses expm1 to
+// keep the relative accuracy of small psi.
+LBM_HD float psi_of(const StepConst<float>& C, int s, float rho) {
+    return C.psi_form == 1 ? rho : -expm1f(-rho * C.inv_rho0[s]);
+}
+LBM_HD double psi_of(const StepConst<double>& C, int s, double rho) {
+    return C.psi_form == 1 ? rho : 1.0 - exp(-rho / C.rho0[s]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Eq. FORCE: F = -psi(x) sum_{l=1..24} K(|c_l|^2) psi(x + c_l) c_l, with
+// K = G1 w + G2 p folded into the tables kx/kz.  p[dz+2][dx+2] = psi(x+dx, z+dz).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+LBM_HD void intra_force(const StepConst<T>& C, int s, const T (&p)[5][5], T& fx, T& fz) {
+    T ax = T(0), az = T(0);
+#pragma unroll
+    for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) {
+            if (dx == 0 && dz == 0) continue;
+            const int i = (dz + 2) * 5 + dx + 2;
+            if (dx != 0) ax += C.kx[s][i] * p[dz + 2][dx + 2];
+            if (dz != 0) az += C.kz[s][i] * p[dz + 2][dx + 2];
+        }
+    fx = -p[2][2] * ax;
+    fz = -p[2][2] * az;
+}
+
+// ---------------------------------------------------------------------------------------
+// Appendix A: interaction stress of one species, shells |c|^2 = 1, 2 (node products),
+// 4 and 8 (node and half-link products), 5 (node products and the c13..c16 pair terms).
+// sq[q] already holds (1/2 or 1/4) * (G1 w(q) + G2 p(q)).  Adds into (sxx, szz, sxz).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+LBM_HD void intra_stress(const StepConst<T>& C, int s, const T (&p)[5][5], T& sxx, T& szz, T& sxz) {
+#define LBM_P(dx, dz) p[(dz) + 2][(dx) + 2]
+    const T p0 = LBM_P(0, 0);
+    const T* q = C.sq[s];
+    // |c|^2 = 1
+    sxx += q[1] * p0 * (LBM_P(1, 0) + LBM_P(-1, 0));
+    szz += q[1] * p0 * (LBM_P(0, 1) + LBM_P(0, -1));
+    // |c|^2 = 2
+    {
+        const T d = LBM_P(1, 1) + LBM_P(-1, -1), a = LBM_P(-1, 1) + LBM_P(1, -1);
+        sxx += q[2] * p0 * (d + a);
+        szz += q[2] * p0 * (d + a);
+        sxz += q[2] * p0 * (d - a);
+    }
+    // |c|^2 = 4: node products and half-link products psi(x - c/2) psi(x + c/2)
+    sxx += T(4) * q[4] * (p0 * (LBM_P(2, 0) + LBM_P(-2, 0)) + T(2) * LBM_P(-1, 0) * LBM_P(1, 0));
+    szz += T(4) * q[4] * (p0 * (LBM_P(0, 2) + LBM_P(0, -2)) + T(2) * LBM_P(0, -1) * LBM_P(0, 1));
+    // |c|^2 = 5: node products over the 8 links (+-2,+-1), (+-1,+-2)
+    {
+        const T a21 = LBM_P(2, 1) + LBM_P(-2, -1), b21 = LBM_P(-2, 1) + LBM_P(2, -1);
+        const T a12 = LBM_P(1, 2) + LBM_P(-1, -2), b12 = LBM_P(-1, 2) + LBM_P(1, -2);
+        sxx += q[5] * p0 * (T(4) * (a21 + b21) + (a12 + b12));
+        szz += q[5] * p0 * ((a21 + b21) + T(4) * (a12 + b12));
+        sxz += q[5] * p0 * (T(2) * (a21 - b21) + T(2) * (a12 - b12));
+        // pair terms: links c13 = (2,1), c14 = (1,2), c15 = (-1,2), c16 = (-2,1)
+        const T t13 = LBM_P(1, 1) * LBM_P(-1, 0) + LBM_P(1, 0) * LBM_P(-1, -1);
+        const T t14 = LBM_P(1, 1) * LBM_P(0, -1) + LBM_P(0, 1) * LBM_P(-1, -1);
+        const T t15 = LBM_P(0, 1) * LBM_P(1, -1) + LBM_P(-1, 1) * LBM_P(0, -1);
+        const T t16 = LBM_P(-1, 1) * LBM_P(1, 0) + LBM_P(-1, 0) * LBM_P(1, -1);
+        sxx += q[5] * (T(4) * t13 + t14 + t15 + T(4) * t16);
+        szz += q[5] * (t13 + T(4) * t14 + T(4) * t15 + t16);
+        sxz += q[5] * (T(2) * t13 + T(2) * t14 - T(2) * t15 - T(2) * t16);
+    }
+    // |c|^2 = 8: node and half-link products over (+-2,+-2)
+    {
+        const T a22 = LBM_P(2, 2) + LBM_P(-2, -2), b22 = LBM_P(-2, 2) + LBM_P(2, -2);
+        const T ha = T(2) * LBM_P(-1, -1) * LBM_P(1, 1), hb = T(2) * LBM_P(-1, 1) * LBM_P(1, -1);
+        sxx += T(4) * q[8] * (p0 * (a22 + b22) + ha + hb);
+        szz += T(4) * q[8] * (p0 * (a22 + b22) + ha + hb);
+        sxz += T(4) * q[8] * (p0 * (a22 - b22) + ha - hb);
+    }
+#undef LBM_P
+}
+
+// ---------------------------------------------------------------------------------------
+// Sec. IV cross repulsion (first belt, rho as the cross pseudopotential):
+// F_A += -G_AB rho_A(x) sum_l w8 rho_B(x+c_l) c_l, and A <-> B.  r?[dz+1][dx+1].
+// ---------------------------------------------------------------------------------------
+template <typename T>
+LBM_HD void cross_force(const StepConst<T>& C, const T (&ra)[3][3], const T (&rb)[3][3], T (&F)[2][2]) {
+    T ax = T(0), az = T(0), bx = T(0), bz = T(0);
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dz == 0) continue;
+            const int i = (dz + 1) * 3 + dx + 1;
+            if (dx != 0) {
+                ax += C.kcx[i] * rb[dz + 1][dx + 1];
+                bx += C.kcx[i] * ra[dz + 1][dx + 1];
+            }
+            if (dz != 0) {
+                az += C.kcz[i] * rb[dz + 1][dx + 1];
+                bz += C.kcz[i] * ra[dz + 1][dx + 1];
+            }
+        }
+    F[0][0] -= ra[1][1] * ax;
+    F[0][1] -= ra[1][1] * az;
+    F[1][0] -= rb[1][1] * bx;
+    F[1][1] -= rb[1][1] * bz;
+}
+
+// Cross-species stress, by analogy with App. A's first-belt shells: the pair product
+// psi(x) psi(x+c) becomes rho_A(x) rho_B(x+c) + rho_B(x) rho_A(x+c).
+template <typename T>
+LBM_HD void cross_stress(const StepConst<T>& C, const T (&ra)[3][3], const T (&rb)[3][3], T& sxx, T& szz, T& sxz) {
+    const T a0 = ra[1][1], b0 = rb[1][1];
+#define LBM_PHI(dx, dz) (a0 * rb[(dz) + 1][(dx) + 1] + b0 * ra[(dz) + 1][(dx) + 1])
+    const T s1x = LBM_PHI(1, 0) + LBM_PHI(-1, 0), s1z = LBM_PHI(0, 1) + LBM_PHI(0, -1);
+    const T d = LBM_PHI(1, 1) + LBM_PHI(-1, -1), a = LBM_PHI(-1, 1) + LBM_PHI(1, -1);
+#undef LBM_PHI
+    sxx += C.sc[1] * s1x + C.sc[2] * (d + a);
+    szz += C.sc[1] * s1z + C.sc[2] * (d + a);
+    sxz += C.sc[2] * (d - a);
+}
+
+// ---------------------------------------------------------------------------------------
+// Moments of Sec. II on stored values (deviations from W_l rho_ref, or plain values with
+// rho_ref = 0): drho = sum f, j = sum f c.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+LBM_HD T sum9(const T (&f)[9]) {
+    return f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+}
+template <typename T>
+LBM_HD void momentum9(const T (&f)[9], T& jx, T& jz) {
+    jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    jz = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+}
+
+// Equilibrium of Sec. II as a deviation from W_l rho_ref: W_l [drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)].
+template <typename T>
+LBM_HD T feq_dev(int l, T drho, T rho, T ux, T uz) {
+    const T cu = T(cx(l)) * ux + T(cz(l)) * uz;
+    const T usq = ux * ux + uz * uz;
+    return wlb<T>(l) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+}
+
+// Shifted-velocity BGK collision of all species at one site (Eq. LB with u_eq = u' + tau F /
+// rho, u' the common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s).  f is overwritten with the
+// post-collision values.  rho[s] is the full density, drho[s] the stored-sum.
+template <typename T, int NS>
+LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], const T (&rho)[NS],
+                    const T (&F)[NS][2]) {
+    T jx[NS], jz[NS];
+    T nx_ = T(0), nz_ = T(0), den = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        momentum9(f[s], jx[s], jz[s]);
+        nx_ += C.omega[s] * jx[s];
+        nz_ += C.omega[s] * jz[s];
+        den += C.omega[s] * rho[s];
+    }
+    const T upx = nx_ / den, upz = nz_ / den;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const T ir = T(1) / rho[s];
+        const T ux = upx + C.tau[s] * F[s][0] * ir;
+        const T uz = upz + C.tau[s] * F[s][1] * ir;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            const T fe = feq_dev<T>(l, drho[s], rho[s], ux, uz);
+            f[s][l] = f[s][l] + C.omega[s] * (fe - f[s][l]);
+        }
+    }
+}
+
+// Ladd's moving-wall bounce-back value for a population g_l (l pointing into a wall that
+// moves with velocity uw along x): g_l - 2 W_l rho (c_l . U_w) / c_s^2.
+template <typename T>
+LBM_HD T bounce(int l, T g, T rho, T uw) {
+    return g - T(6) * wlb<T>(l) * rho * T(cx(l)) * uw;
+}
+
+// Per-site observables that need the populations (before collision): the barycentric
+// velocity and the kinetic shear stress.  Returns (ux, uz, kinetic xz momentum flux).
+template <typename T, int NS>
+LBM_HD void site_kinetics(const StepConst<T>& C, const T (&f)[NS][9], const T (&drho)[NS], const T (&rho)[NS],
+                          const T (&F)[NS][2], T& ux, T& uz, T& pixz, T& rtot, T& mx, T& mz) {
+    mx = T(0);
+    mz = T(0);
+    rtot = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        T jx, jz;
+        momentum9(f[s], jx, jz);
+        mx += jx + T(0.5) * F[s][0];
+        mz += jz + T(0.5) * F[s][1];
+        rtot += rho[s];
+    }
+    ux = mx / rtot;
+    uz = mz / rtot;
+    // (1 - 1/(2 tau)) sum_l (f_l - feq_l(rho_s, u)) c_lx c_lz + rho u_x u_z
+    T visc = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        T m = T(0);
+#pragma unroll
+        for (int l = 5; l <= 8; ++l) {
+            const T d = f[s][l] - feq_dev<T>(l, drho[s], rho[s], ux, uz);
+            m += T(cx(l) * cz(l)) * d;
+        }
+        visc += (T(1) - T(0.5) * C.omega[s]) * m;
+    }
+    pixz = visc + rtot * ux * uz;
+}
+
+// Index helpers.
+LBM_HD int wrap_index(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+// Reflection of a row index about the walls at z = -1/2 and z = n - 1/2.
+LBM_HD int mirror_index(int z, int n) {
+    int m = z % (2 * n);
+    if (m < 0) m += 2 * n;
+    return m >= n ? 2 * n - 1 - m : m;
+}
+
+// Row whose density stands at row r: periodic wrap, or with walls the mirror image (or -1
+// for the zero ghost reading).
+template <typename T>
+LBM_HD int source_row(const StepConst<T>& C, int r) {
+    if (C.zbc == 0) return wrap_index(r, C.nz);
+    if (r >= 0 && r < C.nz) return r;
+    return C.psi_wall == 1 ? -1 : mirror_index(r, C.nz);
+}
+
+// Observable partial sums: per row (summed over x) and per column (summed over z).
+enum { QR_UX = 0, QR_RHOA, QR_RHOB, QR_SXZ, QR_MX, QR_MZ, QR_WALLB, QR_WALLT, NQR };
+enum { QC_PS = 0, QC_PXX, NQC };
+
+}  // namespace lbm

@@ -1,0 +1,65 @@
+// lbm_internal.h -- declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_core.cuh"
+
+namespace lbm {
+
+// Kernel modes (bit set).
+enum { M_WRITE = 1, M_OBS = 2, M_FIELDS = 4 };
+
+// Width of the strip a warp owns in the fused sweep: 32 lanes minus a 2-column halo on
+// each side (the reach of the 5x5 interaction stencil).
+constexpr int STRIP_W = 28;
+
+struct SweepGeom {
+    int nstrips;  // ceil(nx / STRIP_W)
+    int nchunks;  // ceil(nz / hz)
+    int hz;       // rows swept by one warp
+};
+
+// Output pointers of the step kernels (device memory).
+struct ObsPtrs {
+    double* part_row;  // [nxpart][nz][NQR]   per-row sums over a group of columns
+    double* part_col;  // [nzpart][nx][NQC]   per-column sums over a group of rows
+    double* fields;    // [ns + 2][nz][nx]    rho_s, u_x, u_z (M_FIELDS)
+    int* flag;         // bit 0: a density <= 0 / NaN / Inf was met
+};
+
+// Two-pass layout: densities and pseudopotentials with ghost cells (2 rows above and
+// below, GX columns left and right), pitch gpitch elements, one plane per field.
+constexpr int GX = 4;
+struct GhostGeom {
+    int gpitch;           // >= nx + 2 GX, multiple of 4 (16-byte rows for TMA)
+    long long gplane;     // (nz + 4) * gpitch
+};
+
+// Observable output layout (doubles) written by the reduction kernel.
+enum { O_MASS = 0, O_MOM = 2, O_GAMMA = 4, O_WALL = 5, O_BAD = 7, O_COUNT = 8, O_PROF = 16 };
+LBM_HD long long obs_len(int nx, int nz) { return O_PROF + 5LL * nz + 2LL * nx; }
+
+// Launchers (return the launch error).
+template <typename T>
+cudaError_t launch_fused(int ns, int mode, const T* fin, T* fout, const StepConst<T>& C, const SweepGeom& G,
+                         const ObsPtrs& O, cudaStream_t st);
+template <typename T>
+cudaError_t launch_density(int ns, const T* f, T* gfield, const StepConst<T>& C, const GhostGeom& GG,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_twopass(int ns, int mode, const T* fin, T* fout, const T* gfield, const StepConst<T>& C,
+                           const GhostGeom& GG, const void* tmap, const ObsPtrs& O, int nxpart, int nzpart,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, cudaStream_t st);
+template <typename T>
+cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, cudaStream_t st);
+cudaError_t launch_reduce(const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc, double* row_sum,
+                          double* col_sum, unsigned* ticket, double* out, double* avg, int accumulate,
+                          cudaStream_t st);
+
+// Twopass tile (threads per CTA: TPX x TPZ sites).
+constexpr int TPX = 32, TPZ = 8;
+
+}  // namespace lbm

@@ -1,0 +1,195 @@
+// lbm_obs.cu -- initial state, state export and the FP64 reduction of the observables.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+// Populations at the equilibrium of Sec. II for given rho, u (stored as deviations from
+// W_l rho_ref; rho_ref = 0 stores plain values).  The arithmetic is done in FP64.
+template <typename T>
+__global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho, const double* __restrict__ u,
+                       const StepConst<T> C) {
+    const long long n = (long long)C.nx * C.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % C.nx), z = (int)(i / C.nx);
+        const double ux = u ? u[i] : 0.0, uz = u ? u[n + i] : 0.0;
+        for (int s = 0; s < ns; ++s) {
+            const double r = rho[s * n + i];
+            const double dr = r - (double)C.rho_ref[s];
+            for (int l = 0; l < 9; ++l)
+                f[(s * 9 + l) * C.plane + (long long)z * C.pitch + x] = (T)feq_dev<double>(l, dr, r, ux, uz);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ out, const StepConst<T> C) {
+    const long long n = (long long)C.nx * C.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % C.nx), z = (int)(i / C.nx);
+        for (int s = 0; s < ns; ++s)
+            for (int l = 0; l < 9; ++l)
+                out[(s * 9 + l) * n + i] = (double)f[(s * 9 + l) * C.plane + (long long)z * C.pitch + x] +
+                                           wlb<double>(l) * (double)C.rho_ref[s];
+    }
+}
+
+__device__ double block_sum(double v, double* sh) {
+    // deterministic: fixed tree over the block
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) sh[t] += sh[t + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+constexpr int RB_THREADS = 256;
+
+// Phase 1: rows (one warp per row, summing the column groups) and columns (one thread per
+// column, summing the row groups).  Phase 2 (last block to finish): profiles, scalars,
+// fluidity and the optional time sums.  All sums run in a fixed order: repeatable results.
+__global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
+                                                       int nrowblocks, double* __restrict__ row_sum,
+                                                       double* __restrict__ col_sum, unsigned* ticket,
+                                                       double* __restrict__ out, double* __restrict__ avg,
+                                                       int accumulate) {
+    __shared__ double sh[RB_THREADS];
+    __shared__ bool last;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if ((int)blockIdx.x < nrowblocks) {
+        const int z = blockIdx.x * (RB_THREADS / 32) + warp;
+        if (z < nz) {
+            for (int k = 0; k < NQR; ++k) {
+                double v = 0.0;
+                for (int p = lane; p < nxpart; p += 32) v += O.part_row[((long long)p * nz + z) * NQR + k];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) row_sum[(long long)z * NQR + k] = v;
+            }
+        }
+    } else {
+        const int x = (blockIdx.x - nrowblocks) * RB_THREADS + t;
+        if (x < nx)
+            for (int k = 0; k < NQC; ++k) {
+                double v = 0.0;
+                for (int p = 0; p < nzpart; ++p) v += O.part_col[((long long)p * nx + x) * NQC + k];
+                col_sum[(long long)x * NQC + k] = v;
+            }
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+
+    double* ux = out + O_PROF;
+    double* rz = ux + nz;
+    double* sx = rz + 2LL * nz;
+    double* fl = sx + nz;
+    double* ps = fl + nz;
+    double* px = ps + nx;
+    for (int z = t; z < nz; z += RB_THREADS) {
+        const double* r = row_sum + (long long)z * NQR;
+        ux[z] = r[QR_UX] / nx;
+        rz[z] = r[QR_RHOA] / nx;
+        rz[nz + z] = r[QR_RHOB] / nx;
+        sx[z] = r[QR_SXZ] / nx;
+    }
+    for (int x = t; x < nx; x += RB_THREADS) {
+        ps[x] = col_sum[(long long)x * NQC + QC_PS] / nz;
+        px[x] = col_sum[(long long)x * NQC + QC_PXX] / nz;
+    }
+    __syncthreads();
+    // Eq. fluidity: shear rate (central difference of ux_z; one-sided at wall rows) / stress
+    for (int z = t; z < nz; z += RB_THREADS) {
+        double gd;
+        if (nz == 1)
+            gd = 0.0;
+        else if (zbc == 0)
+            gd = 0.5 * (ux[z + 1 < nz ? z + 1 : 0] - ux[z > 0 ? z - 1 : nz - 1]);
+        else if (z == 0)
+            gd = ux[1] - ux[0];
+        else if (z == nz - 1)
+            gd = ux[nz - 1] - ux[nz - 2];
+        else
+            gd = 0.5 * (ux[z + 1] - ux[z - 1]);
+        fl[z] = gd / sx[z];
+    }
+    double m0 = 0.0, m1 = 0.0, mx = 0.0, mz = 0.0, g = 0.0;
+    for (int z = t; z < nz; z += RB_THREADS) {
+        const double* r = row_sum + (long long)z * NQR;
+        m0 += r[QR_RHOA];
+        m1 += r[QR_RHOB];
+        mx += r[QR_MX];
+        mz += r[QR_MZ];
+    }
+    for (int x = t; x < nx; x += RB_THREADS) g += ps[x];
+    m0 = block_sum(m0, sh);
+    m1 = block_sum(m1, sh);
+    mx = block_sum(mx, sh);
+    mz = block_sum(mz, sh);
+    g = block_sum(g, sh);
+    if (t == 0) {
+        out[O_MASS] = m0;
+        out[O_MASS + 1] = m1;
+        out[O_MOM] = mx;
+        out[O_MOM + 1] = mz;
+        out[O_GAMMA] = g;
+        out[O_WALL] = zbc ? row_sum[QR_WALLB] / nx : 0.0;
+        out[O_WALL + 1] = zbc ? row_sum[(long long)(nz - 1) * NQR + QR_WALLT] / nx : 0.0;
+        const bool bad = (O.flag[0] & 1) || !isfinite(m0) || !isfinite(m1) || !isfinite(mx) || !isfinite(mz) ||
+                         !isfinite(g);
+        out[O_BAD] = bad ? 1.0 : 0.0;
+        *ticket = 0u;
+    }
+    if (accumulate) {
+        __syncthreads();
+        const long long len = obs_len(nx, nz);
+        for (long long i = t; i < len; i += RB_THREADS)
+            if (i < O_COUNT) avg[i] += out[i];
+            else if (i == O_COUNT) avg[i] += 1.0;
+            else if (i >= O_PROF) avg[i] += out[i];
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, cudaStream_t st) {
+    const long long n = (long long)C.nx * C.nz;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_init<T><<<blocks, 256, 0, st>>>(ns, f, rho, u, C);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, cudaStream_t st) {
+    const long long n = (long long)C.nx * C.nz;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_export<T><<<blocks, 256, 0, st>>>(ns, f, out, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc, double* row_sum,
+                          double* col_sum, unsigned* ticket, double* out, double* avg, int accumulate,
+                          cudaStream_t st) {
+    const int rb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+    const int cb = (nx + RB_THREADS - 1) / RB_THREADS;
+    k_reduce<<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket, out, avg,
+                                             accumulate);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_init<float>(int, float*, const double*, const double*, const StepConst<float>&, cudaStream_t);
+template cudaError_t launch_init<double>(int, double*, const double*, const double*, const StepConst<double>&,
+                                         cudaStream_t);
+template cudaError_t launch_export<float>(int, const float*, double*, const StepConst<float>&, cudaStream_t);
+template cudaError_t launch_export<double>(int, const double*, double*, const StepConst<double>&, cudaStream_t);
+
+}  // namespace lbm

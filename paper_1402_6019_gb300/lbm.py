@@ -1,0 +1,316 @@
+"""Python binding of liblbm.so (argument marshalling only).
+
+The functions below carry the names of the C ABI in include/lbm.h and do nothing but convert
+arguments; every step of the method runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is missing or cannot be loaded, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT = range(6)
+LBM_FP64, LBM_FP32 = 0, 1
+LBM_PERIODIC, LBM_BOUNCEBACK = 0, 1
+LBM_KERNEL_AUTO, LBM_KERNEL_FUSED, LBM_KERNEL_TWO_PASS = 0, 1, 2
+LBM_PSI_EXP, LBM_PSI_RHO = 0, 1
+LBM_WEIGHTS_PAPER, LBM_WEIGHTS_CHEM09 = 0, 1
+LBM_WALL_MIRROR, LBM_WALL_ZERO = 0, 1
+LBM_HOST, LBM_DEVICE = 0, 1
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class lbm_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("n_species", ctypes.c_int),
+                ("precision", ctypes.c_int), ("z_boundary", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("rows_per_warp", ctypes.c_int)]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double * 2), ("G1", ctypes.c_double * 2), ("G2", ctypes.c_double * 2),
+                ("G_AB", ctypes.c_double), ("psi_form", ctypes.c_int), ("rho0", ctypes.c_double * 2),
+                ("weight_preset", ctypes.c_int), ("weight_norm", ctypes.c_double),
+                ("body_force", ctypes.c_double), ("wall_u", ctypes.c_double * 2),
+                ("psi_wall", ctypes.c_int), ("rho_ref", ctypes.c_double * 2)]
+
+
+class lbm_obs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 2), ("momentum", ctypes.c_double * 2), ("gamma", ctypes.c_double),
+                ("wall_force", ctypes.c_double * 2), ("nonfinite", ctypes.c_int),
+                ("step", ctypes.c_longlong), ("samples", ctypes.c_longlong),
+                ("ux_z", _DP), ("rho_z", _DP), ("sxz_z", _DP), ("fluid_z", _DP), ("ps_x", _DP),
+                ("pxx_x", _DP)]
+
+
+# Every symbol declared in include/lbm.h: name -> (restype, argtypes)
+_VP = ctypes.c_void_p
+SIGNATURES = {
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(lbm_desc)]),
+    "lbm_validate_desc": (ctypes.c_int, [ctypes.POINTER(lbm_desc)]),
+    "lbm_validate_params": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int]),
+    "lbm_default_desc": (None, [ctypes.POINTER(lbm_desc)]),
+    "lbm_default_params": (None, [ctypes.POINTER(lbm_params)]),
+    "lbm_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_params)]),
+    "lbm_set_fields": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    "lbm_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "lbm_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm_set_observe": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm_observables": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_obs)]),
+    "lbm_averages": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_obs), ctypes.c_int]),
+    "lbm_synchronize": (ctypes.c_int, [_VP]),
+    "lbm_launch_count": (ctypes.c_longlong, [_VP]),
+    "lbm_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_last_error": (ctypes.c_char_p, [_VP]),
+    "lbm_destroy": (None, [_VP]),
+    "lbm_abi_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm.so (building it first when it is missing and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing; build it with __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = load().lbm_last_error(ctx)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    """Host float64 C-contiguous array, or an object with data_ptr() (a CUDA torch tensor)."""
+    if a is None:
+        return None, LBM_HOST
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), LBM_DEVICE
+    assert a.dtype == np.float64 and a.flags.c_contiguous, "host arrays must be C-contiguous float64"
+    return ctypes.c_void_p(a.ctypes.data), LBM_HOST
+
+
+# ---- thin wrappers with the C names -------------------------------------------------------
+
+def lbm_default_desc() -> lbm_desc:
+    d = lbm_desc()
+    load().lbm_default_desc(ctypes.byref(d))
+    return d
+
+
+def lbm_default_params() -> lbm_params:
+    p = lbm_params()
+    load().lbm_default_params(ctypes.byref(p))
+    return p
+
+
+def lbm_validate_desc(d: lbm_desc) -> int:
+    return load().lbm_validate_desc(ctypes.byref(d))
+
+
+def lbm_validate_params(p: lbm_params, n_species: int) -> int:
+    return load().lbm_validate_params(ctypes.byref(p), n_species)
+
+
+def lbm_create(d: lbm_desc):
+    h = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(h), ctypes.byref(d)), None)
+    return h
+
+
+def lbm_set_params(h, p: lbm_params):
+    _check(load().lbm_set_params(h, ctypes.byref(p)), h)
+
+
+def lbm_set_fields(h, rho, u=None):
+    pr, where = _dptr(rho)
+    pu, where_u = _dptr(u)
+    if u is not None and where_u != where:
+        raise ValueError("rho and u must both be host arrays or both device tensors")
+    _check(load().lbm_set_fields(h, pr, pu, where), h)
+
+
+def lbm_get_fields(h, rho=None, u=None, f=None):
+    ptrs = [_dptr(a) for a in (rho, u, f)]
+    wheres = {w for (p, w), a in zip(ptrs, (rho, u, f)) if a is not None}
+    if len(wheres) > 1:
+        raise ValueError("outputs must all be host arrays or all device tensors")
+    where = wheres.pop() if wheres else LBM_HOST
+    _check(load().lbm_get_fields(h, ptrs[0][0], ptrs[1][0], ptrs[2][0], where), h)
+
+
+def lbm_step(h, nsteps: int):
+    _check(load().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_set_observe(h, every: int):
+    _check(load().lbm_set_observe(h, int(every)), h)
+
+
+def lbm_observables(h, o: lbm_obs):
+    _check(load().lbm_observables(h, ctypes.byref(o)), h)
+
+
+def lbm_averages(h, o: lbm_obs, reset: bool = False):
+    _check(load().lbm_averages(h, ctypes.byref(o), 1 if reset else 0), h)
+
+
+def lbm_synchronize(h):
+    _check(load().lbm_synchronize(h), h)
+
+
+def lbm_launch_count(h) -> int:
+    return load().lbm_launch_count(h)
+
+
+def lbm_profile(h, enable: bool):
+    _check(load().lbm_profile(h, 1 if enable else 0), h)
+
+
+def lbm_profile_read(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(load().lbm_profile_read(h, ctypes.byref(ms), ctypes.byref(n)), h)
+    return ms.value, n.value
+
+
+def lbm_last_error(h=None) -> str:
+    m = load().lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def lbm_destroy(h):
+    load().lbm_destroy(h)
+
+
+def lbm_abi_version() -> int:
+    return load().lbm_abi_version()
+
+
+# ---- convenience ---------------------------------------------------------------------------
+
+def make_params(**kw) -> lbm_params:
+    """lbm_params from keyword values; pairs may be given as scalars."""
+    p = lbm_default_params()
+    for k, v in kw.items():
+        if k in ("tau", "G1", "G2", "rho0", "wall_u", "rho_ref"):
+            v = list(v) if hasattr(v, "__len__") else [v, v]
+            arr = getattr(p, k)
+            arr[0] = v[0]
+            arr[1] = v[1] if len(v) > 1 else v[0]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Lattice:
+    """One simulation on the GPU: create + params + fields, with numpy I/O."""
+
+    def __init__(self, nx, nz, n_species=1, precision=LBM_FP64, z_boundary=LBM_PERIODIC,
+                 kernel=LBM_KERNEL_AUTO, device=0, stream=None, rows_per_warp=0, **params):
+        d = lbm_default_desc()
+        d.nx, d.nz, d.n_species, d.precision = nx, nz, n_species, precision
+        d.z_boundary, d.kernel, d.device, d.rows_per_warp = z_boundary, kernel, device, rows_per_warp
+        d.stream = stream
+        self.desc = d
+        self.nx, self.nz, self.ns = nx, nz, n_species
+        self.h = lbm_create(d)
+        self.set_params(**params)
+
+    def set_params(self, **params):
+        self.params = make_params(**params)
+        lbm_set_params(self.h, self.params)
+
+    def set_fields(self, rho, u=None):
+        if not hasattr(rho, "data_ptr"):
+            rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ns, self.nz, self.nx)
+            if u is not None:
+                u = np.ascontiguousarray(u, dtype=np.float64).reshape(2, self.nz, self.nx)
+        lbm_set_fields(self.h, rho, u)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def fields(self, populations=True):
+        rho = np.zeros((self.ns, self.nz, self.nx))
+        u = np.zeros((2, self.nz, self.nx))
+        f = np.zeros((self.ns, 9, self.nz, self.nx)) if populations else None
+        lbm_get_fields(self.h, rho, u, f)
+        return rho, u, f
+
+    def _obs_struct(self):
+        nz, nx = self.nz, self.nx
+        prof = dict(ux_z=np.zeros(nz), rho_z=np.zeros(self.ns * nz), sxz_z=np.zeros(nz),
+                    fluid_z=np.zeros(nz), ps_x=np.zeros(nx), pxx_x=np.zeros(nx))
+        o = lbm_obs()
+        for k, v in prof.items():
+            setattr(o, k, v.ctypes.data_as(_DP))
+        return o, prof
+
+    def _obs_dict(self, o, prof):
+        res = dict(mass=np.array(o.mass[:]), momentum=np.array(o.momentum[:]), gamma=o.gamma,
+                   wall_force=np.array(o.wall_force[:]), nonfinite=bool(o.nonfinite), step=o.step,
+                   samples=o.samples)
+        prof["rho_z"] = prof["rho_z"].reshape(self.ns, self.nz)
+        res.update(prof)
+        return res
+
+    def observables(self):
+        o, prof = self._obs_struct()
+        lbm_observables(self.h, o)
+        return self._obs_dict(o, prof)
+
+    def set_observe(self, every):
+        lbm_set_observe(self.h, every)
+
+    def averages(self, reset=False):
+        o, prof = self._obs_struct()
+        lbm_averages(self.h, o, reset)
+        return self._obs_dict(o, prof)
+
+    def synchronize(self):
+        lbm_synchronize(self.h)
+
+    @property
+    def launches(self):
+        return lbm_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

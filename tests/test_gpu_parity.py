@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances:
+* FP64 path: relative L-inf <= 1e-12 on rho and u (the contract for the FP64 mode).  The two
+  sides differ only by rounding (summation order, FMA, exp), and the workloads are not chaotic
+  over these horizons.
+* FP32 path (populations stored as deviations from W_l rho_ref): relative L-inf <= 1e-4 on rho
+  and u after 1000 steps (the contract for the FP32 mode).
+"""
+import numpy as np
+import pytest
+
+from paper_1402_6019_gb300 import lbm as L
+from paper_1402_6019_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-4
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def pair(oracle, nx, nz, ns, zbc, precision, rho, steps, u=None, kernel=L.LBM_KERNEL_AUTO, rpw=0, **prm):
+    ref = oracle.RefLattice(nx, nz, ns, zbc, **prm)
+    ref.set_fields(rho, u)
+    ref.step(steps)
+    lat = L.Lattice(nx, nz, ns, precision, zbc, kernel=kernel, rows_per_warp=rpw, **prm)
+    lat.set_fields(rho, u)
+    lat.step(steps)
+    return ref, lat
+
+
+def check_fields(ref, lat, tol, pops=True):
+    r_rho, r_u, r_f = ref.fields()
+    g_rho, g_u, g_f = lat.fields(populations=pops)
+    e_rho, e_u = rel(g_rho, r_rho), rel(g_u, r_u)
+    assert e_rho <= tol, f"rho rel err {e_rho}"
+    assert e_u <= tol, f"u rel err {e_u}"
+    if pops:
+        assert rel(g_f, r_f) <= tol
+    return e_rho, e_u
+
+
+def check_obs(ref, lat, tol):
+    a, b = lat.observables(), ref.observables()
+    scale = np.abs(b["mass"]).max()
+    assert np.allclose(a["mass"], b["mass"], rtol=tol, atol=0)
+    assert np.allclose(a["momentum"], b["momentum"], rtol=0, atol=tol * scale)
+    for k in ("ux_z", "sxz_z", "ps_x", "pxx_x", "rho_z"):
+        s = max(np.abs(b[k]).max(), 1e-30)
+        assert np.abs(a[k] - b[k]).max() <= 10 * tol * s + 1e-15, k
+    gs = np.abs(b["ps_x"]).sum() + 1e-30
+    assert abs(a["gamma"] - b["gamma"]) <= 10 * tol * gs
+    assert np.allclose(a["wall_force"], b["wall_force"], rtol=10 * tol, atol=1e-17)
+    assert not a["nonfinite"]
+
+
+# --- FP64: the contract at 1e-12 ------------------------------------------------------------
+
+def test_fp64_single_component_128_periodic_1000_steps(oracle):
+    w = W.workload("single_128")
+    ref, lat = pair(oracle, 128, 128, 1, 0, L.LBM_FP64, w["rho"], 1000, **w["params"])
+    check_fields(ref, lat, TOL64)
+    check_obs(ref, lat, 1e-11)
+    o = lat.observables()
+    assert abs(o["mass"][0] - w["rho"].sum()) / w["rho"].sum() < 1e-13
+
+
+@pytest.mark.parametrize("G_AB", [0.405, 0.587])
+def test_fp64_emulsion_ragged_periodic(oracle, G_AB):
+    nx, nz = 100, 72  # 100 = 3 strips of 28 + 16: ragged last strip
+    rho, _ = W.disk_packing(nx, nz, 0.8, seed=3, r_mean=8, r_spread=2)
+    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP64, rho, 300, **dict(W.EMULSION_PARAMS, G_AB=G_AB))
+    check_fields(ref, lat, TOL64)
+    check_obs(ref, lat, 1e-11)
+
+
+@pytest.mark.parametrize("psi_wall", [0, 1])
+def test_fp64_channel_walls_drives(oracle, psi_wall):
+    nx, nz = 61, 37
+    rho, _ = W.disk_packing(nx, nz, 0.7, seed=5, r_mean=6, r_spread=2, periodic_z=False)
+    prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(-0.01, 0.02), body_force=1e-5, psi_wall=psi_wall)
+    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP64, rho, 300, **prm)
+    check_fields(ref, lat, TOL64)
+    check_obs(ref, lat, 1e-11)
+
+
+def test_fp64_unequal_tau_chem09_rho_psi(oracle):
+    nx, nz = 45, 33
+    rho, _ = W.disk_packing(nx, nz, 0.6, seed=8, r_mean=5, r_spread=1)
+    prm = dict(W.EMULSION_PARAMS, tau=(0.8, 1.3), weight_preset=1, psi_form=1, G_AB=0.3,
+               G1=(-1.0, -0.8), G2=(0.6, 0.5))
+    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP64, rho, 200, **prm)
+    check_fields(ref, lat, TOL64)
+
+
+@pytest.mark.parametrize("nx,nz,ns,zbc", [(1, 1, 1, 0), (5, 7, 2, 0), (3, 1, 1, 1), (29, 5, 2, 1),
+                                           (30, 2, 1, 0), (57, 3, 2, 0), (2, 9, 2, 1)])
+def test_fp64_tiny_and_degenerate(oracle, nx, nz, ns, zbc):
+    rho = W.noise_field(nx, nz, seed=nx * 100 + nz, mean=0.8, amp=0.2, n_species=ns)
+    u = 0.01 * W.noise_field(nx, nz, seed=7, mean=0.0, amp=1.0, n_species=2)
+    prm = dict(W.EMULSION_PARAMS if ns == 2 else W.SINGLE_PARAMS, wall_u=(0.01, -0.02), body_force=2e-5)
+    ref, lat = pair(oracle, nx, nz, ns, zbc, L.LBM_FP64, rho, 60, u=u, **prm)
+    check_fields(ref, lat, TOL64)
+    check_obs(ref, lat, 1e-11)
+
+
+@pytest.mark.parametrize("rpw", [1, 3, 200])
+def test_fp64_row_chunking(oracle, rpw):
+    nx, nz = 64, 50
+    rho, _ = W.disk_packing(nx, nz, 0.7, seed=9, r_mean=6, r_spread=2, periodic_z=False)
+    prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(0.0, 0.01))
+    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP64, rho, 50, rpw=rpw, **prm)
+    check_fields(ref, lat, TOL64)
+    check_obs(ref, lat, 1e-11)
+
+
+def test_graph_replay_equals_single_steps():
+    nx, nz = 80, 40
+    rho, _ = W.disk_packing(nx, nz, 0.7, seed=2, r_mean=6, r_spread=2)
+    a = L.Lattice(nx, nz, 2, L.LBM_FP64, 0, **W.EMULSION_PARAMS)
+    b = L.Lattice(nx, nz, 2, L.LBM_FP64, 0, **W.EMULSION_PARAMS)
+    a.set_fields(rho)
+    b.set_fields(rho)
+    a.step(45)  # graph replays of 16 steps + 13 single steps
+    for _ in range(45):
+        b.step(1)
+    fa, fb = a.fields()[2], b.fields()[2]
+    assert np.array_equal(fa, fb)
+
+
+# --- FP32 deviations: the contract at 1e-4 after 1000 steps --------------------------------
+
+def test_fp32_emulsion_1000_steps(oracle):
+    nx = nz = 128
+    rho, _ = W.disk_packing(nx, nz, 0.8, seed=1402)
+    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP32, rho, 1000, **W.EMULSION_PARAMS)
+    e_rho, e_u = check_fields(ref, lat, TOL32, pops=False)
+    check_obs(ref, lat, 1e-4)
+
+
+def test_fp32_channel_1000_steps(oracle):
+    nx, nz = 192, 64
+    rho, _ = W.disk_packing(nx, nz, 0.85, seed=11, periodic_z=False)
+    prm = dict(W.EMULSION_PARAMS, wall_u=(-0.01, 0.01), body_force=1e-6)
+    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP32, rho, 1000, **prm)
+    check_fields(ref, lat, TOL32, pops=False)
+
+
+def test_fp32_full_size_1024_against_oracle(oracle):
+    """The benchmarked workload (1024^2 emulsion, FP32, the launch configuration of bench.py):
+    every site against the oracle after 20 steps, and conservation after 1000 steps."""
+    w = W.workload("emulsion_1024")
+    ref, lat = pair(oracle, 1024, 1024, 2, 0, L.LBM_FP32, w["rho"], 20, **w["params"])
+    check_fields(ref, lat, TOL32, pops=False)
+    m0 = w["rho"].sum(axis=(1, 2))
+    lat.step(980)
+    o = lat.observables()
+    assert np.allclose(o["mass"], m0, rtol=1e-5)
+    assert np.abs(o["momentum"]).max() < 1e-6 * m0.sum()
+
+
+def test_fp32_faster_path_is_fp32():
+    lat = L.Lattice(64, 64, 2, L.LBM_FP32, 0, **W.EMULSION_PARAMS)
+    rho, _ = W.disk_packing(64, 64, 0.5, seed=4, r_mean=6, r_spread=1)
+    lat.set_fields(rho)
+    f = lat.fields()[2]
+    # deviations stored in FP32: exported populations carry FP32 rounding of the equilibrium
+    assert f.dtype == np.float64 and np.isfinite(f).all()
+
+
+# --- observables, averages, errors ------------------------------------------------------------
+
+def test_time_averages_match_oracle_mean(oracle):
+    nx, nz = 48, 32
+    rho, _ = W.disk_packing(nx, nz, 0.6, seed=12, r_mean=5, r_spread=1, periodic_z=False)
+    prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(-0.01, 0.01))
+    ref = oracle.RefLattice(nx, nz, 2, 1, **prm)
+    ref.set_fields(rho)
+    lat = L.Lattice(nx, nz, 2, L.LBM_FP64, 1, **prm)
+    lat.set_fields(rho)
+    lat.set_observe(1)
+    n = 20
+    lat.step(n)  # 16 in a graph + 4 single
+    acc = None
+    for _ in range(n):
+        o = ref.observables()
+        acc = {k: o[k] / n for k in ("ux_z", "sxz_z", "fluid_z", "ps_x")} if acc is None else \
+            {k: acc[k] + o[k] / n for k in acc}
+        ref.step(1)
+    av = lat.averages(reset=True)
+    assert av["samples"] == n
+    for k, v in acc.items():
+        assert np.abs(av[k] - v).max() <= 1e-10 * max(np.abs(v).max(), 1e-12), k
+    assert lat.averages()["samples"] == 0
+
+
+def test_invalid_fields_rejected():
+    lat = L.Lattice(8, 8, 2, L.LBM_FP32, 0, **W.EMULSION_PARAMS)
+    rho = np.ones((2, 8, 8))
+    rho[1, 3, 4] = 0.0
+    with pytest.raises(L.LbmError) as e:
+        lat.set_fields(rho)
+    assert e.value.code == L.LBM_EINVAL
+    rho[1, 3, 4] = np.nan
+    with pytest.raises(L.LbmError):
+        lat.set_fields(rho)
+    with pytest.raises(L.LbmError):
+        lat.step(1)  # no fields yet
+    with pytest.raises(L.LbmError):
+        lat.set_params(tau=0.5)
+
+
+def test_nonfinite_state_is_reported():
+    """An unstable coupling drives densities negative; the kernels flag it and the host reports
+    LBM_ENONFINITE (a property of the data: no GPU fault is involved)."""
+    lat = L.Lattice(32, 32, 1, L.LBM_FP64, 0, G1=-60.0, G2=0.0, psi_form=1, weight_norm=1.0)
+    lat.set_fields(W.noise_field(32, 32, seed=3, mean=1.0, amp=0.3))
+    lat.step(200)
+    with pytest.raises(L.LbmError) as e:
+        lat.synchronize()
+    assert e.value.code == L.LBM_ENONFINITE
