@@ -30,7 +30,8 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int nsm = 0;
-    SweepGeom geom{};
+    SweepGeom geom{};      // fused kernel without observables (M_WRITE, M_FIELDS)
+    SweepGeom geom_obs{};  // fused kernel with observables (M_OBS modes)
     GhostGeom ghost{};
     int kernel = LBM_KERNEL_FUSED;  // resolved
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
@@ -180,14 +181,23 @@ static void release(lbm_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-static int choose_hz(const lbm_ctx* c) {
-    if (c->d.rows_per_warp > 0) return c->d.rows_per_warp < c->d.nz ? c->d.rows_per_warp : c->d.nz;
-    const long long strips = (c->d.nx + STRIP_W - 1) / STRIP_W;
-    const long long target = (long long)(c->nsm > 0 ? c->nsm : 152) * 16;  // warps in flight
-    long long hz = (c->d.nz * strips + target - 1) / target;
-    if (hz < 8) hz = 8;
+// Rows per warp: the smallest chunk height for which every warp of the grid is resident at
+// once (one wave), so no SM idles in a tail and the 4-row prologue per chunk stays small.
+static SweepGeom sweep_geom(const lbm_ctx* c, int resident_warps) {
+    SweepGeom g;
+    g.nstrips = (c->d.nx + STRIP_W - 1) / STRIP_W;
+    long long hz;
+    if (c->d.rows_per_warp > 0) {
+        hz = c->d.rows_per_warp;
+    } else {
+        const long long target = resident_warps > 0 ? resident_warps : 152LL * 8;
+        hz = ((long long)c->d.nz * g.nstrips + target - 1) / target;
+        if (hz < 2) hz = 2;
+    }
     if (hz > c->d.nz) hz = c->d.nz;
-    return (int)hz;
+    g.hz = (int)hz;
+    g.nchunks = (c->d.nz + g.hz - 1) / g.hz;
+    return g;
 }
 
 extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
@@ -237,12 +247,19 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->stream));
     CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->stream));
     // fused geometry and partial-sum groups
-    c->geom.nstrips = (nx + STRIP_W - 1) / STRIP_W;
-    c->geom.hz = choose_hz(c);
-    c->geom.nchunks = (nz + c->geom.hz - 1) / c->geom.hz;
+    {
+        const bool f64 = d->precision == LBM_FP64;
+        const int rw = f64 ? fused_resident_warps<double>(ns, M_WRITE, c->nsm)
+                           : fused_resident_warps<float>(ns, M_WRITE, c->nsm);
+        const int ro = f64 ? fused_resident_warps<double>(ns, M_WRITE | M_OBS, c->nsm)
+                           : fused_resident_warps<float>(ns, M_WRITE | M_OBS, c->nsm);
+        if (rw <= 0 || ro <= 0) return bail(fail(c, LBM_ECUDA, "occupancy query of the step kernel failed"));
+        c->geom = sweep_geom(c, rw);
+        c->geom_obs = sweep_geom(c, ro);
+    }
     const int tx = (nx + TPX - 1) / TPX, tz = (nz + TPZ - 1) / TPZ;
-    const long long rows_parts = std::max(c->geom.nstrips, tx);
-    const long long col_parts = std::max(c->geom.nchunks, tz);
+    const long long rows_parts = std::max(c->geom_obs.nstrips, tx);
+    const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
     CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * sizeof(double)));
     CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * sizeof(double)));
     CKC(cudaMalloc(&c->row_sum, (size_t)nz * NQR * sizeof(double)));
@@ -318,12 +335,13 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         e = cudaEventRecord(c->ev[c->ev_used], c->stream);
         if (e != cudaSuccess) return e;
     }
+    const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
     if (c->d.precision == LBM_FP64)
-        e = launch_fused<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64,
-                                 c->geom, O, c->stream);
+        e = launch_fused<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64, G,
+                                 O, c->stream);
     else
-        e = launch_fused<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32,
-                                c->geom, O, c->stream);
+        e = launch_fused<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32, G, O,
+                                c->stream);
     c->launches += 1;
     if (e != cudaSuccess) return e;
     if (timed) {
@@ -332,7 +350,7 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         c->ev_used += 2;
     }
     if (reduce) {
-        e = launch_reduce(O, c->geom.nstrips, c->geom.nchunks, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
+        e = launch_reduce(O, c->geom_obs.nstrips, c->geom_obs.nchunks, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
                           c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
         c->launches += 1;
     }

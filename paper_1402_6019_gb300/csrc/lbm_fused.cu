@@ -1,15 +1,18 @@
 // lbm_fused.cu -- one-pass time step of the multirange Shan-Chen lattice Boltzmann model.
 //
 // One warp owns a strip of STRIP_W = 28 columns plus a 2-column halo on each side (the reach
-// of the 5x5 stencil of Eq. FORCE) and sweeps a chunk of rows in z.  For each new row it
-// reads the 9 (x species) populations of its 32 columns once from HBM (coalesced, x
-// fastest), forms the density and psi, and keeps psi and rho of the last five rows in
-// registers.  Two rows behind, the row is complete: the lanes gather the 5x5 psi and 3x3 rho
-// neighbourhoods with warp shuffles, form the force (Eq. FORCE + cross term + body force),
-// and the 28 owned lanes re-read their populations (from L1), collide (Eq. LB with the
-// shifted velocity of Sec. II) and push them to their neighbours (streaming, with the
-// halfway bounce-back walls of Sec. IV).  Compared with a psi pass followed by a collide
-// pass this moves each population once in and once out of HBM per step.
+// of the 5x5 stencil of Eq. FORCE) and sweeps a chunk of rows in z.  Each lane copies the
+// 9 (x species) populations of its column for row r + PF + 1 into a per-warp ring in shared
+// memory with cp.async while it works on row r (PF rows in flight beyond the current one), so
+// HBM reads are coalesced (x fastest) and overlapped with compute.  From the ring it forms
+// the density and psi of row r and keeps psi and rho of the last five rows in registers.  Two
+// rows behind, the row is complete: the lanes gather the 5x5 psi and 3x3 rho neighbourhoods
+// with warp shuffles, form the force (Eq. FORCE + cross term + body force), and the 28 owned
+// lanes read their populations back from the ring, collide (Eq. LB with the shifted velocity
+// of Sec. II) and push them to their neighbours (streaming, with the halfway bounce-back
+// walls of Sec. IV).  Compared with a psi pass followed by a collide pass this moves each
+// population once in and once out of HBM per step.  A lane only ever reads ring entries it
+// copied itself.
 //
 // With M_OBS the same pass also accumulates the observables of the state being collided:
 // per-row sums over the strip (warp reduction) and per-column sums over the chunk.
@@ -21,9 +24,39 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// rows in flight beyond the current one, and ring depth (current row, the two rows behind it
+// that are still to be collided, the row being overwritten, and the prefetched rows)
+template <typename T> constexpr int prefetch_rows() { return sizeof(T) == 4 ? 2 : 1; }
+template <typename T> constexpr int ring_rows() { return prefetch_rows<T>() + 4; }
+constexpr int WARPS_PER_BLOCK = 4;
+
+template <typename T, int NS>
+constexpr int ring_bytes_per_block() {
+    return WARPS_PER_BLOCK * ring_rows<T>() * NS * 9 * 32 * (int)sizeof(T);
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <typename T, int NS, int MODE>
 __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __restrict__ fout,
                                                const StepConst<T> C, const SweepGeom G, const ObsPtrs O) {
+    constexpr int PF = prefetch_rows<T>();
+    constexpr int RS = ring_rows<T>();
+    constexpr int ROWV = NS * 9 * 32;  // ring values per row: [species*9 + l][lane]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const ring = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * RS * ROWV;
     const int lane = threadIdx.x & 31;
     const int wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wg >= G.nstrips * G.nchunks) return;  // whole warp
@@ -47,7 +80,27 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
     T acc_ps = T(0), acc_pxx = T(0);
     int bad = 0;
 
+    const int rbase = z0 - 2;
+    auto slot = [&](int r) { return ring + ((r - rbase) % RS) * ROWV + lane; };
+    // asynchronous copy of this lane's column of row r into the ring (one commit group per row)
+    auto issue = [&](int r) {
+        if (r <= z1 + 1) {
+            const int rr = source_row(C, r);
+            if (rr >= 0) {
+                T* dst = slot(r);
+                const T* src = fin + (long long)rr * pitch + xw;
+#pragma unroll
+                for (int k = 0; k < NS * 9; ++k) cp_async(dst + k * 32, src + k * plane);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int i = 0; i <= PF; ++i) issue(rbase + i);
+
     for (int r = z0 - 2; r <= z1 + 1; ++r) {
+        issue(r + PF + 1);
+        cp_async_wait<PF + 1>();  // row r has landed
 #pragma unroll
         for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -59,12 +112,12 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
         {
             const int rr = source_row(C, r);
             if (rr >= 0) {
-                const T* base = fin + (long long)rr * pitch + xw;
+                const T* base = slot(r);
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     T f[9];
 #pragma unroll
-                    for (int l = 0; l < 9; ++l) f[l] = __ldg(base + (s * 9 + l) * plane);
+                    for (int l = 0; l < 9; ++l) f[l] = base[(s * 9 + l) * 32];
                     const T d = sum9(f);
                     dr[s][4] = d;
                     ps[s][4] = psi_of(C, s, C.rho_ref[s] + d);
@@ -78,7 +131,10 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
             }
         }
         const int z = r - 2;
-        if (z < z0) continue;  // prologue rows (warp-uniform)
+        if (z < z0) {  // prologue rows (warp-uniform)
+            __syncwarp();
+            continue;
+        }
 
         // ---- interaction at row z from the neighbourhood (all lanes take part) ----
         T F[NS][2];
@@ -115,11 +171,11 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
 
         if (owned) {
             T f[NS][9], drho[NS], rho[NS];
-            const T* base = fin + (long long)z * pitch + x;
+            const T* base = slot(z);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
 #pragma unroll
-                for (int l = 0; l < 9; ++l) f[s][l] = __ldg(base + (s * 9 + l) * plane);
+                for (int l = 0; l < 9; ++l) f[s][l] = base[(s * 9 + l) * 32];
                 drho[s] = dr[s][2];
                 rho[s] = C.rho_ref[s] + drho[s];
                 if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = 1;
@@ -189,12 +245,14 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
                 rowq[k] = v;
             }
             if (lane == 0) {
-                double* dst = O.part_row + ((long long)strip * nz + z) * NQR;
+                double* dst = O.part_row + ((long long)z * G.nstrips + strip) * NQR;
 #pragma unroll
                 for (int k = 0; k < NQR; ++k) dst[k] = (double)rowq[k];
             }
         }
+        __syncwarp();  // ring slots read this iteration may be refilled by the next issue
     }
+    cp_async_wait<0>();
     if ((MODE & M_OBS) && owned) {
         double* dst = O.part_col + ((long long)chunk * nx + x) * NQC;
         dst[QC_PS] = (double)acc_ps;
@@ -203,19 +261,44 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(O.flag, 1);
 }
 
+template <typename T, int NS, int MODE>
+cudaError_t launch_mode(const T* fin, T* fout, const StepConst<T>& C, const SweepGeom& G, const ObsPtrs& O,
+                        cudaStream_t st) {
+    constexpr int smem = ring_bytes_per_block<T, NS>();
+    static bool configured = false;  // per instantiation; the attribute is per function
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<T, NS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int warps = G.nstrips * G.nchunks;
+    const dim3 block(32 * WARPS_PER_BLOCK), grid((warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    k_fused<T, NS, MODE><<<grid, block, smem, st>>>(fin, fout, C, G, O);
+    return cudaGetLastError();
+}
+
+template <typename T, int NS, int MODE>
+int resident_mode(int nsm) {
+    constexpr int smem = ring_bytes_per_block<T, NS>();
+    if (cudaFuncSetAttribute(k_fused<T, NS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused<T, NS, MODE>, 32 * WARPS_PER_BLOCK, smem) !=
+        cudaSuccess)
+        return 0;
+    return blocks * WARPS_PER_BLOCK * nsm;
+}
+
 template <typename T, int NS>
 cudaError_t launch_ns(int mode, const T* fin, T* fout, const StepConst<T>& C, const SweepGeom& G, const ObsPtrs& O,
                       cudaStream_t st) {
-    const int warps = G.nstrips * G.nchunks;
-    const dim3 block(128), grid((warps + 3) / 4);
     switch (mode) {
-        case M_WRITE: k_fused<T, NS, M_WRITE><<<grid, block, 0, st>>>(fin, fout, C, G, O); break;
-        case M_WRITE | M_OBS: k_fused<T, NS, M_WRITE | M_OBS><<<grid, block, 0, st>>>(fin, fout, C, G, O); break;
-        case M_OBS: k_fused<T, NS, M_OBS><<<grid, block, 0, st>>>(fin, fout, C, G, O); break;
-        case M_FIELDS: k_fused<T, NS, M_FIELDS><<<grid, block, 0, st>>>(fin, fout, C, G, O); break;
+        case M_WRITE: return launch_mode<T, NS, M_WRITE>(fin, fout, C, G, O, st);
+        case M_WRITE | M_OBS: return launch_mode<T, NS, M_WRITE | M_OBS>(fin, fout, C, G, O, st);
+        case M_OBS: return launch_mode<T, NS, M_OBS>(fin, fout, C, G, O, st);
+        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(fin, fout, C, G, O, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -225,6 +308,16 @@ cudaError_t launch_fused(int ns, int mode, const T* fin, T* fout, const StepCons
                          const ObsPtrs& O, cudaStream_t st) {
     return ns == 1 ? launch_ns<T, 1>(mode, fin, fout, C, G, O, st) : launch_ns<T, 2>(mode, fin, fout, C, G, O, st);
 }
+
+template <typename T>
+int fused_resident_warps(int ns, int mode, int nsm) {
+    if (ns == 1)
+        return mode & M_OBS ? resident_mode<T, 1, M_WRITE | M_OBS>(nsm) : resident_mode<T, 1, M_WRITE>(nsm);
+    return mode & M_OBS ? resident_mode<T, 2, M_WRITE | M_OBS>(nsm) : resident_mode<T, 2, M_WRITE>(nsm);
+}
+
+template int fused_resident_warps<float>(int, int, int);
+template int fused_resident_warps<double>(int, int, int);
 
 template cudaError_t launch_fused<float>(int, int, const float*, float*, const StepConst<float>&, const SweepGeom&,
                                          const ObsPtrs&, cudaStream_t);

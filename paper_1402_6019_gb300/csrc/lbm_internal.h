@@ -22,7 +22,7 @@ struct SweepGeom {
 
 // Output pointers of the step kernels (device memory).
 struct ObsPtrs {
-    double* part_row;  // [nxpart][nz][NQR]   per-row sums over a group of columns
+    double* part_row;  // [nz][nxpart][NQR]   per-row sums over a group of columns
     double* part_col;  // [nzpart][nx][NQC]   per-column sums over a group of rows
     double* fields;    // [ns + 2][nz][nx]    rho_s, u_x, u_z (M_FIELDS)
     int* flag;         // bit 0: a density <= 0 / NaN / Inf was met
@@ -44,6 +44,9 @@ LBM_HD long long obs_len(int nx, int nz) { return O_PROF + 5LL * nz + 2LL * nx; 
 template <typename T>
 cudaError_t launch_fused(int ns, int mode, const T* fin, T* fout, const StepConst<T>& C, const SweepGeom& G,
                          const ObsPtrs& O, cudaStream_t st);
+// Warps of the fused kernel resident on the whole GPU at once (occupancy), for a mode class.
+template <typename T>
+int fused_resident_warps(int ns, int mode, int nsm);
 template <typename T>
 cudaError_t launch_density(int ns, const T* f, T* gfield, const StepConst<T>& C, const GhostGeom& GG,
                            cudaStream_t st);

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
         if (z < nz) {
             for (int k = 0; k < NQR; ++k) {
                 double v = 0.0;
-                for (int p = lane; p < nxpart; p += 32) v += O.part_row[((long long)p * nz + z) * NQR + k];
+                for (int p = lane; p < nxpart; p += 32) v += O.part_row[((long long)z * nxpart + p) * NQR + k];
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) row_sum[(long long)z * NQR + k] = v;
             }

@@ -33,14 +33,30 @@ def pair(oracle, nx, nz, ns, zbc, precision, rho, steps, u=None, kernel=L.LBM_KE
     return ref, lat
 
 
+def u_scale(ref):
+    """Scale of the terms the velocity is formed from: u = sum_s (j_s + F_s/2) / rho.  Near rest
+    j ~ -F/2, so u itself is a small difference and its relative error is ill-conditioned; the
+    error is measured against max over sites of sum_s (|j_s| + |F_s|/2) / rho."""
+    rho, u, f = ref.fields()
+    F = ref.site_fields()["F"]
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], float)
+    cz = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], float)
+    jx = np.einsum("slzx,l->szx", f, cx)
+    jz = np.einsum("slzx,l->szx", f, cz)
+    mag = (np.abs(jx) + np.abs(jz) + 0.5 * (np.abs(F[:, 0]) + np.abs(F[:, 1]))).sum(0) / rho.sum(0)
+    return max(float(mag.max()), float(np.abs(u).max()))
+
+
 def check_fields(ref, lat, tol, pops=True):
     r_rho, r_u, r_f = ref.fields()
     g_rho, g_u, g_f = lat.fields(populations=pops)
-    e_rho, e_u = rel(g_rho, r_rho), rel(g_u, r_u)
+    e_rho = rel(g_rho, r_rho)
+    e_u = float(np.abs(g_u - r_u).max() / u_scale(ref))
     assert e_rho <= tol, f"rho rel err {e_rho}"
-    assert e_u <= tol, f"u rel err {e_u}"
+    assert e_u <= tol, f"u err {e_u} (relative to the momentum scale)"
     if pops:
-        assert rel(g_f, r_f) <= tol
+        e_f = rel(g_f, r_f)
+        assert e_f <= tol, f"populations rel err {e_f}"
     return e_rho, e_u
 
 
@@ -52,8 +68,9 @@ def check_obs(ref, lat, tol):
     for k in ("ux_z", "sxz_z", "ps_x", "pxx_x", "rho_z"):
         s = max(np.abs(b[k]).max(), 1e-30)
         assert np.abs(a[k] - b[k]).max() <= 10 * tol * s + 1e-15, k
-    gs = np.abs(b["ps_x"]).sum() + 1e-30
-    assert abs(a["gamma"] - b["gamma"]) <= 10 * tol * gs
+    # gamma sums differences P_xx - P_zz of O(1) terms: rounding floor 1e-14 * sum |P_xx|
+    gs = np.abs(b["ps_x"]).sum()
+    assert abs(a["gamma"] - b["gamma"]) <= 10 * tol * gs + 1e-14 * np.abs(b["pxx_x"]).sum()
     assert np.allclose(a["wall_force"], b["wall_force"], rtol=10 * tol, atol=1e-17)
     assert not a["nonfinite"]
 
