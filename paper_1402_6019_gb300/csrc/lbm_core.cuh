@@ -191,9 +191,40 @@ LBM_HD T feq_dev(int l, T drho, T rho, T ux, T uz) {
     return wlb<T>(l) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
 }
 
+// Division and reciprocal: exact IEEE in FP64; in FP32 on the device the fast hardware
+// approximation (a few ulp), well inside the FP32 mode's error budget.
+LBM_HD double div_(double a, double b) { return a / b; }
+LBM_HD float div_(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
+// The nine equilibria of Sec. II as deviations from W_l rho_ref, using the pair structure of
+// D2Q9: l and its opposite share the even part W (drho + rho (9/2 cu^2 - 3/2 u^2)) and have
+// odd parts +-3 W rho cu.
+template <typename T>
+LBM_HD void feq9_dev(T drho, T rho, T ux, T uz, T (&fe)[9]) {
+    const T u15 = T(1.5) * (ux * ux + uz * uz);
+    const T w1 = T(1) / T(9), w2 = T(1) / T(36);
+    fe[0] = T(4) / T(9) * (drho - rho * u15);
+    const T cu[4] = {ux, uz, ux + uz, uz - ux};  // pairs (1,3), (2,4), (5,7), (6,8)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T w = k < 2 ? w1 : w2;
+        const T even = w * (drho + rho * (T(4.5) * cu[k] * cu[k] - u15));
+        const T odd = w * T(3) * rho * cu[k];
+        const int lp = k < 2 ? k + 1 : k + 3;  // 1, 2, 5, 6
+        fe[lp] = even + odd;
+        fe[opp(lp)] = even - odd;
+    }
+}
+
 // Shifted-velocity BGK collision of all species at one site (Eq. LB with u_eq = u' + tau F /
 // rho, u' the common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s).  f is overwritten with the
-// post-collision values.  rho[s] is the full density, drho[s] the stored-sum.
+// post-collision values.  rho[s] is the full density, drho[s] the stored sum.
 template <typename T, int NS>
 LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], const T (&rho)[NS],
                     const T (&F)[NS][2]) {
@@ -206,17 +237,17 @@ LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], c
         nz_ += C.omega[s] * jz[s];
         den += C.omega[s] * rho[s];
     }
-    const T upx = nx_ / den, upz = nz_ / den;
+    const T iden = div_(T(1), den);
+    const T upx = nx_ * iden, upz = nz_ * iden;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const T ir = T(1) / rho[s];
-        const T ux = upx + C.tau[s] * F[s][0] * ir;
-        const T uz = upz + C.tau[s] * F[s][1] * ir;
+        const T tir = div_(C.tau[s], rho[s]);
+        const T ux = upx + F[s][0] * tir;
+        const T uz = upz + F[s][1] * tir;
+        T fe[9];
+        feq9_dev<T>(drho[s], rho[s], ux, uz, fe);
 #pragma unroll
-        for (int l = 0; l < 9; ++l) {
-            const T fe = feq_dev<T>(l, drho[s], rho[s], ux, uz);
-            f[s][l] = f[s][l] + C.omega[s] * (fe - f[s][l]);
-        }
+        for (int l = 0; l < 9; ++l) f[s][l] = f[s][l] + C.omega[s] * (fe[l] - f[s][l]);
     }
 }
 

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
     }
     cp_async_wait<0>();
     if ((MODE & M_OBS) && owned) {
-        double* dst = O.part_col + ((long long)chunk * nx + x) * NQC;
+        double* dst = O.part_col + ((long long)x * G.nchunks + chunk) * NQC;
         dst[QC_PS] = (double)acc_ps;
         dst[QC_PXX] = (double)acc_pxx;
     }

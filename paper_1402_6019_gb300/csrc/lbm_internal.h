@@ -23,7 +23,7 @@ struct SweepGeom {
 // Output pointers of the step kernels (device memory).
 struct ObsPtrs {
     double* part_row;  // [nz][nxpart][NQR]   per-row sums over a group of columns
-    double* part_col;  // [nzpart][nx][NQC]   per-column sums over a group of rows
+    double* part_col;  // [nx][nzpart][NQC]   per-column sums over a group of rows
     double* fields;    // [ns + 2][nz][nx]    rho_s, u_x, u_z (M_FIELDS)
     int* flag;         // bit 0: a density <= 0 / NaN / Inf was met
 };

@@ -62,24 +62,37 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     __shared__ double sh[RB_THREADS];
     __shared__ bool last;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int WPB = RB_THREADS / 32;  // one warp per row (or column)
     if ((int)blockIdx.x < nrowblocks) {
-        const int z = blockIdx.x * (RB_THREADS / 32) + warp;
+        const int z = blockIdx.x * WPB + warp;
         if (z < nz) {
+            double v[NQR];
+            for (int k = 0; k < NQR; ++k) v[k] = 0.0;
+            for (int p = lane; p < nxpart; p += 32) {
+                const double* src = O.part_row + ((long long)z * nxpart + p) * NQR;
+                for (int k = 0; k < NQR; ++k) v[k] += src[k];
+            }
             for (int k = 0; k < NQR; ++k) {
-                double v = 0.0;
-                for (int p = lane; p < nxpart; p += 32) v += O.part_row[((long long)z * nxpart + p) * NQR + k];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) row_sum[(long long)z * NQR + k] = v;
+                double a = v[k];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) row_sum[(long long)z * NQR + k] = a;
             }
         }
     } else {
-        const int x = (blockIdx.x - nrowblocks) * RB_THREADS + t;
-        if (x < nx)
-            for (int k = 0; k < NQC; ++k) {
-                double v = 0.0;
-                for (int p = 0; p < nzpart; ++p) v += O.part_col[((long long)p * nx + x) * NQC + k];
-                col_sum[(long long)x * NQC + k] = v;
+        const int x = (blockIdx.x - nrowblocks) * WPB + warp;
+        if (x < nx) {
+            double v[NQC];
+            for (int k = 0; k < NQC; ++k) v[k] = 0.0;
+            for (int p = lane; p < nzpart; p += 32) {
+                const double* src = O.part_col + ((long long)x * nzpart + p) * NQC;
+                for (int k = 0; k < NQC; ++k) v[k] += src[k];
             }
+            for (int k = 0; k < NQC; ++k) {
+                double a = v[k];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) col_sum[(long long)x * NQC + k] = a;
+            }
+        }
     }
     __threadfence();
     __syncthreads();
@@ -180,7 +193,7 @@ cudaError_t launch_reduce(const ObsPtrs& O, int nxpart, int nzpart, int nx, int 
                           double* col_sum, unsigned* ticket, double* out, double* avg, int accumulate,
                           cudaStream_t st) {
     const int rb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-    const int cb = (nx + RB_THREADS - 1) / RB_THREADS;
+    const int cb = (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     k_reduce<<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket, out, avg,
                                              accumulate);
     return cudaGetLastError();
