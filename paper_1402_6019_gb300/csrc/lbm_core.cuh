@@ -48,10 +48,14 @@ struct StepConst {
     T kin[2];                 // (tau_s - 1/2)^2 of the Sec. III stress
 };
 
-// Pseudopotential of Sec. IV, psi = 1 - exp(-rho/rho0) (or psi = rho).  FP32 uses expm1 to
-// keep the relative accuracy of small psi.
+// Pseudopotential of Sec. IV, psi = 1 - exp(-rho/rho0) (or psi = rho).  FP32 on the device
+// uses the hardware exponential (absolute error ~1e-7 in psi, inside the FP32 mode's budget).
 LBM_HD float psi_of(const StepConst<float>& C, int s, float rho) {
+#if defined(__CUDA_ARCH__)
+    return C.psi_form == 1 ? rho : 1.0f - __expf(-rho * C.inv_rho0[s]);
+#else
     return C.psi_form == 1 ? rho : -expm1f(-rho * C.inv_rho0[s]);
+#endif
 }
 LBM_HD double psi_of(const StepConst<double>& C, int s, double rho) {
     return C.psi_form == 1 ? rho : 1.0 - exp(-rho / C.rho0[s]);
@@ -224,15 +228,14 @@ LBM_HD void feq9_dev(T drho, T rho, T ux, T uz, T (&fe)[9]) {
 
 // Shifted-velocity BGK collision of all species at one site (Eq. LB with u_eq = u' + tau F /
 // rho, u' the common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s).  f is overwritten with the
-// post-collision values.  rho[s] is the full density, drho[s] the stored sum.
+// post-collision values.  rho[s] is the full density, drho[s] the stored sum, ir[s] = 1/rho[s],
+// (jx, jz) the momenta of the stored values.
 template <typename T, int NS>
 LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], const T (&rho)[NS],
-                    const T (&F)[NS][2]) {
-    T jx[NS], jz[NS];
+                    const T (&ir)[NS], const T (&jx)[NS], const T (&jz)[NS], const T (&F)[NS][2]) {
     T nx_ = T(0), nz_ = T(0), den = T(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        momentum9(f[s], jx[s], jz[s]);
         nx_ += C.omega[s] * jx[s];
         nz_ += C.omega[s] * jz[s];
         den += C.omega[s] * rho[s];
@@ -241,7 +244,7 @@ LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], c
     const T upx = nx_ * iden, upz = nz_ * iden;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const T tir = div_(C.tau[s], rho[s]);
+        const T tir = C.tau[s] * ir[s];
         const T ux = upx + F[s][0] * tir;
         const T uz = upz + F[s][1] * tir;
         T fe[9];
@@ -259,36 +262,33 @@ LBM_HD T bounce(int l, T g, T rho, T uw) {
 }
 
 // Per-site observables that need the populations (before collision): the barycentric
-// velocity and the kinetic shear stress.  Returns (ux, uz, kinetic xz momentum flux).
+// velocity (sum_s j_s + F_s/2) / sum_s rho_s, and the kinetic xz momentum flux
+//   sum_s (1 - 1/(2 tau_s)) sum_l (f_l - feq_l(rho_s, u)) c_lx c_lz + rho u_x u_z,
+// using sum_l feq_l c_lx c_lz = rho_s u_x u_z (the second moment of Sec. II) and that only the
+// diagonal links have c_lx c_lz != 0.
 template <typename T, int NS>
-LBM_HD void site_kinetics(const StepConst<T>& C, const T (&f)[NS][9], const T (&drho)[NS], const T (&rho)[NS],
-                          const T (&F)[NS][2], T& ux, T& uz, T& pixz, T& rtot, T& mx, T& mz) {
+LBM_HD void site_kinetics(const StepConst<T>& C, const T (&f)[NS][9], const T (&rho)[NS], const T (&jx)[NS],
+                          const T (&jz)[NS], const T (&F)[NS][2], T& ux, T& uz, T& pixz, T& rtot, T& mx, T& mz) {
     mx = T(0);
     mz = T(0);
     rtot = T(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        T jx, jz;
-        momentum9(f[s], jx, jz);
-        mx += jx + T(0.5) * F[s][0];
-        mz += jz + T(0.5) * F[s][1];
+        mx += jx[s] + T(0.5) * F[s][0];
+        mz += jz[s] + T(0.5) * F[s][1];
         rtot += rho[s];
     }
-    ux = mx / rtot;
-    uz = mz / rtot;
-    // (1 - 1/(2 tau)) sum_l (f_l - feq_l(rho_s, u)) c_lx c_lz + rho u_x u_z
+    const T irt = div_(T(1), rtot);
+    ux = mx * irt;
+    uz = mz * irt;
+    const T uxz = ux * uz;
     T visc = T(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        T m = T(0);
-#pragma unroll
-        for (int l = 5; l <= 8; ++l) {
-            const T d = f[s][l] - feq_dev<T>(l, drho[s], rho[s], ux, uz);
-            m += T(cx(l) * cz(l)) * d;
-        }
+        const T m = (f[s][5] + f[s][7]) - (f[s][6] + f[s][8]) - rho[s] * uxz;
         visc += (T(1) - T(0.5) * C.omega[s]) * m;
     }
-    pixz = visc + rtot * ux * uz;
+    pixz = visc + rtot * uxz;
 }
 
 // Index helpers.

@@ -80,23 +80,27 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
     T acc_ps = T(0), acc_pxx = T(0);
     int bad = 0;
 
-    const int rbase = z0 - 2;
-    auto slot = [&](int r) { return ring + ((r - rbase) % RS) * ROWV + lane; };
+    // ring slots (rolling): row r lives in slot (r - (z0 - 2)) mod RS
+    T* const lane_ring = ring + lane;
+    int s_issue = 0;  // slot of the next row to issue
+    int s_cur = 0;    // slot of the current row r
+    int s_col = RS - 2 < 0 ? 0 : RS - 2;  // slot of row r - 2 (meaningful once r - 2 >= z0)
     // asynchronous copy of this lane's column of row r into the ring (one commit group per row)
     auto issue = [&](int r) {
         if (r <= z1 + 1) {
             const int rr = source_row(C, r);
             if (rr >= 0) {
-                T* dst = slot(r);
+                T* dst = lane_ring + s_issue * ROWV;
                 const T* src = fin + (long long)rr * pitch + xw;
 #pragma unroll
                 for (int k = 0; k < NS * 9; ++k) cp_async(dst + k * 32, src + k * plane);
             }
         }
         cp_async_commit();
+        s_issue = s_issue + 1 == RS ? 0 : s_issue + 1;
     };
 #pragma unroll
-    for (int i = 0; i <= PF; ++i) issue(rbase + i);
+    for (int i = 0; i <= PF; ++i) issue(z0 - 2 + i);
 
     for (int r = z0 - 2; r <= z1 + 1; ++r) {
         issue(r + PF + 1);
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
         {
             const int rr = source_row(C, r);
             if (rr >= 0) {
-                const T* base = slot(r);
+                const T* base = lane_ring + s_cur * ROWV;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     T f[9];
@@ -131,6 +135,9 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
             }
         }
         const int z = r - 2;
+        const int s_z = s_col;  // slot of row z
+        s_col = s_col + 1 == RS ? 0 : s_col + 1;
+        s_cur = s_cur + 1 == RS ? 0 : s_cur + 1;
         if (z < z0) {  // prologue rows (warp-uniform)
             __syncwarp();
             continue;
@@ -170,8 +177,8 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
         for (int k = 0; k < NQR; ++k) rowq[k] = T(0);
 
         if (owned) {
-            T f[NS][9], drho[NS], rho[NS];
-            const T* base = slot(z);
+            T f[NS][9], drho[NS], rho[NS], ir[NS], jx[NS], jz[NS];
+            const T* base = lane_ring + s_z * ROWV;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
 #pragma unroll
@@ -179,11 +186,13 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
                 drho[s] = dr[s][2];
                 rho[s] = C.rho_ref[s] + drho[s];
                 if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = 1;
+                ir[s] = div_(T(1), rho[s]);
+                momentum9(f[s], jx[s], jz[s]);
                 F[s][0] += rho[s] * C.g;
             }
             if (MODE & (M_OBS | M_FIELDS)) {
                 T ux, uz, pixz, rtot, mx, mz;
-                site_kinetics<T, NS>(C, f, drho, rho, F, ux, uz, pixz, rtot, mx, mz);
+                site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
                 if (MODE & M_FIELDS) {
                     const long long i = (long long)z * nx + x;
                     const long long np = (long long)nx * nz;
@@ -196,9 +205,8 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
                     T pxx = sxx, pzz = szz;
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
-                        const T ir = T(1) / rho[s];
-                        pxx += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][0] * F[s][0] * ir;
-                        pzz += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][1] * F[s][1] * ir;
+                        pxx += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][0] * F[s][0] * ir[s];
+                        pzz += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][1] * F[s][1] * ir[s];
                     }
                     acc_ps += pxx - pzz;
                     acc_pxx += pxx;
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
             if (MODE & (M_WRITE | M_OBS)) {
                 const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
                 if ((MODE & M_WRITE) || wall_row) {
-                    collide<T, NS>(C, f, drho, rho, F);
+                    collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
                     // streaming: f_l(x + c_l) = g_l(x), periodic in x, periodic or walls in z
 #pragma unroll
                     for (int s = 0; s < NS; ++s)

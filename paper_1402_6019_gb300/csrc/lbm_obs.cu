@@ -51,9 +51,23 @@ __device__ double block_sum(double v, double* sh) {
 
 constexpr int RB_THREADS = 256;
 
-// Phase 1: rows (one warp per row, summing the column groups) and columns (one thread per
-// column, summing the row groups).  Phase 2 (last block to finish): profiles, scalars,
-// fluidity and the optional time sums.  All sums run in a fixed order: repeatable results.
+__device__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the column groups of one quantity of row z (whole warp; fixed order).
+__device__ double row_total(const ObsPtrs& O, int nxpart, int z, int k) {
+    double v = 0.0;
+    for (int p = threadIdx.x & 31; p < nxpart; p += 32) v += O.part_row[((long long)z * nxpart + p) * NQR + k];
+    return warp_sum(v);
+}
+
+// Phase 1, one warp per row: the row's sums, its profile entries (x-averages), the fluidity
+// of Eq. fluidity (shear rate = central difference of ux_z, one-sided at wall rows, wrapped
+// when periodic) and, when sampling, the row's time sums.  One warp per column: the
+// z-averages of P_xx - P_zz and P_xx.  Phase 2 (the last block to finish): the scalars.
+// All sums run in a fixed order, so results are repeatable.
 __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
                                                        int nrowblocks, double* __restrict__ row_sum,
                                                        double* __restrict__ col_sum, unsigned* ticket,
@@ -61,21 +75,54 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                                                        int accumulate) {
     __shared__ double sh[RB_THREADS];
     __shared__ bool last;
+    constexpr int WPB = RB_THREADS / 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int WPB = RB_THREADS / 32;  // one warp per row (or column)
+    const double inx = 1.0 / nx, inz = 1.0 / nz;
+    double* const ux = out + O_PROF;
+    double* const rz = ux + nz;
+    double* const sx = rz + 2LL * nz;
+    double* const fl = sx + nz;
+    double* const ps = fl + nz;
+    double* const px = ps + nx;
     if ((int)blockIdx.x < nrowblocks) {
         const int z = blockIdx.x * WPB + warp;
         if (z < nz) {
             double v[NQR];
-            for (int k = 0; k < NQR; ++k) v[k] = 0.0;
-            for (int p = lane; p < nxpart; p += 32) {
-                const double* src = O.part_row + ((long long)z * nxpart + p) * NQR;
-                for (int k = 0; k < NQR; ++k) v[k] += src[k];
+            for (int k = 0; k < NQR; ++k) v[k] = row_total(O, nxpart, z, k);
+            // neighbours' mean velocity for the shear rate
+            int zl = z - 1, zr = z + 1;
+            double wl = 0.5, wr = 0.5;
+            if (nz == 1) {
+                zl = zr = z;
+            } else if (zbc == 0) {
+                zl = z == 0 ? nz - 1 : z - 1;
+                zr = z == nz - 1 ? 0 : z + 1;
+            } else if (z == 0) {
+                zl = 0;
+                wl = wr = 1.0;
+            } else if (z == nz - 1) {
+                zr = nz - 1;
+                wl = wr = 1.0;
             }
-            for (int k = 0; k < NQR; ++k) {
-                double a = v[k];
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (lane == 0) row_sum[(long long)z * NQR + k] = a;
+            const double ul = zl == z ? v[QR_UX] : row_total(O, nxpart, zl, QR_UX);
+            const double ur = zr == z ? v[QR_UX] : row_total(O, nxpart, zr, QR_UX);
+            if (lane == 0) {
+                for (int k = 0; k < NQR; ++k) row_sum[(long long)z * NQR + k] = v[k];
+                const double gd = nz == 1 ? 0.0 : (wr * ur - wl * ul) * inx;
+                const double sxz = v[QR_SXZ] * inx;
+                ux[z] = v[QR_UX] * inx;
+                rz[z] = v[QR_RHOA] * inx;
+                rz[nz + z] = v[QR_RHOB] * inx;
+                sx[z] = sxz;
+                fl[z] = gd / sxz;
+                if (accumulate) {
+                    double* a = avg + O_PROF;
+                    a[z] += ux[z];
+                    a[nz + z] += rz[z];
+                    a[2LL * nz + z] += rz[nz + z];
+                    a[3LL * nz + z] += sxz;
+                    a[4LL * nz + z] += fl[z];
+                }
             }
         }
     } else {
@@ -87,10 +134,15 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                 const double* src = O.part_col + ((long long)x * nzpart + p) * NQC;
                 for (int k = 0; k < NQC; ++k) v[k] += src[k];
             }
-            for (int k = 0; k < NQC; ++k) {
-                double a = v[k];
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (lane == 0) col_sum[(long long)x * NQC + k] = a;
+            for (int k = 0; k < NQC; ++k) v[k] = warp_sum(v[k]);
+            if (lane == 0) {
+                ps[x] = v[QC_PS] * inz;
+                px[x] = v[QC_PXX] * inz;
+                if (accumulate) {
+                    double* a = avg + O_PROF + 5LL * nz;
+                    a[x] += ps[x];
+                    a[nx + x] += px[x];
+                }
             }
         }
     }
@@ -101,39 +153,6 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     if (!last) return;
     __threadfence();
 
-    double* ux = out + O_PROF;
-    double* rz = ux + nz;
-    double* sx = rz + 2LL * nz;
-    double* fl = sx + nz;
-    double* ps = fl + nz;
-    double* px = ps + nx;
-    for (int z = t; z < nz; z += RB_THREADS) {
-        const double* r = row_sum + (long long)z * NQR;
-        ux[z] = r[QR_UX] / nx;
-        rz[z] = r[QR_RHOA] / nx;
-        rz[nz + z] = r[QR_RHOB] / nx;
-        sx[z] = r[QR_SXZ] / nx;
-    }
-    for (int x = t; x < nx; x += RB_THREADS) {
-        ps[x] = col_sum[(long long)x * NQC + QC_PS] / nz;
-        px[x] = col_sum[(long long)x * NQC + QC_PXX] / nz;
-    }
-    __syncthreads();
-    // Eq. fluidity: shear rate (central difference of ux_z; one-sided at wall rows) / stress
-    for (int z = t; z < nz; z += RB_THREADS) {
-        double gd;
-        if (nz == 1)
-            gd = 0.0;
-        else if (zbc == 0)
-            gd = 0.5 * (ux[z + 1 < nz ? z + 1 : 0] - ux[z > 0 ? z - 1 : nz - 1]);
-        else if (z == 0)
-            gd = ux[1] - ux[0];
-        else if (z == nz - 1)
-            gd = ux[nz - 1] - ux[nz - 2];
-        else
-            gd = 0.5 * (ux[z + 1] - ux[z - 1]);
-        fl[z] = gd / sx[z];
-    }
     double m0 = 0.0, m1 = 0.0, mx = 0.0, mz = 0.0, g = 0.0;
     for (int z = t; z < nz; z += RB_THREADS) {
         const double* r = row_sum + (long long)z * NQR;
@@ -154,20 +173,17 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
         out[O_MOM] = mx;
         out[O_MOM + 1] = mz;
         out[O_GAMMA] = g;
-        out[O_WALL] = zbc ? row_sum[QR_WALLB] / nx : 0.0;
-        out[O_WALL + 1] = zbc ? row_sum[(long long)(nz - 1) * NQR + QR_WALLT] / nx : 0.0;
+        out[O_WALL] = zbc ? row_sum[QR_WALLB] * inx : 0.0;
+        out[O_WALL + 1] = zbc ? row_sum[(long long)(nz - 1) * NQR + QR_WALLT] * inx : 0.0;
         const bool bad = (O.flag[0] & 1) || !isfinite(m0) || !isfinite(m1) || !isfinite(mx) || !isfinite(mz) ||
                          !isfinite(g);
         out[O_BAD] = bad ? 1.0 : 0.0;
+        if (accumulate) {
+            for (int i = 0; i < O_BAD; ++i) avg[i] += out[i];
+            avg[O_BAD] = (avg[O_BAD] != 0.0 || bad) ? 1.0 : 0.0;
+            avg[O_COUNT] += 1.0;
+        }
         *ticket = 0u;
-    }
-    if (accumulate) {
-        __syncthreads();
-        const long long len = obs_len(nx, nz);
-        for (long long i = t; i < len; i += RB_THREADS)
-            if (i < O_COUNT) avg[i] += out[i];
-            else if (i == O_COUNT) avg[i] += 1.0;
-            else if (i >= O_PROF) avg[i] += out[i];
     }
 }
 
