@@ -51,10 +51,10 @@ def _args():
 
 
 def _dist():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1402_6019_gb300 import replicas
+
+    r = replicas.from_env()
+    return r.rank, r.world, r.local
 
 
 class Clocks:
@@ -202,8 +202,10 @@ def main():
     a = _args()
     from paper_1402_6019_gb300 import workloads as W
 
+    from paper_1402_6019_gb300 import replicas
+
     rank, world, local = _dist()
-    w = W.workload(a.workload, seed=1402 + rank)
+    w = W.workload(a.workload, seed=replicas.replica_seed(1402, replicas.from_env()))
     if a.impl == "reference":
         return run_reference(a, w)
 
@@ -258,13 +260,10 @@ def main():
     kern_ms, kern_n = L.lbm_profile_read(lat.h)
     L.lbm_profile(lat.h, False)
     lat.synchronize()
-    if dist:
-        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-
-    ms_per_step = step_ms / a.steps
-    value = sites * world / (ms_per_step * 1e-3) / 1e6
+    # whole job: the slowest rank's time, every rank's sites
+    step_s, job_sites = replicas.aggregate(step_ms * 1e-3, sites, dist=dist, device="cuda")
+    ms_per_step = step_s * 1e3 / a.steps
+    value = job_sites / (ms_per_step * 1e-3) / 1e6
 
     # roofline of the dominant kernel (the fused step kernel)
     bps = BYTES_PER_SITE[(a.precision, ns)]
@@ -292,13 +291,10 @@ def main():
             lat.step(1)
             L.lbm_averages(lat.h, o, True)
         barrier()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt, e2e_sites = replicas.aggregate(time.perf_counter() - t0, sites * a.e2e_steps, dist=dist,
+                                           device="cuda")
         obs_bytes = (16 + 5 * nz + 2 * nx) * 8
-        e2e = {"value": round(sites * world * a.e2e_steps / dt / 1e6, 2), "unit": "MLUPS",
+        e2e = {"value": round(e2e_sites / dt / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": int(rho_np.nbytes // a.e2e_steps), "d2h_bytes_per_step": obs_bytes,
                "steps": a.e2e_steps}
 

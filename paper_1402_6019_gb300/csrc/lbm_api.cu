@@ -35,8 +35,8 @@ struct lbm_ctx {
     GhostGeom ghost{};
     int kernel = LBM_KERNEL_FUSED;  // resolved
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
-    double* part_row = nullptr;
-    double* part_col = nullptr;
+    void* part_row = nullptr;  // partial sums in the populations' precision
+    void* part_col = nullptr;
     double* row_sum = nullptr;
     double* col_sum = nullptr;
     unsigned* ticket = nullptr;
@@ -260,8 +260,8 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     const int tx = (nx + TPX - 1) / TPX, tz = (nz + TPZ - 1) / TPZ;
     const long long rows_parts = std::max(c->geom_obs.nstrips, tx);
     const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
-    CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * sizeof(double)));
-    CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * sizeof(double)));
+    CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * c->esize));
+    CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * c->esize));
     CKC(cudaMalloc(&c->row_sum, (size_t)nz * NQR * sizeof(double)));
     CKC(cudaMalloc(&c->col_sum, (size_t)nx * NQC * sizeof(double)));
     CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
@@ -350,7 +350,7 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         c->ev_used += 2;
     }
     if (reduce) {
-        e = launch_reduce(O, c->geom_obs.nstrips, c->geom_obs.nchunks, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
+        e = launch_reduce((int)c->esize, O, c->geom_obs.nstrips, c->geom_obs.nchunks, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
                           c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
         c->launches += 1;
     }

@@ -304,11 +304,11 @@ LBM_HD int mirror_index(int z, int n) {
 }
 
 // Row whose density stands at row r: periodic wrap, or with walls the mirror image (or -1
-// for the zero ghost reading).
+// for the zero ghost reading).  Rows inside the lattice take the branch without division.
 template <typename T>
 LBM_HD int source_row(const StepConst<T>& C, int r) {
-    if (C.zbc == 0) return wrap_index(r, C.nz);
     if (r >= 0 && r < C.nz) return r;
+    if (C.zbc == 0) return wrap_index(r, C.nz);
     return C.psi_wall == 1 ? -1 : mirror_index(r, C.nz);
 }
 

@@ -219,52 +219,86 @@ __global__ void __launch_bounds__(128) k_fused(const T* __restrict__ fin, T* __r
                 }
             }
             if (MODE & (M_WRITE | M_OBS)) {
-                const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+                const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);  // warp-uniform
                 if ((MODE & M_WRITE) || wall_row) {
                     collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
                     // streaming: f_l(x + c_l) = g_l(x), periodic in x, periodic or walls in z
+                    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+                    const long long rz0 = (long long)z * pitch;
+                    const long long rzm = (long long)(z == 0 ? nz - 1 : z - 1) * pitch;
+                    const long long rzp = (long long)(z == nz - 1 ? 0 : z + 1) * pitch;
+                    if (!wall_row) {
+                        if (MODE & M_WRITE) {
 #pragma unroll
-                    for (int s = 0; s < NS; ++s)
+                            for (int s = 0; s < NS; ++s)
 #pragma unroll
-                        for (int l = 0; l < 9; ++l) {
-                            int zd = z + cz(l);
-                            int xd = x + cx(l);
-                            xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                            if (C.zbc == 0) {
-                                zd = zd < 0 ? zd + nz : (zd >= nz ? zd - nz : zd);
-                            } else if (zd < 0 || zd >= nz) {
-                                const int w = zd < 0 ? 0 : 1;
-                                const T back = bounce<T>(l, f[s][l], rho[s], C.wall_u[w]);
-                                if (MODE & M_WRITE) fout[(s * 9 + opp(l)) * plane + (long long)z * pitch + x] = back;
-                                if (MODE & M_OBS) rowq[QR_WALLB + w] += T(cx(l)) * (f[s][l] + back);
-                                continue;
-                            }
-                            if (MODE & M_WRITE) fout[(s * 9 + l) * plane + (long long)zd * pitch + xd] = f[s][l];
+                                for (int l = 0; l < 9; ++l) {
+                                    const long long row = cz(l) < 0 ? rzm : (cz(l) > 0 ? rzp : rz0);
+                                    const int col = cx(l) < 0 ? xm : (cx(l) > 0 ? xp : x);
+                                    fout[(s * 9 + l) * plane + row + col] = f[s][l];
+                                }
                         }
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < NS; ++s)
+#pragma unroll
+                            for (int l = 0; l < 9; ++l) {
+                                const int zd = z + cz(l);
+                                const int col = cx(l) < 0 ? xm : (cx(l) > 0 ? xp : x);
+                                if (zd < 0 || zd >= nz) {  // halfway bounce-back with Ladd's term
+                                    const int w = zd < 0 ? 0 : 1;
+                                    const T back = bounce<T>(l, f[s][l], rho[s], C.wall_u[w]);
+                                    if (MODE & M_WRITE) fout[(s * 9 + opp(l)) * plane + rz0 + x] = back;
+                                    if (MODE & M_OBS) {  // constant indices keep rowq in registers
+                                        const T dm = T(cx(l)) * (f[s][l] + back);
+                                        if (w == 0)
+                                            rowq[QR_WALLB] += dm;
+                                        else
+                                            rowq[QR_WALLT] += dm;
+                                    }
+                                } else if (MODE & M_WRITE) {
+                                    fout[(s * 9 + l) * plane + (long long)zd * pitch + col] = f[s][l];
+                                }
+                            }
+                    }
                 }
             }
         }
         if (MODE & M_OBS) {
+            // transpose-reduce of the NQR = 8 row quantities over the 32 lanes: each halving
+            // step exchanges half of the remaining values, 4 + 2 + 1 + 1 + 1 shuffles in all;
+            // afterwards lane 4q holds the warp sum of quantity q (fixed order: repeatable)
+            static_assert(NQR == 8, "row reduction is written for 8 quantities");
+            T v4[4], v2[2], v1;
+            const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
 #pragma unroll
-            for (int k = 0; k < NQR; ++k) {
-                T v = rowq[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-                rowq[k] = v;
+            for (int k = 0; k < 4; ++k) {
+                const T keep = b4 ? rowq[k + 4] : rowq[k], send = b4 ? rowq[k] : rowq[k + 4];
+                v4[k] = keep + __shfl_xor_sync(FULL, send, 16);
             }
-            if (lane == 0) {
-                double* dst = O.part_row + ((long long)z * G.nstrips + strip) * NQR;
 #pragma unroll
-                for (int k = 0; k < NQR; ++k) dst[k] = (double)rowq[k];
+            for (int k = 0; k < 2; ++k) {
+                const T keep = b3 ? v4[k + 2] : v4[k], send = b3 ? v4[k] : v4[k + 2];
+                v2[k] = keep + __shfl_xor_sync(FULL, send, 8);
+            }
+            {
+                const T keep = b2 ? v2[1] : v2[0], send = b2 ? v2[0] : v2[1];
+                v1 = keep + __shfl_xor_sync(FULL, send, 4);
+            }
+            v1 += __shfl_xor_sync(FULL, v1, 2);
+            v1 += __shfl_xor_sync(FULL, v1, 1);
+            if ((lane & 3) == 0) {
+                const int q = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+                static_cast<T*>(O.part_row)[((long long)z * G.nstrips + strip) * NQR + q] = v1;
             }
         }
         __syncwarp();  // ring slots read this iteration may be refilled by the next issue
     }
     cp_async_wait<0>();
     if ((MODE & M_OBS) && owned) {
-        double* dst = O.part_col + ((long long)x * G.nchunks + chunk) * NQC;
-        dst[QC_PS] = (double)acc_ps;
-        dst[QC_PXX] = (double)acc_pxx;
+        T* dst = static_cast<T*>(O.part_col) + ((long long)x * G.nchunks + chunk) * NQC;
+        dst[QC_PS] = acc_ps;
+        dst[QC_PXX] = acc_pxx;
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(O.flag, 1);
 }

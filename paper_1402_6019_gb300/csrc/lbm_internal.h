@@ -20,10 +20,11 @@ struct SweepGeom {
     int hz;       // rows swept by one warp
 };
 
-// Output pointers of the step kernels (device memory).
+// Output pointers of the step kernels (device memory).  The partial sums are stored in the
+// precision of the populations (float or double) and widened to FP64 by the reduction.
 struct ObsPtrs {
-    double* part_row;  // [nz][nxpart][NQR]   per-row sums over a group of columns
-    double* part_col;  // [nx][nzpart][NQC]   per-column sums over a group of rows
+    void* part_row;    // [nz][nxpart][NQR]   per-row sums over a group of columns
+    void* part_col;    // [nx][nzpart][NQC]   per-column sums over a group of rows
     double* fields;    // [ns + 2][nz][nx]    rho_s, u_x, u_z (M_FIELDS)
     int* flag;         // bit 0: a density <= 0 / NaN / Inf was met
 };
@@ -58,7 +59,7 @@ template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, cudaStream_t st);
 template <typename T>
 cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, cudaStream_t st);
-cudaError_t launch_reduce(const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc, double* row_sum,
+cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc, double* row_sum,
                           double* col_sum, unsigned* ticket, double* out, double* avg, int accumulate,
                           cudaStream_t st);
 

@@ -56,18 +56,15 @@ __device__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the column groups of one quantity of row z (whole warp; fixed order).
-__device__ double row_total(const ObsPtrs& O, int nxpart, int z, int k) {
-    double v = 0.0;
-    for (int p = threadIdx.x & 31; p < nxpart; p += 32) v += O.part_row[((long long)z * nxpart + p) * NQR + k];
-    return warp_sum(v);
-}
+constexpr int MAXP = 4;  // partial groups a lane loads up front (x 32 lanes); more loop
 
 // Phase 1, one warp per row: the row's sums, its profile entries (x-averages), the fluidity
 // of Eq. fluidity (shear rate = central difference of ux_z, one-sided at wall rows, wrapped
 // when periodic) and, when sampling, the row's time sums.  One warp per column: the
 // z-averages of P_xx - P_zz and P_xx.  Phase 2 (the last block to finish): the scalars.
-// All sums run in a fixed order, so results are repeatable.
+// Every lane issues all its loads before reducing (one memory latency per warp).  All sums
+// run in a fixed order, so results are repeatable.
+template <typename PT>
 __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
                                                        int nrowblocks, double* __restrict__ row_sum,
                                                        double* __restrict__ col_sum, unsigned* ticket,
@@ -78,6 +75,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     constexpr int WPB = RB_THREADS / 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const double inx = 1.0 / nx, inz = 1.0 / nz;
+    const PT* const prow = static_cast<const PT*>(O.part_row);
+    const PT* const pcol = static_cast<const PT*>(O.part_col);
     double* const ux = out + O_PROF;
     double* const rz = ux + nz;
     double* const sx = rz + 2LL * nz;
@@ -87,9 +86,6 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     if ((int)blockIdx.x < nrowblocks) {
         const int z = blockIdx.x * WPB + warp;
         if (z < nz) {
-            double v[NQR];
-            for (int k = 0; k < NQR; ++k) v[k] = row_total(O, nxpart, z, k);
-            // neighbours' mean velocity for the shear rate
             int zl = z - 1, zr = z + 1;
             double wl = 0.5, wr = 0.5;
             if (nz == 1) {
@@ -104,11 +100,32 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                 zr = nz - 1;
                 wl = wr = 1.0;
             }
-            const double ul = zl == z ? v[QR_UX] : row_total(O, nxpart, zl, QR_UX);
-            const double ur = zr == z ? v[QR_UX] : row_total(O, nxpart, zr, QR_UX);
+            double v[NQR + 2];
+            for (int k = 0; k < NQR + 2; ++k) v[k] = 0.0;
+            for (int p0 = 0; p0 < nxpart; p0 += 32 * MAXP) {
+                PT a[MAXP][NQR], bl[MAXP], br[MAXP];
+#pragma unroll
+                for (int i = 0; i < MAXP; ++i) {
+                    const int p = p0 + lane + 32 * i;
+                    const bool ok = p < nxpart;
+#pragma unroll
+                    for (int k = 0; k < NQR; ++k) a[i][k] = ok ? prow[((long long)z * nxpart + p) * NQR + k] : PT(0);
+                    bl[i] = ok ? prow[((long long)zl * nxpart + p) * NQR + QR_UX] : PT(0);
+                    br[i] = ok ? prow[((long long)zr * nxpart + p) * NQR + QR_UX] : PT(0);
+                }
+#pragma unroll
+                for (int i = 0; i < MAXP; ++i) {
+#pragma unroll
+                    for (int k = 0; k < NQR; ++k) v[k] += (double)a[i][k];
+                    v[NQR] += (double)bl[i];
+                    v[NQR + 1] += (double)br[i];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NQR + 2; ++k) v[k] = warp_sum(v[k]);
             if (lane == 0) {
                 for (int k = 0; k < NQR; ++k) row_sum[(long long)z * NQR + k] = v[k];
-                const double gd = nz == 1 ? 0.0 : (wr * ur - wl * ul) * inx;
+                const double gd = nz == 1 ? 0.0 : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
                 const double sxz = v[QR_SXZ] * inx;
                 ux[z] = v[QR_UX] * inx;
                 rz[z] = v[QR_RHOA] * inx;
@@ -130,10 +147,21 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
         if (x < nx) {
             double v[NQC];
             for (int k = 0; k < NQC; ++k) v[k] = 0.0;
-            for (int p = lane; p < nzpart; p += 32) {
-                const double* src = O.part_col + ((long long)x * nzpart + p) * NQC;
-                for (int k = 0; k < NQC; ++k) v[k] += src[k];
+            for (int p0 = 0; p0 < nzpart; p0 += 32 * MAXP) {
+                PT a[MAXP][NQC];
+#pragma unroll
+                for (int i = 0; i < MAXP; ++i) {
+                    const int p = p0 + lane + 32 * i;
+#pragma unroll
+                    for (int k = 0; k < NQC; ++k)
+                        a[i][k] = p < nzpart ? pcol[((long long)x * nzpart + p) * NQC + k] : PT(0);
+                }
+#pragma unroll
+                for (int i = 0; i < MAXP; ++i)
+#pragma unroll
+                    for (int k = 0; k < NQC; ++k) v[k] += (double)a[i][k];
             }
+#pragma unroll
             for (int k = 0; k < NQC; ++k) v[k] = warp_sum(v[k]);
             if (lane == 0) {
                 ps[x] = v[QC_PS] * inz;
@@ -205,13 +233,17 @@ cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc, double* row_sum,
-                          double* col_sum, unsigned* ticket, double* out, double* avg, int accumulate,
-                          cudaStream_t st) {
+cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
+                          double* row_sum, double* col_sum, unsigned* ticket, double* out, double* avg,
+                          int accumulate, cudaStream_t st) {
     const int rb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int cb = (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-    k_reduce<<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket, out, avg,
-                                             accumulate);
+    if (precision_bytes == 4)
+        k_reduce<float><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket,
+                                                        out, avg, accumulate);
+    else
+        k_reduce<double><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket,
+                                                         out, avg, accumulate);
     return cudaGetLastError();
 }
 
