@@ -45,6 +45,7 @@ def _args():
     ap.add_argument("--workload", default="emulsion_1024")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--rows-per-warp", type=int, default=0)
+    ap.add_argument("--kernel", choices=["fused", "twopass"], default="fused")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     return ap.parse_args()
@@ -232,7 +233,8 @@ def main():
     # a non-default stream: the library runs on it, and the events below are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=L.LBM_KERNEL_FUSED, device=local,
+    kern = L.LBM_KERNEL_FUSED if a.kernel == "fused" else L.LBM_KERNEL_TWO_PASS
+    lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
                     stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, **w["params"])
     lat.set_fields(w["rho"])
     lat.set_observe(1)  # every step reduces the observables of the state it collides
@@ -273,7 +275,9 @@ def main():
     traffic = _traffic(kernel_source_hash(), a.workload, a.precision)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "lbm::k_fused<T, 2, M_WRITE|M_OBS>", "kernel_ms": round(kern_avg_ms, 5),
+                "kernel": ("lbm::k_fused<T, 2, M_WRITE|M_OBS>" if a.kernel == "fused"
+                           else "lbm::k_density + lbm::k_twopass<T, 2, M_WRITE|M_OBS>"),
+                "kernel_ms": round(kern_avg_ms, 5),
                 "algorithmic_bytes_per_site": bps}
 
     # end to end through the public API with host buffers: upload the fields from pinned host
@@ -308,7 +312,7 @@ def main():
         "config": {"workload": a.workload, "nx": nx, "nz": nz, "n_species": ns,
                    "precision": a.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "flushed between timed steps (256 MiB write)", "observables": "every step",
-                   "rows_per_warp": lat.desc.rows_per_warp},
+                   "rows_per_warp": lat.desc.rows_per_warp, "kernel": a.kernel},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

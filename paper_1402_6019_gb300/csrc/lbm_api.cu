@@ -46,6 +46,7 @@ struct lbm_ctx {
     double* staging = nullptr;  // (ns + 2) * n doubles
     double* fexport = nullptr;  // ns * 9 * n doubles
     void* gfield = nullptr;     // two-pass ghost fields
+    alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
     double* host_out = nullptr; // pinned
     StepConst<float> c32{};
     StepConst<double> c64{};
@@ -275,10 +276,12 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     CKC(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
     CKC(cudaMemsetAsync(c->avg, 0, olen, c->stream));
     if (c->kernel == LBM_KERNEL_TWO_PASS) {
-        c->ghost.gpitch = (nx + 2 * GX + 3) / 4 * 4;
+        c->ghost.gpitch = (nx + 2 * GX + 3) / 4 * 4;  // 16-byte rows for the TMA descriptor
         c->ghost.gplane = (long long)(nz + 4) * c->ghost.gpitch;
         CKC(cudaMalloc(&c->gfield, (size_t)2 * ns * c->ghost.gplane * c->esize));
         CKC(cudaMemsetAsync(c->gfield, 0, (size_t)2 * ns * c->ghost.gplane * c->esize, c->stream));
+        if (make_field_tmap(c->tmap, c->gfield, (int)c->esize, ns, nz, c->ghost) != 0)
+            return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the two-pass field planes"));
     }
     CKC(cudaStreamSynchronize(c->stream));
 #undef CKC
@@ -335,13 +338,33 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         e = cudaEventRecord(c->ev[c->ev_used], c->stream);
         if (e != cudaSuccess) return e;
     }
-    const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
-    if (c->d.precision == LBM_FP64)
-        e = launch_fused<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64, G,
-                                 O, c->stream);
-    else
-        e = launch_fused<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32, G, O,
-                                c->stream);
+    const bool twopass = c->kernel == LBM_KERNEL_TWO_PASS && (mode & M_WRITE);
+    const int tpx = (c->d.nx + TPX - 1) / TPX, tpz = (c->d.nz + TPZ - 1) / TPZ;
+    if (twopass) {
+        // K1: densities and pseudopotentials into the ghost-padded planes; K2: collide and push
+        if (c->d.precision == LBM_FP64) {
+            e = launch_density<double>(c->d.n_species, (const double*)c->f[cur], (double*)c->gfield, c->c64, c->ghost,
+                                       c->stream);
+            if (e == cudaSuccess)
+                e = launch_twopass<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1],
+                                           (const double*)c->gfield, c->c64, c->ghost, c->tmap, O, tpx, tpz, c->stream);
+        } else {
+            e = launch_density<float>(c->d.n_species, (const float*)c->f[cur], (float*)c->gfield, c->c32, c->ghost,
+                                      c->stream);
+            if (e == cudaSuccess)
+                e = launch_twopass<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1],
+                                          (const float*)c->gfield, c->c32, c->ghost, c->tmap, O, tpx, tpz, c->stream);
+        }
+        c->launches += 1;
+    } else {
+        const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
+        if (c->d.precision == LBM_FP64)
+            e = launch_fused<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64, G,
+                                     O, c->stream);
+        else
+            e = launch_fused<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32, G, O,
+                                    c->stream);
+    }
     c->launches += 1;
     if (e != cudaSuccess) return e;
     if (timed) {
@@ -350,7 +373,8 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         c->ev_used += 2;
     }
     if (reduce) {
-        e = launch_reduce((int)c->esize, O, c->geom_obs.nstrips, c->geom_obs.nchunks, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
+        const int nxp = twopass ? tpx : c->geom_obs.nstrips, nzp = twopass ? tpz : c->geom_obs.nchunks;
+        e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
                           c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
         c->launches += 1;
     }
@@ -556,6 +580,7 @@ extern "C" int lbm_synchronize(lbm_ctx* c) {
     CK(cudaStreamSynchronize(c->stream));
     int flag = 0;
     CK(cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 2) return fail(c, LBM_ETIMEOUT, "a bounded device-side wait for a tile load gave up");
     if (flag & 1) return fail(c, LBM_ENONFINITE, "a step met a density <= 0, NaN or Inf");
     return LBM_OK;
 }

@@ -55,6 +55,9 @@ template <typename T>
 cudaError_t launch_twopass(int ns, int mode, const T* fin, T* fout, const T* gfield, const StepConst<T>& C,
                            const GhostGeom& GG, const void* tmap, const ObsPtrs& O, int nxpart, int nzpart,
                            cudaStream_t st);
+// Encodes the TMA descriptor (CUtensorMap, 128 bytes at out) of the two-pass field planes.
+// Returns 0 on success.
+int make_field_tmap(void* out, const void* g, int esize, int ns, int nz, const GhostGeom& GG);
 template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, cudaStream_t st);
 template <typename T>

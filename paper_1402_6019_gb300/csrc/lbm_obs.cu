@@ -51,19 +51,20 @@ __device__ double block_sum(double v, double* sh) {
 
 constexpr int RB_THREADS = 256;
 
-__device__ double warp_sum(double v) {
+template <typename PT>
+__device__ PT warp_sum(PT v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-constexpr int MAXP = 4;  // partial groups a lane loads up front (x 32 lanes); more loop
-
-// Phase 1, one warp per row: the row's sums, its profile entries (x-averages), the fluidity
-// of Eq. fluidity (shear rate = central difference of ux_z, one-sided at wall rows, wrapped
-// when periodic) and, when sampling, the row's time sums.  One warp per column: the
-// z-averages of P_xx - P_zz and P_xx.  Phase 2 (the last block to finish): the scalars.
-// Every lane issues all its loads before reducing (one memory latency per warp).  All sums
-// run in a fixed order, so results are repeatable.
+// Phase 1, one warp per row: the row's sums over its column groups, its profile entries
+// (x-averages), the fluidity of Eq. fluidity (shear rate = central difference of ux_z,
+// one-sided at wall rows, wrapped when periodic) and, when sampling, the row's time sums.  One
+// warp per column: the z-averages of P_xx - P_zz and P_xx.  Phase 2 (the last block to
+// finish): the global scalars (mass, momentum, gamma, wall stress) summed in FP64.
+// Group sums within a row or a column stay in the populations' precision PT (in FP32 mode they
+// are sums of FP32 values; FP64 arithmetic is scarce on this GPU); each row or column total is
+// widened to FP64 once.  All sums run in a fixed order, so results are repeatable.
 template <typename PT>
 __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
                                                        int nrowblocks, double* __restrict__ row_sum,
@@ -100,36 +101,25 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                 zr = nz - 1;
                 wl = wr = 1.0;
             }
-            double v[NQR + 2];
-            for (int k = 0; k < NQR + 2; ++k) v[k] = 0.0;
-            for (int p0 = 0; p0 < nxpart; p0 += 32 * MAXP) {
-                PT a[MAXP][NQR], bl[MAXP], br[MAXP];
+            PT v[NQR + 2];
 #pragma unroll
-                for (int i = 0; i < MAXP; ++i) {
-                    const int p = p0 + lane + 32 * i;
-                    const bool ok = p < nxpart;
+            for (int k = 0; k < NQR + 2; ++k) v[k] = PT(0);
+            for (int p = lane; p < nxpart; p += 32) {
+                const PT* src = prow + ((long long)z * nxpart + p) * NQR;
 #pragma unroll
-                    for (int k = 0; k < NQR; ++k) a[i][k] = ok ? prow[((long long)z * nxpart + p) * NQR + k] : PT(0);
-                    bl[i] = ok ? prow[((long long)zl * nxpart + p) * NQR + QR_UX] : PT(0);
-                    br[i] = ok ? prow[((long long)zr * nxpart + p) * NQR + QR_UX] : PT(0);
-                }
-#pragma unroll
-                for (int i = 0; i < MAXP; ++i) {
-#pragma unroll
-                    for (int k = 0; k < NQR; ++k) v[k] += (double)a[i][k];
-                    v[NQR] += (double)bl[i];
-                    v[NQR + 1] += (double)br[i];
-                }
+                for (int k = 0; k < NQR; ++k) v[k] += src[k];
+                v[NQR] += prow[((long long)zl * nxpart + p) * NQR + QR_UX];
+                v[NQR + 1] += prow[((long long)zr * nxpart + p) * NQR + QR_UX];
             }
 #pragma unroll
             for (int k = 0; k < NQR + 2; ++k) v[k] = warp_sum(v[k]);
             if (lane == 0) {
-                for (int k = 0; k < NQR; ++k) row_sum[(long long)z * NQR + k] = v[k];
-                const double gd = nz == 1 ? 0.0 : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
-                const double sxz = v[QR_SXZ] * inx;
-                ux[z] = v[QR_UX] * inx;
-                rz[z] = v[QR_RHOA] * inx;
-                rz[nz + z] = v[QR_RHOB] * inx;
+                for (int k = 0; k < NQR; ++k) row_sum[(long long)z * NQR + k] = (double)v[k];
+                const double gd = nz == 1 ? 0.0 : (wr * (double)v[NQR + 1] - wl * (double)v[NQR]) * inx;
+                const double sxz = (double)v[QR_SXZ] * inx;
+                ux[z] = (double)v[QR_UX] * inx;
+                rz[z] = (double)v[QR_RHOA] * inx;
+                rz[nz + z] = (double)v[QR_RHOB] * inx;
                 sx[z] = sxz;
                 fl[z] = gd / sxz;
                 if (accumulate) {
@@ -145,27 +135,19 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     } else {
         const int x = (blockIdx.x - nrowblocks) * WPB + warp;
         if (x < nx) {
-            double v[NQC];
-            for (int k = 0; k < NQC; ++k) v[k] = 0.0;
-            for (int p0 = 0; p0 < nzpart; p0 += 32 * MAXP) {
-                PT a[MAXP][NQC];
+            PT v[NQC];
 #pragma unroll
-                for (int i = 0; i < MAXP; ++i) {
-                    const int p = p0 + lane + 32 * i;
+            for (int k = 0; k < NQC; ++k) v[k] = PT(0);
+            for (int p = lane; p < nzpart; p += 32) {
+                const PT* src = pcol + ((long long)x * nzpart + p) * NQC;
 #pragma unroll
-                    for (int k = 0; k < NQC; ++k)
-                        a[i][k] = p < nzpart ? pcol[((long long)x * nzpart + p) * NQC + k] : PT(0);
-                }
-#pragma unroll
-                for (int i = 0; i < MAXP; ++i)
-#pragma unroll
-                    for (int k = 0; k < NQC; ++k) v[k] += (double)a[i][k];
+                for (int k = 0; k < NQC; ++k) v[k] += src[k];
             }
 #pragma unroll
             for (int k = 0; k < NQC; ++k) v[k] = warp_sum(v[k]);
             if (lane == 0) {
-                ps[x] = v[QC_PS] * inz;
-                px[x] = v[QC_PXX] * inz;
+                ps[x] = (double)v[QC_PS] * inz;
+                px[x] = (double)v[QC_PXX] * inz;
                 if (accumulate) {
                     double* a = avg + O_PROF + 5LL * nz;
                     a[x] += ps[x];

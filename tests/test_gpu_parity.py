@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 1e-4
+KERNELS = pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWO_PASS], ids=["fused", "twopass"])
 
 
 def rel(a, b):
@@ -85,21 +86,24 @@ def test_fp64_single_component_128_periodic_1000_steps(oracle):
     assert abs(o["mass"][0] - w["rho"].sum()) / w["rho"].sum() < 1e-13
 
 
+@KERNELS
 @pytest.mark.parametrize("G_AB", [0.405, 0.587])
-def test_fp64_emulsion_ragged_periodic(oracle, G_AB):
-    nx, nz = 100, 72  # 100 = 3 strips of 28 + 16: ragged last strip
+def test_fp64_emulsion_ragged_periodic(oracle, G_AB, kernel):
+    nx, nz = 100, 75  # 100 = 3 strips of 28 + 16, and 3 tiles of 32 + 4: ragged in x and z
     rho, _ = W.disk_packing(nx, nz, 0.8, seed=3, r_mean=8, r_spread=2)
-    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP64, rho, 300, **dict(W.EMULSION_PARAMS, G_AB=G_AB))
+    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP64, rho, 300, kernel=kernel,
+                    **dict(W.EMULSION_PARAMS, G_AB=G_AB))
     check_fields(ref, lat, TOL64)
     check_obs(ref, lat, 1e-11)
 
 
+@KERNELS
 @pytest.mark.parametrize("psi_wall", [0, 1])
-def test_fp64_channel_walls_drives(oracle, psi_wall):
+def test_fp64_channel_walls_drives(oracle, psi_wall, kernel):
     nx, nz = 61, 37
     rho, _ = W.disk_packing(nx, nz, 0.7, seed=5, r_mean=6, r_spread=2, periodic_z=False)
     prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(-0.01, 0.02), body_force=1e-5, psi_wall=psi_wall)
-    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP64, rho, 300, **prm)
+    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP64, rho, 300, kernel=kernel, **prm)
     check_fields(ref, lat, TOL64)
     check_obs(ref, lat, 1e-11)
 
@@ -113,13 +117,14 @@ def test_fp64_unequal_tau_chem09_rho_psi(oracle):
     check_fields(ref, lat, TOL64)
 
 
+@KERNELS
 @pytest.mark.parametrize("nx,nz,ns,zbc", [(1, 1, 1, 0), (5, 7, 2, 0), (3, 1, 1, 1), (29, 5, 2, 1),
                                            (30, 2, 1, 0), (57, 3, 2, 0), (2, 9, 2, 1)])
-def test_fp64_tiny_and_degenerate(oracle, nx, nz, ns, zbc):
+def test_fp64_tiny_and_degenerate(oracle, nx, nz, ns, zbc, kernel):
     rho = W.noise_field(nx, nz, seed=nx * 100 + nz, mean=0.8, amp=0.2, n_species=ns)
     u = 0.01 * W.noise_field(nx, nz, seed=7, mean=0.0, amp=1.0, n_species=2)
     prm = dict(W.EMULSION_PARAMS if ns == 2 else W.SINGLE_PARAMS, wall_u=(0.01, -0.02), body_force=2e-5)
-    ref, lat = pair(oracle, nx, nz, ns, zbc, L.LBM_FP64, rho, 60, u=u, **prm)
+    ref, lat = pair(oracle, nx, nz, ns, zbc, L.LBM_FP64, rho, 60, u=u, kernel=kernel, **prm)
     check_fields(ref, lat, TOL64)
     check_obs(ref, lat, 1e-11)
 
@@ -150,10 +155,11 @@ def test_graph_replay_equals_single_steps():
 
 # --- FP32 deviations: the contract at 1e-4 after 1000 steps --------------------------------
 
-def test_fp32_emulsion_1000_steps(oracle):
+@KERNELS
+def test_fp32_emulsion_1000_steps(oracle, kernel):
     nx = nz = 128
     rho, _ = W.disk_packing(nx, nz, 0.8, seed=1402)
-    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP32, rho, 1000, **W.EMULSION_PARAMS)
+    ref, lat = pair(oracle, nx, nz, 2, 0, L.LBM_FP32, rho, 1000, kernel=kernel, **W.EMULSION_PARAMS)
     e_rho, e_u = check_fields(ref, lat, TOL32, pops=False)
     check_obs(ref, lat, 1e-4)
 
@@ -190,13 +196,14 @@ def test_fp32_faster_path_is_fp32():
 
 # --- observables, averages, errors ------------------------------------------------------------
 
-def test_time_averages_match_oracle_mean(oracle):
+@KERNELS
+def test_time_averages_match_oracle_mean(oracle, kernel):
     nx, nz = 48, 32
     rho, _ = W.disk_packing(nx, nz, 0.6, seed=12, r_mean=5, r_spread=1, periodic_z=False)
     prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(-0.01, 0.01))
     ref = oracle.RefLattice(nx, nz, 2, 1, **prm)
     ref.set_fields(rho)
-    lat = L.Lattice(nx, nz, 2, L.LBM_FP64, 1, **prm)
+    lat = L.Lattice(nx, nz, 2, L.LBM_FP64, 1, kernel=kernel, **prm)
     lat.set_fields(rho)
     lat.set_observe(1)
     n = 20
