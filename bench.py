@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--workload", default="emulsion_1024")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--rows-per-warp", type=int, default=0)
-    ap.add_argument("--kernel", choices=["fused", "twopass"], default="fused")
+    ap.add_argument("--kernel", choices=["fused", "twopass", "sweep"], default="fused")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     return ap.parse_args()
@@ -132,7 +132,7 @@ def _traffic(kernel_src_hash, workload, precision):
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for f in ("lbm_fused.cu", "lbm_core.cuh"):
+    for f in ("lbm_tile.cu", "lbm_core.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1402_6019_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -233,7 +233,7 @@ def main():
     # a non-default stream: the library runs on it, and the events below are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    kern = L.LBM_KERNEL_FUSED if a.kernel == "fused" else L.LBM_KERNEL_TWO_PASS
+    kern = {"fused": L.LBM_KERNEL_FUSED, "twopass": L.LBM_KERNEL_TWO_PASS, "sweep": L.LBM_KERNEL_SWEEP}[a.kernel]
     lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
                     stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, **w["params"])
     lat.set_fields(w["rho"])
@@ -275,8 +275,9 @@ def main():
     traffic = _traffic(kernel_source_hash(), a.workload, a.precision)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "kernel": ("lbm::k_fused<T, 2, M_WRITE|M_OBS>" if a.kernel == "fused"
-                           else "lbm::k_density + lbm::k_twopass<T, 2, M_WRITE|M_OBS>"),
+                "kernel": {"fused": "lbm::k_tile<T, 2, M_WRITE|M_OBS>",
+                           "twopass": "lbm::k_density + lbm::k_twopass<T, 2, M_WRITE|M_OBS>",
+                           "sweep": "lbm::k_fused<T, 2, M_WRITE|M_OBS>"}[a.kernel],
                 "kernel_ms": round(kern_avg_ms, 5),
                 "algorithmic_bytes_per_site": bps}
 

@@ -133,7 +133,7 @@ static int check_desc(lbm_ctx* c, const lbm_desc* d) {
     if (d->precision != LBM_FP64 && d->precision != LBM_FP32) return fail(c, LBM_EINVAL, "unknown precision");
     if (d->z_boundary != LBM_PERIODIC && d->z_boundary != LBM_BOUNCEBACK)
         return fail(c, LBM_EINVAL, "unknown z boundary");
-    if (d->kernel < LBM_KERNEL_AUTO || d->kernel > LBM_KERNEL_TWO_PASS) return fail(c, LBM_EINVAL, "unknown kernel");
+    if (d->kernel < LBM_KERNEL_AUTO || d->kernel > LBM_KERNEL_SWEEP) return fail(c, LBM_EINVAL, "unknown kernel");
     if (d->rows_per_warp < 0 || d->rows_per_warp > 65536) return fail(c, LBM_EINVAL, "rows_per_warp out of range");
     if (d->device < 0) return fail(c, LBM_EINVAL, "negative device ordinal");
     return LBM_OK;
@@ -241,7 +241,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
     c->pitch = (nx + 31) / 32 * 32;
     c->plane = (long long)nz * c->pitch;
-    c->kernel = d->kernel == LBM_KERNEL_TWO_PASS ? LBM_KERNEL_TWO_PASS : LBM_KERNEL_FUSED;
+    c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_FUSED : d->kernel;
     const size_t fbytes = (size_t)ns * 9 * c->plane * c->esize;
     CKC(cudaMalloc(&c->f[0], fbytes));
     CKC(cudaMalloc(&c->f[1], fbytes));
@@ -263,8 +263,8 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
     CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * c->esize));
     CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * c->esize));
-    CKC(cudaMalloc(&c->row_sum, (size_t)nz * NQR * sizeof(double)));
-    CKC(cudaMalloc(&c->col_sum, (size_t)nx * NQC * sizeof(double)));
+    CKC(cudaMalloc(&c->row_sum, (size_t)2 * sizeof(double)));                 // wall momenta
+    CKC(cudaMalloc(&c->col_sum, (size_t)(nx + nz) * 5 * sizeof(double)));    // scalar slots
     CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
     CKC(cudaMalloc(&c->flag, sizeof(int)));
     const size_t olen = (size_t)obs_len(nx, nz) * sizeof(double);
@@ -356,7 +356,7 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
                                           (const float*)c->gfield, c->c32, c->ghost, c->tmap, O, tpx, tpz, c->stream);
         }
         c->launches += 1;
-    } else {
+    } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
             e = launch_fused<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64, G,
@@ -364,6 +364,13 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         else
             e = launch_fused<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32, G, O,
                                     c->stream);
+    } else {
+        if (c->d.precision == LBM_FP64)
+            e = launch_tile<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64, O,
+                                    c->stream);
+        else
+            e = launch_tile<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32, O,
+                                   c->stream);
     }
     c->launches += 1;
     if (e != cudaSuccess) return e;
@@ -373,7 +380,8 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         c->ev_used += 2;
     }
     if (reduce) {
-        const int nxp = twopass ? tpx : c->geom_obs.nstrips, nzp = twopass ? tpz : c->geom_obs.nchunks;
+        const bool sweep = c->kernel == LBM_KERNEL_SWEEP;
+        const int nxp = sweep ? c->geom_obs.nstrips : tpx, nzp = sweep ? c->geom_obs.nchunks : tpz;
         e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
                           c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
         c->launches += 1;

@@ -67,18 +67,24 @@ LBM_HD double psi_of(const StepConst<double>& C, int s, double rho) {
 // ---------------------------------------------------------------------------------------
 template <typename T>
 LBM_HD void intra_force(const StepConst<T>& C, int s, const T (&p)[5][5], T& fx, T& fz) {
-    T ax = T(0), az = T(0);
+    // one partial sum per stencil row: five independent chains instead of one long one
+    T ax[5], az[5];
 #pragma unroll
-    for (int dz = -2; dz <= 2; ++dz)
+    for (int dz = -2; dz <= 2; ++dz) {
+        ax[dz + 2] = T(0);
+        az[dz + 2] = T(0);
 #pragma unroll
         for (int dx = -2; dx <= 2; ++dx) {
             if (dx == 0 && dz == 0) continue;
             const int i = (dz + 2) * 5 + dx + 2;
-            if (dx != 0) ax += C.kx[s][i] * p[dz + 2][dx + 2];
-            if (dz != 0) az += C.kz[s][i] * p[dz + 2][dx + 2];
+            if (dx != 0) ax[dz + 2] += C.kx[s][i] * p[dz + 2][dx + 2];
+            if (dz != 0) az[dz + 2] += C.kz[s][i] * p[dz + 2][dx + 2];
         }
-    fx = -p[2][2] * ax;
-    fz = -p[2][2] * az;
+    }
+    const T sx = (ax[0] + ax[4]) + (ax[1] + ax[3]) + ax[2];
+    const T sz = (az[0] + az[4]) + (az[1] + az[3]);
+    fx = -p[2][2] * sx;
+    fz = -p[2][2] * sz;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -91,43 +97,33 @@ LBM_HD void intra_stress(const StepConst<T>& C, int s, const T (&p)[5][5], T& sx
 #define LBM_P(dx, dz) p[(dz) + 2][(dx) + 2]
     const T p0 = LBM_P(0, 0);
     const T* q = C.sq[s];
-    // |c|^2 = 1
-    sxx += q[1] * p0 * (LBM_P(1, 0) + LBM_P(-1, 0));
-    szz += q[1] * p0 * (LBM_P(0, 1) + LBM_P(0, -1));
-    // |c|^2 = 2
-    {
-        const T d = LBM_P(1, 1) + LBM_P(-1, -1), a = LBM_P(-1, 1) + LBM_P(1, -1);
-        sxx += q[2] * p0 * (d + a);
-        szz += q[2] * p0 * (d + a);
-        sxz += q[2] * p0 * (d - a);
-    }
+    // |c|^2 = 1 and 2: node products
+    const T d2 = LBM_P(1, 1) + LBM_P(-1, -1), a2 = LBM_P(-1, 1) + LBM_P(1, -1);
+    const T n12x = q[1] * (LBM_P(1, 0) + LBM_P(-1, 0)) + q[2] * (d2 + a2);
+    const T n12z = q[1] * (LBM_P(0, 1) + LBM_P(0, -1)) + q[2] * (d2 + a2);
+    const T n12xz = q[2] * (d2 - a2);
     // |c|^2 = 4: node products and half-link products psi(x - c/2) psi(x + c/2)
-    sxx += T(4) * q[4] * (p0 * (LBM_P(2, 0) + LBM_P(-2, 0)) + T(2) * LBM_P(-1, 0) * LBM_P(1, 0));
-    szz += T(4) * q[4] * (p0 * (LBM_P(0, 2) + LBM_P(0, -2)) + T(2) * LBM_P(0, -1) * LBM_P(0, 1));
-    // |c|^2 = 5: node products over the 8 links (+-2,+-1), (+-1,+-2)
-    {
-        const T a21 = LBM_P(2, 1) + LBM_P(-2, -1), b21 = LBM_P(-2, 1) + LBM_P(2, -1);
-        const T a12 = LBM_P(1, 2) + LBM_P(-1, -2), b12 = LBM_P(-1, 2) + LBM_P(1, -2);
-        sxx += q[5] * p0 * (T(4) * (a21 + b21) + (a12 + b12));
-        szz += q[5] * p0 * ((a21 + b21) + T(4) * (a12 + b12));
-        sxz += q[5] * p0 * (T(2) * (a21 - b21) + T(2) * (a12 - b12));
-        // pair terms: links c13 = (2,1), c14 = (1,2), c15 = (-1,2), c16 = (-2,1)
-        const T t13 = LBM_P(1, 1) * LBM_P(-1, 0) + LBM_P(1, 0) * LBM_P(-1, -1);
-        const T t14 = LBM_P(1, 1) * LBM_P(0, -1) + LBM_P(0, 1) * LBM_P(-1, -1);
-        const T t15 = LBM_P(0, 1) * LBM_P(1, -1) + LBM_P(-1, 1) * LBM_P(0, -1);
-        const T t16 = LBM_P(-1, 1) * LBM_P(1, 0) + LBM_P(-1, 0) * LBM_P(1, -1);
-        sxx += q[5] * (T(4) * t13 + t14 + t15 + T(4) * t16);
-        szz += q[5] * (t13 + T(4) * t14 + T(4) * t15 + t16);
-        sxz += q[5] * (T(2) * t13 + T(2) * t14 - T(2) * t15 - T(2) * t16);
-    }
+    const T s4x = T(4) * q[4] * (p0 * (LBM_P(2, 0) + LBM_P(-2, 0)) + T(2) * LBM_P(-1, 0) * LBM_P(1, 0));
+    const T s4z = T(4) * q[4] * (p0 * (LBM_P(0, 2) + LBM_P(0, -2)) + T(2) * LBM_P(0, -1) * LBM_P(0, 1));
+    // |c|^2 = 5: node products over the 8 links (+-2,+-1), (+-1,+-2), and the pair terms of
+    // links c13 = (2,1), c14 = (1,2), c15 = (-1,2), c16 = (-2,1)
+    const T a21 = LBM_P(2, 1) + LBM_P(-2, -1), b21 = LBM_P(-2, 1) + LBM_P(2, -1);
+    const T a12 = LBM_P(1, 2) + LBM_P(-1, -2), b12 = LBM_P(-1, 2) + LBM_P(1, -2);
+    const T t13 = LBM_P(1, 1) * LBM_P(-1, 0) + LBM_P(1, 0) * LBM_P(-1, -1);
+    const T t14 = LBM_P(1, 1) * LBM_P(0, -1) + LBM_P(0, 1) * LBM_P(-1, -1);
+    const T t15 = LBM_P(0, 1) * LBM_P(1, -1) + LBM_P(-1, 1) * LBM_P(0, -1);
+    const T t16 = LBM_P(-1, 1) * LBM_P(1, 0) + LBM_P(-1, 0) * LBM_P(1, -1);
+    const T s5x = q[5] * (p0 * (T(4) * (a21 + b21) + (a12 + b12)) + (T(4) * (t13 + t16) + (t14 + t15)));
+    const T s5z = q[5] * (p0 * ((a21 + b21) + T(4) * (a12 + b12)) + ((t13 + t16) + T(4) * (t14 + t15)));
+    const T s5xz = q[5] * (T(2) * p0 * ((a21 - b21) + (a12 - b12)) + T(2) * ((t13 + t14) - (t15 + t16)));
     // |c|^2 = 8: node and half-link products over (+-2,+-2)
-    {
-        const T a22 = LBM_P(2, 2) + LBM_P(-2, -2), b22 = LBM_P(-2, 2) + LBM_P(2, -2);
-        const T ha = T(2) * LBM_P(-1, -1) * LBM_P(1, 1), hb = T(2) * LBM_P(-1, 1) * LBM_P(1, -1);
-        sxx += T(4) * q[8] * (p0 * (a22 + b22) + ha + hb);
-        szz += T(4) * q[8] * (p0 * (a22 + b22) + ha + hb);
-        sxz += T(4) * q[8] * (p0 * (a22 - b22) + ha - hb);
-    }
+    const T a22 = LBM_P(2, 2) + LBM_P(-2, -2), b22 = LBM_P(-2, 2) + LBM_P(2, -2);
+    const T ha = T(2) * LBM_P(-1, -1) * LBM_P(1, 1), hb = T(2) * LBM_P(-1, 1) * LBM_P(1, -1);
+    const T s8 = T(4) * q[8] * (p0 * (a22 + b22) + (ha + hb));
+    const T s8xz = T(4) * q[8] * (p0 * (a22 - b22) + (ha - hb));
+    sxx += (p0 * n12x + s4x) + (s5x + s8);
+    szz += (p0 * n12z + s4z) + (s5z + s8);
+    sxz += (p0 * n12xz + s5xz) + s8xz;
 #undef LBM_P
 }
 
@@ -179,7 +175,7 @@ LBM_HD void cross_stress(const StepConst<T>& C, const T (&ra)[3][3], const T (&r
 // ---------------------------------------------------------------------------------------
 template <typename T>
 LBM_HD T sum9(const T (&f)[9]) {
-    return f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
 }
 template <typename T>
 LBM_HD void momentum9(const T (&f)[9], T& jx, T& jz) {

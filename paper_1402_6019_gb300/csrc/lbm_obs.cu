@@ -35,21 +35,8 @@ __global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ o
     }
 }
 
-__device__ double block_sum(double v, double* sh) {
-    // deterministic: fixed tree over the block
-    const int t = threadIdx.x;
-    sh[t] = v;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (t < o) sh[t] += sh[t + o];
-        __syncthreads();
-    }
-    const double r = sh[0];
-    __syncthreads();
-    return r;
-}
-
 constexpr int RB_THREADS = 256;
+constexpr int NSC = 5;  // scalar slots per row / column: mass A, mass B, momentum x, z; gamma
 
 template <typename PT>
 __device__ PT warp_sum(PT v) {
@@ -71,7 +58,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                                                        double* __restrict__ col_sum, unsigned* ticket,
                                                        double* __restrict__ out, double* __restrict__ avg,
                                                        int accumulate) {
-    __shared__ double sh[RB_THREADS];
+    __shared__ double sh5[NSC * RB_THREADS];
     __shared__ bool last;
     constexpr int WPB = RB_THREADS / 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -114,7 +101,14 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 #pragma unroll
             for (int k = 0; k < NQR + 2; ++k) v[k] = warp_sum(v[k]);
             if (lane == 0) {
-                for (int k = 0; k < NQR; ++k) row_sum[(long long)z * NQR + k] = (double)v[k];
+                // this row's contributions to the scalars (mass A, mass B, momentum x, z)
+                double* w = col_sum + (long long)z * NSC;
+                w[0] = (double)v[QR_RHOA];
+                w[1] = (double)v[QR_RHOB];
+                w[2] = (double)v[QR_MX];
+                w[3] = (double)v[QR_MZ];
+                if (z == 0) row_sum[0] = (double)v[QR_WALLB];
+                if (z == nz - 1) row_sum[1] = (double)v[QR_WALLT];
                 const double gd = nz == 1 ? 0.0 : (wr * (double)v[NQR + 1] - wl * (double)v[NQR]) * inx;
                 const double sxz = (double)v[QR_SXZ] * inx;
                 ux[z] = (double)v[QR_UX] * inx;
@@ -148,6 +142,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
             if (lane == 0) {
                 ps[x] = (double)v[QC_PS] * inz;
                 px[x] = (double)v[QC_PXX] * inz;
+                col_sum[((long long)nz + x) * NSC + 4] = ps[x];  // this column's share of gamma
                 if (accumulate) {
                     double* a = avg + O_PROF + 5LL * nz;
                     a[x] += ps[x];
@@ -163,28 +158,29 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     if (!last) return;
     __threadfence();
 
-    double m0 = 0.0, m1 = 0.0, mx = 0.0, mz = 0.0, g = 0.0;
-    for (int z = t; z < nz; z += RB_THREADS) {
-        const double* r = row_sum + (long long)z * NQR;
-        m0 += r[QR_RHOA];
-        m1 += r[QR_RHOB];
-        mx += r[QR_MX];
-        mz += r[QR_MZ];
+    // scalars: rows hold slots 0..3, columns slot 4, in fixed order
+    double acc[NSC] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int z = t; z < nz; z += RB_THREADS)
+        for (int k = 0; k < 4; ++k) acc[k] += col_sum[(long long)z * NSC + k];
+    for (int x = t; x < nx; x += RB_THREADS) acc[4] += col_sum[((long long)nz + x) * NSC + 4];
+    double* shv = sh5;
+    for (int k = 0; k < NSC; ++k) shv[k * RB_THREADS + t] = acc[k];
+    __syncthreads();
+    for (int o = RB_THREADS / 2; o > 0; o >>= 1) {
+        if (t < o)
+            for (int k = 0; k < NSC; ++k) shv[k * RB_THREADS + t] += shv[k * RB_THREADS + t + o];
+        __syncthreads();
     }
-    for (int x = t; x < nx; x += RB_THREADS) g += ps[x];
-    m0 = block_sum(m0, sh);
-    m1 = block_sum(m1, sh);
-    mx = block_sum(mx, sh);
-    mz = block_sum(mz, sh);
-    g = block_sum(g, sh);
     if (t == 0) {
+        const double m0 = shv[0], m1 = shv[RB_THREADS], mx = shv[2 * RB_THREADS], mz = shv[3 * RB_THREADS],
+                     g = shv[4 * RB_THREADS];
         out[O_MASS] = m0;
         out[O_MASS + 1] = m1;
         out[O_MOM] = mx;
         out[O_MOM + 1] = mz;
         out[O_GAMMA] = g;
-        out[O_WALL] = zbc ? row_sum[QR_WALLB] * inx : 0.0;
-        out[O_WALL + 1] = zbc ? row_sum[(long long)(nz - 1) * NQR + QR_WALLT] * inx : 0.0;
+        out[O_WALL] = zbc ? row_sum[0] * inx : 0.0;
+        out[O_WALL + 1] = zbc ? row_sum[1] * inx : 0.0;
         const bool bad = (O.flag[0] & 1) || !isfinite(m0) || !isfinite(m1) || !isfinite(mx) || !isfinite(mz) ||
                          !isfinite(g);
         out[O_BAD] = bad ? 1.0 : 0.0;

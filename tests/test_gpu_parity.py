@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 1e-4
-KERNELS = pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWO_PASS], ids=["fused", "twopass"])
+KERNELS = pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWO_PASS, L.LBM_KERNEL_SWEEP],
+                                  ids=["tile", "twopass", "sweep"])
 
 
 def rel(a, b):
@@ -130,11 +131,11 @@ def test_fp64_tiny_and_degenerate(oracle, nx, nz, ns, zbc, kernel):
 
 
 @pytest.mark.parametrize("rpw", [1, 3, 200])
-def test_fp64_row_chunking(oracle, rpw):
+def test_fp64_sweep_row_chunking(oracle, rpw):
     nx, nz = 64, 50
     rho, _ = W.disk_packing(nx, nz, 0.7, seed=9, r_mean=6, r_spread=2, periodic_z=False)
     prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(0.0, 0.01))
-    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP64, rho, 50, rpw=rpw, **prm)
+    ref, lat = pair(oracle, nx, nz, 2, 1, L.LBM_FP64, rho, 50, rpw=rpw, kernel=L.LBM_KERNEL_SWEEP, **prm)
     check_fields(ref, lat, TOL64)
     check_obs(ref, lat, 1e-11)
 
