@@ -57,12 +57,11 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                                                        int nrowblocks, double* __restrict__ row_sum,
                                                        double* __restrict__ col_sum, unsigned* ticket,
                                                        double* __restrict__ out, double* __restrict__ avg,
-                                                       int accumulate) {
+                                                       int accumulate, double inx, double inz) {
     __shared__ double sh5[NSC * RB_THREADS];
     __shared__ bool last;
     constexpr int WPB = RB_THREADS / 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const double inx = 1.0 / nx, inz = 1.0 / nz;
     const PT* const prow = static_cast<const PT*>(O.part_row);
     const PT* const pcol = static_cast<const PT*>(O.part_col);
     double* const ux = out + O_PROF;
@@ -151,12 +150,16 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
             }
         }
     }
-    __threadfence();
+    // the block's writes happen before thread 0's fence (barrier), and the fence is cumulative:
+    // whichever block draws the last ticket sees every block's results
     __syncthreads();
-    if (t == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (t == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (last) __threadfence();
+    }
     __syncthreads();
     if (!last) return;
-    __threadfence();
 
     // scalars: rows hold slots 0..3, columns slot 4, in fixed order
     double acc[NSC] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -218,10 +221,10 @@ cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int
     const int cb = (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     if (precision_bytes == 4)
         k_reduce<float><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket,
-                                                        out, avg, accumulate);
+                                                        out, avg, accumulate, 1.0 / nx, 1.0 / nz);
     else
         k_reduce<double><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, row_sum, col_sum, ticket,
-                                                         out, avg, accumulate);
+                                                         out, avg, accumulate, 1.0 / nx, 1.0 / nz);
     return cudaGetLastError();
 }
 

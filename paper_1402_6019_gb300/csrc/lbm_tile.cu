@@ -21,28 +21,6 @@ constexpr int HW = TPX + 4;  // halo tile width
 constexpr int HH = TPZ + 4;  // halo tile height
 constexpr int NRING = HW * HH - TPX * TPZ;
 
-template <typename T, int NS>
-__device__ __forceinline__ void site_density(const T* __restrict__ fin, const StepConst<T>& C, int xs, int zs,
-                                             T (&rho)[NS], T (&psi)[NS]) {
-    const int rr = source_row(C, zs);
-    if (rr < 0) {  // zero ghost row beyond a wall
-#pragma unroll
-        for (int s = 0; s < NS; ++s) rho[s] = psi[s] = T(0);
-        return;
-    }
-    const int xw = xs < 0 ? xs + C.nx : (xs >= C.nx ? xs - C.nx : xs);
-    const int xx = (xw >= 0 && xw < C.nx) ? xw : wrap_index(xs, C.nx);
-    const T* base = fin + (long long)rr * C.pitch + xx;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        T v[9];
-#pragma unroll
-        for (int l = 0; l < 9; ++l) v[l] = __ldg(base + (s * 9 + l) * C.plane);
-        rho[s] = C.rho_ref[s] + sum9(v);
-        psi[s] = psi_of(C, s, rho[s]);
-    }
-}
-
 template <typename T, int NS, int MODE>
 __global__ void __launch_bounds__(TPX* TPZ) k_tile(const T* __restrict__ fin, T* __restrict__ fout,
                                                    const StepConst<T> C, const ObsPtrs O, int nxpart, int nzpart) {
@@ -57,49 +35,59 @@ __global__ void __launch_bounds__(TPX* TPZ) k_tile(const T* __restrict__ fin, T*
     const bool live = x < nx && z < nz;
 
     // ---- phase A: densities and psi of the tile and its 2-cell ring ----
+    // Every thread loads its own site and (threads below NRING) one ring site before summing,
+    // so both sets of loads are in flight together.
     T f[NS][9];
     T drho[NS];
-    if (live) {
-        const T* base = fin + (long long)z * C.pitch + x;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-#pragma unroll
-            for (int l = 0; l < 9; ++l) f[s][l] = __ldg(base + (s * 9 + l) * plane);
-            drho[s] = sum9(f[s]);
-            const T r = C.rho_ref[s] + drho[s];
-            srh[s][tz + 2][tx + 2] = r;
-            sps[s][tz + 2][tx + 2] = psi_of(C, s, r);
-        }
-    } else {  // a position of a ragged tile beyond the lattice: its periodic / mirror image
-        T r[NS], p[NS];
-        site_density<T, NS>(fin, C, x, z, r, p);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            srh[s][tz + 2][tx + 2] = r[s];
-            sps[s][tz + 2][tx + 2] = p[s];
+    int rhx = 0, rhz = 0;
+    const bool ring = tid < NRING;
+    if (ring) {  // ring order: top two rows, bottom two rows, then two columns on each side
+        if (tid < 2 * HW) {
+            rhz = tid / HW;
+            rhx = tid % HW;
+        } else if (tid < 4 * HW) {
+            rhz = HH - 2 + (tid - 2 * HW) / HW;
+            rhx = (tid - 2 * HW) % HW;
+        } else {
+            const int j = tid - 4 * HW;  // 0 .. 4 TPZ - 1
+            rhz = 2 + (j >> 2);
+            const int c = j & 3;
+            rhx = c < 2 ? c : HW - 4 + c;
         }
     }
-    for (int k = tid; k < NRING; k += TPX * TPZ) {
-        // ring order: top two rows, bottom two rows, then the two columns on each side
-        int hx, hz;
-        if (k < 2 * HW) {
-            hz = k / HW;
-            hx = k % HW;
-        } else if (k < 4 * HW) {
-            hz = HH - 2 + (k - 2 * HW) / HW;
-            hx = (k - 2 * HW) % HW;
-        } else {
-            const int j = k - 4 * HW;  // 0 .. 4 TPZ - 1
-            hz = 2 + (j >> 2);
-            const int c = j & 3;
-            hx = c < 2 ? c : HW - 4 + c;
-        }
-        T r[NS], p[NS];
-        site_density<T, NS>(fin, C, x0 - 2 + hx, z0 - 2 + hz, r, p);
+    static_assert(NRING <= TPX * TPZ, "one ring site per thread at most");
+    const int own_x = live ? x : x0 - 2 + (tx + 2), own_z = live ? z : z0 - 2 + (tz + 2);
+    const int own_r = source_row(C, own_z);
+    const int ring_r = ring ? source_row(C, z0 - 2 + rhz) : -1;
+    auto wrapx = [&](int xs) {
+        const int xw = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        return (xw >= 0 && xw < nx) ? xw : wrap_index(xs, nx);
+    };
+    T g[NS][9];
+    if (own_r >= 0) {
+        const T* base = fin + (long long)own_r * C.pitch + wrapx(own_x);
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            srh[s][hz][hx] = r[s];
-            sps[s][hz][hx] = p[s];
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int l = 0; l < 9; ++l) f[s][l] = __ldg(base + (s * 9 + l) * plane);
+    }
+    if (ring_r >= 0) {
+        const T* base = fin + (long long)ring_r * C.pitch + wrapx(x0 - 2 + rhx);
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int l = 0; l < 9; ++l) g[s][l] = __ldg(base + (s * 9 + l) * plane);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        drho[s] = own_r >= 0 ? sum9(f[s]) : -C.rho_ref[s];
+        const T r = C.rho_ref[s] + drho[s];
+        srh[s][tz + 2][tx + 2] = r;
+        sps[s][tz + 2][tx + 2] = own_r >= 0 ? psi_of(C, s, r) : T(0);
+        if (ring) {
+            const T rr = ring_r >= 0 ? C.rho_ref[s] + sum9(g[s]) : T(0);
+            srh[s][rhz][rhx] = rr;
+            sps[s][rhz][rhx] = ring_r >= 0 ? psi_of(C, s, rr) : T(0);
         }
     }
     __syncthreads();
