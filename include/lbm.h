@@ -171,6 +171,33 @@ void lbm_destroy(lbm_ctx *c);
 /* LBM_ABI_VERSION of the library. */
 int lbm_abi_version(void);
 
+/* Observables without any allocation.  The paper has no counterpart: this serves callers
+   that cannot let a library allocate device memory while they run -- code being recorded
+   into a CUDA graph (cudaMalloc may not be called during stream capture), real-time loops
+   that must not wait on the allocator, and applications whose own pool holds the whole
+   device.  It computes what lbm_observables computes, for a state the caller holds:
+     f       device pointer, FP64 populations after streaming, [n_species][9][nz][nx] (the
+             layout lbm_get_fields writes), read on `stream`;
+     p       the model parameters (host);
+     out     device pointer to 16 + 5 nz + 2 nx doubles, written on `stream`: [0..1] mass,
+             [2..3] momentum, [4] gamma, [5..6] wall force (bottom, top), [7] 1 if a density
+             <= 0, NaN or Inf was met, [8..15] unused, then ux_z[nz], rho_z[2][nz], sxz_z[nz],
+             fluid_z[nz], ps_x[nx], pxx_x[nx] (definitions as in lbm_obs; rho_z of species B
+             is zero for one species).
+   It allocates nothing: its scratch is one file-scope device array of
+   LBM_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit, which bounds
+   the lattice: bytes needed = r256(nz*ceil(nx/32)*64) + r256(nx*ceil(nz/8)*16)
+   + r256((nx+nz)*40) + 256, r256 rounding up to a multiple of 256 (a 1024 x 1024 lattice
+   needs about 4.3 MB).  The first call on a device looks up the array's device address with
+   that device current, so make the first call before any stream capture.  All calls share the
+   array: calls that overlap on the GPU (other streams, other threads) race and must be
+   serialised by the caller.  Asynchronous on `stream` (NULL = the default stream).
+   Returns LBM_OK, LBM_EINVAL (NULL pointer or invalid description/parameters), LBM_ENOMEM
+   (the lattice does not fit the fixed scratch) or LBM_ECUDA (no device / launch failure). */
+#define LBM_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+int lbm_observables_noalloc(const double *f, int nx, int nz, int n_species, int z_boundary,
+                            const lbm_params *p, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

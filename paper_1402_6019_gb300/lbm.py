@@ -69,6 +69,8 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, [_VP]),
     "lbm_destroy": (None, [_VP]),
     "lbm_abi_version": (ctypes.c_int, []),
+    "lbm_observables_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(lbm_params), _VP, _VP]),
 }
 
 _lib = None
@@ -214,6 +216,13 @@ def lbm_destroy(h):
 
 def lbm_abi_version() -> int:
     return load().lbm_abi_version()
+
+
+def lbm_observables_noalloc(f_dev_ptr, nx, nz, n_species, z_boundary, p: lbm_params, out_dev_ptr, stream=None):
+    """Observables of FP64 populations held in caller device memory, with no allocation
+    (see include/lbm.h); returns the status code."""
+    return load().lbm_observables_noalloc(ctypes.c_void_p(f_dev_ptr), nx, nz, n_species, z_boundary,
+                                          ctypes.byref(p), ctypes.c_void_p(out_dev_ptr), ctypes.c_void_p(stream))
 
 
 # ---- convenience ---------------------------------------------------------------------------
