@@ -48,6 +48,9 @@ def _args():
     ap.add_argument("--kernel", choices=["fused", "twopass", "sweep"], default="fused")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--observe-every", type=int, default=1,
+                    help="sample the observables every k steps (1 = every step, the full hot path; "
+                         "0 = never, for analysis only)")
     return ap.parse_args()
 
 
@@ -237,7 +240,7 @@ def main():
     lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
                     stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, **w["params"])
     lat.set_fields(w["rho"])
-    lat.set_observe(1)  # every step reduces the observables of the state it collides
+    lat.set_observe(a.observe_every)  # 1: every step reduces the observables of the state it collides
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(a.warmup):
@@ -312,7 +315,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": a.workload, "nx": nx, "nz": nz, "n_species": ns,
                    "precision": a.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MiB write)", "observables": "every step",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "observables": ("every step" if a.observe_every == 1 else
+                                   "never" if a.observe_every == 0 else f"every {a.observe_every} steps"),
                    "rows_per_warp": lat.desc.rows_per_warp, "kernel": a.kernel},
         "roofline": roofline,
         "e2e": e2e,

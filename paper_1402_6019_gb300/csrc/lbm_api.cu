@@ -384,7 +384,7 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const int nxp = sweep ? c->geom_obs.nstrips : tpx, nzp = sweep ? c->geom_obs.nchunks : tpz;
         e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
                           c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
-        c->launches += 1;
+        c->launches += 2;  // row/column totals, then scalars
     }
     return e;
 }
@@ -420,7 +420,7 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
                 CK(e);
             }
             CK(cudaGraphLaunch(ge, c->stream));
-            c->launches += (long long)G * (ob ? 2 : 1);
+            c->launches += (long long)G * (ob ? 3 : 1);
             c->step += G;  // G is even: the parity of cur is unchanged
             left -= G;
             continue;
