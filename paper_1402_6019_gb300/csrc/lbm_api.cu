@@ -264,7 +264,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * c->esize));
     CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * c->esize));
     CKC(cudaMalloc(&c->row_sum, (size_t)2 * sizeof(double)));                 // wall momenta
-    CKC(cudaMalloc(&c->col_sum, (size_t)(nx + nz) * 5 * sizeof(double)));    // scalar slots
+    CKC(cudaMalloc(&c->col_sum, (size_t)(nx + nz) * 5 * sizeof(double)));    // per-block scalar partials
     CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
     CKC(cudaMalloc(&c->flag, sizeof(int)));
     const size_t olen = (size_t)obs_len(nx, nz) * sizeof(double);
@@ -384,7 +384,7 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const int nxp = sweep ? c->geom_obs.nstrips : tpx, nzp = sweep ? c->geom_obs.nchunks : tpz;
         e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
                           c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
-        c->launches += 2;  // row/column totals, then scalars
+        c->launches += 1;
     }
     return e;
 }
@@ -420,7 +420,7 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
                 CK(e);
             }
             CK(cudaGraphLaunch(ge, c->stream));
-            c->launches += (long long)G * (ob ? 3 : 1);
+            c->launches += (long long)G * (ob ? 2 : 1);
             c->step += G;  // G is even: the parity of cur is unchanged
             left -= G;
             continue;

@@ -22,7 +22,7 @@ constexpr int HH = TPZ + 4;  // halo tile height
 constexpr int NRING = HW * HH - TPX * TPZ;
 
 template <typename T, int NS, int MODE>
-__global__ void __launch_bounds__(TPX* TPZ) k_tile(const T* __restrict__ fin, T* __restrict__ fout,
+__global__ void __launch_bounds__(TPX* TPZ, sizeof(T) == 4 ? 4 : 2) k_tile(const T* __restrict__ fin, T* __restrict__ fout,
                                                    const StepConst<T> C, const ObsPtrs O, int nxpart, int nzpart) {
     __shared__ T sps[NS][HH][HW];
     __shared__ T srh[NS][HH][HW];
@@ -169,28 +169,40 @@ __global__ void __launch_bounds__(TPX* TPZ) k_tile(const T* __restrict__ fin, T*
                 const long long rz0 = (long long)z * C.pitch;
                 const long long rzm = (long long)(z == 0 ? nz - 1 : z - 1) * C.pitch;
                 const long long rzp = (long long)(z == nz - 1 ? 0 : z + 1) * C.pitch;
+                if (!wall_row) {  // warp-uniform: every destination lies in the lattice
+                    if (MODE & M_WRITE) {
 #pragma unroll
-                for (int s = 0; s < NS; ++s)
+                        for (int s = 0; s < NS; ++s)
 #pragma unroll
-                    for (int l = 0; l < 9; ++l) {
-                        const int zd = z + cz(l);
-                        if (wall_row && (zd < 0 || zd >= nz)) {  // halfway bounce-back with Ladd's term
-                            const int w = zd < 0 ? 0 : 1;
-                            const T back = bounce<T>(l, f[s][l], rho[s], C.wall_u[w]);
-                            if (MODE & M_WRITE) fout[(s * 9 + opp(l)) * plane + rz0 + x] = back;
-                            if (MODE & M_OBS) {
-                                const T dm = T(cx(l)) * (f[s][l] + back);
-                                if (w == 0)
-                                    rowq[QR_WALLB] += dm;
-                                else
-                                    rowq[QR_WALLT] += dm;
+                            for (int l = 0; l < 9; ++l) {
+                                const long long row = cz(l) < 0 ? rzm : (cz(l) > 0 ? rzp : rz0);
+                                const int col = cx(l) < 0 ? xm : (cx(l) > 0 ? xp : x);
+                                fout[(s * 9 + l) * plane + row + col] = f[s][l];
                             }
-                        } else if (MODE & M_WRITE) {
-                            const long long row = cz(l) < 0 ? rzm : (cz(l) > 0 ? rzp : rz0);
-                            const int col = cx(l) < 0 ? xm : (cx(l) > 0 ? xp : x);
-                            fout[(s * 9 + l) * plane + row + col] = f[s][l];
-                        }
                     }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+#pragma unroll
+                        for (int l = 0; l < 9; ++l) {
+                            const int zd = z + cz(l);
+                            const int col = cx(l) < 0 ? xm : (cx(l) > 0 ? xp : x);
+                            if (zd < 0 || zd >= nz) {  // halfway bounce-back with Ladd's term
+                                const int w = zd < 0 ? 0 : 1;
+                                const T back = bounce<T>(l, f[s][l], rho[s], C.wall_u[w]);
+                                if (MODE & M_WRITE) fout[(s * 9 + opp(l)) * plane + rz0 + x] = back;
+                                if (MODE & M_OBS) {
+                                    const T dm = T(cx(l)) * (f[s][l] + back);
+                                    if (w == 0)
+                                        rowq[QR_WALLB] += dm;
+                                    else
+                                        rowq[QR_WALLT] += dm;
+                                }
+                            } else if (MODE & M_WRITE) {
+                                fout[(s * 9 + l) * plane + (long long)zd * C.pitch + col] = f[s][l];
+                            }
+                        }
+                }
             }
         }
     }
