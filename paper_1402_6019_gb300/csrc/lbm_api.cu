@@ -523,33 +523,37 @@ extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int
 // ---------------------------------------------------------------------------------------
 // Observables
 // ---------------------------------------------------------------------------------------
+// Entry i of the device observable buffers: a double (FP64 mode) or a (hi, lo) float pair
+// (FP32 mode, compensated sums); widened here to FP64.
+static double entry(const lbm_ctx* c, const double* buf, long long i) {
+    if (c->d.precision == LBM_FP64) return buf[i];
+    const float* p = reinterpret_cast<const float*>(buf) + 2 * i;
+    return (double)p[0] + (double)p[1];
+}
+
 static void unpack(const lbm_ctx* c, const double* buf, lbm_obs* o, double scale) {
     const int nx = c->d.nx, nz = c->d.nz, ns = c->d.n_species;
-    o->mass[0] = buf[O_MASS] * scale;
-    o->mass[1] = ns == 2 ? buf[O_MASS + 1] * scale : 0.0;
-    o->momentum[0] = buf[O_MOM] * scale;
-    o->momentum[1] = buf[O_MOM + 1] * scale;
-    o->gamma = buf[O_GAMMA] * scale;
-    o->wall_force[0] = buf[O_WALL] * scale;
-    o->wall_force[1] = buf[O_WALL + 1] * scale;
-    o->nonfinite = buf[O_BAD] != 0.0;
+    auto E = [&](long long i) { return entry(c, buf, i); };
+    o->mass[0] = E(O_MASS) * scale;
+    o->mass[1] = ns == 2 ? E(O_MASS + 1) * scale : 0.0;
+    o->momentum[0] = E(O_MOM) * scale;
+    o->momentum[1] = E(O_MOM + 1) * scale;
+    o->gamma = E(O_GAMMA) * scale;
+    o->wall_force[0] = E(O_WALL) * scale;
+    o->wall_force[1] = E(O_WALL + 1) * scale;
+    o->nonfinite = E(O_BAD) != 0.0;
     o->step = c->step;
-    const double* ux = buf + O_PROF;
-    const double* rz = ux + nz;
-    const double* sx = rz + 2LL * nz;
-    const double* fl = sx + nz;
-    const double* ps = fl + nz;
-    const double* px = ps + nx;
+    const long long ux = O_PROF, rz = ux + nz, sx = rz + 2LL * nz, fl = sx + nz, ps = fl + nz, px = ps + nx;
     for (int z = 0; z < nz; ++z) {
-        if (o->ux_z) o->ux_z[z] = ux[z] * scale;
-        if (o->sxz_z) o->sxz_z[z] = sx[z] * scale;
-        if (o->fluid_z) o->fluid_z[z] = fl[z] * scale;
+        if (o->ux_z) o->ux_z[z] = E(ux + z) * scale;
+        if (o->sxz_z) o->sxz_z[z] = E(sx + z) * scale;
+        if (o->fluid_z) o->fluid_z[z] = E(fl + z) * scale;
         if (o->rho_z)
-            for (int s = 0; s < ns; ++s) o->rho_z[s * nz + z] = rz[s * nz + z] * scale;
+            for (int s = 0; s < ns; ++s) o->rho_z[s * nz + z] = E(rz + (long long)s * nz + z) * scale;
     }
     for (int x = 0; x < nx; ++x) {
-        if (o->ps_x) o->ps_x[x] = ps[x] * scale;
-        if (o->pxx_x) o->pxx_x[x] = px[x] * scale;
+        if (o->ps_x) o->ps_x[x] = E(ps + x) * scale;
+        if (o->pxx_x) o->pxx_x[x] = E(px + x) * scale;
     }
 }
 
@@ -574,9 +578,9 @@ extern "C" int lbm_averages(lbm_ctx* c, lbm_obs* o, int reset) {
     const size_t olen = (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double);
     CK(cudaMemcpyAsync(c->host_out, c->avg, olen, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    const double n = c->host_out[O_COUNT];
+    const double n = entry(c, c->host_out, O_COUNT);
     unpack(c, c->host_out, o, n > 0 ? 1.0 / n : 0.0);
-    o->nonfinite = c->host_out[O_BAD] != 0.0;
+    o->nonfinite = entry(c, c->host_out, O_BAD) != 0.0;
     o->samples = (long long)n;
     if (reset) CK(cudaMemsetAsync(c->avg, 0, olen, c->stream));
     return LBM_OK;

@@ -44,40 +44,83 @@ __device__ PT warp_sum(PT v) {
     return v;
 }
 
+// Accumulators of the reduction.  FP64 mode: plain doubles.  FP32 mode: double-float pairs
+// (hi + lo, compensated summation with Knuth's TwoSum on the FP32 pipes, about 48 significant
+// bits) -- the FP64 unit of this GPU has long latency and low throughput, and on the
+// reduction's short dependent chains each FP64 operation cost microseconds, so in FP32 mode no
+// FP64 arithmetic is issued; the host widens hi + lo to FP64.  Entry i of `out` and `avg` is an
+// 8-byte double (FP64 mode) or an 8-byte (hi, lo) float pair (FP32 mode).
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float2 s = two_sum(a.x, b.x);
+    const float lo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(s.x, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s.x)));
+}
+
+template <typename PT> struct Red;
+template <> struct Red<double> {
+    using A = double;
+    __device__ static A zero() { return 0.0; }
+    __device__ static A from(double v) { return v; }
+    __device__ static A add(A a, A b) { return a + b; }
+    __device__ static void put(void* buf, long long i, A v) { static_cast<double*>(buf)[i] = v; }
+    __device__ static void acc(void* buf, long long i, A v) { static_cast<double*>(buf)[i] += v; }
+    __device__ static A get(const void* buf, long long i) { return static_cast<const double*>(buf)[i]; }
+    __device__ static bool finite(A a) { return isfinite(a); }
+    __device__ static bool nonzero(A a) { return a != 0.0; }
+};
+template <> struct Red<float> {
+    using A = float2;
+    __device__ static A zero() { return make_float2(0.f, 0.f); }
+    __device__ static A from(float v) { return make_float2(v, 0.f); }
+    __device__ static A add(A a, A b) { return ff_add(a, b); }
+    __device__ static void put(void* buf, long long i, A v) { static_cast<float2*>(buf)[i] = v; }
+    __device__ static void acc(void* buf, long long i, A v) {
+        float2* p = static_cast<float2*>(buf) + i;
+        *p = ff_add(*p, v);
+    }
+    __device__ static A get(const void* buf, long long i) { return static_cast<const float2*>(buf)[i]; }
+    __device__ static bool finite(A a) { return isfinite(a.x) && isfinite(a.y); }
+    __device__ static bool nonzero(A a) { return a.x != 0.f || a.y != 0.f; }
+};
+
 // One warp per row: the row's totals over its column groups, its profile entries
 // (x-averages), its fluidity (Eq. fluidity: shear rate = central difference of ux_z, one-sided
 // at wall rows, wrapped when periodic, over the shear stress) and, when sampling, its time
 // sums.  One warp per column: the z-averages of P_xx - P_zz and P_xx.  Each block folds the
 // scalar contributions of its rows (mass A, B, momentum x, z) or columns (gamma) into one
-// FP64 partial; the last block to finish sums the block partials.  Group sums within a row or
-// a column stay in the populations' precision PT (in FP32 mode they are sums of FP32 values;
-// FP64 arithmetic is scarce on this GPU, so the FP64 work is spread over all blocks); each
-// total is widened to FP64 once.  Every sum runs in a fixed order: repeatable results.
+// partial; the last block to finish sums the block partials.  Group sums within a row or a
+// column stay in the populations' precision PT; the scalars and time sums use the
+// accumulators above.  Every sum runs in a fixed order: repeatable results.
 template <typename PT>
 __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
-                                                       int nrowblocks, double* __restrict__ walls,
-                                                       double* __restrict__ bpart, unsigned* ticket,
-                                                       double* __restrict__ out, double* __restrict__ avg,
-                                                       int accumulate, double inx, double inz) {
+                                                       int nrowblocks, PT* __restrict__ walls,
+                                                       void* __restrict__ bpart, unsigned* ticket,
+                                                       void* __restrict__ out, void* __restrict__ avg,
+                                                       int accumulate, PT inx, PT inz) {
+    using R = Red<PT>;
+    using A = typename R::A;
     constexpr int WPB = RB_THREADS / 32;
-    __shared__ double wsc[WPB][NSC];
-    __shared__ double fin[NSC][RB_THREADS];
+    __shared__ A wsc[WPB][NSC];
+    __shared__ A fin[NSC][RB_THREADS];
     __shared__ bool last;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const PT* const prow = static_cast<const PT*>(O.part_row);
     const PT* const pcol = static_cast<const PT*>(O.part_col);
-    double* const ux = out + O_PROF;
-    double* const rz = ux + nz;
-    double* const sx = rz + 2LL * nz;
-    double* const fl = sx + nz;
-    double* const ps = fl + nz;
-    double* const px = ps + nx;
-    for (int k = lane; k < NSC; k += 32) wsc[warp][k] = 0.0;
+    const long long iux = O_PROF, irz = O_PROF + nz, isx = O_PROF + 3LL * nz, ifl = O_PROF + 4LL * nz,
+                    ips = O_PROF + 5LL * nz, ipx = ips + nx;
+    for (int k = lane; k < NSC; k += 32) wsc[warp][k] = R::zero();
     if ((int)blockIdx.x < nrowblocks) {
         const int z = blockIdx.x * WPB + warp;
         if (z < nz) {
             int zl = z - 1, zr = z + 1;
-            double wl = 0.5, wr = 0.5;
+            PT wl = PT(0.5), wr = PT(0.5);
             if (nz == 1) {
                 zl = zr = z;
             } else if (zbc == 0) {
@@ -85,10 +128,10 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                 zr = z == nz - 1 ? 0 : z + 1;
             } else if (z == 0) {
                 zl = 0;
-                wl = wr = 1.0;
+                wl = wr = PT(1);
             } else if (z == nz - 1) {
                 zr = nz - 1;
-                wl = wr = 1.0;
+                wl = wr = PT(1);
             }
             PT v[NQR + 2];
 #pragma unroll
@@ -108,36 +151,36 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 #pragma unroll
                 for (int k = 1; k < NQR; ++k)
                     if (lane == k) mine = v[k];
-                const double d = (double)mine;
+                const A d = R::from(mine);
+                const A dn = R::from(mine * inx);
                 switch (lane) {
                     case QR_UX:
-                        ux[z] = d * inx;
-                        if (accumulate) avg[O_PROF + z] += d * inx;
+                        R::put(out, iux + z, dn);
+                        if (accumulate) R::acc(avg, iux + z, dn);
                         break;
                     case QR_RHOA:
-                        rz[z] = d * inx;
+                        R::put(out, irz + z, dn);
                         wsc[warp][0] = d;
-                        if (accumulate) avg[O_PROF + nz + z] += d * inx;
+                        if (accumulate) R::acc(avg, irz + z, dn);
                         break;
                     case QR_RHOB:
-                        rz[nz + z] = d * inx;
+                        R::put(out, irz + nz + z, dn);
                         wsc[warp][1] = d;
-                        if (accumulate) avg[O_PROF + 2LL * nz + z] += d * inx;
+                        if (accumulate) R::acc(avg, irz + nz + z, dn);
                         break;
                     case QR_SXZ:
-                        sx[z] = d * inx;
-                        if (accumulate) avg[O_PROF + 3LL * nz + z] += d * inx;
+                        R::put(out, isx + z, dn);
+                        if (accumulate) R::acc(avg, isx + z, dn);
                         break;
                     case QR_MX: wsc[warp][2] = d; break;
                     case QR_MZ: wsc[warp][3] = d; break;
-                    case QR_WALLB: if (z == 0) walls[0] = d; break;
-                    case QR_WALLT: if (z == nz - 1) walls[1] = d; break;
+                    case QR_WALLB: if (z == 0) walls[0] = mine; break;
+                    case QR_WALLT: if (z == nz - 1) walls[1] = mine; break;
                     case NQR: {  // fluidity
-                        const double gd =
-                            nz == 1 ? 0.0 : (wr * (double)v[NQR + 1] - wl * (double)v[NQR]) * inx;
-                        const double f = gd / ((double)v[QR_SXZ] * inx);
-                        fl[z] = f;
-                        if (accumulate) avg[O_PROF + 4LL * nz + z] += f;
+                        const PT gd = nz == 1 ? PT(0) : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
+                        const A f = R::from(gd / (v[QR_SXZ] * inx));
+                        R::put(out, ifl + z, f);
+                        if (accumulate) R::acc(avg, ifl + z, f);
                         break;
                     }
                 }
@@ -157,22 +200,22 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 #pragma unroll
             for (int k = 0; k < NQC; ++k) v[k] = warp_sum(v[k]);
             if (lane == 0) {
-                const double a = (double)v[QC_PS] * inz;
-                ps[x] = a;
+                const A a = R::from(v[QC_PS] * inz);
+                R::put(out, ips + x, a);
                 wsc[warp][4] = a;
-                if (accumulate) avg[O_PROF + 5LL * nz + x] += a;
+                if (accumulate) R::acc(avg, ips + x, a);
             } else if (lane == 1) {
-                const double b = (double)v[QC_PXX] * inz;
-                px[x] = b;
-                if (accumulate) avg[O_PROF + 5LL * nz + nx + x] += b;
+                const A b = R::from(v[QC_PXX] * inz);
+                R::put(out, ipx + x, b);
+                if (accumulate) R::acc(avg, ipx + x, b);
             }
         }
     }
     __syncthreads();
     if (t < NSC) {  // this block's share of the scalars, warps in order
-        double a = 0.0;
-        for (int w = 0; w < WPB; ++w) a += wsc[w][t];
-        bpart[(long long)blockIdx.x * NSC + t] = a;
+        A a = R::zero();
+        for (int w = 0; w < WPB; ++w) a = R::add(a, wsc[w][t]);
+        static_cast<A*>(bpart)[(long long)blockIdx.x * NSC + t] = a;
     }
     // the block's writes happen before thread 0's fence (barrier); the fence is cumulative, so
     // the block drawing the last ticket sees every block's results
@@ -184,32 +227,32 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     }
     __syncthreads();
     if (!last) return;
-    double acc[NSC] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    A acc[NSC];
+    for (int k = 0; k < NSC; ++k) acc[k] = R::zero();
     for (int b = t; b < (int)gridDim.x; b += RB_THREADS)
-        for (int k = 0; k < NSC; ++k) acc[k] += bpart[(long long)b * NSC + k];
+        for (int k = 0; k < NSC; ++k) acc[k] = R::add(acc[k], static_cast<const A*>(bpart)[(long long)b * NSC + k]);
     for (int k = 0; k < NSC; ++k) fin[k][t] = acc[k];
     __syncthreads();
     for (int o = RB_THREADS / 2; o > 0; o >>= 1) {
         if (t < o)
-            for (int k = 0; k < NSC; ++k) fin[k][t] += fin[k][t + o];
+            for (int k = 0; k < NSC; ++k) fin[k][t] = R::add(fin[k][t], fin[k][t + o]);
         __syncthreads();
     }
     if (t == 0) {
-        const double m0 = fin[0][0], m1 = fin[1][0], mx = fin[2][0], mz = fin[3][0], g = fin[4][0];
-        out[O_MASS] = m0;
-        out[O_MASS + 1] = m1;
-        out[O_MOM] = mx;
-        out[O_MOM + 1] = mz;
-        out[O_GAMMA] = g;
-        out[O_WALL] = zbc ? walls[0] * inx : 0.0;
-        out[O_WALL + 1] = zbc ? walls[1] * inx : 0.0;
-        const bool bad = (O.flag[0] & 1) || !isfinite(m0) || !isfinite(m1) || !isfinite(mx) || !isfinite(mz) ||
-                         !isfinite(g);
-        out[O_BAD] = bad ? 1.0 : 0.0;
+        R::put(out, O_MASS, fin[0][0]);
+        R::put(out, O_MASS + 1, fin[1][0]);
+        R::put(out, O_MOM, fin[2][0]);
+        R::put(out, O_MOM + 1, fin[3][0]);
+        R::put(out, O_GAMMA, fin[4][0]);
+        R::put(out, O_WALL, R::from(zbc ? walls[0] * inx : PT(0)));
+        R::put(out, O_WALL + 1, R::from(zbc ? walls[1] * inx : PT(0)));
+        bool bad = (O.flag[0] & 1) != 0;
+        for (int k = 0; k < NSC; ++k) bad = bad || !R::finite(fin[k][0]);
+        R::put(out, O_BAD, R::from(bad ? PT(1) : PT(0)));
         if (accumulate) {
-            for (int i = 0; i < O_BAD; ++i) avg[i] += out[i];
-            avg[O_BAD] = (avg[O_BAD] != 0.0 || bad) ? 1.0 : 0.0;
-            avg[O_COUNT] += 1.0;
+            for (int i = 0; i < O_BAD; ++i) R::acc(avg, i, R::get(out, i));
+            R::put(avg, O_BAD, R::from((R::nonzero(R::get(avg, O_BAD)) || bad) ? PT(1) : PT(0)));
+            R::acc(avg, O_COUNT, R::from(PT(1)));
         }
         *ticket = 0u;
     }
@@ -238,13 +281,12 @@ cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int
                           cudaStream_t st) {
     const int rb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int cb = (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-    const double inx = 1.0 / nx, inz = 1.0 / nz;
     if (precision_bytes == 4)
-        k_reduce<float><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, walls, bpart, ticket, out,
-                                                        avg, accumulate, inx, inz);
+        k_reduce<float><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, reinterpret_cast<float*>(walls),
+                                                        bpart, ticket, out, avg, accumulate, 1.0f / nx, 1.0f / nz);
     else
         k_reduce<double><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, walls, bpart, ticket, out,
-                                                         avg, accumulate, inx, inz);
+                                                         avg, accumulate, 1.0 / nx, 1.0 / nz);
     return cudaGetLastError();
 }
 

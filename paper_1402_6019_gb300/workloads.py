@@ -57,20 +57,32 @@ def disk_packing(nx: int, nz: int, fraction: float, seed: int, r_mean: float = 1
     if not (0.0 <= fraction < 1.0):
         raise ValueError("fraction must be in [0, 1)")
     covered = np.zeros((nz, nx), dtype=bool)
-    xs = np.arange(nx, dtype=np.float64)
-    zs = np.arange(nz, dtype=np.float64)
     target = fraction * nx * nz
+    count = 0
     k = 0
-    while covered.sum() < target and k < max_disks:
+    while count < target and k < max_disks:
         u = uniform(seed, 3, offset=3 * k)
         cx, cz = u[0] * nx, u[1] * nz
         r = r_mean + r_spread * (2.0 * u[2] - 1.0)
-        dx = np.abs(xs - cx)
-        dx = np.minimum(dx, nx - dx)
-        dz = np.abs(zs - cz)
+        # the disk's bounding box (periodic images in x, and in z when periodic)
+        ix = np.arange(int(np.floor(cx - r)), int(np.ceil(cx + r)) + 1)
+        iz = np.arange(int(np.floor(cz - r)), int(np.ceil(cz + r)) + 1)
+        if not periodic_z:
+            iz = iz[(iz >= 0) & (iz < nz)]
+        xw, zw = ix % nx, iz % nz
+        # distance to the nearest image, as on the full grid
+        dx = np.minimum(np.abs(xw - cx), nx - np.abs(xw - cx))
         if periodic_z:
-            dz = np.minimum(dz, nz - dz)
-        covered |= (dz[:, None] ** 2 + dx[None, :] ** 2) <= r * r
+            dz = np.minimum(np.abs(zw - cz), nz - np.abs(zw - cz))
+        else:
+            dz = np.abs(zw - cz)
+        inside = (dz[:, None] ** 2 + dx[None, :] ** 2) <= r * r
+        xu, first = np.unique(xw, return_index=True)
+        zu, zfirst = np.unique(zw, return_index=True)
+        inside = inside[zfirst][:, first]
+        sub = covered[np.ix_(zu, xu)]
+        count += int(np.count_nonzero(inside & ~sub))
+        covered[np.ix_(zu, xu)] = sub | inside
         k += 1
     rho = np.empty((2, nz, nx))
     rho[0] = np.where(covered, rho_in, rho_out)
@@ -108,7 +120,7 @@ def workload(name: str, seed: int = 1402):
         rho, frac = disk_packing(1024, 1024, 0.8, seed)
         return dict(nx=1024, nz=1024, n_species=2, z_boundary=0, params=dict(EMULSION_PARAMS),
                     rho=rho, note=f"1024x1024 periodic disk packing, covered {frac:.3f}")
-    if name.startswith("emulsion_"):
+    if name.startswith("emulsion_"):  # emulsion_N: an N x N lattice of the same emulsion
         n = int(name.split("_")[1])
         rho, frac = disk_packing(n, n, 0.8, seed)
         return dict(nx=n, nz=n, n_species=2, z_boundary=0, params=dict(EMULSION_PARAMS),
