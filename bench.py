@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--rows-per-warp", type=int, default=0)
     ap.add_argument("--kernel", choices=["fused", "twopass", "sweep"], default="fused")
+    ap.add_argument("--tile-rows", type=int, default=0, help="FUSED kernel tile height (8 or 16; 0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--observe-every", type=int, default=1,
@@ -238,7 +239,8 @@ def main():
     torch.cuda.set_stream(stream)
     kern = {"fused": L.LBM_KERNEL_FUSED, "twopass": L.LBM_KERNEL_TWO_PASS, "sweep": L.LBM_KERNEL_SWEEP}[a.kernel]
     lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
-                    stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, **w["params"])
+                    stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, tile_rows=a.tile_rows,
+                    **w["params"])
     lat.set_fields(w["rho"])
     lat.set_observe(a.observe_every)  # 1: every step reduces the observables of the state it collides
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -318,7 +320,7 @@ def main():
                    "l2": "flushed between timed steps (256 MiB write)",
                    "observables": ("every step" if a.observe_every == 1 else
                                    "never" if a.observe_every == 0 else f"every {a.observe_every} steps"),
-                   "rows_per_warp": lat.desc.rows_per_warp, "kernel": a.kernel},
+                   "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

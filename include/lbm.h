@@ -63,6 +63,7 @@ typedef struct {
     int device;          /* CUDA device ordinal                                          */
     void *stream;        /* cudaStream_t to run on; NULL = a stream owned by the context  */
     int rows_per_warp;   /* SWEEP kernel: rows of one strip swept by a warp; 0 = auto      */
+    int tile_rows;       /* FUSED kernel: tile height, 8 or 16 rows; 0 = auto             */
 } lbm_desc;
 
 /* Model parameters (Eq. LB, Eq. FORCE, Sec. IV).  Species index 0 = A, 1 = B. */

@@ -34,6 +34,7 @@ struct lbm_ctx {
     SweepGeom geom_obs{};  // fused kernel with observables (M_OBS modes)
     GhostGeom ghost{};
     int kernel = LBM_KERNEL_FUSED;  // resolved
+    int tile_rows = 8;              // resolved tile height of the FUSED kernel
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
     void* part_row = nullptr;  // partial sums in the populations' precision
     void* part_col = nullptr;
@@ -135,6 +136,8 @@ static int check_desc(lbm_ctx* c, const lbm_desc* d) {
         return fail(c, LBM_EINVAL, "unknown z boundary");
     if (d->kernel < LBM_KERNEL_AUTO || d->kernel > LBM_KERNEL_SWEEP) return fail(c, LBM_EINVAL, "unknown kernel");
     if (d->rows_per_warp < 0 || d->rows_per_warp > 65536) return fail(c, LBM_EINVAL, "rows_per_warp out of range");
+    if (d->tile_rows != 0 && d->tile_rows != 8 && d->tile_rows != 16)
+        return fail(c, LBM_EINVAL, "tile_rows must be 0, 8 or 16");
     if (d->device < 0) return fail(c, LBM_EINVAL, "negative device ordinal");
     return LBM_OK;
 }
@@ -242,6 +245,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     c->pitch = (nx + 31) / 32 * 32;
     c->plane = (long long)nz * c->pitch;
     c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_FUSED : d->kernel;
+    c->tile_rows = d->tile_rows == 0 ? 8 : d->tile_rows;
     const size_t fbytes = (size_t)ns * 9 * c->plane * c->esize;
     CKC(cudaMalloc(&c->f[0], fbytes));
     CKC(cudaMalloc(&c->f[1], fbytes));
@@ -258,7 +262,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
         c->geom = sweep_geom(c, rw);
         c->geom_obs = sweep_geom(c, ro);
     }
-    const int tx = (nx + TPX - 1) / TPX, tz = (nz + TPZ - 1) / TPZ;
+    const int tx = (nx + TPX - 1) / TPX, tz = (nz + std::min(TPZ, 8) - 1) / std::min(TPZ, 8);
     const long long rows_parts = std::max(c->geom_obs.nstrips, tx);
     const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
     CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * c->esize));
@@ -339,7 +343,9 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         if (e != cudaSuccess) return e;
     }
     const bool twopass = c->kernel == LBM_KERNEL_TWO_PASS && (mode & M_WRITE);
-    const int tpx = (c->d.nx + TPX - 1) / TPX, tpz = (c->d.nz + TPZ - 1) / TPZ;
+    const int tpx = (c->d.nx + TPX - 1) / TPX;
+    const int tzrows = twopass ? TPZ : c->tile_rows;
+    const int tpz = (c->d.nz + tzrows - 1) / tzrows;
     if (twopass) {
         // K1: densities and pseudopotentials into the ghost-padded planes; K2: collide and push
         if (c->d.precision == LBM_FP64) {
@@ -366,11 +372,11 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
                                     c->stream);
     } else {
         if (c->d.precision == LBM_FP64)
-            e = launch_tile<double>(c->d.n_species, mode, (const double*)c->f[cur], (double*)c->f[cur ^ 1], c->c64, O,
-                                    c->stream);
+            e = launch_tile<double>(c->d.n_species, mode, c->tile_rows, (const double*)c->f[cur], (double*)c->f[cur ^ 1],
+                                    c->c64, O, c->stream);
         else
-            e = launch_tile<float>(c->d.n_species, mode, (const float*)c->f[cur], (float*)c->f[cur ^ 1], c->c32, O,
-                                   c->stream);
+            e = launch_tile<float>(c->d.n_species, mode, c->tile_rows, (const float*)c->f[cur], (float*)c->f[cur ^ 1],
+                                   c->c32, O, c->stream);
     }
     c->launches += 1;
     if (e != cudaSuccess) return e;

@@ -45,9 +45,10 @@ LBM_HD long long obs_len(int nx, int nz) { return O_PROF + 5LL * nz + 2LL * nx; 
 template <typename T>
 cudaError_t launch_fused(int ns, int mode, const T* fin, T* fout, const StepConst<T>& C, const SweepGeom& G,
                          const ObsPtrs& O, cudaStream_t st);
+// One-pass tile kernel; tile_rows = 8 or 16 (tile height).
 template <typename T>
-cudaError_t launch_tile(int ns, int mode, const T* fin, T* fout, const StepConst<T>& C, const ObsPtrs& O,
-                        cudaStream_t st);
+cudaError_t launch_tile(int ns, int mode, int tile_rows, const T* fin, T* fout, const StepConst<T>& C,
+                        const ObsPtrs& O, cudaStream_t st);
 // Warps of the sweep kernel resident on the whole GPU at once (occupancy), for a mode class.
 template <typename T>
 int fused_resident_warps(int ns, int mode, int nsm);

@@ -67,7 +67,7 @@ extern "C" int lbm_observables_noalloc(const double* f, int nx, int nz, int n_sp
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: the ticket and the flag must start at zero
     cudaError_t e = cudaMemsetAsync(walls, 0, b_small, st);
-    if (e == cudaSuccess) e = launch_tile<double>(n_species, M_OBS, f, nullptr, C, O, st);
+    if (e == cudaSuccess) e = launch_tile<double>(n_species, M_OBS, TPZ, f, nullptr, C, O, st);
     if (e == cudaSuccess)
         e = launch_reduce((int)sizeof(double), O, nxpart, nzpart, nx, nz, z_boundary, walls, slots, ticket, out,
                           nullptr, 0, st);

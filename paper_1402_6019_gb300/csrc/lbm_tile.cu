@@ -18,12 +18,16 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int HW = TPX + 4;  // halo tile width
-constexpr int HH = TPZ + 4;  // halo tile height
-constexpr int NRING = HW * HH - TPX * TPZ;
 
-template <typename T, int NS, int MODE>
-__global__ void __launch_bounds__(TPX* TPZ, sizeof(T) == 4 ? 4 : 2) k_tile(const T* __restrict__ fin, T* __restrict__ fout,
-                                                   const StepConst<T> C, const ObsPtrs O, int nxpart, int nzpart) {
+// TZ: tile height (8 or 16 rows, one warp per row).  Registers are capped so that 32 warps fit
+// on an SM in FP32 (64 per thread); FP64 keeps more registers and half the warps.
+template <typename T, int NS, int MODE, int TZ>
+__global__ void __launch_bounds__(TPX* TZ, (sizeof(T) == 4 ? 1024 : 512) / (TPX * TZ))
+    k_tile(const T* __restrict__ fin, T* __restrict__ fout, const StepConst<T> C, const ObsPtrs O, int nxpart,
+           int nzpart) {
+    constexpr int TPZ = TZ;
+    constexpr int HH = TPZ + 4;  // halo tile height
+    constexpr int NRING = HW * HH - TPX * TPZ;
     __shared__ T sps[NS][HH][HW];
     __shared__ T srh[NS][HH][HW];
     __shared__ T colsum[TPZ][NQC][TPX];
@@ -245,21 +249,21 @@ __global__ void __launch_bounds__(TPX* TPZ, sizeof(T) == 4 ? 4 : 2) k_tile(const
     }
 }
 
-template <typename T, int NS, int MODE>
+template <typename T, int NS, int MODE, int TZ>
 cudaError_t launch_mode(const T* fin, T* fout, const StepConst<T>& C, const ObsPtrs& O, cudaStream_t st) {
-    const int nxpart = (C.nx + TPX - 1) / TPX, nzpart = (C.nz + TPZ - 1) / TPZ;
-    const dim3 block(TPX, TPZ), grid(nxpart, nzpart);
-    k_tile<T, NS, MODE><<<grid, block, 0, st>>>(fin, fout, C, O, nxpart, nzpart);
+    const int nxpart = (C.nx + TPX - 1) / TPX, nzpart = (C.nz + TZ - 1) / TZ;
+    const dim3 block(TPX, TZ), grid(nxpart, nzpart);
+    k_tile<T, NS, MODE, TZ><<<grid, block, 0, st>>>(fin, fout, C, O, nxpart, nzpart);
     return cudaGetLastError();
 }
 
-template <typename T, int NS>
+template <typename T, int NS, int TZ>
 cudaError_t launch_ns(int mode, const T* fin, T* fout, const StepConst<T>& C, const ObsPtrs& O, cudaStream_t st) {
     switch (mode) {
-        case M_WRITE: return launch_mode<T, NS, M_WRITE>(fin, fout, C, O, st);
-        case M_WRITE | M_OBS: return launch_mode<T, NS, M_WRITE | M_OBS>(fin, fout, C, O, st);
-        case M_OBS: return launch_mode<T, NS, M_OBS>(fin, fout, C, O, st);
-        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(fin, fout, C, O, st);
+        case M_WRITE: return launch_mode<T, NS, M_WRITE, TZ>(fin, fout, C, O, st);
+        case M_WRITE | M_OBS: return launch_mode<T, NS, M_WRITE | M_OBS, TZ>(fin, fout, C, O, st);
+        case M_OBS: return launch_mode<T, NS, M_OBS, TZ>(fin, fout, C, O, st);
+        case M_FIELDS: return launch_mode<T, NS, M_FIELDS, TZ>(fin, fout, C, O, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -267,14 +271,18 @@ cudaError_t launch_ns(int mode, const T* fin, T* fout, const StepConst<T>& C, co
 }  // namespace
 
 template <typename T>
-cudaError_t launch_tile(int ns, int mode, const T* fin, T* fout, const StepConst<T>& C, const ObsPtrs& O,
-                        cudaStream_t st) {
-    return ns == 1 ? launch_ns<T, 1>(mode, fin, fout, C, O, st) : launch_ns<T, 2>(mode, fin, fout, C, O, st);
+cudaError_t launch_tile(int ns, int mode, int tile_rows, const T* fin, T* fout, const StepConst<T>& C,
+                        const ObsPtrs& O, cudaStream_t st) {
+    if (tile_rows == 16)
+        return ns == 1 ? launch_ns<T, 1, 16>(mode, fin, fout, C, O, st) : launch_ns<T, 2, 16>(mode, fin, fout, C, O, st);
+    if (tile_rows == 8)
+        return ns == 1 ? launch_ns<T, 1, 8>(mode, fin, fout, C, O, st) : launch_ns<T, 2, 8>(mode, fin, fout, C, O, st);
+    return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_tile<float>(int, int, const float*, float*, const StepConst<float>&, const ObsPtrs&,
+template cudaError_t launch_tile<float>(int, int, int, const float*, float*, const StepConst<float>&, const ObsPtrs&,
                                         cudaStream_t);
-template cudaError_t launch_tile<double>(int, int, const double*, double*, const StepConst<double>&, const ObsPtrs&,
-                                         cudaStream_t);
+template cudaError_t launch_tile<double>(int, int, int, const double*, double*, const StepConst<double>&,
+                                         const ObsPtrs&, cudaStream_t);
 
 }  // namespace lbm

@@ -28,7 +28,8 @@ _DP = ctypes.POINTER(ctypes.c_double)
 class lbm_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("n_species", ctypes.c_int),
                 ("precision", ctypes.c_int), ("z_boundary", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("rows_per_warp", ctypes.c_int)]
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("rows_per_warp", ctypes.c_int),
+                ("tile_rows", ctypes.c_int)]
 
 
 class lbm_params(ctypes.Structure):
@@ -245,10 +246,11 @@ class Lattice:
     """One simulation on the GPU: create + params + fields, with numpy I/O."""
 
     def __init__(self, nx, nz, n_species=1, precision=LBM_FP64, z_boundary=LBM_PERIODIC,
-                 kernel=LBM_KERNEL_AUTO, device=0, stream=None, rows_per_warp=0, **params):
+                 kernel=LBM_KERNEL_AUTO, device=0, stream=None, rows_per_warp=0, tile_rows=0, **params):
         d = lbm_default_desc()
         d.nx, d.nz, d.n_species, d.precision = nx, nz, n_species, precision
         d.z_boundary, d.kernel, d.device, d.rows_per_warp = z_boundary, kernel, device, rows_per_warp
+        d.tile_rows = tile_rows
         d.stream = stream
         self.desc = d
         self.nx, self.nz, self.ns = nx, nz, n_species
