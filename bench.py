@@ -121,14 +121,14 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic(kernel_src_hash, workload, precision):
+def _traffic(kernel_src_hash, workload, precision, kernel):
     """DRAM bytes per launch of the step kernel from the committed ncu summary, or None when
-    the summary is for another source of the kernel or another workload."""
+    the summary is for another source of the kernel, another kernel or another workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    e = d.get(f"{workload}/{precision}")
+    e = d.get(f"{workload}/{precision}/{kernel}")
     if not e or e.get("kernel_source_sha1") != kernel_src_hash:
         return None
     return e.get("dram_bytes_per_launch")
@@ -277,7 +277,8 @@ def main():
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = bps * sites / (kern_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _traffic(kernel_source_hash(), a.workload, a.precision)
+    traffic = _traffic(kernel_source_hash(), a.workload, a.precision,
+                       a.kernel if a.tile_rows in (0, 8) else f"{a.kernel}{a.tile_rows}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                 "kernel": {"fused": "lbm::k_tile<T, 2, M_WRITE|M_OBS>",

@@ -38,8 +38,6 @@ struct lbm_ctx {
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
     void* part_row = nullptr;  // partial sums in the populations' precision
     void* part_col = nullptr;
-    double* row_sum = nullptr;
-    double* col_sum = nullptr;
     unsigned* ticket = nullptr;
     int* flag = nullptr;
     double* out = nullptr;
@@ -54,6 +52,7 @@ struct lbm_ctx {
     double rho_ref[2] = {0.0, 0.0};
     bool have_params = false, have_fields = false;
     int observe_every = 0;
+    long long samples = 0;  // states accumulated into the time sums since the last reset
     long long step = 0;
     long long launches = 0;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][observe]
@@ -101,6 +100,10 @@ static void drop_graphs(lbm_ctx* c) {
                 cudaGraphExecDestroy(g);
                 g = nullptr;
             }
+}
+
+static size_t obs_bytes(const lbm_ctx* c) {
+    return (size_t)(obs_len(c->d.nx, c->d.nz) + 5LL * reduce_blocks(c->d.nx, c->d.nz)) * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -177,8 +180,8 @@ static void release(lbm_ctx* c) {
     drop_graphs(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
-    void* ptrs[] = {c->f[0], c->f[1], c->part_row, c->part_col, c->row_sum, c->col_sum, c->ticket,
-                    c->flag, c->out,  c->avg,  c->staging,  c->fexport,  c->gfield};
+    void* ptrs[] = {c->f[0], c->f[1], c->part_row, c->part_col, c->ticket, c->flag,
+                    c->out,  c->avg,  c->staging, c->fexport, c->gfield};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_out) cudaFreeHost(c->host_out);
@@ -267,11 +270,10 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
     CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * c->esize));
     CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * c->esize));
-    CKC(cudaMalloc(&c->row_sum, (size_t)2 * sizeof(double)));                 // wall momenta
-    CKC(cudaMalloc(&c->col_sum, (size_t)(nx + nz) * 5 * sizeof(double)));    // per-block scalar partials
     CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
     CKC(cudaMalloc(&c->flag, sizeof(int)));
-    const size_t olen = (size_t)obs_len(nx, nz) * sizeof(double);
+    // observables: obs_len entries, then the reduction's block partials of the scalars
+    const size_t olen = (size_t)(obs_len(nx, nz) + 5LL * reduce_blocks(nx, nz)) * sizeof(double);
     CKC(cudaMalloc(&c->out, olen));
     CKC(cudaMalloc(&c->avg, olen));
     CKC(cudaMalloc(&c->staging, (size_t)(ns + 2) * nx * nz * sizeof(double)));
@@ -388,9 +390,11 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
     if (reduce) {
         const bool sweep = c->kernel == LBM_KERNEL_SWEEP;
         const int nxp = sweep ? c->geom_obs.nstrips : tpx, nzp = sweep ? c->geom_obs.nchunks : tpz;
-        e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->row_sum,
-                          c->col_sum, c->ticket, c->out, c->avg, accumulate ? 1 : 0, c->stream);
+        const long long ol = obs_len(c->d.nx, c->d.nz);
+        e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->ticket, c->out, c->avg,
+                          c->out + ol, c->avg + ol, accumulate ? 1 : 0, false, c->stream);
         c->launches += 1;
+        if (accumulate) c->samples += 1;
     }
     return e;
 }
@@ -413,12 +417,13 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
             if (!ge) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-                const long long saved = c->launches;
+                const long long saved = c->launches, saved_samples = c->samples;
                 cudaError_t e = cudaSuccess;
                 for (int i = 0; i < G && e == cudaSuccess; ++i)
                     e = enqueue_pass(c, (c->cur + i) & 1, M_WRITE | (ob ? M_OBS : 0), ob, ob);
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
                 c->launches = saved;
+                c->samples = saved_samples;
                 CK(e);
                 CK(e2);
                 e = cudaGraphInstantiate(&ge, g, 0);
@@ -427,6 +432,7 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
             }
             CK(cudaGraphLaunch(ge, c->stream));
             c->launches += (long long)G * (ob ? 2 : 1);
+            if (ob) c->samples += G;
             c->step += G;  // G is even: the parity of cur is unchanged
             left -= G;
             continue;
@@ -445,7 +451,8 @@ extern "C" int lbm_set_observe(lbm_ctx* c, int every) {
     if (every < 0) return fail(c, LBM_EINVAL, "every must be >= 0");
     CK(cudaSetDevice(c->d.device));
     c->observe_every = every;
-    CK(cudaMemsetAsync(c->avg, 0, (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double), c->stream));
+    c->samples = 0;
+    CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
     return LBM_OK;
 }
 
@@ -493,7 +500,8 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
         CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->stream));
     c->launches += 1;
     CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
-    CK(cudaMemsetAsync(c->avg, 0, (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
+    c->samples = 0;
     CK(cudaStreamSynchronize(c->stream));
     c->step = 0;
     c->have_fields = true;
@@ -540,14 +548,21 @@ static double entry(const lbm_ctx* c, const double* buf, long long i) {
 static void unpack(const lbm_ctx* c, const double* buf, lbm_obs* o, double scale) {
     const int nx = c->d.nx, nz = c->d.nz, ns = c->d.n_species;
     auto E = [&](long long i) { return entry(c, buf, i); };
-    o->mass[0] = E(O_MASS) * scale;
-    o->mass[1] = ns == 2 ? E(O_MASS + 1) * scale : 0.0;
-    o->momentum[0] = E(O_MOM) * scale;
-    o->momentum[1] = E(O_MOM + 1) * scale;
-    o->gamma = E(O_GAMMA) * scale;
-    o->wall_force[0] = E(O_WALL) * scale;
-    o->wall_force[1] = E(O_WALL + 1) * scale;
-    o->nonfinite = E(O_BAD) != 0.0;
+    // the scalars: FP64 sums, in block order, of the reduction's block partials
+    const long long ol = obs_len(nx, nz), nb = reduce_blocks(nx, nz);
+    double sc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long b = 0; b < nb; ++b)
+        for (int k = 0; k < 5; ++k) sc[k] += E(ol + 5 * b + k);
+    o->mass[0] = sc[0] * scale;
+    o->mass[1] = ns == 2 ? sc[1] * scale : 0.0;
+    o->momentum[0] = sc[2] * scale;
+    o->momentum[1] = sc[3] * scale;
+    o->gamma = sc[4] * scale;
+    o->wall_force[0] = c->d.z_boundary ? E(O_WALL) * scale : 0.0;
+    o->wall_force[1] = c->d.z_boundary ? E(O_WALL + 1) * scale : 0.0;
+    bool bad = E(O_BAD) != 0.0;
+    for (int k = 0; k < 5; ++k) bad = bad || !std::isfinite(sc[k]);
+    o->nonfinite = bad;
     o->step = c->step;
     const long long ux = O_PROF, rz = ux + nz, sx = rz + 2LL * nz, fl = sx + nz, ps = fl + nz, px = ps + nx;
     for (int z = 0; z < nz; ++z) {
@@ -569,8 +584,7 @@ extern "C" int lbm_observables(lbm_ctx* c, lbm_obs* o) {
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
     CK(cudaSetDevice(c->d.device));
     CK(enqueue_pass(c, c->cur, M_OBS, true, false));
-    const size_t olen = (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double);
-    CK(cudaMemcpyAsync(c->host_out, c->out, olen, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->host_out, c->out, obs_bytes(c), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     unpack(c, c->host_out, o, 1.0);
     o->samples = 1;
@@ -581,14 +595,15 @@ extern "C" int lbm_averages(lbm_ctx* c, lbm_obs* o, int reset) {
     if (!c) return LBM_EINVAL;
     if (!o) return fail(c, LBM_EINVAL, "out is NULL");
     CK(cudaSetDevice(c->d.device));
-    const size_t olen = (size_t)obs_len(c->d.nx, c->d.nz) * sizeof(double);
-    CK(cudaMemcpyAsync(c->host_out, c->avg, olen, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->host_out, c->avg, obs_bytes(c), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    const double n = entry(c, c->host_out, O_COUNT);
+    const double n = (double)c->samples;
     unpack(c, c->host_out, o, n > 0 ? 1.0 / n : 0.0);
-    o->nonfinite = entry(c, c->host_out, O_BAD) != 0.0;
-    o->samples = (long long)n;
-    if (reset) CK(cudaMemsetAsync(c->avg, 0, olen, c->stream));
+    o->samples = c->samples;
+    if (reset) {
+        CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
+        c->samples = 0;
+    }
     return LBM_OK;
 }
 

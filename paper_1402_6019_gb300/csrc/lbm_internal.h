@@ -66,9 +66,15 @@ template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, cudaStream_t st);
 template <typename T>
 cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, cudaStream_t st);
-cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc, double* row_sum,
-                          double* col_sum, unsigned* ticket, double* out, double* avg, int accumulate,
-                          cudaStream_t st);
+// Reduction of the step kernels' partial sums into the observables.  `out` / `avg` hold
+// obs_len(nx, nz) entries (profiles, wall forces, flag); `bpart` / `bavg` hold
+// reduce_blocks(nx, nz) * 5 block partials of the scalars (mass A, B, momentum x, z, gamma) and
+// their time sums.  With tail the scalar sums are also written into out[O_MASS..].  Entries are
+// doubles (FP64 mode) or (hi, lo) float pairs (FP32 mode).
+int reduce_blocks(int nx, int nz);
+cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
+                          unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
+                          bool tail, cudaStream_t st);
 
 // Twopass tile (threads per CTA: TPX x TPZ sites).
 constexpr int TPX = 32, TPZ = 8;

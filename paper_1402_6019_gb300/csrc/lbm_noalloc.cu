@@ -69,7 +69,7 @@ extern "C" int lbm_observables_noalloc(const double* f, int nx, int nz, int n_sp
     cudaError_t e = cudaMemsetAsync(walls, 0, b_small, st);
     if (e == cudaSuccess) e = launch_tile<double>(n_species, M_OBS, TPZ, f, nullptr, C, O, st);
     if (e == cudaSuccess)
-        e = launch_reduce((int)sizeof(double), O, nxpart, nzpart, nx, nz, z_boundary, walls, slots, ticket, out,
-                          nullptr, 0, st);
+        e = launch_reduce((int)sizeof(double), O, nxpart, nzpart, nx, nz, z_boundary, ticket, out, nullptr, slots,
+                          nullptr, 0, true, st);
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

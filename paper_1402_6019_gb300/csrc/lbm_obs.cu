@@ -92,18 +92,19 @@ template <> struct Red<float> {
 
 // One warp per row: the row's totals over its column groups, its profile entries
 // (x-averages), its fluidity (Eq. fluidity: shear rate = central difference of ux_z, one-sided
-// at wall rows, wrapped when periodic, over the shear stress) and, when sampling, its time
-// sums.  One warp per column: the z-averages of P_xx - P_zz and P_xx.  Each block folds the
-// scalar contributions of its rows (mass A, B, momentum x, z) or columns (gamma) into one
-// partial; the last block to finish sums the block partials.  Group sums within a row or a
-// column stay in the populations' precision PT; the scalars and time sums use the
-// accumulators above.  Every sum runs in a fixed order: repeatable results.
-template <typename PT>
+// at wall rows, wrapped when periodic, over the shear stress), its wall momenta and, when
+// sampling, its time sums.  One warp per column: the z-averages of P_xx - P_zz and P_xx.  Each
+// block folds the scalar contributions of its rows (mass A, B, momentum x, z) or columns
+// (gamma) into one partial, stored after the profiles (and added to its own time sum).  The
+// sum over blocks is left to the reader (the host sums the block partials in FP64), except
+// with TAIL, where the last block to finish writes the scalars into `out` on the device.
+// Group sums within a row or a column stay in the populations' precision PT; time sums and
+// block partials use the accumulators above.  Fixed summation order: repeatable results.
+template <typename PT, bool TAIL>
 __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
-                                                       int nrowblocks, PT* __restrict__ walls,
-                                                       void* __restrict__ bpart, unsigned* ticket,
-                                                       void* __restrict__ out, void* __restrict__ avg,
-                                                       int accumulate, PT inx, PT inz) {
+                                                       int nrowblocks, unsigned* ticket, void* __restrict__ out,
+                                                       void* __restrict__ avg, void* __restrict__ bpart,
+                                                       void* __restrict__ bavg, int accumulate, PT inx, PT inz) {
     using R = Red<PT>;
     using A = typename R::A;
     constexpr int WPB = RB_THREADS / 32;
@@ -116,6 +117,11 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     const long long iux = O_PROF, irz = O_PROF + nz, isx = O_PROF + 3LL * nz, ifl = O_PROF + 4LL * nz,
                     ips = O_PROF + 5LL * nz, ipx = ips + nx;
     for (int k = lane; k < NSC; k += 32) wsc[warp][k] = R::zero();
+    if (blockIdx.x == 0 && t == 0) {  // the step kernels' flag of a bad density
+        const bool bad = (O.flag[0] & 1) != 0;
+        R::put(out, O_BAD, R::from(bad ? PT(1) : PT(0)));
+        if (accumulate && bad) R::put(avg, O_BAD, R::from(PT(1)));
+    }
     if ((int)blockIdx.x < nrowblocks) {
         const int z = blockIdx.x * WPB + warp;
         if (z < nz) {
@@ -133,6 +139,18 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                 zr = nz - 1;
                 wl = wr = PT(1);
             }
+            // the output entry of this lane (lanes 0..8), -1 for none
+            long long oi = -1;
+            switch (lane) {
+                case QR_UX: oi = iux + z; break;
+                case QR_RHOA: oi = irz + z; break;
+                case QR_RHOB: oi = irz + nz + z; break;
+                case QR_SXZ: oi = isx + z; break;
+                case QR_WALLB: oi = (zbc && z == 0) ? O_WALL : -1; break;
+                case QR_WALLT: oi = (zbc && z == nz - 1) ? O_WALL + 1 : -1; break;
+                case NQR: oi = ifl + z; break;
+                default: break;
+            }
             PT v[NQR + 2];
 #pragma unroll
             for (int k = 0; k < NQR + 2; ++k) v[k] = PT(0);
@@ -143,52 +161,35 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
                 v[NQR] += prow[((long long)zl * nxpart + p) * NQR + QR_UX];
                 v[NQR + 1] += prow[((long long)zr * nxpart + p) * NQR + QR_UX];
             }
+            const A old = (accumulate && oi >= 0) ? R::get(avg, oi) : R::zero();  // in flight with the sums
 #pragma unroll
             for (int k = 0; k < NQR + 2; ++k) v[k] = warp_sum(v[k]);
-            // lanes 0..8 finish one output each
             if (lane <= NQR) {
                 PT mine = v[0];
 #pragma unroll
                 for (int k = 1; k < NQR; ++k)
                     if (lane == k) mine = v[k];
-                const A d = R::from(mine);
-                const A dn = R::from(mine * inx);
-                switch (lane) {
-                    case QR_UX:
-                        R::put(out, iux + z, dn);
-                        if (accumulate) R::acc(avg, iux + z, dn);
-                        break;
-                    case QR_RHOA:
-                        R::put(out, irz + z, dn);
-                        wsc[warp][0] = d;
-                        if (accumulate) R::acc(avg, irz + z, dn);
-                        break;
-                    case QR_RHOB:
-                        R::put(out, irz + nz + z, dn);
-                        wsc[warp][1] = d;
-                        if (accumulate) R::acc(avg, irz + nz + z, dn);
-                        break;
-                    case QR_SXZ:
-                        R::put(out, isx + z, dn);
-                        if (accumulate) R::acc(avg, isx + z, dn);
-                        break;
-                    case QR_MX: wsc[warp][2] = d; break;
-                    case QR_MZ: wsc[warp][3] = d; break;
-                    case QR_WALLB: if (z == 0) walls[0] = mine; break;
-                    case QR_WALLT: if (z == nz - 1) walls[1] = mine; break;
-                    case NQR: {  // fluidity
-                        const PT gd = nz == 1 ? PT(0) : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
-                        const A f = R::from(gd / (v[QR_SXZ] * inx));
-                        R::put(out, ifl + z, f);
-                        if (accumulate) R::acc(avg, ifl + z, f);
-                        break;
-                    }
+                A val;
+                if (lane == NQR) {  // fluidity
+                    const PT gd = nz == 1 ? PT(0) : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
+                    val = R::from(gd / (v[QR_SXZ] * inx));
+                } else {
+                    val = R::from(mine * inx);
+                }
+                if (lane == QR_RHOA) wsc[warp][0] = R::from(mine);
+                if (lane == QR_RHOB) wsc[warp][1] = R::from(mine);
+                if (lane == QR_MX) wsc[warp][2] = R::from(mine);
+                if (lane == QR_MZ) wsc[warp][3] = R::from(mine);
+                if (oi >= 0) {
+                    R::put(out, oi, val);
+                    if (accumulate) R::put(avg, oi, R::add(old, val));
                 }
             }
         }
     } else {
         const int x = (blockIdx.x - nrowblocks) * WPB + warp;
         if (x < nx) {
+            const long long oi = lane == 0 ? ips + x : (lane == 1 ? ipx + x : -1);
             PT v[NQC];
 #pragma unroll
             for (int k = 0; k < NQC; ++k) v[k] = PT(0);
@@ -197,64 +198,68 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 #pragma unroll
                 for (int k = 0; k < NQC; ++k) v[k] += src[k];
             }
+            const A old = (accumulate && oi >= 0) ? R::get(avg, oi) : R::zero();
 #pragma unroll
             for (int k = 0; k < NQC; ++k) v[k] = warp_sum(v[k]);
-            if (lane == 0) {
-                const A a = R::from(v[QC_PS] * inz);
-                R::put(out, ips + x, a);
-                wsc[warp][4] = a;
-                if (accumulate) R::acc(avg, ips + x, a);
-            } else if (lane == 1) {
-                const A b = R::from(v[QC_PXX] * inz);
-                R::put(out, ipx + x, b);
-                if (accumulate) R::acc(avg, ipx + x, b);
+            if (oi >= 0) {
+                const A val = R::from((lane == 0 ? v[QC_PS] : v[QC_PXX]) * inz);
+                if (lane == 0) wsc[warp][4] = val;
+                R::put(out, oi, val);
+                if (accumulate) R::put(avg, oi, R::add(old, val));
             }
         }
     }
     __syncthreads();
+    A bsum = R::zero();
     if (t < NSC) {  // this block's share of the scalars, warps in order
-        A a = R::zero();
-        for (int w = 0; w < WPB; ++w) a = R::add(a, wsc[w][t]);
-        static_cast<A*>(bpart)[(long long)blockIdx.x * NSC + t] = a;
+        const long long i = (long long)blockIdx.x * NSC + t;
+        const A old = accumulate ? R::get(bavg, i) : R::zero();
+        for (int w = 0; w < WPB; ++w) bsum = R::add(bsum, wsc[w][t]);
+        R::put(bpart, i, bsum);
+        if (accumulate) R::put(bavg, i, R::add(old, bsum));
     }
-    // the block's writes happen before thread 0's fence (barrier); the fence is cumulative, so
-    // the block drawing the last ticket sees every block's results
-    __syncthreads();
-    if (t == 0) {
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-        if (last) __threadfence();
-    }
-    __syncthreads();
-    if (!last) return;
-    A acc[NSC];
-    for (int k = 0; k < NSC; ++k) acc[k] = R::zero();
-    for (int b = t; b < (int)gridDim.x; b += RB_THREADS)
-        for (int k = 0; k < NSC; ++k) acc[k] = R::add(acc[k], static_cast<const A*>(bpart)[(long long)b * NSC + k]);
-    for (int k = 0; k < NSC; ++k) fin[k][t] = acc[k];
-    __syncthreads();
-    for (int o = RB_THREADS / 2; o > 0; o >>= 1) {
-        if (t < o)
-            for (int k = 0; k < NSC; ++k) fin[k][t] = R::add(fin[k][t], fin[k][t + o]);
+    if constexpr (TAIL) {
+        // the block's writes happen before thread 0's fence (barrier); the fence is
+        // cumulative, so the block drawing the last ticket sees every block's results
         __syncthreads();
-    }
-    if (t == 0) {
-        R::put(out, O_MASS, fin[0][0]);
-        R::put(out, O_MASS + 1, fin[1][0]);
-        R::put(out, O_MOM, fin[2][0]);
-        R::put(out, O_MOM + 1, fin[3][0]);
-        R::put(out, O_GAMMA, fin[4][0]);
-        R::put(out, O_WALL, R::from(zbc ? walls[0] * inx : PT(0)));
-        R::put(out, O_WALL + 1, R::from(zbc ? walls[1] * inx : PT(0)));
-        bool bad = (O.flag[0] & 1) != 0;
-        for (int k = 0; k < NSC; ++k) bad = bad || !R::finite(fin[k][0]);
-        R::put(out, O_BAD, R::from(bad ? PT(1) : PT(0)));
-        if (accumulate) {
-            for (int i = 0; i < O_BAD; ++i) R::acc(avg, i, R::get(out, i));
-            R::put(avg, O_BAD, R::from((R::nonzero(R::get(avg, O_BAD)) || bad) ? PT(1) : PT(0)));
-            R::acc(avg, O_COUNT, R::from(PT(1)));
+        if (t == 0) {
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+            if (last) __threadfence();
         }
-        *ticket = 0u;
+        __syncthreads();
+        if (!last) return;
+        A acc[NSC];
+        for (int k = 0; k < NSC; ++k) acc[k] = R::zero();
+        for (int b = t; b < (int)gridDim.x; b += RB_THREADS)
+            for (int k = 0; k < NSC; ++k) acc[k] = R::add(acc[k], R::get(bpart, (long long)b * NSC + k));
+        for (int k = 0; k < NSC; ++k) fin[k][t] = acc[k];
+        __syncthreads();
+        for (int o = RB_THREADS / 2; o > 0; o >>= 1) {
+            if (t < o)
+                for (int k = 0; k < NSC; ++k) fin[k][t] = R::add(fin[k][t], fin[k][t + o]);
+            __syncthreads();
+        }
+        if (t == 0) {
+            R::put(out, O_MASS, fin[0][0]);
+            R::put(out, O_MASS + 1, fin[1][0]);
+            R::put(out, O_MOM, fin[2][0]);
+            R::put(out, O_MOM + 1, fin[3][0]);
+            R::put(out, O_GAMMA, fin[4][0]);
+            bool bad = (O.flag[0] & 1) != 0;
+            for (int k = 0; k < NSC; ++k) bad = bad || !R::finite(fin[k][0]);
+            R::put(out, O_BAD, R::from(bad ? PT(1) : PT(0)));
+            if (!zbc) {
+                R::put(out, O_WALL, R::zero());
+                R::put(out, O_WALL + 1, R::zero());
+            }
+            *ticket = 0u;
+        }
+    } else {
+        (void)bsum;
+        (void)ticket;
+        (void)fin;
+        (void)last;
     }
 }
 
@@ -276,17 +281,30 @@ cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C
     return cudaGetLastError();
 }
 
+int reduce_blocks(int nx, int nz) {
+    return (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32) + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+}
+
 cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
-                          double* walls, double* bpart, unsigned* ticket, double* out, double* avg, int accumulate,
-                          cudaStream_t st) {
+                          unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
+                          bool tail, cudaStream_t st) {
     const int rb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-    const int cb = (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-    if (precision_bytes == 4)
-        k_reduce<float><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, reinterpret_cast<float*>(walls),
-                                                        bpart, ticket, out, avg, accumulate, 1.0f / nx, 1.0f / nz);
-    else
-        k_reduce<double><<<rb + cb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, walls, bpart, ticket, out,
-                                                         avg, accumulate, 1.0 / nx, 1.0 / nz);
+    const int nb = reduce_blocks(nx, nz);
+    if (precision_bytes == 4) {
+        if (tail)
+            k_reduce<float, true><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
+                                                             bpart, bavg, accumulate, 1.0f / nx, 1.0f / nz);
+        else
+            k_reduce<float, false><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
+                                                              bpart, bavg, accumulate, 1.0f / nx, 1.0f / nz);
+    } else {
+        if (tail)
+            k_reduce<double, true><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
+                                                              bpart, bavg, accumulate, 1.0 / nx, 1.0 / nz);
+        else
+            k_reduce<double, false><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
+                                                               bpart, bavg, accumulate, 1.0 / nx, 1.0 / nz);
+    }
     return cudaGetLastError();
 }
 
