@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--workload", default="emulsion_1024")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--rows-per-warp", type=int, default=0)
-    ap.add_argument("--kernel", choices=["fused", "twopass", "sweep"], default="fused")
+    ap.add_argument("--kernel", choices=["pull", "fused", "twopass", "sweep"], default="pull")
     ap.add_argument("--tile-rows", type=int, default=0, help="FUSED kernel tile height (8 or 16; 0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
@@ -134,9 +134,12 @@ def _traffic(kernel_src_hash, workload, precision, kernel):
     return e.get("dram_bytes_per_launch")
 
 
-def kernel_source_hash():
+KERNEL_SOURCE = {"pull": "lbm_pull.cu", "fused": "lbm_tile.cu", "twopass": "lbm_twopass.cu", "sweep": "lbm_fused.cu"}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha1()
-    for f in ("lbm_tile.cu", "lbm_core.cuh"):
+    for f in (KERNEL_SOURCE[kernel], "lbm_core.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1402_6019_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -237,7 +240,8 @@ def main():
     # a non-default stream: the library runs on it, and the events below are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    kern = {"fused": L.LBM_KERNEL_FUSED, "twopass": L.LBM_KERNEL_TWO_PASS, "sweep": L.LBM_KERNEL_SWEEP}[a.kernel]
+    kern = {"pull": L.LBM_KERNEL_PULL, "fused": L.LBM_KERNEL_FUSED, "twopass": L.LBM_KERNEL_TWO_PASS,
+            "sweep": L.LBM_KERNEL_SWEEP}[a.kernel]
     lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
                     stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, tile_rows=a.tile_rows,
                     **w["params"])
@@ -277,11 +281,12 @@ def main():
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = bps * sites / (kern_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _traffic(kernel_source_hash(), a.workload, a.precision,
+    traffic = _traffic(kernel_source_hash(a.kernel), a.workload, a.precision,
                        a.kernel if a.tile_rows in (0, 8) else f"{a.kernel}{a.tile_rows}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "kernel": {"fused": "lbm::k_tile<T, 2, M_WRITE|M_OBS>",
+                "kernel": {"pull": "lbm::k_pull<T, 2, M_WRITE|M_OBS>",
+                           "fused": "lbm::k_tile<T, 2, M_WRITE|M_OBS>",
                            "twopass": "lbm::k_density + lbm::k_twopass<T, 2, M_WRITE|M_OBS>",
                            "sweep": "lbm::k_fused<T, 2, M_WRITE|M_OBS>"}[a.kernel],
                 "kernel_ms": round(kern_avg_ms, 5),

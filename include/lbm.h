@@ -41,10 +41,14 @@ enum {
 
 enum { LBM_FP64 = 0, LBM_FP32 = 1 };            /* storage + arithmetic of the populations  */
 enum { LBM_PERIODIC = 0, LBM_BOUNCEBACK = 1 };  /* boundary in z (x is always periodic)     */
-/* step kernels: FUSED = one pass on 2-D tiles with the density halo recomputed (default);
+/* step kernels: PULL = one pass of persistent CTAs on 2-D tiles moved by TMA tensor loads and
+   stores, populations kept in the pull layout (post-collision values; the default, AUTO);
+   FUSED = one pass on 2-D tiles with the density halo recomputed from plain loads;
    TWO_PASS = a density/psi pass, then a collide pass staging the psi/rho tile by TMA;
-   SWEEP = one pass of warp strips sweeping rows with a cp.async shared-memory ring */
-enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_FUSED = 1, LBM_KERNEL_TWO_PASS = 2, LBM_KERNEL_SWEEP = 3 };
+   SWEEP = one pass of warp strips sweeping rows with a cp.async shared-memory ring.
+   FUSED, TWO_PASS and SWEEP keep the push layout (post-streaming values).  The layout is
+   internal: every entry point takes and returns the post-streaming populations of Sec. II. */
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_FUSED = 1, LBM_KERNEL_TWO_PASS = 2, LBM_KERNEL_SWEEP = 3, LBM_KERNEL_PULL = 4 };
 enum { LBM_PSI_EXP = 0, LBM_PSI_RHO = 1 };
 enum { LBM_WEIGHTS_PAPER = 0, LBM_WEIGHTS_CHEM09 = 1 };
 enum { LBM_WALL_MIRROR = 0, LBM_WALL_ZERO = 1 };
@@ -59,7 +63,7 @@ typedef struct {
     int precision;       /* LBM_FP64, or LBM_FP32: populations stored and relaxed in FP32
                             as deviations f_l - W_l rho_ref from the rest weights           */
     int z_boundary;      /* LBM_PERIODIC or LBM_BOUNCEBACK (walls at z = -1/2, nz - 1/2)  */
-    int kernel;          /* LBM_KERNEL_AUTO / _FUSED / _TWO_PASS / _SWEEP (see above)     */
+    int kernel;          /* LBM_KERNEL_AUTO / _PULL / _FUSED / _TWO_PASS / _SWEEP (above)   */
     int device;          /* CUDA device ordinal                                          */
     void *stream;        /* cudaStream_t to run on; NULL = a stream owned by the context  */
     int rows_per_warp;   /* SWEEP kernel: rows of one strip swept by a warp; 0 = auto      */

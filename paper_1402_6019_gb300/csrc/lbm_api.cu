@@ -36,8 +36,14 @@ struct lbm_ctx {
     int kernel = LBM_KERNEL_FUSED;  // resolved
     int tile_rows = 8;              // resolved tile height of the FUSED kernel
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
-    void* part_row = nullptr;  // partial sums in the populations' precision
-    void* part_col = nullptr;
+    void* part_row[2] = {nullptr, nullptr};  // partial sums in the populations' precision, one
+    void* part_col[2] = {nullptr, nullptr};  // set per population buffer parity
+    unsigned* sched = nullptr;               // pull: tile scheduler counters
+    // pull: the last observing step's partial sums (in part_*[pending_buf]) still to be reduced;
+    // the next pull launch folds the reduction in, a host read flushes it with k_reduce
+    bool pending = false;
+    bool pending_acc = false;
+    int pending_buf = 0;
     unsigned* ticket = nullptr;
     int* flag = nullptr;
     double* out = nullptr;
@@ -46,6 +52,10 @@ struct lbm_ctx {
     double* fexport = nullptr;  // ns * 9 * n doubles
     void* gfield = nullptr;     // two-pass ghost fields
     alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
+    bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
+    alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
+    alignas(64) unsigned char pmap_out[2][128] = {};  // pull: store descriptors of f[0], f[1]
+    int pull_grid[8] = {};                            // pull: resident CTAs per mode
     double* host_out = nullptr; // pinned
     StepConst<float> c32{};
     StepConst<double> c64{};
@@ -55,7 +65,9 @@ struct lbm_ctx {
     long long samples = 0;  // states accumulated into the time sums since the last reset
     long long step = 0;
     long long launches = 0;
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][observe]
+    // [parity][observe][first launch folds no pending reduction (0), one without (1) / with (2)
+    // accumulation into the time sums]
+    cudaGraphExec_t graph[2][2][3] = {};
     int graph_steps = 16;
     bool profiling = false;
     std::vector<cudaEvent_t> ev;  // pairs around step-kernel launches
@@ -95,11 +107,12 @@ static void refresh_const(lbm_ctx* c) {
 
 static void drop_graphs(lbm_ctx* c) {
     for (auto& pr : c->graph)
-        for (auto& g : pr)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
+        for (auto& po : pr)
+            for (auto& g : po)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
 }
 
 static size_t obs_bytes(const lbm_ctx* c) {
@@ -137,7 +150,7 @@ static int check_desc(lbm_ctx* c, const lbm_desc* d) {
     if (d->precision != LBM_FP64 && d->precision != LBM_FP32) return fail(c, LBM_EINVAL, "unknown precision");
     if (d->z_boundary != LBM_PERIODIC && d->z_boundary != LBM_BOUNCEBACK)
         return fail(c, LBM_EINVAL, "unknown z boundary");
-    if (d->kernel < LBM_KERNEL_AUTO || d->kernel > LBM_KERNEL_SWEEP) return fail(c, LBM_EINVAL, "unknown kernel");
+    if (d->kernel < LBM_KERNEL_AUTO || d->kernel > LBM_KERNEL_PULL) return fail(c, LBM_EINVAL, "unknown kernel");
     if (d->rows_per_warp < 0 || d->rows_per_warp > 65536) return fail(c, LBM_EINVAL, "rows_per_warp out of range");
     if (d->tile_rows != 0 && d->tile_rows != 8 && d->tile_rows != 16)
         return fail(c, LBM_EINVAL, "tile_rows must be 0, 8 or 16");
@@ -180,8 +193,9 @@ static void release(lbm_ctx* c) {
     drop_graphs(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
-    void* ptrs[] = {c->f[0], c->f[1], c->part_row, c->part_col, c->ticket, c->flag,
-                    c->out,  c->avg,  c->staging, c->fexport, c->gfield};
+    void* ptrs[] = {c->f[0],       c->f[1],       c->part_row[0], c->part_row[1], c->part_col[0],
+                    c->part_col[1], c->sched,      c->ticket,      c->flag,        c->out,
+                    c->avg,         c->staging,    c->fexport,     c->gfield};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_out) cudaFreeHost(c->host_out);
@@ -247,8 +261,9 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
     c->pitch = (nx + 31) / 32 * 32;
     c->plane = (long long)nz * c->pitch;
-    c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_FUSED : d->kernel;
-    c->tile_rows = d->tile_rows == 0 ? 8 : d->tile_rows;
+    c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_PULL : d->kernel;
+    c->pull = c->kernel == LBM_KERNEL_PULL;
+    c->tile_rows = c->pull || d->tile_rows == 0 ? 8 : d->tile_rows;
     const size_t fbytes = (size_t)ns * 9 * c->plane * c->esize;
     CKC(cudaMalloc(&c->f[0], fbytes));
     CKC(cudaMalloc(&c->f[1], fbytes));
@@ -268,8 +283,12 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     const int tx = (nx + TPX - 1) / TPX, tz = (nz + std::min(TPZ, 8) - 1) / std::min(TPZ, 8);
     const long long rows_parts = std::max(c->geom_obs.nstrips, tx);
     const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
-    CKC(cudaMalloc(&c->part_row, (size_t)rows_parts * nz * NQR * c->esize));
-    CKC(cudaMalloc(&c->part_col, (size_t)col_parts * nx * NQC * c->esize));
+    for (int b = 0; b < 2; ++b) {
+        CKC(cudaMalloc(&c->part_row[b], (size_t)rows_parts * nz * NQR * c->esize));
+        CKC(cudaMalloc(&c->part_col[b], (size_t)col_parts * nx * NQC * c->esize));
+    }
+    CKC(cudaMalloc(&c->sched, 2 * sizeof(unsigned)));
+    CKC(cudaMemsetAsync(c->sched, 0, 2 * sizeof(unsigned), c->stream));
     CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
     CKC(cudaMalloc(&c->flag, sizeof(int)));
     // observables: obs_len entries, then the reduction's block partials of the scalars
@@ -288,6 +307,18 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
         CKC(cudaMemsetAsync(c->gfield, 0, (size_t)2 * ns * c->ghost.gplane * c->esize, c->stream));
         if (make_field_tmap(c->tmap, c->gfield, (int)c->esize, ns, nz, c->ghost) != 0)
             return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the two-pass field planes"));
+    }
+    if (c->pull) {
+        for (int b = 0; b < 2; ++b)
+            if (make_pop_tmaps(c->pmap_in[b], c->pmap_out[b], c->f[b], (int)c->esize, ns, nx, nz, c->pitch, c->plane) !=
+                0)
+                return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
+        const int modes[4] = {M_WRITE, M_WRITE | M_OBS, M_OBS, M_FIELDS};
+        for (int m : modes) {
+            const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m) : pull_blocks_per_sm<float>(ns, m);
+            if (nb < 1) return bail(fail(c, LBM_ECUDA, "occupancy query of the pull kernel failed"));
+            c->pull_grid[m] = nb * c->nsm;
+        }
     }
     CKC(cudaStreamSynchronize(c->stream));
 #undef CKC
@@ -317,20 +348,65 @@ extern "C" int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
 // ---------------------------------------------------------------------------------------
 // Step kernels
 // ---------------------------------------------------------------------------------------
-static ObsPtrs obs_ptrs(const lbm_ctx* c) {
+static ObsPtrs obs_ptrs(const lbm_ctx* c, int buf) {
     ObsPtrs O;
-    O.part_row = c->part_row;
-    O.part_col = c->part_col;
+    O.part_row = c->part_row[buf];
+    O.part_col = c->part_col[buf];
     O.fields = c->staging;
     O.flag = c->flag;
     return O;
 }
 
+// The reduction kernel over the partial sums in part_*[buf] (of a pass at parity buf).
+static cudaError_t reduce_now(lbm_ctx* c, int buf, bool accumulate) {
+    const bool sweep = c->kernel == LBM_KERNEL_SWEEP;
+    const int tzrows = c->kernel == LBM_KERNEL_TWO_PASS ? TPZ : c->tile_rows;
+    const int nxp = sweep ? c->geom_obs.nstrips : (c->d.nx + TPX - 1) / TPX;
+    const int nzp = sweep ? c->geom_obs.nchunks : (c->d.nz + tzrows - 1) / tzrows;
+    const long long ol = obs_len(c->d.nx, c->d.nz);
+    c->launches += 1;
+    return launch_reduce((int)c->esize, obs_ptrs(c, buf), nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->ticket,
+                         c->out, c->avg, c->out + ol, c->avg + ol, accumulate ? 1 : 0, false, c->stream);
+}
+
+// A reduction left pending by the pull kernel, run now (before the host reads or resets the
+// observable buffers).
+static cudaError_t flush_pending(lbm_ctx* c) {
+    if (!c->pending) return cudaSuccess;
+    c->pending = false;
+    return reduce_now(c, c->pending_buf, c->pending_acc);
+}
+
 // One pass of the step kernel over the state in f[cur] (mode: M_WRITE into f[cur^1],
-// M_OBS partial sums, M_FIELDS per-site fields), plus the reduction when M_OBS.
-static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool accumulate) {
-    const ObsPtrs O = obs_ptrs(c);
+// M_OBS partial sums into part_*[cur], M_FIELDS per-site fields), plus the reduction when
+// `reduce`.  With the pull kernel and `defer` the reduction is left pending and folded into the
+// next pull launch; any pending reduction is folded into this launch.
+static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool accumulate, bool defer) {
+    const ObsPtrs O = obs_ptrs(c, cur);
     cudaError_t e;
+    Fold Rd{};
+    if (c->pull && c->pending) {
+        if (c->pending_buf == cur && (mode & M_OBS)) {
+            e = flush_pending(c);  // this pass would overwrite the pending partial sums
+            if (e != cudaSuccess) return e;
+        } else {
+            const long long ol = obs_len(c->d.nx, c->d.nz);
+            Rd.part_row = c->part_row[c->pending_buf];
+            Rd.part_col = c->part_col[c->pending_buf];
+            Rd.out = c->out;
+            Rd.avg = c->avg;
+            Rd.bpart = c->out + ol;
+            Rd.bavg = c->avg + ol;
+            Rd.nxpart = (c->d.nx + TPX - 1) / TPX;
+            Rd.nzpart = (c->d.nz + c->tile_rows - 1) / c->tile_rows;
+            Rd.accumulate = c->pending_acc ? 1 : 0;
+            Rd.enabled = 1;
+            // the reciprocals in the populations' precision, as the reduction kernel takes them
+            Rd.inx = c->esize == 4 ? (double)(1.0f / (float)c->d.nx) : 1.0 / c->d.nx;
+            Rd.inz = c->esize == 4 ? (double)(1.0f / (float)c->d.nz) : 1.0 / c->d.nz;
+            c->pending = false;
+        }
+    }
     const bool timed = c->profiling && (mode & M_WRITE);
     if (timed) {
         if (c->ev_used + 2 > c->ev.size()) {
@@ -364,6 +440,15 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
                                           (const float*)c->gfield, c->c32, c->ghost, c->tmap, O, tpx, tpz, c->stream);
         }
         c->launches += 1;
+    } else if (c->pull) {
+        const void* tin = c->pmap_in[cur];
+        const void* tout = c->pmap_out[cur ^ 1];
+        if (c->d.precision == LBM_FP64)
+            e = launch_pull<double>(c->d.n_species, mode, tin, tout, (const double*)c->f[cur], c->c64, O, Rd,
+                                    c->sched, c->pull_grid[mode], c->stream);
+        else
+            e = launch_pull<float>(c->d.n_species, mode, tin, tout, (const float*)c->f[cur], c->c32, O, Rd,
+                                   c->sched, c->pull_grid[mode], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
@@ -388,12 +473,13 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         c->ev_used += 2;
     }
     if (reduce) {
-        const bool sweep = c->kernel == LBM_KERNEL_SWEEP;
-        const int nxp = sweep ? c->geom_obs.nstrips : tpx, nzp = sweep ? c->geom_obs.nchunks : tpz;
-        const long long ol = obs_len(c->d.nx, c->d.nz);
-        e = launch_reduce((int)c->esize, O, nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->ticket, c->out, c->avg,
-                          c->out + ol, c->avg + ol, accumulate ? 1 : 0, false, c->stream);
-        c->launches += 1;
+        if (c->pull && defer) {
+            c->pending = true;
+            c->pending_buf = cur;
+            c->pending_acc = accumulate;
+        } else {
+            e = reduce_now(c, cur, accumulate);
+        }
         if (accumulate) c->samples += 1;
     }
     return e;
@@ -413,17 +499,23 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
     while (left > 0) {
         if (graphable && left >= G) {
             const int ob = c->observe_every == 1 ? 1 : 0;
-            cudaGraphExec_t& ge = c->graph[c->cur][ob];
+            const int ff = c->pull && c->pending ? (c->pending_acc ? 2 : 1) : 0;
+            cudaGraphExec_t& ge = c->graph[c->cur][ob][ff];
             if (!ge) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 const long long saved = c->launches, saved_samples = c->samples;
+                const bool saved_pending = c->pending, saved_acc = c->pending_acc;
+                const int saved_buf = c->pending_buf;
                 cudaError_t e = cudaSuccess;
                 for (int i = 0; i < G && e == cudaSuccess; ++i)
-                    e = enqueue_pass(c, (c->cur + i) & 1, M_WRITE | (ob ? M_OBS : 0), ob, ob);
+                    e = enqueue_pass(c, (c->cur + i) & 1, M_WRITE | (ob ? M_OBS : 0), ob, ob, true);
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
                 c->launches = saved;
                 c->samples = saved_samples;
+                c->pending = saved_pending;
+                c->pending_acc = saved_acc;
+                c->pending_buf = saved_buf;
                 CK(e);
                 CK(e2);
                 e = cudaGraphInstantiate(&ge, g, 0);
@@ -431,14 +523,19 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
                 CK(e);
             }
             CK(cudaGraphLaunch(ge, c->stream));
-            c->launches += (long long)G * (ob ? 2 : 1);
+            c->launches += (long long)G * (ob && !c->pull ? 2 : 1);
             if (ob) c->samples += G;
+            if (c->pull) {  // the last step's reduction is pending; an earlier one was folded in
+                c->pending = ob;
+                c->pending_acc = ob;
+                c->pending_buf = c->cur ^ 1;  // parity of the graph's last launch (G is even)
+            }
             c->step += G;  // G is even: the parity of cur is unchanged
             left -= G;
             continue;
         }
         const bool ob = observe_now(c, c->step);
-        CK(enqueue_pass(c, c->cur, M_WRITE | (ob ? M_OBS : 0), ob, ob));
+        CK(enqueue_pass(c, c->cur, M_WRITE | (ob ? M_OBS : 0), ob, ob, true));
         c->cur ^= 1;
         c->step += 1;
         left -= 1;
@@ -450,6 +547,7 @@ extern "C" int lbm_set_observe(lbm_ctx* c, int every) {
     if (!c) return LBM_EINVAL;
     if (every < 0) return fail(c, LBM_EINVAL, "every must be >= 0");
     CK(cudaSetDevice(c->d.device));
+    CK(flush_pending(c));  // its sample belongs to the sums being cleared
     c->observe_every = every;
     c->samples = 0;
     CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
@@ -495,13 +593,14 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
     drop_graphs(c);
     c->cur = 0;
     if (c->d.precision == LBM_FP64)
-        CK(launch_init<double>(ns, (double*)c->f[0], c->staging, du, c->c64, c->stream));
+        CK(launch_init<double>(ns, (double*)c->f[0], c->staging, du, c->c64, c->pull, c->stream));
     else
-        CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->stream));
+        CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->pull, c->stream));
     c->launches += 1;
     CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
     c->samples = 0;
+    c->pending = false;  // partial sums of the replaced state
     CK(cudaStreamSynchronize(c->stream));
     c->step = 0;
     c->have_fields = true;
@@ -517,16 +616,16 @@ extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int
     const long long n = (long long)c->d.nx * c->d.nz;
     const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (rho || u) {
-        CK(enqueue_pass(c, c->cur, M_FIELDS, false, false));
+        CK(enqueue_pass(c, c->cur, M_FIELDS, false, false, false));
         if (rho) CK(cudaMemcpyAsync(rho, c->staging, (size_t)ns * n * sizeof(double), kind, c->stream));
         if (u) CK(cudaMemcpyAsync(u, c->staging + ns * n, (size_t)2 * n * sizeof(double), kind, c->stream));
     }
     if (f) {
         if (!c->fexport) CK(cudaMalloc(&c->fexport, (size_t)ns * 9 * n * sizeof(double)));
         if (c->d.precision == LBM_FP64)
-            CK(launch_export<double>(ns, (const double*)c->f[c->cur], c->fexport, c->c64, c->stream));
+            CK(launch_export<double>(ns, (const double*)c->f[c->cur], c->fexport, c->c64, c->pull, c->stream));
         else
-            CK(launch_export<float>(ns, (const float*)c->f[c->cur], c->fexport, c->c32, c->stream));
+            CK(launch_export<float>(ns, (const float*)c->f[c->cur], c->fexport, c->c32, c->pull, c->stream));
         c->launches += 1;
         CK(cudaMemcpyAsync(f, c->fexport, (size_t)ns * 9 * n * sizeof(double), kind, c->stream));
     }
@@ -583,7 +682,7 @@ extern "C" int lbm_observables(lbm_ctx* c, lbm_obs* o) {
     if (!o) return fail(c, LBM_EINVAL, "out is NULL");
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
     CK(cudaSetDevice(c->d.device));
-    CK(enqueue_pass(c, c->cur, M_OBS, true, false));
+    CK(enqueue_pass(c, c->cur, M_OBS, true, false, false));
     CK(cudaMemcpyAsync(c->host_out, c->out, obs_bytes(c), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     unpack(c, c->host_out, o, 1.0);
@@ -595,6 +694,7 @@ extern "C" int lbm_averages(lbm_ctx* c, lbm_obs* o, int reset) {
     if (!c) return LBM_EINVAL;
     if (!o) return fail(c, LBM_EINVAL, "out is NULL");
     CK(cudaSetDevice(c->d.device));
+    CK(flush_pending(c));
     CK(cudaMemcpyAsync(c->host_out, c->avg, obs_bytes(c), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const double n = (double)c->samples;

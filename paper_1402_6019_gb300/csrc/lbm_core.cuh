@@ -224,7 +224,10 @@ LBM_HD void feq9_dev(T drho, T rho, T ux, T uz, T (&fe)[9]) {
 
 // Shifted-velocity BGK collision of all species at one site (Eq. LB with u_eq = u' + tau F /
 // rho, u' the common velocity sum_s j_s/tau_s / sum_s rho_s/tau_s).  f is overwritten with the
-// post-collision values.  rho[s] is the full density, drho[s] the stored sum, ir[s] = 1/rho[s],
+// post-collision values f + omega (feq - f) = (1 - omega) f + omega feq.  omega is folded into
+// the equilibrium's coefficients, and the pair structure of D2Q9 is used: l and its opposite
+// share the even part omega W (drho + rho (9/2 cu^2 - 3/2 u^2)) and have odd parts
+// +-3 omega W rho cu.  rho[s] is the full density, drho[s] the stored sum, ir[s] = 1/rho[s],
 // (jx, jz) the momenta of the stored values.
 template <typename T, int NS>
 LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], const T (&rho)[NS],
@@ -240,13 +243,26 @@ LBM_HD void collide(const StepConst<T>& C, T (&f)[NS][9], const T (&drho)[NS], c
     const T upx = nx_ * iden, upz = nz_ * iden;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
+        const T om = C.omega[s], keep = T(1) - om;
         const T tir = C.tau[s] * ir[s];
         const T ux = upx + F[s][0] * tir;
         const T uz = upz + F[s][1] * tir;
-        T fe[9];
-        feq9_dev<T>(drho[s], rho[s], ux, uz, fe);
+        const T u15 = T(1.5) * (ux * ux + uz * uz);
+        const T b = om * rho[s];
+        const T base = om * drho[s] - b * u15;  // omega (drho - 3/2 rho u^2)
+        // even part e + c cu^2 and odd part d cu, axis (W = 1/9) and diagonal (W = 1/36) pairs
+        const T e1 = base * T(1.0 / 9.0), c1 = b * T(0.5), d1 = b * T(1.0 / 3.0);
+        const T e2 = base * T(1.0 / 36.0), c2 = b * T(0.125), d2 = b * T(1.0 / 12.0);
+        f[s][0] = f[s][0] * keep + base * T(4.0 / 9.0);
+        const T cu[4] = {ux, uz, ux + uz, uz - ux};  // pairs (1,3), (2,4), (5,7), (6,8)
 #pragma unroll
-        for (int l = 0; l < 9; ++l) f[s][l] = f[s][l] + C.omega[s] * (fe[l] - f[s][l]);
+        for (int k = 0; k < 4; ++k) {
+            const T even = k < 2 ? e1 + (c1 * cu[k]) * cu[k] : e2 + (c2 * cu[k]) * cu[k];
+            const T odd = (k < 2 ? d1 : d2) * cu[k];
+            const int lp = k < 2 ? k + 1 : k + 3;  // 1, 2, 5, 6
+            f[s][lp] = (f[s][lp] * keep + even) + odd;
+            f[s][opp(lp)] = (f[s][opp(lp)] * keep + even) - odd;
+        }
     }
 }
 

@@ -59,13 +59,50 @@ template <typename T>
 cudaError_t launch_twopass(int ns, int mode, const T* fin, T* fout, const T* gfield, const StepConst<T>& C,
                            const GhostGeom& GG, const void* tmap, const ObsPtrs& O, int nxpart, int nzpart,
                            cudaStream_t st);
+// The driver's cuTensorMapEncodeTiled (resolved once through the runtime), or null.
+void* tensor_map_encoder();
 // Encodes the TMA descriptor (CUtensorMap, 128 bytes at out) of the two-pass field planes.
 // Returns 0 on success.
 int make_field_tmap(void* out, const void* g, int esize, int ns, int nz, const GhostGeom& GG);
+// The reduction of an earlier pass's partial sums, folded into a pull-kernel launch (its CTAs
+// run the work items of the reduction kernel before their first tile).  Pointers as for
+// launch_reduce; enabled = 0: nothing to reduce.
+struct Fold {
+    const void* part_row;
+    const void* part_col;
+    double* out;
+    double* avg;
+    double* bpart;
+    double* bavg;
+    int nxpart, nzpart;
+    int accumulate;
+    int enabled;
+    double inx, inz;  // 1/nx, 1/nz
+};
+
+// Pull-layout kernel: TMA descriptors of one population buffer f ([9 ns][nz][pitch] values):
+// the load box of a tile with its 3-cell ring (in_map) and the store box of a tile (out_map),
+// 128 bytes each.  Returns 0 on success.
+int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int nz, int pitch,
+                   long long plane);
+// CTAs of the pull kernel resident per SM for a mode (sets the kernel's shared-memory limit on
+// the current device); 0 on failure.
 template <typename T>
-cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, cudaStream_t st);
+int pull_blocks_per_sm(int ns, int mode);
+// One pass of the pull kernel: loads through tin (a buffer's in_map), stores through tout (the
+// other buffer's out_map); fin is the loaded buffer (for the periodic-edge patches).  grid_max:
+// resident CTAs on the device.  sched: two zeroed counters of the dynamic tile scheduler (the
+// kernel leaves them zeroed).  fold: a pending reduction run by the same launch.
 template <typename T>
-cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, cudaStream_t st);
+cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, const T* fin, const StepConst<T>& C,
+                        const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st);
+// Initial state / export of the populations of Sec. II (post-streaming, plain FP64 values),
+// in the push layout or (pull) the pull layout of the pull kernel.
+template <typename T>
+cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, bool pull,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, bool pull, cudaStream_t st);
 // Reduction of the step kernels' partial sums into the observables.  `out` / `avg` hold
 // obs_len(nx, nz) entries (profiles, wall forces, flag); `bpart` / `bavg` hold
 // reduce_blocks(nx, nz) * 5 block partials of the scalars (mass A, B, momentum x, z, gamma) and

@@ -1,0 +1,514 @@
+// lbm_pull.cu -- one-pass time step in the pull layout: persistent CTAs, tiles moved by TMA.
+//
+// Layout.  The stored value S(x, l) is the post-collision population f*_l(x) of the previous
+// step, except that a population leaving x through a wall (x + c_l beyond z = -1/2 or
+// z = nz - 1/2) is stored already reflected, S(x, l) = f*_l(x) - 6 W_l rho(x) c_lx U_w (halfway
+// bounce-back with Ladd's moving-wall term, Sec. IV): the value that enters x as opp(l) at the
+// next step.  The post-streaming populations of Sec. II are then
+//     f_l(x) = S(x - c_l, l)          if x - c_l lies in the lattice (x and periodic z wrap),
+//     f_l(x) = S(x, opp(l))           if x - c_l lies beyond a wall,
+// the same numbers the push layout of the other kernels stores.
+//
+// Work.  A CTA of PX x PZ threads (one warp per tile row) loops over tiles.  The populations of
+// the tile and of a 3-cell ring around it (2 cells for the psi stencil of Eq. FORCE, 1 more for
+// the gather) arrive in shared memory with one 3-D cp.async.bulk.tensor load whose x origin is
+// rounded down to a 16-byte boundary (x0 - 4); the new populations leave through one tensor
+// store of the tile.  No thread forms a global address on the hot path, and the tensor bounds
+// clip the ragged right and bottom tiles.  As soon as a tile's box has been read (densities of
+// the tile and ring formed), the load of the CTA's next tile is issued, so it runs under this
+// tile's force, collision and observables.  Tiles at the periodic edges patch the wrapped
+// columns and rows of their box with plain loads.  Every wait on the load is bounded.
+//
+// Tiles are handed out in row-major order by an atomic counter (the CTA that finishes last
+// resets it), so CTAs that drew the slower edge tiles simply take fewer tiles.  A launch can
+// also carry the reduction of the previous pass's observable partial sums (Fold): each CTA runs
+// its share of the reduction's work items while its first tile load is in flight.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "lbm_reduce.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int PX = 32, PZ = 8, NT = PX * PZ;
+constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3
+constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2
+constexpr int HW = PX + 4, HH = PZ + 4;   // psi/rho tile: x0 - 2 .. x0 + PX + 1, z0 - 2 .. z0 + PZ + 1
+constexpr int NRING = HW * HH - PX * PZ;  // psi/rho tile positions outside the tile
+static_assert(NRING <= NT, "one ring position per thread at most");
+static_assert(NT == RB_THREADS, "a CTA runs the reduction's work items");
+
+template <typename T, int NS>
+struct PullSmem {
+    T box[9 * NS][BZ][BX];             // TMA destination (box column bx = x - x0 + 4, row bz = z - z0 + 3)
+    alignas(128) T out[9 * NS][PZ][PX];  // TMA source: the tile's new stored values
+    T ps[NS][HH][HW];                  // psi and rho of the tile and its 2-cell ring
+    T rh[NS][HH][HW];
+    T colsum[PZ][NQC][PX];
+    typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
+    alignas(8) unsigned long long bar;
+    int next;  // the CTA's next tile
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <typename T, int NS>
+__device__ __forceinline__ void issue_load(PullSmem<T, NS>& S, const CUtensorMap* map, int x, int z) {
+    constexpr unsigned bytes = (unsigned)(sizeof(T) * 9 * NS * BZ * BX);
+    const unsigned bar = smem_u32(&S.bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(&S.box[0][0][0])),
+        "l"(map), "r"(x), "r"(z), "r"(0), "r"(bar)
+        : "memory");
+}
+
+// Bounded wait for the phase of the load barrier (about 1 s at 2 GHz); false on expiry.
+__device__ __forceinline__ bool wait_load(unsigned bar, unsigned parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
+// Post-streaming populations at box position (bx, bz): the gather of the pull layout.  lo / hi:
+// the site is the bottom / top row next to a wall, where populations coming from beyond the
+// wall are the site's own reflected values.
+template <typename T, int NS>
+__device__ __forceinline__ void gather(const PullSmem<T, NS>& S, int bx, int bz, T (&f)[NS][9]) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int l = 0; l < 9; ++l) f[s][l] = S.box[s * 9 + l][bz - cz(l)][bx - cx(l)];
+}
+template <typename T, int NS>
+__device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int bx, int bz, bool lo, bool hi,
+                                            T (&f)[NS][9]) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            const bool refl = (cz(l) > 0 && lo) || (cz(l) < 0 && hi);
+            f[s][l] = refl ? S.box[s * 9 + opp(l)][bz][bx] : S.box[s * 9 + l][bz - cz(l)][bx - cx(l)];
+        }
+}
+
+// rho and psi at psi/rho tile position (px, pz) for a position that is not a live site of the
+// tile: the ring, and the padding of ragged tiles.  With walls, rows beyond a wall take the
+// mirror image (or zero, Sec. IV's two readings of the ghost rows).  Positions that no live
+// site reads (far padding of ragged tiles) are set to zero.
+template <typename T, int NS>
+__device__ __forceinline__ void side_density(PullSmem<T, NS>& S, const StepConst<T>& C, int px, int pz, int z0) {
+    const int Z = z0 - 2 + pz;
+    int Zs = Z;
+    bool zero = false;
+    if (C.zbc && (Z < 0 || Z >= C.nz)) {
+        if (C.psi_wall == 1)
+            zero = true;
+        else
+            Zs = mirror_index(Z, C.nz);
+    }
+    const int bz = Zs - z0 + 3, bx = px + 2;
+    if (bz < 1 || bz > BZ - 2) zero = true;
+    T r[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) r[s] = T(0);
+    if (!zero) {
+        T g[NS][9];
+        const bool lo = C.zbc && Zs == 0, hi = C.zbc && Zs == C.nz - 1;
+        if (lo || hi)
+            gather_wall<T, NS>(S, bx, bz, lo, hi, g);
+        else
+            gather<T, NS>(S, bx, bz, g);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) r[s] = sum9(g[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const T rho = C.rho_ref[s] + r[s];
+        S.rh[s][pz][px] = zero ? T(0) : rho;
+        S.ps[s][pz][px] = zero ? T(0) : psi_of(C, s, rho);
+    }
+}
+
+template <typename T, int NS, int MODE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+    k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, const T* __restrict__ fin,
+           const StepConst<T> C, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched, int ntx, int ntz) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    PullSmem<T, NS>& S = *reinterpret_cast<PullSmem<T, NS>*>(smem_raw);
+    const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
+    const int nx = C.nx, nz = C.nz;
+    const int ntiles = ntx * ntz;
+    const unsigned bar = smem_u32(&S.bar);
+
+    // ring position of this thread (psi/rho tile coordinates): the top two rows, the bottom
+    // two rows, then two columns on each side of the tile rows
+    const bool ring = tid < NRING;
+    int rpx = 0, rpz = 0;
+    if (ring) {
+        if (tid < 2 * HW) {
+            rpz = tid / HW;
+            rpx = tid % HW;
+        } else if (tid < 4 * HW) {
+            rpz = HH - 2 + (tid - 2 * HW) / HW;
+            rpx = (tid - 2 * HW) % HW;
+        } else {
+            const int j = tid - 4 * HW;
+            rpz = 2 + (j >> 2);
+            const int c = j & 3;
+            rpx = c < 2 ? c : HW - 4 + c;
+        }
+    }
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        const int t0 = (int)atomicAdd(&sched[0], 1u);
+        S.next = t0;
+        if (t0 < ntiles) issue_load(S, &tin, (t0 % ntx) * PX - 4, (t0 / ntx) * PZ - 3);
+    }
+    __syncthreads();
+    if (Rd.enabled) {  // the previous pass's reduction, under the first load
+        const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+        const int nb = nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+        for (int b = blockIdx.x; b < nb; b += gridDim.x)
+            reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
+                            Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc);
+    }
+    int t = S.next;
+    unsigned parity = 0;
+    bool failed = false;
+    for (; t < ntiles; t = S.next, parity ^= 1u) {
+        const int x0 = (t % ntx) * PX, z0 = (t / ntx) * PZ;
+        const int x = x0 + tx, z = z0 + tz;
+        const bool live = x < nx && z < nz;
+        const bool ok = wait_load(bar, parity);
+
+        // periodic edges: columns (and without walls rows) outside the lattice get the wrapped
+        // values; the needed part of the box is columns x0 - 3 .. xe + 3, rows z0 - 3 .. ze + 3
+        const int xe = min(x0 + PX, nx) - 1, ze = min(z0 + PZ, nz) - 1;
+        if (x0 == 0 || xe + 3 >= nx || (!C.zbc && (z0 < 3 || ze + 3 >= nz))) {
+            const int wx = xe - x0 + 7, wz = ze - z0 + 7;
+            for (int i = tid; i < wx * wz; i += NT) {
+                const int bx = 1 + i % wx, bz = i / wx;
+                const int X = x0 - 4 + bx, Z = z0 - 3 + bz;
+                const bool xin = X >= 0 && X < nx, zin = Z >= 0 && Z < nz;
+                if ((xin && zin) || (!zin && C.zbc)) continue;
+                const int Xw = xin ? X : wrap_index(X, nx), Zw = zin ? Z : wrap_index(Z, nz);
+                const T* src = fin + (long long)Zw * C.pitch + Xw;
+#pragma unroll
+                for (int p = 0; p < 9 * NS; ++p) S.box[p][bz][bx] = src[p * C.plane];
+            }
+            __syncthreads();
+        }
+
+        // ---- phase A: this site's populations, rho and psi of the tile and its ring ----
+        T f[NS][9];
+        T drho[NS];
+        if (live) {
+            const bool lo = C.zbc && z == 0, hi = C.zbc && z == nz - 1;
+            if (lo || hi)
+                gather_wall<T, NS>(S, tx + 4, tz + 3, lo, hi, f);
+            else
+                gather<T, NS>(S, tx + 4, tz + 3, f);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                drho[s] = sum9(f[s]);
+                const T r = C.rho_ref[s] + drho[s];
+                S.rh[s][tz + 2][tx + 2] = r;
+                S.ps[s][tz + 2][tx + 2] = psi_of(C, s, r);
+            }
+        } else {
+            side_density<T, NS>(S, C, tx + 2, tz + 2, z0);
+        }
+        if (ring) side_density<T, NS>(S, C, rpx, rpz, z0);
+        if ((MODE & M_WRITE) && tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        // the box is free: draw this CTA's next tile and start its load
+        if (tid == 0) {
+            const int tn = (int)atomicAdd(&sched[0], 1u);
+            S.next = tn;  // read by all after the barrier that ends this tile
+            if (tn < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                issue_load(S, &tin, (tn % ntx) * PX - 4, (tn / ntx) * PZ - 3);
+            }
+        }
+
+        // ---- phase B: interaction, collision, new stored values, observables ----
+        T F[NS][2];
+        T sxx = T(0), szz = T(0), sxz = T(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            T p[5][5];
+#pragma unroll
+            for (int dz = 0; dz < 5; ++dz)
+#pragma unroll
+                for (int dx = 0; dx < 5; ++dx) p[dz][dx] = S.ps[s][tz + dz][tx + dx];
+            intra_force(C, s, p, F[s][0], F[s][1]);
+            if (MODE & M_OBS) intra_stress(C, s, p, sxx, szz, sxz);
+        }
+        if constexpr (NS == 2) {
+            T ra[3][3], rb[3][3];
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    ra[dz][dx] = S.rh[0][tz + 1 + dz][tx + 1 + dx];
+                    rb[dz][dx] = S.rh[1][tz + 1 + dz][tx + 1 + dx];
+                }
+            cross_force(C, ra, rb, F);
+            if (MODE & M_OBS) cross_stress(C, ra, rb, sxx, szz, sxz);
+        }
+
+        T rowq[NQR];
+#pragma unroll
+        for (int k = 0; k < NQR; ++k) rowq[k] = T(0);
+        T cps = T(0), cpx = T(0);
+        int bad = 0;
+        if (live) {
+            T rho[NS], ir[NS], jx[NS], jz[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                rho[s] = C.rho_ref[s] + drho[s];
+                if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = 1;
+                ir[s] = div_(T(1), rho[s]);
+                momentum9(f[s], jx[s], jz[s]);
+                F[s][0] += rho[s] * C.g;
+            }
+            if (MODE & (M_OBS | M_FIELDS)) {
+                T ux, uz, pixz, rtot, mx, mz;
+                site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
+                if (MODE & M_FIELDS) {
+                    const long long i = (long long)z * nx + x;
+                    const long long np = (long long)nx * nz;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) O.fields[s * np + i] = (double)rho[s];
+                    O.fields[NS * np + i] = (double)ux;
+                    O.fields[(NS + 1) * np + i] = (double)uz;
+                }
+                if (MODE & M_OBS) {
+                    T pxx = sxx, pzz = szz;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        pxx += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][0] * F[s][0] * ir[s];
+                        pzz += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][1] * F[s][1] * ir[s];
+                    }
+                    cps = pxx - pzz;
+                    cpx = pxx;
+                    rowq[QR_UX] = ux;
+                    rowq[QR_RHOA] = rho[0];
+                    rowq[QR_RHOB] = NS == 2 ? rho[NS - 1] : T(0);
+                    rowq[QR_SXZ] = -pixz - sxz;
+                    rowq[QR_MX] = mx;
+                    rowq[QR_MZ] = mz;
+                }
+            }
+            if (MODE & (M_WRITE | M_OBS)) {
+                const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+                if ((MODE & M_WRITE) || wall_row) {
+                    collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
+                    if (!wall_row) {  // warp-uniform
+                        if (MODE & M_WRITE) {
+#pragma unroll
+                            for (int s = 0; s < NS; ++s)
+#pragma unroll
+                                for (int l = 0; l < 9; ++l) S.out[s * 9 + l][tz][tx] = f[s][l];
+                        }
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < NS; ++s)
+#pragma unroll
+                            for (int l = 0; l < 9; ++l) {
+                                const int zd = z + cz(l);
+                                T v = f[s][l];
+                                if (zd < 0 || zd >= nz) {  // leaves through a wall: store it reflected
+                                    const int w = zd < 0 ? 0 : 1;
+                                    const T back = bounce<T>(l, f[s][l], rho[s], C.wall_u[w]);
+                                    v = back;
+                                    if (MODE & M_OBS) {
+                                        const T dm = T(cx(l)) * (f[s][l] + back);
+                                        if (w == 0)
+                                            rowq[QR_WALLB] += dm;
+                                        else
+                                            rowq[QR_WALLT] += dm;
+                                    }
+                                }
+                                if (MODE & M_WRITE) S.out[s * 9 + l][tz][tx] = v;
+                            }
+                    }
+                }
+            }
+        }
+        if (__any_sync(FULL, bad) && tx == 0) atomicOr(O.flag, 1);
+        if (MODE & M_WRITE) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (MODE & M_OBS) {
+            // per-row sums over the 32 sites of this warp: transpose-reduce, lane 4q holds quantity q
+            static_assert(NQR == 8, "row reduction is written for 8 quantities");
+            T v4[4], v2[2], v1;
+            const bool b4 = tx & 16, b3 = tx & 8, b2 = tx & 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T keep = b4 ? rowq[k + 4] : rowq[k], send = b4 ? rowq[k] : rowq[k + 4];
+                v4[k] = keep + __shfl_xor_sync(FULL, send, 16);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const T keep = b3 ? v4[k + 2] : v4[k], send = b3 ? v4[k] : v4[k + 2];
+                v2[k] = keep + __shfl_xor_sync(FULL, send, 8);
+            }
+            {
+                const T keep = b2 ? v2[1] : v2[0], send = b2 ? v2[0] : v2[1];
+                v1 = keep + __shfl_xor_sync(FULL, send, 4);
+            }
+            v1 += __shfl_xor_sync(FULL, v1, 2);
+            v1 += __shfl_xor_sync(FULL, v1, 1);
+            if ((tx & 3) == 0 && z < nz) {
+                const int q = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+                static_cast<T*>(O.part_row)[((long long)z * ntx + x0 / PX) * NQR + q] = v1;
+            }
+            S.colsum[tz][QC_PS][tx] = cps;
+            S.colsum[tz][QC_PXX][tx] = cpx;
+        }
+        __syncthreads();
+        if ((MODE & M_WRITE) && tid == 0) {
+            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                             &tout),
+                         "r"(x0), "r"(z0), "r"(0), "r"(smem_u32(&S.out[0][0][0]))
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        }
+        if (MODE & M_OBS) {
+            // per-column sums over the PZ rows of the tile
+            if (tz < NQC && x < nx) {
+                T v = T(0);
+#pragma unroll
+                for (int r = 0; r < PZ; ++r) v += S.colsum[r][tz][tx];
+                static_cast<T*>(O.part_col)[((long long)x * ntz + z0 / PZ) * NQC + tz] = v;
+            }
+        }
+    }
+    if (tid == 0) {
+        if (failed) {
+            atomicOr(O.flag, 2);
+            wait_load(bar, parity);  // the load that did not arrive in time, before the CTA exits
+        }
+        asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+        // the last CTA out resets the scheduler for the next launch (every CTA's draws on
+        // sched[0] come before its fence and its increment of sched[1])
+        __threadfence();
+        if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
+            atomicExch(&sched[0], 0u);
+            atomicExch(&sched[1], 0u);
+        }
+    }
+}
+
+template <typename T, int NS, int MODE>
+int pull_occupancy() {
+    const size_t smem = sizeof(PullSmem<T, NS>);
+    if (cudaFuncSetAttribute(k_pull<T, NS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pull<T, NS, MODE>, NT, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+template <typename T, int NS, int MODE>
+cudaError_t launch_mode(const void* tin, const void* tout, const T* fin, const StepConst<T>& C, const ObsPtrs& O,
+                        const Fold& Rd, unsigned* sched, int grid_max, cudaStream_t st) {
+    const int ntx = (C.nx + PX - 1) / PX, ntz = (C.nz + PZ - 1) / PZ;
+    const long long ntiles = (long long)ntx * ntz;
+    int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
+    if (Rd.enabled && grid < 1) grid = 1;
+    k_pull<T, NS, MODE><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS>), st>>>(
+        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fin, C, O, Rd, sched, ntx, ntz);
+    return cudaGetLastError();
+}
+
+template <typename T, int NS>
+cudaError_t launch_ns(int mode, const void* tin, const void* tout, const T* fin, const StepConst<T>& C,
+                      const ObsPtrs& O, const Fold& Rd, unsigned* sched, int grid_max, cudaStream_t st) {
+    switch (mode) {
+        case M_WRITE: return launch_mode<T, NS, M_WRITE>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
+        case M_WRITE | M_OBS:
+            return launch_mode<T, NS, M_WRITE | M_OBS>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
+        case M_OBS: return launch_mode<T, NS, M_OBS>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
+        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+int pull_blocks_per_sm(int ns, int mode) {
+    if (ns == 1) {
+        switch (mode) {
+            case M_WRITE: return pull_occupancy<T, 1, M_WRITE>();
+            case M_WRITE | M_OBS: return pull_occupancy<T, 1, M_WRITE | M_OBS>();
+            case M_OBS: return pull_occupancy<T, 1, M_OBS>();
+            case M_FIELDS: return pull_occupancy<T, 1, M_FIELDS>();
+            default: return 0;
+        }
+    }
+    switch (mode) {
+        case M_WRITE: return pull_occupancy<T, 2, M_WRITE>();
+        case M_WRITE | M_OBS: return pull_occupancy<T, 2, M_WRITE | M_OBS>();
+        case M_OBS: return pull_occupancy<T, 2, M_OBS>();
+        case M_FIELDS: return pull_occupancy<T, 2, M_FIELDS>();
+        default: return 0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, const T* fin, const StepConst<T>& C,
+                        const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st) {
+    if (grid_max < 1) return cudaErrorInvalidConfiguration;
+    return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fin, C, O, fold, sched, grid_max, st)
+                   : launch_ns<T, 2>(mode, tin, tout, fin, C, O, fold, sched, grid_max, st);
+}
+
+int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int nz, int pitch,
+                   long long plane) {
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!encode) return 1;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)nz, (cuuint64_t)(9 * ns)};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
+    const cuuint32_t box_in[3] = {(cuuint32_t)BX, (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
+    const cuuint32_t box_out[3] = {(cuuint32_t)PX, (cuuint32_t)PZ, (cuuint32_t)(9 * ns)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    CUresult r = encode(static_cast<CUtensorMap*>(in_map), dt, 3, const_cast<void*>(f), dims, strides, box_in, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return 2;
+    r = encode(static_cast<CUtensorMap*>(out_map), dt, 3, const_cast<void*>(f), dims, strides, box_out, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : 2;
+}
+
+template int pull_blocks_per_sm<float>(int, int);
+template int pull_blocks_per_sm<double>(int, int);
+template cudaError_t launch_pull<float>(int, int, const void*, const void*, const float*, const StepConst<float>&,
+                                        const ObsPtrs&, const Fold&, unsigned*, int, cudaStream_t);
+template cudaError_t launch_pull<double>(int, int, const void*, const void*, const double*, const StepConst<double>&,
+                                         const ObsPtrs&, const Fold&, unsigned*, int, cudaStream_t);
+
+}  // namespace lbm

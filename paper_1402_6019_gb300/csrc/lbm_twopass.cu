@@ -294,17 +294,23 @@ cudaError_t launch_twopass(int ns, int mode, const T* fin, T* fout, const T* /*g
 }
 
 // Tensor map of the field planes [2 ns][nz + 4][gpitch], box (TPX + 2 GX) x (TPZ + 4) x 2 ns.
-int make_field_tmap(void* out, const void* g, int esize, int ns, int nz, const GhostGeom& GG) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+void* tensor_map_encoder() {
+    static void* encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !fn)
-            return 1;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+            return nullptr;
+        encode = fn;
     }
+    return encode;
+}
+
+int make_field_tmap(void* out, const void* g, int esize, int ns, int nz, const GhostGeom& GG) {
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!encode) return 1;
     const cuuint64_t dims[3] = {(cuuint64_t)GG.gpitch, (cuuint64_t)(nz + 4), (cuuint64_t)(2 * ns)};
     const cuuint64_t strides[2] = {(cuuint64_t)GG.gpitch * esize, (cuuint64_t)GG.gplane * esize};
     const cuuint32_t box[3] = {(cuuint32_t)TW, (cuuint32_t)TH, (cuuint32_t)(2 * ns)};

@@ -16,7 +16,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENOMEM, LBM_ENONFINITE, LBM_ETIMEOUT = range(6)
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_PERIODIC, LBM_BOUNCEBACK = 0, 1
-LBM_KERNEL_AUTO, LBM_KERNEL_FUSED, LBM_KERNEL_TWO_PASS, LBM_KERNEL_SWEEP = 0, 1, 2, 3
+LBM_KERNEL_AUTO, LBM_KERNEL_FUSED, LBM_KERNEL_TWO_PASS, LBM_KERNEL_SWEEP, LBM_KERNEL_PULL = 0, 1, 2, 3, 4
 LBM_PSI_EXP, LBM_PSI_RHO = 0, 1
 LBM_WEIGHTS_PAPER, LBM_WEIGHTS_CHEM09 = 0, 1
 LBM_WALL_MIRROR, LBM_WALL_ZERO = 0, 1

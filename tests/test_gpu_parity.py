@@ -17,8 +17,8 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 1e-4
-KERNELS = pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWO_PASS, L.LBM_KERNEL_SWEEP],
-                                  ids=["tile", "twopass", "sweep"])
+KERNELS = pytest.mark.parametrize("kernel", [L.LBM_KERNEL_PULL, L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWO_PASS,
+                                             L.LBM_KERNEL_SWEEP], ids=["pull", "tile", "twopass", "sweep"])
 
 
 def rel(a, b):
