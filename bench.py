@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_SITE = {("fp32", 2): 144, ("fp64", 2): 288, ("fp32", 1): 72, ("fp64", 1): 144}
 L2_FLUSH_BYTES = 256 << 20
+L2_BYTES = 126 << 20          # L2 of a GB300 (nvidia-smi / device properties: 126.5 MiB)
+ROTATE_BYTES = 512 << 20      # working set of the rotated lattices, well above L2
 
 
 def _args():
@@ -49,6 +51,10 @@ def _args():
     ap.add_argument("--tile-rows", type=int, default=0, help="FUSED kernel tile height (8 or 16; 0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--l2", choices=["rotate", "flush"], default="rotate",
+                    help="rotate: step several lattices of the workload in turn, so that each step's input "
+                         "was evicted from L2 by the others' traffic (no flush); flush: one lattice, a 256 MiB "
+                         "write then a 256 MiB read between timed steps")
     ap.add_argument("--observe-every", type=int, default=1,
                     help="sample the observables every k steps (1 = every step, the full hot path; "
                          "0 = never, for analysis only)")
@@ -242,35 +248,66 @@ def main():
     torch.cuda.set_stream(stream)
     kern = {"pull": L.LBM_KERNEL_PULL, "fused": L.LBM_KERNEL_FUSED, "twopass": L.LBM_KERNEL_TWO_PASS,
             "sweep": L.LBM_KERNEL_SWEEP}[a.kernel]
-    lat = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
-                    stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, tile_rows=a.tile_rows,
-                    **w["params"])
-    lat.set_fields(w["rho"])
-    lat.set_observe(a.observe_every)  # 1: every step reduces the observables of the state it collides
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    def make_lattice():
+        lt = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
+                       stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, tile_rows=a.tile_rows,
+                       **w["params"])
+        lt.set_fields(w["rho"])
+        lt.set_observe(a.observe_every)  # 1: every step reduces the observables of the state it collides
+        return lt
 
-    for _ in range(a.warmup):
-        flush.fill_(1.0)
-        lat.step(1)
-    lat.synchronize()
+    esize = 4 if a.precision == "fp32" else 8
+    lattice_bytes = 2 * 9 * ns * sites * esize  # both population buffers
+    n_rot = 1 if a.l2 == "flush" else max(1, min(8, -(-ROTATE_BYTES // lattice_bytes)))
+    lats = [make_lattice() for _ in range(n_rot)]
+    lat = lats[0]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
+    flush_src = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    L.lbm_profile(lat.h, True)
-    launches0 = lat.launches
+    def l2_flush(k):
+        # write a buffer larger than L2, then read another one, so that the step starts with none
+        # of its data in L2 and no foreign dirty lines to write back
+        flush.fill_(float(k))
+        flush_src.sum()
+
+    for k in range(a.warmup):
+        for lt in lats:
+            if flush is not None:
+                l2_flush(k)
+            lt.step(1)
+    for lt in lats:
+        lt.synchronize()
+
+    for lt in lats:
+        L.lbm_profile(lt.h, True)
+    launches0 = sum(lt.launches for lt in lats)
     barrier()
     with Clocks(local) as clk:
-        for k in range(a.steps):
-            flush.fill_(float(k))
-            starts[k].record(stream)
-            lat.step(1)
-            ends[k].record(stream)
-        barrier()
-    launches = lat.launches - launches0
-    step_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
-    kern_ms, kern_n = L.lbm_profile_read(lat.h)
-    L.lbm_profile(lat.h, False)
-    lat.synchronize()
+        if flush is not None:
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+            for k in range(a.steps):
+                l2_flush(k)
+                starts[k].record(stream)
+                lat.step(1)
+                ends[k].record(stream)
+            barrier()
+            step_ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+        else:
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for k in range(a.steps):
+                lats[k % n_rot].step(1)
+            t1.record(stream)
+            barrier()
+            step_ms = float(t0.elapsed_time(t1))
+    launches = sum(lt.launches for lt in lats) - launches0
+    kern_ms, kern_n = 0.0, 0
+    for lt in lats:
+        km, kn = L.lbm_profile_read(lt.h)
+        kern_ms, kern_n = kern_ms + km, kern_n + kn
+        L.lbm_profile(lt.h, False)
+        lt.synchronize()
     # whole job: the slowest rank's time, every rank's sites
     step_s, job_sites = replicas.aggregate(step_ms * 1e-3, sites, dist=dist, device="cuda")
     ms_per_step = step_s * 1e3 / a.steps
@@ -323,7 +360,10 @@ def main():
         "data": "synthetic",
         "config": {"workload": a.workload, "nx": nx, "nz": nz, "n_species": ns,
                    "precision": a.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MiB write)",
+                   "l2": (f"{n_rot} lattices of the workload stepped in turn, back to back "
+                          f"({n_rot * lattice_bytes / 2**20:.0f} MiB of populations > {L2_BYTES / 2**20:.0f} MiB L2); "
+                          "no flush" if flush is None else
+                          "one lattice; a 256 MiB write then a 256 MiB read between timed steps"),
                    "observables": ("every step" if a.observe_every == 1 else
                                    "never" if a.observe_every == 0 else f"every {a.observe_every} steps"),
                    "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel},
