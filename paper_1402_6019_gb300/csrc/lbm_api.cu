@@ -38,7 +38,7 @@ struct lbm_ctx {
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
     void* part_row[2] = {nullptr, nullptr};  // partial sums in the populations' precision, one
     void* part_col[2] = {nullptr, nullptr};  // set per population buffer parity
-    unsigned* sched = nullptr;               // pull: tile scheduler counters
+    unsigned* sched = nullptr;  // pull: work-item counters (zero between launches)
     // pull: the last observing step's partial sums (in part_*[pending_buf]) still to be reduced;
     // the next pull launch folds the reduction in, a host read flushes it with k_reduce
     bool pending = false;
@@ -259,10 +259,15 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     const int nx = d->nx, nz = d->nz, ns = d->n_species;
     c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
-    c->pitch = (nx + 31) / 32 * 32;
-    c->plane = (long long)nz * c->pitch;
     c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_PULL : d->kernel;
     c->pull = c->kernel == LBM_KERNEL_PULL;
+    if (c->pull) {  // ghost columns and rows around every plane; 128-byte rows
+        c->pitch = (nx + 2 * PULL_GX + 31) / 32 * 32;
+        c->plane = (long long)(nz + 2 * PULL_GZ) * c->pitch;
+    } else {
+        c->pitch = (nx + 31) / 32 * 32;
+        c->plane = (long long)nz * c->pitch;
+    }
     c->tile_rows = c->pull || d->tile_rows == 0 ? 8 : d->tile_rows;
     const size_t fbytes = (size_t)ns * 9 * c->plane * c->esize;
     CKC(cudaMalloc(&c->f[0], fbytes));
@@ -444,10 +449,10 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const void* tin = c->pmap_in[cur];
         const void* tout = c->pmap_out[cur ^ 1];
         if (c->d.precision == LBM_FP64)
-            e = launch_pull<double>(c->d.n_species, mode, tin, tout, (const double*)c->f[cur], c->c64, O, Rd,
+            e = launch_pull<double>(c->d.n_species, mode, tin, tout, (double*)c->f[cur ^ 1], c->c64, O, Rd,
                                     c->sched, c->pull_grid[mode], c->stream);
         else
-            e = launch_pull<float>(c->d.n_species, mode, tin, tout, (const float*)c->f[cur], c->c32, O, Rd,
+            e = launch_pull<float>(c->d.n_species, mode, tin, tout, (float*)c->f[cur ^ 1], c->c32, O, Rd,
                                    c->sched, c->pull_grid[mode], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
@@ -592,11 +597,14 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
     refresh_const(c);
     drop_graphs(c);
     c->cur = 0;
-    if (c->d.precision == LBM_FP64)
+    if (c->d.precision == LBM_FP64) {
         CK(launch_init<double>(ns, (double*)c->f[0], c->staging, du, c->c64, c->pull, c->stream));
-    else
+        if (c->pull) CK(launch_pull_images<double>(ns, (double*)c->f[0], c->c64, c->stream));
+    } else {
         CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->pull, c->stream));
-    c->launches += 1;
+        if (c->pull) CK(launch_pull_images<float>(ns, (float*)c->f[0], c->c32, c->stream));
+    }
+    c->launches += c->pull ? 2 : 1;
     CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
     c->samples = 0;

@@ -80,7 +80,12 @@ struct Fold {
     double inx, inz;  // 1/nx, 1/nz
 };
 
-// Pull-layout kernel: TMA descriptors of one population buffer f ([9 ns][nz][pitch] values):
+// Pull layout: ghost columns on either side and ghost rows above and below each plane; lattice
+// site (x, z) sits at padded column x + PULL_GX, padded row z + PULL_GZ.  pitch >= nx + 2 PULL_GX,
+// plane = (nz + 2 PULL_GZ) pitch.
+constexpr int PULL_GX = 4, PULL_GZ = 3;
+
+// Pull-layout kernel: TMA descriptors of one population buffer f ([9 ns][nz + 6][pitch] values):
 // the load box of a tile with its 3-cell ring (in_map) and the store box of a tile (out_map),
 // 128 bytes each.  Returns 0 on success.
 int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int nz, int pitch,
@@ -90,14 +95,18 @@ int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns
 template <typename T>
 int pull_blocks_per_sm(int ns, int mode);
 // One pass of the pull kernel: loads through tin (a buffer's in_map), stores through tout (the
-// other buffer's out_map); fin is the loaded buffer (for the periodic-edge patches).  grid_max:
-// resident CTAs on the device.  sched: two zeroed counters of the dynamic tile scheduler (the
-// kernel leaves them zeroed).  fold: a pending reduction run by the same launch.
+// other buffer's out_map); fout is that other buffer (periodic images are stored to it
+// directly).  fold: a pending reduction run by the same launch.  sched: two counters, zero
+// before the launch and left zero by it.  grid_max: resident CTAs on the device.
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, const T* fin, const StepConst<T>& C,
+cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
                         const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st);
+// Fills the ghost columns and rows of a pull-layout buffer with the periodic images.
+template <typename T>
+cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, cudaStream_t st);
 // Initial state / export of the populations of Sec. II (post-streaming, plain FP64 values),
-// in the push layout or (pull) the pull layout of the pull kernel.
+// in the push layout or (pull) the padded pull layout of the pull kernel (C.pitch, C.plane are
+// the buffer's; the ghosts are filled by launch_pull_images).
 template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, bool pull,
                         cudaStream_t st);

@@ -24,10 +24,13 @@ __global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho
                 int ls = l;
                 if (pull) {
                     const int zs = z - cz(l);
-                    if (C.zbc && (zs < 0 || zs >= C.nz))
+                    if (C.zbc && (zs < 0 || zs >= C.nz)) {
                         ls = opp(l);
-                    else
-                        o = (long long)wrap_index(zs, C.nz) * C.pitch + wrap_index(x - cx(l), C.nx);
+                        o = (long long)(z + PULL_GZ) * C.pitch + x + PULL_GX;
+                    } else {
+                        o = (long long)(wrap_index(zs, C.nz) + PULL_GZ) * C.pitch + wrap_index(x - cx(l), C.nx) +
+                            PULL_GX;
+                    }
                 }
                 f[(s * 9 + ls) * C.plane + o] = (T)feq_dev<double>(l, dr, r, ux, uz);
             }
@@ -48,10 +51,13 @@ __global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ o
                 int ls = l;
                 if (pull) {
                     const int zs = z - cz(l);
-                    if (C.zbc && (zs < 0 || zs >= C.nz))
+                    if (C.zbc && (zs < 0 || zs >= C.nz)) {
                         ls = opp(l);
-                    else
-                        o = (long long)wrap_index(zs, C.nz) * C.pitch + wrap_index(x - cx(l), C.nx);
+                        o = (long long)(z + PULL_GZ) * C.pitch + x + PULL_GX;
+                    } else {
+                        o = (long long)(wrap_index(zs, C.nz) + PULL_GZ) * C.pitch + wrap_index(x - cx(l), C.nx) +
+                            PULL_GX;
+                    }
                 }
                 out[(s * 9 + l) * n + i] = (double)f[(s * 9 + ls) * C.plane + o] + wlb<double>(l) * (double)C.rho_ref[s];
             }

@@ -7,22 +7,24 @@
 // next step.  The post-streaming populations of Sec. II are then
 //     f_l(x) = S(x - c_l, l)          if x - c_l lies in the lattice (x and periodic z wrap),
 //     f_l(x) = S(x, opp(l))           if x - c_l lies beyond a wall,
-// the same numbers the push layout of the other kernels stores.
+// the same numbers the push layout of the other kernels stores.  Each plane is padded with
+// PULL_GX ghost columns on either side and PULL_GZ ghost rows above and below, which hold the
+// periodic images of the lattice (rows only without walls); the kernel that writes a boundary
+// site also writes its images, so every tile's read is one in-bounds rectangle.
 //
 // Work.  A CTA of PX x PZ threads (one warp per tile row) loops over tiles.  The populations of
 // the tile and of a 3-cell ring around it (2 cells for the psi stencil of Eq. FORCE, 1 more for
-// the gather) arrive in shared memory with one 3-D cp.async.bulk.tensor load whose x origin is
-// rounded down to a 16-byte boundary (x0 - 4); the new populations leave through one tensor
-// store of the tile.  No thread forms a global address on the hot path, and the tensor bounds
-// clip the ragged right and bottom tiles.  As soon as a tile's box has been read (densities of
-// the tile and ring formed), the load of the CTA's next tile is issued, so it runs under this
-// tile's force, collision and observables.  Tiles at the periodic edges patch the wrapped
-// columns and rows of their box with plain loads.  Every wait on the load is bounded.
+// the gather, x rounded to a 16-byte boundary) arrive in shared memory with one 3-D
+// cp.async.bulk.tensor load; the new populations leave through one tensor store of the tile.
+// No thread forms a global address on the hot path.  As soon as a tile's box has been read
+// (densities of the tile and ring formed), the load of the CTA's next tile is issued, so it
+// runs under this tile's force, collision and observables.  Every wait on a load is bounded.
 //
 // Tiles are handed out in row-major order by an atomic counter (the CTA that finishes last
-// resets it), so CTAs that drew the slower edge tiles simply take fewer tiles.  A launch can
-// also carry the reduction of the previous pass's observable partial sums (Fold): each CTA runs
-// its share of the reduction's work items while its first tile load is in flight.
+// resets it), so the CTAs at work at any moment cover a band of rows and read each other's halo
+// while it is in L2.  A launch can also carry the reduction of the previous pass's observable
+// partial sums (Fold): each CTA runs its share of the reduction's work items while its first
+// tile load is in flight.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -34,12 +36,13 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int PX = 32, PZ = 8, NT = PX * PZ;
-constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3
-constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2
+constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3 (padded x0 .. x0 + PX + 7)
+constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2 (padded z0 .. z0 + PZ + 5)
 constexpr int HW = PX + 4, HH = PZ + 4;   // psi/rho tile: x0 - 2 .. x0 + PX + 1, z0 - 2 .. z0 + PZ + 1
 constexpr int NRING = HW * HH - PX * PZ;  // psi/rho tile positions outside the tile
 static_assert(NRING <= NT, "one ring position per thread at most");
 static_assert(NT == RB_THREADS, "a CTA runs the reduction's work items");
+static_assert(PULL_GX == 4 && PULL_GZ == 3, "the box starts at padded (x0, z0)");
 
 template <typename T, int NS>
 struct PullSmem {
@@ -142,9 +145,37 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, const StepConst
     }
 }
 
+// The periodic images of site (x, z): plain stores of its new values (read back from the
+// staging tile) into the ghost columns (and, without walls, ghost rows) that wrap onto it.
+template <typename T, int NS>
+__device__ __noinline__ void write_images(const PullSmem<T, NS>& S, const StepConst<T>& C, T* __restrict__ fout,
+                                          int x, int z, int tx, int tz) {
+    const int nx = C.nx, nz = C.nz;
+    int xs[2 * PULL_GX + 1], zs[2 * PULL_GZ + 1];
+    int nxs = 0, nzs = 0;
+    xs[nxs++] = x;
+    zs[nzs++] = z;
+    for (int g = 0; g < 2 * PULL_GX; ++g) {
+        const int gx = g < PULL_GX ? g - PULL_GX : nx + g - PULL_GX;
+        if (wrap_index(gx, nx) == x) xs[nxs++] = gx;
+    }
+    if (!C.zbc)
+        for (int g = 0; g < 2 * PULL_GZ; ++g) {
+            const int gz = g < PULL_GZ ? g - PULL_GZ : nz + g - PULL_GZ;
+            if (wrap_index(gz, nz) == z) zs[nzs++] = gz;
+        }
+    for (int a = 0; a < nxs; ++a)
+        for (int b = 0; b < nzs; ++b) {
+            if (a == 0 && b == 0) continue;
+            T* dst = fout + (long long)(zs[b] + PULL_GZ) * C.pitch + (xs[a] + PULL_GX);
+#pragma unroll
+            for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
+        }
+}
+
 template <typename T, int NS, int MODE>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
-    k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, const T* __restrict__ fin,
+    k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, T* __restrict__ fout,
            const StepConst<T> C, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched, int ntx, int ntz) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PullSmem<T, NS>& S = *reinterpret_cast<PullSmem<T, NS>*>(smem_raw);
@@ -177,7 +208,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         const int t0 = (int)atomicAdd(&sched[0], 1u);
         S.next = t0;
-        if (t0 < ntiles) issue_load(S, &tin, (t0 % ntx) * PX - 4, (t0 / ntx) * PZ - 3);
+        if (t0 < ntiles) issue_load(S, &tin, (t0 % ntx) * PX, (t0 / ntx) * PZ);  // padded (x0, z0)
     }
     __syncthreads();
     if (Rd.enabled) {  // the previous pass's reduction, under the first load
@@ -195,24 +226,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         const int x = x0 + tx, z = z0 + tz;
         const bool live = x < nx && z < nz;
         const bool ok = wait_load(bar, parity);
-
-        // periodic edges: columns (and without walls rows) outside the lattice get the wrapped
-        // values; the needed part of the box is columns x0 - 3 .. xe + 3, rows z0 - 3 .. ze + 3
-        const int xe = min(x0 + PX, nx) - 1, ze = min(z0 + PZ, nz) - 1;
-        if (x0 == 0 || xe + 3 >= nx || (!C.zbc && (z0 < 3 || ze + 3 >= nz))) {
-            const int wx = xe - x0 + 7, wz = ze - z0 + 7;
-            for (int i = tid; i < wx * wz; i += NT) {
-                const int bx = 1 + i % wx, bz = i / wx;
-                const int X = x0 - 4 + bx, Z = z0 - 3 + bz;
-                const bool xin = X >= 0 && X < nx, zin = Z >= 0 && Z < nz;
-                if ((xin && zin) || (!zin && C.zbc)) continue;
-                const int Xw = xin ? X : wrap_index(X, nx), Zw = zin ? Z : wrap_index(Z, nz);
-                const T* src = fin + (long long)Zw * C.pitch + Xw;
-#pragma unroll
-                for (int p = 0; p < 9 * NS; ++p) S.box[p][bz][bx] = src[p * C.plane];
-            }
-            __syncthreads();
-        }
 
         // ---- phase A: this site's populations, rho and psi of the tile and its ring ----
         T f[NS][9];
@@ -245,7 +258,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
             S.next = tn;  // read by all after the barrier that ends this tile
             if (tn < ntiles) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                issue_load(S, &tin, (tn % ntx) * PX - 4, (tn / ntx) * PZ - 3);
+                issue_load(S, &tin, (tn % ntx) * PX, (tn / ntx) * PZ);
             }
         }
 
@@ -385,12 +398,26 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
             S.colsum[tz][QC_PXX][tx] = cpx;
         }
         __syncthreads();
-        if ((MODE & M_WRITE) && tid == 0) {
-            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
-                             &tout),
-                         "r"(x0), "r"(z0), "r"(0), "r"(smem_u32(&S.out[0][0][0]))
-                         : "memory");
-            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        if (MODE & M_WRITE) {
+            if (x0 + PX <= nx) {
+                if (tid == 0) {
+                    // padded column x0 + 4 is lattice column x0, padded row z0 + 3 is lattice row z0
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                            &tout),
+                        "r"(x0 + PULL_GX), "r"(z0 + PULL_GZ), "r"(0), "r"(smem_u32(&S.out[0][0][0]))
+                        : "memory");
+                    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                }
+            } else if (live) {
+                // the ragged last strip: the store's x bound is checked in 16-byte units, and the
+                // columns past nx are ghost columns written by the first strip -- plain stores
+                T* dst = fout + (long long)(z + PULL_GZ) * C.pitch + (x + PULL_GX);
+#pragma unroll
+                for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
+            }
+            if (live && (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= nz - PULL_GZ))))
+                write_images<T, NS>(S, C, fout, x, z, tx, tz);
         }
         if (MODE & M_OBS) {
             // per-column sums over the PZ rows of the tile
@@ -430,27 +457,44 @@ int pull_occupancy() {
 }
 
 template <typename T, int NS, int MODE>
-cudaError_t launch_mode(const void* tin, const void* tout, const T* fin, const StepConst<T>& C, const ObsPtrs& O,
+cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepConst<T>& C, const ObsPtrs& O,
                         const Fold& Rd, unsigned* sched, int grid_max, cudaStream_t st) {
     const int ntx = (C.nx + PX - 1) / PX, ntz = (C.nz + PZ - 1) / PZ;
     const long long ntiles = (long long)ntx * ntz;
     int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
     if (Rd.enabled && grid < 1) grid = 1;
     k_pull<T, NS, MODE><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS>), st>>>(
-        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fin, C, O, Rd, sched, ntx, ntz);
+        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, O, Rd, sched, ntx, ntz);
     return cudaGetLastError();
 }
 
 template <typename T, int NS>
-cudaError_t launch_ns(int mode, const void* tin, const void* tout, const T* fin, const StepConst<T>& C,
+cudaError_t launch_ns(int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
                       const ObsPtrs& O, const Fold& Rd, unsigned* sched, int grid_max, cudaStream_t st) {
     switch (mode) {
-        case M_WRITE: return launch_mode<T, NS, M_WRITE>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
+        case M_WRITE: return launch_mode<T, NS, M_WRITE>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
         case M_WRITE | M_OBS:
-            return launch_mode<T, NS, M_WRITE | M_OBS>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
-        case M_OBS: return launch_mode<T, NS, M_OBS>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
-        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(tin, tout, fin, C, O, Rd, sched, grid_max, st);
+            return launch_mode<T, NS, M_WRITE | M_OBS>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
+        case M_OBS: return launch_mode<T, NS, M_OBS>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
+        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+// Ghost columns and rows of a pull-layout buffer from the lattice (after the initial state).
+template <typename T>
+__global__ void k_images(int ns, T* __restrict__ f, const StepConst<T> C) {
+    const int wz = C.nz + 2 * PULL_GZ, wx = C.nx + 2 * PULL_GX;
+    const long long n = (long long)wz * wx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int gx = (int)(i % wx) - PULL_GX, gz = (int)(i / wx) - PULL_GZ;
+        const bool xin = gx >= 0 && gx < C.nx, zin = gz >= 0 && gz < C.nz;
+        if (xin && zin) continue;
+        if (!zin && C.zbc) continue;
+        const int sx = wrap_index(gx, C.nx), sz = wrap_index(gz, C.nz);
+        const long long src = (long long)(sz + PULL_GZ) * C.pitch + sx + PULL_GX;
+        const long long dst = (long long)(gz + PULL_GZ) * C.pitch + gx + PULL_GX;
+        for (int p = 0; p < 9 * ns; ++p) f[p * C.plane + dst] = f[p * C.plane + src];
     }
 }
 
@@ -477,28 +521,36 @@ int pull_blocks_per_sm(int ns, int mode) {
 }
 
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, const T* fin, const StepConst<T>& C,
+cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
                         const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st) {
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
-    return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fin, C, O, fold, sched, grid_max, st)
-                   : launch_ns<T, 2>(mode, tin, tout, fin, C, O, fold, sched, grid_max, st);
+    return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fout, C, O, fold, sched, grid_max, st)
+                   : launch_ns<T, 2>(mode, tin, tout, fout, C, O, fold, sched, grid_max, st);
+}
+
+template <typename T>
+cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, cudaStream_t st) {
+    k_images<T><<<256, 256, 0, st>>>(ns, f, C);
+    return cudaGetLastError();
 }
 
 int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int nz, int pitch,
                    long long plane) {
     const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!encode) return 1;
-    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)nz, (cuuint64_t)(9 * ns)};
+    // loads: the whole padded plane; stores: clipped at the lattice's last column and row
+    const cuuint64_t dims_in[3] = {(cuuint64_t)pitch, (cuuint64_t)(nz + 2 * PULL_GZ), (cuuint64_t)(9 * ns)};
+    const cuuint64_t dims_out[3] = {(cuuint64_t)(nx + PULL_GX), (cuuint64_t)(nz + PULL_GZ), (cuuint64_t)(9 * ns)};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
     const cuuint32_t box_in[3] = {(cuuint32_t)BX, (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
     const cuuint32_t box_out[3] = {(cuuint32_t)PX, (cuuint32_t)PZ, (cuuint32_t)(9 * ns)};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    CUresult r = encode(static_cast<CUtensorMap*>(in_map), dt, 3, const_cast<void*>(f), dims, strides, box_in, estr,
+    CUresult r = encode(static_cast<CUtensorMap*>(in_map), dt, 3, const_cast<void*>(f), dims_in, strides, box_in, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return 2;
-    r = encode(static_cast<CUtensorMap*>(out_map), dt, 3, const_cast<void*>(f), dims, strides, box_out, estr,
+    r = encode(static_cast<CUtensorMap*>(out_map), dt, 3, const_cast<void*>(f), dims_out, strides, box_out, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : 2;
@@ -506,9 +558,11 @@ int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns
 
 template int pull_blocks_per_sm<float>(int, int);
 template int pull_blocks_per_sm<double>(int, int);
-template cudaError_t launch_pull<float>(int, int, const void*, const void*, const float*, const StepConst<float>&,
+template cudaError_t launch_pull<float>(int, int, const void*, const void*, float*, const StepConst<float>&,
                                         const ObsPtrs&, const Fold&, unsigned*, int, cudaStream_t);
-template cudaError_t launch_pull<double>(int, int, const void*, const void*, const double*, const StepConst<double>&,
+template cudaError_t launch_pull<double>(int, int, const void*, const void*, double*, const StepConst<double>&,
                                          const ObsPtrs&, const Fold&, unsigned*, int, cudaStream_t);
+template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, cudaStream_t);
+template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, cudaStream_t);
 
 }  // namespace lbm
