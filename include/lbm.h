@@ -203,6 +203,16 @@ int lbm_abi_version(void);
 int lbm_observables_noalloc(const double *f, int nx, int nz, int n_species, int z_boundary,
                             const lbm_params *p, double *out, void *stream);
 
+/* Self-test of failure detection (no counterpart in the paper).  The step kernels' only
+   device-side waits are bounded waits on TMA copies; an expired wait sets a flag that the next
+   synchronising call reports as LBM_ETIMEOUT, and the kernel leaves without faulting.  This
+   runs the same bounded wait on a barrier that nothing completes, for `cycles` SM clock cycles
+   (1 <= cycles <= 4e9), on the context's stream, then synchronises.  Returns LBM_ETIMEOUT
+   (the expected result: the wait expired and was reported, the context stays usable), LBM_OK
+   (the wait did not expire: a defect), LBM_EINVAL or LBM_ECUDA.  The flag is cleared again so
+   that the context's later calls are unaffected. */
+int lbm_selftest_wait(lbm_ctx *c, long long cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -755,3 +755,21 @@ extern "C" int lbm_profile_read(lbm_ctx* c, double* ms, long long* n) {
 extern "C" const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 extern "C" int lbm_abi_version(void) { return LBM_ABI_VERSION; }
+
+extern "C" int lbm_selftest_wait(lbm_ctx* c, long long cycles) {
+    if (!c) return LBM_EINVAL;
+    if (cycles < 1 || cycles > 4000000000LL) return fail(c, LBM_EINVAL, "cycles out of range");
+    CK(cudaSetDevice(c->d.device));
+    int saved = 0;
+    CK(cudaMemcpyAsync(&saved, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(launch_wait_selftest(c->flag, cycles, c->stream));
+    c->launches += 1;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->flag, &saved, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (flag & 2) return fail(c, LBM_ETIMEOUT, "the self-test wait expired after %lld cycles (expected)", cycles);
+    return LBM_OK;
+}

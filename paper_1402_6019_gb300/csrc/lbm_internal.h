@@ -101,6 +101,8 @@ int pull_blocks_per_sm(int ns, int mode);
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
                         const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st);
+// One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.
+cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st);
 // Fills the ghost columns and rows of a pull-layout buffer with the periodic images.
 template <typename T>
 cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, cudaStream_t st);

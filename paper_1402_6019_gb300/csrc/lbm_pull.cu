@@ -40,7 +40,7 @@ constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3 
 constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2 (padded z0 .. z0 + PZ + 5)
 constexpr int HW = PX + 4, HH = PZ + 4;   // psi/rho tile: x0 - 2 .. x0 + PX + 1, z0 - 2 .. z0 + PZ + 1
 constexpr int NRING = HW * HH - PX * PZ;  // psi/rho tile positions outside the tile
-static_assert(NRING <= NT, "one ring position per thread at most");
+static_assert(NRING % PZ == 0 && NRING / PZ <= PX, "the ring shared evenly over the warps");
 static_assert(NT == RB_THREADS, "a CTA runs the reduction's work items");
 static_assert(PULL_GX == 4 && PULL_GZ == 3, "the box starts at padded (x0, z0)");
 
@@ -70,8 +70,10 @@ __device__ __forceinline__ void issue_load(PullSmem<T, NS>& S, const CUtensorMap
         : "memory");
 }
 
-// Bounded wait for the phase of the load barrier (about 1 s at 2 GHz); false on expiry.
-__device__ __forceinline__ bool wait_load(unsigned bar, unsigned parity) {
+// Bounded wait for the phase of a load barrier: false once `limit` clock cycles have passed
+// (the step kernel allows 2e9, about 1 s at 2 GHz).
+constexpr long long WAIT_LIMIT = 2000000000LL;
+__device__ __forceinline__ bool wait_load(unsigned bar, unsigned parity, long long limit = WAIT_LIMIT) {
     const long long t0 = clock64();
     for (;;) {
         unsigned done;
@@ -81,8 +83,17 @@ __device__ __forceinline__ bool wait_load(unsigned bar, unsigned parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// Self-test of the bounded wait: one thread waits on a barrier that no copy and no thread ever
+// completes, and records the expiry in flag bit 1 (as the step kernel does).
+__global__ void k_wait_selftest(int* flag, long long limit) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+    if (!wait_load(b, 0u, limit)) atomicOr(flag, 2);
 }
 
 // Post-streaming populations at box position (bx, bz): the gather of the pull layout.  lo / hi:
@@ -184,31 +195,38 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     const int ntiles = ntx * ntz;
     const unsigned bar = smem_u32(&S.bar);
 
-    // ring position of this thread (psi/rho tile coordinates): the top two rows, the bottom
-    // two rows, then two columns on each side of the tile rows
-    const bool ring = tid < NRING;
+    // ring position of this thread (psi/rho tile coordinates), NRING / PZ = 22 per warp so that
+    // every warp has the same phase-A work: in ring order the top two rows, the bottom two rows,
+    // then two columns on each side of the tile rows
+    const bool ring = tx < NRING / PZ;
     int rpx = 0, rpz = 0;
     if (ring) {
-        if (tid < 2 * HW) {
-            rpz = tid / HW;
-            rpx = tid % HW;
-        } else if (tid < 4 * HW) {
-            rpz = HH - 2 + (tid - 2 * HW) / HW;
-            rpx = (tid - 2 * HW) % HW;
+        const int k = tz * (NRING / PZ) + tx;
+        if (k < 2 * HW) {
+            rpz = k / HW;
+            rpx = k % HW;
+        } else if (k < 4 * HW) {
+            rpz = HH - 2 + (k - 2 * HW) / HW;
+            rpx = (k - 2 * HW) % HW;
         } else {
-            const int j = tid - 4 * HW;
+            const int j = k - 4 * HW;
             rpz = 2 + (j >> 2);
             const int c = j & 3;
             rpx = c < 2 ? c : HW - 4 + c;
         }
     }
+    // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden
+    int upcoming = 0;
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         const int t0 = (int)atomicAdd(&sched[0], 1u);
         S.next = t0;
-        if (t0 < ntiles) issue_load(S, &tin, (t0 % ntx) * PX, (t0 / ntx) * PZ);  // padded (x0, z0)
+        if (t0 < ntiles) {
+            issue_load(S, &tin, (t0 % ntx) * PX, (t0 / ntx) * PZ);  // padded (x0, z0)
+            upcoming = (int)atomicAdd(&sched[0], 1u);
+        }
     }
     __syncthreads();
     if (Rd.enabled) {  // the previous pass's reduction, under the first load
@@ -252,13 +270,15 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
             failed = true;
             break;
         }
-        // the box is free: draw this CTA's next tile and start its load
+        // the box is free: start the load of this CTA's next tile (drawn during the last tile)
+        // and draw the one after it
         if (tid == 0) {
-            const int tn = (int)atomicAdd(&sched[0], 1u);
+            const int tn = upcoming;
             S.next = tn;  // read by all after the barrier that ends this tile
             if (tn < ntiles) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 issue_load(S, &tin, (tn % ntx) * PX, (tn / ntx) * PZ);
+                upcoming = (int)atomicAdd(&sched[0], 1u);
             }
         }
 
@@ -526,6 +546,11 @@ cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* 
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
     return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fout, C, O, fold, sched, grid_max, st)
                    : launch_ns<T, 2>(mode, tin, tout, fout, C, O, fold, sched, grid_max, st);
+}
+
+cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
+    k_wait_selftest<<<1, 1, 0, st>>>(flag, cycles);
+    return cudaGetLastError();
 }
 
 template <typename T>

@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_abi_version": (ctypes.c_int, []),
     "lbm_observables_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(lbm_params), _VP, _VP]),
+    "lbm_selftest_wait": (ctypes.c_int, [_VP, ctypes.c_longlong]),
 }
 
 _lib = None
@@ -224,6 +225,12 @@ def lbm_observables_noalloc(f_dev_ptr, nx, nz, n_species, z_boundary, p: lbm_par
     (see include/lbm.h); returns the status code."""
     return load().lbm_observables_noalloc(ctypes.c_void_p(f_dev_ptr), nx, nz, n_species, z_boundary,
                                           ctypes.byref(p), ctypes.c_void_p(out_dev_ptr), ctypes.c_void_p(stream))
+
+
+def lbm_selftest_wait(h, cycles: int) -> int:
+    """Runs the step kernels' bounded wait on a barrier nothing completes; returns the status
+    (LBM_ETIMEOUT when the expiry was detected and reported, as intended)."""
+    return load().lbm_selftest_wait(h, ctypes.c_longlong(cycles))
 
 
 # ---- convenience ---------------------------------------------------------------------------
