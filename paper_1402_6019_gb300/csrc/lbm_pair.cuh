@@ -1,0 +1,186 @@
+// lbm_pair.cuh -- the per-site arithmetic of the two-species FP32 step with the species in
+// lockstep: a float2 holds (species A, species B), and Blackwell's packed FP32 instructions
+// (__ffma2_rn, __fadd2_rn, __fmul2_rn) do both species' work in one instruction.  Same formulas
+// as lbm_core.cuh (Eq. FORCE, the cross repulsion of Sec. IV, Appendix A's stresses, the shifted
+// equilibrium and BGK relaxation of Sec. II); only the grouping of the arithmetic differs.
+// Device-only.
+#pragma once
+
+#include "lbm_core.cuh"
+
+namespace lbm {
+
+using f2 = float2;
+
+__device__ __forceinline__ f2 p2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 sp(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 swap2(f2 a) { return make_float2(a.y, a.x); }
+
+// Constant tables of the step as (A, B) pairs, built on the host from StepConst<float>.
+struct PairConst {
+    f2 kx[25], kz[25];  // K_s(|c|^2) c of Eq. FORCE, index (dz + 2) * 5 + dx + 2
+    f2 sq[9];           // App. A shell prefactors by |c|^2
+    f2 omega, tau, rho_ref, nexp;  // nexp = -log2(e) / rho0 (psi = 1 - 2^(nexp rho))
+    f2 kin;             // (tau - 1/2)^2
+    f2 keep;            // 1 - omega
+    f2 half_om;         // 1 - omega / 2
+};
+
+// The pairs from the per-species tables (host).
+inline void fill_pair_const(PairConst& K, const StepConst<float>& C) {
+    for (int i = 0; i < 25; ++i) {
+        K.kx[i] = make_float2(C.kx[0][i], C.kx[1][i]);
+        K.kz[i] = make_float2(C.kz[0][i], C.kz[1][i]);
+    }
+    for (int q = 0; q < 9; ++q) K.sq[q] = make_float2(C.sq[0][q], C.sq[1][q]);
+    K.omega = make_float2(C.omega[0], C.omega[1]);
+    K.tau = make_float2(C.tau[0], C.tau[1]);
+    K.rho_ref = make_float2(C.rho_ref[0], C.rho_ref[1]);
+    const float log2e = 1.4426950408889634f;
+    K.nexp = make_float2(-log2e * C.inv_rho0[0], -log2e * C.inv_rho0[1]);
+    K.kin = make_float2(C.kin[0], C.kin[1]);
+    K.keep = make_float2(1.0f - C.omega[0], 1.0f - C.omega[1]);
+    K.half_om = make_float2(1.0f - 0.5f * C.omega[0], 1.0f - 0.5f * C.omega[1]);
+}
+
+// Pseudopotential of Sec. IV for both species: psi = 1 - exp(-rho / rho0) (hardware exp2), or
+// psi = rho.
+__device__ __forceinline__ f2 psi2(const StepConst<float>& C, const PairConst& K, f2 rho) {
+    if (C.psi_form == 1) return rho;
+    const f2 a = mul2(rho, K.nexp);
+    return p2(1.0f - exp2f(a.x), 1.0f - exp2f(a.y));
+}
+
+// Eq. FORCE for both species: F = -psi(x) sum_l K(|c_l|^2) psi(x + c_l) c_l.
+__device__ __forceinline__ void intra_force2(const PairConst& K, const f2 (&p)[5][5], f2& fx, f2& fz) {
+    f2 ax[5], az[5];
+#pragma unroll
+    for (int dz = -2; dz <= 2; ++dz) {
+        ax[dz + 2] = sp(0.f);
+        az[dz + 2] = sp(0.f);
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) {
+            if (dx == 0 && dz == 0) continue;
+            const int i = (dz + 2) * 5 + dx + 2;
+            if (dx != 0) ax[dz + 2] = fma2(K.kx[i], p[dz + 2][dx + 2], ax[dz + 2]);
+            if (dz != 0) az[dz + 2] = fma2(K.kz[i], p[dz + 2][dx + 2], az[dz + 2]);
+        }
+    }
+    const f2 sx = add2(add2(add2(ax[0], ax[4]), add2(ax[1], ax[3])), ax[2]);
+    const f2 sz = add2(add2(az[0], az[4]), add2(az[1], az[3]));
+    const f2 m = p2(-p[2][2].x, -p[2][2].y);
+    fx = mul2(m, sx);
+    fz = mul2(m, sz);
+}
+
+// Appendix A stresses of both species, returned as (A, B) pairs of (sxx, szz, sxz).
+__device__ __forceinline__ void intra_stress2(const PairConst& K, const f2 (&p)[5][5], f2& sxx, f2& szz, f2& sxz) {
+#define LBM_Q(dx, dz) p[(dz) + 2][(dx) + 2]
+    const f2 p0 = LBM_Q(0, 0);
+    const f2 four = sp(4.f), two = sp(2.f);
+    const f2 d2 = add2(LBM_Q(1, 1), LBM_Q(-1, -1)), a2 = add2(LBM_Q(-1, 1), LBM_Q(1, -1));
+    const f2 da = add2(d2, a2);
+    const f2 n12x = fma2(K.sq[1], add2(LBM_Q(1, 0), LBM_Q(-1, 0)), mul2(K.sq[2], da));
+    const f2 n12z = fma2(K.sq[1], add2(LBM_Q(0, 1), LBM_Q(0, -1)), mul2(K.sq[2], da));
+    const f2 n12xz = mul2(K.sq[2], sub2(d2, a2));
+    const f2 q4 = mul2(four, K.sq[4]);
+    const f2 s4x = mul2(q4, fma2(p0, add2(LBM_Q(2, 0), LBM_Q(-2, 0)), mul2(two, mul2(LBM_Q(-1, 0), LBM_Q(1, 0)))));
+    const f2 s4z = mul2(q4, fma2(p0, add2(LBM_Q(0, 2), LBM_Q(0, -2)), mul2(two, mul2(LBM_Q(0, -1), LBM_Q(0, 1)))));
+    const f2 a21 = add2(LBM_Q(2, 1), LBM_Q(-2, -1)), b21 = add2(LBM_Q(-2, 1), LBM_Q(2, -1));
+    const f2 a12 = add2(LBM_Q(1, 2), LBM_Q(-1, -2)), b12 = add2(LBM_Q(-1, 2), LBM_Q(1, -2));
+    const f2 t13 = fma2(LBM_Q(1, 1), LBM_Q(-1, 0), mul2(LBM_Q(1, 0), LBM_Q(-1, -1)));
+    const f2 t14 = fma2(LBM_Q(1, 1), LBM_Q(0, -1), mul2(LBM_Q(0, 1), LBM_Q(-1, -1)));
+    const f2 t15 = fma2(LBM_Q(0, 1), LBM_Q(1, -1), mul2(LBM_Q(-1, 1), LBM_Q(0, -1)));
+    const f2 t16 = fma2(LBM_Q(-1, 1), LBM_Q(1, 0), mul2(LBM_Q(-1, 0), LBM_Q(1, -1)));
+    const f2 s21 = add2(a21, b21), s12 = add2(a12, b12);
+    const f2 t1316 = add2(t13, t16), t1415 = add2(t14, t15);
+    const f2 s5x = mul2(K.sq[5], add2(mul2(p0, fma2(four, s21, s12)), fma2(four, t1316, t1415)));
+    const f2 s5z = mul2(K.sq[5], add2(mul2(p0, fma2(four, s12, s21)), fma2(four, t1415, t1316)));
+    const f2 s5xz = mul2(K.sq[5], mul2(two, add2(mul2(p0, add2(sub2(a21, b21), sub2(a12, b12))),
+                                               sub2(add2(t13, t14), add2(t15, t16)))));
+    const f2 a22 = add2(LBM_Q(2, 2), LBM_Q(-2, -2)), b22 = add2(LBM_Q(-2, 2), LBM_Q(2, -2));
+    const f2 ha = mul2(two, mul2(LBM_Q(-1, -1), LBM_Q(1, 1))), hb = mul2(two, mul2(LBM_Q(-1, 1), LBM_Q(1, -1)));
+    const f2 q8 = mul2(four, K.sq[8]);
+    const f2 s8 = mul2(q8, fma2(p0, add2(a22, b22), add2(ha, hb)));
+    const f2 s8xz = mul2(q8, fma2(p0, sub2(a22, b22), sub2(ha, hb)));
+    sxx = add2(fma2(p0, n12x, s4x), add2(s5x, s8));
+    szz = add2(fma2(p0, n12z, s4z), add2(s5z, s8));
+    sxz = add2(fma2(p0, n12xz, s5xz), s8xz);
+#undef LBM_Q
+}
+
+// Sec. IV cross repulsion for both species (first belt, rho as the cross pseudopotential):
+// F_A += -G_AB rho_A(x) sum_l w8 rho_B(x + c_l) c_l, and A <-> B.  r[dz+1][dx+1] = (rho_A, rho_B).
+__device__ __forceinline__ void cross_force2(const StepConst<float>& C, const f2 (&r)[3][3], f2& fx, f2& fz) {
+    f2 sx = sp(0.f), sz = sp(0.f);
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dz == 0) continue;
+            const int i = (dz + 1) * 3 + dx + 1;
+            if (dx != 0) sx = fma2(sp(C.kcx[i]), r[dz + 1][dx + 1], sx);
+            if (dz != 0) sz = fma2(sp(C.kcz[i]), r[dz + 1][dx + 1], sz);
+        }
+    // species A takes the sums over rho_B, species B those over rho_A
+    const f2 m = p2(-r[1][1].x, -r[1][1].y);
+    fx = fma2(m, swap2(sx), fx);
+    fz = fma2(m, swap2(sz), fz);
+}
+
+// Cross-species stress (the pair product psi(x) psi(x + c) read as rho_A(x) rho_B(x + c) +
+// rho_B(x) rho_A(x + c)); returns the sums into scalars.
+__device__ __forceinline__ void cross_stress2(const StepConst<float>& C, const f2 (&r)[3][3], float& sxx, float& szz,
+                                              float& sxz) {
+    const f2 ba = swap2(r[1][1]);  // (rho_B(x), rho_A(x)): phi(c) = ba . r(c)
+    const f2 e1x = mul2(ba, add2(r[1][2], r[1][0]));
+    const f2 e1z = mul2(ba, add2(r[2][1], r[0][1]));
+    const f2 ed = mul2(ba, add2(r[2][2], r[0][0]));
+    const f2 ea = mul2(ba, add2(r[2][0], r[0][2]));
+    const float s1x = e1x.x + e1x.y, s1z = e1z.x + e1z.y, d = ed.x + ed.y, a = ea.x + ea.y;
+    sxx += C.sc[1] * s1x + C.sc[2] * (d + a);
+    szz += C.sc[1] * s1z + C.sc[2] * (d + a);
+    sxz += C.sc[2] * (d - a);
+}
+
+__device__ __forceinline__ f2 sum9_2(const f2 (&f)[9]) {
+    return add2(add2(add2(f[0], f[1]), add2(f[2], f[3])), add2(add2(add2(f[4], f[5]), add2(f[6], f[7])), f[8]));
+}
+__device__ __forceinline__ void momentum9_2(const f2 (&f)[9], f2& jx, f2& jz) {
+    jx = add2(add2(sub2(f[1], f[3]), sub2(f[5], f[6])), sub2(f[8], f[7]));
+    jz = add2(add2(sub2(f[2], f[4]), sub2(f[5], f[7])), sub2(f[6], f[8]));
+}
+
+// Shifted-velocity BGK collision of both species (Eq. LB, Sec. II), f overwritten with
+// (1 - omega) f + omega feq; omega folded into the equilibrium's coefficients and the pair
+// structure of D2Q9 used as in lbm_core.cuh's collide.
+__device__ __forceinline__ void collide2(const PairConst& K, f2 (&f)[9], f2 drho, f2 rho, f2 ir, f2 jx, f2 jz, f2 Fx,
+                                         f2 Fz) {
+    const f2 wj = mul2(K.omega, jx), wk = mul2(K.omega, jz), wr = mul2(K.omega, rho);
+    const float iden = __fdividef(1.0f, wr.x + wr.y);
+    const f2 up = sp((wj.x + wj.y) * iden), vp = sp((wk.x + wk.y) * iden);
+    const f2 tir = mul2(K.tau, ir);
+    const f2 ux = fma2(Fx, tir, up);
+    const f2 uz = fma2(Fz, tir, vp);
+    const f2 u15 = mul2(sp(1.5f), fma2(ux, ux, mul2(uz, uz)));
+    const f2 b = mul2(K.omega, rho);
+    const f2 base = sub2(mul2(K.omega, drho), mul2(b, u15));  // omega (drho - 3/2 rho u^2)
+    const f2 e1 = mul2(base, sp(1.0f / 9.0f)), c1 = mul2(b, sp(0.5f)), d1 = mul2(b, sp(1.0f / 3.0f));
+    const f2 e2 = mul2(base, sp(1.0f / 36.0f)), c2 = mul2(b, sp(0.125f)), d2 = mul2(b, sp(1.0f / 12.0f));
+    f[0] = fma2(f[0], K.keep, mul2(base, sp(4.0f / 9.0f)));
+    const f2 cu[4] = {ux, uz, add2(ux, uz), sub2(uz, ux)};  // pairs (1,3), (2,4), (5,7), (6,8)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const f2 even = k < 2 ? fma2(mul2(c1, cu[k]), cu[k], e1) : fma2(mul2(c2, cu[k]), cu[k], e2);
+        const f2 odd = mul2(k < 2 ? d1 : d2, cu[k]);
+        const int lp = k < 2 ? k + 1 : k + 3;
+        f[lp] = add2(fma2(f[lp], K.keep, even), odd);
+        f[opp(lp)] = sub2(fma2(f[opp(lp)], K.keep, even), odd);
+    }
+}
+
+}  // namespace lbm

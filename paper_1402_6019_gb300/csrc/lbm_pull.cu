@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "lbm_pair.cuh"
 #include "lbm_reduce.cuh"
 
 namespace lbm {
@@ -40,32 +41,48 @@ constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3 
 constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2 (padded z0 .. z0 + PZ + 5)
 constexpr int HW = PX + 4, HH = PZ + 4;   // psi/rho tile: x0 - 2 .. x0 + PX + 1, z0 - 2 .. z0 + PZ + 1
 constexpr int NRING = HW * HH - PX * PZ;  // psi/rho tile positions outside the tile
+constexpr int STAGES = 2;                 // boxes in flight per CTA: tiles are loaded two ahead
 static_assert(NRING % PZ == 0 && NRING / PZ <= PX, "the ring shared evenly over the warps");
 static_assert(NT == RB_THREADS, "a CTA runs the reduction's work items");
 static_assert(PULL_GX == 4 && PULL_GZ == 3, "the box starts at padded (x0, z0)");
 
+// Two species in FP32: the species go through the per-site arithmetic in lockstep (lbm_pair.cuh).
+template <typename T, int NS>
+constexpr bool kPair = sizeof(T) == 4 && NS == 2;
+
+// psi and rho of the tile and its 2-cell ring: per species, or (species A, B) pairs
+template <typename T, int NS, bool PAIR = kPair<T, NS>>
+struct PsiTile {
+    T ps[NS][HH][HW];
+    T rh[NS][HH][HW];
+};
+template <>
+struct PsiTile<float, 2, true> {
+    f2 ps[HH][HW];
+    f2 rh[HH][HW];
+};
+
 template <typename T, int NS>
 struct PullSmem {
-    T box[9 * NS][BZ][BX];             // TMA destination (box column bx = x - x0 + 4, row bz = z - z0 + 3)
+    T box[STAGES][9 * NS][BZ][BX];     // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
     alignas(128) T out[9 * NS][PZ][PX];  // TMA source: the tile's new stored values
-    T ps[NS][HH][HW];                  // psi and rho of the tile and its 2-cell ring
-    T rh[NS][HH][HW];
+    PsiTile<T, NS> q;
     T colsum[PZ][NQC][PX];
     typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
-    alignas(8) unsigned long long bar;
-    int next;  // the CTA's next tile
+    alignas(8) unsigned long long bar[STAGES];
+    int tile[STAGES];  // the tile each box holds (or is loading)
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 template <typename T, int NS>
-__device__ __forceinline__ void issue_load(PullSmem<T, NS>& S, const CUtensorMap* map, int x, int z) {
+__device__ __forceinline__ void issue_load(PullSmem<T, NS>& S, const CUtensorMap* map, int x, int z, int sl) {
     constexpr unsigned bytes = (unsigned)(sizeof(T) * 9 * NS * BZ * BX);
-    const unsigned bar = smem_u32(&S.bar);
+    const unsigned bar = smem_u32(&S.bar[sl]);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(smem_u32(&S.box[0][0][0])),
+        "[%5];\n" ::"r"(smem_u32(&S.box[sl][0][0][0])),
         "l"(map), "r"(x), "r"(z), "r"(0), "r"(bar)
         : "memory");
 }
@@ -100,21 +117,21 @@ __global__ void k_wait_selftest(int* flag, long long limit) {
 // the site is the bottom / top row next to a wall, where populations coming from beyond the
 // wall are the site's own reflected values.
 template <typename T, int NS>
-__device__ __forceinline__ void gather(const PullSmem<T, NS>& S, int bx, int bz, T (&f)[NS][9]) {
+__device__ __forceinline__ void gather(const PullSmem<T, NS>& S, int sl, int bx, int bz, T (&f)[NS][9]) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
-        for (int l = 0; l < 9; ++l) f[s][l] = S.box[s * 9 + l][bz - cz(l)][bx - cx(l)];
+        for (int l = 0; l < 9; ++l) f[s][l] = S.box[sl][s * 9 + l][bz - cz(l)][bx - cx(l)];
 }
 template <typename T, int NS>
-__device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int bx, int bz, bool lo, bool hi,
+__device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int sl, int bx, int bz, bool lo, bool hi,
                                             T (&f)[NS][9]) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int l = 0; l < 9; ++l) {
             const bool refl = (cz(l) > 0 && lo) || (cz(l) < 0 && hi);
-            f[s][l] = refl ? S.box[s * 9 + opp(l)][bz][bx] : S.box[s * 9 + l][bz - cz(l)][bx - cx(l)];
+            f[s][l] = refl ? S.box[sl][s * 9 + opp(l)][bz][bx] : S.box[sl][s * 9 + l][bz - cz(l)][bx - cx(l)];
         }
 }
 
@@ -123,7 +140,8 @@ __device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int bx, in
 // mirror image (or zero, Sec. IV's two readings of the ghost rows).  Positions that no live
 // site reads (far padding of ragged tiles) are set to zero.
 template <typename T, int NS>
-__device__ __forceinline__ void side_density(PullSmem<T, NS>& S, const StepConst<T>& C, int px, int pz, int z0) {
+__device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const StepConst<T>& C, const PairConst& K,
+                                             int px, int pz, int z0) {
     const int Z = z0 - 2 + pz;
     int Zs = Z;
     bool zero = false;
@@ -135,24 +153,30 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, const StepConst
     }
     const int bz = Zs - z0 + 3, bx = px + 2;
     if (bz < 1 || bz > BZ - 2) zero = true;
-    T r[NS];
+    T sum[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) r[s] = T(0);
+    for (int s = 0; s < NS; ++s) sum[s] = T(0);
     if (!zero) {
         T g[NS][9];
         const bool lo = C.zbc && Zs == 0, hi = C.zbc && Zs == C.nz - 1;
         if (lo || hi)
-            gather_wall<T, NS>(S, bx, bz, lo, hi, g);
+            gather_wall<T, NS>(S, sl, bx, bz, lo, hi, g);
         else
-            gather<T, NS>(S, bx, bz, g);
+            gather<T, NS>(S, sl, bx, bz, g);
 #pragma unroll
-        for (int s = 0; s < NS; ++s) r[s] = sum9(g[s]);
+        for (int s = 0; s < NS; ++s) sum[s] = sum9(g[s]);
     }
+    if constexpr (kPair<T, NS>) {
+        const f2 rho = add2(K.rho_ref, p2(sum[0], sum[1]));
+        S.q.rh[pz][px] = zero ? sp(0.f) : rho;
+        S.q.ps[pz][px] = zero ? sp(0.f) : psi2(C, K, rho);
+    } else {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        const T rho = C.rho_ref[s] + r[s];
-        S.rh[s][pz][px] = zero ? T(0) : rho;
-        S.ps[s][pz][px] = zero ? T(0) : psi_of(C, s, rho);
+        for (int s = 0; s < NS; ++s) {
+            const T rho = C.rho_ref[s] + sum[s];
+            S.q.rh[s][pz][px] = zero ? T(0) : rho;
+            S.q.ps[s][pz][px] = zero ? T(0) : psi_of(C, s, rho);
+        }
     }
 }
 
@@ -185,15 +209,15 @@ __device__ __noinline__ void write_images(const PullSmem<T, NS>& S, const StepCo
 }
 
 template <typename T, int NS, int MODE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, T* __restrict__ fout,
-           const StepConst<T> C, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched, int ntx, int ntz) {
+           const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
+           int ntx, int ntz) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PullSmem<T, NS>& S = *reinterpret_cast<PullSmem<T, NS>*>(smem_raw);
     const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
     const int nx = C.nx, nz = C.nz;
     const int ntiles = ntx * ntz;
-    const unsigned bar = smem_u32(&S.bar);
 
     // ring position of this thread (psi/rho tile coordinates), NRING / PZ = 22 per warp so that
     // every warp has the same phase-A work: in ring order the top two rows, the bottom two rows,
@@ -219,14 +243,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     int upcoming = 0;
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        for (int sl = 0; sl < STAGES; ++sl)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.bar[sl])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        const int t0 = (int)atomicAdd(&sched[0], 1u);
-        S.next = t0;
-        if (t0 < ntiles) {
-            issue_load(S, &tin, (t0 % ntx) * PX, (t0 / ntx) * PZ);  // padded (x0, z0)
-            upcoming = (int)atomicAdd(&sched[0], 1u);
+        // the first STAGES tiles go into the boxes at once (padded (x0, z0) is the box origin)
+        bool more = true;
+        for (int sl = 0; sl < STAGES; ++sl) {
+            const int t0 = more ? (int)atomicAdd(&sched[0], 1u) : ntiles;
+            S.tile[sl] = t0;
+            more = t0 < ntiles;
+            if (more) issue_load(S, &tin, (t0 % ntx) * PX, (t0 / ntx) * PZ, sl);
         }
+        if (more) upcoming = (int)atomicAdd(&sched[0], 1u);
     }
     __syncthreads();
     if (Rd.enabled) {  // the previous pass's reduction, under the first load
@@ -236,14 +264,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
             reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
                             Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc);
     }
-    int t = S.next;
-    unsigned parity = 0;
+    unsigned parity = 0;  // bit sl: phase of box sl's barrier
     bool failed = false;
-    for (; t < ntiles; t = S.next, parity ^= 1u) {
+    for (int k = 0;; ++k) {
+        const int sl = k % STAGES;
+        const int t = S.tile[sl];
+        if (t >= ntiles) break;
         const int x0 = (t % ntx) * PX, z0 = (t / ntx) * PZ;
         const int x = x0 + tx, z = z0 + tz;
         const bool live = x < nx && z < nz;
-        const bool ok = wait_load(bar, parity);
+        const bool ok = wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
+        if (ok) parity ^= 1u << sl;  // on expiry the exit path waits on the same phase again
 
         // ---- phase A: this site's populations, rho and psi of the tile and its ring ----
         T f[NS][9];
@@ -251,140 +282,236 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         if (live) {
             const bool lo = C.zbc && z == 0, hi = C.zbc && z == nz - 1;
             if (lo || hi)
-                gather_wall<T, NS>(S, tx + 4, tz + 3, lo, hi, f);
+                gather_wall<T, NS>(S, sl, tx + 4, tz + 3, lo, hi, f);
             else
-                gather<T, NS>(S, tx + 4, tz + 3, f);
+                gather<T, NS>(S, sl, tx + 4, tz + 3, f);
+            if constexpr (kPair<T, NS>) {
+                f2 fp[9];
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                drho[s] = sum9(f[s]);
-                const T r = C.rho_ref[s] + drho[s];
-                S.rh[s][tz + 2][tx + 2] = r;
-                S.ps[s][tz + 2][tx + 2] = psi_of(C, s, r);
+                for (int l = 0; l < 9; ++l) fp[l] = p2(f[0][l], f[1][l]);
+                const f2 d = sum9_2(fp);
+                drho[0] = d.x;
+                drho[NS - 1] = d.y;
+                const f2 r = add2(K.rho_ref, d);
+                S.q.rh[tz + 2][tx + 2] = r;
+                S.q.ps[tz + 2][tx + 2] = psi2(C, K, r);
+            } else {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    drho[s] = sum9(f[s]);
+                    const T r = C.rho_ref[s] + drho[s];
+                    S.q.rh[s][tz + 2][tx + 2] = r;
+                    S.q.ps[s][tz + 2][tx + 2] = psi_of(C, s, r);
+                }
             }
         } else {
-            side_density<T, NS>(S, C, tx + 2, tz + 2, z0);
+            side_density<T, NS>(S, sl, C, K, tx + 2, tz + 2, z0);
         }
-        if (ring) side_density<T, NS>(S, C, rpx, rpz, z0);
+        if (ring) side_density<T, NS>(S, sl, C, K, rpx, rpz, z0);
         if ((MODE & M_WRITE) && tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
-        // the box is free: start the load of this CTA's next tile (drawn during the last tile)
+        // box sl is free: start the load of the tile STAGES ahead (drawn during the last tile)
         // and draw the one after it
         if (tid == 0) {
             const int tn = upcoming;
-            S.next = tn;  // read by all after the barrier that ends this tile
+            S.tile[sl] = tn;  // read by all after the barrier that ends tile k + STAGES - 1
             if (tn < ntiles) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                issue_load(S, &tin, (tn % ntx) * PX, (tn / ntx) * PZ);
+                issue_load(S, &tin, (tn % ntx) * PX, (tn / ntx) * PZ, sl);
                 upcoming = (int)atomicAdd(&sched[0], 1u);
             }
         }
 
         // ---- phase B: interaction, collision, new stored values, observables ----
-        T F[NS][2];
-        T sxx = T(0), szz = T(0), sxz = T(0);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            T p[5][5];
-#pragma unroll
-            for (int dz = 0; dz < 5; ++dz)
-#pragma unroll
-                for (int dx = 0; dx < 5; ++dx) p[dz][dx] = S.ps[s][tz + dz][tx + dx];
-            intra_force(C, s, p, F[s][0], F[s][1]);
-            if (MODE & M_OBS) intra_stress(C, s, p, sxx, szz, sxz);
-        }
-        if constexpr (NS == 2) {
-            T ra[3][3], rb[3][3];
-#pragma unroll
-            for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    ra[dz][dx] = S.rh[0][tz + 1 + dz][tx + 1 + dx];
-                    rb[dz][dx] = S.rh[1][tz + 1 + dz][tx + 1 + dx];
-                }
-            cross_force(C, ra, rb, F);
-            if (MODE & M_OBS) cross_stress(C, ra, rb, sxx, szz, sxz);
-        }
-
         T rowq[NQR];
 #pragma unroll
         for (int k = 0; k < NQR; ++k) rowq[k] = T(0);
         T cps = T(0), cpx = T(0);
         int bad = 0;
-        if (live) {
-            T rho[NS], ir[NS], jx[NS], jz[NS];
+        bool collided = false;  // f holds the post-collision values of a live site
+        T rho[NS];
+        if constexpr (kPair<T, NS>) {
+            f2 p[5][5];
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                rho[s] = C.rho_ref[s] + drho[s];
-                if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = 1;
-                ir[s] = div_(T(1), rho[s]);
-                momentum9(f[s], jx[s], jz[s]);
-                F[s][0] += rho[s] * C.g;
+            for (int dz = 0; dz < 5; ++dz)
+#pragma unroll
+                for (int dx = 0; dx < 5; ++dx) p[dz][dx] = S.q.ps[tz + dz][tx + dx];
+            f2 Fx, Fz;
+            intra_force2(K, p, Fx, Fz);
+            float sxx = 0.f, szz = 0.f, sxz = 0.f;
+            if (MODE & M_OBS) {
+                f2 a2, b2, c2;
+                intra_stress2(K, p, a2, b2, c2);
+                sxx = a2.x + a2.y;
+                szz = b2.x + b2.y;
+                sxz = c2.x + c2.y;
             }
-            if (MODE & (M_OBS | M_FIELDS)) {
-                T ux, uz, pixz, rtot, mx, mz;
-                site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
-                if (MODE & M_FIELDS) {
-                    const long long i = (long long)z * nx + x;
-                    const long long np = (long long)nx * nz;
+            f2 r[3][3];
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) O.fields[s * np + i] = (double)rho[s];
-                    O.fields[NS * np + i] = (double)ux;
-                    O.fields[(NS + 1) * np + i] = (double)uz;
-                }
-                if (MODE & M_OBS) {
-                    T pxx = sxx, pzz = szz;
+            for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) {
-                        pxx += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][0] * F[s][0] * ir[s];
-                        pzz += rho[s] * T(1.0 / 3.0) + C.kin[s] * F[s][1] * F[s][1] * ir[s];
+                for (int dx = 0; dx < 3; ++dx) r[dz][dx] = S.q.rh[tz + 1 + dz][tx + 1 + dx];
+            cross_force2(C, r, Fx, Fz);
+            if (MODE & M_OBS) cross_stress2(C, r, sxx, szz, sxz);
+            if (live) {
+                f2 fp[9];
+#pragma unroll
+                for (int l = 0; l < 9; ++l) fp[l] = p2(f[0][l], f[1][l]);
+                const f2 dr = p2(drho[0], drho[1]);
+                const f2 rh = add2(K.rho_ref, dr);
+                rho[0] = rh.x;
+                rho[1] = rh.y;
+                if (!(rh.x > 0.f) || !(rh.x < 1e30f) || !(rh.y > 0.f) || !(rh.y < 1e30f)) bad = 1;
+                const f2 ir = p2(__fdividef(1.f, rh.x), __fdividef(1.f, rh.y));
+                f2 jx, jz;
+                momentum9_2(fp, jx, jz);
+                Fx = fma2(rh, sp(C.g), Fx);
+                if (MODE & (M_OBS | M_FIELDS)) {
+                    // barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s and the kinetic flux
+                    const f2 m = fma2(Fx, sp(0.5f), jx), n = fma2(Fz, sp(0.5f), jz);
+                    const float mx = m.x + m.y, mz = n.x + n.y, rtot = rh.x + rh.y;
+                    const float irt = __fdividef(1.f, rtot);
+                    const float ux = mx * irt, uz = mz * irt, uxz = ux * uz;
+                    if (MODE & M_FIELDS) {
+                        const long long i = (long long)z * nx + x;
+                        const long long np = (long long)nx * nz;
+                        O.fields[i] = (double)rh.x;
+                        O.fields[np + i] = (double)rh.y;
+                        O.fields[2 * np + i] = (double)ux;
+                        O.fields[3 * np + i] = (double)uz;
                     }
-                    cps = pxx - pzz;
-                    cpx = pxx;
-                    rowq[QR_UX] = ux;
-                    rowq[QR_RHOA] = rho[0];
-                    rowq[QR_RHOB] = NS == 2 ? rho[NS - 1] : T(0);
-                    rowq[QR_SXZ] = -pixz - sxz;
-                    rowq[QR_MX] = mx;
-                    rowq[QR_MZ] = mz;
+                    if (MODE & M_OBS) {
+                        const f2 mm = sub2(sub2(add2(fp[5], fp[7]), add2(fp[6], fp[8])), mul2(rh, sp(uxz)));
+                        const f2 v = mul2(K.half_om, mm);
+                        const float pixz = (v.x + v.y) + rtot * uxz;
+                        const f2 third = mul2(rh, sp(1.f / 3.f));
+                        const f2 kx2 = fma2(mul2(K.kin, mul2(Fx, Fx)), ir, third);
+                        const f2 kz2 = fma2(mul2(K.kin, mul2(Fz, Fz)), ir, third);
+                        const float pxx = sxx + (kx2.x + kx2.y), pzz = szz + (kz2.x + kz2.y);
+                        cps = pxx - pzz;
+                        cpx = pxx;
+                        rowq[QR_UX] = ux;
+                        rowq[QR_RHOA] = rh.x;
+                        rowq[QR_RHOB] = rh.y;
+                        rowq[QR_SXZ] = -pixz - sxz;
+                        rowq[QR_MX] = mx;
+                        rowq[QR_MZ] = mz;
+                    }
                 }
-            }
-            if (MODE & (M_WRITE | M_OBS)) {
                 const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
-                if ((MODE & M_WRITE) || wall_row) {
-                    collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
-                    if (!wall_row) {  // warp-uniform
-                        if (MODE & M_WRITE) {
+                if ((MODE & M_WRITE) || ((MODE & M_OBS) && wall_row)) {
+                    collide2(K, fp, dr, rh, ir, jx, jz, Fx, Fz);
 #pragma unroll
-                            for (int s = 0; s < NS; ++s)
+                    for (int l = 0; l < 9; ++l) {
+                        f[0][l] = fp[l].x;
+                        f[NS - 1][l] = fp[l].y;
+                    }
+                    collided = true;
+                }
+            }
+        } else {
+            T F[NS][2];
+            T sxx = T(0), szz = T(0), sxz = T(0);
 #pragma unroll
-                                for (int l = 0; l < 9; ++l) S.out[s * 9 + l][tz][tx] = f[s][l];
+            for (int s2 = 0; s2 < NS; ++s2) {
+                T p[5][5];
+#pragma unroll
+                for (int dz = 0; dz < 5; ++dz)
+#pragma unroll
+                    for (int dx = 0; dx < 5; ++dx) p[dz][dx] = S.q.ps[s2][tz + dz][tx + dx];
+                intra_force(C, s2, p, F[s2][0], F[s2][1]);
+                if (MODE & M_OBS) intra_stress(C, s2, p, sxx, szz, sxz);
+            }
+            if constexpr (NS == 2) {
+                T ra[3][3], rb[3][3];
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        ra[dz][dx] = S.q.rh[0][tz + 1 + dz][tx + 1 + dx];
+                        rb[dz][dx] = S.q.rh[1][tz + 1 + dz][tx + 1 + dx];
+                    }
+                cross_force(C, ra, rb, F);
+                if (MODE & M_OBS) cross_stress(C, ra, rb, sxx, szz, sxz);
+            }
+            if (live) {
+                T ir[NS], jx[NS], jz[NS];
+#pragma unroll
+                for (int s2 = 0; s2 < NS; ++s2) {
+                    rho[s2] = C.rho_ref[s2] + drho[s2];
+                    if (!(rho[s2] > T(0)) || !(rho[s2] < T(1e30))) bad = 1;
+                    ir[s2] = div_(T(1), rho[s2]);
+                    momentum9(f[s2], jx[s2], jz[s2]);
+                    F[s2][0] += rho[s2] * C.g;
+                }
+                if (MODE & (M_OBS | M_FIELDS)) {
+                    T ux, uz, pixz, rtot, mx, mz;
+                    site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
+                    if (MODE & M_FIELDS) {
+                        const long long i = (long long)z * nx + x;
+                        const long long np = (long long)nx * nz;
+#pragma unroll
+                        for (int s2 = 0; s2 < NS; ++s2) O.fields[s2 * np + i] = (double)rho[s2];
+                        O.fields[NS * np + i] = (double)ux;
+                        O.fields[(NS + 1) * np + i] = (double)uz;
+                    }
+                    if (MODE & M_OBS) {
+                        T pxx = sxx, pzz = szz;
+#pragma unroll
+                        for (int s2 = 0; s2 < NS; ++s2) {
+                            pxx += rho[s2] * T(1.0 / 3.0) + C.kin[s2] * F[s2][0] * F[s2][0] * ir[s2];
+                            pzz += rho[s2] * T(1.0 / 3.0) + C.kin[s2] * F[s2][1] * F[s2][1] * ir[s2];
                         }
-                    } else {
-#pragma unroll
-                        for (int s = 0; s < NS; ++s)
-#pragma unroll
-                            for (int l = 0; l < 9; ++l) {
-                                const int zd = z + cz(l);
-                                T v = f[s][l];
-                                if (zd < 0 || zd >= nz) {  // leaves through a wall: store it reflected
-                                    const int w = zd < 0 ? 0 : 1;
-                                    const T back = bounce<T>(l, f[s][l], rho[s], C.wall_u[w]);
-                                    v = back;
-                                    if (MODE & M_OBS) {
-                                        const T dm = T(cx(l)) * (f[s][l] + back);
-                                        if (w == 0)
-                                            rowq[QR_WALLB] += dm;
-                                        else
-                                            rowq[QR_WALLT] += dm;
-                                    }
-                                }
-                                if (MODE & M_WRITE) S.out[s * 9 + l][tz][tx] = v;
-                            }
+                        cps = pxx - pzz;
+                        cpx = pxx;
+                        rowq[QR_UX] = ux;
+                        rowq[QR_RHOA] = rho[0];
+                        rowq[QR_RHOB] = NS == 2 ? rho[NS - 1] : T(0);
+                        rowq[QR_SXZ] = -pixz - sxz;
+                        rowq[QR_MX] = mx;
+                        rowq[QR_MZ] = mz;
                     }
                 }
+                const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+                if ((MODE & M_WRITE) || ((MODE & M_OBS) && wall_row)) {
+                    collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
+                    collided = true;
+                }
+            }
+        }
+        if (collided) {  // new stored values; with walls the populations leaving through a wall reflected
+            const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+            if (!wall_row) {  // warp-uniform
+                if (MODE & M_WRITE) {
+#pragma unroll
+                    for (int s2 = 0; s2 < NS; ++s2)
+#pragma unroll
+                        for (int l = 0; l < 9; ++l) S.out[s2 * 9 + l][tz][tx] = f[s2][l];
+                }
+            } else {
+#pragma unroll
+                for (int s2 = 0; s2 < NS; ++s2)
+#pragma unroll
+                    for (int l = 0; l < 9; ++l) {
+                        const int zd = z + cz(l);
+                        T v = f[s2][l];
+                        if (zd < 0 || zd >= nz) {  // leaves through a wall: store it reflected
+                            const int w = zd < 0 ? 0 : 1;
+                            const T back = bounce<T>(l, f[s2][l], rho[s2], C.wall_u[w]);
+                            v = back;
+                            if (MODE & M_OBS) {
+                                const T dm = T(cx(l)) * (f[s2][l] + back);
+                                if (w == 0)
+                                    rowq[QR_WALLB] += dm;
+                                else
+                                    rowq[QR_WALLT] += dm;
+                            }
+                        }
+                        if (MODE & M_WRITE) S.out[s2 * 9 + l][tz][tx] = v;
+                    }
             }
         }
         if (__any_sync(FULL, bad) && tx == 0) atomicOr(O.flag, 1);
@@ -452,7 +579,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     if (tid == 0) {
         if (failed) {
             atomicOr(O.flag, 2);
-            wait_load(bar, parity);  // the load that did not arrive in time, before the CTA exits
+            // loads still in flight (the one that did not arrive in time, the one after it) before
+            // the CTA exits
+            for (int sl = 0; sl < STAGES; ++sl)
+                if (S.tile[sl] < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
         }
         asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
         // the last CTA out resets the scheduler for the next launch (every CTA's draws on
@@ -483,8 +613,11 @@ cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepCo
     const long long ntiles = (long long)ntx * ntz;
     int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
     if (Rd.enabled && grid < 1) grid = 1;
+    PairConst K{};
+    if constexpr (kPair<T, NS>) fill_pair_const(K, C);
     k_pull<T, NS, MODE><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS>), st>>>(
-        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, O, Rd, sched, ntx, ntz);
+        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, ntx,
+        ntz);
     return cudaGetLastError();
 }
 
