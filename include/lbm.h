@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 /* status codes */
 enum {
@@ -68,6 +68,14 @@ typedef struct {
     void *stream;        /* cudaStream_t to run on; NULL = a stream owned by the context  */
     int rows_per_warp;   /* SWEEP kernel: rows of one strip swept by a warp; 0 = auto      */
     int tile_rows;       /* FUSED kernel: tile height, 8 or 16 rows; 0 = auto             */
+    int n_instances;     /* 0 or 1: one lattice.  > 1: a batch of that many channels (at
+                            most 4096) stepped together by the PULL kernel: lattice i has
+                            inst_nz[i] rows, the same nx, couplings and walls
+                            (LBM_BOUNCEBACK), its own drive (lbm_set_instance_drive), and
+                            nz must equal the sum of inst_nz.  Fields and profiles of the
+                            batch stack the lattices' rows in order.                      */
+    const int *inst_nz;  /* n_instances > 1: host array of the lattices' heights (read by
+                            lbm_create only)                                              */
 } lbm_desc;
 
 /* Model parameters (Eq. LB, Eq. FORCE, Sec. IV).  Species index 0 = A, 1 = B. */
@@ -184,11 +192,13 @@ int lbm_abi_version(void);
      f       device pointer, FP64 populations after streaming, [n_species][9][nz][nx] (the
              layout lbm_get_fields writes), read on `stream`;
      p       the model parameters (host);
-     out     device pointer to 16 + 5 nz + 2 nx doubles, written on `stream`: [0..1] mass,
+     out     device pointer to 16 + 9 nz + 2 nx doubles, written on `stream`: [0..1] mass,
              [2..3] momentum, [4] gamma, [5..6] wall force (bottom, top), [7] 1 if a density
              <= 0, NaN or Inf was met, [8..15] unused, then ux_z[nz], rho_z[2][nz], sxz_z[nz],
              fluid_z[nz], ps_x[nx], pxx_x[nx] (definitions as in lbm_obs; rho_z of species B
-             is zero for one species).
+             is zero for one species), then the x-averages of the momentum mx_z[nz], mz_z[nz]
+             and of the wall momentum exchange wallb_z[nz], wallt_z[nz] (nonzero on the first
+             and last row).
    It allocates nothing: its scratch is one file-scope device array of
    LBM_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit, which bounds
    the lattice: bytes needed = r256(nz*ceil(nx/32)*64) + r256(nx*ceil(nz/8)*16)
@@ -202,6 +212,19 @@ int lbm_abi_version(void);
 #define LBM_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 int lbm_observables_noalloc(const double *f, int nx, int nz, int n_species, int z_boundary,
                             const lbm_params *p, double *out, void *stream);
+
+/* Batches (no counterpart in the paper: they serve sweeps over channel widths and drives, like
+   the cooperative-length analysis of Sec. V).  The drive of lattice i of a batch: body force
+   g along x and the wall velocities.  Defaults to the parameters' body_force and wall_u, and
+   lbm_set_params resets every lattice to them.  Takes effect from the next step. */
+int lbm_set_instance_drive(lbm_ctx *c, int i, double body_force, double wall_u_bottom, double wall_u_top);
+
+/* Observables of lattice i of a batch (also valid for i = 0 of one lattice): the current state
+   (averages = 0, synchronises and computes them) or the time averages sampled so far
+   (averages != 0; reset with lbm_averages).  mass, momentum, wall_force and the z profiles
+   (sized inst_nz[i]) are lattice i's; gamma, ps_x and pxx_x are left zero / untouched (the
+   batch's column profiles average over all its lattices and are in lbm_observables). */
+int lbm_instance_observables(lbm_ctx *c, int i, lbm_obs *out, int averages);
 
 /* Self-test of failure detection (no counterpart in the paper).  The step kernels' only
    device-side waits are bounded waits on TMA copies; an expired wait sets a flag that the next

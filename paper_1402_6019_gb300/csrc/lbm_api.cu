@@ -56,6 +56,12 @@ struct lbm_ctx {
     alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
     alignas(64) unsigned char pmap_out[2][128] = {};  // pull: store descriptors of f[0], f[1]
     int pull_grid[8] = {};                            // pull: resident CTAs per mode
+    // the lattices of a batch (one entry for a single lattice): host and device copies
+    std::vector<InstGeom> inst;
+    InstGeom* inst_d = nullptr;
+    std::vector<char> drive_set;  // lattice's drive set by lbm_set_instance_drive
+    int ntz_all = 0;              // pull: tile rows of all lattices
+    int prows = 0;                // pull: padded rows of a population plane
     double* host_out = nullptr; // pinned
     StepConst<float> c32{};
     StepConst<double> c64{};
@@ -98,11 +104,25 @@ static int fail(lbm_ctx* c, int code, const char* fmt, ...) {
                         cudaGetErrorString(e_), __FILE__, __LINE__);                              \
     } while (0)
 
+static Batch batch(const lbm_ctx* c) { return Batch{c->inst_d, (int)c->inst.size(), c->ntz_all}; }
+
+// Device copy of the lattices' table (geometry and drives).
+static cudaError_t upload_inst(lbm_ctx* c) {
+    return cudaMemcpyAsync(c->inst_d, c->inst.data(), c->inst.size() * sizeof(InstGeom), cudaMemcpyHostToDevice,
+                           c->stream);
+}
+
 static void refresh_const(lbm_ctx* c) {
     fill_step_const<float>(c->c32, c->p, c->d.nx, c->d.nz, c->pitch, c->plane, c->d.n_species, c->d.z_boundary,
                            c->rho_ref);
     fill_step_const<double>(c->c64, c->p, c->d.nx, c->d.nz, c->pitch, c->plane, c->d.n_species, c->d.z_boundary,
                             c->rho_ref);
+    for (size_t i = 0; i < c->inst.size(); ++i)  // the parameters' drive, where no lattice drive is set
+        if (!c->drive_set[i]) {
+            c->inst[i].g = c->p.body_force;
+            c->inst[i].wall_u[0] = c->p.wall_u[0];
+            c->inst[i].wall_u[1] = c->p.wall_u[1];
+        }
 }
 
 static void drop_graphs(lbm_ctx* c) {
@@ -155,6 +175,19 @@ static int check_desc(lbm_ctx* c, const lbm_desc* d) {
     if (d->tile_rows != 0 && d->tile_rows != 8 && d->tile_rows != 16)
         return fail(c, LBM_EINVAL, "tile_rows must be 0, 8 or 16");
     if (d->device < 0) return fail(c, LBM_EINVAL, "negative device ordinal");
+    if (d->n_instances < 0 || d->n_instances > 4096) return fail(c, LBM_EINVAL, "n_instances must be in [0, 4096]");
+    if (d->n_instances > 1) {
+        if (!d->inst_nz) return fail(c, LBM_EINVAL, "inst_nz is NULL");
+        long long sum = 0;
+        for (int i = 0; i < d->n_instances; ++i) {
+            if (d->inst_nz[i] < 1) return fail(c, LBM_EINVAL, "inst_nz[%d] = %d is not >= 1", i, d->inst_nz[i]);
+            sum += d->inst_nz[i];
+        }
+        if (sum != d->nz) return fail(c, LBM_EINVAL, "nz (%d) must equal the sum of inst_nz (%lld)", d->nz, sum);
+        if (d->z_boundary != LBM_BOUNCEBACK) return fail(c, LBM_EINVAL, "a batch needs LBM_BOUNCEBACK walls");
+        if (d->kernel != LBM_KERNEL_AUTO && d->kernel != LBM_KERNEL_PULL)
+            return fail(c, LBM_EINVAL, "a batch runs on the PULL kernel");
+    }
     return LBM_OK;
 }
 
@@ -193,9 +226,9 @@ static void release(lbm_ctx* c) {
     drop_graphs(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
-    void* ptrs[] = {c->f[0],       c->f[1],       c->part_row[0], c->part_row[1], c->part_col[0],
-                    c->part_col[1], c->sched,      c->ticket,      c->flag,        c->out,
-                    c->avg,         c->staging,    c->fexport,     c->gfield};
+    void* ptrs[] = {c->f[0],       c->f[1],    c->part_row[0], c->part_row[1], c->part_col[0],
+                    c->part_col[1], c->sched,   c->ticket,      c->flag,        c->out,
+                    c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_out) cudaFreeHost(c->host_out);
@@ -261,9 +294,30 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
     c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_PULL : d->kernel;
     c->pull = c->kernel == LBM_KERNEL_PULL;
-    if (c->pull) {  // ghost columns and rows around every plane; 128-byte rows
+    {  // the lattices: rows stacked in order, each with its own ghost rows in the planes
+        const int ni = d->n_instances > 1 ? d->n_instances : 1;
+        const int ntx = (nx + 31) / 32;
+        c->inst.assign(ni, InstGeom{});
+        c->drive_set.assign(ni, 0);
+        int zrow = 0, prow = 0, trow = 0;
+        for (int i = 0; i < ni; ++i) {
+            InstGeom& g = c->inst[i];
+            g.nz = ni > 1 ? d->inst_nz[i] : nz;
+            g.zrow0 = zrow;
+            g.prow0 = prow;
+            g.tile0 = trow * ntx;
+            g.ntz = (g.nz + 7) / 8;
+            zrow += g.nz;
+            prow += g.nz + 2 * PULL_GZ;
+            trow += g.ntz;
+        }
+        c->ntz_all = trow;
+        c->prows = prow;
+        CKC(cudaMalloc(&c->inst_d, ni * sizeof(InstGeom)));
+    }
+    if (c->pull) {  // ghost columns and rows around every lattice; 128-byte rows
         c->pitch = (nx + 2 * PULL_GX + 31) / 32 * 32;
-        c->plane = (long long)(nz + 2 * PULL_GZ) * c->pitch;
+        c->plane = (long long)c->prows * c->pitch;
     } else {
         c->pitch = (nx + 31) / 32 * 32;
         c->plane = (long long)nz * c->pitch;
@@ -287,7 +341,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     const int tx = (nx + TPX - 1) / TPX, tz = (nz + std::min(TPZ, 8) - 1) / std::min(TPZ, 8);
     const long long rows_parts = std::max(c->geom_obs.nstrips, tx);
-    const long long col_parts = std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz);
+    const long long col_parts = std::max(std::max(std::max(c->geom_obs.nchunks, c->geom.nchunks), tz), c->ntz_all);
     for (int b = 0; b < 2; ++b) {
         CKC(cudaMalloc(&c->part_row[b], (size_t)rows_parts * nz * NQR * c->esize));
         CKC(cudaMalloc(&c->part_col[b], (size_t)col_parts * nx * NQC * c->esize));
@@ -315,8 +369,8 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     if (c->pull) {
         for (int b = 0; b < 2; ++b)
-            if (make_pop_tmaps(c->pmap_in[b], c->pmap_out[b], c->f[b], (int)c->esize, ns, nx, nz, c->pitch, c->plane) !=
-                0)
+            if (make_pop_tmaps(c->pmap_in[b], c->pmap_out[b], c->f[b], (int)c->esize, ns, nx, c->prows, c->pitch,
+                               c->plane) != 0)
                 return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
         const int modes[4] = {M_WRITE, M_WRITE | M_OBS, M_OBS, M_FIELDS};
         for (int m : modes) {
@@ -325,9 +379,10 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
             c->pull_grid[m] = nb * c->nsm;
         }
     }
+    refresh_const(c);
+    CKC(upload_inst(c));
     CKC(cudaStreamSynchronize(c->stream));
 #undef CKC
-    refresh_const(c);
     *out = c;
     return LBM_OK;
 }
@@ -345,8 +400,32 @@ extern "C" int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
     if (rc) return rc;
     c->p = *p;
     c->have_params = true;
+    std::fill(c->drive_set.begin(), c->drive_set.end(), 0);
     refresh_const(c);
+    CK(upload_inst(c));
     drop_graphs(c);
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_instance_drive(lbm_ctx* c, int i, double body_force, double wall_u_bottom,
+                                      double wall_u_top) {
+    if (!c) return LBM_EINVAL;
+    if (i < 0 || i >= (int)c->inst.size()) return fail(c, LBM_EINVAL, "lattice %d not in the batch", i);
+    if (!std::isfinite(body_force) || !std::isfinite(wall_u_bottom) || !std::isfinite(wall_u_top))
+        return fail(c, LBM_EINVAL, "drive values must be finite");
+    CK(cudaSetDevice(c->d.device));
+    if (!c->pull) {  // one lattice on another kernel: the drive lives in the step constants
+        c->p.body_force = body_force;
+        c->p.wall_u[0] = wall_u_bottom;
+        c->p.wall_u[1] = wall_u_top;
+        refresh_const(c);
+        drop_graphs(c);
+    }
+    c->inst[i].g = body_force;
+    c->inst[i].wall_u[0] = wall_u_bottom;
+    c->inst[i].wall_u[1] = wall_u_top;
+    c->drive_set[i] = 1;
+    CK(upload_inst(c));  // the kernels read the table at run time: captured graphs stay valid
     return LBM_OK;
 }
 
@@ -367,11 +446,13 @@ static cudaError_t reduce_now(lbm_ctx* c, int buf, bool accumulate) {
     const bool sweep = c->kernel == LBM_KERNEL_SWEEP;
     const int tzrows = c->kernel == LBM_KERNEL_TWO_PASS ? TPZ : c->tile_rows;
     const int nxp = sweep ? c->geom_obs.nstrips : (c->d.nx + TPX - 1) / TPX;
-    const int nzp = sweep ? c->geom_obs.nchunks : (c->d.nz + tzrows - 1) / tzrows;
+    const int nzp = sweep ? c->geom_obs.nchunks : c->pull ? c->ntz_all : (c->d.nz + tzrows - 1) / tzrows;
     const long long ol = obs_len(c->d.nx, c->d.nz);
+    const int ni = (int)c->inst.size();
     c->launches += 1;
     return launch_reduce((int)c->esize, obs_ptrs(c, buf), nxp, nzp, c->d.nx, c->d.nz, c->d.z_boundary, c->ticket,
-                         c->out, c->avg, c->out + ol, c->avg + ol, accumulate ? 1 : 0, false, c->stream);
+                         c->out, c->avg, c->out + ol, c->avg + ol, accumulate ? 1 : 0, false,
+                         ni > 1 ? c->inst_d : nullptr, ni, c->stream);
 }
 
 // A reduction left pending by the pull kernel, run now (before the host reads or resets the
@@ -403,7 +484,7 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
             Rd.bpart = c->out + ol;
             Rd.bavg = c->avg + ol;
             Rd.nxpart = (c->d.nx + TPX - 1) / TPX;
-            Rd.nzpart = (c->d.nz + c->tile_rows - 1) / c->tile_rows;
+            Rd.nzpart = c->ntz_all;
             Rd.accumulate = c->pending_acc ? 1 : 0;
             Rd.enabled = 1;
             // the reciprocals in the populations' precision, as the reduction kernel takes them
@@ -448,12 +529,13 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
     } else if (c->pull) {
         const void* tin = c->pmap_in[cur];
         const void* tout = c->pmap_out[cur ^ 1];
+        const Batch B = batch(c);
         if (c->d.precision == LBM_FP64)
             e = launch_pull<double>(c->d.n_species, mode, tin, tout, (double*)c->f[cur ^ 1], c->c64, O, Rd,
-                                    c->sched, c->pull_grid[mode], c->stream);
+                                    c->sched, B, c->pull_grid[mode], c->stream);
         else
             e = launch_pull<float>(c->d.n_species, mode, tin, tout, (float*)c->f[cur ^ 1], c->c32, O, Rd,
-                                   c->sched, c->pull_grid[mode], c->stream);
+                                   c->sched, B, c->pull_grid[mode], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
@@ -567,6 +649,7 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
     if (!rho) return fail(c, LBM_EINVAL, "rho is NULL");
     if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
     CK(cudaSetDevice(c->d.device));
+    const Batch B = batch(c);
     const int ns = c->d.n_species;
     const long long n = (long long)c->d.nx * c->d.nz;
     // validation and the reference densities need the values on the host
@@ -598,11 +681,11 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
     drop_graphs(c);
     c->cur = 0;
     if (c->d.precision == LBM_FP64) {
-        CK(launch_init<double>(ns, (double*)c->f[0], c->staging, du, c->c64, c->pull, c->stream));
-        if (c->pull) CK(launch_pull_images<double>(ns, (double*)c->f[0], c->c64, c->stream));
+        CK(launch_init<double>(ns, (double*)c->f[0], c->staging, du, c->c64, c->pull ? &B : nullptr, c->stream));
+        if (c->pull) CK(launch_pull_images<double>(ns, (double*)c->f[0], c->c64, B, c->stream));
     } else {
-        CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->pull, c->stream));
-        if (c->pull) CK(launch_pull_images<float>(ns, (float*)c->f[0], c->c32, c->stream));
+        CK(launch_init<float>(ns, (float*)c->f[0], c->staging, du, c->c32, c->pull ? &B : nullptr, c->stream));
+        if (c->pull) CK(launch_pull_images<float>(ns, (float*)c->f[0], c->c32, B, c->stream));
     }
     c->launches += c->pull ? 2 : 1;
     CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
@@ -620,6 +703,7 @@ extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
     if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
     CK(cudaSetDevice(c->d.device));
+    const Batch B = batch(c);
     const int ns = c->d.n_species;
     const long long n = (long long)c->d.nx * c->d.nz;
     const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -631,9 +715,11 @@ extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int
     if (f) {
         if (!c->fexport) CK(cudaMalloc(&c->fexport, (size_t)ns * 9 * n * sizeof(double)));
         if (c->d.precision == LBM_FP64)
-            CK(launch_export<double>(ns, (const double*)c->f[c->cur], c->fexport, c->c64, c->pull, c->stream));
+            CK(launch_export<double>(ns, (const double*)c->f[c->cur], c->fexport, c->c64, c->pull ? &B : nullptr,
+                                     c->stream));
         else
-            CK(launch_export<float>(ns, (const float*)c->f[c->cur], c->fexport, c->c32, c->pull, c->stream));
+            CK(launch_export<float>(ns, (const float*)c->f[c->cur], c->fexport, c->c32, c->pull ? &B : nullptr,
+                                    c->stream));
         c->launches += 1;
         CK(cudaMemcpyAsync(f, c->fexport, (size_t)ns * 9 * n * sizeof(double), kind, c->stream));
     }
@@ -665,8 +751,16 @@ static void unpack(const lbm_ctx* c, const double* buf, lbm_obs* o, double scale
     o->momentum[0] = sc[2] * scale;
     o->momentum[1] = sc[3] * scale;
     o->gamma = sc[4] * scale;
-    o->wall_force[0] = c->d.z_boundary ? E(O_WALL) * scale : 0.0;
-    o->wall_force[1] = c->d.z_boundary ? E(O_WALL + 1) * scale : 0.0;
+    // wall forces: the sums of the wall profiles (of every lattice of a batch)
+    const long long wb = O_PROF + 7LL * nz + 2LL * nx, wt = wb + nz;
+    double fb = 0.0, ft = 0.0;
+    if (c->d.z_boundary)
+        for (int z = 0; z < nz; ++z) {
+            fb += E(wb + z);
+            ft += E(wt + z);
+        }
+    o->wall_force[0] = fb * scale;
+    o->wall_force[1] = ft * scale;
     bool bad = E(O_BAD) != 0.0;
     for (int k = 0; k < 5; ++k) bad = bad || !std::isfinite(sc[k]);
     o->nonfinite = bad;
@@ -683,6 +777,61 @@ static void unpack(const lbm_ctx* c, const double* buf, lbm_obs* o, double scale
         if (o->ps_x) o->ps_x[x] = E(ps + x) * scale;
         if (o->pxx_x) o->pxx_x[x] = E(px + x) * scale;
     }
+}
+
+// Lattice i of a batch from the row profiles of the observable buffer buf.
+static void unpack_instance(const lbm_ctx* c, const double* buf, int i, lbm_obs* o, double scale) {
+    const int nx = c->d.nx, nz = c->d.nz, ns = c->d.n_species;
+    const InstGeom& g = c->inst[i];
+    auto E = [&](long long k) { return entry(c, buf, k); };
+    const long long ux = O_PROF, rz = ux + nz, sx = rz + 2LL * nz, fl = sx + nz, mx = fl + nz + 2LL * nx,
+                    mz = mx + nz, wb = mz + nz, wt = wb + nz;
+    double m[2] = {0.0, 0.0}, j[2] = {0.0, 0.0}, w[2] = {0.0, 0.0};
+    for (int k = 0; k < g.nz; ++k) {
+        const long long z = g.zrow0 + k;
+        for (int s = 0; s < ns; ++s) m[s] += E(rz + (long long)s * nz + z);
+        j[0] += E(mx + z);
+        j[1] += E(mz + z);
+        w[0] += E(wb + z);
+        w[1] += E(wt + z);
+        if (o->ux_z) o->ux_z[k] = E(ux + z) * scale;
+        if (o->sxz_z) o->sxz_z[k] = E(sx + z) * scale;
+        if (o->fluid_z) o->fluid_z[k] = E(fl + z) * scale;
+        if (o->rho_z)
+            for (int s = 0; s < ns; ++s) o->rho_z[s * g.nz + k] = E(rz + (long long)s * nz + z) * scale;
+    }
+    // the profiles are x-averages: sums over the lattice are nx times their sums over rows
+    o->mass[0] = m[0] * nx * scale;
+    o->mass[1] = m[1] * nx * scale;
+    o->momentum[0] = j[0] * nx * scale;
+    o->momentum[1] = j[1] * nx * scale;
+    o->wall_force[0] = w[0] * scale;
+    o->wall_force[1] = w[1] * scale;
+    o->gamma = 0.0;
+    o->nonfinite = E(O_BAD) != 0.0;
+    o->step = c->step;
+}
+
+extern "C" int lbm_instance_observables(lbm_ctx* c, int i, lbm_obs* o, int averages) {
+    if (!c) return LBM_EINVAL;
+    if (!o) return fail(c, LBM_EINVAL, "out is NULL");
+    if (i < 0 || i >= (int)c->inst.size()) return fail(c, LBM_EINVAL, "lattice %d not in the batch", i);
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    if (averages) {
+        CK(flush_pending(c));
+        CK(cudaMemcpyAsync(c->host_out, c->avg, obs_bytes(c), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        unpack_instance(c, c->host_out, i, o, c->samples > 0 ? 1.0 / (double)c->samples : 0.0);
+        o->samples = c->samples;
+        return LBM_OK;
+    }
+    CK(enqueue_pass(c, c->cur, M_OBS, true, false, false));
+    CK(cudaMemcpyAsync(c->host_out, c->out, obs_bytes(c), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    unpack_instance(c, c->host_out, i, o, 1.0);
+    o->samples = 1;
+    return o->nonfinite ? fail(c, LBM_ENONFINITE, "state holds a density <= 0, NaN or Inf") : LBM_OK;
 }
 
 extern "C" int lbm_observables(lbm_ctx* c, lbm_obs* o) {

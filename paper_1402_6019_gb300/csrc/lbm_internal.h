@@ -37,9 +37,57 @@ struct GhostGeom {
     long long gplane;     // (nz + 4) * gpitch
 };
 
-// Observable output layout (doubles) written by the reduction kernel.
+// Observable output layout (doubles) written by the reduction kernel: scalars, then the row
+// profiles ux_z, rho_z[2], sxz_z, fluid_z, the column profiles ps_x, pxx_x, and the row profiles
+// mx_z, mz_z (x-averaged momentum) and wallb_z, wallt_z (x-averaged wall momentum exchange,
+// nonzero on a lattice's first / last row).  nz counts all rows of a stacked batch.
 enum { O_MASS = 0, O_MOM = 2, O_GAMMA = 4, O_WALL = 5, O_BAD = 7, O_COUNT = 8, O_PROF = 16 };
-LBM_HD long long obs_len(int nx, int nz) { return O_PROF + 5LL * nz + 2LL * nx; }
+LBM_HD long long obs_len(int nx, int nz) { return O_PROF + 9LL * nz + 2LL * nx; }
+
+// One lattice of a stacked batch (a single lattice is a batch of one).  All lattices share nx
+// and the model parameters except the drive; lattice i's rows follow lattice i - 1's, in the
+// fields' layout (compact rows) and in the population planes (each with its own ghost rows).
+struct InstGeom {
+    int nz;       // rows of the lattice
+    int zrow0;    // its row 0 among the compact rows of the batch
+    int prow0;    // padded plane row of its row -PULL_GZ (its row z sits at prow0 + PULL_GZ + z)
+    int tile0;    // its first tile in the pull kernel's numbering (ntx tiles per tile row)
+    int ntz;      // its tile rows
+    int pad_;
+    double g;          // body acceleration along x
+    double wall_u[2];  // bottom, top wall velocity along x
+};
+// The lattices of a pull-kernel context, as the kernels see them: the device copy of the table,
+// its length, and the tile rows of all lattices together.
+struct Batch {
+    const InstGeom* inst;
+    int ninst;
+    int ntz;
+};
+
+// The lattice holding compact row zg, or tile t (binary search over ascending starts).
+LBM_HD int inst_of_row(const InstGeom* I, int n, int zg) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (I[mid].zrow0 <= zg)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+LBM_HD int inst_of_tile(const InstGeom* I, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (I[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 // Launchers (return the launch error).
 template <typename T>
@@ -80,15 +128,16 @@ struct Fold {
     double inx, inz;  // 1/nx, 1/nz
 };
 
-// Pull layout: ghost columns on either side and ghost rows above and below each plane; lattice
-// site (x, z) sits at padded column x + PULL_GX, padded row z + PULL_GZ.  pitch >= nx + 2 PULL_GX,
-// plane = (nz + 2 PULL_GZ) pitch.
+// Pull layout: ghost columns on either side and ghost rows above and below each lattice in the
+// plane; lattice site (x, z) sits at padded column x + PULL_GX, padded row prow0 + z + PULL_GZ
+// (prow0 = 0 for a single lattice).  pitch >= nx + 2 PULL_GX, plane = prows * pitch with
+// prows = sum over the lattices of (nz + 2 PULL_GZ).
 constexpr int PULL_GX = 4, PULL_GZ = 3;
 
-// Pull-layout kernel: TMA descriptors of one population buffer f ([9 ns][nz + 6][pitch] values):
+// Pull-layout kernel: TMA descriptors of one population buffer f ([9 ns][prows][pitch] values):
 // the load box of a tile with its 3-cell ring (in_map) and the store box of a tile (out_map),
 // 128 bytes each.  Returns 0 on success.
-int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int nz, int pitch,
+int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int prows, int pitch,
                    long long plane);
 // CTAs of the pull kernel resident per SM for a mode (sets the kernel's shared-memory limit on
 // the current device); 0 on failure.
@@ -100,29 +149,31 @@ int pull_blocks_per_sm(int ns, int mode);
 // before the launch and left zero by it.  grid_max: resident CTAs on the device.
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
-                        const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st);
+                        const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B, int grid_max,
+                        cudaStream_t st);
 // One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st);
 // Fills the ghost columns and rows of a pull-layout buffer with the periodic images.
 template <typename T>
-cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, cudaStream_t st);
+cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, const Batch& B, cudaStream_t st);
 // Initial state / export of the populations of Sec. II (post-streaming, plain FP64 values),
-// in the push layout or (pull) the padded pull layout of the pull kernel (C.pitch, C.plane are
-// the buffer's; the ghosts are filled by launch_pull_images).
+// in the push layout (B null) or the padded pull layout of the pull kernel's lattices (C.pitch,
+// C.plane are the buffer's; the ghosts are filled by launch_pull_images).
 template <typename T>
-cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, bool pull,
+cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, const Batch* B,
                         cudaStream_t st);
 template <typename T>
-cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, bool pull, cudaStream_t st);
+cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, const Batch* B, cudaStream_t st);
 // Reduction of the step kernels' partial sums into the observables.  `out` / `avg` hold
 // obs_len(nx, nz) entries (profiles, wall forces, flag); `bpart` / `bavg` hold
 // reduce_blocks(nx, nz) * 5 block partials of the scalars (mass A, B, momentum x, z, gamma) and
 // their time sums.  With tail the scalar sums are also written into out[O_MASS..].  Entries are
-// doubles (FP64 mode) or (hi, lo) float pairs (FP32 mode).
+// doubles (FP64 mode) or (hi, lo) float pairs (FP32 mode).  inst / ninst: the device table of a
+// stacked batch (rows of different lattices are not neighbours), null for one lattice.
 int reduce_blocks(int nx, int nz);
 cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
                           unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
-                          bool tail, cudaStream_t st);
+                          bool tail, const InstGeom* inst, int ninst, cudaStream_t st);
 
 // Twopass tile (threads per CTA: TPX x TPZ sites).
 constexpr int TPX = 32, TPZ = 8;

@@ -70,6 +70,6 @@ extern "C" int lbm_observables_noalloc(const double* f, int nx, int nz, int n_sp
     if (e == cudaSuccess) e = launch_tile<double>(n_species, M_OBS, TPZ, f, nullptr, C, O, st);
     if (e == cudaSuccess)
         e = launch_reduce((int)sizeof(double), O, nxpart, nzpart, nx, nz, z_boundary, ticket, out, nullptr, slots,
-                          nullptr, 0, true, st);
+                          nullptr, 0, true, nullptr, 0, st);
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

@@ -5,33 +5,41 @@ namespace lbm {
 
 namespace {
 
+// Slot of population l of site (x, z) of the lattice whose row -PULL_GZ is padded row prow0 (nz
+// rows) in the pull layout: where its gather reads it, at x - c_l, or at (x, opp(l)) when
+// x - c_l lies beyond a wall.  Returns the offset within a plane and sets ls to the plane.
+template <typename T>
+__device__ long long pull_slot(const StepConst<T>& C, int x, int z, int nz, int prow0, int l, int& ls) {
+    const int zs = z - cz(l);
+    if (C.zbc && (zs < 0 || zs >= nz)) {
+        ls = opp(l);
+        return (long long)(prow0 + z + PULL_GZ) * C.pitch + x + PULL_GX;
+    }
+    ls = l;
+    return (long long)(prow0 + wrap_index(zs, nz) + PULL_GZ) * C.pitch + wrap_index(x - cx(l), C.nx) + PULL_GX;
+}
+
 // Populations at the equilibrium of Sec. II for given rho, u (stored as deviations from
-// W_l rho_ref; rho_ref = 0 stores plain values).  The arithmetic is done in FP64.  Push layout:
-// the value of (x, l) sits at (x, l).  Pull layout: it sits where the gather of (x, l) reads it,
-// at x - c_l, or at (x, opp(l)) when x - c_l lies beyond a wall; every slot is written once.
+// W_l rho_ref; rho_ref = 0 stores plain values).  The arithmetic is done in FP64.  Push layout
+// (inst null): the value of (x, l) sits at (x, l).  Pull layout: it sits where the gather of
+// (x, l) reads it (pull_slot); every slot is written once.  z runs over the compact rows of all
+// lattices of a batch.
 template <typename T>
 __global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho, const double* __restrict__ u,
-                       const StepConst<T> C, int pull) {
+                       const StepConst<T> C, const InstGeom* __restrict__ inst, int ninst) {
     const long long n = (long long)C.nx * C.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % C.nx), z = (int)(i / C.nx);
+        const int x = (int)(i % C.nx), zg = (int)(i / C.nx);
         const double ux = u ? u[i] : 0.0, uz = u ? u[n + i] : 0.0;
+        int k = 0;
+        if (inst && ninst > 1) k = inst_of_row(inst, ninst, zg);
         for (int s = 0; s < ns; ++s) {
             const double r = rho[s * n + i];
             const double dr = r - (double)C.rho_ref[s];
             for (int l = 0; l < 9; ++l) {
-                long long o = (long long)z * C.pitch + x;
+                long long o = (long long)zg * C.pitch + x;
                 int ls = l;
-                if (pull) {
-                    const int zs = z - cz(l);
-                    if (C.zbc && (zs < 0 || zs >= C.nz)) {
-                        ls = opp(l);
-                        o = (long long)(z + PULL_GZ) * C.pitch + x + PULL_GX;
-                    } else {
-                        o = (long long)(wrap_index(zs, C.nz) + PULL_GZ) * C.pitch + wrap_index(x - cx(l), C.nx) +
-                            PULL_GX;
-                    }
-                }
+                if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
                 f[(s * 9 + ls) * C.plane + o] = (T)feq_dev<double>(l, dr, r, ux, uz);
             }
         }
@@ -41,24 +49,18 @@ __global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho
 // The post-streaming populations as plain FP64 values, [ns][9][nz][nx]: the stored value of
 // (x, l) in the push layout, the gather of the pull layout.
 template <typename T>
-__global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ out, const StepConst<T> C, int pull) {
+__global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ out, const StepConst<T> C,
+                         const InstGeom* __restrict__ inst, int ninst) {
     const long long n = (long long)C.nx * C.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % C.nx), z = (int)(i / C.nx);
+        const int x = (int)(i % C.nx), zg = (int)(i / C.nx);
+        int k = 0;
+        if (inst && ninst > 1) k = inst_of_row(inst, ninst, zg);
         for (int s = 0; s < ns; ++s)
             for (int l = 0; l < 9; ++l) {
-                long long o = (long long)z * C.pitch + x;
+                long long o = (long long)zg * C.pitch + x;
                 int ls = l;
-                if (pull) {
-                    const int zs = z - cz(l);
-                    if (C.zbc && (zs < 0 || zs >= C.nz)) {
-                        ls = opp(l);
-                        o = (long long)(z + PULL_GZ) * C.pitch + x + PULL_GX;
-                    } else {
-                        o = (long long)(wrap_index(zs, C.nz) + PULL_GZ) * C.pitch + wrap_index(x - cx(l), C.nx) +
-                            PULL_GX;
-                    }
-                }
+                if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
                 out[(s * 9 + l) * n + i] = (double)f[(s * 9 + ls) * C.plane + o] + wlb<double>(l) * (double)C.rho_ref[s];
             }
     }
@@ -70,7 +72,8 @@ template <typename PT, bool TAIL>
 __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpart, int nzpart, int nx, int nz, int zbc,
                                                        int nrowblocks, unsigned* ticket, void* __restrict__ out,
                                                        void* __restrict__ avg, void* __restrict__ bpart,
-                                                       void* __restrict__ bavg, int accumulate, PT inx, PT inz) {
+                                                       void* __restrict__ bavg, int accumulate, PT inx, PT inz,
+                                                       const InstGeom* __restrict__ inst, int ninst) {
     using R = Red<PT>;
     using A = typename R::A;
     __shared__ A wsc[RB_THREADS / 32][NSC];
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
     __shared__ bool last;
     const int t = threadIdx.x;
     reduce_block<PT>(blockIdx.x, O.part_row, O.part_col, O.flag, nxpart, nzpart, nx, nz, zbc, nrowblocks, out, avg,
-                     bpart, bavg, accumulate, inx, inz, wsc);
+                     bpart, bavg, accumulate, inx, inz, wsc, inst, ninst);
     if constexpr (TAIL) {
         // the block's writes happen before thread 0's fence (barrier); the fence is
         // cumulative, so the block drawing the last ticket sees every block's results
@@ -127,19 +130,19 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 }  // namespace
 
 template <typename T>
-cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, bool pull,
+cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, const Batch* B,
                         cudaStream_t st) {
     const long long n = (long long)C.nx * C.nz;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_init<T><<<blocks, 256, 0, st>>>(ns, f, rho, u, C, pull ? 1 : 0);
+    k_init<T><<<blocks, 256, 0, st>>>(ns, f, rho, u, C, B ? B->inst : nullptr, B ? B->ninst : 0);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, bool pull, cudaStream_t st) {
+cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, const Batch* B, cudaStream_t st) {
     const long long n = (long long)C.nx * C.nz;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_export<T><<<blocks, 256, 0, st>>>(ns, f, out, C, pull ? 1 : 0);
+    k_export<T><<<blocks, 256, 0, st>>>(ns, f, out, C, B ? B->inst : nullptr, B ? B->ninst : 0);
     return cudaGetLastError();
 }
 
@@ -149,33 +152,38 @@ int reduce_blocks(int nx, int nz) {
 
 cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
                           unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
-                          bool tail, cudaStream_t st) {
+                          bool tail, const InstGeom* inst, int ninst, cudaStream_t st) {
     const int rb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int nb = reduce_blocks(nx, nz);
     if (precision_bytes == 4) {
         if (tail)
             k_reduce<float, true><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
-                                                             bpart, bavg, accumulate, 1.0f / nx, 1.0f / nz);
+                                                             bpart, bavg, accumulate, 1.0f / nx, 1.0f / nz, inst,
+                                                              ninst);
         else
             k_reduce<float, false><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
-                                                              bpart, bavg, accumulate, 1.0f / nx, 1.0f / nz);
+                                                              bpart, bavg, accumulate, 1.0f / nx, 1.0f / nz, inst,
+                                                              ninst);
     } else {
         if (tail)
             k_reduce<double, true><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
-                                                              bpart, bavg, accumulate, 1.0 / nx, 1.0 / nz);
+                                                              bpart, bavg, accumulate, 1.0 / nx, 1.0 / nz, inst,
+                                                               ninst);
         else
             k_reduce<double, false><<<nb, RB_THREADS, 0, st>>>(O, nxpart, nzpart, nx, nz, zbc, rb, ticket, out, avg,
-                                                               bpart, bavg, accumulate, 1.0 / nx, 1.0 / nz);
+                                                               bpart, bavg, accumulate, 1.0 / nx, 1.0 / nz, inst,
+                                                               ninst);
     }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_init<float>(int, float*, const double*, const double*, const StepConst<float>&, bool,
-                                        cudaStream_t);
-template cudaError_t launch_init<double>(int, double*, const double*, const double*, const StepConst<double>&, bool,
-                                         cudaStream_t);
-template cudaError_t launch_export<float>(int, const float*, double*, const StepConst<float>&, bool, cudaStream_t);
-template cudaError_t launch_export<double>(int, const double*, double*, const StepConst<double>&, bool,
+template cudaError_t launch_init<float>(int, float*, const double*, const double*, const StepConst<float>&,
+                                        const Batch*, cudaStream_t);
+template cudaError_t launch_init<double>(int, double*, const double*, const double*, const StepConst<double>&,
+                                         const Batch*, cudaStream_t);
+template cudaError_t launch_export<float>(int, const float*, double*, const StepConst<float>&, const Batch*,
+                                          cudaStream_t);
+template cudaError_t launch_export<double>(int, const double*, double*, const StepConst<double>&, const Batch*,
                                            cudaStream_t);
 
 }  // namespace lbm

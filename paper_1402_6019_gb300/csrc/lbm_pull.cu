@@ -71,6 +71,7 @@ struct PullSmem {
     typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
     alignas(8) unsigned long long bar[STAGES];
     int tile[STAGES];  // the tile each box holds (or is loading)
+    int inst[STAGES];  // and the lattice of the batch it belongs to
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -141,15 +142,15 @@ __device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int sl, in
 // site reads (far padding of ragged tiles) are set to zero.
 template <typename T, int NS>
 __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const StepConst<T>& C, const PairConst& K,
-                                             int px, int pz, int z0) {
+                                             int px, int pz, int z0, int nz) {
     const int Z = z0 - 2 + pz;
     int Zs = Z;
     bool zero = false;
-    if (C.zbc && (Z < 0 || Z >= C.nz)) {
+    if (C.zbc && (Z < 0 || Z >= nz)) {
         if (C.psi_wall == 1)
             zero = true;
         else
-            Zs = mirror_index(Z, C.nz);
+            Zs = mirror_index(Z, nz);
     }
     const int bz = Zs - z0 + 3, bx = px + 2;
     if (bz < 1 || bz > BZ - 2) zero = true;
@@ -158,7 +159,7 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const S
     for (int s = 0; s < NS; ++s) sum[s] = T(0);
     if (!zero) {
         T g[NS][9];
-        const bool lo = C.zbc && Zs == 0, hi = C.zbc && Zs == C.nz - 1;
+        const bool lo = C.zbc && Zs == 0, hi = C.zbc && Zs == nz - 1;
         if (lo || hi)
             gather_wall<T, NS>(S, sl, bx, bz, lo, hi, g);
         else
@@ -180,12 +181,13 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const S
     }
 }
 
-// The periodic images of site (x, z): plain stores of its new values (read back from the
-// staging tile) into the ghost columns (and, without walls, ghost rows) that wrap onto it.
+// The periodic images of site (x, z) of a lattice of nz rows whose row -PULL_GZ is padded row
+// prow0: plain stores of its new values (read back from the staging tile) into the ghost columns
+// (and, without walls, ghost rows) that wrap onto it.
 template <typename T, int NS>
 __device__ __noinline__ void write_images(const PullSmem<T, NS>& S, const StepConst<T>& C, T* __restrict__ fout,
-                                          int x, int z, int tx, int tz) {
-    const int nx = C.nx, nz = C.nz;
+                                          int x, int z, int nz, int prow0, int tx, int tz) {
+    const int nx = C.nx;
     int xs[2 * PULL_GX + 1], zs[2 * PULL_GZ + 1];
     int nxs = 0, nzs = 0;
     xs[nxs++] = x;
@@ -202,7 +204,7 @@ __device__ __noinline__ void write_images(const PullSmem<T, NS>& S, const StepCo
     for (int a = 0; a < nxs; ++a)
         for (int b = 0; b < nzs; ++b) {
             if (a == 0 && b == 0) continue;
-            T* dst = fout + (long long)(zs[b] + PULL_GZ) * C.pitch + (xs[a] + PULL_GX);
+            T* dst = fout + (long long)(prow0 + zs[b] + PULL_GZ) * C.pitch + (xs[a] + PULL_GX);
 #pragma unroll
             for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
         }
@@ -212,10 +214,11 @@ template <typename T, int NS, int MODE>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
-           int ntx, int ntz) {
+           const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PullSmem<T, NS>& S = *reinterpret_cast<PullSmem<T, NS>*>(smem_raw);
     const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
+    // nz: rows of all lattices; ntz: their tile rows; tiles are numbered lattice by lattice
     const int nx = C.nx, nz = C.nz;
     const int ntiles = ntx * ntz;
 
@@ -252,7 +255,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             const int t0 = more ? (int)atomicAdd(&sched[0], 1u) : ntiles;
             S.tile[sl] = t0;
             more = t0 < ntiles;
-            if (more) issue_load(S, &tin, (t0 % ntx) * PX, (t0 / ntx) * PZ, sl);
+            if (more) {
+                const int k = ninst > 1 ? inst_of_tile(inst, ninst, t0) : 0;
+                S.inst[sl] = k;
+                const int tl = t0 - inst[k].tile0;
+                issue_load(S, &tin, (tl % ntx) * PX, inst[k].prow0 + (tl / ntx) * PZ, sl);
+            }
         }
         if (more) upcoming = (int)atomicAdd(&sched[0], 1u);
     }
@@ -262,7 +270,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         const int nb = nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
         for (int b = blockIdx.x; b < nb; b += gridDim.x)
             reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
-                            Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc);
+                            Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc,
+                            ninst > 1 ? inst : nullptr, ninst);
     }
     unsigned parity = 0;  // bit sl: phase of box sl's barrier
     bool failed = false;
@@ -270,9 +279,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         const int sl = k % STAGES;
         const int t = S.tile[sl];
         if (t >= ntiles) break;
-        const int x0 = (t % ntx) * PX, z0 = (t / ntx) * PZ;
+        // this tile's lattice: rows, first compact row, first padded row, first tile, drive
+        const InstGeom* const I = inst + S.inst[sl];
+        const int lnz = I->nz, zrow0 = I->zrow0, prow0 = I->prow0, tl = t - I->tile0;
+        const int s = tl % ntx, j = tl / ntx;
+        const int x0 = s * PX, z0 = j * PZ;  // z: rows of this lattice
+        const int jg = I->tile0 / ntx + j;   // tile row among all lattices
         const int x = x0 + tx, z = z0 + tz;
-        const bool live = x < nx && z < nz;
+        const bool live = x < nx && z < lnz;
         const bool ok = wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
         if (ok) parity ^= 1u << sl;  // on expiry the exit path waits on the same phase again
 
@@ -280,7 +294,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         T f[NS][9];
         T drho[NS];
         if (live) {
-            const bool lo = C.zbc && z == 0, hi = C.zbc && z == nz - 1;
+            const bool lo = C.zbc && z == 0, hi = C.zbc && z == lnz - 1;
             if (lo || hi)
                 gather_wall<T, NS>(S, sl, tx + 4, tz + 3, lo, hi, f);
             else
@@ -305,9 +319,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                 }
             }
         } else {
-            side_density<T, NS>(S, sl, C, K, tx + 2, tz + 2, z0);
+            side_density<T, NS>(S, sl, C, K, tx + 2, tz + 2, z0, lnz);
         }
-        if (ring) side_density<T, NS>(S, sl, C, K, rpx, rpz, z0);
+        if (ring) side_density<T, NS>(S, sl, C, K, rpx, rpz, z0, lnz);
         if ((MODE & M_WRITE) && tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -319,8 +333,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             const int tn = upcoming;
             S.tile[sl] = tn;  // read by all after the barrier that ends tile k + STAGES - 1
             if (tn < ntiles) {
+                const int kn = ninst > 1 ? inst_of_tile(inst, ninst, tn) : 0;
+                S.inst[sl] = kn;
+                const int tln = tn - inst[kn].tile0;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                issue_load(S, &tin, (tn % ntx) * PX, (tn / ntx) * PZ, sl);
+                issue_load(S, &tin, (tln % ntx) * PX, inst[kn].prow0 + (tln / ntx) * PZ, sl);
                 upcoming = (int)atomicAdd(&sched[0], 1u);
             }
         }
@@ -368,7 +385,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                 const f2 ir = p2(__fdividef(1.f, rh.x), __fdividef(1.f, rh.y));
                 f2 jx, jz;
                 momentum9_2(fp, jx, jz);
-                Fx = fma2(rh, sp(C.g), Fx);
+                Fx = fma2(rh, sp((float)I->g), Fx);
                 if (MODE & (M_OBS | M_FIELDS)) {
                     // barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s and the kinetic flux
                     const f2 m = fma2(Fx, sp(0.5f), jx), n = fma2(Fz, sp(0.5f), jz);
@@ -376,7 +393,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                     const float irt = __fdividef(1.f, rtot);
                     const float ux = mx * irt, uz = mz * irt, uxz = ux * uz;
                     if (MODE & M_FIELDS) {
-                        const long long i = (long long)z * nx + x;
+                        const long long i = (long long)(zrow0 + z) * nx + x;
                         const long long np = (long long)nx * nz;
                         O.fields[i] = (double)rh.x;
                         O.fields[np + i] = (double)rh.y;
@@ -401,7 +418,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                         rowq[QR_MZ] = mz;
                     }
                 }
-                const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+                const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
                 if ((MODE & M_WRITE) || ((MODE & M_OBS) && wall_row)) {
                     collide2(K, fp, dr, rh, ir, jx, jz, Fx, Fz);
 #pragma unroll
@@ -445,13 +462,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                     if (!(rho[s2] > T(0)) || !(rho[s2] < T(1e30))) bad = 1;
                     ir[s2] = div_(T(1), rho[s2]);
                     momentum9(f[s2], jx[s2], jz[s2]);
-                    F[s2][0] += rho[s2] * C.g;
+                    F[s2][0] += rho[s2] * T(I->g);
                 }
                 if (MODE & (M_OBS | M_FIELDS)) {
                     T ux, uz, pixz, rtot, mx, mz;
                     site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
                     if (MODE & M_FIELDS) {
-                        const long long i = (long long)z * nx + x;
+                        const long long i = (long long)(zrow0 + z) * nx + x;
                         const long long np = (long long)nx * nz;
 #pragma unroll
                         for (int s2 = 0; s2 < NS; ++s2) O.fields[s2 * np + i] = (double)rho[s2];
@@ -475,7 +492,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                         rowq[QR_MZ] = mz;
                     }
                 }
-                const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+                const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
                 if ((MODE & M_WRITE) || ((MODE & M_OBS) && wall_row)) {
                     collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
                     collided = true;
@@ -483,7 +500,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             }
         }
         if (collided) {  // new stored values; with walls the populations leaving through a wall reflected
-            const bool wall_row = C.zbc == 1 && (z == 0 || z == nz - 1);
+            const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
             if (!wall_row) {  // warp-uniform
                 if (MODE & M_WRITE) {
 #pragma unroll
@@ -498,9 +515,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                     for (int l = 0; l < 9; ++l) {
                         const int zd = z + cz(l);
                         T v = f[s2][l];
-                        if (zd < 0 || zd >= nz) {  // leaves through a wall: store it reflected
+                        if (zd < 0 || zd >= lnz) {  // leaves through a wall: store it reflected
                             const int w = zd < 0 ? 0 : 1;
-                            const T back = bounce<T>(l, f[s2][l], rho[s2], C.wall_u[w]);
+                            const T back = bounce<T>(l, f[s2][l], rho[s2], T(I->wall_u[w]));
                             v = back;
                             if (MODE & M_OBS) {
                                 const T dm = T(cx(l)) * (f[s2][l] + back);
@@ -537,34 +554,35 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             }
             v1 += __shfl_xor_sync(FULL, v1, 2);
             v1 += __shfl_xor_sync(FULL, v1, 1);
-            if ((tx & 3) == 0 && z < nz) {
+            if ((tx & 3) == 0 && z < lnz) {
                 const int q = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-                static_cast<T*>(O.part_row)[((long long)z * ntx + x0 / PX) * NQR + q] = v1;
+                static_cast<T*>(O.part_row)[((long long)(zrow0 + z) * ntx + s) * NQR + q] = v1;
             }
             S.colsum[tz][QC_PS][tx] = cps;
             S.colsum[tz][QC_PXX][tx] = cpx;
         }
         __syncthreads();
         if (MODE & M_WRITE) {
-            if (x0 + PX <= nx) {
+            if (x0 + PX <= nx && z0 + PZ <= lnz) {
                 if (tid == 0) {
-                    // padded column x0 + 4 is lattice column x0, padded row z0 + 3 is lattice row z0
+                    // padded column x0 + 4 is lattice column x0, padded row prow0 + 3 + z0 is row z0
                     asm volatile(
                         "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
                             &tout),
-                        "r"(x0 + PULL_GX), "r"(z0 + PULL_GZ), "r"(0), "r"(smem_u32(&S.out[0][0][0]))
+                        "r"(x0 + PULL_GX), "r"(prow0 + z0 + PULL_GZ), "r"(0), "r"(smem_u32(&S.out[0][0][0]))
                         : "memory");
                     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
                 }
             } else if (live) {
-                // the ragged last strip: the store's x bound is checked in 16-byte units, and the
-                // columns past nx are ghost columns written by the first strip -- plain stores
-                T* dst = fout + (long long)(z + PULL_GZ) * C.pitch + (x + PULL_GX);
+                // a ragged tile: the store's x bound would be checked in 16-byte units, the columns
+                // past nx are ghost columns written by the first strip, and the rows past the
+                // lattice's last row belong to its ghost rows or to the next lattice -- plain stores
+                T* dst = fout + (long long)(prow0 + z + PULL_GZ) * C.pitch + (x + PULL_GX);
 #pragma unroll
                 for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
             }
-            if (live && (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= nz - PULL_GZ))))
-                write_images<T, NS>(S, C, fout, x, z, tx, tz);
+            if (live && (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= lnz - PULL_GZ))))
+                write_images<T, NS>(S, C, fout, x, z, lnz, prow0, tx, tz);
         }
         if (MODE & M_OBS) {
             // per-column sums over the PZ rows of the tile
@@ -572,7 +590,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                 T v = T(0);
 #pragma unroll
                 for (int r = 0; r < PZ; ++r) v += S.colsum[r][tz][tx];
-                static_cast<T*>(O.part_col)[((long long)x * ntz + z0 / PZ) * NQC + tz] = v;
+                static_cast<T*>(O.part_col)[((long long)x * ntz + jg) * NQC + tz] = v;
             }
         }
     }
@@ -608,45 +626,59 @@ int pull_occupancy() {
 
 template <typename T, int NS, int MODE>
 cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepConst<T>& C, const ObsPtrs& O,
-                        const Fold& Rd, unsigned* sched, int grid_max, cudaStream_t st) {
-    const int ntx = (C.nx + PX - 1) / PX, ntz = (C.nz + PZ - 1) / PZ;
-    const long long ntiles = (long long)ntx * ntz;
+                        const Fold& Rd, unsigned* sched, const Batch& B, int grid_max, cudaStream_t st) {
+    const int ntx = (C.nx + PX - 1) / PX;
+    const long long ntiles = (long long)ntx * B.ntz;
     int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
     if (Rd.enabled && grid < 1) grid = 1;
     PairConst K{};
     if constexpr (kPair<T, NS>) fill_pair_const(K, C);
     k_pull<T, NS, MODE><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS>), st>>>(
-        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, ntx,
-        ntz);
+        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, B.inst,
+        B.ninst, ntx, B.ntz);
     return cudaGetLastError();
 }
 
 template <typename T, int NS>
 cudaError_t launch_ns(int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
-                      const ObsPtrs& O, const Fold& Rd, unsigned* sched, int grid_max, cudaStream_t st) {
+                      const ObsPtrs& O, const Fold& Rd, unsigned* sched, const Batch& B, int grid_max,
+                      cudaStream_t st) {
     switch (mode) {
-        case M_WRITE: return launch_mode<T, NS, M_WRITE>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
+        case M_WRITE: return launch_mode<T, NS, M_WRITE>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
         case M_WRITE | M_OBS:
-            return launch_mode<T, NS, M_WRITE | M_OBS>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
-        case M_OBS: return launch_mode<T, NS, M_OBS>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
-        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(tin, tout, fout, C, O, Rd, sched, grid_max, st);
+            return launch_mode<T, NS, M_WRITE | M_OBS>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+        case M_OBS: return launch_mode<T, NS, M_OBS>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Ghost columns and rows of a pull-layout buffer from the lattice (after the initial state).
+// Ghost columns of every row of every lattice, and (one periodic lattice) the ghost rows, from
+// the lattice values (after the initial state).
 template <typename T>
-__global__ void k_images(int ns, T* __restrict__ f, const StepConst<T> C) {
-    const int wz = C.nz + 2 * PULL_GZ, wx = C.nx + 2 * PULL_GX;
-    const long long n = (long long)wz * wx;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int gx = (int)(i % wx) - PULL_GX, gz = (int)(i / wx) - PULL_GZ;
-        const bool xin = gx >= 0 && gx < C.nx, zin = gz >= 0 && gz < C.nz;
-        if (xin && zin) continue;
-        if (!zin && C.zbc) continue;
-        const int sx = wrap_index(gx, C.nx), sz = wrap_index(gz, C.nz);
-        const long long src = (long long)(sz + PULL_GZ) * C.pitch + sx + PULL_GX;
-        const long long dst = (long long)(gz + PULL_GZ) * C.pitch + gx + PULL_GX;
+__global__ void k_images(int ns, T* __restrict__ f, const StepConst<T> C, const InstGeom* __restrict__ inst,
+                         int ninst) {
+    const int wx = C.nx + 2 * PULL_GX;
+    const long long nrow = (long long)C.nz * 2 * PULL_GX;          // x ghosts of the compact rows
+    const long long nz_ghost = C.zbc ? 0 : (long long)2 * PULL_GZ * wx;  // ghost rows (single lattice)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrow + nz_ghost;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long src, dst;
+        if (i < nrow) {
+            const int zg = (int)(i / (2 * PULL_GX)), g = (int)(i % (2 * PULL_GX));
+            const int k = ninst > 1 ? inst_of_row(inst, ninst, zg) : 0;
+            const int z = zg - inst[k].zrow0;
+            const int gx = g < PULL_GX ? g - PULL_GX : C.nx + g - PULL_GX;
+            const long long row = (long long)(inst[k].prow0 + z + PULL_GZ) * C.pitch;
+            src = row + wrap_index(gx, C.nx) + PULL_GX;
+            dst = row + gx + PULL_GX;
+        } else {
+            const long long q = i - nrow;
+            const int gx = (int)(q % wx) - PULL_GX, r = (int)(q / wx);
+            const int gz = r < PULL_GZ ? r - PULL_GZ : C.nz + r - PULL_GZ;
+            src = (long long)(wrap_index(gz, C.nz) + PULL_GZ) * C.pitch + wrap_index(gx, C.nx) + PULL_GX;
+            dst = (long long)(gz + PULL_GZ) * C.pitch + gx + PULL_GX;
+        }
         for (int p = 0; p < 9 * ns; ++p) f[p * C.plane + dst] = f[p * C.plane + src];
     }
 }
@@ -675,10 +707,11 @@ int pull_blocks_per_sm(int ns, int mode) {
 
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
-                        const ObsPtrs& O, const Fold& fold, unsigned* sched, int grid_max, cudaStream_t st) {
+                        const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B, int grid_max,
+                        cudaStream_t st) {
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
-    return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fout, C, O, fold, sched, grid_max, st)
-                   : launch_ns<T, 2>(mode, tin, tout, fout, C, O, fold, sched, grid_max, st);
+    return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st)
+                   : launch_ns<T, 2>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st);
 }
 
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
@@ -687,18 +720,19 @@ cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, cudaStream_t st) {
-    k_images<T><<<256, 256, 0, st>>>(ns, f, C);
+cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, const Batch& B, cudaStream_t st) {
+    k_images<T><<<256, 256, 0, st>>>(ns, f, C, B.inst, B.ninst);
     return cudaGetLastError();
 }
 
-int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int nz, int pitch,
+int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int prows, int pitch,
                    long long plane) {
     const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!encode) return 1;
-    // loads: the whole padded plane; stores: clipped at the lattice's last column and row
-    const cuuint64_t dims_in[3] = {(cuuint64_t)pitch, (cuuint64_t)(nz + 2 * PULL_GZ), (cuuint64_t)(9 * ns)};
-    const cuuint64_t dims_out[3] = {(cuuint64_t)(nx + PULL_GX), (cuuint64_t)(nz + PULL_GZ), (cuuint64_t)(9 * ns)};
+    // loads: the whole padded plane (prows rows); stores (full tiles only): up to the last
+    // lattice column
+    const cuuint64_t dims_in[3] = {(cuuint64_t)pitch, (cuuint64_t)prows, (cuuint64_t)(9 * ns)};
+    const cuuint64_t dims_out[3] = {(cuuint64_t)(nx + PULL_GX), (cuuint64_t)prows, (cuuint64_t)(9 * ns)};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
     const cuuint32_t box_in[3] = {(cuuint32_t)BX, (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
     const cuuint32_t box_out[3] = {(cuuint32_t)PX, (cuuint32_t)PZ, (cuuint32_t)(9 * ns)};
@@ -717,10 +751,10 @@ int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns
 template int pull_blocks_per_sm<float>(int, int);
 template int pull_blocks_per_sm<double>(int, int);
 template cudaError_t launch_pull<float>(int, int, const void*, const void*, float*, const StepConst<float>&,
-                                        const ObsPtrs&, const Fold&, unsigned*, int, cudaStream_t);
+                                        const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
 template cudaError_t launch_pull<double>(int, int, const void*, const void*, double*, const StepConst<double>&,
-                                         const ObsPtrs&, const Fold&, unsigned*, int, cudaStream_t);
-template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, cudaStream_t);
-template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, cudaStream_t);
+                                         const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
+template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, const Batch&, cudaStream_t);
+template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, const Batch&, cudaStream_t);
 
 }  // namespace lbm

@@ -72,12 +72,15 @@ template <> struct Red<float> {
 // with TAIL, where the last block to finish writes the scalars into `out` on the device.
 // Group sums within a row or a column stay in the populations' precision PT; time sums and
 // block partials use the accumulators above.  Fixed summation order: repeatable results.
+// inst / ninst: the lattices of a stacked batch (rows of different lattices are not neighbours);
+// null for a single lattice of nz rows.
 template <typename PT>
 __device__ __forceinline__ void reduce_block(int blk, const void* part_row, const void* part_col, const int* flag,
                                              int nxpart, int nzpart, int nx, int nz, int zbc, int nrowblocks,
                                              void* __restrict__ out, void* __restrict__ avg,
                                              void* __restrict__ bpart, void* __restrict__ bavg, int accumulate,
-                                             PT inx, PT inz, typename Red<PT>::A (*wsc)[NSC]) {
+                                             PT inx, PT inz, typename Red<PT>::A (*wsc)[NSC],
+                                             const InstGeom* __restrict__ inst = nullptr, int ninst = 0) {
     using R = Red<PT>;
     using A = typename R::A;
     constexpr int WPB = RB_THREADS / 32;
@@ -85,7 +88,8 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
     const PT* const prow = static_cast<const PT*>(part_row);
     const PT* const pcol = static_cast<const PT*>(part_col);
     const long long iux = O_PROF, irz = O_PROF + nz, isx = O_PROF + 3LL * nz, ifl = O_PROF + 4LL * nz,
-                    ips = O_PROF + 5LL * nz, ipx = ips + nx;
+                    ips = O_PROF + 5LL * nz, ipx = ips + nx, imx = ipx + nx, imz = imx + nz, iwb = imz + nz,
+                    iwt = iwb + nz;
     for (int k = lane; k < NSC; k += 32) wsc[warp][k] = R::zero();
     if (blk == 0 && t == 0) {  // the step kernels' flag of a bad density
         const bool bad = (flag[0] & 1) != 0;
@@ -95,29 +99,48 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
     if (blk < nrowblocks) {
         const int z = blk * WPB + warp;
         if (z < nz) {
-            int zl = z - 1, zr = z + 1;
+            // this row's lattice: its first compact row and height
+            int z0 = 0, nzi = nz;
+            if (inst) {
+                const int k = inst_of_row(inst, ninst, z);
+                z0 = inst[k].zrow0;
+                nzi = inst[k].nz;
+            }
+            const int zi = z - z0;  // row within the lattice
+            int zl = zi - 1, zr = zi + 1;
             PT wl = PT(0.5), wr = PT(0.5);
-            if (nz == 1) {
-                zl = zr = z;
+            if (nzi == 1) {
+                zl = zr = zi;
             } else if (zbc == 0) {
-                zl = z == 0 ? nz - 1 : z - 1;
-                zr = z == nz - 1 ? 0 : z + 1;
-            } else if (z == 0) {
+                zl = zi == 0 ? nzi - 1 : zi - 1;
+                zr = zi == nzi - 1 ? 0 : zi + 1;
+            } else if (zi == 0) {
                 zl = 0;
                 wl = wr = PT(1);
-            } else if (z == nz - 1) {
-                zr = nz - 1;
+            } else if (zi == nzi - 1) {
+                zr = nzi - 1;
                 wl = wr = PT(1);
             }
-            // the output entry of this lane (lanes 0..8), -1 for none
-            long long oi = -1;
+            zl += z0;
+            zr += z0;
+            // the output entries of this lane (lanes 0..8), -1 for none; the second is the wall
+            // force scalar of a single lattice
+            long long oi = -1, oi2 = -1;
             switch (lane) {
                 case QR_UX: oi = iux + z; break;
                 case QR_RHOA: oi = irz + z; break;
                 case QR_RHOB: oi = irz + nz + z; break;
                 case QR_SXZ: oi = isx + z; break;
-                case QR_WALLB: oi = (zbc && z == 0) ? O_WALL : -1; break;
-                case QR_WALLT: oi = (zbc && z == nz - 1) ? O_WALL + 1 : -1; break;
+                case QR_MX: oi = imx + z; break;
+                case QR_MZ: oi = imz + z; break;
+                case QR_WALLB:
+                    oi = iwb + z;
+                    oi2 = (!inst && zbc && z == 0) ? O_WALL : -1;
+                    break;
+                case QR_WALLT:
+                    oi = iwt + z;
+                    oi2 = (!inst && zbc && z == nz - 1) ? O_WALL + 1 : -1;
+                    break;
                 case NQR: oi = ifl + z; break;
                 default: break;
             }
@@ -132,6 +155,7 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
                 v[NQR + 1] += prow[((long long)zr * nxpart + p) * NQR + QR_UX];
             }
             const A old = (accumulate && oi >= 0) ? R::get(avg, oi) : R::zero();  // in flight with the sums
+            const A old2 = (accumulate && oi2 >= 0) ? R::get(avg, oi2) : R::zero();
 #pragma unroll
             for (int k = 0; k < NQR + 2; ++k) v[k] = warp_sum(v[k]);
             if (lane <= NQR) {
@@ -141,7 +165,7 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
                     if (lane == k) mine = v[k];
                 A val;
                 if (lane == NQR) {  // fluidity
-                    const PT gd = nz == 1 ? PT(0) : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
+                    const PT gd = nzi == 1 ? PT(0) : (wr * v[NQR + 1] - wl * v[NQR]) * inx;
                     val = R::from(gd / (v[QR_SXZ] * inx));
                 } else {
                     val = R::from(mine * inx);
@@ -153,6 +177,10 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
                 if (oi >= 0) {
                     R::put(out, oi, val);
                     if (accumulate) R::put(avg, oi, R::add(old, val));
+                }
+                if (oi2 >= 0) {
+                    R::put(out, oi2, val);
+                    if (accumulate) R::put(avg, oi2, R::add(old2, val));
                 }
             }
         }

@@ -29,7 +29,8 @@ class lbm_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("n_species", ctypes.c_int),
                 ("precision", ctypes.c_int), ("z_boundary", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("rows_per_warp", ctypes.c_int),
-                ("tile_rows", ctypes.c_int)]
+                ("tile_rows", ctypes.c_int), ("n_instances", ctypes.c_int),
+                ("inst_nz", ctypes.POINTER(ctypes.c_int))]
 
 
 class lbm_params(ctypes.Structure):
@@ -73,6 +74,8 @@ SIGNATURES = {
     "lbm_observables_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(lbm_params), _VP, _VP]),
     "lbm_selftest_wait": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "lbm_set_instance_drive": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
 }
 
 _lib = None
@@ -253,16 +256,42 @@ class Lattice:
     """One simulation on the GPU: create + params + fields, with numpy I/O."""
 
     def __init__(self, nx, nz, n_species=1, precision=LBM_FP64, z_boundary=LBM_PERIODIC,
-                 kernel=LBM_KERNEL_AUTO, device=0, stream=None, rows_per_warp=0, tile_rows=0, **params):
+                 kernel=LBM_KERNEL_AUTO, device=0, stream=None, rows_per_warp=0, tile_rows=0, instances=None,
+                 **params):
+        """instances: heights of the lattices of a batch (nz is then their sum; walls only)."""
         d = lbm_default_desc()
+        if instances is not None:
+            instances = [int(h) for h in instances]
+            nz = sum(instances)
+            self._inst_nz = (ctypes.c_int * len(instances))(*instances)  # alive while lbm_create reads it
+            d.n_instances, d.inst_nz = len(instances), self._inst_nz
         d.nx, d.nz, d.n_species, d.precision = nx, nz, n_species, precision
         d.z_boundary, d.kernel, d.device, d.rows_per_warp = z_boundary, kernel, device, rows_per_warp
         d.tile_rows = tile_rows
         d.stream = stream
         self.desc = d
         self.nx, self.nz, self.ns = nx, nz, n_species
+        self.instances = instances or [nz]
         self.h = lbm_create(d)
         self.set_params(**params)
+
+    def set_instance_drive(self, i, body_force=0.0, wall_u=(0.0, 0.0)):
+        _check(load().lbm_set_instance_drive(self.h, i, body_force, wall_u[0], wall_u[1]), self.h)
+
+    def instance_observables(self, i, averages=False):
+        """Observables of lattice i of the batch: scalars and its z profiles."""
+        nz = self.instances[i]
+        prof = dict(ux_z=np.zeros(nz), rho_z=np.zeros(self.ns * nz), sxz_z=np.zeros(nz), fluid_z=np.zeros(nz))
+        o = lbm_obs()
+        for k, v in prof.items():
+            setattr(o, k, v.ctypes.data_as(_DP))
+        _check(load().lbm_instance_observables(self.h, i, ctypes.byref(o), 1 if averages else 0), self.h)
+        res = dict(mass=np.array(o.mass[:]), momentum=np.array(o.momentum[:]),
+                   wall_force=np.array(o.wall_force[:]), nonfinite=bool(o.nonfinite), step=o.step,
+                   samples=o.samples)
+        prof["rho_z"] = prof["rho_z"].reshape(self.ns, nz)
+        res.update(prof)
+        return res
 
     def set_params(self, **params):
         self.params = make_params(**params)

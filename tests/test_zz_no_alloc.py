@@ -37,7 +37,7 @@ def test_noalloc_matches_lbm_observables_twice(zbc):
     lat = L.Lattice(nx, nz, ns, L.LBM_FP64, zbc, **prm)
     rho, _ = W.disk_packing(nx, nz, 0.7, seed=31 + zbc, r_mean=7, r_spread=2, periodic_z=(zbc == 0))
     lat.set_fields(rho)
-    out = torch.zeros(16 + 5 * nz + 2 * nx, dtype=torch.float64, device="cuda")
+    out = torch.zeros(16 + 9 * nz + 2 * nx, dtype=torch.float64, device="cuda")
     f = torch.zeros((ns, 9, nz, nx), dtype=torch.float64, device="cuda")
     for call in range(2):
         lat.step(7 + call)
