@@ -55,6 +55,9 @@ def _args():
                     help="rotate: step several lattices of the workload in turn, so that each step's input "
                          "was evicted from L2 by the others' traffic (no flush); flush: one lattice, a 256 MiB "
                          "write then a 256 MiB read between timed steps")
+    ap.add_argument("--autotune", type=int, default=0, metavar="STEPS",
+                    help="before timing, let the library pick the pull kernel's launch shape by timing STEPS "
+                         "steps of each (0 = the default shape)")
     ap.add_argument("--observe-every", type=int, default=1,
                     help="sample the observables every k steps (1 = every step, the full hot path; "
                          "0 = never, for analysis only)")
@@ -150,6 +153,17 @@ def kernel_source_hash(kernel):
     return h.hexdigest()
 
 
+def oracle_sample(w, n=256):
+    """The oracle's bounded sample of a workload: an n x n cut (of the tallest channel of a
+    batch, with its drive) as (rho, n_species, z_boundary, params)."""
+    if "instances" in w:
+        i = int(np.argmax(w["instances"]))
+        z0 = int(np.sum(w["instances"][:i]))
+        rho = w["rho"][:, z0:z0 + min(n, w["instances"][i]), :n]
+        return np.ascontiguousarray(rho), dict(w["params"], **w["drives"][i])
+    return np.ascontiguousarray(w["rho"][:, :n, :n]), dict(w["params"])
+
+
 def cpu_baseline(w, seconds=12.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
     whole oracle steps (step + observables, like the GPU step) on a 256 x 256 lattice cut from
@@ -158,8 +172,8 @@ def cpu_baseline(w, seconds=12.0):
 
     oracle.build()
     n = 256
-    rho = np.ascontiguousarray(w["rho"][:, :n, :n])
-    ref = oracle.RefLattice(n, n, w["n_species"], w["z_boundary"], **w["params"])
+    rho, prm = oracle_sample(w, n)
+    ref = oracle.RefLattice(n, rho.shape[1], w["n_species"], w["z_boundary"], **prm)
     ref.set_fields(rho)
     t0 = time.perf_counter()
     k = 0
@@ -171,7 +185,7 @@ def cpu_baseline(w, seconds=12.0):
             break
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(n * n * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+    return {"value": round(n * rho.shape[1] * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{k} oracle steps (step + observables) on a {n}x{n} cut of the workload, "
                       f"{dt:.1f} s wall, OpenMP threads={cores}"}
 
@@ -187,8 +201,8 @@ def run_reference(a, w):
         return
     oracle.build()
     n = 256
-    rho = np.ascontiguousarray(w["rho"][:, :n, :n])
-    ref = oracle.RefLattice(n, n, w["n_species"], w["z_boundary"], **w["params"])
+    rho, prm = oracle_sample(w, n)
+    ref = oracle.RefLattice(n, rho.shape[1], w["n_species"], w["z_boundary"], **prm)
     ref.set_fields(rho)
     for _ in range(a.warmup):
         ref.step(1)
@@ -199,7 +213,7 @@ def run_reference(a, w):
         ref.observables()
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    value = n * n * a.steps / dt / 1e6
+    value = n * rho.shape[1] * a.steps / dt / 1e6
     sample = f"{a.steps} timed oracle steps (step + observables) on a {n}x{n} cut of {a.workload}"
     print(json.dumps({
         "impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS",
@@ -251,7 +265,9 @@ def main():
     def make_lattice():
         lt = L.Lattice(nx, nz, ns, prec, w["z_boundary"], kernel=kern, device=local,
                        stream=stream.cuda_stream, rows_per_warp=a.rows_per_warp, tile_rows=a.tile_rows,
-                       **w["params"])
+                       instances=w.get("instances"), **w["params"])
+        for i, d in enumerate(w.get("drives", [])):
+            lt.set_instance_drive(i, d["body_force"], d["wall_u"])
         lt.set_fields(w["rho"])
         lt.set_observe(a.observe_every)  # 1: every step reduces the observables of the state it collides
         return lt
@@ -261,6 +277,10 @@ def main():
     n_rot = 1 if a.l2 == "flush" else max(1, min(8, -(-ROTATE_BYTES // lattice_bytes)))
     lats = [make_lattice() for _ in range(n_rot)]
     lat = lats[0]
+    depth = None
+    if a.autotune > 0:
+        for lt in lats:
+            depth, _ = lt.autotune(a.autotune)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
     flush_src = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
 
@@ -366,7 +386,9 @@ def main():
                           "one lattice; a 256 MiB write then a 256 MiB read between timed steps"),
                    "observables": ("every step" if a.observe_every == 1 else
                                    "never" if a.observe_every == 0 else f"every {a.observe_every} steps"),
-                   "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel},
+                   "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel,
+                   **({"instances": len(w["instances"])} if "instances" in w else {}),
+                   **({"pipeline_depth": depth} if depth is not None else {})},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -226,6 +226,15 @@ int lbm_set_instance_drive(lbm_ctx *c, int i, double body_force, double wall_u_b
    batch's column profiles average over all its lattices and are in lbm_observables). */
 int lbm_instance_observables(lbm_ctx *c, int i, lbm_obs *out, int averages);
 
+/* Autotuner (no counterpart in the paper).  Times the launch shapes of the PULL kernel on the
+   context's own lattices -- depth 1 (one tile load in flight per CTA, 3 CTAs per SM in FP32) and
+   depth 2 (two, 2 CTAs per SM) -- for `steps` steps each (1..10000) with the current sampling,
+   keeps the faster for the context, and puts the state, time sums and step count back, so the
+   simulation does not advance.  chosen (may be NULL) receives the depth kept (0 for the other
+   kernels, which have nothing to choose), ms_per_step[2] (may be NULL) the measured step times.
+   Synchronises. */
+int lbm_autotune(lbm_ctx *c, int steps, int *chosen, double *ms_per_step);
+
 /* Self-test of failure detection (no counterpart in the paper).  The step kernels' only
    device-side waits are bounded waits on TMA copies; an expired wait sets a flag that the next
    synchronising call reports as LBM_ETIMEOUT, and the kernel leaves without faulting.  This

@@ -55,7 +55,8 @@ struct lbm_ctx {
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
     alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
     alignas(64) unsigned char pmap_out[2][128] = {};  // pull: store descriptors of f[0], f[1]
-    int pull_grid[8] = {};                            // pull: resident CTAs per mode
+    int pull_grid[8][2] = {};                         // pull: resident CTAs per mode and depth
+    int stages = 2;                                   // pull: boxes in flight per CTA (1 or 2)
     // the lattices of a batch (one entry for a single lattice): host and device copies
     std::vector<InstGeom> inst;
     InstGeom* inst_d = nullptr;
@@ -373,11 +374,13 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
                                c->plane) != 0)
                 return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
         const int modes[4] = {M_WRITE, M_WRITE | M_OBS, M_OBS, M_FIELDS};
-        for (int m : modes) {
-            const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m) : pull_blocks_per_sm<float>(ns, m);
-            if (nb < 1) return bail(fail(c, LBM_ECUDA, "occupancy query of the pull kernel failed"));
-            c->pull_grid[m] = nb * c->nsm;
-        }
+        for (int m : modes)
+            for (int st = 1; st <= 2; ++st) {
+                const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m, st)
+                                                        : pull_blocks_per_sm<float>(ns, m, st);
+                if (nb < 1) return bail(fail(c, LBM_ECUDA, "occupancy query of the pull kernel failed"));
+                c->pull_grid[m][st - 1] = nb * c->nsm;
+            }
     }
     refresh_const(c);
     CKC(upload_inst(c));
@@ -531,11 +534,11 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const void* tout = c->pmap_out[cur ^ 1];
         const Batch B = batch(c);
         if (c->d.precision == LBM_FP64)
-            e = launch_pull<double>(c->d.n_species, mode, tin, tout, (double*)c->f[cur ^ 1], c->c64, O, Rd,
-                                    c->sched, B, c->pull_grid[mode], c->stream);
+            e = launch_pull<double>(c->d.n_species, mode, c->stages, tin, tout, (double*)c->f[cur ^ 1], c->c64, O,
+                                    Rd, c->sched, B, c->pull_grid[mode][c->stages - 1], c->stream);
         else
-            e = launch_pull<float>(c->d.n_species, mode, tin, tout, (float*)c->f[cur ^ 1], c->c32, O, Rd,
-                                   c->sched, B, c->pull_grid[mode], c->stream);
+            e = launch_pull<float>(c->d.n_species, mode, c->stages, tin, tout, (float*)c->f[cur ^ 1], c->c32, O,
+                                   Rd, c->sched, B, c->pull_grid[mode][c->stages - 1], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
@@ -920,5 +923,82 @@ extern "C" int lbm_selftest_wait(lbm_ctx* c, long long cycles) {
     CK(cudaMemcpyAsync(c->flag, &saved, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (flag & 2) return fail(c, LBM_ETIMEOUT, "the self-test wait expired after %lld cycles (expected)", cycles);
+    return LBM_OK;
+}
+
+// Autotuner of the pull kernel's launch shape: every candidate (pipeline depth 1 with 3 CTAs per
+// SM, depth 2 with 2) steps the context's own lattices `steps` times with the current sampling,
+// timed by events; the fastest is kept.  The state, the time sums and the step count are put
+// back afterwards, so tuning does not advance the simulation.
+extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_step) {
+    if (!c) return LBM_EINVAL;
+    if (steps < 1 || steps > 10000) return fail(c, LBM_EINVAL, "steps must be in [1, 10000]");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    if (!c->pull) {  // nothing to choose for the other kernels
+        if (chosen) *chosen = 0;
+        return LBM_OK;
+    }
+    CK(flush_pending(c));
+    const size_t fbytes = (size_t)c->d.n_species * 9 * c->plane * c->esize;
+    void* save = nullptr;
+    CK(cudaMalloc(&save, 2 * fbytes + obs_bytes(c) + sizeof(int)));
+    unsigned char* sv = static_cast<unsigned char*>(save);
+    cudaError_t e = cudaMemcpyAsync(sv, c->f[0], fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv + fbytes, c->f[1], fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv + 2 * fbytes, c->avg, obs_bytes(c), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv + 2 * fbytes + obs_bytes(c), c->flag, sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
+    const int cur = c->cur, saved_stages = c->stages;
+    const long long step = c->step, samples = c->samples, launches = c->launches;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    double best = 1e300, ms[2] = {0.0, 0.0};
+    int pick = saved_stages;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    for (int st = 1; st <= 2 && e == cudaSuccess; ++st) {
+        c->stages = st;
+        for (int k = 0; k < 2 + steps && e == cudaSuccess; ++k) {  // two warm-up steps, then the timed ones
+            if (k == 2) e = cudaEventRecord(a, c->stream);
+            const bool ob = c->observe_every > 0;
+            if (e == cudaSuccess) e = enqueue_pass(c, c->cur, M_WRITE | (ob ? M_OBS : 0), ob, ob, true);
+            c->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        ms[st - 1] = (double)t / steps;
+        if (e == cudaSuccess && ms[st - 1] < best) {
+            best = ms[st - 1];
+            pick = st;
+        }
+    }
+    // put the state back
+    c->pending = false;
+    c->cur = cur;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->f[0], sv, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->f[1], sv + fbytes, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->avg, sv + 2 * fbytes, obs_bytes(c), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->flag, sv + 2 * fbytes + obs_bytes(c), sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(save);
+    c->step = step;
+    c->samples = samples;
+    c->launches = launches;
+    c->profiling = prof;
+    c->stages = e == cudaSuccess ? pick : saved_stages;
+    drop_graphs(c);
+    CK(e);
+    if (chosen) *chosen = pick;
+    if (ms_per_step) {
+        ms_per_step[0] = ms[0];
+        ms_per_step[1] = ms[1];
+    }
     return LBM_OK;
 }

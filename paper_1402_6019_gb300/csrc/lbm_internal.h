@@ -139,18 +139,19 @@ constexpr int PULL_GX = 4, PULL_GZ = 3;
 // 128 bytes each.  Returns 0 on success.
 int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int prows, int pitch,
                    long long plane);
-// CTAs of the pull kernel resident per SM for a mode (sets the kernel's shared-memory limit on
-// the current device); 0 on failure.
+// CTAs of the pull kernel resident per SM for a mode and a pipeline depth (stages = boxes in
+// flight per CTA, 1 or 2; sets the kernel's shared-memory limit on the current device); 0 on
+// failure.
 template <typename T>
-int pull_blocks_per_sm(int ns, int mode);
+int pull_blocks_per_sm(int ns, int mode, int stages);
 // One pass of the pull kernel: loads through tin (a buffer's in_map), stores through tout (the
 // other buffer's out_map); fout is that other buffer (periodic images are stored to it
 // directly).  fold: a pending reduction run by the same launch.  sched: two counters, zero
 // before the launch and left zero by it.  grid_max: resident CTAs on the device.
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
-                        const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B, int grid_max,
-                        cudaStream_t st);
+cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, const void* tout, T* fout,
+                        const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
+                        int grid_max, cudaStream_t st);
 // One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st);
 // Fills the ghost columns and rows of a pull-layout buffer with the periodic images.

@@ -41,7 +41,8 @@ constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3 
 constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2 (padded z0 .. z0 + PZ + 5)
 constexpr int HW = PX + 4, HH = PZ + 4;   // psi/rho tile: x0 - 2 .. x0 + PX + 1, z0 - 2 .. z0 + PZ + 1
 constexpr int NRING = HW * HH - PX * PZ;  // psi/rho tile positions outside the tile
-constexpr int STAGES = 2;                 // boxes in flight per CTA: tiles are loaded two ahead
+// ST (template parameter): boxes in flight per CTA.  2: tiles are loaded two ahead, 2 CTAs per
+// SM in FP32; 1: one ahead, 3 CTAs per SM with fewer registers each.  Chosen by lbm_autotune.
 static_assert(NRING % PZ == 0 && NRING / PZ <= PX, "the ring shared evenly over the warps");
 static_assert(NT == RB_THREADS, "a CTA runs the reduction's work items");
 static_assert(PULL_GX == 4 && PULL_GZ == 3, "the box starts at padded (x0, z0)");
@@ -62,22 +63,22 @@ struct PsiTile<float, 2, true> {
     f2 rh[HH][HW];
 };
 
-template <typename T, int NS>
+template <typename T, int NS, int ST>
 struct PullSmem {
-    T box[STAGES][9 * NS][BZ][BX];     // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
+    T box[ST][9 * NS][BZ][BX];         // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
     alignas(128) T out[9 * NS][PZ][PX];  // TMA source: the tile's new stored values
     PsiTile<T, NS> q;
     T colsum[PZ][NQC][PX];
     typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
-    alignas(8) unsigned long long bar[STAGES];
-    int tile[STAGES];  // the tile each box holds (or is loading)
-    int inst[STAGES];  // and the lattice of the batch it belongs to
+    alignas(8) unsigned long long bar[ST];
+    int tile[ST];  // the tile each box holds (or is loading)
+    int inst[ST];  // and the lattice of the batch it belongs to
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-template <typename T, int NS>
-__device__ __forceinline__ void issue_load(PullSmem<T, NS>& S, const CUtensorMap* map, int x, int z, int sl) {
+template <typename T, int NS, int ST>
+__device__ __forceinline__ void issue_load(PullSmem<T, NS, ST>& S, const CUtensorMap* map, int x, int z, int sl) {
     constexpr unsigned bytes = (unsigned)(sizeof(T) * 9 * NS * BZ * BX);
     const unsigned bar = smem_u32(&S.bar[sl]);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
@@ -117,15 +118,15 @@ __global__ void k_wait_selftest(int* flag, long long limit) {
 // Post-streaming populations at box position (bx, bz): the gather of the pull layout.  lo / hi:
 // the site is the bottom / top row next to a wall, where populations coming from beyond the
 // wall are the site's own reflected values.
-template <typename T, int NS>
-__device__ __forceinline__ void gather(const PullSmem<T, NS>& S, int sl, int bx, int bz, T (&f)[NS][9]) {
+template <typename T, int NS, int ST>
+__device__ __forceinline__ void gather(const PullSmem<T, NS, ST>& S, int sl, int bx, int bz, T (&f)[NS][9]) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int l = 0; l < 9; ++l) f[s][l] = S.box[sl][s * 9 + l][bz - cz(l)][bx - cx(l)];
 }
-template <typename T, int NS>
-__device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int sl, int bx, int bz, bool lo, bool hi,
+template <typename T, int NS, int ST>
+__device__ __forceinline__ void gather_wall(const PullSmem<T, NS, ST>& S, int sl, int bx, int bz, bool lo, bool hi,
                                             T (&f)[NS][9]) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -140,8 +141,8 @@ __device__ __forceinline__ void gather_wall(const PullSmem<T, NS>& S, int sl, in
 // tile: the ring, and the padding of ragged tiles.  With walls, rows beyond a wall take the
 // mirror image (or zero, Sec. IV's two readings of the ghost rows).  Positions that no live
 // site reads (far padding of ragged tiles) are set to zero.
-template <typename T, int NS>
-__device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const StepConst<T>& C, const PairConst& K,
+template <typename T, int NS, int ST>
+__device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, const StepConst<T>& C, const PairConst& K,
                                              int px, int pz, int z0, int nz) {
     const int Z = z0 - 2 + pz;
     int Zs = Z;
@@ -161,9 +162,9 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const S
         T g[NS][9];
         const bool lo = C.zbc && Zs == 0, hi = C.zbc && Zs == nz - 1;
         if (lo || hi)
-            gather_wall<T, NS>(S, sl, bx, bz, lo, hi, g);
+            gather_wall<T, NS, ST>(S, sl, bx, bz, lo, hi, g);
         else
-            gather<T, NS>(S, sl, bx, bz, g);
+            gather<T, NS, ST>(S, sl, bx, bz, g);
 #pragma unroll
         for (int s = 0; s < NS; ++s) sum[s] = sum9(g[s]);
     }
@@ -184,8 +185,8 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS>& S, int sl, const S
 // The periodic images of site (x, z) of a lattice of nz rows whose row -PULL_GZ is padded row
 // prow0: plain stores of its new values (read back from the staging tile) into the ghost columns
 // (and, without walls, ghost rows) that wrap onto it.
-template <typename T, int NS>
-__device__ __noinline__ void write_images(const PullSmem<T, NS>& S, const StepConst<T>& C, T* __restrict__ fout,
+template <typename T, int NS, int ST>
+__device__ __noinline__ void write_images(const PullSmem<T, NS, ST>& S, const StepConst<T>& C, T* __restrict__ fout,
                                           int x, int z, int nz, int prow0, int tx, int tz) {
     const int nx = C.nx;
     int xs[2 * PULL_GX + 1], zs[2 * PULL_GZ + 1];
@@ -210,13 +211,13 @@ __device__ __noinline__ void write_images(const PullSmem<T, NS>& S, const StepCo
         }
 }
 
-template <typename T, int NS, int MODE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+template <typename T, int NS, int MODE, int ST>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
            const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    PullSmem<T, NS>& S = *reinterpret_cast<PullSmem<T, NS>*>(smem_raw);
+    PullSmem<T, NS, ST>& S = *reinterpret_cast<PullSmem<T, NS, ST>*>(smem_raw);
     const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
     // nz: rows of all lattices; ntz: their tile rows; tiles are numbered lattice by lattice
     const int nx = C.nx, nz = C.nz;
@@ -246,12 +247,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     int upcoming = 0;
 
     if (tid == 0) {
-        for (int sl = 0; sl < STAGES; ++sl)
+        for (int sl = 0; sl < ST; ++sl)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.bar[sl])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        // the first STAGES tiles go into the boxes at once (padded (x0, z0) is the box origin)
+        // the first ST tiles go into the boxes at once (padded (x0, z0) is the box origin)
         bool more = true;
-        for (int sl = 0; sl < STAGES; ++sl) {
+        for (int sl = 0; sl < ST; ++sl) {
             const int t0 = more ? (int)atomicAdd(&sched[0], 1u) : ntiles;
             S.tile[sl] = t0;
             more = t0 < ntiles;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     unsigned parity = 0;  // bit sl: phase of box sl's barrier
     bool failed = false;
     for (int k = 0;; ++k) {
-        const int sl = k % STAGES;
+        const int sl = k % ST;
         const int t = S.tile[sl];
         if (t >= ntiles) break;
         // this tile's lattice: rows, first compact row, first padded row, first tile, drive
@@ -296,9 +297,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         if (live) {
             const bool lo = C.zbc && z == 0, hi = C.zbc && z == lnz - 1;
             if (lo || hi)
-                gather_wall<T, NS>(S, sl, tx + 4, tz + 3, lo, hi, f);
+                gather_wall<T, NS, ST>(S, sl, tx + 4, tz + 3, lo, hi, f);
             else
-                gather<T, NS>(S, sl, tx + 4, tz + 3, f);
+                gather<T, NS, ST>(S, sl, tx + 4, tz + 3, f);
             if constexpr (kPair<T, NS>) {
                 f2 fp[9];
 #pragma unroll
@@ -319,19 +320,19 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                 }
             }
         } else {
-            side_density<T, NS>(S, sl, C, K, tx + 2, tz + 2, z0, lnz);
+            side_density<T, NS, ST>(S, sl, C, K, tx + 2, tz + 2, z0, lnz);
         }
-        if (ring) side_density<T, NS>(S, sl, C, K, rpx, rpz, z0, lnz);
+        if (ring) side_density<T, NS, ST>(S, sl, C, K, rpx, rpz, z0, lnz);
         if ((MODE & M_WRITE) && tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
-        // box sl is free: start the load of the tile STAGES ahead (drawn during the last tile)
+        // box sl is free: start the load of the tile ST ahead (drawn during the last tile)
         // and draw the one after it
         if (tid == 0) {
             const int tn = upcoming;
-            S.tile[sl] = tn;  // read by all after the barrier that ends tile k + STAGES - 1
+            S.tile[sl] = tn;  // read by all after the barrier that ends tile k + ST - 1
             if (tn < ntiles) {
                 const int kn = ninst > 1 ? inst_of_tile(inst, ninst, tn) : 0;
                 S.inst[sl] = kn;
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
                 for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
             }
             if (live && (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= lnz - PULL_GZ))))
-                write_images<T, NS>(S, C, fout, x, z, lnz, prow0, tx, tz);
+                write_images<T, NS, ST>(S, C, fout, x, z, lnz, prow0, tx, tz);
         }
         if (MODE & M_OBS) {
             // per-column sums over the PZ rows of the tile
@@ -599,7 +600,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             atomicOr(O.flag, 2);
             // loads still in flight (the one that did not arrive in time, the one after it) before
             // the CTA exits
-            for (int sl = 0; sl < STAGES; ++sl)
+            for (int sl = 0; sl < ST; ++sl)
                 if (S.tile[sl] < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
         }
         asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
@@ -613,18 +614,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
 }
 
-template <typename T, int NS, int MODE>
+template <typename T, int NS, int MODE, int ST>
 int pull_occupancy() {
-    const size_t smem = sizeof(PullSmem<T, NS>);
-    if (cudaFuncSetAttribute(k_pull<T, NS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const size_t smem = sizeof(PullSmem<T, NS, ST>);
+    if (cudaFuncSetAttribute(k_pull<T, NS, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pull<T, NS, MODE>, NT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pull<T, NS, MODE, ST>, NT, smem) != cudaSuccess) return 0;
     return nb;
 }
 
-template <typename T, int NS, int MODE>
+template <typename T, int NS, int MODE, int ST>
 cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepConst<T>& C, const ObsPtrs& O,
                         const Fold& Rd, unsigned* sched, const Batch& B, int grid_max, cudaStream_t st) {
     const int ntx = (C.nx + PX - 1) / PX;
@@ -633,22 +634,22 @@ cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepCo
     if (Rd.enabled && grid < 1) grid = 1;
     PairConst K{};
     if constexpr (kPair<T, NS>) fill_pair_const(K, C);
-    k_pull<T, NS, MODE><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS>), st>>>(
+    k_pull<T, NS, MODE, ST><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS, ST>), st>>>(
         *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, B.inst,
         B.ninst, ntx, B.ntz);
     return cudaGetLastError();
 }
 
-template <typename T, int NS>
+template <typename T, int NS, int ST>
 cudaError_t launch_ns(int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
                       const ObsPtrs& O, const Fold& Rd, unsigned* sched, const Batch& B, int grid_max,
                       cudaStream_t st) {
     switch (mode) {
-        case M_WRITE: return launch_mode<T, NS, M_WRITE>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+        case M_WRITE: return launch_mode<T, NS, M_WRITE, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
         case M_WRITE | M_OBS:
-            return launch_mode<T, NS, M_WRITE | M_OBS>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
-        case M_OBS: return launch_mode<T, NS, M_OBS>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
-        case M_FIELDS: return launch_mode<T, NS, M_FIELDS>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+            return launch_mode<T, NS, M_WRITE | M_OBS, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+        case M_OBS: return launch_mode<T, NS, M_OBS, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+        case M_FIELDS: return launch_mode<T, NS, M_FIELDS, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -685,33 +686,41 @@ __global__ void k_images(int ns, T* __restrict__ f, const StepConst<T> C, const 
 
 }  // namespace
 
-template <typename T>
-int pull_blocks_per_sm(int ns, int mode) {
+template <typename T, int ST>
+int blocks_per_sm(int ns, int mode) {
     if (ns == 1) {
         switch (mode) {
-            case M_WRITE: return pull_occupancy<T, 1, M_WRITE>();
-            case M_WRITE | M_OBS: return pull_occupancy<T, 1, M_WRITE | M_OBS>();
-            case M_OBS: return pull_occupancy<T, 1, M_OBS>();
-            case M_FIELDS: return pull_occupancy<T, 1, M_FIELDS>();
+            case M_WRITE: return pull_occupancy<T, 1, M_WRITE, ST>();
+            case M_WRITE | M_OBS: return pull_occupancy<T, 1, M_WRITE | M_OBS, ST>();
+            case M_OBS: return pull_occupancy<T, 1, M_OBS, ST>();
+            case M_FIELDS: return pull_occupancy<T, 1, M_FIELDS, ST>();
             default: return 0;
         }
     }
     switch (mode) {
-        case M_WRITE: return pull_occupancy<T, 2, M_WRITE>();
-        case M_WRITE | M_OBS: return pull_occupancy<T, 2, M_WRITE | M_OBS>();
-        case M_OBS: return pull_occupancy<T, 2, M_OBS>();
-        case M_FIELDS: return pull_occupancy<T, 2, M_FIELDS>();
+        case M_WRITE: return pull_occupancy<T, 2, M_WRITE, ST>();
+        case M_WRITE | M_OBS: return pull_occupancy<T, 2, M_WRITE | M_OBS, ST>();
+        case M_OBS: return pull_occupancy<T, 2, M_OBS, ST>();
+        case M_FIELDS: return pull_occupancy<T, 2, M_FIELDS, ST>();
         default: return 0;
     }
 }
 
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
-                        const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B, int grid_max,
-                        cudaStream_t st) {
+int pull_blocks_per_sm(int ns, int mode, int stages) {
+    return stages == 1 ? blocks_per_sm<T, 1>(ns, mode) : blocks_per_sm<T, 2>(ns, mode);
+}
+
+template <typename T>
+cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, const void* tout, T* fout,
+                        const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
+                        int grid_max, cudaStream_t st) {
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
-    return ns == 1 ? launch_ns<T, 1>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st)
-                   : launch_ns<T, 2>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st);
+    if (stages == 1)
+        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st)
+                       : launch_ns<T, 2, 1>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st);
+    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st)
+                   : launch_ns<T, 2, 2>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st);
 }
 
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
@@ -748,11 +757,11 @@ int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns
     return r == CUDA_SUCCESS ? 0 : 2;
 }
 
-template int pull_blocks_per_sm<float>(int, int);
-template int pull_blocks_per_sm<double>(int, int);
-template cudaError_t launch_pull<float>(int, int, const void*, const void*, float*, const StepConst<float>&,
+template int pull_blocks_per_sm<float>(int, int, int);
+template int pull_blocks_per_sm<double>(int, int, int);
+template cudaError_t launch_pull<float>(int, int, int, const void*, const void*, float*, const StepConst<float>&,
                                         const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
-template cudaError_t launch_pull<double>(int, int, const void*, const void*, double*, const StepConst<double>&,
+template cudaError_t launch_pull<double>(int, int, int, const void*, const void*, double*, const StepConst<double>&,
                                          const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
 template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, const Batch&, cudaStream_t);
 template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, const Batch&, cudaStream_t);

@@ -76,6 +76,7 @@ SIGNATURES = {
     "lbm_selftest_wait": (ctypes.c_int, [_VP, ctypes.c_longlong]),
     "lbm_set_instance_drive": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
+    "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -274,6 +275,14 @@ class Lattice:
         self.instances = instances or [nz]
         self.h = lbm_create(d)
         self.set_params(**params)
+
+    def autotune(self, steps=20):
+        """Pick the pull kernel's launch shape by timing it here; returns (depth, ms per step of
+        depth 1 and 2).  The state is left as it was."""
+        chosen = ctypes.c_int(0)
+        ms = (ctypes.c_double * 2)()
+        _check(load().lbm_autotune(self.h, steps, ctypes.byref(chosen), ms), self.h)
+        return chosen.value, (ms[0], ms[1])
 
     def set_instance_drive(self, i, body_force=0.0, wall_u=(0.0, 0.0)):
         _check(load().lbm_set_instance_drive(self.h, i, body_force, wall_u[0], wall_u[1]), self.h)

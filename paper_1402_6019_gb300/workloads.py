@@ -134,4 +134,18 @@ def workload(name: str, seed: int = 1402):
             p["body_force"] = 1e-6
         return dict(nx=2048, nz=256, n_species=2, z_boundary=1, params=p, rho=rho,
                     note=f"2048x256 walled channel, packing {frac:.3f}")
+    if name == "channel_sweep_48":
+        # the width and drive sweep behind the cooperative-length analysis (Sec. V): channels of
+        # height H = 32, 64, ..., 512 and length 1024, each under body forces 1e-6, 3e-6, 1e-5,
+        # every channel with its own seeded packing at fraction 0.85
+        heights, drives, rhos = [], [], []
+        for k, h in enumerate(range(32, 513, 32)):
+            for j, g in enumerate((1e-6, 3e-6, 1e-5)):
+                r, _ = disk_packing(1024, h, 0.85, seed + 97 * k + j, periodic_z=False)
+                heights.append(h)
+                drives.append(dict(body_force=g, wall_u=(0.0, 0.0)))
+                rhos.append(r)
+        return dict(nx=1024, nz=sum(heights), n_species=2, z_boundary=1, params=dict(EMULSION_PARAMS),
+                    rho=np.concatenate(rhos, axis=1), instances=heights, drives=drives,
+                    note="48 walled channels, 1024 x (32, 64, ..., 512) x 3 body forces, packing 0.85")
     raise KeyError(name)

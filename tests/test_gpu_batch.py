@@ -103,3 +103,27 @@ def test_batch_validation():
         lat.set_instance_drive(2, 1e-6)
     with pytest.raises(L.LbmError):
         lat.set_instance_drive(0, float("nan"))
+
+
+def test_autotune_keeps_state_and_results():
+    """Tuning times both launch shapes on the lattice itself, then puts the state back; the shape
+    kept changes the schedule of the tiles, not their arithmetic."""
+    nx = 96
+    rho = np.concatenate([channel_rho(nx, h, 5 + i) for i, h in enumerate(HEIGHTS)], axis=1)
+    lats = []
+    for tune in (False, True):
+        lat = L.Lattice(nx, None, 2, L.LBM_FP32, L.LBM_BOUNCEBACK, instances=HEIGHTS, **W.EMULSION_PARAMS)
+        lat.set_fields(rho)
+        lat.set_observe(1)
+        lat.step(7)
+        lats.append(lat)
+    before = lats[1].fields()[2]
+    depth, ms = lats[1].autotune(steps=5)
+    assert depth in (1, 2) and ms[0] > 0 and ms[1] > 0
+    assert np.array_equal(lats[1].fields()[2], before)
+    for lat in lats:
+        lat.step(9)
+    assert np.array_equal(lats[0].fields()[2], lats[1].fields()[2])
+    a, b = lats[0].averages(), lats[1].averages()
+    assert a["samples"] == b["samples"] == 16
+    assert np.array_equal(a["ux_z"], b["ux_z"])
