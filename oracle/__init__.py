@@ -106,6 +106,7 @@ def _load():
             lib.lbmref_tables.restype = None
             lib.lbmref_feq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]
             lib.lbmref_feq.restype = None
+            lib.lbmref_adjoint_step.argtypes = [vp, _DP, _DP, _DP]
             _lib = lib
     return _lib
 
@@ -217,6 +218,15 @@ class RefLattice:
                                            _ptr(out["sxz"])) == 0
         return out
 
+    def adjoint_step(self, lam_next, grad=None):
+        """dJ/df_n from dJ/df_{n+1} at the current state (periodic lattices); adds the
+        parameter derivatives to grad (G1 A, B; G2 A, B; G_AB; tau A, B; body_force)."""
+        lam_next = np.ascontiguousarray(lam_next, dtype=np.float64).reshape(self.ns, 9, self.nz, self.nx)
+        lam = np.zeros_like(lam_next)
+        grad = np.zeros(NPARAM) if grad is None else grad
+        assert self.lib.lbmref_adjoint_step(self.h, _ptr(lam_next), _ptr(lam), _ptr(grad)) == 0
+        return lam, grad
+
     def observables(self):
         nz, nx = self.nz, self.nx
         prof = dict(ux_z=np.zeros(nz), rho_z=np.zeros(self.ns * nz), sxz_z=np.zeros(nz),
@@ -231,3 +241,53 @@ class RefLattice:
         prof["rho_z"] = prof["rho_z"].reshape(self.ns, nz)
         res.update(prof)
         return res
+
+
+# ---------------------------------------------------------------------------------------
+# Calibration objective and its gradient through a run (the adjoint written out plainly)
+# ---------------------------------------------------------------------------------------
+NPARAM = 8  # G1 A, G1 B, G2 A, G2 B, G_AB, tau A, tau B, body_force
+
+
+def profile_objective(f, target_u, target_rho):
+    """J = sum_z (ubar(z) - target_u(z))^2 + (rhobar_A(z) - target_rho(z))^2 for the populations
+    f [ns, 9, nz, nx]: ubar = x-average of u = sum_s j_x,s / sum_s rho_s, rhobar_A = x-average of
+    rho_A.  Returns (J, dJ/df)."""
+    cq, _ = tables()[1:3]
+    cx = np.array([c[0] for c in cq], dtype=float)
+    ns, _, nz, nx = f.shape
+    rho = f.sum(axis=1)                                 # [ns, nz, nx]
+    jx = np.einsum("l,slzx->szx", cx, f)
+    rt = rho.sum(axis=0)
+    u = jx.sum(axis=0) / rt                             # [nz, nx]
+    du = u.mean(axis=1) - target_u                      # [nz]
+    dr = rho[0].mean(axis=1) - target_rho
+    J = float((du ** 2).sum() + (dr ** 2).sum())
+    # dJ/du(x, z) = 2 du(z) / nx; du/df_s,l = (c_lx - u) / rho_tot; dJ/drho_A(x, z) = 2 dr(z) / nx
+    gu = (2.0 * du / nx)[:, None] / rt                  # [nz, nx]
+    g = np.empty_like(f)
+    for s in range(ns):
+        for l in range(9):
+            g[s, l] = gu * (cx[l] - u) + (2.0 * dr / nx)[:, None] * (1.0 if s == 0 else 0.0)
+    return J, g
+
+
+def rollout_gradient(nx, nz, ns, rho_init, steps, target_u, target_rho, **params):
+    """J after `steps` oracle steps from the equilibrium at rest with densities rho_init, and
+    its gradient with respect to rho_init [ns, nz, nx] and the parameters (NPARAM entries),
+    by the discrete adjoint: forward storing every state, then lambda backwards."""
+    ref = RefLattice(nx, nz, ns, PERIODIC, **params)
+    ref.set_fields(rho_init)
+    states = []
+    for _ in range(steps):
+        states.append(ref.fields()[2])
+        ref.step(1)
+    J, lam = profile_objective(ref.fields()[2], target_u, target_rho)
+    grad = np.zeros(NPARAM)
+    for f in reversed(states):
+        ref.set_populations(f)
+        lam, grad = ref.adjoint_step(lam, grad)
+    # the initial populations are W_l rho_init (equilibrium at rest)
+    wq = tables()[2]
+    g_rho = np.einsum("l,slzx->szx", wq, lam)
+    return J, g_rho, grad

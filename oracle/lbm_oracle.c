@@ -623,3 +623,145 @@ int lbmref_observables(lbmref_ctx *c, lbmref_obs *o) {
     free(ux); free(sx); free(rz); free(ps); free(px);
     return LBMREF_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Discrete adjoint of one step (periodic lattice)                           */
+/* ------------------------------------------------------------------------- */
+
+/* Vector-Jacobian product of one step f_n -> f_{n+1} = S(f_n; theta) at the state
+   held by the context: given lam_next = dJ/df_{n+1}, writes lam = dJ/df_n and adds
+   dJ/dtheta to grad[LBMREF_NPARAM] (G1[A], G1[B], G2[A], G2[B], G_AB, tau[A], tau[B],
+   body_force).  Each forward stage of the step (moments, pseudopotential, force,
+   common velocity, shifted equilibrium, relaxation, streaming) is differentiated by
+   hand and applied in reverse order, with plain loops and the neighbour terms of
+   the force scattered back to the neighbours they came from. */
+int lbmref_adjoint_step(lbmref_ctx *c, const double *lam_next, double *lam, double *grad) {
+    if (!c || !lam_next || !lam || !grad) return LBMREF_EINVAL;
+    if (c->zbc != LBMREF_PERIODIC) return LBMREF_EINVAL;
+    const size_t n = nsites(c);
+    const int ns = c->ns;
+    prepare(c); /* rho, j, psi, F of the state f_n */
+    double *mu = calloc((size_t)ns * 9 * n, sizeof(double));  /* dJ/d(post-collision) */
+    double *dF = calloc((size_t)ns * 2 * n, sizeof(double));  /* dJ/dF_s (x, z)       */
+    double *drho = calloc((size_t)ns * n, sizeof(double));    /* dJ/drho_s            */
+    double *dpsi = calloc((size_t)ns * n, sizeof(double));    /* dJ/dpsi_s            */
+    double *djx = calloc((size_t)ns * n, sizeof(double));     /* dJ/dj_s              */
+    double *djz = calloc((size_t)ns * n, sizeof(double));
+    if (!mu || !dF || !drho || !dpsi || !djx || !djz) {
+        free(mu), free(dF), free(drho), free(dpsi), free(djx), free(djz);
+        return LBMREF_ENOMEM;
+    }
+    /* streaming, transposed: the post-collision g_l(x) became f_l(x + c_l) */
+    for (int s = 0; s < ns; ++s)
+        for (int l = 0; l < 9; ++l)
+            for (int z = 0; z < c->nz; ++z)
+                for (int x = 0; x < c->nx; ++x)
+                    pop(c, mu, s, l)[site(c, x, z)] =
+                        lam_next[((size_t)s * 9 + l) * n + site(c, wrap(x + CX[l], c->nx), wrap(z + CZ[l], c->nz))];
+    /* relaxation, equilibrium, shifted velocity, common velocity: site by site */
+    for (size_t i = 0; i < n; ++i) {
+        double numx = 0.0, numz = 0.0, den = 0.0;
+        for (int k = 0; k < ns; ++k) {
+            numx += c->jx[k * n + i] / c->p.tau[k];
+            numz += c->jz[k * n + i] / c->p.tau[k];
+            den += c->rho[k * n + i] / c->p.tau[k];
+        }
+        const double upx = numx / den, upz = numz / den;
+        double dupx = 0.0, dupz = 0.0; /* dJ/du' */
+        for (int s = 0; s < ns; ++s) {
+            const double r = c->rho[s * n + i], tau = c->p.tau[s];
+            const double Fx = c->Fx[s * n + i], Fz = c->Fz[s * n + i];
+            const double ux = upx + tau * Fx / r, uz = upz + tau * Fz / r;
+            double feq[9];
+            lbmref_feq(r, ux, uz, feq);
+            /* g_l = f_l - (f_l - feq_l)/tau */
+            double dfeq[9];
+            for (int l = 0; l < 9; ++l) {
+                const double m = pop(c, mu, s, l)[i];
+                const double fl = pop(c, c->f, s, l)[i];
+                dfeq[l] = m / tau;
+                grad[5 + s] += m * (fl - feq[l]) / (tau * tau);
+            }
+            /* feq_l = W_l rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u) */
+            double ar = 0.0, aux = 0.0, auz = 0.0;
+            for (int l = 0; l < 9; ++l) {
+                const double cu = CX[l] * ux + CZ[l] * uz;
+                ar += dfeq[l] * WLB[l] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uz * uz));
+                aux += dfeq[l] * WLB[l] * r * (3.0 * CX[l] + 9.0 * cu * CX[l] - 3.0 * ux);
+                auz += dfeq[l] * WLB[l] * r * (3.0 * CZ[l] + 9.0 * cu * CZ[l] - 3.0 * uz);
+            }
+            /* u_s = u' + tau F_s / rho_s */
+            dupx += aux;
+            dupz += auz;
+            dF[(s * 2 + 0) * n + i] = aux * tau / r;
+            dF[(s * 2 + 1) * n + i] = auz * tau / r;
+            drho[s * n + i] += ar - (aux * Fx + auz * Fz) * tau / (r * r);
+            grad[5 + s] += (aux * Fx + auz * Fz) / r;
+        }
+        /* u' = sum_k j_k / tau_k / sum_k rho_k / tau_k */
+        const double dnx = dupx / den, dnz = dupz / den, dden = -(dupx * upx + dupz * upz) / den;
+        for (int k = 0; k < ns; ++k) {
+            const double tk = c->p.tau[k];
+            djx[k * n + i] += dnx / tk;
+            djz[k * n + i] += dnz / tk;
+            drho[k * n + i] += dden / tk;
+            grad[5 + k] += -(c->jx[k * n + i] * dnx + c->jz[k * n + i] * dnz + c->rho[k * n + i] * dden) / (tk * tk);
+        }
+    }
+    /* the force of Eq. FORCE, the cross term and the drive, scattered back */
+    for (int s = 0; s < ns; ++s) {
+        const double *psi = c->psi + s * n;
+        for (int z = 0; z < c->nz; ++z)
+            for (int x = 0; x < c->nx; ++x) {
+                const size_t i = site(c, x, z);
+                const double bx = dF[(s * 2 + 0) * n + i], bz = dF[(s * 2 + 1) * n + i];
+                const double r = c->rho[s * n + i];
+                /* F = -G1 psi(x) sum w psi(x+c) c - G2 psi(x) sum p psi(x+c) c */
+                double ax = 0.0, az = 0.0, rx = 0.0, rz = 0.0;
+                for (int l = 1; l <= 24; ++l) {
+                    const size_t j = site(c, wrap(x + LX[l], c->nx), wrap(z + LZ[l], c->nz));
+                    const int q = LX[l] * LX[l] + LZ[l] * LZ[l];
+                    const double bc = bx * LX[l] + bz * LZ[l];
+                    const double wa = l <= c->na ? c->wa[q] : 0.0, wr = c->wr[q];
+                    ax += wa * psi[j] * LX[l];
+                    az += wa * psi[j] * LZ[l];
+                    rx += wr * psi[j] * LX[l];
+                    rz += wr * psi[j] * LZ[l];
+                    dpsi[s * n + j] += -psi[i] * (c->p.G1[s] * wa + c->p.G2[s] * wr) * bc;
+                }
+                dpsi[s * n + i] += -(c->p.G1[s] * (bx * ax + bz * az) + c->p.G2[s] * (bx * rx + bz * rz));
+                grad[0 + s] += -psi[i] * (bx * ax + bz * az);
+                grad[2 + s] += -psi[i] * (bx * rx + bz * rz);
+                /* cross: F_s += -G_AB rho_s(x) sum w8 rho_s'(x+c) c */
+                if (ns == 2) {
+                    const double *rho_o = c->rho + (1 - s) * n;
+                    double cx = 0.0, cz = 0.0;
+                    for (int l = 1; l <= 8; ++l) {
+                        const size_t j = site(c, wrap(x + LX[l], c->nx), wrap(z + LZ[l], c->nz));
+                        const double wl = c->wc[LX[l] * LX[l] + LZ[l] * LZ[l]];
+                        cx += wl * rho_o[j] * LX[l];
+                        cz += wl * rho_o[j] * LZ[l];
+                        drho[(1 - s) * n + j] += -c->p.G_AB * r * wl * (bx * LX[l] + bz * LZ[l]);
+                    }
+                    drho[s * n + i] += -c->p.G_AB * (bx * cx + bz * cz);
+                    grad[4] += -r * (bx * cx + bz * cz);
+                }
+                /* drive: F_s += rho_s g x */
+                drho[s * n + i] += bx * c->p.body_force;
+                grad[7] += r * bx;
+            }
+    }
+    /* pseudopotential, then the moments rho = sum f, j = sum f c */
+    for (int s = 0; s < ns; ++s)
+        for (size_t i = 0; i < n; ++i) {
+            const double r = c->rho[s * n + i];
+            const double dpr = c->p.psi_form == LBMREF_PSI_EXP ? exp(-r / c->p.rho0[s]) / c->p.rho0[s] : 1.0;
+            const double dr = drho[s * n + i] + dpr * dpsi[s * n + i];
+            const double tau = c->p.tau[s];
+            for (int l = 0; l < 9; ++l)
+                lam[((size_t)s * 9 + l) * n + i] = (1.0 - 1.0 / tau) * pop(c, mu, s, l)[i] + dr +
+                                                   djx[s * n + i] * CX[l] + djz[s * n + i] * CZ[l];
+        }
+    free(mu), free(dF), free(drho), free(dpsi), free(djx), free(djz);
+    return LBMREF_OK;
+}

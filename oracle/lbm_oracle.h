@@ -79,6 +79,14 @@ int  lbmref_site_fields(lbmref_ctx *c, double *psi, double *F, double *sint,
 long long lbmref_step_count(const lbmref_ctx *c);
 void lbmref_destroy(lbmref_ctx *c);
 
+/* Discrete adjoint of one step on a periodic lattice (EINVAL with walls), linearised at
+   the context's current state f_n (set it with lbmref_set_populations): from
+   lam_next = dJ/df_{n+1} [ns][9][nz][nx] it writes lam = dJ/df_n and adds to
+   grad[LBMREF_NPARAM] the derivatives with respect to, in order: G1[A], G1[B], G2[A],
+   G2[B], G_AB, tau[A], tau[B], body_force.  The state is left unchanged. */
+enum { LBMREF_NPARAM = 8 };
+int  lbmref_adjoint_step(lbmref_ctx *c, const double *lam_next, double *lam, double *grad);
+
 /* Tables.  c25 [25][2] link vectors (row 0 unused); cq [9][2] and wq [9] D2Q9;
    wsh [3][9] interaction weights by |c|^2 for (attraction, repulsion, cross) under
    the given preset, before weight_norm. */
