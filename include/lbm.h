@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 2
+#define LBM_ABI_VERSION 3
 
 /* status codes */
 enum {
@@ -244,6 +244,41 @@ int lbm_autotune(lbm_ctx *c, int steps, int *chosen, double *ms_per_step);
    (the wait did not expire: a defect), LBM_EINVAL or LBM_ECUDA.  The flag is cleared again so
    that the context's later calls are unaffected. */
 int lbm_selftest_wait(lbm_ctx *c, long long cycles);
+
+/* Set the state from populations after streaming, f [n_species][9][nz][nx] FP64 (the layout
+   lbm_get_fields writes): restores a state read earlier, e.g. a checkpoint of a run that is
+   recomputed for its adjoint.  The values are not checked: a density <= 0 or a NaN shows as
+   LBM_ENONFINITE after the next step.  FP32 contexts store deviations from the parameters'
+   rho_ref when it is >= 0, else from the reference densities of the last lbm_set_fields
+   (LBM_EINVAL if there was none).  Resets the step counter and the time averages.
+   Synchronises. */
+int lbm_set_populations(lbm_ctx *c, const double *f, int where);
+
+/* Discrete adjoint (no counterpart in the paper: it differentiates the step of Eq. LB with the
+   forces of Eq. FORCE and Sec. IV so that the couplings, relaxation times, drive and initial
+   densities can be fitted to target profiles like those of Sec. IV).  Single periodic lattices
+   only (LBM_PERIODIC, n_instances <= 1), otherwise LBM_EINVAL.  The arithmetic is FP64 for any
+   precision of the context; the model parameters are the context's (lbm_set_params, and the
+   drive of lbm_set_instance_drive for lattice 0).  All pointers are device memory on the
+   context's device, FP64, used on the context's stream; the calls are asynchronous.
+
+   lbm_adjoint_step: for the step f_n -> f_{n+1} taken from the state f = f_n
+   ([n_species][9][nz][nx], the layout lbm_get_fields writes) and lam_next = dJ/df_{n+1} (same
+   layout), writes lam = dJ/df_n (same layout; must not overlap f or lam_next) and ADDS
+   dJ/dtheta to grad[8], theta = (G1[A], G1[B], G2[A], G2[B], G_AB, tau[A], tau[B],
+   body_force).  The context's own state is neither read nor changed. */
+int lbm_adjoint_step(lbm_ctx *c, const double *f, const double *lam_next, double *lam, double *grad);
+
+/* The calibration objective J = sum_z (ubar(z) - target_u[z])^2 + (rhobar_A(z) - target_rho[z])^2
+   of the populations f (as above): ubar is the x-average of u = sum_s j_x,s / sum_s rho_s,
+   rhobar_A the x-average of rho_A; target_u, target_rho hold nz doubles.  Writes J (one double)
+   and, unless dJdf is NULL, dJ/df (the layout of f): the lam_next of the last step. */
+int lbm_adjoint_objective(lbm_ctx *c, const double *f, const double *target_u, const double *target_rho,
+                          double *J, double *dJdf);
+
+/* For a run started by lbm_set_fields with u = NULL (populations W_l rho): the derivative with
+   respect to those densities, g_rho [n_species][nz][nx] = sum_l W_l lam0[s][l], lam0 = dJ/df_0. */
+int lbm_adjoint_initial(lbm_ctx *c, const double *lam0, double *g_rho);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,7 @@ struct lbm_ctx {
     double* avg = nullptr;
     double* staging = nullptr;  // (ns + 2) * n doubles
     double* fexport = nullptr;  // ns * 9 * n doubles
+    double* adj_scratch = nullptr;  // adjoint: adjoint_scratch_doubles(nx, nz, ns)
     void* gfield = nullptr;     // two-pass ghost fields
     alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
@@ -229,7 +230,8 @@ static void release(lbm_ctx* c) {
     c->ev.clear();
     void* ptrs[] = {c->f[0],       c->f[1],    c->part_row[0], c->part_row[1], c->part_col[0],
                     c->part_col[1], c->sched,   c->ticket,      c->flag,        c->out,
-                    c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d};
+                    c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d,
+                    c->adj_scratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_out) cudaFreeHost(c->host_out);
@@ -701,6 +703,46 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
     return LBM_OK;
 }
 
+extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, int where) {
+    if (!c) return LBM_EINVAL;
+    if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
+    CK(cudaSetDevice(c->d.device));
+    const Batch B = batch(c);
+    const int ns = c->d.n_species;
+    const long long n = (long long)c->d.nx * c->d.nz;
+    const size_t bytes = (size_t)ns * 9 * n * sizeof(double);
+    if (!c->fexport) CK(cudaMalloc(&c->fexport, bytes));
+    CK(cudaMemcpyAsync(c->fexport, f, bytes, where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       c->stream));
+    if (c->d.precision == LBM_FP32)
+        for (int s = 0; s < ns; ++s)
+            if (c->p.rho_ref[s] >= 0.0)
+                c->rho_ref[s] = c->p.rho_ref[s];
+            else if (!c->have_fields)
+                return fail(c, LBM_EINVAL,
+                            "FP32 populations need a reference density: set rho_ref >= 0 or call lbm_set_fields first");
+    refresh_const(c);
+    drop_graphs(c);
+    c->cur = 0;
+    if (c->d.precision == LBM_FP64) {
+        CK(launch_import<double>(ns, (double*)c->f[0], c->fexport, c->c64, c->pull ? &B : nullptr, c->stream));
+        if (c->pull) CK(launch_pull_images<double>(ns, (double*)c->f[0], c->c64, B, c->stream));
+    } else {
+        CK(launch_import<float>(ns, (float*)c->f[0], c->fexport, c->c32, c->pull ? &B : nullptr, c->stream));
+        if (c->pull) CK(launch_pull_images<float>(ns, (float*)c->f[0], c->c32, B, c->stream));
+    }
+    c->launches += c->pull ? 2 : 1;
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
+    c->samples = 0;
+    c->pending = false;
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = 0;
+    c->have_fields = true;
+    return LBM_OK;
+}
+
 extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int where) {
     if (!c) return LBM_EINVAL;
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
@@ -1000,5 +1042,51 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
         ms_per_step[0] = ms[0];
         ms_per_step[1] = ms[1];
     }
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Discrete adjoint (periodic single lattice, FP64)
+// ---------------------------------------------------------------------------------------
+static int adjoint_ready(lbm_ctx* c, AdjConst& A) {
+    if (c->d.z_boundary != LBM_PERIODIC) return fail(c, LBM_EINVAL, "the adjoint needs a periodic lattice");
+    if (c->inst.size() > 1) return fail(c, LBM_EINVAL, "the adjoint is for a single lattice, not a batch");
+    CK(cudaSetDevice(c->d.device));
+    if (!c->adj_scratch)
+        CK(cudaMalloc(&c->adj_scratch,
+                      (size_t)adjoint_scratch_doubles(c->d.nx, c->d.nz, c->d.n_species) * sizeof(double)));
+    fill_adj_const(A, c->p, c->d.nx, c->d.nz, c->d.n_species, c->inst.empty() ? c->p.body_force : c->inst[0].g);
+    return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_step(lbm_ctx* c, const double* f, const double* lam_next, double* lam, double* grad) {
+    if (!c) return LBM_EINVAL;
+    if (!f || !lam_next || !lam || !grad) return fail(c, LBM_EINVAL, "NULL pointer");
+    if (lam == lam_next || lam == f) return fail(c, LBM_EINVAL, "lam must not overlap lam_next or f");
+    AdjConst A;
+    if (int r = adjoint_ready(c, A)) return r;
+    CK(launch_adjoint_step(A, f, lam_next, lam, grad, c->adj_scratch, c->stream));
+    c->launches += 5;
+    return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_objective(lbm_ctx* c, const double* f, const double* target_u, const double* target_rho,
+                                     double* J, double* dJdf) {
+    if (!c) return LBM_EINVAL;
+    if (!f || !target_u || !target_rho || !J) return fail(c, LBM_EINVAL, "NULL pointer");
+    AdjConst A;
+    if (int r = adjoint_ready(c, A)) return r;
+    CK(launch_adjoint_objective(A, f, target_u, target_rho, J, dJdf, c->adj_scratch, c->stream));
+    c->launches += dJdf ? 3 : 2;
+    return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_initial(lbm_ctx* c, const double* lam0, double* g_rho) {
+    if (!c) return LBM_EINVAL;
+    if (!lam0 || !g_rho) return fail(c, LBM_EINVAL, "NULL pointer");
+    AdjConst A;
+    if (int r = adjoint_ready(c, A)) return r;
+    CK(launch_adjoint_initial(A, lam0, g_rho, c->stream));
+    c->launches += 1;
     return LBM_OK;
 }

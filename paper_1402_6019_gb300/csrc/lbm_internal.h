@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm.h"
 #include "lbm_core.cuh"
 
 namespace lbm {
@@ -165,6 +166,10 @@ cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const 
                         cudaStream_t st);
 template <typename T>
 cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, const Batch* B, cudaStream_t st);
+// The inverse of launch_export: plain FP64 post-streaming populations in, the stored layout out
+// (deviations from W_l rho_ref); the pull layout's ghosts are filled by launch_pull_images.
+template <typename T>
+cudaError_t launch_import(int ns, T* f, const double* in, const StepConst<T>& C, const Batch* B, cudaStream_t st);
 // Reduction of the step kernels' partial sums into the observables.  `out` / `avg` hold
 // obs_len(nx, nz) entries (profiles, wall forces, flag); `bpart` / `bavg` hold
 // reduce_blocks(nx, nz) * 5 block partials of the scalars (mass A, B, momentum x, z, gamma) and
@@ -175,6 +180,29 @@ int reduce_blocks(int nx, int nz);
 cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
                           unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
                           bool tail, const InstGeom* inst, int ninst, cudaStream_t st);
+
+// Discrete adjoint of the step on a periodic lattice (FP64, plain [ns][9][nz][nx] layouts).
+// Couplings and weights as the step uses them: wa / wr / wc = weight_norm x the attraction,
+// repulsion and cross weights by |c|^2.
+struct AdjConst {
+    int nx, nz, ns, psi_form;
+    double wa[9], wr[9], wc[9];
+    double G1[2], G2[2], tau[2], rho0[2];
+    double G_AB, g;
+};
+void fill_adj_const(AdjConst& A, const lbm_params& p, int nx, int nz, int ns, double body_force);
+// Doubles of scratch launch_adjoint_step and launch_adjoint_objective need.
+long long adjoint_scratch_doubles(int nx, int nz, int ns);
+// lam = dJ/df_n from lam_next = dJ/df_{n+1} at the state f = f_n; adds dJ/dtheta to grad[8].
+cudaError_t launch_adjoint_step(const AdjConst& A, const double* f, const double* lam_next, double* lam,
+                                double* grad, double* scratch, cudaStream_t st);
+// J (one double) of the velocity / density profile objective at f and, when g is not null,
+// g = dJ/df.
+cudaError_t launch_adjoint_objective(const AdjConst& A, const double* f, const double* tu, const double* tr,
+                                     double* J, double* g, double* scratch, cudaStream_t st);
+// g [ns][nz][nx] = sum_l W_l lam0: the derivative with respect to the densities of an initial
+// state at rest.
+cudaError_t launch_adjoint_initial(const AdjConst& A, const double* lam0, double* g, cudaStream_t st);
 
 // Twopass tile (threads per CTA: TPX x TPZ sites).
 constexpr int TPX = 32, TPZ = 8;

@@ -66,6 +66,25 @@ __global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ o
     }
 }
 
+// The inverse of k_export: plain FP64 post-streaming values in, stored values out.
+template <typename T>
+__global__ void k_import(int ns, T* __restrict__ f, const double* __restrict__ in, const StepConst<T> C,
+                         const InstGeom* __restrict__ inst, int ninst) {
+    const long long n = (long long)C.nx * C.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % C.nx), zg = (int)(i / C.nx);
+        int k = 0;
+        if (inst && ninst > 1) k = inst_of_row(inst, ninst, zg);
+        for (int s = 0; s < ns; ++s)
+            for (int l = 0; l < 9; ++l) {
+                long long o = (long long)zg * C.pitch + x;
+                int ls = l;
+                if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
+                f[(s * 9 + ls) * C.plane + o] = (T)(in[(s * 9 + l) * n + i] - wlb<double>(l) * (double)C.rho_ref[s]);
+            }
+    }
+}
+
 // The reduction kernel: work item blockIdx.x, and with TAIL the last block to finish writes the
 // scalar sums into out[O_MASS..] on the device.
 template <typename PT, bool TAIL>
@@ -146,6 +165,14 @@ cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_import(int ns, T* f, const double* in, const StepConst<T>& C, const Batch* B, cudaStream_t st) {
+    const long long n = (long long)C.nx * C.nz;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_import<T><<<blocks, 256, 0, st>>>(ns, f, in, C, B ? B->inst : nullptr, B ? B->ninst : 0);
+    return cudaGetLastError();
+}
+
 int reduce_blocks(int nx, int nz) {
     return (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32) + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
 }
@@ -184,6 +211,10 @@ template cudaError_t launch_init<double>(int, double*, const double*, const doub
 template cudaError_t launch_export<float>(int, const float*, double*, const StepConst<float>&, const Batch*,
                                           cudaStream_t);
 template cudaError_t launch_export<double>(int, const double*, double*, const StepConst<double>&, const Batch*,
+                                           cudaStream_t);
+template cudaError_t launch_import<float>(int, float*, const double*, const StepConst<float>&, const Batch*,
+                                          cudaStream_t);
+template cudaError_t launch_import<double>(int, double*, const double*, const StepConst<double>&, const Batch*,
                                            cudaStream_t);
 
 }  // namespace lbm

@@ -77,6 +77,10 @@ SIGNATURES = {
     "lbm_set_instance_drive": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "lbm_set_populations": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "lbm_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "lbm_adjoint_objective": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "lbm_adjoint_initial": (ctypes.c_int, [_VP, _VP, _VP]),
 }
 
 _lib = None
@@ -237,6 +241,33 @@ def lbm_selftest_wait(h, cycles: int) -> int:
     return load().lbm_selftest_wait(h, ctypes.c_longlong(cycles))
 
 
+def lbm_set_populations(h, f):
+    """f: host float64 [ns, 9, nz, nx] array or a CUDA float64 tensor of that layout."""
+    pf, where = _dptr(f)
+    _check(load().lbm_set_populations(h, pf, where), h)
+
+
+def _dev(t):
+    if t is None:
+        return None
+    if not hasattr(t, "data_ptr"):
+        raise TypeError("the adjoint entry points take CUDA float64 tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lbm_adjoint_step(h, f, lam_next, lam, grad):
+    """Device tensors (float64): lam <- dJ/df_n, grad[8] += dJ/dtheta (asynchronous)."""
+    _check(load().lbm_adjoint_step(h, _dev(f), _dev(lam_next), _dev(lam), _dev(grad)), h)
+
+
+def lbm_adjoint_objective(h, f, target_u, target_rho, J, dJdf=None):
+    _check(load().lbm_adjoint_objective(h, _dev(f), _dev(target_u), _dev(target_rho), _dev(J), _dev(dJdf)), h)
+
+
+def lbm_adjoint_initial(h, lam0, g_rho):
+    _check(load().lbm_adjoint_initial(h, _dev(lam0), _dev(g_rho)), h)
+
+
 # ---- convenience ---------------------------------------------------------------------------
 
 def make_params(**kw) -> lbm_params:
@@ -315,6 +346,11 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.h, n)
+
+    def set_populations(self, f):
+        if not hasattr(f, "data_ptr"):
+            f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ns, 9, self.nz, self.nx)
+        lbm_set_populations(self.h, f)
 
     def fields(self, populations=True):
         rho = np.zeros((self.ns, self.nz, self.nx))
