@@ -254,31 +254,61 @@ int lbm_selftest_wait(lbm_ctx *c, long long cycles);
    Synchronises. */
 int lbm_set_populations(lbm_ctx *c, const double *f, int where);
 
+/* Snapshots (exact checkpoints): lbm_snapshot copies the current state -- the populations in
+   the context's internal layout and precision, the step counter and the FP32 reference
+   densities -- into lbm_snapshot_bytes(c) bytes of device memory at dst (asynchronous);
+   lbm_restore makes such a snapshot the current state again, bit for bit, and resets the time
+   averages (synchronises).  A snapshot is only meaningful to the context that wrote it. */
+long long lbm_snapshot_bytes(const lbm_ctx *c);
+int lbm_snapshot(lbm_ctx *c, void *dst);
+int lbm_restore(lbm_ctx *c, const void *src);
+
+/* The current state as populations after streaming, f [n_species][9][nz][nx] in device memory,
+   double (LBM_FP64) or float (LBM_FP32) values: lbm_get_fields without the synchronisation and
+   in a chosen precision.  Asynchronous. */
+int lbm_export_state(lbm_ctx *c, void *f, int precision);
+
 /* Discrete adjoint (no counterpart in the paper: it differentiates the step of Eq. LB with the
    forces of Eq. FORCE and Sec. IV so that the couplings, relaxation times, drive and initial
    densities can be fitted to target profiles like those of Sec. IV).  Single periodic lattices
-   only (LBM_PERIODIC, n_instances <= 1), otherwise LBM_EINVAL.  The arithmetic is FP64 for any
-   precision of the context; the model parameters are the context's (lbm_set_params, and the
-   drive of lbm_set_instance_drive for lattice 0).  All pointers are device memory on the
-   context's device, FP64, used on the context's stream; the calls are asynchronous.
+   only (LBM_PERIODIC, n_instances <= 1), otherwise LBM_EINVAL.  The model parameters are the
+   context's (lbm_set_params, and the drive of lbm_set_instance_drive for lattice 0); the
+   context's own state is neither read nor changed by the adjoint calls.  All pointers are device
+   memory on the context's device, used on the context's stream; the calls are asynchronous.
+   `precision` (LBM_FP64 or LBM_FP32, independent of the context's) is the type of the state and
+   adjoint arrays (double or float) and of their arithmetic; the parameter derivatives are
+   accumulated in FP64 in both (per block in FP64 or double-float pairs, over blocks and steps
+   in FP64).  A state array is [n_species][9][nz][nx] (the layout lbm_get_fields writes); an
+   adjoint array lam = dJ/df has the same layout.  theta, the order of grad[8]: G1[A], G1[B],
+   G2[A], G2[B], G_AB, tau[A], tau[B], body_force.
 
-   lbm_adjoint_step: for the step f_n -> f_{n+1} taken from the state f = f_n
-   ([n_species][9][nz][nx], the layout lbm_get_fields writes) and lam_next = dJ/df_{n+1} (same
-   layout), writes lam = dJ/df_n (same layout; must not overlap f or lam_next) and ADDS
-   dJ/dtheta to grad[8], theta = (G1[A], G1[B], G2[A], G2[B], G_AB, tau[A], tau[B],
-   body_force).  The context's own state is neither read nor changed. */
-int lbm_adjoint_step(lbm_ctx *c, const double *f, const double *lam_next, double *lam, double *grad);
+   lbm_record_states: for k = 0 .. nsteps - 1, writes the current state into states + k m
+   (m = n_species 9 nz nx values of `precision`), then takes one step (as lbm_step): the states a
+   backward sweep over these steps needs.  Asynchronous. */
+int lbm_record_states(lbm_ctx *c, int nsteps, void *states, int precision);
+
+/* One step back: for the step f_n -> f_{n+1} taken from the state f = f_n and lam_next =
+   dJ/df_{n+1}, writes lam = dJ/df_n (must not overlap f or lam_next) and ADDS dJ/dtheta to
+   grad[8]. */
+int lbm_adjoint_step(lbm_ctx *c, const void *f, const void *lam_next, void *lam, double *grad, int precision);
+
+/* nsteps steps back over the states recorded by lbm_record_states (states[k] = f_{n+k}): lam
+   holds dJ/df_{n+nsteps} on entry and dJ/df_n on return (in place; the context keeps a second
+   buffer); grad[8] += dJ/dtheta of those steps. */
+int lbm_adjoint_steps(lbm_ctx *c, int nsteps, const void *states, void *lam, double *grad, int precision);
 
 /* The calibration objective J = sum_z (ubar(z) - target_u[z])^2 + (rhobar_A(z) - target_rho[z])^2
-   of the populations f (as above): ubar is the x-average of u = sum_s j_x,s / sum_s rho_s,
-   rhobar_A the x-average of rho_A; target_u, target_rho hold nz doubles.  Writes J (one double)
-   and, unless dJdf is NULL, dJ/df (the layout of f): the lam_next of the last step. */
-int lbm_adjoint_objective(lbm_ctx *c, const double *f, const double *target_u, const double *target_rho,
-                          double *J, double *dJdf);
+   of the state f: ubar is the x-average of u = sum_s j_x,s / sum_s rho_s, rhobar_A the
+   x-average of rho_A; target_u, target_rho hold nz doubles.  Writes J (one double, FP64 sums
+   of the rows) and, unless dJdf is NULL, dJ/df (the layout and precision of f): the lam of the
+   last state. */
+int lbm_adjoint_objective(lbm_ctx *c, const void *f, const double *target_u, const double *target_rho,
+                          double *J, void *dJdf, int precision);
 
 /* For a run started by lbm_set_fields with u = NULL (populations W_l rho): the derivative with
-   respect to those densities, g_rho [n_species][nz][nx] = sum_l W_l lam0[s][l], lam0 = dJ/df_0. */
-int lbm_adjoint_initial(lbm_ctx *c, const double *lam0, double *g_rho);
+   respect to those densities, g_rho [n_species][nz][nx] doubles = sum_l W_l lam0[s][l],
+   lam0 = dJ/df_0 in `precision`. */
+int lbm_adjoint_initial(lbm_ctx *c, const void *lam0, double *g_rho, int precision);
 
 #ifdef __cplusplus
 }

@@ -1,4 +1,4 @@
-// lbm_adjoint.cu -- discrete adjoint of the time step (periodic lattice), in FP64.
+// lbm_adjoint.cu -- discrete adjoint of the time step (periodic lattice), in FP64 or FP32.
 //
 // The step maps the post-streaming populations f_n to f_{n+1} = S(f_n; theta):
 //   rho_s = sum_l f_l, j_s = sum_l f_l c_l (Sec. II); psi_s = psi(rho_s) (Sec. IV);
@@ -7,27 +7,30 @@
 //   u' = sum_s j_s / tau_s / sum_s rho_s / tau_s, u_s = u' + tau_s F_s / rho_s;
 //   feq_l = W_l rho_s (1 + 3 c.u_s + 9/2 (c.u_s)^2 - 3/2 u_s.u_s);
 //   g_l = f_l - (f_l - feq_l) / tau_s (Eq. LB);  f_{n+1}(x + c_l, l) = g_l(x).
-// Given lam_{n+1} = dJ/df_{n+1}, the kernels below form lam_n = dJ/df_n and the derivatives
-// with respect to theta = (G1 A, G1 B, G2 A, G2 B, G_AB, tau A, tau B, g) by applying the
-// transposed derivative of each stage in reverse order:
-//   k_adj_fields   moments, psi and the force of the state f_n (the linearisation point);
-//   k_adj_local    streaming transposed (a gather of lam_{n+1}), relaxation, equilibrium,
-//                  shifted and common velocity: dJ/dF_s, the local dJ/drho_s, dJ/dj_s;
-//   k_adj_final    the force transposed (each site gathers what its neighbours' forces owe
-//                  to its psi and rho), the pseudopotential and the moments: lam_n.
-// Parameter derivatives are summed per block, then over the blocks in a fixed order (FP64).
+// Given lam_{n+1} = dJ/df_{n+1}, three kernels form lam_n = dJ/df_n and the derivatives with
+// respect to theta = (G1 A, G1 B, G2 A, G2 B, G_AB, tau A, tau B, g) by applying the transposed
+// derivative of each stage in reverse order:
+//   k_adj_moments  rho, j and psi of the state f_n (the linearisation point);
+//   k_adj_local    the force at the site (from its neighbours' psi and rho), then streaming
+//                  transposed (a gather of lam_{n+1}), relaxation, equilibrium, shifted and
+//                  common velocity transposed: dJ/dF_s, the site's own share of dJ/drho_s and
+//                  dJ/dj_s, and every parameter derivative of the site;
+//   k_adj_final    the neighbour shares of the force transposed (each site gathers what the
+//                  forces at x - c owe to its psi and rho), the pseudopotential and the
+//                  moments: lam_n.
+// T is the precision of the states and of lam (FP64, or FP32 for FP32 forward runs).  The
+// parameter derivatives are summed per block (FP64, or double-float pairs in FP32 mode), kept
+// per block across the steps of a call, then summed over the blocks in FP64 in a fixed order.
 #include "lbm_consts.h"
 #include "lbm_internal.h"
+#include "lbm_reduce.cuh"
 
 namespace lbm {
 
 namespace {
 
 constexpr int AT = 256;  // threads per block
-
-struct Site {
-    int x, z;
-};
+constexpr int NPAR = 8;
 
 __device__ __forceinline__ int wrapi(int i, int n) {
     int r = i % n;
@@ -38,41 +41,68 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 __constant__ int LKX[24] = {1, 0, -1, 0, 1, -1, -1, 1, 2, 0, -2, 0, 2, 1, -1, -2, -2, -1, 1, 2, 2, -2, -2, 2};
 __constant__ int LKZ[24] = {0, 1, 0, -1, 1, 1, -1, -1, 0, 2, 0, -2, 1, 2, 2, 1, -1, -2, -2, -1, 2, 2, -2, -2};
 
-__device__ __forceinline__ double psi_fn(const AdjConst& A, int s, double r) {
-    return A.psi_form == 1 ? r : 1.0 - exp(-r / A.rho0[s]);
-}
-__device__ __forceinline__ double dpsi_fn(const AdjConst& A, int s, double r) {
-    return A.psi_form == 1 ? 1.0 : exp(-r / A.rho0[s]) / A.rho0[s];
-}
+template <typename T>
+struct AdjC {
+    int nx, nz, ns, psi_form;
+    T wa[9], wr[9], wc[9];  // by |c|^2, weight_norm included
+    T G1[2], G2[2], tau[2], itau[2], irho0[2];
+    T G_AB, g;
+};
 
-// Block sums of the per-thread values v[k] (k < K), written to part[blockIdx.x * NPAR + k0 + k].
-// The parameter derivatives are summed in two fixed-order stages (blocks, then k_adj_sum), so
-// a gradient does not depend on the order in which blocks finish.
-constexpr int NPAR = 8;
-template <int K>
-__device__ void block_sum(double (&v)[K], double* part, int k0) {
-    __shared__ double red[AT / 32][K];
+__device__ __forceinline__ double psi_t(double r, double ir0, int form) { return form == 1 ? r : -expm1(-r * ir0); }
+__device__ __forceinline__ float psi_t(float r, float ir0, int form) { return form == 1 ? r : -expm1f(-r * ir0); }
+__device__ __forceinline__ double dpsi_t(double r, double ir0, int form) { return form == 1 ? 1.0 : exp(-r * ir0) * ir0; }
+__device__ __forceinline__ float dpsi_t(float r, float ir0, int form) { return form == 1 ? 1.f : expf(-r * ir0) * ir0; }
+
+// Block accumulators: FP64, or a double-float pair (hi, lo) summed with TwoSum on the FP32 pipes.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    using A = double;
+    __device__ static A from(double v) { return v; }
+    __device__ static A add(A a, A b) { return a + b; }
+    __device__ static A shfl(A a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ static double wide(A a) { return a; }
+};
+template <> struct Acc<float> {
+    using A = float2;
+    __device__ static A from(float v) { return make_float2(v, 0.f); }
+    __device__ static A add(A a, A b) { return ff_add(a, b); }
+    __device__ static A shfl(A a, int o) {
+        return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+    }
+    __device__ static double wide(A a) { return (double)a.x + (double)a.y; }
+};
+
+// Block sums of the per-thread values v[k] (k < NPAR), stored to part[blockIdx.x][k], or added
+// to it (accumulate): fixed order, so results repeat bit for bit.
+template <typename T>
+__device__ void block_sum(const T (&v)[NPAR], typename Acc<T>::A* part, int accumulate) {
+    using A = typename Acc<T>::A;
+    __shared__ A red[AT / 32][NPAR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double t = v[k];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    for (int k = 0; k < NPAR; ++k) {
+        A t = Acc<T>::from(v[k]);
+        for (int o = 16; o > 0; o >>= 1) t = Acc<T>::add(t, Acc<T>::shfl(t, o));
         if (lane == 0) red[w][k] = t;
     }
     __syncthreads();
-    if (threadIdx.x < K) {
-        double t = 0.0;
-        for (int i = 0; i < AT / 32; ++i) t += red[i][threadIdx.x];
-        part[(long long)blockIdx.x * NPAR + k0 + threadIdx.x] = t;
+    if (threadIdx.x < NPAR) {
+        A t = red[0][threadIdx.x];
+        for (int i = 1; i < AT / 32; ++i) t = Acc<T>::add(t, red[i][threadIdx.x]);
+        A* p = part + (long long)blockIdx.x * NPAR + threadIdx.x;
+        *p = accumulate ? Acc<T>::add(*p, t) : t;
     }
 }
 
-// grad[k] += sum over nb blocks of part[b][k]; one block, fixed order.
-__global__ void __launch_bounds__(AT) k_adj_sum(const double* __restrict__ part, long long nb, double* __restrict__ grad) {
+// grad[k] += sum over the nb blocks of part[b][k]: one block, FP64, fixed order.
+template <typename T>
+__global__ void __launch_bounds__(AT) k_adj_sum(const typename Acc<T>::A* __restrict__ part, long long nb,
+                                                double* __restrict__ grad) {
     __shared__ double red[AT / 32];
     for (int k = 0; k < NPAR; ++k) {
         double t = 0.0;
-        for (long long b = threadIdx.x; b < nb; b += AT) t += part[b * NPAR + k];
+        for (long long b = threadIdx.x; b < nb; b += AT) t += Acc<T>::wide(part[b * NPAR + k]);
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
         __syncthreads();
@@ -85,203 +115,213 @@ __global__ void __launch_bounds__(AT) k_adj_sum(const double* __restrict__ part,
     }
 }
 
-// Moments, pseudopotential (per site), then the force (needs the neighbours' psi, rho).
-__global__ void k_adj_moments(const double* __restrict__ f, const AdjConst A, double* __restrict__ rho,
-                              double* __restrict__ jx, double* __restrict__ jz, double* __restrict__ psi) {
-    const long long n = (long long)A.nx * A.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        for (int s = 0; s < A.ns; ++s) {
-            double r = 0.0, mx = 0.0, mz = 0.0;
-            for (int l = 0; l < 9; ++l) {
-                const double v = f[(s * 9 + l) * n + i];
-                r += v;
-                mx += v * cx(l);
-                mz += v * cz(l);
-            }
-            rho[s * n + i] = r;
-            jx[s * n + i] = mx;
-            jz[s * n + i] = mz;
-            psi[s * n + i] = psi_fn(A, s, r);
-        }
-}
+// Intermediate fields of one adjoint step, [ns][n] each.
+template <typename T>
+struct AdjBuf {
+    T *rho, *jx, *jz, *psi;  // the state's moments and pseudopotential
+    T *qx, *qz;              // psi_s dJ/dF_s: what the force at x owes to psi_s(x + c)
+    T *rx, *rz;              // rho_s dJ/dF_s: what it owes to rho_s'(x + c)
+    T *dloc, *djx, *djz;     // the site's own dJ/drho_s (psi' folded in), dJ/dj_s
+    T* dps;                  // psi'(rho_s)
+};
 
-__global__ void k_adj_force(const AdjConst A, const double* __restrict__ rho, const double* __restrict__ psi,
-                            double* __restrict__ Fx, double* __restrict__ Fz) {
+template <typename T, int NS>
+__global__ void __launch_bounds__(AT) k_adj_moments(const T* __restrict__ f, const AdjC<T> A, AdjBuf<T> B) {
     const long long n = (long long)A.nx * A.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % A.nx), z = (int)(i / A.nx);
-        for (int s = 0; s < A.ns; ++s) {
-            double ax = 0.0, az = 0.0, rx = 0.0, rz = 0.0, bx = 0.0, bz = 0.0;
-            for (int k = 0; k < 24; ++k) {
-                const long long j = (long long)wrapi(z + LKZ[k], A.nz) * A.nx + wrapi(x + LKX[k], A.nx);
-                const int q = LKX[k] * LKX[k] + LKZ[k] * LKZ[k];
-                const double p = psi[s * n + j];
-                ax += A.wa[q] * p * LKX[k];
-                az += A.wa[q] * p * LKZ[k];
-                rx += A.wr[q] * p * LKX[k];
-                rz += A.wr[q] * p * LKZ[k];
-                if (A.ns == 2 && k < 8) {
-                    const double ro = rho[(1 - s) * n + j];
-                    bx += A.wc[q] * ro * LKX[k];
-                    bz += A.wc[q] * ro * LKZ[k];
-                }
-            }
-            const double ps = psi[s * n + i], r = rho[s * n + i];
-            Fx[s * n + i] = -A.G1[s] * ps * ax - A.G2[s] * ps * rx - A.G_AB * r * bx + r * A.g;
-            Fz[s * n + i] = -A.G1[s] * ps * az - A.G2[s] * ps * rz - A.G_AB * r * bz;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        T r = 0, mx = 0, mz = 0;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            const T v = f[(s * 9 + l) * n + i];
+            r += v;
+            mx += v * (T)cx(l);
+            mz += v * (T)cz(l);
         }
+        B.rho[s * n + i] = r;
+        B.jx[s * n + i] = mx;
+        B.jz[s * n + i] = mz;
+        B.psi[s * n + i] = psi_t(r, A.irho0[s], A.psi_form);
     }
 }
 
-// Streaming, relaxation, equilibrium and velocities, transposed.  One site per thread.
-__global__ void __launch_bounds__(AT) k_adj_local(const double* __restrict__ f, const double* __restrict__ lam_next,
-                                                  const AdjConst A, const double* __restrict__ rho,
-                                                  const double* __restrict__ jx, const double* __restrict__ jz,
-                                                  const double* __restrict__ Fx, const double* __restrict__ Fz,
-                                                  double* __restrict__ dF, double* __restrict__ drho,
-                                                  double* __restrict__ djx, double* __restrict__ djz,
-                                                  double* __restrict__ part) {
+template <typename T, int NS>
+__global__ void __launch_bounds__(AT) k_adj_local(const T* __restrict__ f, const T* __restrict__ lam_next,
+                                                  const AdjC<T> A, AdjBuf<T> B,
+                                                  typename Acc<T>::A* __restrict__ part, int accumulate) {
     const long long n = (long long)A.nx * A.nz;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double gt[2] = {0.0, 0.0};  // d/dtau A, B
+    T gp[NPAR] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (i < n) {
         const int x = (int)(i % A.nx), z = (int)(i / A.nx);
-        double numx = 0.0, numz = 0.0, den = 0.0;
-        for (int k = 0; k < A.ns; ++k) {
-            numx += jx[k * n + i] / A.tau[k];
-            numz += jz[k * n + i] / A.tau[k];
-            den += rho[k * n + i] / A.tau[k];
+        // the force at the site, keeping its three sums (attraction a, repulsion p, cross b)
+        T ax[NS], az[NS], px[NS], pz[NS], bx[NS], bz[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) ax[s] = az[s] = px[s] = pz[s] = bx[s] = bz[s] = 0;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            const long long j = (long long)wrapi(z + LKZ[k], A.nz) * A.nx + wrapi(x + LKX[k], A.nx);
+            const int q = LKX[k] * LKX[k] + LKZ[k] * LKZ[k];
+            const T ex = (T)LKX[k], ez = (T)LKZ[k];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const T p = B.psi[s * n + j];
+                ax[s] += A.wa[q] * p * ex;
+                az[s] += A.wa[q] * p * ez;
+                px[s] += A.wr[q] * p * ex;
+                pz[s] += A.wr[q] * p * ez;
+                if (NS == 2 && k < 8) {
+                    const T ro = B.rho[(1 - s) * n + j];
+                    bx[s] += A.wc[q] * ro * ex;
+                    bz[s] += A.wc[q] * ro * ez;
+                }
+            }
         }
-        const double upx = numx / den, upz = numz / den;
-        double dupx = 0.0, dupz = 0.0;
-        double dr[2] = {0.0, 0.0};
-        for (int s = 0; s < A.ns; ++s) {
-            const double r = rho[s * n + i], tau = A.tau[s];
-            const double fx = Fx[s * n + i], fz = Fz[s * n + i];
-            const double ux = upx + tau * fx / r, uz = upz + tau * fz / r;
-            const double usq = ux * ux + uz * uz;
-            double ar = 0.0, aux = 0.0, auz = 0.0;
+        T rho[NS], psi[NS], Fx[NS], Fz[NS], jx[NS], jz[NS];
+        T numx = 0, numz = 0, den = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            rho[s] = B.rho[s * n + i];
+            psi[s] = B.psi[s * n + i];
+            jx[s] = B.jx[s * n + i];
+            jz[s] = B.jz[s * n + i];
+            Fx[s] = -A.G1[s] * psi[s] * ax[s] - A.G2[s] * psi[s] * px[s] - A.G_AB * rho[s] * bx[s] + rho[s] * A.g;
+            Fz[s] = -A.G1[s] * psi[s] * az[s] - A.G2[s] * psi[s] * pz[s] - A.G_AB * rho[s] * bz[s];
+            numx += jx[s] * A.itau[s];
+            numz += jz[s] * A.itau[s];
+            den += rho[s] * A.itau[s];
+        }
+        const T iden = (T)1 / den;
+        const T upx = numx * iden, upz = numz * iden;
+        T dupx = 0, dupz = 0, dr[NS], dFx[NS], dFz[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const T r = rho[s], tau = A.tau[s], it = A.itau[s], ir = (T)1 / r;
+            const T ux = upx + tau * Fx[s] * ir, uz = upz + tau * Fz[s] * ir;
+            const T usq = ux * ux + uz * uz;
+            // d/dtau of g = f - (f - feq) / tau is (f - feq) / tau^2.  sum_l (f_l - feq_l) = 0
+            // (the equilibrium keeps rho), so sum_l m_l (f_l - feq_l) = sum_l (m_l - m_0)(f_l - feq_l):
+            // the part of lam common to all l, often the largest, would only multiply rounding
+            T ar = 0, aux = 0, auz = 0, gt = 0;
+            const T m0 = lam_next[(s * 9) * n + i];
+#pragma unroll
             for (int l = 0; l < 9; ++l) {
                 // streaming transposed: g_l(x) became f_l(x + c_l)
                 const long long j = (long long)wrapi(z + cz(l), A.nz) * A.nx + wrapi(x + cx(l), A.nx);
-                const double m = lam_next[(s * 9 + l) * n + j];
-                const double cu = cx(l) * ux + cz(l) * uz;
-                const double fe = wlb<double>(l) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-                const double dfe = m / tau;  // g = f - (f - feq) / tau
-                gt[s] += m * (f[(s * 9 + l) * n + i] - fe) / (tau * tau);
-                ar += dfe * fe / r;
-                aux += dfe * wlb<double>(l) * r * (3.0 * cx(l) + 9.0 * cu * cx(l) - 3.0 * ux);
-                auz += dfe * wlb<double>(l) * r * (3.0 * cz(l) + 9.0 * cu * cz(l) - 3.0 * uz);
+                const T m = lam_next[(s * 9 + l) * n + j];
+                const T ex = (T)cx(l), ez = (T)cz(l);
+                const T cu = ex * ux + ez * uz;
+                const T wr = wlb<T>(l) * r;
+                const T fe = wr * ((T)1 + (T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * usq);
+                const T dfe = m * it;  // g = f - (f - feq) / tau
+                gt += (m - m0) * (f[(s * 9 + l) * n + i] - fe);
+                ar += dfe * fe;
+                aux += dfe * wr * ((T)3 * ex + (T)9 * cu * ex - (T)3 * ux);
+                auz += dfe * wr * ((T)3 * ez + (T)9 * cu * ez - (T)3 * uz);
             }
             // u_s = u' + tau F_s / rho_s
             dupx += aux;
             dupz += auz;
-            dF[(s * 2 + 0) * n + i] = aux * tau / r;
-            dF[(s * 2 + 1) * n + i] = auz * tau / r;
-            dr[s] += ar - (aux * fx + auz * fz) * tau / (r * r);
-            gt[s] += (aux * fx + auz * fz) / r;
+            dFx[s] = aux * tau * ir;
+            dFz[s] = auz * tau * ir;
+            const T fu = (aux * Fx[s] + auz * Fz[s]) * ir;
+            dr[s] = ar * ir - fu * tau * ir;
+            gp[5 + s] += gt * it * it + fu;
         }
         // u' = sum_k j_k / tau_k / sum_k rho_k / tau_k
-        const double dnx = dupx / den, dnz = dupz / den, dden = -(dupx * upx + dupz * upz) / den;
-        for (int k = 0; k < A.ns; ++k) {
-            const double tk = A.tau[k];
-            djx[k * n + i] = dnx / tk;
-            djz[k * n + i] = dnz / tk;
-            drho[k * n + i] = dr[k] + dden / tk;
-            gt[k] += -(jx[k * n + i] * dnx + jz[k * n + i] * dnz + rho[k * n + i] * dden) / (tk * tk);
+        const T dnx = dupx * iden, dnz = dupz * iden, dden = -(dupx * upx + dupz * upz) * iden;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const T it = A.itau[s];
+            gp[5 + s] -= (jx[s] * dnx + jz[s] * dnz + rho[s] * dden) * it * it;
+            dr[s] += dden * it;
+            // the site's own terms of the force: F_s depends on psi_s(x), rho_s(x) and g
+            const T ba = dFx[s] * ax[s] + dFz[s] * az[s], bp = dFx[s] * px[s] + dFz[s] * pz[s];
+            const T bb = dFx[s] * bx[s] + dFz[s] * bz[s];
+            const T dps = dpsi_t(rho[s], A.irho0[s], A.psi_form);
+            gp[0 + s] -= psi[s] * ba;
+            gp[2 + s] -= psi[s] * bp;
+            if (NS == 2) gp[4] -= rho[s] * bb;
+            gp[7] += rho[s] * dFx[s];
+            B.dloc[s * n + i] = dr[s] - A.G_AB * bb + dFx[s] * A.g - dps * (A.G1[s] * ba + A.G2[s] * bp);
+            B.djx[s * n + i] = dnx * it;
+            B.djz[s * n + i] = dnz * it;
+            B.dps[s * n + i] = dps;
+            B.qx[s * n + i] = psi[s] * dFx[s];
+            B.qz[s * n + i] = psi[s] * dFz[s];
+            B.rx[s * n + i] = rho[s] * dFx[s];
+            B.rz[s * n + i] = rho[s] * dFz[s];
         }
     }
-    block_sum<2>(gt, part, 5);
+    block_sum<T>(gp, part, accumulate);
 }
 
-// The force transposed (gathered from the neighbours whose force used this site), then the
-// pseudopotential and the moments: lam_n.
-__global__ void __launch_bounds__(AT) k_adj_final(const double* __restrict__ lam_next, const AdjConst A,
-                                                  const double* __restrict__ rho, const double* __restrict__ psi,
-                                                  const double* __restrict__ dF, const double* __restrict__ drho,
-                                                  const double* __restrict__ djx, const double* __restrict__ djz,
-                                                  double* __restrict__ lam, double* __restrict__ part) {
+template <typename T, int NS>
+__global__ void __launch_bounds__(AT) k_adj_final(const T* __restrict__ lam_next, const AdjC<T> A, AdjBuf<T> B,
+                                                  T* __restrict__ lam) {
     const long long n = (long long)A.nx * A.nz;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double gp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // G1 A, B; G2 A, B; G_AB; g
-    if (i < n) {
-        const int x = (int)(i % A.nx), z = (int)(i / A.nx);
-        double dps[2] = {0.0, 0.0}, dro[2] = {0.0, 0.0};
-        for (int s = 0; s < A.ns; ++s) {
-            dro[s] += drho[s * n + i];
-            const double bx = dF[(s * 2 + 0) * n + i], bz = dF[(s * 2 + 1) * n + i];
-            const double ps = psi[s * n + i], r = rho[s * n + i];
-            double ax = 0.0, az = 0.0, rx = 0.0, rz = 0.0, cxs = 0.0, czs = 0.0;
-            for (int k = 0; k < 24; ++k) {
-                const int q = LKX[k] * LKX[k] + LKZ[k] * LKZ[k];
-                // this site as the source of the force: its neighbours' psi and rho
-                const long long jf = (long long)wrapi(z + LKZ[k], A.nz) * A.nx + wrapi(x + LKX[k], A.nx);
-                const double pf = psi[s * n + jf];
-                ax += A.wa[q] * pf * LKX[k];
-                az += A.wa[q] * pf * LKZ[k];
-                rx += A.wr[q] * pf * LKX[k];
-                rz += A.wr[q] * pf * LKZ[k];
-                // this site as a neighbour of x - c: what that site's force owes to its psi
-                const long long jb = (long long)wrapi(z - LKZ[k], A.nz) * A.nx + wrapi(x - LKX[k], A.nx);
-                const double bbc = dF[(s * 2 + 0) * n + jb] * LKX[k] + dF[(s * 2 + 1) * n + jb] * LKZ[k];
-                dps[s] += -psi[s * n + jb] * (A.G1[s] * A.wa[q] + A.G2[s] * A.wr[q]) * bbc;
-                if (A.ns == 2 && k < 8) {
-                    cxs += A.wc[q] * rho[(1 - s) * n + jf] * LKX[k];
-                    czs += A.wc[q] * rho[(1 - s) * n + jf] * LKZ[k];
-                    // the other species' force at x - c used this site's rho_s as its rho_s'
-                    const double obc = dF[((1 - s) * 2 + 0) * n + jb] * LKX[k] + dF[((1 - s) * 2 + 1) * n + jb] * LKZ[k];
-                    dro[s] += -A.G_AB * rho[(1 - s) * n + jb] * A.wc[q] * obc;
-                }
-            }
-            dps[s] += -(A.G1[s] * (bx * ax + bz * az) + A.G2[s] * (bx * rx + bz * rz));
-            gp[0 + s] += -ps * (bx * ax + bz * az);
-            gp[2 + s] += -ps * (bx * rx + bz * rz);
-            if (A.ns == 2) {
-                dro[s] += -A.G_AB * (bx * cxs + bz * czs);
-                gp[4] += -r * (bx * cxs + bz * czs);
-            }
-            dro[s] += bx * A.g;
-            gp[5] += r * bx;
-        }
-        for (int s = 0; s < A.ns; ++s) {
-            const double d = dro[s] + dpsi_fn(A, s, rho[s * n + i]) * dps[s];
-            const double keep = 1.0 - 1.0 / A.tau[s];
-            for (int l = 0; l < 9; ++l) {
-                const long long j = (long long)wrapi(z + cz(l), A.nz) * A.nx + wrapi(x + cx(l), A.nx);
-                lam[(s * 9 + l) * n + i] =
-                    keep * lam_next[(s * 9 + l) * n + j] + d + djx[s * n + i] * cx(l) + djz[s * n + i] * cz(l);
+    if (i >= n) return;
+    const int x = (int)(i % A.nx), z = (int)(i / A.nx);
+    // this site as the neighbour x + c of the sites x - c: their forces' dependence on its psi
+    // (species s) and, through the cross term of the other species, on its rho_s
+    T dps[NS], dro[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dps[s] = dro[s] = 0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+        const long long jb = (long long)wrapi(z - LKZ[k], A.nz) * A.nx + wrapi(x - LKX[k], A.nx);
+        const int q = LKX[k] * LKX[k] + LKZ[k] * LKZ[k];
+        const T ex = (T)LKX[k], ez = (T)LKZ[k];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const T bc = B.qx[s * n + jb] * ex + B.qz[s * n + jb] * ez;
+            dps[s] -= (A.G1[s] * A.wa[q] + A.G2[s] * A.wr[q]) * bc;
+            if (NS == 2 && k < 8) {
+                const T oc = B.rx[(1 - s) * n + jb] * ex + B.rz[(1 - s) * n + jb] * ez;
+                dro[s] -= A.G_AB * A.wc[q] * oc;
             }
         }
     }
-    double g5[5] = {gp[0], gp[1], gp[2], gp[3], gp[4]};
-    block_sum<5>(g5, part, 0);
-    double g1[1] = {gp[5]};
-    block_sum<1>(g1, part, 7);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const T d = B.dloc[s * n + i] + dro[s] + B.dps[s * n + i] * dps[s];
+        const T keep = (T)1 - A.itau[s];
+        const T djx = B.djx[s * n + i], djz = B.djz[s * n + i];
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            const long long j = (long long)wrapi(z + cz(l), A.nz) * A.nx + wrapi(x + cx(l), A.nx);
+            lam[(s * 9 + l) * n + i] = keep * lam_next[(s * 9 + l) * n + j] + d + djx * (T)cx(l) + djz * (T)cz(l);
+        }
+    }
 }
 
 // Calibration objective: J = sum_z (ubar(z) - tu(z))^2 + (rhobar_A(z) - tr(z))^2, ubar the
 // x-average of u = sum_s j_x,s / sum_s rho_s, rhobar_A the x-average of rho_A.  One block per
-// row forms the averages; k_obj_total sums the rows' shares in a fixed order.
-__global__ void __launch_bounds__(AT) k_obj_rows(const double* __restrict__ f, const AdjConst A,
-                                                 double* __restrict__ ubar, double* __restrict__ rbar) {
+// row forms the averages (in T, widened to FP64); k_obj_total sums the rows' shares in a fixed
+// order.
+template <typename T>
+__global__ void __launch_bounds__(AT) k_obj_rows(const T* __restrict__ f, const AdjC<T> A, double* __restrict__ ubar,
+                                                 double* __restrict__ rbar) {
     const long long n = (long long)A.nx * A.nz;
     const int z = blockIdx.x;
-    double su = 0.0, sr = 0.0;
+    T su = 0, sr = 0;
     for (int x = threadIdx.x; x < A.nx; x += AT) {
         const long long i = (long long)z * A.nx + x;
-        double rt = 0.0, mx = 0.0, ra = 0.0;
+        T rt = 0, mx = 0, ra = 0;
         for (int s = 0; s < A.ns; ++s)
             for (int l = 0; l < 9; ++l) {
-                const double v = f[(s * 9 + l) * n + i];
+                const T v = f[(s * 9 + l) * n + i];
                 rt += v;
-                mx += v * cx(l);
+                mx += v * (T)cx(l);
                 if (s == 0) ra += v;
             }
         su += mx / rt;
         sr += ra;
     }
-    __shared__ double red[2][AT / 32];
+    __shared__ T red[2][AT / 32];
     for (int o = 16; o > 0; o >>= 1) {
         su += __shfl_xor_sync(0xffffffffu, su, o);
         sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -294,20 +334,20 @@ __global__ void __launch_bounds__(AT) k_obj_rows(const double* __restrict__ f, c
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
         for (int w = 0; w < AT / 32; ++w) {
-            a += red[0][w];
-            b += red[1][w];
+            a += (double)red[0][w];
+            b += (double)red[1][w];
         }
         ubar[z] = a / A.nx;
         rbar[z] = b / A.nx;
     }
 }
 
-__global__ void __launch_bounds__(AT) k_obj_total(const AdjConst A, const double* __restrict__ tu,
-                                                  const double* __restrict__ tr, const double* __restrict__ ubar,
-                                                  const double* __restrict__ rbar, double* __restrict__ J) {
+__global__ void __launch_bounds__(AT) k_obj_total(int nz, const double* __restrict__ tu, const double* __restrict__ tr,
+                                                  const double* __restrict__ ubar, const double* __restrict__ rbar,
+                                                  double* __restrict__ J) {
     __shared__ double red[AT / 32];
     double t = 0.0;
-    for (int z = threadIdx.x; z < A.nz; z += AT)
+    for (int z = threadIdx.x; z < nz; z += AT)
         t += (ubar[z] - tu[z]) * (ubar[z] - tu[z]) + (rbar[z] - tr[z]) * (rbar[z] - tr[z]);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
@@ -319,40 +359,96 @@ __global__ void __launch_bounds__(AT) k_obj_total(const AdjConst A, const double
     }
 }
 
-__global__ void k_obj_grad(const double* __restrict__ f, const AdjConst A, const double* __restrict__ tu,
-                           const double* __restrict__ tr, const double* __restrict__ ubar,
-                           const double* __restrict__ rbar, double* __restrict__ g) {
+// dJ/df of row z: 2 (ubar - tu) / nx (c_lx - u) / rho_tot + [s = A] 2 (rhobar_A - tr) / nx; the
+// row's two coefficients are formed in FP64 and rounded to T once.
+template <typename T>
+__global__ void __launch_bounds__(AT) k_obj_grad(const T* __restrict__ f, const AdjC<T> A, const double* __restrict__ tu,
+                                                 const double* __restrict__ tr, const double* __restrict__ ubar,
+                                                 const double* __restrict__ rbar, T* __restrict__ g) {
     const long long n = (long long)A.nx * A.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int z = (int)(i / A.nx);
-        double rt = 0.0, mx = 0.0;
+    const int z = blockIdx.x;
+    const T cu = (T)(2.0 * (ubar[z] - tu[z]) / A.nx), cr = (T)(2.0 * (rbar[z] - tr[z]) / A.nx);
+    for (int x = threadIdx.x; x < A.nx; x += AT) {
+        const long long i = (long long)z * A.nx + x;
+        T rt = 0, mx = 0;
         for (int s = 0; s < A.ns; ++s)
             for (int l = 0; l < 9; ++l) {
-                const double v = f[(s * 9 + l) * n + i];
+                const T v = f[(s * 9 + l) * n + i];
                 rt += v;
-                mx += v * cx(l);
+                mx += v * (T)cx(l);
             }
-        const double u = mx / rt;
-        const double gu = 2.0 * (ubar[z] - tu[z]) / A.nx / rt, gr = 2.0 * (rbar[z] - tr[z]) / A.nx;
+        const T u = mx / rt, gu = cu / rt;
         for (int s = 0; s < A.ns; ++s)
-            for (int l = 0; l < 9; ++l) g[(s * 9 + l) * n + i] = gu * (cx(l) - u) + (s == 0 ? gr : 0.0);
+            for (int l = 0; l < 9; ++l) g[(s * 9 + l) * n + i] = gu * ((T)cx(l) - u) + (s == 0 ? cr : (T)0);
     }
 }
 
 // The initial populations are W_l rho (equilibrium at rest): dJ/drho_s = sum_l W_l lam_0.
-__global__ void k_adj_initial(const double* __restrict__ lam0, const AdjConst A, double* __restrict__ g) {
+template <typename T>
+__global__ void k_adj_initial(const T* __restrict__ lam0, const AdjC<T> A, double* __restrict__ g) {
     const long long n = (long long)A.nx * A.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         for (int s = 0; s < A.ns; ++s) {
-            double t = 0.0;
-            for (int l = 0; l < 9; ++l) t += wlb<double>(l) * lam0[(s * 9 + l) * n + i];
-            g[s * n + i] = t;
+            T t = 0;
+            for (int l = 0; l < 9; ++l) t += wlb<T>(l) * lam0[(s * 9 + l) * n + i];
+            g[s * n + i] = (double)t;
         }
 }
 
 int grid_of(long long n) { return (int)((n + AT - 1) / AT); }
+
+template <typename T>
+AdjC<T> adj_const(const AdjConst& D) {
+    AdjC<T> A;
+    A.nx = D.nx;
+    A.nz = D.nz;
+    A.ns = D.ns;
+    A.psi_form = D.psi_form;
+    for (int q = 0; q < 9; ++q) {
+        A.wa[q] = (T)D.wa[q];
+        A.wr[q] = (T)D.wr[q];
+        A.wc[q] = (T)D.wc[q];
+    }
+    for (int s = 0; s < 2; ++s) {
+        A.G1[s] = (T)D.G1[s];
+        A.G2[s] = (T)D.G2[s];
+        A.tau[s] = (T)D.tau[s];
+        A.itau[s] = (T)(1.0 / D.tau[s]);
+        A.irho0[s] = (T)(1.0 / D.rho0[s]);
+    }
+    A.G_AB = (T)D.G_AB;
+    A.g = (T)D.g;
+    return A;
+}
+
+// Scratch of a context: the intermediate fields (12 ns n values, sized for FP64), then the block
+// partials (NPAR 8-byte accumulators per block), then the objective's row averages (2 nz doubles).
+size_t field_bytes(long long n, int ns) { return ((size_t)12 * ns * n * 8 + 255) & ~(size_t)255; }
+size_t part_bytes(long long n) { return ((size_t)NPAR * grid_of(n) * 8 + 255) & ~(size_t)255; }
+
+template <typename T>
+AdjBuf<T> adj_buf(void* scratch, long long n, int ns) {
+    T* p = static_cast<T*>(scratch);
+    const long long m = (long long)ns * n;
+    AdjBuf<T> B;
+    T** fields[] = {&B.rho, &B.jx, &B.jz, &B.psi, &B.qx, &B.qz, &B.rx, &B.rz, &B.dloc, &B.djx, &B.djz, &B.dps};
+    for (int k = 0; k < 12; ++k) *fields[k] = p + k * m;
+    return B;
+}
+
+template <typename T, int NS>
+void enqueue_steps(const AdjC<T>& A, AdjBuf<T> B, typename Acc<T>::A* part, int nb, int nsteps, const T* states,
+                   long long stride, const T*& next, T* const bufs[2], cudaStream_t st) {
+    for (int k = nsteps - 1, t = 0; k >= 0; --k, ++t) {
+        const T* f = states + (long long)k * stride;
+        T* out = bufs[t & 1];
+        k_adj_moments<T, NS><<<nb, AT, 0, st>>>(f, A, B);
+        k_adj_local<T, NS><<<nb, AT, 0, st>>>(f, next, A, B, part, t > 0);
+        k_adj_final<T, NS><<<nb, AT, 0, st>>>(next, A, B, out);
+        next = out;
+    }
+}
 
 }  // namespace
 
@@ -378,41 +474,58 @@ void fill_adj_const(AdjConst& A, const lbm_params& p, int nx, int nz, int ns, do
     A.g = body_force;
 }
 
-cudaError_t launch_adjoint_step(const AdjConst& A, const double* f, const double* lam_next, double* lam,
-                                double* grad, double* scratch, cudaStream_t st) {
-    const long long n = (long long)A.nx * A.nz;
-    const long long m = (long long)A.ns * n;
-    double *rho = scratch, *jx = rho + m, *jz = jx + m, *psi = jz + m, *Fx = psi + m, *Fz = Fx + m;
-    double *dF = Fz + m, *drho = dF + 2 * m, *djx = drho + m, *djz = djx + m, *part = djz + m;
-    const int gb = grid_of(n) < 4096 ? grid_of(n) : 4096;
-    k_adj_moments<<<gb, AT, 0, st>>>(f, A, rho, jx, jz, psi);
-    k_adj_force<<<gb, AT, 0, st>>>(A, rho, psi, Fx, Fz);
-    k_adj_local<<<grid_of(n), AT, 0, st>>>(f, lam_next, A, rho, jx, jz, Fx, Fz, dF, drho, djx, djz, part);
-    k_adj_final<<<grid_of(n), AT, 0, st>>>(lam_next, A, rho, psi, dF, drho, djx, djz, lam, part);
-    k_adj_sum<<<1, AT, 0, st>>>(part, grid_of(n), grad);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_objective(const AdjConst& A, const double* f, const double* tu, const double* tr,
-                                     double* J, double* g, double* scratch, cudaStream_t st) {
-    const long long n = (long long)A.nx * A.nz;
-    double *ubar = scratch, *rbar = scratch + A.nz;
-    k_obj_rows<<<A.nz, AT, 0, st>>>(f, A, ubar, rbar);
-    k_obj_total<<<1, AT, 0, st>>>(A, tu, tr, ubar, rbar, J);
-    if (g) k_obj_grad<<<grid_of(n) < 4096 ? grid_of(n) : 4096, AT, 0, st>>>(f, A, tu, tr, ubar, rbar, g);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_initial(const AdjConst& A, const double* lam0, double* g, cudaStream_t st) {
-    const long long n = (long long)A.nx * A.nz;
-    k_adj_initial<<<grid_of(n) < 4096 ? grid_of(n) : 4096, AT, 0, st>>>(lam0, A, g);
-    return cudaGetLastError();
-}
-
-long long adjoint_scratch_doubles(int nx, int nz, int ns) {
+size_t adjoint_scratch_bytes(int nx, int nz, int ns) {
     const long long n = (long long)nx * nz;
-    const long long step = 11LL * ns * n + (long long)NPAR * grid_of(n);
-    return step > 2LL * nz ? step : 2LL * nz;
+    return field_bytes(n, ns) + part_bytes(n) + (size_t)2 * nz * sizeof(double);
 }
+
+template <typename T>
+cudaError_t launch_adjoint_steps(const AdjConst& D, int nsteps, const T* states, long long stride, const T* lam_in,
+                                 T* lam_a, T* lam_b, const T** lam_out, double* grad, void* scratch, cudaStream_t st) {
+    const long long n = (long long)D.nx * D.nz;
+    const AdjC<T> A = adj_const<T>(D);
+    const AdjBuf<T> B = adj_buf<T>(scratch, n, D.ns);
+    auto* part = reinterpret_cast<typename Acc<T>::A*>(static_cast<char*>(scratch) + field_bytes(n, D.ns));
+    const int nb = grid_of(n);
+    const T* next = lam_in;
+    T* const bufs[2] = {lam_a, lam_b};
+    if (D.ns == 2)
+        enqueue_steps<T, 2>(A, B, part, nb, nsteps, states, stride, next, bufs, st);
+    else
+        enqueue_steps<T, 1>(A, B, part, nb, nsteps, states, stride, next, bufs, st);
+    if (nsteps > 0) k_adj_sum<T><<<1, AT, 0, st>>>(part, nb, grad);
+    *lam_out = next;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_objective(const AdjConst& D, const T* f, const double* tu, const double* tr, double* J,
+                                     T* g, void* scratch, cudaStream_t st) {
+    const long long n = (long long)D.nx * D.nz;
+    const AdjC<T> A = adj_const<T>(D);
+    double* ubar = reinterpret_cast<double*>(static_cast<char*>(scratch) + field_bytes(n, D.ns) + part_bytes(n));
+    double* rbar = ubar + D.nz;
+    k_obj_rows<T><<<D.nz, AT, 0, st>>>(f, A, ubar, rbar);
+    k_obj_total<<<1, AT, 0, st>>>(D.nz, tu, tr, ubar, rbar, J);
+    if (g) k_obj_grad<T><<<D.nz, AT, 0, st>>>(f, A, tu, tr, ubar, rbar, g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_initial(const AdjConst& D, const T* lam0, double* g, cudaStream_t st) {
+    const long long n = (long long)D.nx * D.nz;
+    const AdjC<T> A = adj_const<T>(D);
+    k_adj_initial<T><<<grid_of(n) < 4096 ? grid_of(n) : 4096, AT, 0, st>>>(lam0, A, g);
+    return cudaGetLastError();
+}
+
+#define LBM_ADJ_INST(T)                                                                                           \
+    template cudaError_t launch_adjoint_steps<T>(const AdjConst&, int, const T*, long long, const T*, T*, T*,     \
+                                                 const T**, double*, void*, cudaStream_t);                       \
+    template cudaError_t launch_adjoint_objective<T>(const AdjConst&, const T*, const double*, const double*,     \
+                                                     double*, T*, void*, cudaStream_t);                          \
+    template cudaError_t launch_adjoint_initial<T>(const AdjConst&, const T*, double*, cudaStream_t);
+LBM_ADJ_INST(double)
+LBM_ADJ_INST(float)
 
 }  // namespace lbm

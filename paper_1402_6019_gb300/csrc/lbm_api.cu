@@ -50,7 +50,8 @@ struct lbm_ctx {
     double* avg = nullptr;
     double* staging = nullptr;  // (ns + 2) * n doubles
     double* fexport = nullptr;  // ns * 9 * n doubles
-    double* adj_scratch = nullptr;  // adjoint: adjoint_scratch_doubles(nx, nz, ns)
+    void* adj_scratch = nullptr;  // adjoint: adjoint_scratch_bytes(nx, nz, ns)
+    void* adj_lam = nullptr;      // adjoint: second lam buffer, ns * 9 * n doubles
     void* gfield = nullptr;     // two-pass ghost fields
     alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
@@ -231,7 +232,7 @@ static void release(lbm_ctx* c) {
     void* ptrs[] = {c->f[0],       c->f[1],    c->part_row[0], c->part_row[1], c->part_col[0],
                     c->part_col[1], c->sched,   c->ticket,      c->flag,        c->out,
                     c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d,
-                    c->adj_scratch};
+                    c->adj_scratch, c->adj_lam};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_out) cudaFreeHost(c->host_out);
@@ -743,6 +744,72 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, int where) {
     return LBM_OK;
 }
 
+// A snapshot: the current population buffer in the internal layout, then a 256-byte tail with
+// the reference densities of the FP32 deviations and the step counter.
+struct SnapTail {
+    double rho_ref[2];
+    long long step;
+};
+static size_t pop_bytes(const lbm_ctx* c) { return (size_t)c->d.n_species * 9 * c->plane * c->esize; }
+
+extern "C" long long lbm_snapshot_bytes(const lbm_ctx* c) { return c ? (long long)(pop_bytes(c) + 256) : -1; }
+
+extern "C" int lbm_snapshot(lbm_ctx* c, void* dst) {
+    if (!c) return LBM_EINVAL;
+    if (!dst) return fail(c, LBM_EINVAL, "dst is NULL");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    CK(cudaMemcpyAsync(dst, c->f[c->cur], pop_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    const SnapTail t{{c->rho_ref[0], c->rho_ref[1]}, c->step};
+    // pageable source: staged before the call returns
+    CK(cudaMemcpyAsync(static_cast<char*>(dst) + pop_bytes(c), &t, sizeof t, cudaMemcpyHostToDevice, c->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_restore(lbm_ctx* c, const void* src) {
+    if (!c) return LBM_EINVAL;
+    if (!src) return fail(c, LBM_EINVAL, "src is NULL");
+    CK(cudaSetDevice(c->d.device));
+    SnapTail t;
+    CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + pop_bytes(c), sizeof t, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->f[0], src, pop_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    if (t.rho_ref[0] != c->rho_ref[0] || t.rho_ref[1] != c->rho_ref[1]) {
+        c->rho_ref[0] = t.rho_ref[0];
+        c->rho_ref[1] = t.rho_ref[1];
+        refresh_const(c);
+        drop_graphs(c);
+    }
+    c->cur = 0;
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
+    c->samples = 0;
+    c->pending = false;
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = t.step;
+    c->have_fields = true;
+    return LBM_OK;
+}
+
+extern "C" int lbm_export_state(lbm_ctx* c, void* f, int precision) {
+    if (!c) return LBM_EINVAL;
+    if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+    if (precision != LBM_FP64 && precision != LBM_FP32) return fail(c, LBM_EINVAL, "precision must be LBM_FP64 or LBM_FP32");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    const Batch B = batch(c);
+    const int ns = c->d.n_species;
+    const Batch* pb = c->pull ? &B : nullptr;
+    if (precision == LBM_FP64)
+        CK(c->d.precision == LBM_FP64 ? launch_export(ns, (const double*)c->f[c->cur], (double*)f, c->c64, pb, c->stream)
+                                      : launch_export(ns, (const float*)c->f[c->cur], (double*)f, c->c32, pb, c->stream));
+    else
+        CK(c->d.precision == LBM_FP64 ? launch_export(ns, (const double*)c->f[c->cur], (float*)f, c->c64, pb, c->stream)
+                                      : launch_export(ns, (const float*)c->f[c->cur], (float*)f, c->c32, pb, c->stream));
+    c->launches += 1;
+    return LBM_OK;
+}
+
 extern "C" int lbm_get_fields(lbm_ctx* c, double* rho, double* u, double* f, int where) {
     if (!c) return LBM_EINVAL;
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
@@ -1046,47 +1113,96 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
 }
 
 // ---------------------------------------------------------------------------------------
-// Discrete adjoint (periodic single lattice, FP64)
+// Discrete adjoint (periodic single lattice)
 // ---------------------------------------------------------------------------------------
-static int adjoint_ready(lbm_ctx* c, AdjConst& A) {
+static int adjoint_ready(lbm_ctx* c, AdjConst& A, int precision) {
+    if (precision != LBM_FP64 && precision != LBM_FP32) return fail(c, LBM_EINVAL, "precision must be LBM_FP64 or LBM_FP32");
     if (c->d.z_boundary != LBM_PERIODIC) return fail(c, LBM_EINVAL, "the adjoint needs a periodic lattice");
     if (c->inst.size() > 1) return fail(c, LBM_EINVAL, "the adjoint is for a single lattice, not a batch");
     CK(cudaSetDevice(c->d.device));
-    if (!c->adj_scratch)
-        CK(cudaMalloc(&c->adj_scratch,
-                      (size_t)adjoint_scratch_doubles(c->d.nx, c->d.nz, c->d.n_species) * sizeof(double)));
+    if (!c->adj_scratch) CK(cudaMalloc(&c->adj_scratch, adjoint_scratch_bytes(c->d.nx, c->d.nz, c->d.n_species)));
     fill_adj_const(A, c->p, c->d.nx, c->d.nz, c->d.n_species, c->inst.empty() ? c->p.body_force : c->inst[0].g);
     return LBM_OK;
 }
 
-extern "C" int lbm_adjoint_step(lbm_ctx* c, const double* f, const double* lam_next, double* lam, double* grad) {
+static size_t state_values(const lbm_ctx* c) { return (size_t)c->d.n_species * 9 * c->d.nx * c->d.nz; }
+
+extern "C" int lbm_record_states(lbm_ctx* c, int nsteps, void* states, int precision) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 0 || (nsteps > 0 && !states)) return fail(c, LBM_EINVAL, "nsteps < 0 or states is NULL");
+    const size_t bytes = state_values(c) * (precision == LBM_FP32 ? sizeof(float) : sizeof(double));
+    for (int k = 0; k < nsteps; ++k) {
+        if (int r = lbm_export_state(c, static_cast<char*>(states) + k * bytes, precision)) return r;
+        if (int r = lbm_step(c, 1)) return r;
+    }
+    return LBM_OK;
+}
+
+template <typename T>
+static int adjoint_steps(lbm_ctx* c, const AdjConst& A, int nsteps, const T* states, const T* lam_in, T* lam_a,
+                         T* lam_b, T* lam_user, double* grad) {
+    const T* out = nullptr;
+    CK(launch_adjoint_steps<T>(A, nsteps, states, (long long)state_values(c), lam_in, lam_a, lam_b, &out, grad,
+                               c->adj_scratch, c->stream));
+    if (out != lam_user)
+        CK(cudaMemcpyAsync(lam_user, out, state_values(c) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    c->launches += 3LL * nsteps + (nsteps > 0 ? 1 : 0);
+    return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_step(lbm_ctx* c, const void* f, const void* lam_next, void* lam, double* grad,
+                                int precision) {
     if (!c) return LBM_EINVAL;
     if (!f || !lam_next || !lam || !grad) return fail(c, LBM_EINVAL, "NULL pointer");
     if (lam == lam_next || lam == f) return fail(c, LBM_EINVAL, "lam must not overlap lam_next or f");
     AdjConst A;
-    if (int r = adjoint_ready(c, A)) return r;
-    CK(launch_adjoint_step(A, f, lam_next, lam, grad, c->adj_scratch, c->stream));
-    c->launches += 5;
-    return LBM_OK;
+    if (int r = adjoint_ready(c, A, precision)) return r;
+    if (precision == LBM_FP64)
+        return adjoint_steps<double>(c, A, 1, (const double*)f, (const double*)lam_next, (double*)lam, nullptr,
+                                     (double*)lam, grad);
+    return adjoint_steps<float>(c, A, 1, (const float*)f, (const float*)lam_next, (float*)lam, nullptr, (float*)lam,
+                                grad);
 }
 
-extern "C" int lbm_adjoint_objective(lbm_ctx* c, const double* f, const double* target_u, const double* target_rho,
-                                     double* J, double* dJdf) {
+extern "C" int lbm_adjoint_steps(lbm_ctx* c, int nsteps, const void* states, void* lam, double* grad, int precision) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 0 || !lam || !grad || (nsteps > 0 && !states)) return fail(c, LBM_EINVAL, "bad argument");
+    AdjConst A;
+    if (int r = adjoint_ready(c, A, precision)) return r;
+    if (!c->adj_lam) CK(cudaMalloc(&c->adj_lam, state_values(c) * sizeof(double)));
+    // the first step writes the context's buffer, the second the caller's (read no more), ...
+    if (precision == LBM_FP64)
+        return adjoint_steps<double>(c, A, nsteps, (const double*)states, (const double*)lam, (double*)c->adj_lam,
+                                     (double*)lam, (double*)lam, grad);
+    return adjoint_steps<float>(c, A, nsteps, (const float*)states, (const float*)lam, (float*)c->adj_lam,
+                                (float*)lam, (float*)lam, grad);
+}
+
+extern "C" int lbm_adjoint_objective(lbm_ctx* c, const void* f, const double* target_u, const double* target_rho,
+                                     double* J, void* dJdf, int precision) {
     if (!c) return LBM_EINVAL;
     if (!f || !target_u || !target_rho || !J) return fail(c, LBM_EINVAL, "NULL pointer");
     AdjConst A;
-    if (int r = adjoint_ready(c, A)) return r;
-    CK(launch_adjoint_objective(A, f, target_u, target_rho, J, dJdf, c->adj_scratch, c->stream));
+    if (int r = adjoint_ready(c, A, precision)) return r;
+    if (precision == LBM_FP64)
+        CK(launch_adjoint_objective<double>(A, (const double*)f, target_u, target_rho, J, (double*)dJdf,
+                                            c->adj_scratch, c->stream));
+    else
+        CK(launch_adjoint_objective<float>(A, (const float*)f, target_u, target_rho, J, (float*)dJdf, c->adj_scratch,
+                                           c->stream));
     c->launches += dJdf ? 3 : 2;
     return LBM_OK;
 }
 
-extern "C" int lbm_adjoint_initial(lbm_ctx* c, const double* lam0, double* g_rho) {
+extern "C" int lbm_adjoint_initial(lbm_ctx* c, const void* lam0, double* g_rho, int precision) {
     if (!c) return LBM_EINVAL;
     if (!lam0 || !g_rho) return fail(c, LBM_EINVAL, "NULL pointer");
     AdjConst A;
-    if (int r = adjoint_ready(c, A)) return r;
-    CK(launch_adjoint_initial(A, lam0, g_rho, c->stream));
+    if (int r = adjoint_ready(c, A, precision)) return r;
+    if (precision == LBM_FP64)
+        CK(launch_adjoint_initial<double>(A, (const double*)lam0, g_rho, c->stream));
+    else
+        CK(launch_adjoint_initial<float>(A, (const float*)lam0, g_rho, c->stream));
     c->launches += 1;
     return LBM_OK;
 }

@@ -164,8 +164,8 @@ cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, const Batch&
 template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, const Batch* B,
                         cudaStream_t st);
-template <typename T>
-cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, const Batch* B, cudaStream_t st);
+template <typename T, typename O>
+cudaError_t launch_export(int ns, const T* f, O* out, const StepConst<T>& C, const Batch* B, cudaStream_t st);
 // The inverse of launch_export: plain FP64 post-streaming populations in, the stored layout out
 // (deviations from W_l rho_ref); the pull layout's ghosts are filled by launch_pull_images.
 template <typename T>
@@ -191,18 +191,25 @@ struct AdjConst {
     double G_AB, g;
 };
 void fill_adj_const(AdjConst& A, const lbm_params& p, int nx, int nz, int ns, double body_force);
-// Doubles of scratch launch_adjoint_step and launch_adjoint_objective need.
-long long adjoint_scratch_doubles(int nx, int nz, int ns);
-// lam = dJ/df_n from lam_next = dJ/df_{n+1} at the state f = f_n; adds dJ/dtheta to grad[8].
-cudaError_t launch_adjoint_step(const AdjConst& A, const double* f, const double* lam_next, double* lam,
-                                double* grad, double* scratch, cudaStream_t st);
+// Bytes of scratch the adjoint launches need (one buffer serves all of them, used in turn).
+size_t adjoint_scratch_bytes(int nx, int nz, int ns);
+// nsteps adjoint steps backwards over the states f_k .. f_{k+nsteps-1} (states[j] at
+// states + j stride): lam_in = dJ/df_{k+nsteps}; the steps write alternately into lam_a and
+// lam_b (neither may be lam_in's buffer while it is read: lam_b may be it, it is first written
+// by the second step); *lam_out receives the buffer holding dJ/df_k (lam_in when nsteps = 0).
+// Adds dJ/dtheta to grad[8].  T = double or float.
+template <typename T>
+cudaError_t launch_adjoint_steps(const AdjConst& D, int nsteps, const T* states, long long stride, const T* lam_in,
+                                 T* lam_a, T* lam_b, const T** lam_out, double* grad, void* scratch, cudaStream_t st);
 // J (one double) of the velocity / density profile objective at f and, when g is not null,
 // g = dJ/df.
-cudaError_t launch_adjoint_objective(const AdjConst& A, const double* f, const double* tu, const double* tr,
-                                     double* J, double* g, double* scratch, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adjoint_objective(const AdjConst& D, const T* f, const double* tu, const double* tr, double* J,
+                                     T* g, void* scratch, cudaStream_t st);
 // g [ns][nz][nx] = sum_l W_l lam0: the derivative with respect to the densities of an initial
 // state at rest.
-cudaError_t launch_adjoint_initial(const AdjConst& A, const double* lam0, double* g, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adjoint_initial(const AdjConst& D, const T* lam0, double* g, cudaStream_t st);
 
 // Twopass tile (threads per CTA: TPX x TPZ sites).
 constexpr int TPX = 32, TPZ = 8;

@@ -48,8 +48,8 @@ __global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho
 
 // The post-streaming populations as plain FP64 values, [ns][9][nz][nx]: the stored value of
 // (x, l) in the push layout, the gather of the pull layout.
-template <typename T>
-__global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ out, const StepConst<T> C,
+template <typename T, typename O>
+__global__ void k_export(int ns, const T* __restrict__ f, O* __restrict__ out, const StepConst<T> C,
                          const InstGeom* __restrict__ inst, int ninst) {
     const long long n = (long long)C.nx * C.nz;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -61,7 +61,7 @@ __global__ void k_export(int ns, const T* __restrict__ f, double* __restrict__ o
                 long long o = (long long)zg * C.pitch + x;
                 int ls = l;
                 if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
-                out[(s * 9 + l) * n + i] = (double)f[(s * 9 + ls) * C.plane + o] + wlb<double>(l) * (double)C.rho_ref[s];
+                out[(s * 9 + l) * n + i] = (O)((double)f[(s * 9 + ls) * C.plane + o] + wlb<double>(l) * (double)C.rho_ref[s]);
             }
     }
 }
@@ -157,11 +157,11 @@ cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const 
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_export(int ns, const T* f, double* out, const StepConst<T>& C, const Batch* B, cudaStream_t st) {
+template <typename T, typename O>
+cudaError_t launch_export(int ns, const T* f, O* out, const StepConst<T>& C, const Batch* B, cudaStream_t st) {
     const long long n = (long long)C.nx * C.nz;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_export<T><<<blocks, 256, 0, st>>>(ns, f, out, C, B ? B->inst : nullptr, B ? B->ninst : 0);
+    k_export<T, O><<<blocks, 256, 0, st>>>(ns, f, out, C, B ? B->inst : nullptr, B ? B->ninst : 0);
     return cudaGetLastError();
 }
 
@@ -208,10 +208,14 @@ template cudaError_t launch_init<float>(int, float*, const double*, const double
                                         const Batch*, cudaStream_t);
 template cudaError_t launch_init<double>(int, double*, const double*, const double*, const StepConst<double>&,
                                          const Batch*, cudaStream_t);
-template cudaError_t launch_export<float>(int, const float*, double*, const StepConst<float>&, const Batch*,
-                                          cudaStream_t);
-template cudaError_t launch_export<double>(int, const double*, double*, const StepConst<double>&, const Batch*,
-                                           cudaStream_t);
+template cudaError_t launch_export<float, double>(int, const float*, double*, const StepConst<float>&, const Batch*,
+                                                  cudaStream_t);
+template cudaError_t launch_export<double, double>(int, const double*, double*, const StepConst<double>&,
+                                                   const Batch*, cudaStream_t);
+template cudaError_t launch_export<float, float>(int, const float*, float*, const StepConst<float>&, const Batch*,
+                                                 cudaStream_t);
+template cudaError_t launch_export<double, float>(int, const double*, float*, const StepConst<double>&, const Batch*,
+                                                  cudaStream_t);
 template cudaError_t launch_import<float>(int, float*, const double*, const StepConst<float>&, const Batch*,
                                           cudaStream_t);
 template cudaError_t launch_import<double>(int, double*, const double*, const StepConst<double>&, const Batch*,

@@ -78,9 +78,15 @@ SIGNATURES = {
     "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "lbm_set_populations": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
-    "lbm_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
-    "lbm_adjoint_objective": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
-    "lbm_adjoint_initial": (ctypes.c_int, [_VP, _VP, _VP]),
+    "lbm_snapshot_bytes": (ctypes.c_longlong, [_VP]),
+    "lbm_snapshot": (ctypes.c_int, [_VP, _VP]),
+    "lbm_restore": (ctypes.c_int, [_VP, _VP]),
+    "lbm_export_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "lbm_record_states": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
+    "lbm_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "lbm_adjoint_steps": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int]),
+    "lbm_adjoint_objective": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
+    "lbm_adjoint_initial": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
 }
 
 _lib = None
@@ -251,21 +257,62 @@ def _dev(t):
     if t is None:
         return None
     if not hasattr(t, "data_ptr"):
-        raise TypeError("the adjoint entry points take CUDA float64 tensors")
+        raise TypeError("the adjoint entry points take CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _prec(*tensors):
+    """LBM_FP64 / LBM_FP32 from the dtype of the state / adjoint tensors (all alike)."""
+    kinds = {str(t.dtype) for t in tensors if t is not None}
+    if kinds == {"torch.float64"}:
+        return LBM_FP64
+    if kinds == {"torch.float32"}:
+        return LBM_FP32
+    raise TypeError(f"state and adjoint tensors must all be float64 or all float32, got {kinds}")
+
+
+def lbm_snapshot_bytes(h) -> int:
+    return load().lbm_snapshot_bytes(h)
+
+
+def lbm_snapshot(h, dst):
+    """dst: CUDA tensor of at least lbm_snapshot_bytes(h) bytes (asynchronous)."""
+    if dst.numel() * dst.element_size() < lbm_snapshot_bytes(h):
+        raise ValueError("snapshot buffer too small")
+    _check(load().lbm_snapshot(h, _dev(dst)), h)
+
+
+def lbm_restore(h, src):
+    _check(load().lbm_restore(h, _dev(src)), h)
+
+
+def lbm_export_state(h, f):
+    """f: CUDA tensor [ns, 9, nz, nx], float64 or float32 (asynchronous)."""
+    _check(load().lbm_export_state(h, _dev(f), _prec(f)), h)
+
+
+def lbm_record_states(h, nsteps, states):
+    """states: CUDA tensor [nsteps, ns, 9, nz, nx] (float64 or float32), written asynchronously."""
+    _check(load().lbm_record_states(h, int(nsteps), _dev(states), _prec(states)), h)
+
+
 def lbm_adjoint_step(h, f, lam_next, lam, grad):
-    """Device tensors (float64): lam <- dJ/df_n, grad[8] += dJ/dtheta (asynchronous)."""
-    _check(load().lbm_adjoint_step(h, _dev(f), _dev(lam_next), _dev(lam), _dev(grad)), h)
+    """CUDA tensors: lam <- dJ/df_n, grad[8] (float64) += dJ/dtheta (asynchronous)."""
+    _check(load().lbm_adjoint_step(h, _dev(f), _dev(lam_next), _dev(lam), _dev(grad), _prec(f, lam_next, lam)), h)
+
+
+def lbm_adjoint_steps(h, nsteps, states, lam, grad):
+    """lam (in place): dJ/df after the recorded steps -> dJ/df before them; grad += dJ/dtheta."""
+    _check(load().lbm_adjoint_steps(h, int(nsteps), _dev(states), _dev(lam), _dev(grad), _prec(states, lam)), h)
 
 
 def lbm_adjoint_objective(h, f, target_u, target_rho, J, dJdf=None):
-    _check(load().lbm_adjoint_objective(h, _dev(f), _dev(target_u), _dev(target_rho), _dev(J), _dev(dJdf)), h)
+    _check(load().lbm_adjoint_objective(h, _dev(f), _dev(target_u), _dev(target_rho), _dev(J), _dev(dJdf),
+                                        _prec(f, dJdf)), h)
 
 
 def lbm_adjoint_initial(h, lam0, g_rho):
-    _check(load().lbm_adjoint_initial(h, _dev(lam0), _dev(g_rho)), h)
+    _check(load().lbm_adjoint_initial(h, _dev(lam0), _dev(g_rho), _prec(lam0)), h)
 
 
 # ---- convenience ---------------------------------------------------------------------------

@@ -148,4 +148,13 @@ def workload(name: str, seed: int = 1402):
         return dict(nx=1024, nz=sum(heights), n_species=2, z_boundary=1, params=dict(EMULSION_PARAMS),
                     rho=np.concatenate(rhos, axis=1), instances=heights, drives=drives,
                     note="48 walled channels, 1024 x (32, 64, ..., 512) x 3 body forces, packing 0.85")
+    if name == "adjoint_256":
+        # calibration run: the emulsion on a 256 x 256 periodic lattice under a body force,
+        # 500 steps, scored against seeded target profiles across the lattice (a velocity of the
+        # order the drive reaches, a density of species A between the two phases' values)
+        rho, frac = disk_packing(256, 256, 0.8, seed)
+        return dict(nx=256, nz=256, n_species=2, z_boundary=0, params=dict(EMULSION_PARAMS, body_force=1e-5),
+                    rho=rho, steps=500, checkpoint=25,
+                    target_u=1e-3 * uniform(seed + 1, 256), target_rho=0.3 + 0.6 * uniform(seed + 2, 256),
+                    note=f"256x256 periodic disk packing, covered {frac:.3f}, body force 1e-5, 500 steps")
     raise KeyError(name)
