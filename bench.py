@@ -10,10 +10,13 @@ Default workload: the two-component A/B emulsion on a 1024 x 1024 periodic latti
 populations stored as deviations, FP64 reductions (disk packing at fraction 0.8, radii
 12 +- 3, G_AA = (-9.0, 8.1), G_BB = (-8.0, 7.1), G_AB = 0.405, rho0 = 0.83).
 
-Metric: MLUPS (million lattice-site updates per second, whole job).  Between timed steps a
-buffer larger than L2 is written (cold L2 for every step); each step is bracketed by CUDA events
-on the library's stream.  The step kernel is additionally timed alone (lbm_profile) for the
-roofline line.
+Metric: MLUPS (million lattice-site updates per second, whole job).  Default L2 handling: four
+lattices of the workload are stepped in turn (each step's input comes from DRAM); --l2 flush
+writes and reads a buffer larger than L2 between steps.  The timed region is bracketed by CUDA
+events on the library's stream.  Roofline: the step kernel's average launch duration over the
+timed region (one launch per step); a second pass with events around every launch
+(lbm_profile) gives its serialised duration.  --workload adjoint_256 measures gradients of a run
+(forward, recompute, adjoint) instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -226,6 +229,199 @@ def run_reference(a, w):
     }))
 
 
+# adjoint kernels: values read and written per site and species (states, lam, intermediate
+# fields of the site; neighbour values come from cache): k_adj_moments reads f (9) and writes
+# rho, j, psi (4); k_adj_local reads f and lam_{n+1} (18) and rho, j, psi (4), and writes
+# psi dF, rho dF (4), the site's own dJ/drho, dJ/dj and psi' (4); k_adj_final reads lam_{n+1}
+# (9) and those 8 fields and writes lam_n (9)
+ADJ_VALUES = {"moments": 13, "local": 30, "final": 26}
+
+
+def adjoint_sample(w, n=64, steps=20):
+    """The oracle's bounded sample of the calibration workload: an n x n cut, `steps` steps."""
+    rho = np.ascontiguousarray(w["rho"][:, :n, :n])
+    return rho, w["target_u"][:n].copy(), w["target_rho"][:n].copy(), steps
+
+
+def cpu_baseline_adjoint(w, seconds=12.0):
+    """The oracle's run gradient (forward storing every state, adjoint step by step) on a bounded
+    sample of the calibration workload, repeated until `seconds` have passed."""
+    import oracle
+
+    oracle.build()
+    rho, tu, tr, steps = adjoint_sample(w)
+    n = rho.shape[1]
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        oracle.rollout_gradient(n, n, w["n_species"], rho, steps, tu, tr, **w["params"])
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n * n * steps * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{k} oracle run gradients ({steps} steps forward + {steps} adjoint steps) on a {n}x{n} cut "
+                      f"of the workload, {dt:.1f} s wall, OpenMP threads={cores} (forward steps; the adjoint is "
+                      "single-threaded)"}
+
+
+def run_reference_adjoint(a, w):
+    import oracle
+
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    oracle.build()
+    rho, tu, tr, steps = adjoint_sample(w)
+    n = rho.shape[1]
+    for _ in range(a.warmup):
+        oracle.rollout_gradient(n, n, w["n_species"], rho, steps, tu, tr, **w["params"])
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.rollout_gradient(n, n, w["n_species"], rho, steps, tu, tr, **w["params"])
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n * n * steps * a.steps / dt / 1e6
+    sample = f"{a.steps} timed oracle run gradients of {steps} steps on a {n}x{n} cut of {a.workload}"
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": a.workload, "sample": f"{n}x{n}, {steps} steps"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_adjoint(a, w):
+    """The calibration workload: one bench step = one whole gradient of the run (forward with a
+    snapshot every `checkpoint` steps, objective, then per segment restore + recorded recompute
+    + adjoint sweep, and the initial-density gradient).  MLUPS = differentiated site-steps per
+    second."""
+    import torch
+
+    from paper_1402_6019_gb300 import adjoint as A
+    from paper_1402_6019_gb300 import lbm as L
+    from paper_1402_6019_gb300 import replicas
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+
+        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    nx, nz, ns, run_steps, ck = w["nx"], w["nz"], w["n_species"], w["steps"], w["checkpoint"]
+    sites = nx * nz
+    prec = L.LBM_FP32 if a.precision == "fp32" else L.LBM_FP64
+    esize = 4 if a.precision == "fp32" else 8
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # torch's work and the library's share one stream
+    lat = L.Lattice(nx, nz, ns, prec, L.LBM_PERIODIC, device=local, stream=stream.cuda_stream, **w["params"])
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    rho, tu, tr = dev(w["rho"]), dev(w["target_u"]), dev(w["target_rho"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush_src = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def gradient():
+        return A.rollout_gradient(lat, rho, run_steps, tu, tr, checkpoint=ck)
+
+    for _ in range(a.warmup):
+        gradient()
+    barrier()
+
+    def timed(profile):
+        if profile:
+            L.lbm_profile(lat.h, True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+        for k in range(a.steps):
+            flush.fill_(float(k))  # no data of the previous gradient left in L2
+            flush_src.sum()
+            starts[k].record(stream)
+            gradient()
+            ends[k].record(stream)
+        barrier()
+        return float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+
+    launches0 = lat.launches
+    with Clocks(local) as clk:
+        grad_ms = timed(False)
+    launches = lat.launches - launches0
+    # the same gradients again with every step-kernel and adjoint-kernel launch bracketed by
+    # events (which also runs the steps one by one instead of in graphs): the kernel durations
+    prof_ms = timed(True)
+    step_ms, step_n = L.lbm_profile_read(lat.h)
+    adj_ms, adj_n = L.lbm_profile_read_adjoint(lat.h)
+    L.lbm_profile(lat.h, False)
+    grad_s, job = replicas.aggregate(grad_ms * 1e-3, sites * run_steps * a.steps, dist=dist, device="cuda")
+    ms_per_grad = grad_s * 1e3 / a.steps
+    value = job / grad_s / 1e6
+
+    # the dominant kernel of the gradient: the step kernel (forward and recompute) or one of the
+    # three adjoint kernels, by summed event time
+    kernels = {"lbm::k_pull<T, 2, M_WRITE>": (step_ms, step_n, 2 * 9 * ns * esize)}
+    for name, ms in zip(("moments", "local", "final"), adj_ms):
+        kernels[f"lbm::k_adj_{name}<T, {ns}>"] = (ms, adj_n, ADJ_VALUES[name] * ns * esize)
+    top = max(kernels, key=lambda k: kernels[k][0])
+    ms, n, bps = kernels[top]
+    avg = ms / max(n, 1)
+    achieved = bps * sites / (avg * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind, "kernel": top,
+                "kernel_ms": round(avg, 5), "algorithmic_bytes_per_site": bps,
+                "share_of_gradient": round(ms / max(prof_ms, 1e-9), 3),
+                "kernels_ms_per_gradient": {k: round(v[0] / a.steps, 3) for k, v in kernels.items()},
+                "timing": "kernel durations from CUDA events around every launch in a second, profiled "
+                          f"pass over the same {a.steps} gradients ({prof_ms / a.steps:.2f} ms per gradient "
+                          "with the events)"}
+
+    # end to end through the public API with host buffers: the initial densities uploaded from
+    # pinned host memory, the gradients (densities and parameters) and J read back
+    rho_pin = torch.from_numpy(np.ascontiguousarray(w["rho"])).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_n = max(1, min(a.steps, 3))
+    for _ in range(e2e_n):
+        r = rho_pin.to("cuda", non_blocking=True)
+        J, g_rho, grad = A.rollout_gradient(lat, r, run_steps, tu, tr, checkpoint=ck)
+        g_host, th_host = g_rho.cpu(), grad.cpu()
+    barrier()
+    dt, e2e_job = replicas.aggregate(time.perf_counter() - t0, sites * run_steps * e2e_n, dist=dist, device="cuda")
+    e2e = {"value": round(e2e_job / dt / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": int(rho_pin.numel() * 8),
+           "d2h_bytes_per_step": int(g_host.numel() * 8 + th_host.numel() * 8 + 8), "steps": e2e_n}
+    if rank != 0:
+        return
+    line = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_per_grad, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "nx": nx, "nz": nz, "n_species": ns, "precision": a.precision,
+                   "run_steps": run_steps, "checkpoint": ck,
+                   "step": "one gradient: forward with snapshots, objective, recompute + adjoint per segment",
+                   "unit": "differentiated site-steps per second",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "a 256 MiB write then a 256 MiB read between timed gradients"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_adjoint(w)
+    print(json.dumps(line))
+
+
 def main():
     a = _args()
     from paper_1402_6019_gb300 import workloads as W
@@ -234,6 +430,8 @@ def main():
 
     rank, world, local = _dist()
     w = W.workload(a.workload, seed=replicas.replica_seed(1402, replicas.from_env()))
+    if "target_u" in w:  # the calibration workload: gradients of a run
+        return run_reference_adjoint(a, w) if a.impl == "reference" else run_adjoint(a, w)
     if a.impl == "reference":
         return run_reference(a, w)
 
@@ -298,11 +496,7 @@ def main():
     for lt in lats:
         lt.synchronize()
 
-    for lt in lats:
-        L.lbm_profile(lt.h, True)
-    launches0 = sum(lt.launches for lt in lats)
-    barrier()
-    with Clocks(local) as clk:
+    def timed():
         if flush is not None:
             starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
             ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -312,16 +506,25 @@ def main():
                 lat.step(1)
                 ends[k].record(stream)
             barrier()
-            step_ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
-        else:
-            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            t0.record(stream)
-            for k in range(a.steps):
-                lats[k % n_rot].step(1)
-            t1.record(stream)
-            barrier()
-            step_ms = float(t0.elapsed_time(t1))
+            return float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(a.steps):
+            lats[k % n_rot].step(1)
+        t1.record(stream)
+        barrier()
+        return float(t0.elapsed_time(t1))
+
+    launches0 = sum(lt.launches for lt in lats)
+    barrier()
+    with Clocks(local) as clk:
+        step_ms = timed()
     launches = sum(lt.launches for lt in lats) - launches0
+    # the same steps again with CUDA events around every step-kernel launch (which serialises the
+    # launches: no overlap of a launch with the previous kernel's drain): the kernel's duration
+    for lt in lats:
+        L.lbm_profile(lt.h, True)
+    prof_ms = timed()
     kern_ms, kern_n = 0.0, 0
     for lt in lats:
         km, kn = L.lbm_profile_read(lt.h)
@@ -333,9 +536,14 @@ def main():
     ms_per_step = step_s * 1e3 / a.steps
     value = job_sites / (ms_per_step * 1e-3) / 1e6
 
-    # roofline of the dominant kernel (the fused step kernel)
+    # roofline of the dominant kernel (the step kernel).  When every step is one launch of it (the
+    # pull kernel folds each step's reduction into the next launch), its average launch duration
+    # is the timed region over the launches, as the launches overlap (programmatic dependent
+    # launch); otherwise the event-bracketed durations of the second pass
     bps = BYTES_PER_SITE[(a.precision, ns)]
-    kern_avg_ms = kern_ms / max(kern_n, 1)
+    kern_ser_ms = kern_ms / max(kern_n, 1)
+    one_launch = launches == a.steps
+    kern_avg_ms = step_ms / a.steps if one_launch else kern_ser_ms
     achieved = bps * sites / (kern_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     traffic = _traffic(kernel_source_hash(a.kernel), a.workload, a.precision,
@@ -347,7 +555,13 @@ def main():
                            "twopass": "lbm::k_density + lbm::k_twopass<T, 2, M_WRITE|M_OBS>",
                            "sweep": "lbm::k_fused<T, 2, M_WRITE|M_OBS>"}[a.kernel],
                 "kernel_ms": round(kern_avg_ms, 5),
-                "algorithmic_bytes_per_site": bps}
+                "kernel_ms_serialised": round(kern_ser_ms, 5),
+                "algorithmic_bytes_per_site": bps,
+                "timing": ("average launch duration over the timed region (one step-kernel launch per step, "
+                           "CUDA events on the library's stream)" if one_launch else
+                           "kernel duration from CUDA events around every launch in a second pass") +
+                          f"; kernel_ms_serialised: events around every launch in a second pass over the same "
+                          f"{a.steps} steps, which serialises the launches ({prof_ms / a.steps * 1e3:.2f} us per step)"}
 
     # end to end through the public API with host buffers: upload the fields from pinned host
     # memory, then per step lbm_step + lbm_averages (D2H of the step's observables)

@@ -173,6 +173,10 @@ long long lbm_launch_count(const lbm_ctx *c);
    launches timed since profiling was enabled.  lbm_profile_read synchronises. */
 int lbm_profile(lbm_ctx *c, int enable);
 int lbm_profile_read(lbm_ctx *c, double *step_kernel_ms, long long *launches);
+/* While profiling is enabled, every adjoint step (lbm_adjoint_step, lbm_adjoint_steps) also
+   brackets each of its three kernels with CUDA events: ms[3] receives their summed times in
+   milliseconds (moments, local, final) and steps the adjoint steps timed.  Synchronises. */
+int lbm_profile_read_adjoint(lbm_ctx *c, double *ms, long long *steps);
 
 /* One-line description of the last failure on c (or of the last lbm_create failure when
    c is NULL).  Valid until the next call on c. */

@@ -29,17 +29,39 @@ namespace lbm {
 
 namespace {
 
-constexpr int AT = 256;  // threads per block
+constexpr int AT = 256;  // threads per block of the objective and sum kernels
+constexpr int ST = 128;  // threads per block of the per-step kernels (more blocks on small lattices)
 constexpr int NPAR = 8;
 
-__device__ __forceinline__ int wrapi(int i, int n) {
-    int r = i % n;
-    return r < 0 ? r + n : r;
+// (dx, dz) of the 24 interaction links, first belt first (|c|^2 = 1, 2), then 4, 5, 8; constant
+// expressions, so an unrolled loop over the links folds them
+LBM_HD constexpr int LKX(int k) {
+    constexpr int t[24] = {1, 0, -1, 0, 1, -1, -1, 1, 2, 0, -2, 0, 2, 1, -1, -2, -2, -1, 1, 2, 2, -2, -2, 2};
+    return t[k];
+}
+LBM_HD constexpr int LKZ(int k) {
+    constexpr int t[24] = {0, 1, 0, -1, 1, 1, -1, -1, 0, 2, 0, -2, 1, 2, 2, 1, -1, -2, -2, -1, 2, 2, -2, -2};
+    return t[k];
 }
 
-// (dx, dz) of the 24 interaction links, first belt first (|c|^2 = 1, 2), then 4, 5, 8
-__constant__ int LKX[24] = {1, 0, -1, 0, 1, -1, -1, 1, 2, 0, -2, 0, 2, 1, -1, -2, -2, -1, 1, 2, 2, -2, -2, 2};
-__constant__ int LKZ[24] = {0, 1, 0, -1, 1, 1, -1, -1, 0, 2, 0, -2, 1, 2, 2, 1, -1, -2, -2, -1, 2, 2, -2, -2};
+// Periodic coordinate v = c + d, |d| <= 2, of a lattice of n sites along that axis.
+__device__ __forceinline__ int wrap2(int v, int n) {
+    if (n < 3) return ((v % n) + n) % n;  // uniform branch: only tiny lattices wrap more than once
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// Site indices of the 5 x 5 neighbourhood of (x, z): xo[dx + 2] + zo[dz + 2].
+struct Nbr {
+    int xo[5], zo[5];
+    __device__ __forceinline__ Nbr(int x, int z, int nx, int nz) {
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            xo[d] = wrap2(x + d - 2, nx);
+            zo[d] = wrap2(z + d - 2, nz) * nx;
+        }
+    }
+    __device__ __forceinline__ long long at(int dx, int dz) const { return (long long)zo[dz + 2] + xo[dx + 2]; }
+};
 
 template <typename T>
 struct AdjC {
@@ -78,7 +100,7 @@ template <> struct Acc<float> {
 template <typename T>
 __device__ void block_sum(const T (&v)[NPAR], typename Acc<T>::A* part, int accumulate) {
     using A = typename Acc<T>::A;
-    __shared__ A red[AT / 32][NPAR];
+    __shared__ A red[ST / 32][NPAR];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NPAR; ++k) {
@@ -89,7 +111,7 @@ __device__ void block_sum(const T (&v)[NPAR], typename Acc<T>::A* part, int accu
     __syncthreads();
     if (threadIdx.x < NPAR) {
         A t = red[0][threadIdx.x];
-        for (int i = 1; i < AT / 32; ++i) t = Acc<T>::add(t, red[i][threadIdx.x]);
+        for (int i = 1; i < ST / 32; ++i) t = Acc<T>::add(t, red[i][threadIdx.x]);
         A* p = part + (long long)blockIdx.x * NPAR + threadIdx.x;
         *p = accumulate ? Acc<T>::add(*p, t) : t;
     }
@@ -125,13 +147,14 @@ struct AdjBuf {
     T* dps;                  // psi'(rho_s)
 };
 
-template <typename T, int NS>
-__global__ void __launch_bounds__(AT) k_adj_moments(const T* __restrict__ f, const AdjC<T> A, AdjBuf<T> B) {
+// One thread per site and species (blockIdx.y = species).
+template <typename T>
+__global__ void __launch_bounds__(ST) k_adj_moments(const T* __restrict__ f, const AdjC<T> A, AdjBuf<T> B) {
     const long long n = (long long)A.nx * A.nz;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
+    {
+        const int s = blockIdx.y;
         T r = 0, mx = 0, mz = 0;
 #pragma unroll
         for (int l = 0; l < 9; ++l) {
@@ -148,23 +171,24 @@ __global__ void __launch_bounds__(AT) k_adj_moments(const T* __restrict__ f, con
 }
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(AT) k_adj_local(const T* __restrict__ f, const T* __restrict__ lam_next,
+__global__ void __launch_bounds__(ST) k_adj_local(const T* __restrict__ f, const T* __restrict__ lam_next,
                                                   const AdjC<T> A, AdjBuf<T> B,
                                                   typename Acc<T>::A* __restrict__ part, int accumulate) {
     const long long n = (long long)A.nx * A.nz;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     T gp[NPAR] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (i < n) {
-        const int x = (int)(i % A.nx), z = (int)(i / A.nx);
+        const int z = (int)(i / A.nx), x = (int)(i - (long long)z * A.nx);
+        const Nbr N(x, z, A.nx, A.nz);
         // the force at the site, keeping its three sums (attraction a, repulsion p, cross b)
         T ax[NS], az[NS], px[NS], pz[NS], bx[NS], bz[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) ax[s] = az[s] = px[s] = pz[s] = bx[s] = bz[s] = 0;
 #pragma unroll
         for (int k = 0; k < 24; ++k) {
-            const long long j = (long long)wrapi(z + LKZ[k], A.nz) * A.nx + wrapi(x + LKX[k], A.nx);
-            const int q = LKX[k] * LKX[k] + LKZ[k] * LKZ[k];
-            const T ex = (T)LKX[k], ez = (T)LKZ[k];
+            const long long j = N.at(LKX(k), LKZ(k));
+            const int q = LKX(k) * LKX(k) + LKZ(k) * LKZ(k);
+            const T ex = (T)LKX(k), ez = (T)LKZ(k);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 const T p = B.psi[s * n + j];
@@ -209,8 +233,7 @@ __global__ void __launch_bounds__(AT) k_adj_local(const T* __restrict__ f, const
 #pragma unroll
             for (int l = 0; l < 9; ++l) {
                 // streaming transposed: g_l(x) became f_l(x + c_l)
-                const long long j = (long long)wrapi(z + cz(l), A.nz) * A.nx + wrapi(x + cx(l), A.nx);
-                const T m = lam_next[(s * 9 + l) * n + j];
+                const T m = lam_next[(s * 9 + l) * n + N.at(cx(l), cz(l))];
                 const T ex = (T)cx(l), ez = (T)cz(l);
                 const T cu = ex * ux + ez * uz;
                 const T wr = wlb<T>(l) * r;
@@ -258,43 +281,38 @@ __global__ void __launch_bounds__(AT) k_adj_local(const T* __restrict__ f, const
     block_sum<T>(gp, part, accumulate);
 }
 
+// One thread per site and species (blockIdx.y = species).
 template <typename T, int NS>
-__global__ void __launch_bounds__(AT) k_adj_final(const T* __restrict__ lam_next, const AdjC<T> A, AdjBuf<T> B,
+__global__ void __launch_bounds__(ST) k_adj_final(const T* __restrict__ lam_next, const AdjC<T> A, AdjBuf<T> B,
                                                   T* __restrict__ lam) {
     const long long n = (long long)A.nx * A.nz;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % A.nx), z = (int)(i / A.nx);
-    // this site as the neighbour x + c of the sites x - c: their forces' dependence on its psi
-    // (species s) and, through the cross term of the other species, on its rho_s
-    T dps[NS], dro[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dps[s] = dro[s] = 0;
+    const int s = blockIdx.y;
+    const int z = (int)(i / A.nx), x = (int)(i - (long long)z * A.nx);
+    const Nbr N(x, z, A.nx, A.nz);
+    // this site as the neighbour x + c of the sites x - c: their forces' dependence on its psi_s
+    // and, through the cross term of the other species, on its rho_s
+    const T* qx = B.qx + s * n;
+    const T* qz = B.qz + s * n;
+    const T* rx = B.rx + (1 - s) * n;
+    const T* rz = B.rz + (1 - s) * n;
+    T dps = 0, dro = 0;
 #pragma unroll
     for (int k = 0; k < 24; ++k) {
-        const long long jb = (long long)wrapi(z - LKZ[k], A.nz) * A.nx + wrapi(x - LKX[k], A.nx);
-        const int q = LKX[k] * LKX[k] + LKZ[k] * LKZ[k];
-        const T ex = (T)LKX[k], ez = (T)LKZ[k];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const T bc = B.qx[s * n + jb] * ex + B.qz[s * n + jb] * ez;
-            dps[s] -= (A.G1[s] * A.wa[q] + A.G2[s] * A.wr[q]) * bc;
-            if (NS == 2 && k < 8) {
-                const T oc = B.rx[(1 - s) * n + jb] * ex + B.rz[(1 - s) * n + jb] * ez;
-                dro[s] -= A.G_AB * A.wc[q] * oc;
-            }
-        }
+        const long long jb = N.at(-LKX(k), -LKZ(k));
+        const int q = LKX(k) * LKX(k) + LKZ(k) * LKZ(k);
+        const T ex = (T)LKX(k), ez = (T)LKZ(k);
+        dps -= (A.G1[s] * A.wa[q] + A.G2[s] * A.wr[q]) * (qx[jb] * ex + qz[jb] * ez);
+        if (NS == 2 && k < 8) dro -= A.G_AB * A.wc[q] * (rx[jb] * ex + rz[jb] * ez);
     }
+    const T d = B.dloc[s * n + i] + dro + B.dps[s * n + i] * dps;
+    const T keep = (T)1 - A.itau[s];
+    const T djx = B.djx[s * n + i], djz = B.djz[s * n + i];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        const T d = B.dloc[s * n + i] + dro[s] + B.dps[s * n + i] * dps[s];
-        const T keep = (T)1 - A.itau[s];
-        const T djx = B.djx[s * n + i], djz = B.djz[s * n + i];
-#pragma unroll
-        for (int l = 0; l < 9; ++l) {
-            const long long j = (long long)wrapi(z + cz(l), A.nz) * A.nx + wrapi(x + cx(l), A.nx);
-            lam[(s * 9 + l) * n + i] = keep * lam_next[(s * 9 + l) * n + j] + d + djx * (T)cx(l) + djz * (T)cz(l);
-        }
+    for (int l = 0; l < 9; ++l) {
+        lam[(s * 9 + l) * n + i] =
+            keep * lam_next[(s * 9 + l) * n + N.at(cx(l), cz(l))] + d + djx * (T)cx(l) + djz * (T)cz(l);
     }
 }
 
@@ -425,7 +443,8 @@ AdjC<T> adj_const(const AdjConst& D) {
 // Scratch of a context: the intermediate fields (12 ns n values, sized for FP64), then the block
 // partials (NPAR 8-byte accumulators per block), then the objective's row averages (2 nz doubles).
 size_t field_bytes(long long n, int ns) { return ((size_t)12 * ns * n * 8 + 255) & ~(size_t)255; }
-size_t part_bytes(long long n) { return ((size_t)NPAR * grid_of(n) * 8 + 255) & ~(size_t)255; }
+int step_grid(long long n) { return (int)((n + ST - 1) / ST); }
+size_t part_bytes(long long n) { return ((size_t)NPAR * step_grid(n) * 8 + 255) & ~(size_t)255; }
 
 template <typename T>
 AdjBuf<T> adj_buf(void* scratch, long long n, int ns) {
@@ -439,13 +458,18 @@ AdjBuf<T> adj_buf(void* scratch, long long n, int ns) {
 
 template <typename T, int NS>
 void enqueue_steps(const AdjC<T>& A, AdjBuf<T> B, typename Acc<T>::A* part, int nb, int nsteps, const T* states,
-                   long long stride, const T*& next, T* const bufs[2], cudaStream_t st) {
+                   long long stride, const T*& next, T* const bufs[2], cudaEvent_t* ev, cudaStream_t st) {
     for (int k = nsteps - 1, t = 0; k >= 0; --k, ++t) {
         const T* f = states + (long long)k * stride;
         T* out = bufs[t & 1];
-        k_adj_moments<T, NS><<<nb, AT, 0, st>>>(f, A, B);
-        k_adj_local<T, NS><<<nb, AT, 0, st>>>(f, next, A, B, part, t > 0);
-        k_adj_final<T, NS><<<nb, AT, 0, st>>>(next, A, B, out);
+        cudaEvent_t* e = ev ? ev + 6 * t : nullptr;
+        if (e) cudaEventRecord(e[0], st);
+        k_adj_moments<T><<<dim3(nb, NS), ST, 0, st>>>(f, A, B);
+        if (e) cudaEventRecord(e[1], st), cudaEventRecord(e[2], st);
+        k_adj_local<T, NS><<<nb, ST, 0, st>>>(f, next, A, B, part, t > 0);
+        if (e) cudaEventRecord(e[3], st), cudaEventRecord(e[4], st);
+        k_adj_final<T, NS><<<dim3(nb, NS), ST, 0, st>>>(next, A, B, out);
+        if (e) cudaEventRecord(e[5], st);
         next = out;
     }
 }
@@ -481,18 +505,19 @@ size_t adjoint_scratch_bytes(int nx, int nz, int ns) {
 
 template <typename T>
 cudaError_t launch_adjoint_steps(const AdjConst& D, int nsteps, const T* states, long long stride, const T* lam_in,
-                                 T* lam_a, T* lam_b, const T** lam_out, double* grad, void* scratch, cudaStream_t st) {
+                                 T* lam_a, T* lam_b, const T** lam_out, double* grad, void* scratch, cudaEvent_t* ev,
+                                 cudaStream_t st) {
     const long long n = (long long)D.nx * D.nz;
     const AdjC<T> A = adj_const<T>(D);
     const AdjBuf<T> B = adj_buf<T>(scratch, n, D.ns);
     auto* part = reinterpret_cast<typename Acc<T>::A*>(static_cast<char*>(scratch) + field_bytes(n, D.ns));
-    const int nb = grid_of(n);
+    const int nb = step_grid(n);
     const T* next = lam_in;
     T* const bufs[2] = {lam_a, lam_b};
     if (D.ns == 2)
-        enqueue_steps<T, 2>(A, B, part, nb, nsteps, states, stride, next, bufs, st);
+        enqueue_steps<T, 2>(A, B, part, nb, nsteps, states, stride, next, bufs, ev, st);
     else
-        enqueue_steps<T, 1>(A, B, part, nb, nsteps, states, stride, next, bufs, st);
+        enqueue_steps<T, 1>(A, B, part, nb, nsteps, states, stride, next, bufs, ev, st);
     if (nsteps > 0) k_adj_sum<T><<<1, AT, 0, st>>>(part, nb, grad);
     *lam_out = next;
     return cudaGetLastError();
@@ -521,7 +546,7 @@ cudaError_t launch_adjoint_initial(const AdjConst& D, const T* lam0, double* g, 
 
 #define LBM_ADJ_INST(T)                                                                                           \
     template cudaError_t launch_adjoint_steps<T>(const AdjConst&, int, const T*, long long, const T*, T*, T*,     \
-                                                 const T**, double*, void*, cudaStream_t);                       \
+                                                 const T**, double*, void*, cudaEvent_t*, cudaStream_t);         \
     template cudaError_t launch_adjoint_objective<T>(const AdjConst&, const T*, const double*, const double*,     \
                                                      double*, T*, void*, cudaStream_t);                          \
     template cudaError_t launch_adjoint_initial<T>(const AdjConst&, const T*, double*, cudaStream_t);

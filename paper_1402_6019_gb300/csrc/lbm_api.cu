@@ -25,7 +25,8 @@ struct lbm_ctx {
     int pitch = 0;
     long long plane = 0;
     size_t esize = 0;  // bytes per stored population value
-    void* f[2] = {nullptr, nullptr};
+    void* f[2] = {nullptr, nullptr};      // the population buffers (lattice layout origin)
+    void* f_raw[2] = {nullptr, nullptr};  // their allocations (f = f_raw + a shift)
     int cur = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -81,6 +82,8 @@ struct lbm_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> ev;  // pairs around step-kernel launches
     size_t ev_used = 0;
+    std::vector<cudaEvent_t> aev;  // adjoint: three pairs per step, around its kernels
+    size_t aev_used = 0;
     std::string err;
 };
 
@@ -229,7 +232,9 @@ static void release(lbm_ctx* c) {
     drop_graphs(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
-    void* ptrs[] = {c->f[0],       c->f[1],    c->part_row[0], c->part_row[1], c->part_col[0],
+    for (cudaEvent_t e : c->aev) cudaEventDestroy(e);
+    c->aev.clear();
+    void* ptrs[] = {c->f_raw[0],   c->f_raw[1], c->part_row[0], c->part_row[1], c->part_col[0],
                     c->part_col[1], c->sched,   c->ticket,      c->flag,        c->out,
                     c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d,
                     c->adj_scratch, c->adj_lam};
@@ -328,8 +333,13 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     c->tile_rows = c->pull || d->tile_rows == 0 ? 8 : d->tile_rows;
     const size_t fbytes = (size_t)ns * 9 * c->plane * c->esize;
-    CKC(cudaMalloc(&c->f[0], fbytes));
-    CKC(cudaMalloc(&c->f[1], fbytes));
+    // pull layout: shift the origin so that every row's first lattice column (padded column
+    // PULL_GX) starts a 128-byte line; the shift keeps the 16-byte alignment tensor maps need
+    const size_t shift = c->pull ? (128 - (PULL_GX * c->esize) % 128) % 128 : 0;
+    for (int b = 0; b < 2; ++b) {
+        CKC(cudaMalloc(&c->f_raw[b], fbytes + 128));
+        c->f[b] = static_cast<char*>(c->f_raw[b]) + shift;
+    }
     CKC(cudaMemsetAsync(c->f[0], 0, fbytes, c->stream));
     CKC(cudaMemsetAsync(c->f[1], 0, fbytes, c->stream));
     // fused geometry and partial-sum groups
@@ -995,6 +1005,24 @@ extern "C" int lbm_profile(lbm_ctx* c, int enable) {
     CK(cudaStreamSynchronize(c->stream));
     c->profiling = enable != 0;
     c->ev_used = 0;
+    c->aev_used = 0;
+    return LBM_OK;
+}
+
+extern "C" int lbm_profile_read_adjoint(lbm_ctx* c, double* ms, long long* steps) {
+    if (!c) return LBM_EINVAL;
+    CK(cudaSetDevice(c->d.device));
+    CK(cudaStreamSynchronize(c->stream));
+    double total[3] = {0.0, 0.0, 0.0};
+    for (size_t k = 0; k + 5 < c->aev_used; k += 6)
+        for (int j = 0; j < 3; ++j) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, c->aev[k + 2 * j], c->aev[k + 2 * j + 1]));
+            total[j] += t;
+        }
+    if (ms)
+        for (int j = 0; j < 3; ++j) ms[j] = total[j];
+    if (steps) *steps = (long long)(c->aev_used / 6);
     return LBM_OK;
 }
 
@@ -1142,8 +1170,18 @@ template <typename T>
 static int adjoint_steps(lbm_ctx* c, const AdjConst& A, int nsteps, const T* states, const T* lam_in, T* lam_a,
                          T* lam_b, T* lam_user, double* grad) {
     const T* out = nullptr;
+    cudaEvent_t* ev = nullptr;
+    if (c->profiling && nsteps > 0) {
+        while (c->aev.size() < c->aev_used + 6 * (size_t)nsteps) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->aev.push_back(e);
+        }
+        ev = c->aev.data() + c->aev_used;
+        c->aev_used += 6 * (size_t)nsteps;
+    }
     CK(launch_adjoint_steps<T>(A, nsteps, states, (long long)state_values(c), lam_in, lam_a, lam_b, &out, grad,
-                               c->adj_scratch, c->stream));
+                               c->adj_scratch, ev, c->stream));
     if (out != lam_user)
         CK(cudaMemcpyAsync(lam_user, out, state_values(c) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
     c->launches += 3LL * nsteps + (nsteps > 0 ? 1 : 0);

@@ -197,10 +197,12 @@ size_t adjoint_scratch_bytes(int nx, int nz, int ns);
 // states + j stride): lam_in = dJ/df_{k+nsteps}; the steps write alternately into lam_a and
 // lam_b (neither may be lam_in's buffer while it is read: lam_b may be it, it is first written
 // by the second step); *lam_out receives the buffer holding dJ/df_k (lam_in when nsteps = 0).
-// Adds dJ/dtheta to grad[8].  T = double or float.
+// Adds dJ/dtheta to grad[8].  T = double or float.  ev: null, or 6 events per step recorded
+// around its three kernels (before / after each, in launch order).
 template <typename T>
 cudaError_t launch_adjoint_steps(const AdjConst& D, int nsteps, const T* states, long long stride, const T* lam_in,
-                                 T* lam_a, T* lam_b, const T** lam_out, double* grad, void* scratch, cudaStream_t st);
+                                 T* lam_a, T* lam_b, const T** lam_out, double* grad, void* scratch, cudaEvent_t* ev,
+                                 cudaStream_t st);
 // J (one double) of the velocity / density profile objective at f and, when g is not null,
 // g = dJ/df.
 template <typename T>

@@ -46,24 +46,38 @@ __global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho
     }
 }
 
-// The post-streaming populations as plain FP64 values, [ns][9][nz][nx]: the stored value of
-// (x, l) in the push layout, the gather of the pull layout.
-template <typename T, typename O>
-__global__ void k_export(int ns, const T* __restrict__ f, O* __restrict__ out, const StepConst<T> C,
-                         const InstGeom* __restrict__ inst, int ninst) {
-    const long long n = (long long)C.nx * C.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % C.nx), zg = (int)(i / C.nx);
-        int k = 0;
-        if (inst && ninst > 1) k = inst_of_row(inst, ninst, zg);
-        for (int s = 0; s < ns; ++s)
-            for (int l = 0; l < 9; ++l) {
-                long long o = (long long)zg * C.pitch + x;
-                int ls = l;
-                if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
-                out[(s * 9 + l) * n + i] = (O)((double)f[(s * 9 + ls) * C.plane + o] + wlb<double>(l) * (double)C.rho_ref[s]);
-            }
+// Where the gather of the pull layout reads population l of site (x, z) (as pull_slot), taking
+// x - c_l and, without walls, z - c_l from the ghost columns and rows, which hold the periodic
+// images of the current state: no wrapping.  For reads only (a write must go to the wrapped slot).
+template <typename T>
+__device__ __forceinline__ long long pull_src(const StepConst<T>& C, int x, int z, int nz, int prow0, int l, int& ls) {
+    const int zs = z - cz(l);
+    if (C.zbc && (zs < 0 || zs >= nz)) {
+        ls = opp(l);
+        return (long long)(prow0 + z + PULL_GZ) * C.pitch + x + PULL_GX;
     }
+    ls = l;
+    return (long long)(prow0 + zs + PULL_GZ) * C.pitch + (x - cx(l) + PULL_GX);
+}
+
+// The post-streaming populations as plain values, [ns][9][nz][nx]: the stored value of (x, l) in
+// the push layout, the gather of the pull layout.  Blocks of 32 x 8 sites of one population
+// (blockIdx.z = s * 9 + l).
+template <typename T, typename O>
+__global__ void __launch_bounds__(256) k_export(int ns, const T* __restrict__ f, O* __restrict__ out,
+                                                const StepConst<T> C, const InstGeom* __restrict__ inst, int ninst) {
+    const long long n = (long long)C.nx * C.nz;
+    const int s = blockIdx.z / 9, l = blockIdx.z % 9;
+    const int x = blockIdx.x * 32 + threadIdx.x, zg = blockIdx.y * 8 + threadIdx.y;
+    if (x >= C.nx || zg >= C.nz) return;
+    const double base = wlb<double>(l) * (double)C.rho_ref[s];
+    long long o = (long long)zg * C.pitch + x;
+    int ls = l;
+    if (inst) {
+        const int k = ninst > 1 ? inst_of_row(inst, ninst, zg) : 0;
+        o = pull_src(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
+    }
+    out[(s * 9 + l) * n + (long long)zg * C.nx + x] = (O)((double)f[(s * 9 + ls) * C.plane + o] + base);
 }
 
 // The inverse of k_export: plain FP64 post-streaming values in, stored values out.
@@ -71,17 +85,17 @@ template <typename T>
 __global__ void k_import(int ns, T* __restrict__ f, const double* __restrict__ in, const StepConst<T> C,
                          const InstGeom* __restrict__ inst, int ninst) {
     const long long n = (long long)C.nx * C.nz;
+    const int s = blockIdx.y / 9, l = blockIdx.y % 9;
+    const double base = wlb<double>(l) * (double)C.rho_ref[s];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % C.nx), zg = (int)(i / C.nx);
-        int k = 0;
-        if (inst && ninst > 1) k = inst_of_row(inst, ninst, zg);
-        for (int s = 0; s < ns; ++s)
-            for (int l = 0; l < 9; ++l) {
-                long long o = (long long)zg * C.pitch + x;
-                int ls = l;
-                if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
-                f[(s * 9 + ls) * C.plane + o] = (T)(in[(s * 9 + l) * n + i] - wlb<double>(l) * (double)C.rho_ref[s]);
-            }
+        long long o = (long long)zg * C.pitch + x;
+        int ls = l;
+        if (inst) {
+            const int k = ninst > 1 ? inst_of_row(inst, ninst, zg) : 0;
+            o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
+        }
+        f[(s * 9 + ls) * C.plane + o] = (T)(in[(s * 9 + l) * n + i] - base);
     }
 }
 
@@ -159,9 +173,8 @@ cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const 
 
 template <typename T, typename O>
 cudaError_t launch_export(int ns, const T* f, O* out, const StepConst<T>& C, const Batch* B, cudaStream_t st) {
-    const long long n = (long long)C.nx * C.nz;
-    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_export<T, O><<<blocks, 256, 0, st>>>(ns, f, out, C, B ? B->inst : nullptr, B ? B->ninst : 0);
+    const dim3 grid((C.nx + 31) / 32, (C.nz + 7) / 8, 9 * ns);
+    k_export<T, O><<<grid, dim3(32, 8), 0, st>>>(ns, f, out, C, B ? B->inst : nullptr, B ? B->ninst : 0);
     return cudaGetLastError();
 }
 
@@ -169,7 +182,7 @@ template <typename T>
 cudaError_t launch_import(int ns, T* f, const double* in, const StepConst<T>& C, const Batch* B, cudaStream_t st) {
     const long long n = (long long)C.nx * C.nz;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_import<T><<<blocks, 256, 0, st>>>(ns, f, in, C, B ? B->inst : nullptr, B ? B->ninst : 0);
+    k_import<T><<<dim3(blocks, 9 * ns), 256, 0, st>>>(ns, f, in, C, B ? B->inst : nullptr, B ? B->ninst : 0);
     return cudaGetLastError();
 }
 

@@ -15,10 +15,12 @@
 // Work.  A CTA of PX x PZ threads (one warp per tile row) loops over tiles.  The populations of
 // the tile and of a 3-cell ring around it (2 cells for the psi stencil of Eq. FORCE, 1 more for
 // the gather, x rounded to a 16-byte boundary) arrive in shared memory with one 3-D
-// cp.async.bulk.tensor load; the new populations leave through one tensor store of the tile.
-// No thread forms a global address on the hot path.  As soon as a tile's box has been read
-// (densities of the tile and ring formed), the load of the CTA's next tile is issued, so it
-// runs under this tile's force, collision and observables.  Every wait on a load is bounded.
+// cp.async.bulk.tensor load; each warp stores the new populations of its row of 32 sites straight
+// from registers, one 128-byte run per plane.  As soon as a tile's box has been read (densities
+// of the tile and ring formed), the load of the CTA's tile ST ahead is issued, so it runs under
+// this tile's force, collision and observables.  One CTA barrier per tile: the psi / rho tile and
+// the column sums are double-buffered by iteration parity, so a warp can start the next tile
+// while others still read this one's.  Every wait on a load is bounded.
 //
 // Tiles are handed out in row-major order by an atomic counter (the CTA that finishes last
 // resets it), so the CTAs at work at any moment cover a band of rows and read each other's halo
@@ -63,16 +65,20 @@ struct PsiTile<float, 2, true> {
     f2 rh[HH][HW];
 };
 
+// Per-iteration ring of the tiles to work on: iteration k works on tile tile[k % NTQ] of lattice
+// inst[k % NTQ], published by thread 0 at the start of iteration k - ST (or before the loop), one
+// CTA barrier ahead of every reader.
+constexpr int NTQ = 4;
+
 template <typename T, int NS, int ST>
 struct PullSmem {
-    T box[ST][9 * NS][BZ][BX];         // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
-    alignas(128) T out[9 * NS][PZ][PX];  // TMA source: the tile's new stored values
-    PsiTile<T, NS> q;
-    T colsum[PZ][NQC][PX];
+    T box[ST][9 * NS][BZ][BX];  // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
+    PsiTile<T, NS> q[2];        // by iteration parity: tile k + 1 fills one while tile k reads the other
+    T colsum[2][PZ][NQC][PX];   // by iteration parity: summed over the tile's rows one tile later
     typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
     alignas(8) unsigned long long bar[ST];
-    int tile[ST];  // the tile each box holds (or is loading)
-    int inst[ST];  // and the lattice of the batch it belongs to
+    int tile[NTQ];
+    int inst[NTQ];
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -142,8 +148,8 @@ __device__ __forceinline__ void gather_wall(const PullSmem<T, NS, ST>& S, int sl
 // mirror image (or zero, Sec. IV's two readings of the ghost rows).  Positions that no live
 // site reads (far padding of ragged tiles) are set to zero.
 template <typename T, int NS, int ST>
-__device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, const StepConst<T>& C, const PairConst& K,
-                                             int px, int pz, int z0, int nz) {
+__device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, int qb, const StepConst<T>& C,
+                                             const PairConst& K, int px, int pz, int z0, int nz) {
     const int Z = z0 - 2 + pz;
     int Zs = Z;
     bool zero = false;
@@ -170,24 +176,24 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, con
     }
     if constexpr (kPair<T, NS>) {
         const f2 rho = add2(K.rho_ref, p2(sum[0], sum[1]));
-        S.q.rh[pz][px] = zero ? sp(0.f) : rho;
-        S.q.ps[pz][px] = zero ? sp(0.f) : psi2(C, K, rho);
+        S.q[qb].rh[pz][px] = zero ? sp(0.f) : rho;
+        S.q[qb].ps[pz][px] = zero ? sp(0.f) : psi2(C, K, rho);
     } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const T rho = C.rho_ref[s] + sum[s];
-            S.q.rh[s][pz][px] = zero ? T(0) : rho;
-            S.q.ps[s][pz][px] = zero ? T(0) : psi_of(C, s, rho);
+            S.q[qb].rh[s][pz][px] = zero ? T(0) : rho;
+            S.q[qb].ps[s][pz][px] = zero ? T(0) : psi_of(C, s, rho);
         }
     }
 }
 
 // The periodic images of site (x, z) of a lattice of nz rows whose row -PULL_GZ is padded row
-// prow0: plain stores of its new values (read back from the staging tile) into the ghost columns
-// (and, without walls, ghost rows) that wrap onto it.
-template <typename T, int NS, int ST>
-__device__ __noinline__ void write_images(const PullSmem<T, NS, ST>& S, const StepConst<T>& C, T* __restrict__ fout,
-                                          int x, int z, int nz, int prow0, int tx, int tz) {
+// prow0: its new values, read back from where this thread has just stored them, copied into the
+// ghost columns (and, without walls, ghost rows) that wrap onto it.
+template <typename T, int NS>
+__device__ __noinline__ void write_images(const StepConst<T>& C, T* __restrict__ fout, int x, int z, int nz,
+                                          int prow0) {
     const int nx = C.nx;
     int xs[2 * PULL_GX + 1], zs[2 * PULL_GZ + 1];
     int nxs = 0, nzs = 0;
@@ -202,12 +208,16 @@ __device__ __noinline__ void write_images(const PullSmem<T, NS, ST>& S, const St
             const int gz = g < PULL_GZ ? g - PULL_GZ : nz + g - PULL_GZ;
             if (wrap_index(gz, nz) == z) zs[nzs++] = gz;
         }
+    const T* src = fout + (long long)(prow0 + z + PULL_GZ) * C.pitch + (x + PULL_GX);
+    T v[9 * NS];
+#pragma unroll
+    for (int p = 0; p < 9 * NS; ++p) v[p] = src[p * C.plane];
     for (int a = 0; a < nxs; ++a)
         for (int b = 0; b < nzs; ++b) {
             if (a == 0 && b == 0) continue;
             T* dst = fout + (long long)(prow0 + zs[b] + PULL_GZ) * C.pitch + (xs[a] + PULL_GX);
 #pragma unroll
-            for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
+            for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = v[p];
         }
 }
 
@@ -219,6 +229,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PullSmem<T, NS, ST>& S = *reinterpret_cast<PullSmem<T, NS, ST>*>(smem_raw);
     const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
+    // Programmatic dependent launch: the next step's CTAs may be scheduled as soon as this grid's
+    // CTAs start retiring; every thread of a grid waits for the previous grid's completion (and
+    // the visibility of its writes) before its first access to global memory.
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     // nz: rows of all lattices; ntz: their tile rows; tiles are numbered lattice by lattice
     const int nx = C.nx, nz = C.nz;
     const int ntiles = ntx * ntz;
@@ -243,8 +258,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             rpx = c < 2 ? c : HW - 4 + c;
         }
     }
-    // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden
-    int upcoming = 0;
+    // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden; ntiles:
+    // nothing more to draw
+    int upcoming = ntiles;
 
     if (tid == 0) {
         for (int sl = 0; sl < ST; ++sl)
@@ -276,12 +292,19 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     }
     unsigned parity = 0;  // bit sl: phase of box sl's barrier
     bool failed = false;
-    for (int k = 0;; ++k) {
-        const int sl = k % ST;
-        const int t = S.tile[sl];
+    // the previous tile's column-sum slot (observables): its column x and tile row, or x = -1
+    int prev_x = -1, prev_jg = 0;
+    int k = 0;
+    for (;; ++k) {
+        const int sl = k % ST, qb = k & 1;
+        const int t = S.tile[k % NTQ];
         if (t >= ntiles) break;
+        if (tid == 0) {  // publish the tile of iteration k + ST, one barrier ahead of its readers
+            S.tile[(k + ST) % NTQ] = upcoming;
+            if (upcoming < ntiles) S.inst[(k + ST) % NTQ] = ninst > 1 ? inst_of_tile(inst, ninst, upcoming) : 0;
+        }
         // this tile's lattice: rows, first compact row, first padded row, first tile, drive
-        const InstGeom* const I = inst + S.inst[sl];
+        const InstGeom* const I = inst + S.inst[k % NTQ];
         const int lnz = I->nz, zrow0 = I->zrow0, prow0 = I->prow0, tl = t - I->tile0;
         const int s = tl % ntx, j = tl / ntx;
         const int x0 = s * PX, z0 = j * PZ;  // z: rows of this lattice
@@ -308,42 +331,54 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 drho[0] = d.x;
                 drho[NS - 1] = d.y;
                 const f2 r = add2(K.rho_ref, d);
-                S.q.rh[tz + 2][tx + 2] = r;
-                S.q.ps[tz + 2][tx + 2] = psi2(C, K, r);
+                S.q[qb].rh[tz + 2][tx + 2] = r;
+                S.q[qb].ps[tz + 2][tx + 2] = psi2(C, K, r);
             } else {
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     drho[s] = sum9(f[s]);
                     const T r = C.rho_ref[s] + drho[s];
-                    S.q.rh[s][tz + 2][tx + 2] = r;
-                    S.q.ps[s][tz + 2][tx + 2] = psi_of(C, s, r);
+                    S.q[qb].rh[s][tz + 2][tx + 2] = r;
+                    S.q[qb].ps[s][tz + 2][tx + 2] = psi_of(C, s, r);
                 }
             }
         } else {
-            side_density<T, NS, ST>(S, sl, C, K, tx + 2, tz + 2, z0, lnz);
+            side_density<T, NS, ST>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz);
         }
-        if (ring) side_density<T, NS, ST>(S, sl, C, K, rpx, rpz, z0, lnz);
-        if ((MODE & M_WRITE) && tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+        if (ring) side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz);
+        // the only CTA barrier of a tile: psi / rho of the tile and ring complete, box sl read
+        // by all, the previous tile's column sums written
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
-        // box sl is free: start the load of the tile ST ahead (drawn during the last tile)
-        // and draw the one after it
+        // box sl is free: start the load of the tile ST ahead (published at the top of this
+        // iteration) and draw the one after it
         if (tid == 0) {
             const int tn = upcoming;
-            S.tile[sl] = tn;  // read by all after the barrier that ends tile k + ST - 1
             if (tn < ntiles) {
-                const int kn = ninst > 1 ? inst_of_tile(inst, ninst, tn) : 0;
-                S.inst[sl] = kn;
+                const int kn = S.inst[(k + ST) % NTQ];
                 const int tln = tn - inst[kn].tile0;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 issue_load(S, &tin, (tln % ntx) * PX, inst[kn].prow0 + (tln / ntx) * PZ, sl);
                 upcoming = (int)atomicAdd(&sched[0], 1u);
+                if (upcoming > ntiles) upcoming = ntiles;
             }
+        }
+        if (MODE & M_OBS) {
+            // the previous tile's per-column sums over its PZ rows
+            if (tz < NQC && prev_x >= 0 && prev_x < nx) {
+                T v = T(0);
+#pragma unroll
+                for (int r = 0; r < PZ; ++r) v += S.colsum[qb ^ 1][r][tz][tx];
+                static_cast<T*>(O.part_col)[((long long)prev_x * ntz + prev_jg) * NQC + tz] = v;
+            }
+            prev_x = x;
+            prev_jg = jg;
         }
 
         // ---- phase B: interaction, collision, new stored values, observables ----
+        const PsiTile<T, NS>& Q = S.q[qb];
         T rowq[NQR];
 #pragma unroll
         for (int k = 0; k < NQR; ++k) rowq[k] = T(0);
@@ -356,7 +391,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
 #pragma unroll
             for (int dz = 0; dz < 5; ++dz)
 #pragma unroll
-                for (int dx = 0; dx < 5; ++dx) p[dz][dx] = S.q.ps[tz + dz][tx + dx];
+                for (int dx = 0; dx < 5; ++dx) p[dz][dx] = Q.ps[tz + dz][tx + dx];
             f2 Fx, Fz;
             intra_force2(K, p, Fx, Fz);
             float sxx = 0.f, szz = 0.f, sxz = 0.f;
@@ -371,7 +406,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
 #pragma unroll
             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx) r[dz][dx] = S.q.rh[tz + 1 + dz][tx + 1 + dx];
+                for (int dx = 0; dx < 3; ++dx) r[dz][dx] = Q.rh[tz + 1 + dz][tx + 1 + dx];
             cross_force2(C, r, Fx, Fz);
             if (MODE & M_OBS) cross_stress2(C, r, sxx, szz, sxz);
             if (live) {
@@ -439,7 +474,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
 #pragma unroll
                 for (int dz = 0; dz < 5; ++dz)
 #pragma unroll
-                    for (int dx = 0; dx < 5; ++dx) p[dz][dx] = S.q.ps[s2][tz + dz][tx + dx];
+                    for (int dx = 0; dx < 5; ++dx) p[dz][dx] = Q.ps[s2][tz + dz][tx + dx];
                 intra_force(C, s2, p, F[s2][0], F[s2][1]);
                 if (MODE & M_OBS) intra_stress(C, s2, p, sxx, szz, sxz);
             }
@@ -449,8 +484,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
-                        ra[dz][dx] = S.q.rh[0][tz + 1 + dz][tx + 1 + dx];
-                        rb[dz][dx] = S.q.rh[1][tz + 1 + dz][tx + 1 + dx];
+                        ra[dz][dx] = Q.rh[0][tz + 1 + dz][tx + 1 + dx];
+                        rb[dz][dx] = Q.rh[1][tz + 1 + dz][tx + 1 + dx];
                     }
                 cross_force(C, ra, rb, F);
                 if (MODE & M_OBS) cross_stress(C, ra, rb, sxx, szz, sxz);
@@ -500,14 +535,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 }
             }
         }
-        if (collided) {  // new stored values; with walls the populations leaving through a wall reflected
+        // new stored values, straight from registers: a warp stores each plane's row of 32
+        // sites as one 128-byte run; with walls the populations leaving through a wall reflected
+        T* const dst = fout + (long long)(prow0 + z + PULL_GZ) * C.pitch + (x + PULL_GX);
+        if (collided) {
             const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
             if (!wall_row) {  // warp-uniform
                 if (MODE & M_WRITE) {
 #pragma unroll
                     for (int s2 = 0; s2 < NS; ++s2)
 #pragma unroll
-                        for (int l = 0; l < 9; ++l) S.out[s2 * 9 + l][tz][tx] = f[s2][l];
+                        for (int l = 0; l < 9; ++l) dst[(s2 * 9 + l) * C.plane] = f[s2][l];
                 }
             } else {
 #pragma unroll
@@ -528,12 +566,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                                     rowq[QR_WALLT] += dm;
                             }
                         }
-                        if (MODE & M_WRITE) S.out[s2 * 9 + l][tz][tx] = v;
+                        if (MODE & M_WRITE) dst[(s2 * 9 + l) * C.plane] = v;
                     }
             }
         }
         if (__any_sync(FULL, bad) && tx == 0) atomicOr(O.flag, 1);
-        if (MODE & M_WRITE) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if ((MODE & M_WRITE) && collided &&
+            (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= lnz - PULL_GZ))))
+            write_images<T, NS>(C, fout, x, z, lnz, prow0);
         if (MODE & M_OBS) {
             // per-row sums over the 32 sites of this warp: transpose-reduce, lane 4q holds quantity q
             static_assert(NQR == 8, "row reduction is written for 8 quantities");
@@ -559,51 +599,30 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 const int q = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
                 static_cast<T*>(O.part_row)[((long long)(zrow0 + z) * ntx + s) * NQR + q] = v1;
             }
-            S.colsum[tz][QC_PS][tx] = cps;
-            S.colsum[tz][QC_PXX][tx] = cpx;
+            S.colsum[qb][tz][QC_PS][tx] = cps;
+            S.colsum[qb][tz][QC_PXX][tx] = cpx;
         }
+    }
+    if ((MODE & M_OBS) && !failed) {
+        // the last tile's per-column sums
         __syncthreads();
-        if (MODE & M_WRITE) {
-            if (x0 + PX <= nx && z0 + PZ <= lnz) {
-                if (tid == 0) {
-                    // padded column x0 + 4 is lattice column x0, padded row prow0 + 3 + z0 is row z0
-                    asm volatile(
-                        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
-                            &tout),
-                        "r"(x0 + PULL_GX), "r"(prow0 + z0 + PULL_GZ), "r"(0), "r"(smem_u32(&S.out[0][0][0]))
-                        : "memory");
-                    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-                }
-            } else if (live) {
-                // a ragged tile: the store's x bound would be checked in 16-byte units, the columns
-                // past nx are ghost columns written by the first strip, and the rows past the
-                // lattice's last row belong to its ghost rows or to the next lattice -- plain stores
-                T* dst = fout + (long long)(prow0 + z + PULL_GZ) * C.pitch + (x + PULL_GX);
+        if (tz < NQC && prev_x >= 0 && prev_x < nx) {
+            T v = T(0);
 #pragma unroll
-                for (int p = 0; p < 9 * NS; ++p) dst[p * C.plane] = S.out[p][tz][tx];
-            }
-            if (live && (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= lnz - PULL_GZ))))
-                write_images<T, NS, ST>(S, C, fout, x, z, lnz, prow0, tx, tz);
-        }
-        if (MODE & M_OBS) {
-            // per-column sums over the PZ rows of the tile
-            if (tz < NQC && x < nx) {
-                T v = T(0);
-#pragma unroll
-                for (int r = 0; r < PZ; ++r) v += S.colsum[r][tz][tx];
-                static_cast<T*>(O.part_col)[((long long)x * ntz + jg) * NQC + tz] = v;
-            }
+            for (int r = 0; r < PZ; ++r) v += S.colsum[(k - 1) & 1][r][tz][tx];
+            static_cast<T*>(O.part_col)[((long long)prev_x * ntz + prev_jg) * NQC + tz] = v;
         }
     }
     if (tid == 0) {
         if (failed) {
             atomicOr(O.flag, 2);
-            // loads still in flight (the one that did not arrive in time, the one after it) before
-            // the CTA exits
-            for (int sl = 0; sl < ST; ++sl)
-                if (S.tile[sl] < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
+            // the loads still in flight -- those of iterations k .. k + ST - 1 (the one that did
+            // not arrive in time and the ones after it) -- before the CTA exits
+            for (int i = 0; i < ST; ++i) {
+                const int sl = (k + i) % ST;
+                if (S.tile[(k + i) % NTQ] < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
+            }
         }
-        asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
         // the last CTA out resets the scheduler for the next launch (every CTA's draws on
         // sched[0] come before its fence and its increment of sched[1])
         __threadfence();
@@ -634,10 +653,21 @@ cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepCo
     if (Rd.enabled && grid < 1) grid = 1;
     PairConst K{};
     if constexpr (kPair<T, NS>) fill_pair_const(K, C);
-    k_pull<T, NS, MODE, ST><<<grid, dim3(PX, PZ), sizeof(PullSmem<T, NS, ST>), st>>>(
-        *static_cast<const CUtensorMap*>(tin), *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, B.inst,
-        B.ninst, ntx, B.ntz);
-    return cudaGetLastError();
+    // launched with programmatic stream serialisation: it may start while the kernel before it
+    // on the stream drains, and waits for it in its prologue (griddepcontrol.wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(PX, PZ);
+    cfg.dynamicSmemBytes = sizeof(PullSmem<T, NS, ST>);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST>, *static_cast<const CUtensorMap*>(tin),
+                              *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, B.inst, B.ninst, ntx,
+                              B.ntz);
 }
 
 template <typename T, int NS, int ST>

@@ -78,6 +78,8 @@ SIGNATURES = {
     "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "lbm_set_populations": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "lbm_profile_read_adjoint": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_snapshot_bytes": (ctypes.c_longlong, [_VP]),
     "lbm_snapshot": (ctypes.c_int, [_VP, _VP]),
     "lbm_restore": (ctypes.c_int, [_VP, _VP]),
@@ -219,6 +221,14 @@ def lbm_profile_read(h):
     n = ctypes.c_longlong()
     _check(load().lbm_profile_read(h, ctypes.byref(ms), ctypes.byref(n)), h)
     return ms.value, n.value
+
+
+def lbm_profile_read_adjoint(h):
+    """(ms of the three adjoint kernels: moments, local, final; adjoint steps timed)."""
+    ms = (ctypes.c_double * 3)()
+    n = ctypes.c_longlong()
+    _check(load().lbm_profile_read_adjoint(h, ms, ctypes.byref(n)), h)
+    return list(ms), n.value
 
 
 def lbm_last_error(h=None) -> str:
