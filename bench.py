@@ -550,7 +550,7 @@ def main():
                        a.kernel if a.tile_rows in (0, 8) else f"{a.kernel}{a.tile_rows}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "kernel": {"pull": "lbm::k_pull<T, 2, M_WRITE|M_OBS>",
+                "kernel": {"pull": "lbm::k_pull<T, 2, M_WRITE|M_OBS>" if a.observe_every else "lbm::k_pull<T, 2, M_WRITE>",
                            "fused": "lbm::k_tile<T, 2, M_WRITE|M_OBS>",
                            "twopass": "lbm::k_density + lbm::k_twopass<T, 2, M_WRITE|M_OBS>",
                            "sweep": "lbm::k_fused<T, 2, M_WRITE|M_OBS>"}[a.kernel],

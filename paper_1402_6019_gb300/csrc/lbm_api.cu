@@ -125,9 +125,7 @@ static void refresh_const(lbm_ctx* c) {
                             c->rho_ref);
     for (size_t i = 0; i < c->inst.size(); ++i)  // the parameters' drive, where no lattice drive is set
         if (!c->drive_set[i]) {
-            c->inst[i].g = c->p.body_force;
-            c->inst[i].wall_u[0] = c->p.wall_u[0];
-            c->inst[i].wall_u[1] = c->p.wall_u[1];
+            set_inst_drive(c->inst[i], c->p.body_force, c->p.wall_u[0], c->p.wall_u[1]);
         }
 }
 
@@ -437,9 +435,7 @@ extern "C" int lbm_set_instance_drive(lbm_ctx* c, int i, double body_force, doub
         refresh_const(c);
         drop_graphs(c);
     }
-    c->inst[i].g = body_force;
-    c->inst[i].wall_u[0] = wall_u_bottom;
-    c->inst[i].wall_u[1] = wall_u_top;
+    set_inst_drive(c->inst[i], body_force, wall_u_bottom, wall_u_top);
     c->drive_set[i] = 1;
     CK(upload_inst(c));  // the kernels read the table at run time: captured graphs stay valid
     return LBM_OK;

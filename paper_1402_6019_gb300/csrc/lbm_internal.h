@@ -54,10 +54,30 @@ struct InstGeom {
     int prow0;    // padded plane row of its row -PULL_GZ (its row z sits at prow0 + PULL_GZ + z)
     int tile0;    // its first tile in the pull kernel's numbering (ntx tiles per tile row)
     int ntz;      // its tile rows
-    int pad_;
-    double g;          // body acceleration along x
-    double wall_u[2];  // bottom, top wall velocity along x
+    float g_f;           // g in FP32 (set with g: the FP32 kernels issue no FP64 conversion)
+    double g;            // body acceleration along x
+    double wall_u[2];    // bottom, top wall velocity along x
+    float wall_u_f[2];   // wall_u in FP32
+    int pad2_[2];
 };
+// The drive of a lattice in the kernels' precision.
+template <typename T>
+LBM_HD T inst_g(const InstGeom& I) {
+    if constexpr (sizeof(T) == 4) return I.g_f; else return I.g;
+}
+template <typename T>
+LBM_HD T inst_wall_u(const InstGeom& I, int w) {
+    if constexpr (sizeof(T) == 4) return I.wall_u_f[w]; else return I.wall_u[w];
+}
+// Sets a lattice's drive (both precisions).
+inline void set_inst_drive(InstGeom& I, double g, double wb, double wt) {
+    I.g = g;
+    I.g_f = (float)g;
+    I.wall_u[0] = wb;
+    I.wall_u[1] = wt;
+    I.wall_u_f[0] = (float)wb;
+    I.wall_u_f[1] = (float)wt;
+}
 // The lattices of a pull-kernel context, as the kernels see them: the device copy of the table,
 // its length, and the tile rows of all lattices together.
 struct Batch {

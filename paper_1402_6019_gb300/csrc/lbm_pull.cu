@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 const f2 ir = p2(__fdividef(1.f, rh.x), __fdividef(1.f, rh.y));
                 f2 jx, jz;
                 momentum9_2(fp, jx, jz);
-                Fx = fma2(rh, sp((float)I->g), Fx);
+                Fx = fma2(rh, sp(inst_g<float>(*I)), Fx);
                 if (MODE & (M_OBS | M_FIELDS)) {
                     // barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s and the kinetic flux
                     const f2 m = fma2(Fx, sp(0.5f), jx), n = fma2(Fz, sp(0.5f), jz);
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                     if (!(rho[s2] > T(0)) || !(rho[s2] < T(1e30))) bad = 1;
                     ir[s2] = div_(T(1), rho[s2]);
                     momentum9(f[s2], jx[s2], jz[s2]);
-                    F[s2][0] += rho[s2] * T(I->g);
+                    F[s2][0] += rho[s2] * inst_g<T>(*I);
                 }
                 if (MODE & (M_OBS | M_FIELDS)) {
                     T ux, uz, pixz, rtot, mx, mz;
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                         T v = f[s2][l];
                         if (zd < 0 || zd >= lnz) {  // leaves through a wall: store it reflected
                             const int w = zd < 0 ? 0 : 1;
-                            const T back = bounce<T>(l, f[s2][l], rho[s2], T(I->wall_u[w]));
+                            const T back = bounce<T>(l, f[s2][l], rho[s2], inst_wall_u<T>(*I, w));
                             v = back;
                             if (MODE & M_OBS) {
                                 const T dm = T(cx(l)) * (f[s2][l] + back);
