@@ -65,10 +65,23 @@ struct PsiTile<float, 2, true> {
     f2 rh[HH][HW];
 };
 
-// Per-iteration ring of the tiles to work on: iteration k works on tile tile[k % NTQ] of lattice
-// inst[k % NTQ], published by thread 0 at the start of iteration k - ST (or before the loop), one
+// Per-iteration ring of the tiles to work on: iteration k works on the tile described by
+// ti[k % NTQ], published by thread 0 at the start of iteration k - ST (or before the loop), one
 // CTA barrier ahead of every reader.
 constexpr int NTQ = 4;
+
+// A tile as thread 0 publishes it: its place and its lattice's geometry and drive, so that no
+// other thread divides by the tile-row length or reads the lattice table.
+template <typename T>
+struct TileInfo {
+    int t;          // tile number; >= the tile count: no more tiles
+    int x0, z0;     // first column; first row among the rows of its lattice
+    int jg;         // tile row among all lattices
+    int lnz, zrow0; // its lattice's rows and first compact row
+    int prow0;      // padded plane row of its lattice's row -PULL_GZ
+    int pad_;
+    T g, wall[2];   // its lattice's drive
+};
 
 template <typename T, int NS, int ST>
 struct PullSmem {
@@ -77,9 +90,26 @@ struct PullSmem {
     T colsum[2][PZ][NQC][PX];   // by iteration parity: summed over the tile's rows one tile later
     typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
     alignas(8) unsigned long long bar[ST];
-    int tile[NTQ];
-    int inst[NTQ];
+    TileInfo<T> ti[NTQ];
 };
+
+template <typename T>
+__device__ __forceinline__ void describe(TileInfo<T>& D, int t, int ntiles, const InstGeom* __restrict__ inst,
+                                         int ninst, int ntx) {
+    D.t = t;
+    if (t >= ntiles) return;
+    const InstGeom& I = inst[ninst > 1 ? inst_of_tile(inst, ninst, t) : 0];
+    const int tl = t - I.tile0, j = tl / ntx;
+    D.x0 = (tl - j * ntx) * PX;
+    D.z0 = j * PZ;
+    D.jg = I.tile0 / ntx + j;
+    D.lnz = I.nz;
+    D.zrow0 = I.zrow0;
+    D.prow0 = I.prow0;
+    D.g = inst_g<T>(I);
+    D.wall[0] = inst_wall_u<T>(I, 0);
+    D.wall[1] = inst_wall_u<T>(I, 1);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -269,15 +299,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         // the first ST tiles go into the boxes at once (padded (x0, z0) is the box origin)
         bool more = true;
         for (int sl = 0; sl < ST; ++sl) {
-            const int t0 = more ? (int)atomicAdd(&sched[0], 1u) : ntiles;
-            S.tile[sl] = t0;
+            int t0 = more ? (int)atomicAdd(&sched[0], 1u) : ntiles;
+            if (t0 > ntiles) t0 = ntiles;
+            describe<T>(S.ti[sl], t0, ntiles, inst, ninst, ntx);
             more = t0 < ntiles;
-            if (more) {
-                const int k = ninst > 1 ? inst_of_tile(inst, ninst, t0) : 0;
-                S.inst[sl] = k;
-                const int tl = t0 - inst[k].tile0;
-                issue_load(S, &tin, (tl % ntx) * PX, inst[k].prow0 + (tl / ntx) * PZ, sl);
-            }
+            if (more) issue_load(S, &tin, S.ti[sl].x0, S.ti[sl].prow0 + S.ti[sl].z0, sl);
         }
         if (more) upcoming = (int)atomicAdd(&sched[0], 1u);
     }
@@ -297,18 +323,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     int k = 0;
     for (;; ++k) {
         const int sl = k % ST, qb = k & 1;
-        const int t = S.tile[k % NTQ];
-        if (t >= ntiles) break;
-        if (tid == 0) {  // publish the tile of iteration k + ST, one barrier ahead of its readers
-            S.tile[(k + ST) % NTQ] = upcoming;
-            if (upcoming < ntiles) S.inst[(k + ST) % NTQ] = ninst > 1 ? inst_of_tile(inst, ninst, upcoming) : 0;
-        }
-        // this tile's lattice: rows, first compact row, first padded row, first tile, drive
-        const InstGeom* const I = inst + S.inst[k % NTQ];
-        const int lnz = I->nz, zrow0 = I->zrow0, prow0 = I->prow0, tl = t - I->tile0;
-        const int s = tl % ntx, j = tl / ntx;
-        const int x0 = s * PX, z0 = j * PZ;  // z: rows of this lattice
-        const int jg = I->tile0 / ntx + j;   // tile row among all lattices
+        const TileInfo<T> D = S.ti[k % NTQ];
+        if (D.t >= ntiles) break;
+        if (tid == 0)  // publish the tile of iteration k + ST, one barrier ahead of its readers
+            describe<T>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx);
+        // this tile: first column and row (rows of its lattice), tile row among all lattices; its
+        // lattice: rows, first compact row, first padded row
+        const int lnz = D.lnz, zrow0 = D.zrow0, prow0 = D.prow0, x0 = D.x0, z0 = D.z0, jg = D.jg;
+        const int s = x0 / PX;  // tile column
         const int x = x0 + tx, z = z0 + tz;
         const bool live = x < nx && z < lnz;
         const bool ok = wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
@@ -357,10 +379,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         if (tid == 0) {
             const int tn = upcoming;
             if (tn < ntiles) {
-                const int kn = S.inst[(k + ST) % NTQ];
-                const int tln = tn - inst[kn].tile0;
+                const TileInfo<T>& N = S.ti[(k + ST) % NTQ];
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                issue_load(S, &tin, (tln % ntx) * PX, inst[kn].prow0 + (tln / ntx) * PZ, sl);
+                issue_load(S, &tin, N.x0, N.prow0 + N.z0, sl);
                 upcoming = (int)atomicAdd(&sched[0], 1u);
                 if (upcoming > ntiles) upcoming = ntiles;
             }
@@ -421,7 +442,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 const f2 ir = p2(__fdividef(1.f, rh.x), __fdividef(1.f, rh.y));
                 f2 jx, jz;
                 momentum9_2(fp, jx, jz);
-                Fx = fma2(rh, sp(inst_g<float>(*I)), Fx);
+                Fx = fma2(rh, sp(D.g), Fx);
                 if (MODE & (M_OBS | M_FIELDS)) {
                     // barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s and the kinetic flux
                     const f2 m = fma2(Fx, sp(0.5f), jx), n = fma2(Fz, sp(0.5f), jz);
@@ -498,7 +519,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                     if (!(rho[s2] > T(0)) || !(rho[s2] < T(1e30))) bad = 1;
                     ir[s2] = div_(T(1), rho[s2]);
                     momentum9(f[s2], jx[s2], jz[s2]);
-                    F[s2][0] += rho[s2] * inst_g<T>(*I);
+                    F[s2][0] += rho[s2] * D.g;
                 }
                 if (MODE & (M_OBS | M_FIELDS)) {
                     T ux, uz, pixz, rtot, mx, mz;
@@ -556,7 +577,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                         T v = f[s2][l];
                         if (zd < 0 || zd >= lnz) {  // leaves through a wall: store it reflected
                             const int w = zd < 0 ? 0 : 1;
-                            const T back = bounce<T>(l, f[s2][l], rho[s2], inst_wall_u<T>(*I, w));
+                            const T back = bounce<T>(l, f[s2][l], rho[s2], w == 0 ? D.wall[0] : D.wall[1]);
                             v = back;
                             if (MODE & M_OBS) {
                                 const T dm = T(cx(l)) * (f[s2][l] + back);
@@ -620,7 +641,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             // not arrive in time and the ones after it) -- before the CTA exits
             for (int i = 0; i < ST; ++i) {
                 const int sl = (k + i) % ST;
-                if (S.tile[(k + i) % NTQ] < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
+                if (S.ti[(k + i) % NTQ].t < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
             }
         }
         // the last CTA out resets the scheduler for the next launch (every CTA's draws on
