@@ -44,7 +44,9 @@ ROTATE_BYTES = 512 << 20      # working set of the rotated lattices, well above 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2000 lattice steps; 5 gradients for adjoint_256; for the reference "
+                         "arm 20 oracle steps, 2 oracle gradients)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="emulsion_1024")
@@ -91,7 +93,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -430,6 +432,9 @@ def main():
 
     rank, world, local = _dist()
     w = W.workload(a.workload, seed=replicas.replica_seed(1402, replicas.from_env()))
+    if a.steps is None:
+        a.steps = {("ours", False): 2000, ("ours", True): 5, ("reference", False): 20,
+                   ("reference", True): 2}[(a.impl, "target_u" in w)]
     if "target_u" in w:  # the calibration workload: gradients of a run
         return run_reference_adjoint(a, w) if a.impl == "reference" else run_adjoint(a, w)
     if a.impl == "reference":

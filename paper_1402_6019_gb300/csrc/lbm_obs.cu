@@ -74,8 +74,12 @@ __global__ void __launch_bounds__(256) k_export(int ns, const T* __restrict__ f,
     long long o = (long long)zg * C.pitch + x;
     int ls = l;
     if (inst) {
-        const int k = ninst > 1 ? inst_of_row(inst, ninst, zg) : 0;
-        o = pull_src(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
+        if (ninst > 1) {
+            const int k = inst_of_row(inst, ninst, zg);
+            o = pull_src(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
+        } else {  // one lattice: its rows start at padded row PULL_GZ
+            o = pull_src(C, x, zg, C.nz, 0, l, ls);
+        }
     }
     out[(s * 9 + l) * n + (long long)zg * C.nx + x] = (O)((double)f[(s * 9 + ls) * C.plane + o] + base);
 }
