@@ -481,9 +481,10 @@ def main():
     lats = [make_lattice() for _ in range(n_rot)]
     lat = lats[0]
     depth = None
+    tune_ms = None
     if a.autotune > 0:
         for lt in lats:
-            depth, _ = lt.autotune(a.autotune)
+            depth, tune_ms = lt.autotune(a.autotune)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
     flush_src = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
 
@@ -607,7 +608,8 @@ def main():
                                    "never" if a.observe_every == 0 else f"every {a.observe_every} steps"),
                    "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel,
                    **({"instances": len(w["instances"])} if "instances" in w else {}),
-                   **({"pipeline_depth": depth} if depth is not None else {})},
+                   **({"pipeline_depth": depth, "autotune_ms": [round(t, 5) for t in tune_ms]}
+                      if depth is not None else {})},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -58,7 +58,7 @@ struct lbm_ctx {
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
     alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
     alignas(64) unsigned char pmap_out[2][128] = {};  // pull: store descriptors of f[0], f[1]
-    int pull_grid[8][2] = {};                         // pull: resident CTAs per mode and depth
+    int pull_grid[16][2] = {};                        // pull: resident CTAs per mode and depth
     int stages = 2;                                   // pull: boxes in flight per CTA (1 or 2)
     // the lattices of a batch (one entry for a single lattice): host and device copies
     std::vector<InstGeom> inst;
@@ -384,7 +384,8 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
             if (make_pop_tmaps(c->pmap_in[b], c->pmap_out[b], c->f[b], (int)c->esize, ns, nx, c->prows, c->pitch,
                                c->plane) != 0)
                 return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
-        const int modes[4] = {M_WRITE, M_WRITE | M_OBS, M_OBS, M_FIELDS};
+        const int per = d->z_boundary == LBM_PERIODIC ? M_PERIODIC : 0;
+        const int modes[4] = {M_WRITE, M_WRITE | M_OBS | per, M_OBS | per, M_FIELDS};
         for (int m : modes)
             for (int st = 1; st <= 2; ++st) {
                 const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m, st)
@@ -542,12 +543,16 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const void* tin = c->pmap_in[cur];
         const void* tout = c->pmap_out[cur ^ 1];
         const Batch B = batch(c);
+        // observing passes on periodic lattices run the build without wall logic (fewer
+        // instructions and registers); the others run the general build, which fits the
+        // depth-1 register budget without spills
+        const int pm = mode | (c->d.z_boundary == LBM_PERIODIC && (mode & M_OBS) ? M_PERIODIC : 0);
         if (c->d.precision == LBM_FP64)
-            e = launch_pull<double>(c->d.n_species, mode, c->stages, tin, tout, (double*)c->f[cur ^ 1], c->c64, O,
-                                    Rd, c->sched, B, c->pull_grid[mode][c->stages - 1], c->stream);
+            e = launch_pull<double>(c->d.n_species, pm, c->stages, tin, tout, (double*)c->f[cur ^ 1], c->c64, O,
+                                    Rd, c->sched, B, c->pull_grid[pm][c->stages - 1], c->stream);
         else
-            e = launch_pull<float>(c->d.n_species, mode, c->stages, tin, tout, (float*)c->f[cur ^ 1], c->c32, O,
-                                   Rd, c->sched, B, c->pull_grid[mode][c->stages - 1], c->stream);
+            e = launch_pull<float>(c->d.n_species, pm, c->stages, tin, tout, (float*)c->f[cur ^ 1], c->c32, O,
+                                   Rd, c->sched, B, c->pull_grid[pm][c->stages - 1], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)

@@ -8,8 +8,9 @@
 
 namespace lbm {
 
-// Kernel modes (bit set).
-enum { M_WRITE = 1, M_OBS = 2, M_FIELDS = 4 };
+// Kernel modes (bit set).  M_PERIODIC (pull kernel only): compiled for periodic z, with no wall
+// logic at all; without it the kernel reads the boundary from the step constants.
+enum { M_WRITE = 1, M_OBS = 2, M_FIELDS = 4, M_PERIODIC = 8 };
 
 // Width of the strip a warp owns in the fused sweep: 32 lanes minus a 2-column halo on
 // each side (the reach of the 5x5 interaction stencil).

@@ -179,11 +179,11 @@ __device__ __forceinline__ void gather_wall(const PullSmem<T, NS, ST>& S, int sl
 // site reads (far padding of ragged tiles) are set to zero.
 template <typename T, int NS, int ST>
 __device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, int qb, const StepConst<T>& C,
-                                             const PairConst& K, int px, int pz, int z0, int nz) {
+                                             const PairConst& K, int px, int pz, int z0, int nz, bool WALL) {
     const int Z = z0 - 2 + pz;
     int Zs = Z;
     bool zero = false;
-    if (C.zbc && (Z < 0 || Z >= nz)) {
+    if (WALL && (Z < 0 || Z >= nz)) {
         if (C.psi_wall == 1)
             zero = true;
         else
@@ -196,8 +196,8 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, int
     for (int s = 0; s < NS; ++s) sum[s] = T(0);
     if (!zero) {
         T g[NS][9];
-        const bool lo = C.zbc && Zs == 0, hi = C.zbc && Zs == nz - 1;
-        if (lo || hi)
+        const bool lo = WALL && Zs == 0, hi = WALL && Zs == nz - 1;
+        if (WALL && (lo || hi))
             gather_wall<T, NS, ST>(S, sl, bx, bz, lo, hi, g);
         else
             gather<T, NS, ST>(S, sl, bx, bz, g);
@@ -256,6 +256,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
            const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz) {
+    // walls in z: never in the periodic build, else as the step constants say
+    const bool WALL = (MODE & M_PERIODIC) ? false : C.zbc != 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PullSmem<T, NS, ST>& S = *reinterpret_cast<PullSmem<T, NS, ST>*>(smem_raw);
     const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
@@ -340,8 +342,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         T f[NS][9];
         T drho[NS];
         if (live) {
-            const bool lo = C.zbc && z == 0, hi = C.zbc && z == lnz - 1;
-            if (lo || hi)
+            const bool lo = WALL && z == 0, hi = WALL && z == lnz - 1;
+            if (WALL && (lo || hi))
                 gather_wall<T, NS, ST>(S, sl, tx + 4, tz + 3, lo, hi, f);
             else
                 gather<T, NS, ST>(S, sl, tx + 4, tz + 3, f);
@@ -365,9 +367,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 }
             }
         } else {
-            side_density<T, NS, ST>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz);
+            side_density<T, NS, ST>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz, WALL);
         }
-        if (ring) side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz);
+        if (ring) side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
         // the only CTA barrier of a tile: psi / rho of the tile and ring complete, box sl read
         // by all, the previous tile's column sums written
         if (__syncthreads_or(!ok)) {
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                         rowq[QR_MZ] = mz;
                     }
                 }
-                const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
+                const bool wall_row = WALL && (z == 0 || z == lnz - 1);
                 if ((MODE & M_WRITE) || ((MODE & M_OBS) && wall_row)) {
                     collide2(K, fp, dr, rh, ir, jx, jz, Fx, Fz);
 #pragma unroll
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                         rowq[QR_MZ] = mz;
                     }
                 }
-                const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
+                const bool wall_row = WALL && (z == 0 || z == lnz - 1);
                 if ((MODE & M_WRITE) || ((MODE & M_OBS) && wall_row)) {
                     collide<T, NS>(C, f, drho, rho, ir, jx, jz, F);
                     collided = true;
@@ -560,7 +562,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         // sites as one 128-byte run; with walls the populations leaving through a wall reflected
         T* const dst = fout + (long long)(prow0 + z + PULL_GZ) * C.pitch + (x + PULL_GX);
         if (collided) {
-            const bool wall_row = C.zbc == 1 && (z == 0 || z == lnz - 1);
+            const bool wall_row = WALL && (z == 0 || z == lnz - 1);
             if (!wall_row) {  // warp-uniform
                 if (MODE & M_WRITE) {
 #pragma unroll
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         }
         if (__any_sync(FULL, bad) && tx == 0) atomicOr(O.flag, 1);
         if ((MODE & M_WRITE) && collided &&
-            (x < PULL_GX || x >= nx - PULL_GX || (!C.zbc && (z < PULL_GZ || z >= lnz - PULL_GZ))))
+            (x < PULL_GX || x >= nx - PULL_GX || (!WALL && (z < PULL_GZ || z >= lnz - PULL_GZ))))
             write_images<T, NS>(C, fout, x, z, lnz, prow0);
         if (MODE & M_OBS) {
             // per-row sums over the 32 sites of this warp: transpose-reduce, lane 4q holds quantity q
@@ -695,14 +697,18 @@ template <typename T, int NS, int ST>
 cudaError_t launch_ns(int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
                       const ObsPtrs& O, const Fold& Rd, unsigned* sched, const Batch& B, int grid_max,
                       cudaStream_t st) {
+#define LBM_PULL_CASE(m) \
+    case m: return launch_mode<T, NS, m, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
     switch (mode) {
-        case M_WRITE: return launch_mode<T, NS, M_WRITE, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
-        case M_WRITE | M_OBS:
-            return launch_mode<T, NS, M_WRITE | M_OBS, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
-        case M_OBS: return launch_mode<T, NS, M_OBS, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
-        case M_FIELDS: return launch_mode<T, NS, M_FIELDS, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+        LBM_PULL_CASE(M_WRITE)
+        LBM_PULL_CASE(M_WRITE | M_OBS)
+        LBM_PULL_CASE(M_OBS)
+        LBM_PULL_CASE(M_FIELDS)
+        LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
+        LBM_PULL_CASE(M_PERIODIC | M_OBS)
         default: return cudaErrorInvalidValue;
     }
+#undef LBM_PULL_CASE
 }
 
 // Ghost columns of every row of every lattice, and (one periodic lattice) the ghost rows, from
@@ -737,24 +743,25 @@ __global__ void k_images(int ns, T* __restrict__ f, const StepConst<T> C, const 
 
 }  // namespace
 
-template <typename T, int ST>
-int blocks_per_sm(int ns, int mode) {
-    if (ns == 1) {
-        switch (mode) {
-            case M_WRITE: return pull_occupancy<T, 1, M_WRITE, ST>();
-            case M_WRITE | M_OBS: return pull_occupancy<T, 1, M_WRITE | M_OBS, ST>();
-            case M_OBS: return pull_occupancy<T, 1, M_OBS, ST>();
-            case M_FIELDS: return pull_occupancy<T, 1, M_FIELDS, ST>();
-            default: return 0;
-        }
-    }
+template <typename T, int NS, int ST>
+int blocks_per_sm_ns(int mode) {
+#define LBM_PULL_CASE(m) \
+    case m: return pull_occupancy<T, NS, m, ST>();
     switch (mode) {
-        case M_WRITE: return pull_occupancy<T, 2, M_WRITE, ST>();
-        case M_WRITE | M_OBS: return pull_occupancy<T, 2, M_WRITE | M_OBS, ST>();
-        case M_OBS: return pull_occupancy<T, 2, M_OBS, ST>();
-        case M_FIELDS: return pull_occupancy<T, 2, M_FIELDS, ST>();
+        LBM_PULL_CASE(M_WRITE)
+        LBM_PULL_CASE(M_WRITE | M_OBS)
+        LBM_PULL_CASE(M_OBS)
+        LBM_PULL_CASE(M_FIELDS)
+        LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
+        LBM_PULL_CASE(M_PERIODIC | M_OBS)
         default: return 0;
     }
+#undef LBM_PULL_CASE
+}
+
+template <typename T, int ST>
+int blocks_per_sm(int ns, int mode) {
+    return ns == 1 ? blocks_per_sm_ns<T, 1, ST>(mode) : blocks_per_sm_ns<T, 2, ST>(mode);
 }
 
 template <typename T>
