@@ -59,7 +59,10 @@ struct lbm_ctx {
     alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
     alignas(64) unsigned char pmap_out[2][128] = {};  // pull: store descriptors of f[0], f[1]
     int pull_grid[16][2] = {};                        // pull: resident CTAs per mode and depth
-    int stages = 2;                                   // pull: boxes in flight per CTA (1 or 2)
+    // pull: boxes in flight per CTA (1 or 2) for passes without [0] and with [1] observables; FP32
+    // defaults from measurements on GB300 (depth 1 runs 3 CTAs per SM within 80 registers, which
+    // the observing build exceeds), FP64 depth 2
+    int stages[2] = {2, 2};
     // the lattices of a batch (one entry for a single lattice): host and device copies
     std::vector<InstGeom> inst;
     InstGeom* inst_d = nullptr;
@@ -299,6 +302,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     const int nx = d->nx, nz = d->nz, ns = d->n_species;
     c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+    if (d->precision == LBM_FP32) c->stages[0] = 1;
     c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_PULL : d->kernel;
     c->pull = c->kernel == LBM_KERNEL_PULL;
     {  // the lattices: rows stacked in order, each with its own ghost rows in the planes
@@ -547,12 +551,13 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         // instructions and registers); the others run the general build, which fits the
         // depth-1 register budget without spills
         const int pm = mode | (c->d.z_boundary == LBM_PERIODIC && (mode & M_OBS) ? M_PERIODIC : 0);
+        const int stg = c->stages[(mode & M_OBS) ? 1 : 0];
         if (c->d.precision == LBM_FP64)
-            e = launch_pull<double>(c->d.n_species, pm, c->stages, tin, tout, (double*)c->f[cur ^ 1], c->c64, O,
-                                    Rd, c->sched, B, c->pull_grid[pm][c->stages - 1], c->stream);
+            e = launch_pull<double>(c->d.n_species, pm, stg, tin, tout, (double*)c->f[cur ^ 1], c->c64, O,
+                                    Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream);
         else
-            e = launch_pull<float>(c->d.n_species, pm, c->stages, tin, tout, (float*)c->f[cur ^ 1], c->c32, O,
-                                   Rd, c->sched, B, c->pull_grid[pm][c->stages - 1], c->stream);
+            e = launch_pull<float>(c->d.n_species, pm, stg, tin, tout, (float*)c->f[cur ^ 1], c->c32, O,
+                                   Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
@@ -1087,7 +1092,8 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
     if (e == cudaSuccess) e = cudaMemcpyAsync(sv + 2 * fbytes, c->avg, obs_bytes(c), cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sv + 2 * fbytes + obs_bytes(c), c->flag, sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
-    const int cur = c->cur, saved_stages = c->stages;
+    const int cls = c->observe_every > 0 ? 1 : 0;  // the pass kind tuned: with or without observables
+    const int cur = c->cur, saved_stages = c->stages[cls];
     const long long step = c->step, samples = c->samples, launches = c->launches;
     const bool prof = c->profiling;
     c->profiling = false;
@@ -1097,7 +1103,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     for (int st = 1; st <= 2 && e == cudaSuccess; ++st) {
-        c->stages = st;
+        c->stages[cls] = st;
         for (int k = 0; k < 2 + steps && e == cudaSuccess; ++k) {  // two warm-up steps, then the timed ones
             if (k == 2) e = cudaEventRecord(a, c->stream);
             const bool ob = c->observe_every > 0;
@@ -1130,7 +1136,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
     c->samples = samples;
     c->launches = launches;
     c->profiling = prof;
-    c->stages = e == cudaSuccess ? pick : saved_stages;
+    c->stages[cls] = e == cudaSuccess ? pick : saved_stages;
     drop_graphs(c);
     CK(e);
     if (chosen) *chosen = pick;
