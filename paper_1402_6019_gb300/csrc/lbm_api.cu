@@ -39,7 +39,7 @@ struct lbm_ctx {
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
     void* part_row[2] = {nullptr, nullptr};  // partial sums in the populations' precision, one
     void* part_col[2] = {nullptr, nullptr};  // set per population buffer parity
-    unsigned* sched = nullptr;  // pull: work-item counters (zero between launches)
+    unsigned* sched = nullptr;  // pull: tile and reduction work-item counters (zero between launches)
     // pull: the last observing step's partial sums (in part_*[pending_buf]) still to be reduced;
     // the next pull launch folds the reduction in, a host read flushes it with k_reduce
     bool pending = false;
@@ -57,7 +57,6 @@ struct lbm_ctx {
     alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
     alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
-    alignas(64) unsigned char pmap_out[2][128] = {};  // pull: store descriptors of f[0], f[1]
     int pull_grid[16][2] = {};                        // pull: resident CTAs per mode and depth
     // pull: boxes in flight per CTA (1 or 2) for passes without [0] and with [1] observables; FP32
     // defaults from measurements on GB300 (depth 1 runs 3 CTAs per SM within 80 registers, which
@@ -362,8 +361,8 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
         CKC(cudaMalloc(&c->part_row[b], (size_t)rows_parts * nz * NQR * c->esize));
         CKC(cudaMalloc(&c->part_col[b], (size_t)col_parts * nx * NQC * c->esize));
     }
-    CKC(cudaMalloc(&c->sched, 2 * sizeof(unsigned)));
-    CKC(cudaMemsetAsync(c->sched, 0, 2 * sizeof(unsigned), c->stream));
+    CKC(cudaMalloc(&c->sched, 4 * sizeof(unsigned)));
+    CKC(cudaMemsetAsync(c->sched, 0, 4 * sizeof(unsigned), c->stream));
     CKC(cudaMalloc(&c->ticket, sizeof(unsigned)));
     CKC(cudaMalloc(&c->flag, sizeof(int)));
     // observables: obs_len entries, then the reduction's block partials of the scalars
@@ -385,8 +384,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     if (c->pull) {
         for (int b = 0; b < 2; ++b)
-            if (make_pop_tmaps(c->pmap_in[b], c->pmap_out[b], c->f[b], (int)c->esize, ns, nx, c->prows, c->pitch,
-                               c->plane) != 0)
+            if (make_pop_tmap(c->pmap_in[b], c->f[b], (int)c->esize, ns, c->prows, c->pitch, c->plane) != 0)
                 return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
         const int per = d->z_boundary == LBM_PERIODIC ? M_PERIODIC : 0;
         const int modes[4] = {M_WRITE, M_WRITE | M_OBS | per, M_OBS | per, M_FIELDS};
@@ -545,7 +543,6 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         c->launches += 1;
     } else if (c->pull) {
         const void* tin = c->pmap_in[cur];
-        const void* tout = c->pmap_out[cur ^ 1];
         const Batch B = batch(c);
         // observing passes on periodic lattices run the build without wall logic (fewer
         // instructions and registers); the others run the general build, which fits the
@@ -553,10 +550,10 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const int pm = mode | (c->d.z_boundary == LBM_PERIODIC && (mode & M_OBS) ? M_PERIODIC : 0);
         const int stg = c->stages[(mode & M_OBS) ? 1 : 0];
         if (c->d.precision == LBM_FP64)
-            e = launch_pull<double>(c->d.n_species, pm, stg, tin, tout, (double*)c->f[cur ^ 1], c->c64, O,
+            e = launch_pull<double>(c->d.n_species, pm, stg, tin, (double*)c->f[cur ^ 1], c->c64, O,
                                     Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream);
         else
-            e = launch_pull<float>(c->d.n_species, pm, stg, tin, tout, (float*)c->f[cur ^ 1], c->c32, O,
+            e = launch_pull<float>(c->d.n_species, pm, stg, tin, (float*)c->f[cur ^ 1], c->c32, O,
                                    Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;

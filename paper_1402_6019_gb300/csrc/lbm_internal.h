@@ -156,22 +156,21 @@ struct Fold {
 // prows = sum over the lattices of (nz + 2 PULL_GZ).
 constexpr int PULL_GX = 4, PULL_GZ = 3;
 
-// Pull-layout kernel: TMA descriptors of one population buffer f ([9 ns][prows][pitch] values):
-// the load box of a tile with its 3-cell ring (in_map) and the store box of a tile (out_map),
-// 128 bytes each.  Returns 0 on success.
-int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int prows, int pitch,
-                   long long plane);
+// Pull-layout kernel: the TMA descriptor (CUtensorMap, 128 bytes at in_map) of one population
+// buffer f ([9 ns][prows][pitch] values) for loading the box of a tile and its 3-cell ring.
+// Returns 0 on success.
+int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int pitch, long long plane);
 // CTAs of the pull kernel resident per SM for a mode and a pipeline depth (stages = boxes in
 // flight per CTA, 1 or 2; sets the kernel's shared-memory limit on the current device); 0 on
 // failure.
 template <typename T>
 int pull_blocks_per_sm(int ns, int mode, int stages);
-// One pass of the pull kernel: loads through tin (a buffer's in_map), stores through tout (the
-// other buffer's out_map); fout is that other buffer (periodic images are stored to it
-// directly).  fold: a pending reduction run by the same launch.  sched: two counters, zero
-// before the launch and left zero by it.  grid_max: resident CTAs on the device.
+// One pass of the pull kernel: loads through tin (a buffer's in_map) and stores the new values
+// into fout, the other buffer (their periodic images too).  fold: a pending reduction run by the same launch.  sched: three counters (tiles,
+// CTAs done, reduction items), zero before the launch and left zero by it.  grid_max: resident
+// CTAs on the device.
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, const void* tout, T* fout,
+cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
                         const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
                         int grid_max, cudaStream_t st);
 // One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.

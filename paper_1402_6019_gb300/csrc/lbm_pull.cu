@@ -25,8 +25,8 @@
 // Tiles are handed out in row-major order by an atomic counter (the CTA that finishes last
 // resets it), so the CTAs at work at any moment cover a band of rows and read each other's halo
 // while it is in L2.  A launch can also carry the reduction of the previous pass's observable
-// partial sums (Fold): each CTA runs its share of the reduction's work items while its first
-// tile load is in flight.
+// partial sums (Fold): CTAs that run out of tiles draw the reduction's work items from a second
+// counter, so they fill the spread of the CTAs' last tiles.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -91,6 +91,7 @@ struct PullSmem {
     typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
     alignas(8) unsigned long long bar[ST];
     TileInfo<T> ti[NTQ];
+    int fold_item;  // the reduction work item thread 0 drew for the CTA
 };
 
 template <typename T>
@@ -253,7 +254,7 @@ __device__ __noinline__ void write_images(const StepConst<T>& C, T* __restrict__
 
 template <typename T, int NS, int MODE, int ST>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
-    k_pull(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, T* __restrict__ fout,
+    k_pull(const __grid_constant__ CUtensorMap tin, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
            const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz) {
     // walls in z: never in the periodic build, else as the step constants say
@@ -310,14 +311,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         if (more) upcoming = (int)atomicAdd(&sched[0], 1u);
     }
     __syncthreads();
-    if (Rd.enabled) {  // the previous pass's reduction, under the first load
-        const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-        const int nb = nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-        for (int b = blockIdx.x; b < nb; b += gridDim.x)
-            reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
-                            Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc,
-                            ninst > 1 ? inst : nullptr, ninst);
-    }
     unsigned parity = 0;  // bit sl: phase of box sl's barrier
     bool failed = false;
     // the previous tile's column-sum slot (observables): its column x and tile row, or x = -1
@@ -636,6 +629,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             static_cast<T*>(O.part_col)[((long long)prev_x * ntz + prev_jg) * NQC + tz] = v;
         }
     }
+    if (Rd.enabled) {
+        // the previous pass's reduction: its work items go to the CTAs as they run out of tiles
+        // (the spread of the CTAs' last tiles is idle time otherwise), drawn from a counter
+        const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+        const int nb = nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+        for (;;) {
+            if (tid == 0) S.fold_item = (int)atomicAdd(&sched[2], 1u);
+            __syncthreads();
+            const int b = S.fold_item;
+            if (b >= nb) break;  // uniform: every thread read the same item
+            reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
+                            Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc,
+                            ninst > 1 ? inst : nullptr, ninst);  // ends with a CTA barrier
+        }
+    }
     if (tid == 0) {
         if (failed) {
             atomicOr(O.flag, 2);
@@ -651,6 +659,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         __threadfence();
         if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
             atomicExch(&sched[0], 0u);
+            atomicExch(&sched[2], 0u);
             atomicExch(&sched[1], 0u);
         }
     }
@@ -668,7 +677,7 @@ int pull_occupancy() {
 }
 
 template <typename T, int NS, int MODE, int ST>
-cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepConst<T>& C, const ObsPtrs& O,
+cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const ObsPtrs& O,
                         const Fold& Rd, unsigned* sched, const Batch& B, int grid_max, cudaStream_t st) {
     const int ntx = (C.nx + PX - 1) / PX;
     const long long ntiles = (long long)ntx * B.ntz;
@@ -688,17 +697,16 @@ cudaError_t launch_mode(const void* tin, const void* tout, T* fout, const StepCo
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST>, *static_cast<const CUtensorMap*>(tin),
-                              *static_cast<const CUtensorMap*>(tout), fout, C, K, O, Rd, sched, B.inst, B.ninst, ntx,
-                              B.ntz);
+    return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST>, *static_cast<const CUtensorMap*>(tin), fout, C, K, O,
+                              Rd, sched, B.inst, B.ninst, ntx, B.ntz);
 }
 
 template <typename T, int NS, int ST>
-cudaError_t launch_ns(int mode, const void* tin, const void* tout, T* fout, const StepConst<T>& C,
+cudaError_t launch_ns(int mode, const void* tin, T* fout, const StepConst<T>& C,
                       const ObsPtrs& O, const Fold& Rd, unsigned* sched, const Batch& B, int grid_max,
                       cudaStream_t st) {
 #define LBM_PULL_CASE(m) \
-    case m: return launch_mode<T, NS, m, ST>(tin, tout, fout, C, O, Rd, sched, B, grid_max, st);
+    case m: return launch_mode<T, NS, m, ST>(tin, fout, C, O, Rd, sched, B, grid_max, st);
     switch (mode) {
         LBM_PULL_CASE(M_WRITE)
         LBM_PULL_CASE(M_WRITE | M_OBS)
@@ -770,15 +778,15 @@ int pull_blocks_per_sm(int ns, int mode, int stages) {
 }
 
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, const void* tout, T* fout,
+cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
                         const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
                         int grid_max, cudaStream_t st) {
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
     if (stages == 1)
-        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st)
-                       : launch_ns<T, 2, 1>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st);
-    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st)
-                   : launch_ns<T, 2, 2>(mode, tin, tout, fout, C, O, fold, sched, B, grid_max, st);
+        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st)
+                       : launch_ns<T, 2, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st);
+    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st)
+                   : launch_ns<T, 2, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st);
 }
 
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
@@ -792,34 +800,26 @@ cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, const Batch&
     return cudaGetLastError();
 }
 
-int make_pop_tmaps(void* in_map, void* out_map, const void* f, int esize, int ns, int nx, int prows, int pitch,
-                   long long plane) {
+int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int pitch, long long plane) {
     const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!encode) return 1;
-    // loads: the whole padded plane (prows rows); stores (full tiles only): up to the last
-    // lattice column
-    const cuuint64_t dims_in[3] = {(cuuint64_t)pitch, (cuuint64_t)prows, (cuuint64_t)(9 * ns)};
-    const cuuint64_t dims_out[3] = {(cuuint64_t)(nx + PULL_GX), (cuuint64_t)prows, (cuuint64_t)(9 * ns)};
+    // the whole padded plane (prows rows), boxes of a tile and its 3-cell ring
+    const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)prows, (cuuint64_t)(9 * ns)};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
-    const cuuint32_t box_in[3] = {(cuuint32_t)BX, (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
-    const cuuint32_t box_out[3] = {(cuuint32_t)PX, (cuuint32_t)PZ, (cuuint32_t)(9 * ns)};
+    const cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    CUresult r = encode(static_cast<CUtensorMap*>(in_map), dt, 3, const_cast<void*>(f), dims_in, strides, box_in, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return 2;
-    r = encode(static_cast<CUtensorMap*>(out_map), dt, 3, const_cast<void*>(f), dims_out, strides, box_out, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r = encode(static_cast<CUtensorMap*>(in_map), dt, 3, const_cast<void*>(f), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : 2;
 }
 
 template int pull_blocks_per_sm<float>(int, int, int);
 template int pull_blocks_per_sm<double>(int, int, int);
-template cudaError_t launch_pull<float>(int, int, int, const void*, const void*, float*, const StepConst<float>&,
+template cudaError_t launch_pull<float>(int, int, int, const void*, float*, const StepConst<float>&,
                                         const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
-template cudaError_t launch_pull<double>(int, int, int, const void*, const void*, double*, const StepConst<double>&,
+template cudaError_t launch_pull<double>(int, int, int, const void*, double*, const StepConst<double>&,
                                          const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
 template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, const Batch&, cudaStream_t);
 template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, const Batch&, cudaStream_t);
