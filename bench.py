@@ -55,7 +55,7 @@ def _args():
     ap.add_argument("--kernel", choices=["pull", "fused", "twopass", "sweep"], default="pull")
     ap.add_argument("--tile-rows", type=int, default=0, help="FUSED kernel tile height (8 or 16; 0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--l2", choices=["rotate", "flush"], default="rotate",
                     help="rotate: step several lattices of the workload in turn, so that each step's input "
                          "was evicted from L2 by the others' traffic (no flush); flush: one lattice, a 256 MiB "
@@ -570,26 +570,36 @@ def main():
                           f"{a.steps} steps, which serialises the launches ({prof_ms / a.steps * 1e3:.2f} us per step)"}
 
     # end to end through the public API with host buffers: upload the fields from pinned host
-    # memory, then per step lbm_step + lbm_averages (D2H of the step's observables)
+    # memory, then per step lbm_step and the read-back of that step's observables into pinned
+    # host memory (lbm_observables_enqueue), each record unpacked on the host while the next
+    # step runs (double-buffered)
     e2e = None
     if a.e2e_steps > 0:
         rho_pin = torch.from_numpy(np.ascontiguousarray(w["rho"])).pin_memory()
         rho_np = rho_pin.numpy()
-        o, prof = lat._obs_struct()
+        reader = lat.reader(depth=2)
         barrier()
         t0 = time.perf_counter()
         lat.set_fields(rho_np)
         lat.set_observe(1)
+        pending = None
         for _ in range(a.e2e_steps):
             lat.step(1)
-            L.lbm_averages(lat.h, o, True)
+            # the step before's observables (this step's reduction runs in the next launch)
+            ticket = reader.enqueue(averages="completed", reset=True)
+            if pending is not None:
+                reader.result(pending)
+            pending = ticket
+        reader.result(pending)
+        reader.result(reader.enqueue(averages=True, reset=True))  # the last step's
         barrier()
         dt, e2e_sites = replicas.aggregate(time.perf_counter() - t0, sites * a.e2e_steps, dist=dist,
                                            device="cuda")
-        obs_bytes = (16 + 5 * nz + 2 * nx) * 8
         e2e = {"value": round(e2e_sites / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": int(rho_np.nbytes // a.e2e_steps), "d2h_bytes_per_step": obs_bytes,
-               "steps": a.e2e_steps}
+               "h2d_bytes_per_step": int(rho_np.nbytes // a.e2e_steps),
+               "d2h_bytes_per_step": int(L.load().lbm_observables_bytes(lat.h)), "steps": a.e2e_steps,
+               "read": "every step's observables (time sums of one sample), double-buffered asynchronous "
+                       "reads of the completed sums, each unpacked on the host while the next step runs"}
 
     if rank != 0:
         return

@@ -161,6 +161,25 @@ int lbm_observables(lbm_ctx *c, lbm_obs *out);
    reset != 0 clears the sums afterwards.  Synchronises the stream. */
 int lbm_averages(lbm_ctx *c, lbm_obs *out, int reset);
 
+/* Reading observables without waiting (no counterpart in the paper): lets a caller overlap the
+   read-back of one step's observables with the next step.
+   lbm_observables_enqueue enqueues on the context's stream what lbm_observables (averages = 0)
+   or lbm_averages (averages = 1; reset != 0 clears the sums after the copy) compute, copying
+   the raw record -- lbm_observables_bytes(c) bytes -- into dst (pinned host memory, or device
+   memory), and returns without waiting; *ticket (may be NULL) identifies the enqueue.
+   averages = 2: the time sums as they stand, without the reduction of the last observing step
+   if it is still pending (the next step's launch adds it; it is counted in the next record), so
+   no separate reduction is launched -- when every step samples, each record then holds the
+   step before the last.
+   lbm_wait waits until the work enqueued up to that ticket is done (an event; the last 64
+   tickets are tracked, older ones wait for the whole stream).  lbm_observables_unpack turns a
+   record that has arrived into lbm_obs (host arithmetic only; returns LBM_ENONFINITE for a
+   current-state record whose state held a bad density). */
+long long lbm_observables_bytes(const lbm_ctx *c);
+int lbm_observables_enqueue(lbm_ctx *c, void *dst, int averages, int reset, long long *ticket);
+int lbm_wait(lbm_ctx *c, long long ticket);
+int lbm_observables_unpack(const lbm_ctx *c, const void *src, lbm_obs *out);
+
 /* Wait for the context's stream; reports LBM_ENONFINITE if a step met a bad density. */
 int lbm_synchronize(lbm_ctx *c);
 

@@ -86,6 +86,8 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<cudaEvent_t> aev;  // adjoint: three pairs per step, around its kernels
     size_t aev_used = 0;
+    cudaEvent_t tev[64] = {};      // asynchronous reads: an event per ticket (ring)
+    long long tickets = 0;         // tickets issued
     std::string err;
 };
 
@@ -234,6 +236,8 @@ static void release(lbm_ctx* c) {
     c->ev.clear();
     for (cudaEvent_t e : c->aev) cudaEventDestroy(e);
     c->aev.clear();
+    for (cudaEvent_t& e : c->tev)
+        if (e) cudaEventDestroy(e);
     void* ptrs[] = {c->f_raw[0],   c->f_raw[1], c->part_row[0], c->part_row[1], c->part_col[0],
                     c->part_col[1], c->sched,   c->ticket,      c->flag,        c->out,
                     c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d,
@@ -367,8 +371,9 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     CKC(cudaMalloc(&c->flag, sizeof(int)));
     // observables: obs_len entries, then the reduction's block partials of the scalars
     const size_t olen = (size_t)(obs_len(nx, nz) + 5LL * reduce_blocks(nx, nz)) * sizeof(double);
-    CKC(cudaMalloc(&c->out, olen));
-    CKC(cudaMalloc(&c->avg, olen));
+    // each followed by room for the trailer of an asynchronous read (lbm_observables_enqueue)
+    CKC(cudaMalloc(&c->out, olen + 64));
+    CKC(cudaMalloc(&c->avg, olen + 64));
     CKC(cudaMalloc(&c->staging, (size_t)(ns + 2) * nx * nz * sizeof(double)));
     CKC(cudaMallocHost(&c->host_out, olen));
     CKC(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->stream));
@@ -987,6 +992,85 @@ extern "C" int lbm_averages(lbm_ctx* c, lbm_obs* o, int reset) {
         c->samples = 0;
     }
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Asynchronous reads of the observables
+// ---------------------------------------------------------------------------------------
+// A record: the observable buffer as the reduction leaves it (obs_bytes), then a trailer.
+struct ObsTrailer {
+    double samples;  // states summed in the record (1: the current state)
+    long long step;  // the step counter when the read was enqueued
+    long long averages;
+    long long pad_;
+};
+
+extern "C" long long lbm_observables_bytes(const lbm_ctx* c) {
+    return c ? (long long)(obs_bytes(c) + sizeof(ObsTrailer)) : -1;
+}
+
+extern "C" int lbm_observables_enqueue(lbm_ctx* c, void* dst, int averages, int reset, long long* ticket) {
+    if (!c) return LBM_EINVAL;
+    if (!dst) return fail(c, LBM_EINVAL, "dst is NULL");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    // the trailer is written on the device right after the buffer it describes, and the two leave
+    // in one device-to-host copy: a host-to-host copy would make the call wait for the stream
+    static_assert(sizeof(ObsTrailer) == 32, "trailer layout");
+    if (averages < 0 || averages > 2) return fail(c, LBM_EINVAL, "averages must be 0, 1 or 2");
+    double* src;
+    double samples;
+    // a reduction left pending by the last observing step, to be added to the time sums by the
+    // next step's launch
+    const bool held = c->pull && c->pending && c->pending_acc;
+    if (averages == 2 && held) {  // the sums as they stand: the pending sample goes to the next read
+        src = c->avg;
+        samples = (double)(c->samples - 1);
+    } else if (averages) {
+        CK(flush_pending(c));
+        src = c->avg;
+        samples = (double)c->samples;
+    } else {
+        CK(enqueue_pass(c, c->cur, M_OBS, true, false, false));
+        src = c->out;
+        samples = 1.0;
+    }
+    CK(launch_obs_trailer(reinterpret_cast<double*>(reinterpret_cast<char*>(src) + obs_bytes(c)), samples, c->step,
+                          averages ? 1 : 0, c->stream));
+    c->launches += 1;
+    CK(cudaMemcpyAsync(dst, src, obs_bytes(c) + sizeof(ObsTrailer), cudaMemcpyDefault, c->stream));
+    if (averages && reset) {
+        CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
+        c->samples = averages == 2 && held ? 1 : 0;
+    }
+    cudaEvent_t& e = c->tev[c->tickets % 64];
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, c->stream));
+    if (ticket) *ticket = c->tickets;
+    c->tickets += 1;
+    return LBM_OK;
+}
+
+extern "C" int lbm_wait(lbm_ctx* c, long long ticket) {
+    if (!c) return LBM_EINVAL;
+    if (ticket < 0 || ticket >= c->tickets) return fail(c, LBM_EINVAL, "ticket %lld was not issued", ticket);
+    CK(cudaSetDevice(c->d.device));
+    if (ticket < c->tickets - 64)
+        CK(cudaStreamSynchronize(c->stream));  // its event was reused: wait for everything
+    else
+        CK(cudaEventSynchronize(c->tev[ticket % 64]));
+    return LBM_OK;
+}
+
+extern "C" int lbm_observables_unpack(const lbm_ctx* c, const void* src, lbm_obs* o) {
+    if (!c || !src || !o) return LBM_EINVAL;
+    const double* buf = static_cast<const double*>(src);
+    ObsTrailer t;
+    memcpy(&t, static_cast<const char*>(src) + obs_bytes(c), sizeof t);
+    unpack(c, buf, o, t.samples > 0 ? 1.0 / t.samples : 0.0);
+    o->step = t.step;
+    o->samples = (long long)t.samples;
+    return o->nonfinite && !t.averages ? LBM_ENONFINITE : LBM_OK;
 }
 
 extern "C" int lbm_synchronize(lbm_ctx* c) {

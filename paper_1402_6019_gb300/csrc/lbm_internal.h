@@ -197,6 +197,9 @@ cudaError_t launch_import(int ns, T* f, const double* in, const StepConst<T>& C,
 // doubles (FP64 mode) or (hi, lo) float pairs (FP32 mode).  inst / ninst: the device table of a
 // stacked batch (rows of different lattices are not neighbours), null for one lattice.
 int reduce_blocks(int nx, int nz);
+// Writes the trailer of an asynchronous read (samples, step, averages, 0: four 8-byte words) at
+// dst, in device memory, in stream order.
+cudaError_t launch_obs_trailer(double* dst, double samples, long long step, long long averages, cudaStream_t st);
 cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
                           unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
                           bool tail, const InstGeom* inst, int ninst, cudaStream_t st);

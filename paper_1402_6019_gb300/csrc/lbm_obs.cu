@@ -190,6 +190,20 @@ cudaError_t launch_import(int ns, T* f, const double* in, const StepConst<T>& C,
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_obs_trailer(double* dst, double samples, long long step, long long averages) {
+    dst[0] = samples;
+    reinterpret_cast<long long*>(dst)[1] = step;
+    reinterpret_cast<long long*>(dst)[2] = averages;
+    reinterpret_cast<long long*>(dst)[3] = 0;
+}
+}  // namespace
+
+cudaError_t launch_obs_trailer(double* dst, double samples, long long step, long long averages, cudaStream_t st) {
+    k_obs_trailer<<<1, 1, 0, st>>>(dst, samples, step, averages);
+    return cudaGetLastError();
+}
+
 int reduce_blocks(int nx, int nz) {
     return (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32) + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
 }

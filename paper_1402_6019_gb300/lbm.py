@@ -78,6 +78,10 @@ SIGNATURES = {
     "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "lbm_set_populations": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "lbm_observables_bytes": (ctypes.c_longlong, [_VP]),
+    "lbm_observables_enqueue": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm_wait": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "lbm_observables_unpack": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(lbm_obs)]),
     "lbm_profile_read_adjoint": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_snapshot_bytes": (ctypes.c_longlong, [_VP]),
@@ -438,6 +442,10 @@ class Lattice:
         lbm_observables(self.h, o)
         return self._obs_dict(o, prof)
 
+    def reader(self, depth=2):
+        """An ObsReader: asynchronous, double-buffered reads of this lattice's observables."""
+        return ObsReader(self, depth)
+
     def set_observe(self, every):
         lbm_set_observe(self.h, every)
 
@@ -463,3 +471,38 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+class ObsReader:
+    """Reads of a lattice's observables that do not wait for the GPU (lbm_observables_enqueue):
+    each enqueue copies a raw record into one of `depth` pinned host buffers, and result(ticket)
+    waits for that record only, then unpacks it.  A buffer is reused `depth` enqueues later, so
+    read each result before then."""
+
+    def __init__(self, lat, depth=2):
+        import torch
+
+        self.lat = lat
+        n = load().lbm_observables_bytes(lat.h)
+        self.bufs = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for _ in range(depth)]
+        self.k = 0
+
+    def enqueue(self, averages=False, reset=False):
+        """averages: False (the current state), True (the time sums), or "completed" (the time
+        sums without a still-pending reduction: no extra launch)."""
+        t = ctypes.c_longlong()
+        buf = self.bufs[self.k % len(self.bufs)]
+        self.k += 1
+        mode = 2 if averages == "completed" else (1 if averages else 0)
+        _check(load().lbm_observables_enqueue(self.lat.h, ctypes.c_void_p(buf.data_ptr()), mode,
+                                              1 if reset else 0, ctypes.byref(t)), self.lat.h)
+        return (t.value, buf)
+
+    def result(self, ticket):
+        t, buf = ticket
+        _check(load().lbm_wait(self.lat.h, t), self.lat.h)
+        o, prof = self.lat._obs_struct()
+        rc = load().lbm_observables_unpack(self.lat.h, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(o))
+        if rc not in (LBM_OK, LBM_ENONFINITE):
+            _check(rc, self.lat.h)
+        return self.lat._obs_dict(o, prof)
