@@ -283,7 +283,10 @@ int lbm_set_populations(lbm_ctx *c, const double *f, int where);
    the context's internal layout and precision, the step counter and the FP32 reference
    densities -- into lbm_snapshot_bytes(c) bytes of device memory at dst (asynchronous);
    lbm_restore makes such a snapshot the current state again, bit for bit, and resets the time
-   averages (synchronises).  A snapshot is only meaningful to the context that wrote it. */
+   averages.  A snapshot is only meaningful to the context that wrote it; the context remembers
+   the step counter and reference densities of the snapshots it wrote (by address), so restoring
+   one of them is asynchronous, while restoring memory it did not write there reads them back
+   from the snapshot (synchronises). */
 long long lbm_snapshot_bytes(const lbm_ctx *c);
 int lbm_snapshot(lbm_ctx *c, void *dst);
 int lbm_restore(lbm_ctx *c, const void *src);

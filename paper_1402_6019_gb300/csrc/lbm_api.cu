@@ -8,7 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -57,7 +59,8 @@ struct lbm_ctx {
     alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
     alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
-    int pull_grid[16][2] = {};                        // pull: resident CTAs per mode and depth
+    int pull_grid[32][2] = {};                        // pull: resident CTAs per mode and depth
+    void* rec = nullptr;                              // pull, M_RECORD pass: where the input state goes
     // pull: boxes in flight per CTA (1 or 2) for passes without [0] and with [1] observables; FP32
     // defaults from measurements on GB300 (depth 1 runs 3 CTAs per SM within 80 registers, which
     // the observing build exceeds), FP64 depth 2
@@ -86,6 +89,8 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<cudaEvent_t> aev;  // adjoint: three pairs per step, around its kernels
     size_t aev_used = 0;
+    std::map<const void*, std::pair<std::array<double, 2>, long long>> snaps;  // tails of this
+                                   // context's snapshots (rho_ref, step), by address
     cudaEvent_t tev[64] = {};      // asynchronous reads: an event per ticket (ring)
     long long tickets = 0;         // tickets issued
     std::string err;
@@ -392,7 +397,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
             if (make_pop_tmap(c->pmap_in[b], c->f[b], (int)c->esize, ns, c->prows, c->pitch, c->plane) != 0)
                 return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
         const int per = d->z_boundary == LBM_PERIODIC ? M_PERIODIC : 0;
-        const int modes[4] = {M_WRITE, M_WRITE | M_OBS | per, M_OBS | per, M_FIELDS};
+        const int modes[5] = {M_WRITE, M_WRITE | M_OBS | per, M_OBS | per, M_FIELDS, M_WRITE | M_RECORD};
         for (int m : modes)
             for (int st = 1; st <= 2; ++st) {
                 const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m, st)
@@ -556,10 +561,10 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const int stg = c->stages[(mode & M_OBS) ? 1 : 0];
         if (c->d.precision == LBM_FP64)
             e = launch_pull<double>(c->d.n_species, pm, stg, tin, (double*)c->f[cur ^ 1], c->c64, O,
-                                    Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream);
+                                    Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream, (double*)c->rec);
         else
             e = launch_pull<float>(c->d.n_species, pm, stg, tin, (float*)c->f[cur ^ 1], c->c32, O,
-                                   Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream);
+                                   Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream, (float*)c->rec);
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
@@ -781,6 +786,7 @@ extern "C" int lbm_snapshot(lbm_ctx* c, void* dst) {
     const SnapTail t{{c->rho_ref[0], c->rho_ref[1]}, c->step};
     // pageable source: staged before the call returns
     CK(cudaMemcpyAsync(static_cast<char*>(dst) + pop_bytes(c), &t, sizeof t, cudaMemcpyHostToDevice, c->stream));
+    c->snaps[dst] = {{t.rho_ref[0], t.rho_ref[1]}, t.step};  // a restore from here needs no read-back
     return LBM_OK;
 }
 
@@ -789,8 +795,17 @@ extern "C" int lbm_restore(lbm_ctx* c, const void* src) {
     if (!src) return fail(c, LBM_EINVAL, "src is NULL");
     CK(cudaSetDevice(c->d.device));
     SnapTail t;
-    CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + pop_bytes(c), sizeof t, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    const auto known = c->snaps.find(src);
+    const bool async = known != c->snaps.end();
+    if (async) {  // a snapshot this context wrote: its tail is known on the host
+        t.rho_ref[0] = known->second.first[0];
+        t.rho_ref[1] = known->second.first[1];
+        t.step = known->second.second;
+    } else {
+        CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + pop_bytes(c), sizeof t, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     CK(cudaMemcpyAsync(c->f[0], src, pop_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
     if (t.rho_ref[0] != c->rho_ref[0] || t.rho_ref[1] != c->rho_ref[1]) {
         c->rho_ref[0] = t.rho_ref[0];
@@ -803,7 +818,7 @@ extern "C" int lbm_restore(lbm_ctx* c, const void* src) {
     CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
     c->samples = 0;
     c->pending = false;
-    CK(cudaStreamSynchronize(c->stream));
+    if (!async) CK(cudaStreamSynchronize(c->stream));
     c->step = t.step;
     c->have_fields = true;
     return LBM_OK;
@@ -1246,10 +1261,26 @@ static size_t state_values(const lbm_ctx* c) { return (size_t)c->d.n_species * 9
 extern "C" int lbm_record_states(lbm_ctx* c, int nsteps, void* states, int precision) {
     if (!c) return LBM_EINVAL;
     if (nsteps < 0 || (nsteps > 0 && !states)) return fail(c, LBM_EINVAL, "nsteps < 0 or states is NULL");
+    if (precision != LBM_FP64 && precision != LBM_FP32) return fail(c, LBM_EINVAL, "precision must be LBM_FP64 or LBM_FP32");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
     const size_t bytes = state_values(c) * (precision == LBM_FP32 ? sizeof(float) : sizeof(double));
+    // the pull kernel writes the state it reads (M_RECORD) when the record is in its own precision,
+    // the lattice is one lattice, and the step does not sample; otherwise export, then step
+    const bool fused = c->pull && c->inst.size() == 1 && precision == c->d.precision;
     for (int k = 0; k < nsteps; ++k) {
-        if (int r = lbm_export_state(c, static_cast<char*>(states) + k * bytes, precision)) return r;
-        if (int r = lbm_step(c, 1)) return r;
+        void* dst = static_cast<char*>(states) + k * bytes;
+        if (fused && !observe_now(c, c->step)) {
+            c->rec = dst;
+            const cudaError_t e = enqueue_pass(c, c->cur, M_WRITE | M_RECORD, false, false, true);
+            c->rec = nullptr;
+            CK(e);
+            c->cur ^= 1;
+            c->step += 1;
+        } else {
+            if (int r = lbm_export_state(c, dst, precision)) return r;
+            if (int r = lbm_step(c, 1)) return r;
+        }
     }
     return LBM_OK;
 }

@@ -9,8 +9,10 @@
 namespace lbm {
 
 // Kernel modes (bit set).  M_PERIODIC (pull kernel only): compiled for periodic z, with no wall
-// logic at all; without it the kernel reads the boundary from the step constants.
-enum { M_WRITE = 1, M_OBS = 2, M_FIELDS = 4, M_PERIODIC = 8 };
+// logic at all; without it the kernel reads the boundary from the step constants.  M_RECORD
+// (pull kernel, with M_WRITE, one lattice): also writes the step's input state, the
+// post-streaming populations as plain values, [ns][9][nz][nx] in the kernel's precision.
+enum { M_WRITE = 1, M_OBS = 2, M_FIELDS = 4, M_PERIODIC = 8, M_RECORD = 16 };
 
 // Width of the strip a warp owns in the fused sweep: 32 lanes minus a 2-column halo on
 // each side (the reach of the 5x5 interaction stencil).
@@ -172,7 +174,7 @@ int pull_blocks_per_sm(int ns, int mode, int stages);
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
                         const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
-                        int grid_max, cudaStream_t st);
+                        int grid_max, cudaStream_t st, T* rec = nullptr);
 // One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st);
 // Fills the ghost columns and rows of a pull-layout buffer with the periodic images.

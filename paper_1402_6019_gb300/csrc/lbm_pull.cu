@@ -256,7 +256,7 @@ template <typename T, int NS, int MODE, int ST>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
-           const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz) {
+           const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz, T* __restrict__ rec) {
     // walls in z: never in the periodic build, else as the step constants say
     const bool WALL = (MODE & M_PERIODIC) ? false : C.zbc != 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -340,6 +340,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 gather_wall<T, NS, ST>(S, sl, tx + 4, tz + 3, lo, hi, f);
             else
                 gather<T, NS, ST>(S, sl, tx + 4, tz + 3, f);
+            if constexpr ((MODE & M_RECORD) != 0) {  // the input state, as plain values (one lattice)
+                const long long n = (long long)nx * nz, i = (long long)z * nx + x;
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+#pragma unroll
+                    for (int l = 0; l < 9; ++l) rec[(s * 9 + l) * n + i] = f[s][l] + wlb<T>(l) * C.rho_ref[s];
+            }
             if constexpr (kPair<T, NS>) {
                 f2 fp[9];
 #pragma unroll
@@ -678,7 +685,7 @@ int pull_occupancy() {
 
 template <typename T, int NS, int MODE, int ST>
 cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const ObsPtrs& O,
-                        const Fold& Rd, unsigned* sched, const Batch& B, int grid_max, cudaStream_t st) {
+                        const Fold& Rd, unsigned* sched, const Batch& B, int grid_max, cudaStream_t st, T* rec) {
     const int ntx = (C.nx + PX - 1) / PX;
     const long long ntiles = (long long)ntx * B.ntz;
     int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
@@ -698,15 +705,15 @@ cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const O
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST>, *static_cast<const CUtensorMap*>(tin), fout, C, K, O,
-                              Rd, sched, B.inst, B.ninst, ntx, B.ntz);
+                              Rd, sched, B.inst, B.ninst, ntx, B.ntz, rec);
 }
 
 template <typename T, int NS, int ST>
 cudaError_t launch_ns(int mode, const void* tin, T* fout, const StepConst<T>& C,
                       const ObsPtrs& O, const Fold& Rd, unsigned* sched, const Batch& B, int grid_max,
-                      cudaStream_t st) {
+                      cudaStream_t st, T* rec) {
 #define LBM_PULL_CASE(m) \
-    case m: return launch_mode<T, NS, m, ST>(tin, fout, C, O, Rd, sched, B, grid_max, st);
+    case m: return launch_mode<T, NS, m, ST>(tin, fout, C, O, Rd, sched, B, grid_max, st, rec);
     switch (mode) {
         LBM_PULL_CASE(M_WRITE)
         LBM_PULL_CASE(M_WRITE | M_OBS)
@@ -714,6 +721,7 @@ cudaError_t launch_ns(int mode, const void* tin, T* fout, const StepConst<T>& C,
         LBM_PULL_CASE(M_FIELDS)
         LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
         LBM_PULL_CASE(M_PERIODIC | M_OBS)
+        LBM_PULL_CASE(M_WRITE | M_RECORD)
         default: return cudaErrorInvalidValue;
     }
 #undef LBM_PULL_CASE
@@ -762,6 +770,7 @@ int blocks_per_sm_ns(int mode) {
         LBM_PULL_CASE(M_FIELDS)
         LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
         LBM_PULL_CASE(M_PERIODIC | M_OBS)
+        LBM_PULL_CASE(M_WRITE | M_RECORD)
         default: return 0;
     }
 #undef LBM_PULL_CASE
@@ -780,13 +789,13 @@ int pull_blocks_per_sm(int ns, int mode, int stages) {
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
                         const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
-                        int grid_max, cudaStream_t st) {
+                        int grid_max, cudaStream_t st, T* rec) {
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
     if (stages == 1)
-        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st)
-                       : launch_ns<T, 2, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st);
-    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st)
-                   : launch_ns<T, 2, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st);
+        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec)
+                       : launch_ns<T, 2, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec);
+    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec)
+                   : launch_ns<T, 2, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec);
 }
 
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
@@ -818,9 +827,9 @@ int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int
 template int pull_blocks_per_sm<float>(int, int, int);
 template int pull_blocks_per_sm<double>(int, int, int);
 template cudaError_t launch_pull<float>(int, int, int, const void*, float*, const StepConst<float>&,
-                                        const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
+                                        const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t, float*);
 template cudaError_t launch_pull<double>(int, int, int, const void*, double*, const StepConst<double>&,
-                                         const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t);
+                                         const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t, double*);
 template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, const Batch&, cudaStream_t);
 template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, const Batch&, cudaStream_t);
 
