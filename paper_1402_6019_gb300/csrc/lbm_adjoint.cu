@@ -10,14 +10,15 @@
 // Given lam_{n+1} = dJ/df_{n+1}, three kernels form lam_n = dJ/df_n and the derivatives with
 // respect to theta = (G1 A, G1 B, G2 A, G2 B, G_AB, tau A, tau B, g) by applying the transposed
 // derivative of each stage in reverse order:
-//   k_adj_moments  rho, j and psi of the state f_n (the linearisation point);
+//   k_adj_moments  rho, j and psi of the state f_n (the linearisation point) -- for the first
+//                  step of a sweep; for the others k_adj_final of the step before forms them;
 //   k_adj_local    the force at the site (from its neighbours' psi and rho), then streaming
 //                  transposed (a gather of lam_{n+1}), relaxation, equilibrium, shifted and
 //                  common velocity transposed: dJ/dF_s, the site's own share of dJ/drho_s and
 //                  dJ/dj_s, and every parameter derivative of the site;
 //   k_adj_final    the neighbour shares of the force transposed (each site gathers what the
 //                  forces at x - c owe to its psi and rho), the pseudopotential and the
-//                  moments: lam_n.
+//                  moments: lam_n; and the moments of f_{n-1} for the next step back.
 // T is the precision of the states and of lam (FP64, or FP32 for FP32 forward runs).  The
 // parameter derivatives are summed per block (FP64, or double-float pairs in FP32 mode), kept
 // per block across the steps of a call, then summed over the blocks in FP64 in a fixed order.
@@ -281,10 +282,12 @@ __global__ void __launch_bounds__(ST) k_adj_local(const T* __restrict__ f, const
     block_sum<T>(gp, part, accumulate);
 }
 
-// One thread per site and species (blockIdx.y = species).
+// One thread per site and species (blockIdx.y = species).  f_prev (may be null): the state of the
+// step before, whose moments this kernel also forms for the next adjoint step (it reads none of
+// the moment fields itself, so it may overwrite them).
 template <typename T, int NS>
 __global__ void __launch_bounds__(ST) k_adj_final(const T* __restrict__ lam_next, const AdjC<T> A, AdjBuf<T> B,
-                                                  T* __restrict__ lam) {
+                                                  T* __restrict__ lam, const T* __restrict__ f_prev) {
     const long long n = (long long)A.nx * A.nz;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -313,6 +316,20 @@ __global__ void __launch_bounds__(ST) k_adj_final(const T* __restrict__ lam_next
     for (int l = 0; l < 9; ++l) {
         lam[(s * 9 + l) * n + i] =
             keep * lam_next[(s * 9 + l) * n + N.at(cx(l), cz(l))] + d + djx * (T)cx(l) + djz * (T)cz(l);
+    }
+    if (f_prev) {
+        T r = 0, mx = 0, mz = 0;
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            const T v = f_prev[(s * 9 + l) * n + i];
+            r += v;
+            mx += v * (T)cx(l);
+            mz += v * (T)cz(l);
+        }
+        B.rho[s * n + i] = r;
+        B.jx[s * n + i] = mx;
+        B.jz[s * n + i] = mz;
+        B.psi[s * n + i] = psi_t(r, A.irho0[s], A.psi_form);
     }
 }
 
@@ -463,12 +480,15 @@ void enqueue_steps(const AdjC<T>& A, AdjBuf<T> B, typename Acc<T>::A* part, int 
         const T* f = states + (long long)k * stride;
         T* out = bufs[t & 1];
         cudaEvent_t* e = ev ? ev + 6 * t : nullptr;
+        // the moments of f: its own kernel for the first step, else formed by the previous step's
+        // final kernel
         if (e) cudaEventRecord(e[0], st);
-        k_adj_moments<T><<<dim3(nb, NS), ST, 0, st>>>(f, A, B);
+        if (t == 0) k_adj_moments<T><<<dim3(nb, NS), ST, 0, st>>>(f, A, B);
         if (e) cudaEventRecord(e[1], st), cudaEventRecord(e[2], st);
         k_adj_local<T, NS><<<nb, ST, 0, st>>>(f, next, A, B, part, t > 0);
         if (e) cudaEventRecord(e[3], st), cudaEventRecord(e[4], st);
-        k_adj_final<T, NS><<<dim3(nb, NS), ST, 0, st>>>(next, A, B, out);
+        const T* f_prev = k > 0 ? states + (long long)(k - 1) * stride : nullptr;
+        k_adj_final<T, NS><<<dim3(nb, NS), ST, 0, st>>>(next, A, B, out, f_prev);
         if (e) cudaEventRecord(e[5], st);
         next = out;
     }

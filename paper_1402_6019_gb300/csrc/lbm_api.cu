@@ -1303,7 +1303,7 @@ static int adjoint_steps(lbm_ctx* c, const AdjConst& A, int nsteps, const T* sta
                                c->adj_scratch, ev, c->stream));
     if (out != lam_user)
         CK(cudaMemcpyAsync(lam_user, out, state_values(c) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
-    c->launches += 3LL * nsteps + (nsteps > 0 ? 1 : 0);
+    c->launches += 2LL * nsteps + (nsteps > 0 ? 2 : 0);
     return LBM_OK;
 }
 
