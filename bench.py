@@ -36,6 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_SITE = {("fp32", 2): 144, ("fp64", 2): 288, ("fp32", 1): 72, ("fp64", 1): 144}
+# The FP64 step (two species, observables every step) is bound by the FP64 pipe: FP64 flops per
+# site-update counted by ncu (331 DFMA, 198 DADD, 101 DMUL; profiles/k_pull_emulsion_1024_fp64.md)
+# against 2 DFMA per SM per cycle x 152 SMs x 2 flops x 2.07 GHz
+FP64_FLOPS_PER_SITE = 961
+FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 L2_BYTES = 126 << 20          # L2 of a GB300 (nvidia-smi / device properties: 126.5 MiB)
 ROTATE_BYTES = 512 << 20      # working set of the rotated lattices, well above L2
@@ -554,7 +559,17 @@ def main():
     peak, peak_kind = _peaks()
     traffic = _traffic(kernel_source_hash(a.kernel), a.workload, a.precision,
                        a.kernel if a.tile_rows in (0, 8) else f"{a.kernel}{a.tile_rows}")
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+    if a.precision == "fp64" and ns == 2 and a.observe_every == 1 and a.kernel == "pull":
+        tf = FP64_FLOPS_PER_SITE * sites / (kern_avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                    "peak_source": "FP64 pipe: 2 DFMA per SM per cycle (ncu peak), 152 SMs, 2.07 GHz",
+                    "flops_per_site": FP64_FLOPS_PER_SITE, "hbm_frac": round(achieved / peak, 4),
+                    "kernel": "lbm::k_pull<double, 2, M_WRITE|M_OBS>", "kernel_ms": round(kern_avg_ms, 5),
+                    "kernel_ms_serialised": round(kern_ser_ms, 5)}
+    else:
+        roofline = None
+    roofline = roofline or {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                 "kernel": {"pull": "lbm::k_pull<T, 2, M_WRITE|M_OBS>" if a.observe_every else "lbm::k_pull<T, 2, M_WRITE>",
                            "fused": "lbm::k_tile<T, 2, M_WRITE|M_OBS>",
