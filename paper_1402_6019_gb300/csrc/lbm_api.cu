@@ -1029,8 +1029,9 @@ extern "C" int lbm_observables_enqueue(lbm_ctx* c, void* dst, int averages, int 
     if (!dst) return fail(c, LBM_EINVAL, "dst is NULL");
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
     CK(cudaSetDevice(c->d.device));
-    // the trailer is written on the device right after the buffer it describes, and the two leave
-    // in one device-to-host copy: a host-to-host copy would make the call wait for the stream
+    // the trailer: written by the CPU into host memory, or on the device right after the buffer it
+    // describes (then the two leave in one copy) -- a host-to-host cudaMemcpyAsync would make the
+    // call wait for the stream
     static_assert(sizeof(ObsTrailer) == 32, "trailer layout");
     if (averages < 0 || averages > 2) return fail(c, LBM_EINVAL, "averages must be 0, 1 or 2");
     double* src;
@@ -1050,10 +1051,21 @@ extern "C" int lbm_observables_enqueue(lbm_ctx* c, void* dst, int averages, int 
         src = c->out;
         samples = 1.0;
     }
-    CK(launch_obs_trailer(reinterpret_cast<double*>(reinterpret_cast<char*>(src) + obs_bytes(c)), samples, c->step,
-                          averages ? 1 : 0, c->stream));
-    c->launches += 1;
-    CK(cudaMemcpyAsync(dst, src, obs_bytes(c) + sizeof(ObsTrailer), cudaMemcpyDefault, c->stream));
+    cudaPointerAttributes pa{};
+    const bool host_dst = cudaPointerGetAttributes(&pa, dst) == cudaSuccess &&
+                          (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered);
+    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    if (host_dst) {
+        // the trailer goes straight into host memory: the copy in flight writes other bytes
+        ObsTrailer t{samples, c->step, averages ? 1 : 0, 0};
+        memcpy(static_cast<char*>(dst) + obs_bytes(c), &t, sizeof t);
+        CK(cudaMemcpyAsync(dst, src, obs_bytes(c), cudaMemcpyDefault, c->stream));
+    } else {
+        CK(launch_obs_trailer(reinterpret_cast<double*>(reinterpret_cast<char*>(src) + obs_bytes(c)), samples,
+                              c->step, averages ? 1 : 0, c->stream));
+        c->launches += 1;
+        CK(cudaMemcpyAsync(dst, src, obs_bytes(c) + sizeof(ObsTrailer), cudaMemcpyDefault, c->stream));
+    }
     if (averages && reset) {
         CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
         c->samples = averages == 2 && held ? 1 : 0;
