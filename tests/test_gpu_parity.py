@@ -186,6 +186,46 @@ def test_fp32_full_size_1024_against_oracle(oracle):
     assert np.abs(o["momentum"]).max() < 1e-6 * m0.sum()
 
 
+@pytest.mark.parametrize("name", ["channel_couette", "channel_poiseuille"])
+def test_fp32_full_size_channels_against_oracle(oracle, name):
+    """The 2048 x 256 walled channel workloads (Couette and Poiseuille drives, FP32, observables
+    every step as bench.py steps them): every site against the oracle after 10 steps."""
+    w = W.workload(name)
+    ref = oracle.RefLattice(w["nx"], w["nz"], 2, w["z_boundary"], **w["params"])
+    ref.set_fields(w["rho"])
+    ref.step(10)
+    lat = L.Lattice(w["nx"], w["nz"], 2, L.LBM_FP32, w["z_boundary"], **w["params"])
+    lat.set_fields(w["rho"])
+    lat.set_observe(1)
+    lat.step(10)
+    check_fields(ref, lat, TOL32, pops=False)
+
+
+def test_fp32_full_size_sweep_against_oracle(oracle):
+    """The 48-channel sweep at full size (13.4 M sites, one launch per step, observables every
+    step): after 5 steps, three channels -- H = 32, 256 and 512 under body forces 1e-6, 1e-5 and
+    3e-6 -- equal the oracle run on each alone."""
+    w = W.workload("channel_sweep_48")
+    hs = w["instances"]
+    lat = L.Lattice(w["nx"], None, 2, L.LBM_FP32, L.LBM_BOUNCEBACK, instances=hs, **w["params"])
+    for i, d in enumerate(w["drives"]):
+        lat.set_instance_drive(i, d["body_force"], d["wall_u"])
+    lat.set_fields(w["rho"])
+    lat.set_observe(1)
+    lat.step(5)
+    g_rho, g_u, _ = lat.fields(populations=False)
+    z0 = np.concatenate([[0], np.cumsum(hs)])
+    for i in (0, 23, 46):
+        rho_i = w["rho"][:, z0[i]:z0[i + 1]]
+        ref = oracle.RefLattice(w["nx"], hs[i], 2, 1, **dict(w["params"], **w["drives"][i]))
+        ref.set_fields(rho_i)
+        ref.step(5)
+        r_rho, r_u, _ = ref.fields()
+        assert rel(g_rho[:, z0[i]:z0[i + 1]], r_rho) <= TOL32, i
+        err_u = float(np.abs(g_u[:, z0[i]:z0[i + 1]] - r_u).max())
+        assert err_u <= TOL32 * float(np.abs(r_u).max()) + 100 * 2.2e-16 * pop_scale(ref), i
+
+
 def test_fp32_faster_path_is_fp32():
     lat = L.Lattice(64, 64, 2, L.LBM_FP32, 0, **W.EMULSION_PARAMS)
     rho, _ = W.disk_packing(64, 64, 0.5, seed=4, r_mean=6, r_spread=1)
