@@ -41,7 +41,8 @@ struct lbm_ctx {
     int nxpart = 0, nzpart = 0;     // partial-sum groups of the kernel in use
     void* part_row[2] = {nullptr, nullptr};  // partial sums in the populations' precision, one
     void* part_col[2] = {nullptr, nullptr};  // set per population buffer parity
-    unsigned* sched = nullptr;  // pull: tile and reduction work-item counters (zero between launches)
+    unsigned* sched = nullptr;  // pull: two pairs of work-item counters, used by alternate launches
+    int sched_set = 0;          // the pair the next pull launch uses (the other is zeroed by it)
     // pull: the last observing step's partial sums (in part_*[pending_buf]) still to be reduced;
     // the next pull launch folds the reduction in, a host read flushes it with k_reduce
     bool pending = false;
@@ -81,8 +82,8 @@ struct lbm_ctx {
     long long step = 0;
     long long launches = 0;
     // [parity][observe][first launch folds no pending reduction (0), one without (1) / with (2)
-    // accumulation into the time sums]
-    cudaGraphExec_t graph[2][2][3] = {};
+    // accumulation into the time sums][counter of the first launch]
+    cudaGraphExec_t graph[2][2][3][2] = {};
     int graph_steps = 16;
     bool profiling = false;
     std::vector<cudaEvent_t> ev;  // pairs around step-kernel launches
@@ -141,11 +142,12 @@ static void refresh_const(lbm_ctx* c) {
 static void drop_graphs(lbm_ctx* c) {
     for (auto& pr : c->graph)
         for (auto& po : pr)
-            for (auto& g : po)
-                if (g) {
-                    cudaGraphExecDestroy(g);
-                    g = nullptr;
-                }
+            for (auto& pf : po)
+                for (auto& g : pf)
+                    if (g) {
+                        cudaGraphExecDestroy(g);
+                        g = nullptr;
+                    }
 }
 
 static size_t obs_bytes(const lbm_ctx* c) {
@@ -561,10 +563,13 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         const int stg = c->stages[(mode & M_OBS) ? 1 : 0];
         if (c->d.precision == LBM_FP64)
             e = launch_pull<double>(c->d.n_species, pm, stg, tin, (double*)c->f[cur ^ 1], c->c64, O,
-                                    Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream, (double*)c->rec);
+                                    Rd, c->sched, c->sched_set, B, c->pull_grid[pm][stg - 1], c->stream,
+                                    (double*)c->rec);
         else
             e = launch_pull<float>(c->d.n_species, pm, stg, tin, (float*)c->f[cur ^ 1], c->c32, O,
-                                   Rd, c->sched, B, c->pull_grid[pm][stg - 1], c->stream, (float*)c->rec);
+                                   Rd, c->sched, c->sched_set, B, c->pull_grid[pm][stg - 1], c->stream,
+                                   (float*)c->rec);
+        if (e == cudaSuccess) c->sched_set ^= 1;
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
         if (c->d.precision == LBM_FP64)
@@ -616,13 +621,13 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
         if (graphable && left >= G) {
             const int ob = c->observe_every == 1 ? 1 : 0;
             const int ff = c->pull && c->pending ? (c->pending_acc ? 2 : 1) : 0;
-            cudaGraphExec_t& ge = c->graph[c->cur][ob][ff];
+            cudaGraphExec_t& ge = c->graph[c->cur][ob][ff][c->sched_set];
             if (!ge) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 const long long saved = c->launches, saved_samples = c->samples;
                 const bool saved_pending = c->pending, saved_acc = c->pending_acc;
-                const int saved_buf = c->pending_buf;
+                const int saved_buf = c->pending_buf, saved_set = c->sched_set;
                 cudaError_t e = cudaSuccess;
                 for (int i = 0; i < G && e == cudaSuccess; ++i)
                     e = enqueue_pass(c, (c->cur + i) & 1, M_WRITE | (ob ? M_OBS : 0), ob, ob, true);
@@ -632,6 +637,7 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps) {
                 c->pending = saved_pending;
                 c->pending_acc = saved_acc;
                 c->pending_buf = saved_buf;
+                c->sched_set = saved_set;  // G is even: a replay leaves the counter of the next launch as it was
                 CK(e);
                 CK(e2);
                 e = cudaGraphInstantiate(&ge, g, 0);

@@ -168,13 +168,15 @@ int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int
 template <typename T>
 int pull_blocks_per_sm(int ns, int mode, int stages);
 // One pass of the pull kernel: loads through tin (a buffer's in_map) and stores the new values
-// into fout, the other buffer (their periodic images too).  fold: a pending reduction run by the same launch.  sched: three counters (tiles,
-// CTAs done, reduction items), zero before the launch and left zero by it.  grid_max: resident
-// CTAs on the device.
+// into fout, the other buffer (their periodic images too).  fold: a pending reduction run by the same launch.  sched: two
+// pairs of work-item counters (tiles, reduction items); consecutive launches of a context
+// alternate set = 0, 1, 0, ...: a launch uses pair `set`, which must be zero when it starts, and
+// zeroes the other pair for the next.
+// grid_max: resident CTAs on the device.
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
-                        const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
-                        int grid_max, cudaStream_t st, T* rec = nullptr);
+                        const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, int set,
+                        const Batch& B, int grid_max, cudaStream_t st, T* rec = nullptr);
 // One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st);
 // Fills the ghost columns and rows of a pull-layout buffer with the periodic images.

@@ -22,11 +22,16 @@
 // the column sums are double-buffered by iteration parity, so a warp can start the next tile
 // while others still read this one's.  Every wait on a load is bounded.
 //
-// Tiles are handed out in row-major order by an atomic counter (the CTA that finishes last
-// resets it), so the CTAs at work at any moment cover a band of rows and read each other's halo
-// while it is in L2.  A launch can also carry the reduction of the previous pass's observable
-// partial sums (Fold): CTAs that run out of tiles draw the reduction's work items from a second
-// counter, so they fill the spread of the CTAs' last tiles.
+// Tiles are numbered in row-major order.  CTA b owns tiles b + i * grid for its first ST tiles
+// (known before the previous kernel has finished, so its first load is issued as soon as that
+// kernel's writes are visible); the rest are drawn from an atomic counter, one draw ahead, so the
+// CTAs at work at any moment cover a band of rows and read each other's halo while it is in L2.
+// A launch can also carry the reduction of the previous pass's observable partial sums (Fold):
+// CTAs that have finished their tiles draw its work items from a second counter, so they fill the
+// spread of the CTAs' last tiles; a CTA that looked at that counter during its last tile and saw
+// no items left exits without drawing.  Launches alternate between two pairs of counters: each
+// launch zeroes the pair the next launch will use, so no CTA has to find out that it is the last
+// one out.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -255,21 +260,21 @@ __device__ __noinline__ void write_images(const StepConst<T>& C, T* __restrict__
 template <typename T, int NS, int MODE, int ST>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, T* __restrict__ fout,
-           const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ sched,
-           const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz, T* __restrict__ rec) {
+           const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ ctr,
+           unsigned* __restrict__ ctr_next, const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz,
+           T* __restrict__ rec) {
     // walls in z: never in the periodic build, else as the step constants say
     const bool WALL = (MODE & M_PERIODIC) ? false : C.zbc != 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PullSmem<T, NS, ST>& S = *reinterpret_cast<PullSmem<T, NS, ST>*>(smem_raw);
     const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
-    // Programmatic dependent launch: the next step's CTAs may be scheduled as soon as this grid's
-    // CTAs start retiring; every thread of a grid waits for the previous grid's completion (and
-    // the visibility of its writes) before its first access to global memory.
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    // nz: rows of all lattices; ntz: their tile rows; tiles are numbered lattice by lattice
     const int nx = C.nx, nz = C.nz;
-    const int ntiles = ntx * ntz;
+    const int ntiles = ntx * ntz;  // nz: rows of all lattices; ntz: their tile rows
+    // tiles 0 .. nstat - 1 are owned by CTA (tile mod grid), the rest come from ctr[0]
+    const int nstat = min(ST * (int)gridDim.x, ntiles);
+    // work items of the folded reduction: blocks of rows, then blocks of columns
+    const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+    const int nfold = Rd.enabled ? nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32) : 0;
 
     // ring position of this thread (psi/rho tile coordinates), NRING / PZ = 22 per warp so that
     // every warp has the same phase-A work: in ring order the top two rows, the bottom two rows,
@@ -291,26 +296,48 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             rpx = c < 2 ? c : HW - 4 + c;
         }
     }
-    // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden; ntiles:
-    // nothing more to draw
+    // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden;
+    // ntiles: nothing more to draw
     int upcoming = ntiles;
-
+    // the CTA's own first tiles, described before the previous kernel has finished: the lattice
+    // table is written by host copies only, never by a kernel
     if (tid == 0) {
         for (int sl = 0; sl < ST; ++sl)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&S.bar[sl])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        // the first ST tiles go into the boxes at once (padded (x0, z0) is the box origin)
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tin) : "memory");
+        for (int sl = 0; sl < ST; ++sl) {
+            const int t = (int)blockIdx.x + sl * (int)gridDim.x;
+            if (t < nstat) describe<T>(S.ti[sl], t, ntiles, inst, ninst, ntx);
+        }
+    }
+    // Programmatic dependent launch: the next step's CTAs may be scheduled as soon as this grid's
+    // CTAs start retiring; every thread of a grid waits for the previous grid's completion (and
+    // the visibility of its writes) before its first access to the populations, the observable
+    // buffers or the counters.
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (tid == 0) {
+        if (blockIdx.x == 0) {  // the next launch's counters (this launch's were zeroed by the last)
+            ctr_next[0] = 0u;
+            ctr_next[1] = 0u;
+        }
+        // the first box goes out at once, the others once it has arrived (iteration 0), so that
+        // the first boxes of all CTAs do not queue behind the second ones
         bool more = true;
         for (int sl = 0; sl < ST; ++sl) {
-            int t0 = more ? (int)atomicAdd(&sched[0], 1u) : ntiles;
-            if (t0 > ntiles) t0 = ntiles;
-            describe<T>(S.ti[sl], t0, ntiles, inst, ninst, ntx);
-            more = t0 < ntiles;
-            if (more) issue_load(S, &tin, S.ti[sl].x0, S.ti[sl].prow0 + S.ti[sl].z0, sl);
+            if (!more) break;  // the slots after the CTA's first non-tile item stay unused
+            const int t = (int)blockIdx.x + sl * (int)gridDim.x;
+            if (t >= nstat)
+                describe<T>(S.ti[sl], min(nstat + (int)atomicAdd(ctr, 1u), ntiles), ntiles, inst, ninst, ntx);
+            more = S.ti[sl].t < ntiles;
+            if (more && sl == 0) issue_load(S, &tin, S.ti[0].x0, S.ti[0].prow0 + S.ti[0].z0, 0);
         }
-        if (more) upcoming = (int)atomicAdd(&sched[0], 1u);
+        if (more) upcoming = min(nstat + (int)atomicAdd(ctr, 1u), ntiles);
     }
     __syncthreads();
+    // thread 0: the reduction's counter as last seen (no draw), during the CTA's last tiles
+    int fold_seen = 0;
     unsigned parity = 0;  // bit sl: phase of box sl's barrier
     bool failed = false;
     // the previous tile's column-sum slot (observables): its column x and tile row, or x = -1
@@ -330,6 +357,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         const bool live = x < nx && z < lnz;
         const bool ok = wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
         if (ok) parity ^= 1u << sl;  // on expiry the exit path waits on the same phase again
+        if (ST > 1 && k == 0 && tid == 0)  // the first box is in: the CTA's other first tiles
+            for (int i = 1; i < ST; ++i) {
+                if (S.ti[i].t >= ntiles) break;
+                issue_load(S, &tin, S.ti[i].x0, S.ti[i].prow0 + S.ti[i].z0, i);
+            }
 
         // ---- phase A: this site's populations, rho and psi of the tile and its ring ----
         T f[NS][9];
@@ -377,15 +409,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             break;
         }
         // box sl is free: start the load of the tile ST ahead (published at the top of this
-        // iteration) and draw the one after it
+        // iteration) and draw the one after it; past the last tile, look at the reduction's
+        // counter instead (its value is only used after the loop)
         if (tid == 0) {
-            const int tn = upcoming;
-            if (tn < ntiles) {
+            if (upcoming < ntiles) {
                 const TileInfo<T>& N = S.ti[(k + ST) % NTQ];
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 issue_load(S, &tin, N.x0, N.prow0 + N.z0, sl);
-                upcoming = (int)atomicAdd(&sched[0], 1u);
-                if (upcoming > ntiles) upcoming = ntiles;
+                upcoming = min(nstat + (int)atomicAdd(ctr, 1u), ntiles);
+            } else if (nfold > 0) {
+                fold_seen = (int)*reinterpret_cast<volatile unsigned*>(ctr + 1);
             }
         }
         if (MODE & M_OBS) {
@@ -636,38 +669,25 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             static_cast<T*>(O.part_col)[((long long)prev_x * ntz + prev_jg) * NQC + tz] = v;
         }
     }
-    if (Rd.enabled) {
-        // the previous pass's reduction: its work items go to the CTAs as they run out of tiles
-        // (the spread of the CTAs' last tiles is idle time otherwise), drawn from a counter
-        const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
-        const int nb = nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
+    if (nfold > 0 && !failed) {
+        // the previous pass's reduction: work items from the second counter until they run out
         for (;;) {
-            if (tid == 0) S.fold_item = (int)atomicAdd(&sched[2], 1u);
+            if (tid == 0) S.fold_item = fold_seen < nfold ? (int)atomicAdd(ctr + 1, 1u) : nfold;
             __syncthreads();
             const int b = S.fold_item;
-            if (b >= nb) break;  // uniform: every thread read the same item
+            if (b >= nfold) break;  // uniform: every thread read the same item
             reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
                             Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc,
                             ninst > 1 ? inst : nullptr, ninst);  // ends with a CTA barrier
         }
     }
-    if (tid == 0) {
-        if (failed) {
-            atomicOr(O.flag, 2);
-            // the loads still in flight -- those of iterations k .. k + ST - 1 (the one that did
-            // not arrive in time and the ones after it) -- before the CTA exits
-            for (int i = 0; i < ST; ++i) {
-                const int sl = (k + i) % ST;
-                if (S.ti[(k + i) % NTQ].t < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
-            }
-        }
-        // the last CTA out resets the scheduler for the next launch (every CTA's draws on
-        // sched[0] come before its fence and its increment of sched[1])
-        __threadfence();
-        if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
-            atomicExch(&sched[0], 0u);
-            atomicExch(&sched[2], 0u);
-            atomicExch(&sched[1], 0u);
+    if (failed && tid == 0) {
+        atomicOr(O.flag, 2);
+        // the loads still in flight -- those of iterations k .. k + ST - 1 (the one that did not
+        // arrive in time and the ones after it) -- before the CTA exits
+        for (int i = 0; i < ST; ++i) {
+            const int sl = (k + i) % ST;
+            if (S.ti[(k + i) % NTQ].t < ntiles) wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
         }
     }
 }
@@ -685,7 +705,8 @@ int pull_occupancy() {
 
 template <typename T, int NS, int MODE, int ST>
 cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const ObsPtrs& O,
-                        const Fold& Rd, unsigned* sched, const Batch& B, int grid_max, cudaStream_t st, T* rec) {
+                        const Fold& Rd, unsigned* sched, int set, const Batch& B, int grid_max, cudaStream_t st,
+                        T* rec) {
     const int ntx = (C.nx + PX - 1) / PX;
     const long long ntiles = (long long)ntx * B.ntz;
     int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
@@ -705,15 +726,15 @@ cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const O
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST>, *static_cast<const CUtensorMap*>(tin), fout, C, K, O,
-                              Rd, sched, B.inst, B.ninst, ntx, B.ntz, rec);
+                              Rd, sched + 2 * set, sched + 2 * (set ^ 1), B.inst, B.ninst, ntx, B.ntz, rec);
 }
 
 template <typename T, int NS, int ST>
 cudaError_t launch_ns(int mode, const void* tin, T* fout, const StepConst<T>& C,
-                      const ObsPtrs& O, const Fold& Rd, unsigned* sched, const Batch& B, int grid_max,
+                      const ObsPtrs& O, const Fold& Rd, unsigned* sched, int set, const Batch& B, int grid_max,
                       cudaStream_t st, T* rec) {
 #define LBM_PULL_CASE(m) \
-    case m: return launch_mode<T, NS, m, ST>(tin, fout, C, O, Rd, sched, B, grid_max, st, rec);
+    case m: return launch_mode<T, NS, m, ST>(tin, fout, C, O, Rd, sched, set, B, grid_max, st, rec);
     switch (mode) {
         LBM_PULL_CASE(M_WRITE)
         LBM_PULL_CASE(M_WRITE | M_OBS)
@@ -788,14 +809,15 @@ int pull_blocks_per_sm(int ns, int mode, int stages) {
 
 template <typename T>
 cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
-                        const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, const Batch& B,
-                        int grid_max, cudaStream_t st, T* rec) {
+                        const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, int set,
+                        const Batch& B, int grid_max, cudaStream_t st, T* rec) {
+    if (set & ~1) return cudaErrorInvalidValue;
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
     if (stages == 1)
-        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec)
-                       : launch_ns<T, 2, 1>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec);
-    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec)
-                   : launch_ns<T, 2, 2>(mode, tin, fout, C, O, fold, sched, B, grid_max, st, rec);
+        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
+                       : launch_ns<T, 2, 1>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
+    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
+                   : launch_ns<T, 2, 2>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
 }
 
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
@@ -827,9 +849,11 @@ int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int
 template int pull_blocks_per_sm<float>(int, int, int);
 template int pull_blocks_per_sm<double>(int, int, int);
 template cudaError_t launch_pull<float>(int, int, int, const void*, float*, const StepConst<float>&,
-                                        const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t, float*);
+                                        const ObsPtrs&, const Fold&, unsigned*, int, const Batch&, int, cudaStream_t,
+                                        float*);
 template cudaError_t launch_pull<double>(int, int, int, const void*, double*, const StepConst<double>&,
-                                         const ObsPtrs&, const Fold&, unsigned*, const Batch&, int, cudaStream_t, double*);
+                                         const ObsPtrs&, const Fold&, unsigned*, int, const Batch&, int, cudaStream_t,
+                                         double*);
 template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, const Batch&, cudaStream_t);
 template cudaError_t launch_pull_images<double>(int, double*, const StepConst<double>&, const Batch&, cudaStream_t);
 
