@@ -99,13 +99,18 @@ struct PullSmem {
     int fold_item;  // the reduction work item thread 0 drew for the CTA
 };
 
+// Tile t of the work order; rot > 0 (one periodic lattice): the order starts rot tiles in, at
+// the last tile row, so the two rows whose sites also write the periodic row images come first
+// and the last tiles of a launch are plain ones.
 template <typename T>
 __device__ __forceinline__ void describe(TileInfo<T>& D, int t, int ntiles, const InstGeom* __restrict__ inst,
-                                         int ninst, int ntx) {
+                                         int ninst, int ntx, int rot) {
     D.t = t;
     if (t >= ntiles) return;
     const InstGeom& I = inst[ninst > 1 ? inst_of_tile(inst, ninst, t) : 0];
-    const int tl = t - I.tile0, j = tl / ntx;
+    int tl = t - I.tile0;
+    if (rot > 0) tl = tl < ntiles - rot ? tl + rot : tl - (ntiles - rot);
+    const int j = tl / ntx;
     D.x0 = (tl - j * ntx) * PX;
     D.z0 = j * PZ;
     D.jg = I.tile0 / ntx + j;
@@ -272,6 +277,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     const int ntiles = ntx * ntz;  // nz: rows of all lattices; ntz: their tile rows
     // tiles 0 .. nstat - 1 are owned by CTA (tile mod grid), the rest come from ctr[0]
     const int nstat = min(ST * (int)gridDim.x, ntiles);
+    const int rot = !WALL && ninst == 1 && ntz > 2 ? ntiles - ntx : 0;  // work order (describe)
     // work items of the folded reduction: blocks of rows, then blocks of columns
     const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int nfold = Rd.enabled ? nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32) : 0;
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tin) : "memory");
         for (int sl = 0; sl < ST; ++sl) {
             const int t = (int)blockIdx.x + sl * (int)gridDim.x;
-            if (t < nstat) describe<T>(S.ti[sl], t, ntiles, inst, ninst, ntx);
+            if (t < nstat) describe<T>(S.ti[sl], t, ntiles, inst, ninst, ntx, rot);
         }
     }
     // Programmatic dependent launch: the next step's CTAs may be scheduled as soon as this grid's
@@ -329,7 +335,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             if (!more) break;  // the slots after the CTA's first non-tile item stay unused
             const int t = (int)blockIdx.x + sl * (int)gridDim.x;
             if (t >= nstat)
-                describe<T>(S.ti[sl], min(nstat + (int)atomicAdd(ctr, 1u), ntiles), ntiles, inst, ninst, ntx);
+                describe<T>(S.ti[sl], min(nstat + (int)atomicAdd(ctr, 1u), ntiles), ntiles, inst, ninst, ntx,
+                            rot);
             more = S.ti[sl].t < ntiles;
             if (more && sl == 0) issue_load(S, &tin, S.ti[0].x0, S.ti[0].prow0 + S.ti[0].z0, 0);
         }
@@ -348,7 +355,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         const TileInfo<T> D = S.ti[k % NTQ];
         if (D.t >= ntiles) break;
         if (tid == 0)  // publish the tile of iteration k + ST, one barrier ahead of its readers
-            describe<T>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx);
+            describe<T>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot);
         // this tile: first column and row (rows of its lattice), tile row among all lattices; its
         // lattice: rows, first compact row, first padded row
         const int lnz = D.lnz, zrow0 = D.zrow0, prow0 = D.prow0, x0 = D.x0, z0 = D.z0, jg = D.jg;
