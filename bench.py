@@ -158,7 +158,7 @@ KERNEL_SOURCE = {"pull": "lbm_pull.cu", "fused": "lbm_tile.cu", "twopass": "lbm_
 
 def kernel_source_hash(kernel):
     h = hashlib.sha1()
-    for f in (KERNEL_SOURCE[kernel], "lbm_core.cuh"):
+    for f in (KERNEL_SOURCE[kernel], "lbm_core.cuh", "lbm_pair.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1402_6019_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -253,8 +253,8 @@ int lbm_instance_observables(lbm_ctx *c, int i, lbm_obs *out, int averages);
    context's own lattices -- depth 1 (one tile load in flight per CTA, 3 CTAs per SM in FP32) and
    depth 2 (two, 2 CTAs per SM) -- for `steps` steps each (1..10000), with observables every step
    if sampling is on and without otherwise, keeps the faster for that kind of pass (a context
-   holds one shape for passes with observables and one for passes without; FP32 defaults: depth 2
-   and depth 1, FP64: depth 2), and puts the state, time sums and step count back, so the
+   holds one shape for passes with observables and one for passes without; FP32 default: depth 1
+   for both, FP64: depth 2), and puts the state, time sums and step count back, so the
    simulation does not advance.  chosen (may be NULL) receives the depth kept (0 for the other
    kernels, which have nothing to choose), ms_per_step[2] (may be NULL) the measured step times.
    Synchronises. */

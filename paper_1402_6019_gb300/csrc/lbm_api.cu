@@ -63,8 +63,8 @@ struct lbm_ctx {
     int pull_grid[32][2] = {};                        // pull: resident CTAs per mode and depth
     void* rec = nullptr;                              // pull, M_RECORD pass: where the input state goes
     // pull: boxes in flight per CTA (1 or 2) for passes without [0] and with [1] observables; FP32
-    // defaults from measurements on GB300 (depth 1 runs 3 CTAs per SM within 80 registers, which
-    // the observing build exceeds), FP64 depth 2
+    // defaults from measurements on GB300: FP32 depth 1 (3 CTAs per SM within 80 registers) with
+    // and without observables; FP64 depth 2
     int stages[2] = {2, 2};
     // the lattices of a batch (one entry for a single lattice): host and device copies
     std::vector<InstGeom> inst;
@@ -312,7 +312,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     }
     const int nx = d->nx, nz = d->nz, ns = d->n_species;
     c->esize = d->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
-    if (d->precision == LBM_FP32) c->stages[0] = 1;
+    if (d->precision == LBM_FP32) c->stages[0] = c->stages[1] = 1;
     c->kernel = d->kernel == LBM_KERNEL_AUTO ? LBM_KERNEL_PULL : d->kernel;
     c->pull = c->kernel == LBM_KERNEL_PULL;
     {  // the lattices: rows stacked in order, each with its own ghost rows in the planes

@@ -22,7 +22,8 @@ __device__ __forceinline__ f2 swap2(f2 a) { return make_float2(a.y, a.x); }
 
 // Constant tables of the step as (A, B) pairs, built on the host from StepConst<float>.
 struct PairConst {
-    f2 kx[25], kz[25];  // K_s(|c|^2) c of Eq. FORCE, index (dz + 2) * 5 + dx + 2
+    f2 kf[5];           // Eq. FORCE by shell: K_s(1), K_s(2), 2 K_s(4), K_s(5), 2 K_s(8)
+    f2 kc[2];           // cross force by shell, both halves alike: G_AB w8(1), G_AB w8(2)
     f2 sq[9];           // App. A shell prefactors by |c|^2
     f2 omega, tau, rho_ref, nexp;  // nexp = -log2(e) / rho0 (psi = 1 - 2^(nexp rho))
     f2 kin;             // (tau - 1/2)^2
@@ -32,10 +33,12 @@ struct PairConst {
 
 // The pairs from the per-species tables (host).
 inline void fill_pair_const(PairConst& K, const StepConst<float>& C) {
-    for (int i = 0; i < 25; ++i) {
-        K.kx[i] = make_float2(C.kx[0][i], C.kx[1][i]);
-        K.kz[i] = make_float2(C.kz[0][i], C.kz[1][i]);
-    }
+    // K_s(q) c_x of the links (1,0), (1,1), (2,0), (1,2), (2,2): exactly K_s(q) or 2 K_s(q)
+    const int at[5] = {2 * 5 + 3, 3 * 5 + 3, 2 * 5 + 4, 4 * 5 + 3, 4 * 5 + 4};
+    for (int k = 0; k < 5; ++k) K.kf[k] = make_float2(C.kx[0][at[k]], C.kx[1][at[k]]);
+    // G_AB w8(q) c_x of the links (1,0), (1,1)
+    K.kc[0] = make_float2(C.kcx[1 * 3 + 2], C.kcx[1 * 3 + 2]);
+    K.kc[1] = make_float2(C.kcx[2 * 3 + 2], C.kcx[2 * 3 + 2]);
     for (int q = 0; q < 9; ++q) K.sq[q] = make_float2(C.sq[0][q], C.sq[1][q]);
     K.omega = make_float2(C.omega[0], C.omega[1]);
     K.tau = make_float2(C.tau[0], C.tau[1]);
@@ -55,26 +58,33 @@ __device__ __forceinline__ f2 psi2(const StepConst<float>& C, const PairConst& K
     return p2(1.0f - exp2f(a.x), 1.0f - exp2f(a.y));
 }
 
-// Eq. FORCE for both species: F = -psi(x) sum_l K(|c_l|^2) psi(x + c_l) c_l.
+// Eq. FORCE for both species: F = -psi(x) sum_l K(|c_l|^2) psi(x + c_l) c_l.  The 24 links come
+// in antipodal pairs with opposite c, so the sum runs over the differences psi(c) - psi(-c) of
+// one link of each pair, gathered shell by shell (one coefficient per shell).
 __device__ __forceinline__ void intra_force2(const PairConst& K, const f2 (&p)[5][5], f2& fx, f2& fz) {
-    f2 ax[5], az[5];
-#pragma unroll
-    for (int dz = -2; dz <= 2; ++dz) {
-        ax[dz + 2] = sp(0.f);
-        az[dz + 2] = sp(0.f);
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-            if (dx == 0 && dz == 0) continue;
-            const int i = (dz + 2) * 5 + dx + 2;
-            if (dx != 0) ax[dz + 2] = fma2(K.kx[i], p[dz + 2][dx + 2], ax[dz + 2]);
-            if (dz != 0) az[dz + 2] = fma2(K.kz[i], p[dz + 2][dx + 2], az[dz + 2]);
-        }
-    }
-    const f2 sx = add2(add2(add2(ax[0], ax[4]), add2(ax[1], ax[3])), ax[2]);
-    const f2 sz = add2(add2(az[0], az[4]), add2(az[1], az[3]));
-    const f2 m = p2(-p[2][2].x, -p[2][2].y);
+#define LBM_Q(dx, dz) p[(dz) + 2][(dx) + 2]
+    const f2 d10 = sub2(LBM_Q(1, 0), LBM_Q(-1, 0)), d01 = sub2(LBM_Q(0, 1), LBM_Q(0, -1));
+    const f2 d11 = sub2(LBM_Q(1, 1), LBM_Q(-1, -1)), e11 = sub2(LBM_Q(-1, 1), LBM_Q(1, -1));
+    const f2 d20 = sub2(LBM_Q(2, 0), LBM_Q(-2, 0)), d02 = sub2(LBM_Q(0, 2), LBM_Q(0, -2));
+    const f2 d21 = sub2(LBM_Q(2, 1), LBM_Q(-2, -1)), e21 = sub2(LBM_Q(-2, 1), LBM_Q(2, -1));
+    const f2 d12 = sub2(LBM_Q(1, 2), LBM_Q(-1, -2)), e12 = sub2(LBM_Q(-1, 2), LBM_Q(1, -2));
+    const f2 d22 = sub2(LBM_Q(2, 2), LBM_Q(-2, -2)), e22 = sub2(LBM_Q(-2, 2), LBM_Q(2, -2));
+    // shell |c|^2 = 5: the links (2,1), (1,2), (-1,2), (-2,1)
+    const f2 x5 = fma2(sp(2.f), sub2(d21, e21), sub2(d12, e12));
+    const f2 z5 = fma2(sp(2.f), add2(d12, e12), add2(d21, e21));
+    f2 sx = mul2(K.kf[0], d10), sz = mul2(K.kf[0], d01);
+    sx = fma2(K.kf[1], sub2(d11, e11), sx);
+    sz = fma2(K.kf[1], add2(d11, e11), sz);
+    sx = fma2(K.kf[2], d20, sx);
+    sz = fma2(K.kf[2], d02, sz);
+    sx = fma2(K.kf[3], x5, sx);
+    sz = fma2(K.kf[3], z5, sz);
+    sx = fma2(K.kf[4], sub2(d22, e22), sx);
+    sz = fma2(K.kf[4], add2(d22, e22), sz);
+    const f2 m = p2(-LBM_Q(0, 0).x, -LBM_Q(0, 0).y);
     fx = mul2(m, sx);
     fz = mul2(m, sz);
+#undef LBM_Q
 }
 
 // Appendix A stresses of both species, returned as (A, B) pairs of (sxx, szz, sxz).
@@ -115,17 +125,12 @@ __device__ __forceinline__ void intra_stress2(const PairConst& K, const f2 (&p)[
 
 // Sec. IV cross repulsion for both species (first belt, rho as the cross pseudopotential):
 // F_A += -G_AB rho_A(x) sum_l w8 rho_B(x + c_l) c_l, and A <-> B.  r[dz+1][dx+1] = (rho_A, rho_B).
-__device__ __forceinline__ void cross_force2(const StepConst<float>& C, const f2 (&r)[3][3], f2& fx, f2& fz) {
-    f2 sx = sp(0.f), sz = sp(0.f);
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dz == 0) continue;
-            const int i = (dz + 1) * 3 + dx + 1;
-            if (dx != 0) sx = fma2(sp(C.kcx[i]), r[dz + 1][dx + 1], sx);
-            if (dz != 0) sz = fma2(sp(C.kcz[i]), r[dz + 1][dx + 1], sz);
-        }
+// As in intra_force2, over the differences of antipodal links, shell by shell.
+__device__ __forceinline__ void cross_force2(const PairConst& K, const f2 (&r)[3][3], f2& fx, f2& fz) {
+    const f2 d10 = sub2(r[1][2], r[1][0]), d01 = sub2(r[2][1], r[0][1]);
+    const f2 d11 = sub2(r[2][2], r[0][0]), e11 = sub2(r[2][0], r[0][2]);  // (1,1), (-1,1)
+    const f2 sx = fma2(K.kc[1], sub2(d11, e11), mul2(K.kc[0], d10));
+    const f2 sz = fma2(K.kc[1], add2(d11, e11), mul2(K.kc[0], d01));
     // species A takes the sums over rho_B, species B those over rho_A
     const f2 m = p2(-r[1][1].x, -r[1][1].y);
     fx = fma2(m, swap2(sx), fx);

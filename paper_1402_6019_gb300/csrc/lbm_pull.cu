@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx) r[dz][dx] = Q.rh[tz + 1 + dz][tx + 1 + dx];
-            cross_force2(C, r, Fx, Fz);
+            cross_force2(K, r, Fx, Fz);
             if (MODE & M_OBS) cross_stress2(C, r, sxx, szz, sxz);
             if (live) {
                 f2 fp[9];
