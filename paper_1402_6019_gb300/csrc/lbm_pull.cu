@@ -262,6 +262,25 @@ __device__ __noinline__ void write_images(const StepConst<T>& C, T* __restrict__
         }
 }
 
+// Ring position (psi/rho tile coordinates) of a thread with tx < NRING / PZ: 22 per warp, so that
+// every warp has the same phase-A work; in ring order the top two rows, the bottom two rows, then
+// two columns on each side of the tile rows.
+__device__ __forceinline__ void ring_position(int tx, int tz, int& rpx, int& rpz) {
+    const int k = tz * (NRING / PZ) + tx;
+    if (k < 2 * HW) {
+        rpz = k / HW;
+        rpx = k % HW;
+    } else if (k < 4 * HW) {
+        rpz = HH - 2 + (k - 2 * HW) / HW;
+        rpx = (k - 2 * HW) % HW;
+    } else {
+        const int j = k - 4 * HW;
+        rpz = 2 + (j >> 2);
+        const int c = j & 3;
+        rpx = c < 2 ? c : HW - 4 + c;
+    }
+}
+
 template <typename T, int NS, int MODE, int ST>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     k_pull(const __grid_constant__ CUtensorMap tin, T* __restrict__ fout,
@@ -282,26 +301,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int nfold = Rd.enabled ? nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32) : 0;
 
-    // ring position of this thread (psi/rho tile coordinates), NRING / PZ = 22 per warp so that
-    // every warp has the same phase-A work: in ring order the top two rows, the bottom two rows,
-    // then two columns on each side of the tile rows
+    // threads with a ring position (ring_position), NRING / PZ = 22 per warp
     const bool ring = tx < NRING / PZ;
-    int rpx = 0, rpz = 0;
-    if (ring) {
-        const int k = tz * (NRING / PZ) + tx;
-        if (k < 2 * HW) {
-            rpz = k / HW;
-            rpx = k % HW;
-        } else if (k < 4 * HW) {
-            rpz = HH - 2 + (k - 2 * HW) / HW;
-            rpx = (k - 2 * HW) % HW;
-        } else {
-            const int j = k - 4 * HW;
-            rpz = 2 + (j >> 2);
-            const int c = j & 3;
-            rpx = c < 2 ? c : HW - 4 + c;
-        }
-    }
     // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden;
     // ntiles: nothing more to draw
     int upcoming = ntiles;
@@ -357,11 +358,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         if (tid == 0)  // publish the tile of iteration k + ST, one barrier ahead of its readers
             describe<T>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot);
         // this tile: first column and row (rows of its lattice), tile row among all lattices; its
-        // lattice: rows, first compact row, first padded row
-        const int lnz = D.lnz, zrow0 = D.zrow0, prow0 = D.prow0, x0 = D.x0, z0 = D.z0, jg = D.jg;
-        const int s = x0 / PX;  // tile column
-        const int x = x0 + tx, z = z0 + tz;
-        const bool live = x < nx && z < lnz;
+        // lattice: rows, first compact row, first padded row (read again from shared memory after
+        // the tile barrier, so that they do not hold registers across it)
+        int lnz = D.lnz, zrow0 = D.zrow0, prow0 = D.prow0, x0 = D.x0, z0 = D.z0, jg = D.jg;
+        int x = x0 + tx, z = z0 + tz;
+        bool live = x < nx && z < lnz;
         const bool ok = wait_load(smem_u32(&S.bar[sl]), (parity >> sl) & 1u);
         if (ok) parity ^= 1u << sl;  // on expiry the exit path waits on the same phase again
         if (ST > 1 && k == 0 && tid == 0)  // the first box is in: the CTA's other first tiles
@@ -408,13 +409,30 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         } else {
             side_density<T, NS, ST>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz, WALL);
         }
-        if (ring) side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
+        if (ring) {  // (recomputed per tile: one register pair less across the tile)
+            int rpx, rpz;
+            ring_position(tx, tz, rpx, rpz);
+            side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
+        }
         // the only CTA barrier of a tile: psi / rho of the tile and ring complete, box sl read
         // by all, the previous tile's column sums written
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
+        {
+            const TileInfo<T>& E = S.ti[k % NTQ];
+            lnz = E.lnz;
+            zrow0 = E.zrow0;
+            prow0 = E.prow0;
+            x0 = E.x0;
+            z0 = E.z0;
+            jg = E.jg;
+            x = x0 + tx;
+            z = z0 + tz;
+            live = x < nx && z < lnz;
+        }
+        const int s = x0 / PX;  // tile column
         // box sl is free: start the load of the tile ST ahead (published at the top of this
         // iteration) and draw the one after it; past the last tile, look at the reduction's
         // counter instead (its value is only used after the loop)
@@ -484,7 +502,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 const f2 ir = p2(__fdividef(1.f, rh.x), __fdividef(1.f, rh.y));
                 f2 jx, jz;
                 momentum9_2(fp, jx, jz);
-                Fx = fma2(rh, sp(D.g), Fx);
+                Fx = fma2(rh, sp(S.ti[k % NTQ].g), Fx);
                 if (MODE & (M_OBS | M_FIELDS)) {
                     // barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s and the kinetic flux
                     const f2 m = fma2(Fx, sp(0.5f), jx), n = fma2(Fz, sp(0.5f), jz);
@@ -561,7 +579,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                     if (!(rho[s2] > T(0)) || !(rho[s2] < T(1e30))) bad = 1;
                     ir[s2] = div_(T(1), rho[s2]);
                     momentum9(f[s2], jx[s2], jz[s2]);
-                    F[s2][0] += rho[s2] * D.g;
+                    F[s2][0] += rho[s2] * S.ti[k % NTQ].g;
                 }
                 if (MODE & (M_OBS | M_FIELDS)) {
                     T ux, uz, pixz, rtot, mx, mz;
@@ -619,7 +637,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                         T v = f[s2][l];
                         if (zd < 0 || zd >= lnz) {  // leaves through a wall: store it reflected
                             const int w = zd < 0 ? 0 : 1;
-                            const T back = bounce<T>(l, f[s2][l], rho[s2], w == 0 ? D.wall[0] : D.wall[1]);
+                            const T back = bounce<T>(l, f[s2][l], rho[s2], S.ti[k % NTQ].wall[w]);
                             v = back;
                             if (MODE & M_OBS) {
                                 const T dm = T(cx(l)) * (f[s2][l] + back);
