@@ -23,6 +23,7 @@ __device__ __forceinline__ f2 swap2(f2 a) { return make_float2(a.y, a.x); }
 // Constant tables of the step as (A, B) pairs, built on the host from StepConst<float>.
 struct PairConst {
     f2 kf[5];           // Eq. FORCE by shell: K_s(1), K_s(2), 2 K_s(4), K_s(5), 2 K_s(8)
+    f2 kf5x2, kf5x2n, kf5n, kf8n;  // 2 K_s(5), -2 K_s(5), -K_s(5), -2 K_s(8)
     f2 kc[2];           // cross force by shell, both halves alike: G_AB w8(1), G_AB w8(2)
     f2 sq[9];           // App. A shell prefactors by |c|^2
     f2 omega, tau, rho_ref, nexp;  // nexp = -log2(e) / rho0 (psi = 1 - 2^(nexp rho))
@@ -36,6 +37,10 @@ inline void fill_pair_const(PairConst& K, const StepConst<float>& C) {
     // K_s(q) c_x of the links (1,0), (1,1), (2,0), (1,2), (2,2): exactly K_s(q) or 2 K_s(q)
     const int at[5] = {2 * 5 + 3, 3 * 5 + 3, 2 * 5 + 4, 4 * 5 + 3, 4 * 5 + 4};
     for (int k = 0; k < 5; ++k) K.kf[k] = make_float2(C.kx[0][at[k]], C.kx[1][at[k]]);
+    K.kf5x2 = make_float2(2.0f * K.kf[3].x, 2.0f * K.kf[3].y);
+    K.kf5x2n = make_float2(-K.kf5x2.x, -K.kf5x2.y);
+    K.kf5n = make_float2(-K.kf[3].x, -K.kf[3].y);
+    K.kf8n = make_float2(-K.kf[4].x, -K.kf[4].y);
     // G_AB w8(q) c_x of the links (1,0), (1,1)
     K.kc[0] = make_float2(C.kcx[1 * 3 + 2], C.kcx[1 * 3 + 2]);
     K.kc[1] = make_float2(C.kcx[2 * 3 + 2], C.kcx[2 * 3 + 2]);
@@ -87,40 +92,112 @@ __device__ __forceinline__ void intra_force2(const PairConst& K, const f2 (&p)[5
 #undef LBM_Q
 }
 
-// Appendix A stresses of both species, returned as (A, B) pairs of (sxx, szz, sxz).
-__device__ __forceinline__ void intra_stress2(const PairConst& K, const f2 (&p)[5][5], f2& sxx, f2& szz, f2& sxz) {
-#define LBM_Q(dx, dz) p[(dz) + 2][(dx) + 2]
-    const f2 p0 = LBM_Q(0, 0);
+// Eq. FORCE and the Appendix A stresses of both species in one pass over the 5 x 5 psi window
+// w (w[(dz + 2) * W + dx + 2] = psi(x + dx, z + dz), shared memory), for the observing passes:
+// the sums of intra_force2 and of Appendix A's shell stresses (as lbm_core.cuh forms them per
+// species).  The 16 values of the shells |c|^2 = 4, 5, 8 enter both only through the difference
+// (force) and the sum (stress) of antipodal links, so they are read pair by pair and folded into
+// the accumulators at once; only the inner 3 x 3 values, which the stresses' products need, are
+// held throughout.  Returns the stresses as (A, B) pairs.
+template <int W>
+__device__ __forceinline__ void force_stress2(const PairConst& K, const f2* __restrict__ w, f2& fx, f2& fz,
+                                              f2& sxx, f2& szz, f2& sxz) {
+#define LBM_W(dx, dz) w[((dz) + 2) * W + (dx) + 2]
+    const f2 p0 = LBM_W(0, 0);
+    const f2 q10 = LBM_W(1, 0), qm10 = LBM_W(-1, 0), q01 = LBM_W(0, 1), q0m1 = LBM_W(0, -1);
+    const f2 q11 = LBM_W(1, 1), qm1m1 = LBM_W(-1, -1), qm11 = LBM_W(-1, 1), q1m1 = LBM_W(1, -1);
+    // force, shells 1 and 2
+    const f2 d11 = sub2(q11, qm1m1), e11 = sub2(qm11, q1m1);
+    f2 sx = fma2(K.kf[1], sub2(d11, e11), mul2(K.kf[0], sub2(q10, qm10)));
+    f2 sz = fma2(K.kf[1], add2(d11, e11), mul2(K.kf[0], sub2(q01, q0m1)));
+    // shells 4, 5, 8 pair by pair: force += K c (psi(c) - psi(-c)); stress accumulators of the
+    // sums psi(c) + psi(-c): a4 (shell 4), a5x = 4 s21 + s12, a5z = s21 + 4 s12,
+    // a5xz = a21 - b21 + a12 - b12, a8 = a22 + b22, a8xz = a22 - b22
+    f2 a4x, a4z, a5x, a5z, a5xz, a8, a8xz;
+    {
+        const f2 u = LBM_W(2, 0), v = LBM_W(-2, 0);
+        sx = fma2(K.kf[2], sub2(u, v), sx);
+        a4x = add2(u, v);
+    }
+    {
+        const f2 u = LBM_W(0, 2), v = LBM_W(0, -2);
+        sz = fma2(K.kf[2], sub2(u, v), sz);
+        a4z = add2(u, v);
+    }
+    {  // (2,1)
+        const f2 u = LBM_W(2, 1), v = LBM_W(-2, -1), d = sub2(u, v), t = add2(u, v);
+        sx = fma2(K.kf5x2, d, sx);
+        sz = fma2(K.kf[3], d, sz);
+        a5x = mul2(sp(4.f), t);
+        a5z = t;
+        a5xz = t;
+    }
+    {  // (-2,1)
+        const f2 u = LBM_W(-2, 1), v = LBM_W(2, -1), d = sub2(u, v), t = add2(u, v);
+        sx = fma2(K.kf5x2n, d, sx);
+        sz = fma2(K.kf[3], d, sz);
+        a5x = fma2(sp(4.f), t, a5x);
+        a5z = add2(a5z, t);
+        a5xz = sub2(a5xz, t);
+    }
+    {  // (1,2)
+        const f2 u = LBM_W(1, 2), v = LBM_W(-1, -2), d = sub2(u, v), t = add2(u, v);
+        sx = fma2(K.kf[3], d, sx);
+        sz = fma2(K.kf5x2, d, sz);
+        a5x = add2(a5x, t);
+        a5z = fma2(sp(4.f), t, a5z);
+        a5xz = add2(a5xz, t);
+    }
+    {  // (-1,2)
+        const f2 u = LBM_W(-1, 2), v = LBM_W(1, -2), d = sub2(u, v), t = add2(u, v);
+        sx = fma2(K.kf5n, d, sx);
+        sz = fma2(K.kf5x2, d, sz);
+        a5x = add2(a5x, t);
+        a5z = fma2(sp(4.f), t, a5z);
+        a5xz = sub2(a5xz, t);
+    }
+    {  // (2,2)
+        const f2 u = LBM_W(2, 2), v = LBM_W(-2, -2), d = sub2(u, v), t = add2(u, v);
+        sx = fma2(K.kf[4], d, sx);
+        sz = fma2(K.kf[4], d, sz);
+        a8 = t;
+        a8xz = t;
+    }
+    {  // (-2,2)
+        const f2 u = LBM_W(-2, 2), v = LBM_W(2, -2), d = sub2(u, v), t = add2(u, v);
+        sx = fma2(K.kf8n, d, sx);
+        sz = fma2(K.kf[4], d, sz);
+        a8 = add2(a8, t);
+        a8xz = sub2(a8xz, t);
+    }
+    const f2 m = p2(-p0.x, -p0.y);
+    fx = mul2(m, sx);
+    fz = mul2(m, sz);
+    // stresses: shells 1 and 2, then the products of the inner values
     const f2 four = sp(4.f), two = sp(2.f);
-    const f2 d2 = add2(LBM_Q(1, 1), LBM_Q(-1, -1)), a2 = add2(LBM_Q(-1, 1), LBM_Q(1, -1));
-    const f2 da = add2(d2, a2);
-    const f2 n12x = fma2(K.sq[1], add2(LBM_Q(1, 0), LBM_Q(-1, 0)), mul2(K.sq[2], da));
-    const f2 n12z = fma2(K.sq[1], add2(LBM_Q(0, 1), LBM_Q(0, -1)), mul2(K.sq[2], da));
+    const f2 d2 = add2(q11, qm1m1), a2 = add2(qm11, q1m1), da = add2(d2, a2);
+    const f2 n12x = fma2(K.sq[1], add2(q10, qm10), mul2(K.sq[2], da));
+    const f2 n12z = fma2(K.sq[1], add2(q01, q0m1), mul2(K.sq[2], da));
     const f2 n12xz = mul2(K.sq[2], sub2(d2, a2));
     const f2 q4 = mul2(four, K.sq[4]);
-    const f2 s4x = mul2(q4, fma2(p0, add2(LBM_Q(2, 0), LBM_Q(-2, 0)), mul2(two, mul2(LBM_Q(-1, 0), LBM_Q(1, 0)))));
-    const f2 s4z = mul2(q4, fma2(p0, add2(LBM_Q(0, 2), LBM_Q(0, -2)), mul2(two, mul2(LBM_Q(0, -1), LBM_Q(0, 1)))));
-    const f2 a21 = add2(LBM_Q(2, 1), LBM_Q(-2, -1)), b21 = add2(LBM_Q(-2, 1), LBM_Q(2, -1));
-    const f2 a12 = add2(LBM_Q(1, 2), LBM_Q(-1, -2)), b12 = add2(LBM_Q(-1, 2), LBM_Q(1, -2));
-    const f2 t13 = fma2(LBM_Q(1, 1), LBM_Q(-1, 0), mul2(LBM_Q(1, 0), LBM_Q(-1, -1)));
-    const f2 t14 = fma2(LBM_Q(1, 1), LBM_Q(0, -1), mul2(LBM_Q(0, 1), LBM_Q(-1, -1)));
-    const f2 t15 = fma2(LBM_Q(0, 1), LBM_Q(1, -1), mul2(LBM_Q(-1, 1), LBM_Q(0, -1)));
-    const f2 t16 = fma2(LBM_Q(-1, 1), LBM_Q(1, 0), mul2(LBM_Q(-1, 0), LBM_Q(1, -1)));
-    const f2 s21 = add2(a21, b21), s12 = add2(a12, b12);
+    const f2 s4x = mul2(q4, fma2(p0, a4x, mul2(two, mul2(qm10, q10))));
+    const f2 s4z = mul2(q4, fma2(p0, a4z, mul2(two, mul2(q0m1, q01))));
+    const f2 t13 = fma2(q11, qm10, mul2(q10, qm1m1));
+    const f2 t14 = fma2(q11, q0m1, mul2(q01, qm1m1));
+    const f2 t15 = fma2(q01, q1m1, mul2(qm11, q0m1));
+    const f2 t16 = fma2(qm11, q10, mul2(qm10, q1m1));
     const f2 t1316 = add2(t13, t16), t1415 = add2(t14, t15);
-    const f2 s5x = mul2(K.sq[5], add2(mul2(p0, fma2(four, s21, s12)), fma2(four, t1316, t1415)));
-    const f2 s5z = mul2(K.sq[5], add2(mul2(p0, fma2(four, s12, s21)), fma2(four, t1415, t1316)));
-    const f2 s5xz = mul2(K.sq[5], mul2(two, add2(mul2(p0, add2(sub2(a21, b21), sub2(a12, b12))),
-                                               sub2(add2(t13, t14), add2(t15, t16)))));
-    const f2 a22 = add2(LBM_Q(2, 2), LBM_Q(-2, -2)), b22 = add2(LBM_Q(-2, 2), LBM_Q(2, -2));
-    const f2 ha = mul2(two, mul2(LBM_Q(-1, -1), LBM_Q(1, 1))), hb = mul2(two, mul2(LBM_Q(-1, 1), LBM_Q(1, -1)));
+    const f2 s5x = mul2(K.sq[5], fma2(p0, a5x, fma2(four, t1316, t1415)));
+    const f2 s5z = mul2(K.sq[5], fma2(p0, a5z, fma2(four, t1415, t1316)));
+    const f2 s5xz = mul2(K.sq[5], mul2(two, fma2(p0, a5xz, sub2(add2(t13, t14), add2(t15, t16)))));
+    const f2 ha = mul2(two, mul2(qm1m1, q11)), hb = mul2(two, mul2(qm11, q1m1));
     const f2 q8 = mul2(four, K.sq[8]);
-    const f2 s8 = mul2(q8, fma2(p0, add2(a22, b22), add2(ha, hb)));
-    const f2 s8xz = mul2(q8, fma2(p0, sub2(a22, b22), sub2(ha, hb)));
+    const f2 s8 = mul2(q8, fma2(p0, a8, add2(ha, hb)));
+    const f2 s8xz = mul2(q8, fma2(p0, a8xz, sub2(ha, hb)));
     sxx = add2(fma2(p0, n12x, s4x), add2(s5x, s8));
     szz = add2(fma2(p0, n12z, s4z), add2(s5z, s8));
     sxz = add2(fma2(p0, n12xz, s5xz), s8xz);
-#undef LBM_Q
+#undef LBM_W
 }
 
 // Sec. IV cross repulsion for both species (first belt, rho as the cross pseudopotential):

@@ -468,20 +468,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         bool collided = false;  // f holds the post-collision values of a live site
         T rho[NS];
         if constexpr (kPair<T, NS>) {
-            f2 p[5][5];
-#pragma unroll
-            for (int dz = 0; dz < 5; ++dz)
-#pragma unroll
-                for (int dx = 0; dx < 5; ++dx) p[dz][dx] = Q.ps[tz + dz][tx + dx];
             f2 Fx, Fz;
-            intra_force2(K, p, Fx, Fz);
             float sxx = 0.f, szz = 0.f, sxz = 0.f;
-            if (MODE & M_OBS) {
+            if constexpr ((MODE & M_OBS) != 0) {
                 f2 a2, b2, c2;
-                intra_stress2(K, p, a2, b2, c2);
+                force_stress2<HW>(K, &Q.ps[tz][tx], Fx, Fz, a2, b2, c2);
                 sxx = a2.x + a2.y;
                 szz = b2.x + b2.y;
                 sxz = c2.x + c2.y;
+            } else {
+                f2 p[5][5];
+#pragma unroll
+                for (int dz = 0; dz < 5; ++dz)
+#pragma unroll
+                    for (int dx = 0; dx < 5; ++dx) p[dz][dx] = Q.ps[tz + dz][tx + dx];
+                intra_force2(K, p, Fx, Fz);
             }
             f2 r[3][3];
 #pragma unroll
