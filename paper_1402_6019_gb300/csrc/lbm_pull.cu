@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         const PsiTile<T, NS>& Q = S.q[qb];
         T rowq[NQR];
 #pragma unroll
-        for (int k = 0; k < NQR; ++k) rowq[k] = T(0);
+        for (int q = 0; q < NQR; ++q) rowq[q] = T(0);
         T cps = T(0), cpx = T(0);
         int bad = 0;
         bool collided = false;  // f holds the post-collision values of a live site
