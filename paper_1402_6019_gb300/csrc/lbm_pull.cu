@@ -301,8 +301,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int nfold = Rd.enabled ? nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32) : 0;
 
-    // threads with a ring position (ring_position), NRING / PZ = 22 per warp
+    // threads with a ring position (ring_position), NRING / PZ = 22 per warp; the observing builds
+    // recompute it per tile instead (one register pair less across the tile, where registers
+    // are short), the others keep it
     const bool ring = tx < NRING / PZ;
+    int rpx0 = 0, rpz0 = 0;
+    if constexpr ((MODE & M_OBS) == 0)
+        if (ring) ring_position(tx, tz, rpx0, rpz0);
     // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden;
     // ntiles: nothing more to draw
     int upcoming = ntiles;
@@ -358,8 +363,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         if (tid == 0)  // publish the tile of iteration k + ST, one barrier ahead of its readers
             describe<T>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot);
         // this tile: first column and row (rows of its lattice), tile row among all lattices; its
-        // lattice: rows, first compact row, first padded row (read again from shared memory after
-        // the tile barrier, so that they do not hold registers across it)
+        // lattice: rows, first compact row, first padded row (the observing builds read them again
+        // from shared memory after the tile barrier, so that they hold no registers across it)
         int lnz = D.lnz, zrow0 = D.zrow0, prow0 = D.prow0, x0 = D.x0, z0 = D.z0, jg = D.jg;
         int x = x0 + tx, z = z0 + tz;
         bool live = x < nx && z < lnz;
@@ -409,9 +414,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         } else {
             side_density<T, NS, ST>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz, WALL);
         }
-        if (ring) {  // (recomputed per tile: one register pair less across the tile)
-            int rpx, rpz;
-            ring_position(tx, tz, rpx, rpz);
+        if (ring) {
+            int rpx = rpx0, rpz = rpz0;
+            if constexpr ((MODE & M_OBS) != 0) ring_position(tx, tz, rpx, rpz);
             side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
         }
         // the only CTA barrier of a tile: psi / rho of the tile and ring complete, box sl read
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             failed = true;
             break;
         }
-        {
+        if constexpr ((MODE & M_OBS) != 0) {
             const TileInfo<T>& E = S.ti[k % NTQ];
             lnz = E.lnz;
             zrow0 = E.zrow0;
