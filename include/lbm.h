@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 3
+#define LBM_ABI_VERSION 4
 
 /* status codes */
 enum {
@@ -179,6 +179,16 @@ long long lbm_observables_bytes(const lbm_ctx *c);
 int lbm_observables_enqueue(lbm_ctx *c, void *dst, int averages, int reset, long long *ticket);
 int lbm_wait(lbm_ctx *c, long long ticket);
 int lbm_observables_unpack(const lbm_ctx *c, const void *src, lbm_obs *out);
+
+/* A time series of observables in one call (no counterpart in the paper): nsteps (>= 0) times,
+   one step (lbm_step(c, 1)) followed by lbm_observables_enqueue(c, dst + i * stride, averages,
+   reset), so the host spends one call, not two per step, and the records go out while the
+   next steps run.  stride >= lbm_observables_bytes(c); dst must hold nsteps records (pinned host
+   or device memory; the caller owns it and keeps it until the records have arrived).  *ticket
+   (may be NULL) receives the ticket of the last record (lbm_wait on it waits for all of them).
+   Stops at the first error and returns it; the steps and records before it stay enqueued. */
+int lbm_step_read(lbm_ctx *c, int nsteps, void *dst, long long stride, int averages, int reset,
+                  long long *ticket);
 
 /* Wait for the context's stream; reports LBM_ENONFINITE if a step met a bad density. */
 int lbm_synchronize(lbm_ctx *c);

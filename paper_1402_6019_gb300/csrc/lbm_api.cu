@@ -1084,6 +1084,22 @@ extern "C" int lbm_observables_enqueue(lbm_ctx* c, void* dst, int averages, int 
     return LBM_OK;
 }
 
+extern "C" int lbm_step_read(lbm_ctx* c, int nsteps, void* dst, long long stride, int averages, int reset,
+                             long long* ticket) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
+    if (!dst && nsteps > 0) return fail(c, LBM_EINVAL, "dst is NULL");
+    if (stride < lbm_observables_bytes(c)) return fail(c, LBM_EINVAL, "stride is below lbm_observables_bytes");
+    for (int i = 0; i < nsteps; ++i) {
+        const int rc = lbm_step(c, 1);
+        if (rc != LBM_OK) return rc;
+        const int rr = lbm_observables_enqueue(c, static_cast<char*>(dst) + (long long)i * stride, averages, reset,
+                                               ticket);
+        if (rr != LBM_OK) return rr;
+    }
+    return LBM_OK;
+}
+
 extern "C" int lbm_wait(lbm_ctx* c, long long ticket) {
     if (!c) return LBM_EINVAL;
     if (ticket < 0 || ticket >= c->tickets) return fail(c, LBM_EINVAL, "ticket %lld was not issued", ticket);

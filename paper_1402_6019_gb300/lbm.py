@@ -81,6 +81,8 @@ SIGNATURES = {
     "lbm_observables_bytes": (ctypes.c_longlong, [_VP]),
     "lbm_observables_enqueue": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_wait": (ctypes.c_int, [_VP, ctypes.c_longlong]),
+    "lbm_step_read": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_longlong)]),
     "lbm_observables_unpack": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(lbm_obs)]),
     "lbm_profile_read_adjoint": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_longlong)]),
@@ -446,6 +448,10 @@ class Lattice:
         """An ObsReader: asynchronous, double-buffered reads of this lattice's observables."""
         return ObsReader(self, depth)
 
+    def series(self, chunk, depth=2):
+        """An ObsSeries: runs of up to `chunk` steps with every step's observables read back."""
+        return ObsSeries(self, chunk, depth)
+
     def set_observe(self, every):
         lbm_set_observe(self.h, every)
 
@@ -506,3 +512,48 @@ class ObsReader:
         if rc not in (LBM_OK, LBM_ENONFINITE):
             _check(rc, self.lat.h)
         return self.lat._obs_dict(o, prof)
+
+
+class ObsSeries:
+    """Time series of observables (lbm_step_read): run(n) enqueues n steps, each followed by the
+    copy of its record into one of `depth` pinned host buffers of `chunk` records, in one library
+    call; results(ticket) waits for that run's records and unpacks them.  A buffer is reused
+    `depth` runs later, so read each run's results before then."""
+
+    def __init__(self, lat, chunk, depth=2):
+        import torch
+
+        if chunk < 1 or depth < 1:
+            raise ValueError("chunk and depth must be >= 1")
+        self.lat, self.chunk = lat, chunk
+        self.rec = load().lbm_observables_bytes(lat.h)
+        self.bufs = [torch.empty(chunk * self.rec, dtype=torch.uint8, pin_memory=True) for _ in range(depth)]
+        self.k = 0
+
+    def run(self, n, averages="completed", reset=True):
+        """n (<= chunk) steps; averages as in ObsReader.enqueue, applied after every step."""
+        if not 0 <= n <= self.chunk:
+            raise ValueError("n must be in 0 .. chunk")
+        buf = self.bufs[self.k % len(self.bufs)]
+        self.k += 1
+        mode = 2 if averages == "completed" else (1 if averages else 0)
+        t = ctypes.c_longlong(-1)
+        _check(load().lbm_step_read(self.lat.h, n, ctypes.c_void_p(buf.data_ptr()), self.rec, mode,
+                                    1 if reset else 0, ctypes.byref(t)), self.lat.h)
+        return (t.value, buf, n)
+
+    def results(self, ticket):
+        """The run's records as observable dicts, in step order."""
+        t, buf, n = ticket
+        if n == 0:
+            return []
+        _check(load().lbm_wait(self.lat.h, t), self.lat.h)
+        out = []
+        for i in range(n):
+            o, prof = self.lat._obs_struct()
+            rc = load().lbm_observables_unpack(self.lat.h, ctypes.c_void_p(buf.data_ptr() + i * self.rec),
+                                               ctypes.byref(o))
+            if rc not in (LBM_OK, LBM_ENONFINITE):
+                _check(rc, self.lat.h)
+            out.append(self.lat._obs_dict(o, prof))
+        return out

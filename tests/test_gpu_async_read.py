@@ -81,3 +81,37 @@ def test_wait_rejects_unknown_tickets():
     r = lat.reader()
     t = r.enqueue()
     assert r.result(t)["samples"] == 1
+
+
+@pytest.mark.parametrize("precision", [L.LBM_FP32, L.LBM_FP64])
+def test_step_read_series_equals_step_by_step_reads(precision):
+    """lbm_step_read: runs of steps with every step's completed sums read back by one call give
+    the records of separate lbm_step + lbm_observables_enqueue calls, bit for bit."""
+    nx, nz = 96, 40
+    rho, _ = W.disk_packing(nx, nz, 0.6, 7, r_mean=5, r_spread=1)
+    a = L.Lattice(nx, nz, 2, precision, L.LBM_PERIODIC, **W.EMULSION_PARAMS)
+    b = L.Lattice(nx, nz, 2, precision, L.LBM_PERIODIC, **W.EMULSION_PARAMS)
+    for lat in (a, b):
+        lat.set_fields(rho)
+        lat.set_observe(1)
+    series = a.series(chunk=20, depth=2)
+    got, pending = [], None
+    for n in (20, 7, 0, 20):
+        t = series.run(n)
+        if pending is not None:
+            got += series.results(pending)
+        pending = t
+    got += series.results(pending)
+    r = b.reader(depth=2)
+    want = []
+    for _ in range(47):
+        b.step(1)
+        want.append(r.result(r.enqueue(averages="completed", reset=True)))
+    assert len(got) == 47
+    for g, w in zip(got, want):
+        same(g, w)
+    assert got[-1]["step"] == 47 and got[-1]["samples"] == 1
+    rc = L.load().lbm_step_read(a.h, 1, series.bufs[0].data_ptr(), series.rec - 8, 2, 1, None)
+    assert rc == L.LBM_EINVAL and a.observables()["step"] == 47  # nothing enqueued
+    with pytest.raises(ValueError):
+        series.run(21)
