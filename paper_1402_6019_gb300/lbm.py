@@ -518,7 +518,8 @@ class ObsSeries:
     """Time series of observables (lbm_step_read): run(n) enqueues n steps, each followed by the
     copy of its record into one of `depth` pinned host buffers of `chunk` records, in one library
     call; results(ticket) waits for that run's records and unpacks them.  A buffer is reused
-    `depth` runs later, so read each run's results before then."""
+    `depth` runs later, so read each run's results before then.  The unpacking targets (profile
+    arrays and lbm_obs structs) are set up once per buffer."""
 
     def __init__(self, lat, chunk, depth=2):
         import torch
@@ -528,32 +529,53 @@ class ObsSeries:
         self.lat, self.chunk = lat, chunk
         self.rec = load().lbm_observables_bytes(lat.h)
         self.bufs = [torch.empty(chunk * self.rec, dtype=torch.uint8, pin_memory=True) for _ in range(depth)]
+        nz, nx, ns = lat.nz, lat.nx, lat.ns
+        self._out = []
+        for _ in range(depth):
+            prof = dict(ux_z=np.zeros((chunk, nz)), rho_z=np.zeros((chunk, ns, nz)), sxz_z=np.zeros((chunk, nz)),
+                        fluid_z=np.zeros((chunk, nz)), ps_x=np.zeros((chunk, nx)), pxx_x=np.zeros((chunk, nx)))
+            structs = []
+            for i in range(chunk):
+                o = lbm_obs()
+                for k, v in prof.items():
+                    setattr(o, k, v[i].ctypes.data_as(_DP))
+                structs.append(o)
+            self._out.append((prof, structs))
         self.k = 0
 
     def run(self, n, averages="completed", reset=True):
         """n (<= chunk) steps; averages as in ObsReader.enqueue, applied after every step."""
         if not 0 <= n <= self.chunk:
             raise ValueError("n must be in 0 .. chunk")
-        buf = self.bufs[self.k % len(self.bufs)]
+        bi = self.k % len(self.bufs)
         self.k += 1
         mode = 2 if averages == "completed" else (1 if averages else 0)
         t = ctypes.c_longlong(-1)
-        _check(load().lbm_step_read(self.lat.h, n, ctypes.c_void_p(buf.data_ptr()), self.rec, mode,
+        _check(load().lbm_step_read(self.lat.h, n, ctypes.c_void_p(self.bufs[bi].data_ptr()), self.rec, mode,
                                     1 if reset else 0, ctypes.byref(t)), self.lat.h)
-        return (t.value, buf, n)
+        return (t.value, bi, n)
 
     def results(self, ticket):
-        """The run's records as observable dicts, in step order."""
-        t, buf, n = ticket
+        """The run's records as observable dicts, in step order (their arrays are the run's own)."""
+        t, bi, n = ticket
         if n == 0:
             return []
-        _check(load().lbm_wait(self.lat.h, t), self.lat.h)
+        lib, h = load(), self.lat.h
+        _check(lib.lbm_wait(h, t), h)
+        prof, structs = self._out[bi]
+        base = self.bufs[bi].data_ptr()
+        for i in range(n):
+            rc = lib.lbm_observables_unpack(h, ctypes.c_void_p(base + i * self.rec), ctypes.byref(structs[i]))
+            if rc not in (LBM_OK, LBM_ENONFINITE):
+                _check(rc, h)
+        run = {k: v[:n].copy() for k, v in prof.items()}  # one copy per run, not per record
         out = []
         for i in range(n):
-            o, prof = self.lat._obs_struct()
-            rc = load().lbm_observables_unpack(self.lat.h, ctypes.c_void_p(buf.data_ptr() + i * self.rec),
-                                               ctypes.byref(o))
-            if rc not in (LBM_OK, LBM_ENONFINITE):
-                _check(rc, self.lat.h)
-            out.append(self.lat._obs_dict(o, prof))
+            o = structs[i]
+            res = dict(mass=np.array(o.mass[:]), momentum=np.array(o.momentum[:]), gamma=o.gamma,
+                       wall_force=np.array(o.wall_force[:]), nonfinite=bool(o.nonfinite), step=o.step,
+                       samples=o.samples)
+            for k, v in run.items():
+                res[k] = v[i]
+            out.append(res)
         return out
