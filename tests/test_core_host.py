@@ -1,4 +1,5 @@
-"""The library's per-site arithmetic (lbm_core.cuh), compiled for the host, against the oracle.
+"""The library's per-site arithmetic (lbm_core.cuh, and the two-species FP32 forms of
+lbm_pair.cuh), compiled for the host, against the oracle.
 
 Checks the force of Eq. FORCE, the cross repulsion, the Appendix A shell stresses and the cross
 stress at every site of small random lattices, for both weight presets.  No GPU needed.
@@ -103,3 +104,57 @@ def test_psi_matches_oracle(oracle, core):
     for s in range(2):
         for i in range(4):
             assert core.core_psi(ctypes.byref(lp), s, rho[s, 0, i]) == pytest.approx(psi[s, 0, i], rel=1e-15)
+
+
+@pytest.fixture(scope="module")
+def pair(tmp_path_factory):
+    out = tmp_path_factory.mktemp("pair") / "libpairhost.so"
+    src = os.path.join(ROOT, "tests", "native", "pair_host.cpp")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_1402_6019_gb300", "csrc"), src, "-o", str(out)],
+                   check=True)
+    lib = ctypes.CDLL(str(out))
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.pair_site.argtypes = [ctypes.POINTER(L.lbm_params), dp, dp, dp, dp, dp, dp, dp]
+    return lib
+
+
+@pytest.mark.parametrize("preset", [0, 1])
+def test_pair_fp32_site_arithmetic_matches_oracle(oracle, pair, preset):
+    """The FP32 two-species forms the step kernel runs (intra_force2, force_stress2, cross_force2,
+    cross_stress2, psi2) at every site of a random 11 x 9 lattice.  Forces and stresses here are
+    at most 0.3 in size and each is a sum of about 30 terms of at most that size, so FP32 rounding
+    (unit 2^-24) bounds their error by 30 * 0.3 * 2^-24 < 1e-6; a dropped term of the outermost
+    shell (|c|^2 = 8) alone would be about 1e-3."""
+    nx, nz = 11, 9
+    rng = np.random.default_rng(70 + preset)
+    rho = 0.1 + 1.2 * rng.random((2, nz, nx))
+    prm = dict(W.EMULSION_PARAMS, G_AB=0.587, weight_preset=preset)
+    ref = oracle.RefLattice(nx, nz, 2, 0, **prm)
+    ref.set_fields(rho)
+    sf = ref.site_fields()
+    rho_o = ref.fields()[0]
+    psi = sf["psi"]
+    lp = _lib_params(**prm)
+    kin = 0.25  # (tau - 1/2)^2 at tau = 1
+    for z in range(nz):
+        for x in range(nx):
+            p25 = np.array([psi[s, (z + dz) % nz, (x + dx) % nx]
+                            for s in range(2) for dz in range(-2, 3) for dx in range(-2, 3)])
+            r9 = np.array([rho_o[s, (z + dz) % nz, (x + dx) % nx]
+                           for s in range(2) for dz in range(-1, 2) for dx in range(-1, 2)])
+            F, F2, si, sc, ps = np.zeros(4), np.zeros(4), np.zeros(6), np.zeros(3), np.zeros(2)
+            pair.pair_site(ctypes.byref(lp), _p(p25), _p(r9), _p(F), _p(F2), _p(si), _p(sc), _p(ps))
+            want_F = sf["F"][:, :, z, x].reshape(-1)
+            assert np.abs(want_F).max() < 0.3
+            assert np.allclose(F, want_F, rtol=0, atol=1e-6), (z, x, F, want_F)
+            assert np.allclose(F2, want_F, rtol=0, atol=1e-6), (z, x, F2, want_F)
+            assert np.allclose(si, sf["sint"][:, :, z, x].reshape(-1), rtol=0, atol=1e-6), (z, x)
+            rest = np.zeros(3)
+            for s in range(2):
+                r, fx, fz = rho_o[s, z, x], sf["F"][s, 0, z, x], sf["F"][s, 1, z, x]
+                rest += np.array([r / 3 + kin * fx * fx / r, r / 3 + kin * fz * fz / r, kin * fx * fz / r])
+                rest += sf["sint"][s, :, z, x]
+            assert np.allclose(sc, sf["P"][:, z, x] - rest, rtol=0, atol=1e-6), (z, x)
+            assert np.allclose(ps, psi[:, z, x], rtol=1e-6, atol=0), (z, x)
