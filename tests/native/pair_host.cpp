@@ -71,3 +71,29 @@ extern "C" int pair_site(const lbm_params* p, const double* psi25, const double*
     psi[1] = ps.y;
     return 0;
 }
+
+// The shifted-velocity BGK collision of both species (collide2) at one site, as the step kernel
+// runs it: populations stored as FP32 deviations from W_l rho_ref, momentum and density formed
+// from them.  f18 = the populations of species A then B (FP64, before collision), F4 = the force
+// (Fx, Fz of A, then of B); out18 receives the post-collision populations (deviation + W_l rho_ref).
+extern "C" int pair_collide(const lbm_params* p, const double* rho_ref, const double* f18, const double* F4,
+                            double* out18) {
+    StepConst<float> C;
+    fill_step_const<float>(C, *p, 8, 8, 32, 256, 2, 0, rho_ref);
+    PairConst K;
+    fill_pair_const(K, C);
+    f2 fp[9];
+    for (int l = 0; l < 9; ++l)
+        fp[l] = make_float2((float)(f18[l] - wlb<double>(l) * rho_ref[0]), (float)(f18[9 + l] - wlb<double>(l) * rho_ref[1]));
+    const f2 dr = sum9_2(fp);
+    const f2 rh = add2(K.rho_ref, dr);
+    const f2 ir = p2(__fdividef(1.f, rh.x), __fdividef(1.f, rh.y));
+    f2 jx, jz;
+    momentum9_2(fp, jx, jz);
+    collide2(K, fp, dr, rh, ir, jx, jz, p2((float)F4[0], (float)F4[2]), p2((float)F4[1], (float)F4[3]));
+    for (int l = 0; l < 9; ++l) {
+        out18[l] = (double)fp[l].x + wlb<double>(l) * (double)C.rho_ref[0];
+        out18[9 + l] = (double)fp[l].y + wlb<double>(l) * (double)C.rho_ref[1];
+    }
+    return 0;
+}
