@@ -28,6 +28,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -62,6 +63,7 @@ def _args():
     ap.add_argument("--tile-rows", type=int, default=0, help="FUSED kernel tile height (8 or 16; 0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--clocks-csv", default=None, help="keep the raw nvidia-smi clock samples in this file")
     ap.add_argument("--l2", choices=["rotate", "flush"], default="rotate",
                     help="rotate: step several lattices of the workload in turn, so that each step's input "
                          "was evicted from L2 by the others' traffic (no flush); flush: one lattice, a 256 MiB "
@@ -89,14 +91,19 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    # where the raw samples go (--clocks-csv); by default a temporary file, since the JSON line
+    # carries their summary
+    csv_path = None
+
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = Clocks.csv_path or os.path.join(tempfile.gettempdir(), f"lbm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -432,6 +439,7 @@ def run_adjoint(a, w):
 
 def main():
     a = _args()
+    Clocks.csv_path = a.clocks_csv
     from paper_1402_6019_gb300 import workloads as W
 
     from paper_1402_6019_gb300 import replicas

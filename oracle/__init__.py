@@ -1,6 +1,6 @@
 """FP64 CPU oracle of the multirange Shan-Chen lattice Boltzmann step -- TEST INFRASTRUCTURE.
 
-This package is the checker, not the product.  Only ``tests/``, ``__graft_entry__.smoke()``
+This package is test infrastructure, not the product.  Only ``tests/``, ``__graft_entry__.smoke()``
 and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  It wraps
 ``lbm_oracle.c`` (plain C, FP64, no FMA contraction), which follows the paper's equations
 (Sbragaglia, Benzi, Bernaschi, Succi, arXiv:1402.6019): Eq. LB (BGK), the moments of Sec. II,
