@@ -131,7 +131,7 @@ template <typename T>
 cudaError_t launch_twopass(int ns, int mode, const T* fin, T* fout, const T* gfield, const StepConst<T>& C,
                            const GhostGeom& GG, const void* tmap, const ObsPtrs& O, int nxpart, int nzpart,
                            cudaStream_t st);
-// The driver's cuTensorMapEncodeTiled (resolved once through the runtime), or null.
+// The CUDA driver API's cuTensorMapEncodeTiled (resolved once through the runtime), or null.
 void* tensor_map_encoder();
 // Encodes the TMA descriptor (CUtensorMap, 128 bytes at out) of the two-pass field planes.
 // Returns 0 on success.
