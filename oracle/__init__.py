@@ -44,6 +44,9 @@ def build(force: bool = False) -> str:
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
+    from . import ref3d  # the three-dimensional oracle (its own library)
+
+    ref3d.build(force)
     return _LIB
 
 
