@@ -8,7 +8,9 @@
  * (Sec. II.B, competing interactions).  This file takes the 2-D model's steps to three
  * dimensions with the same readings:
  *  - lattice: D3Q19 (rest, 6 axis, 12 edge velocities; weights 1/3, 1/18, 1/36; c_s^2 = 1/3),
- *    Eq. LB with the equilibrium of Sec. II, periodic in x, y and z;
+ *    Eq. LB with the equilibrium of Sec. II, periodic in x and y, and in z or between walls
+ *    (halfway bounce-back with Ladd's moving-wall term, psi and rho mirrored beyond a wall, as
+ *    in two dimensions);
  *  - Eq. FORCE over the integer links of |c|^2 = 1, 2, 3, 4 (attraction, G1, 32 links) and
  *    |c|^2 = 1, 2, 3, 4, 5, 6, 8 (repulsion, G2, 92 links), with the weights that solve
  *    Appendix B's constraints in three dimensions: attraction e2 = 1 and isotropic to 6th order,
@@ -33,6 +35,13 @@ static const int C19[19][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0}, 
                                {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
 static double w19(int l) { return l == 0 ? 1.0 / 3.0 : (l <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+/* the velocity opposite to c_l */
+static int opp19(int l) {
+    for (int m = 0; m < 19; ++m)
+        if (C19[m][0] == -C19[l][0] && C19[m][1] == -C19[l][1] && C19[m][2] == -C19[l][2]) return m;
+    return 0;
+}
 
 /* Interaction weights by shell |c|^2 (index 0..8; zero where the shell is not used). */
 static const double W_ATT[9] = {0, 2.0 / 15.0, 1.0 / 15.0, 1.0 / 60.0, 1.0 / 120.0, 0, 0, 0, 0};
@@ -75,6 +84,16 @@ static long long idx(const lbmref3 *L, int x, int y, int z) {
     y = ((y % L->ny) + L->ny) % L->ny;
     z = ((z % L->nz) + L->nz) % L->nz;
     return ((long long)z * L->ny + y) * L->nx + x;
+}
+
+/* The site whose psi / rho a neighbour at height z reads: periodic in z, or with walls the
+   mirror image about the wall plane (z = -1 reads row 0, z = -2 row 1; likewise at the top). */
+static long long nbr(const lbmref3 *L, int x, int y, int z) {
+    if (L->p.zbc) {
+        if (z < 0) z = -1 - z;
+        if (z >= L->nz) z = 2 * L->nz - 1 - z;
+    }
+    return idx(L, x, y, z);
 }
 
 static double psi_of(const lbmref3 *L, int s, double rho) {
@@ -194,7 +213,7 @@ static void forces(const lbmref3 *L, const double *rho, double *psi, double *F /
                         const int *c = LINKS[k];
                         const int q = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
                         const double K = wn * (L->p.G1[s] * W_ATT[q] + L->p.G2[s] * W_REP[q]);
-                        const double pn = psi[s * L->n + idx(L, x + c[0], y + c[1], z + c[2])];
+                        const double pn = psi[s * L->n + nbr(L, x + c[0], y + c[1], z + c[2])];
                         for (int d = 0; d < 3; ++d) a[d] += K * pn * c[d];
                     }
                     double Fs[3];
@@ -205,7 +224,7 @@ static void forces(const lbmref3 *L, const double *rho, double *psi, double *F /
                         for (int l = 1; l < 19; ++l) {
                             const int *c = C19[l];
                             const int q = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-                            const double rn = rho[o * L->n + idx(L, x + c[0], y + c[1], z + c[2])];
+                            const double rn = rho[o * L->n + nbr(L, x + c[0], y + c[1], z + c[2])];
                             for (int d = 0; d < 3; ++d) b[d] += wn * W_CROSS[q] * rn * c[d];
                         }
                         for (int d = 0; d < 3; ++d) Fs[d] += -L->p.G_AB * rho[s * L->n + i] * b[d];
@@ -278,9 +297,19 @@ static int step1(lbmref3 *L) {
         for (int l = 0; l < 19; ++l)
             for (int z = 0; z < L->nz; ++z)
                 for (int y = 0; y < L->ny; ++y)
-                    for (int x = 0; x < L->nx; ++x)
-                        L->ftmp[(s * 19 + l) * n + idx(L, x + C19[l][0], y + C19[l][1], z + C19[l][2])] =
-                            L->f[(s * 19 + l) * n + idx(L, x, y, z)];
+                    for (int x = 0; x < L->nx; ++x) {
+                        const long long i = idx(L, x, y, z);
+                        const int zd = z + C19[l][2];
+                        const double v = L->f[(s * 19 + l) * n + i];
+                        if (L->p.zbc && (zd < 0 || zd >= L->nz)) {
+                            /* halfway bounce-back: back into this site as opp(l), with Ladd's
+                               term for a wall moving along x: -6 W_l rho (c_l . U_w) */
+                            const double uw = zd < 0 ? L->p.wall_u[0] : L->p.wall_u[1];
+                            L->ftmp[(s * 19 + opp19(l)) * n + i] = v - 6.0 * w19(l) * rho[s * n + i] * C19[l][0] * uw;
+                        } else {
+                            L->ftmp[(s * 19 + l) * n + idx(L, x + C19[l][0], y + C19[l][1], zd)] = v;
+                        }
+                    }
     double *t = L->f;
     L->f = L->ftmp;
     L->ftmp = t;

@@ -18,6 +18,10 @@ typedef struct {
     double weight_norm;  /* scale of every interaction weight (1/3: Eq. BULK)             */
     double body_force;   /* acceleration g along x: F_s += rho_s g                        */
     int psi_form;        /* 0: psi = 1 - exp(-rho / rho0); 1: psi = rho                    */
+    int zbc;             /* 0: periodic in z; 1: walls at z = -1/2 and nz - 1/2 (halfway
+                            bounce-back with Ladd's moving-wall term, Sec. IV); psi and rho
+                            beyond a wall are the mirror image of the fluid rows           */
+    double wall_u[2];    /* x-velocity of the bottom and top walls                        */
 } lbmref3_params;
 
 typedef struct lbmref3 lbmref3;

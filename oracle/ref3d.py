@@ -3,12 +3,13 @@ INFRASTRUCTURE (only ``tests/`` may import it).
 
 Wraps ``lbm_oracle3d.c``: D3Q19, Eq. FORCE over the 3-D links of |c|^2 <= 4 (attraction) and
 <= 8 (repulsion) with the weights that solve Appendix B's constraints in three dimensions, the
-first-belt cross repulsion, and the shifted-velocity BGK collision of Sec. II, periodic in x, y
-and z.  It shares no code with the CUDA path.
+first-belt cross repulsion, and the shifted-velocity BGK collision of Sec. II, periodic in x and
+y, and in z or between bounce-back walls (Sec. IV).  It shares no code with the CUDA path.
 
 Parity: pinned by ``tests/test_oracle3d.py`` against the isotropy sums of the weights, the
 D3Q19 equilibrium moments, mass and momentum conservation, the closed-form force on sinusoidal
-fields and the dispersion relation of sound on a uniform state.
+fields, the dispersion relation of sound on a uniform state, equal bulk pressures across a
+relaxed flat interface, and the exact Couette and Poiseuille profiles between walls.
 """
 from __future__ import annotations
 
@@ -48,6 +49,8 @@ class Params3(ctypes.Structure):
         ("weight_norm", ctypes.c_double),
         ("body_force", ctypes.c_double),
         ("psi_form", ctypes.c_int),
+        ("zbc", ctypes.c_int),
+        ("wall_u", ctypes.c_double * 2),
     ]
 
 
@@ -99,17 +102,20 @@ def feq(rho, u):
 
 
 def make_params(tau=1.0, G1=0.0, G2=0.0, G_AB=0.0, rho0=1.0, weight_norm=1.0 / 3.0, body_force=0.0,
-                psi_form=0) -> Params3:
+                psi_form=0, zbc=0, wall_u=(0.0, 0.0)) -> Params3:
     p = Params3()
     for name, v in (("tau", tau), ("G1", G1), ("G2", G2), ("rho0", rho0)):
         v = list(v) if hasattr(v, "__len__") else [v, v]
         getattr(p, name)[0], getattr(p, name)[1] = v[0], v[-1]
     p.G_AB, p.weight_norm, p.body_force, p.psi_form = G_AB, weight_norm, body_force, psi_form
+    p.zbc = zbc
+    p.wall_u[0], p.wall_u[1] = wall_u
     return p
 
 
 class RefLattice3D:
-    """A periodic nx x ny x nz lattice of one or two species (arrays indexed [z][y][x])."""
+    """An nx x ny x nz lattice of one or two species (arrays indexed [z][y][x]), periodic in x
+    and y, and in z unless zbc = 1 (walls)."""
 
     def __init__(self, nx, ny, nz, n_species=1, **params):
         self.lib = _load()
