@@ -472,3 +472,185 @@ def test_unstable_wave_grows_at_the_dispersion_rate(oracle, rho_b):
     slope = np.polyfit(t, np.log(np.abs(A[250:401])), 1)[0]
     assert slope == pytest.approx(gamma, rel=0.03)
     assert np.abs(A).max() < 1e-4  # still linear
+
+
+# --------------------------------------------------------------------------------------------
+# Eq. MECHANICAL on a two-dimensional state: every stress component, intra and cross
+# --------------------------------------------------------------------------------------------
+
+def _bonds(c25, wsh, wn, p, ns):
+    """The pair interactions of Eq. FORCE and of the cross term as bonds (a, a + c), each counted
+    once (c_z > 0, or c_z = 0 and c_x > 0): (kind, species, coupling K, c).  kind 'intra' pairs
+    psi_s(a) psi_s(a + c); kind 'cross' pairs rho_A(a) rho_B(a + c) + rho_B(a) rho_A(a + c)."""
+    out = []
+    for l in range(1, 25):
+        cx, cz = (int(v) for v in c25[l])
+        if not (cz > 0 or (cz == 0 and cx > 0)):
+            continue
+        q = cx * cx + cz * cz
+        for s in range(ns):
+            K = p["G2"][s] * wsh[1][q] * wn + (p["G1"][s] * wsh[0][q] * wn if l <= 12 else 0.0)
+            if K != 0.0:
+                out.append(("intra", s, K, cx, cz))
+        if ns == 2 and l <= 8 and p.get("G_AB", 0.0) != 0.0:
+            out.append(("cross", -1, p["G_AB"] * wsh[2][q] * wn, cx, cz))
+    return out
+
+
+def _line_fluxes(bonds, psi, rho, select):
+    """Momentum carried by the bonds across the lattice lines (periodic lattice).
+    TH[i, z] is the i-momentum (i = x, z) crossing the horizontal line between rows z and z + 1
+    (a bond with c_z > 0 crosses c_z such lines, each carrying K * product * c_i); TV[i, x] the
+    i-momentum crossing the vertical line between columns x and x + 1 (|c_x| lines)."""
+    _, nz, nx = psi.shape
+    TH = np.zeros((2, nz))
+    TV = np.zeros((2, nx))
+    for kind, s, K, cx, cz in bonds:
+        if not select(kind, s):
+            continue
+        sh = lambda a: np.roll(np.roll(a, -cz, axis=0), -cx, axis=1)  # a(x + c)
+        if kind == "intra":
+            prod = psi[s] * sh(psi[s])
+        else:
+            prod = rho[0] * sh(rho[1]) + rho[1] * sh(rho[0])
+        row, col = prod.sum(axis=1), prod.sum(axis=0)  # per starting row / column of a
+        for i, ci in enumerate((cx, cz)):
+            for k in range(cz):  # lines z_a + k + 1/2
+                TH[i] += K * ci * np.roll(row, k)
+            for k in range(abs(cx)):  # lines x_a + 1/2 ... (c_x > 0) or x_a - 1/2 ... (c_x < 0)
+                sgn = 1 if cx > 0 else -1
+                shift = k if cx > 0 else -(k + 1)
+                TV[i] += sgn * K * ci * np.roll(col, shift)
+    return TH, TV
+
+
+@pytest.mark.parametrize("G_AB", [0.0, 0.405])
+def test_mechanical_balance_two_dimensional_state(oracle, G_AB):
+    """Eq. MECHANICAL on a state that varies in x and z (droplets, not a flat interface), for every
+    stress component including xz.  The bonds of Eq. FORCE carry momentum across the lattice's
+    lines; on a periodic lattice, exactly:
+      * the force summed over a row (column) is minus the difference of the line fluxes above and
+        below it (left and right of it), for both components;
+      * Appendix A's node stress summed over a row is the mean of the two adjacent horizontal line
+        fluxes (sigma_xz for x-momentum, sigma_zz for z-momentum), and summed over a column the
+        mean of the two adjacent vertical ones (sigma_xx, sigma_xz).
+    The second holds shell by shell for Appendix A's split of a bond over its end points (shells
+    1, 2), its midpoint (4, 8) and its two middle nodes (the c13..c16 pair terms of shell 5), so
+    a wrong sign, index or node of any term fails it; the cross stress is checked the same way.
+    Rounding only: 1e-13 of the largest flux."""
+    nx, nz = 40, 36
+    rho, _ = W.disk_packing(nx, nz, 0.55, seed=31, r_mean=5, r_spread=2)
+    x = np.arange(nx)[None, :]
+    z = np.arange(nz)[:, None]
+    rho = rho * (1.0 + 0.05 * np.sin(2 * np.pi * (2 * x / nx + z / nz)))[None]
+    p = dict(W.EMULSION_PARAMS, G_AB=G_AB, tau=(1.0, 0.8))
+    L = _lat(oracle, nx, nz, 2, 0, **p)
+    L.set_fields(rho)
+    L.step(40)
+    r, _, _ = L.fields()
+    sf = L.site_fields()
+    psi, F, sint, P = sf["psi"], sf["F"], sf["sint"], sf["P"]
+    c25, _, _, wsh = oracle.tables()
+    bonds = _bonds(c25, wsh, p["weight_norm"], p, 2)
+    # the cross stress is what P holds beyond the species' own terms (Sec. III's tensor)
+    kin = np.zeros_like(P)
+    for s in range(2):
+        k2 = (p["tau"][s] - 0.5) ** 2
+        kin[0] += CS2 * r[s] + sint[s, 0] + k2 * F[s, 0] ** 2 / r[s]
+        kin[1] += CS2 * r[s] + sint[s, 1] + k2 * F[s, 1] ** 2 / r[s]
+        kin[2] += sint[s, 2] + k2 * F[s, 0] * F[s, 1] / r[s]
+    sab = P - kin
+    groups = [("intra A", lambda k, s: k == "intra" and s == 0, F[0], sint[0]),
+              ("intra B", lambda k, s: k == "intra" and s == 1, F[1], sint[1])]
+    if G_AB:
+        # per species the cross force is not a divergence; their sum is, with the cross stress
+        groups = [("all", lambda k, s: True, F[0] + F[1], sint[0] + sint[1] + sab)]
+    else:
+        assert np.abs(sab).max() < 1e-13
+    for name, sel, Fg, sg in groups:
+        TH, TV = _line_fluxes(bonds, psi, r, sel)
+        scale = max(np.abs(TH).max(), np.abs(TV).max())
+        assert scale > 1e-3, name  # the state is far from uniform
+        tol = 1e-13 * scale
+        for i in range(2):  # force: minus the difference of line fluxes
+            assert np.abs(Fg[i].sum(axis=1) + (TH[i] - np.roll(TH[i], 1))).max() < tol, (name, i)
+            assert np.abs(Fg[i].sum(axis=0) + (TV[i] - np.roll(TV[i], 1))).max() < tol, (name, i)
+        mean = lambda T: 0.5 * (T + np.roll(T, 1))
+        assert np.abs(sg[2].sum(axis=1) - mean(TH[0])).max() < tol, (name, "xz rows")
+        assert np.abs(sg[1].sum(axis=1) - mean(TH[1])).max() < tol, (name, "zz rows")
+        assert np.abs(sg[0].sum(axis=0) - mean(TV[0])).max() < tol, (name, "xx columns")
+        assert np.abs(sg[2].sum(axis=0) - mean(TV[1])).max() < tol, (name, "xz columns")
+        assert np.abs(TH[0]).max() > 1e-3 * scale and np.abs(TV[1]).max() > 1e-3 * scale, name
+
+
+def test_unequal_tau_common_velocity_conserves_momentum(oracle):
+    """Sec. II's shifted-velocity forcing with the common velocity of the mixture (reading: u' =
+    sum_s (j_s/tau_s) / sum_s (rho_s/tau_s)): the collision changes the total momentum at every
+    site by exactly the total force, sum_s F_s, whatever the species' relaxation times.  Streaming
+    only moves populations, so on a periodic lattice the post-collision populations at x are the
+    streamed ones at x + c_l.  Checked site by site after a step from a state whose species move
+    at different velocities, with tau_A != tau_B (a plain barycentric u' breaks the identity by
+    sum_s (1/tau_s)(rho_s u' - j_s), which is nonzero there) and a body force."""
+    nx, nz = 30, 26
+    rho, _ = W.disk_packing(nx, nz, 0.5, seed=41, r_mean=5, r_spread=1)
+    p = dict(W.EMULSION_PARAMS, tau=(0.7, 1.6), body_force=2e-5)
+    L = _lat(oracle, nx, nz, 2, 0, **p)
+    L.set_fields(rho)
+    L.step(30)  # species velocities now differ (different forces per unit mass)
+    c25, cq, _, _ = oracle.tables()
+    cxz = cq.astype(float)
+    r0, _, f0 = L.fields()
+    F = L.site_fields()["F"]
+    j0 = np.einsum("slzx,lk->kzx", f0, cxz)           # total lattice momentum per site
+    ja = np.einsum("lzx,lk->kzx", f0[0], cxz)
+    jb = np.einsum("lzx,lk->kzx", f0[1], cxz)
+    # the species move at different velocities: a barycentric u' would differ from the reading
+    assert np.abs(ja / r0[0] - jb / r0[1]).max() > 1e-4
+    L.step(1)
+    f1 = L.fields()[2]
+    post = np.empty_like(f1)  # f*_l(x) = f_l(x + c_l) after streaming
+    for l in range(9):
+        cx, cz = cq[l]
+        post[:, l] = np.roll(np.roll(f1[:, l], -cz, axis=1), -cx, axis=2)
+    j1 = np.einsum("slzx,lk->kzx", post, cxz)
+    Fs = F.sum(axis=0)
+    scale = np.abs(f0).max()
+    assert np.abs((j1 - j0) - Fs).max() < 1e-14 * scale * 9
+    # and each species keeps its mass at every site through the collision
+    assert np.abs(post.sum(axis=1) - f0.sum(axis=1)).max() < 1e-14 * scale * 9
+    # the lattice total: momentum grows by g sum(rho) per step
+    assert (j1.sum(axis=(1, 2)) - j0.sum(axis=(1, 2)))[0] == pytest.approx(
+        p["body_force"] * r0.sum(), rel=1e-9)
+
+
+def test_sheared_droplet_stress_is_uniform_and_equals_the_wall_stress(oracle):
+    """Sec. IV's fluidity divides the shear rate by the stress; in a channel sheared by its walls
+    the x-momentum of every row is steady, so the x-averaged shear stress must be the same in
+    every row and equal to the stress each wall takes (momentum balance, Eq. MECHANICAL applied
+    across rows).  A droplet of the emulsion sheared between walls at -+U_w (Sec. IV's Couette
+    cells) reaches a steady deformed shape; there the interaction stress (App. A shells and the
+    cross term) carries a sizeable part of the stress in the droplet's rows, so a wrong sign or
+    a dropped part of S_xz (interaction, species drift, forcing) breaks the balance by tens of
+    percent.  Tolerance 1e-5: what is left of the approach to the steady state after 12000 steps
+    (the balance is exact at the steady state)."""
+    nx, nz, R, U = 40, 32, 10.0, 0.01
+    X, Z = np.meshgrid(np.arange(nx), np.arange(nz))
+    s = 0.5 * (1 - np.tanh((np.hypot(X - nx / 2 + 0.5, Z - nz / 2 + 0.5) - R) / 1.5))
+    g = _golden()
+    p = dict(W.EMULSION_PARAMS, G_AB=g["emulsion_GAB"], wall_u=(-U, U))
+    L = _lat(oracle, nx, nz, 2, 1, **p)
+    L.set_fields(np.stack([0.05 + 1.15 * s, 1.2 - 1.15 * s]))
+    L.step(12000)
+    o = L.observables()
+    rho = L.fields()[0]
+    assert rho[0].max() > 1.1 and rho[0].min() < 0.2  # the droplet is still there
+    wb, wt = o["wall_force"]
+    assert wb > 0 and wt == pytest.approx(-wb, rel=1e-6)
+    assert np.abs(o["sxz_z"] / wb - 1.0).max() < 1e-5
+    # the interaction stress in the droplet's rows: a large share of the total
+    sf = L.site_fields()
+    F, sint, P = sf["F"], sf["sint"], sf["P"]
+    k2 = [(t - 0.5) ** 2 for t in p["tau"]]
+    sab = P[2] - sum(sint[q, 2] + k2[q] * F[q, 0] * F[q, 1] / rho[q] for q in range(2))
+    inter = (sint[0, 2] + sint[1, 2] + sab).mean(axis=1)
+    assert np.abs(inter).max() > 0.1 * wb
