@@ -469,10 +469,15 @@ static void cross_stress(const lbmref_ctx *c, int x, int z, double *out) {
    P: pressure tensor of Sec. III, summed over species,
       P_ij = sum_s [c_s^2 rho_s delta_ij + sint_s,ij + (tau_s - 1/2)^2 F_s,i F_s,j / rho_s]
              + sigma^AB_ij.
-   S_xz: shear stress (reading; the paper only names "the stress"):
-      S_xz = -[ sum_s (1 - 1/(2 tau_s)) sum_l (f_l,s - f_eq,l(rho_s, u)) c_lx c_lz
-                + rho u_x u_z ] - [ sum_s sint_s,xz + sigma^AB_xz ],
-      u the barycentric velocity (sum_s j_s + F_s/2) / sum_s rho_s. */
+   S_xz: shear stress (reading; the paper only names "the stress"): minus the xz momentum flux
+      of the lattice, kinetic and interaction,
+      S_xz = -sum_s (1/2) sum_l (f_l,s + g_l,s) c_lx c_lz - [ sum_s sint_s,xz + sigma^AB_xz ],
+      with g the post-collision populations of Eq. LB (collide_site).  The kinetic part is the
+      second moment averaged over the collision: the populations that cross the lattice lines
+      around x are the ones streamed into x (f) and out of x (g), so at a steady state the row
+      sums of S_xz equal the x-momentum that crosses the rows above and below (Eq. MECHANICAL's
+      balance), including the drift of each species and the forcing of Sec. II.
+   u: the barycentric velocity (sum_s j_s + F_s/2) / sum_s rho_s. */
 static void site_stress(const lbmref_ctx *c, int x, int z, double sint[2][3], double P[3],
                         double *Sxz, double u[2]) {
     size_t n = nsites(c), i = site(c, x, z);
@@ -500,15 +505,14 @@ static void site_stress(const lbmref_ctx *c, int x, int z, double sint[2][3], do
     }
     u[0] = mx / rt;
     u[1] = mz / rt;
-    double visc = 0.0, sint_xz = cr[2];
+    double kin = 0.0, sint_xz = cr[2];
     for (int s = 0; s < c->ns; ++s) {
-        double feq[9], m = 0.0;
-        lbmref_feq(c->rho[s * n + i], u[0], u[1], feq);
-        for (int l = 0; l < 9; ++l) m += (pop(c, c->f, s, l)[i] - feq[l]) * CX[l] * CZ[l];
-        visc += (1.0 - 0.5 / c->p.tau[s]) * m;
+        double g[9];
+        collide_site(c, s, i, g);
+        for (int l = 0; l < 9; ++l) kin += 0.5 * (pop(c, c->f, s, l)[i] + g[l]) * CX[l] * CZ[l];
         sint_xz += sint[s][2];
     }
-    *Sxz = -(visc + rt * u[0] * u[1]) - sint_xz;
+    *Sxz = -kin - sint_xz;
 }
 
 int lbmref_site_fields(lbmref_ctx *c, double *psi, double *F, double *sint, double *P,

@@ -274,33 +274,44 @@ LBM_HD T bounce(int l, T g, T rho, T uw) {
 }
 
 // Per-site observables that need the populations (before collision): the barycentric
-// velocity (sum_s j_s + F_s/2) / sum_s rho_s, and the kinetic xz momentum flux
-//   sum_s (1 - 1/(2 tau_s)) sum_l (f_l - feq_l(rho_s, u)) c_lx c_lz + rho u_x u_z,
-// using sum_l feq_l c_lx c_lz = rho_s u_x u_z (the second moment of Sec. II) and that only the
-// diagonal links have c_lx c_lz != 0.
+// velocity (sum_s j_s + F_s/2) / sum_s rho_s, and the kinetic xz momentum flux, the xz second
+// moment averaged over the collision of Eq. LB:
+//   sum_s (1/2) (Pi_s + Pi*_s),  Pi*_s = (1 - omega_s) Pi_s + omega_s rho_s ueq_x ueq_z,
+// i.e. sum_s (1 - omega_s/2) Pi_s + (omega_s/2) rho_s ueq_x ueq_z, where Pi_s = sum_l f_l c_lx c_lz
+// (only the diagonal links have c_lx c_lz != 0; the rest weights cancel, so FP32 deviations
+// give the same) and ueq_s = u' + tau_s F_s / rho_s the velocity of the shifted equilibrium
+// (u' = sum_s omega_s j_s / sum_s omega_s rho_s), whose second moment is rho_s ueq_x ueq_z.
 template <typename T, int NS>
-LBM_HD void site_kinetics(const StepConst<T>& C, const T (&f)[NS][9], const T (&rho)[NS], const T (&jx)[NS],
-                          const T (&jz)[NS], const T (&F)[NS][2], T& ux, T& uz, T& pixz, T& rtot, T& mx, T& mz) {
+LBM_HD void site_kinetics(const StepConst<T>& C, const T (&f)[NS][9], const T (&rho)[NS], const T (&ir)[NS],
+                          const T (&jx)[NS], const T (&jz)[NS], const T (&F)[NS][2], T& ux, T& uz, T& pixz,
+                          T& rtot, T& mx, T& mz) {
     mx = T(0);
     mz = T(0);
     rtot = T(0);
+    T nx_ = T(0), nz_ = T(0), den = T(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         mx += jx[s] + T(0.5) * F[s][0];
         mz += jz[s] + T(0.5) * F[s][1];
         rtot += rho[s];
+        nx_ += C.omega[s] * jx[s];
+        nz_ += C.omega[s] * jz[s];
+        den += C.omega[s] * rho[s];
     }
     const T irt = div_(T(1), rtot);
     ux = mx * irt;
     uz = mz * irt;
-    const T uxz = ux * uz;
-    T visc = T(0);
+    const T iden = div_(T(1), den);
+    const T upx = nx_ * iden, upz = nz_ * iden;
+    pixz = T(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const T m = (f[s][5] + f[s][7]) - (f[s][6] + f[s][8]) - rho[s] * uxz;
-        visc += (T(1) - T(0.5) * C.omega[s]) * m;
+        const T pi = (f[s][5] + f[s][7]) - (f[s][6] + f[s][8]);
+        const T tir = C.tau[s] * ir[s];
+        const T ex = upx + F[s][0] * tir, ez = upz + F[s][1] * tir;
+        const T hom = T(0.5) * C.omega[s];
+        pixz += (T(1) - hom) * pi + hom * rho[s] * ex * ez;
     }
-    pixz = visc + rtot * uxz;
 }
 
 // Index helpers.

@@ -30,6 +30,7 @@ struct PairConst {
     f2 kin;             // (tau - 1/2)^2
     f2 keep;            // 1 - omega
     f2 half_om;         // 1 - omega / 2
+    f2 hom;             // omega / 2
 };
 
 // The pairs from the per-species tables (host).
@@ -53,6 +54,7 @@ inline void fill_pair_const(PairConst& K, const StepConst<float>& C) {
     K.kin = make_float2(C.kin[0], C.kin[1]);
     K.keep = make_float2(1.0f - C.omega[0], 1.0f - C.omega[1]);
     K.half_om = make_float2(1.0f - 0.5f * C.omega[0], 1.0f - 0.5f * C.omega[1]);
+    K.hom = make_float2(0.5f * C.omega[0], 0.5f * C.omega[1]);
 }
 
 // Pseudopotential of Sec. IV for both species: psi = 1 - exp(-rho / rho0) (hardware exp2), or

@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                     const f2 m = fma2(Fx, sp(0.5f), jx), n = fma2(Fz, sp(0.5f), jz);
                     const float mx = m.x + m.y, mz = n.x + n.y, rtot = rh.x + rh.y;
                     const float irt = __fdividef(1.f, rtot);
-                    const float ux = mx * irt, uz = mz * irt, uxz = ux * uz;
+                    const float ux = mx * irt, uz = mz * irt;
                     if (MODE & M_FIELDS) {
                         const long long i = (long long)(zrow0 + z) * nx + x;
                         const long long np = (long long)nx * nz;
@@ -524,9 +524,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                         O.fields[3 * np + i] = (double)uz;
                     }
                     if (MODE & M_OBS) {
-                        const f2 mm = sub2(sub2(add2(fp[5], fp[7]), add2(fp[6], fp[8])), mul2(rh, sp(uxz)));
-                        const f2 v = mul2(K.half_om, mm);
-                        const float pixz = (v.x + v.y) + rtot * uxz;
+                        // xz second moment averaged over the collision (site_kinetics):
+                        // (1 - omega/2) Pi + (omega/2) rho ueq_x ueq_z per species
+                        const f2 pi = sub2(add2(fp[5], fp[7]), add2(fp[6], fp[8]));
+                        const f2 wj = mul2(K.omega, jx), wk = mul2(K.omega, jz), wr = mul2(K.omega, rh);
+                        const float iden = __fdividef(1.f, wr.x + wr.y);
+                        const f2 tir = mul2(K.tau, ir);
+                        const f2 ex = fma2(Fx, tir, sp((wj.x + wj.y) * iden));
+                        const f2 ez = fma2(Fz, tir, sp((wk.x + wk.y) * iden));
+                        const f2 v = fma2(K.half_om, pi, mul2(K.hom, mul2(rh, mul2(ex, ez))));
+                        const float pixz = v.x + v.y;
                         const f2 third = mul2(rh, sp(1.f / 3.f));
                         const f2 kx2 = fma2(mul2(K.kin, mul2(Fx, Fx)), ir, third);
                         const f2 kz2 = fma2(mul2(K.kin, mul2(Fz, Fz)), ir, third);
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 }
                 if (MODE & (M_OBS | M_FIELDS)) {
                     T ux, uz, pixz, rtot, mx, mz;
-                    site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
+                    site_kinetics<T, NS>(C, f, rho, ir, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
                     if (MODE & M_FIELDS) {
                         const long long i = (long long)(zrow0 + z) * nx + x;
                         const long long np = (long long)nx * nz;

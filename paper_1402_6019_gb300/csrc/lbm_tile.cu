@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TPX* TZ, (sizeof(T) == 4 ? 1024 : 512) / (TPX 
         }
         if (MODE & (M_OBS | M_FIELDS)) {
             T ux, uz, pixz, rtot, mx, mz;
-            site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
+            site_kinetics<T, NS>(C, f, rho, ir, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
             if (MODE & M_FIELDS) {
                 const long long i = (long long)z * nx + x;
                 const long long np = (long long)nx * nz;

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(TPX* TPZ) k_twopass(const T* __restrict__ fin,
         }
         if (MODE & M_OBS) {
             T ux, uz, pixz, rtot, mx, mz;
-            site_kinetics<T, NS>(C, f, rho, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
+            site_kinetics<T, NS>(C, f, rho, ir, jx, jz, F, ux, uz, pixz, rtot, mx, mz);
             T pxx = sxx, pzz = szz;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
