@@ -236,8 +236,10 @@ int lbm_abi_version(void);
    LBM_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit, which bounds
    the lattice: bytes needed = r256(nz*ceil(nx/32)*64) + r256(nx*ceil(nz/8)*16)
    + r256((nx+nz)*40) + 256, r256 rounding up to a multiple of 256 (a 1024 x 1024 lattice
-   needs about 4.3 MB).  The first call on a device looks up the array's device address with
-   that device current, so make the first call before any stream capture.  All calls share the
+   needs about 4.3 MB).  A call made outside a stream capture looks up the array's device
+   address with the calling thread's current device (so a device reset is followed); a call
+   made during a capture uses the address of the last lookup on that device, so make the first
+   call on a device before any stream capture.  All calls share the
    array: calls that overlap on the GPU (other streams, other threads) race and must be
    serialised by the caller.  Asynchronous on `stream` (NULL = the default stream).
    Returns LBM_OK, LBM_EINVAL (NULL pointer or invalid description/parameters), LBM_ENOMEM
@@ -291,15 +293,22 @@ int lbm_set_populations(lbm_ctx *c, const double *f, int where);
 
 /* Snapshots (exact checkpoints): lbm_snapshot copies the current state -- the populations in
    the context's internal layout and precision, the step counter and the FP32 reference
-   densities -- into lbm_snapshot_bytes(c) bytes of device memory at dst (asynchronous);
-   lbm_restore makes such a snapshot the current state again, bit for bit, and resets the time
-   averages.  A snapshot is only meaningful to the context that wrote it; the context remembers
-   the step counter and reference densities of the snapshots it wrote (by address), so restoring
-   one of them is asynchronous, while restoring memory it did not write there reads them back
-   from the snapshot (synchronises). */
+   densities -- into lbm_snapshot_bytes(c) bytes of device memory at dst (asynchronous).  The
+   last 256 bytes are a tail that also records the writing context, a sequence number and the
+   shape.  lbm_restore makes the snapshot at src the current state again, bit for bit, and
+   resets the time averages: it reads the tail back (synchronises), so it is right whatever was
+   written at src since, and it returns LBM_EINVAL when src holds no snapshot of a context of
+   this shape and precision.
+   lbm_restore_own is the asynchronous form for a snapshot this context wrote at src with its
+   last lbm_snapshot there: the step counter and reference densities come from the context's
+   record of that call (it keeps the latest 1024 addresses; other addresses fall back to
+   lbm_restore), and a one-thread kernel compares the tail's writer and sequence number with
+   the record.  If src was overwritten since (the buffer freed and reused, another snapshot),
+   the next synchronising call returns LBM_EINVAL and the restored state must not be used. */
 long long lbm_snapshot_bytes(const lbm_ctx *c);
 int lbm_snapshot(lbm_ctx *c, void *dst);
 int lbm_restore(lbm_ctx *c, const void *src);
+int lbm_restore_own(lbm_ctx *c, const void *src);
 
 /* The current state as populations after streaming, f [n_species][9][nz][nx] in device memory,
    double (LBM_FP64) or float (LBM_FP32) values: lbm_get_fields without the synchronisation and

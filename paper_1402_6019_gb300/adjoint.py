@@ -9,7 +9,7 @@ G1 A, G1 B, G2 A, G2 B, G_AB, tau A, tau B, body_force.
 
 The backward sweep needs every state f_n in reverse order.  Storing them all takes
 steps x 9 ns nx nz values, so the forward keeps an exact snapshot every `checkpoint` steps and
-the backward recomputes one segment at a time from its snapshot (lbm_restore, then
+the backward recomputes one segment at a time from its snapshot (lbm_restore_own, then
 lbm_record_states), sweeping it back with lbm_adjoint_steps: device memory for
 ceil(steps / checkpoint) snapshots and `checkpoint` recorded states, and one extra forward run.
 
@@ -101,7 +101,7 @@ class Run:
         _handoff(lam.device)
         for k in reversed(range(len(self.snaps))):
             n = min(self.checkpoint, self.steps - k * self.checkpoint)
-            L.lbm_restore(lat.h, self.snaps[k])
+            L.lbm_restore_own(lat.h, self.snaps[k])
             L.lbm_record_states(lat.h, n, seg)
             L.lbm_adjoint_steps(lat.h, n, seg, lam, grad)
         g_rho = torch.empty((lat.ns, lat.nz, lat.nx), dtype=torch.float64, device=lam.device)

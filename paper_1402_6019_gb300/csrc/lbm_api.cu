@@ -4,11 +4,13 @@
 // tables of the kernels, and enqueues the kernels on the context's stream.  Every entry
 // point returns a status; nothing throws across the ABI.
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <new>
@@ -20,6 +22,19 @@
 #include "lbm_internal.h"
 
 using namespace lbm;
+
+// The 256-byte tail of a snapshot: the reference densities of the FP32 deviations, the step
+// counter, the writer's tag (context serial << 32 | snapshot sequence number) and the shape the
+// populations were written for.
+struct SnapTail {
+    double rho_ref[2];
+    long long step;
+    unsigned long long tag;
+    int nx, nz, ns, precision, n_inst, pad;
+};
+static_assert(sizeof(SnapTail) <= 256, "snapshot tail");
+static std::atomic<unsigned> g_ctx_serial{0};
+static const size_t SNAP_CACHE_MAX = 1024;  // remembered snapshot tails per context
 
 struct lbm_ctx {
     lbm_desc d{};
@@ -90,8 +105,10 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<cudaEvent_t> aev;  // adjoint: three pairs per step, around its kernels
     size_t aev_used = 0;
-    std::map<const void*, std::pair<std::array<double, 2>, long long>> snaps;  // tails of this
-                                   // context's snapshots (rho_ref, step), by address
+    unsigned serial = 0;           // this context's number among the contexts of the process
+    unsigned snap_seq = 0;         // snapshots written so far
+    std::map<const void*, SnapTail> snaps;  // tails of this context's latest snapshots, by address
+    std::vector<const void*> snap_order;    // their addresses, oldest first (bounds the map)
     cudaEvent_t tev[64] = {};      // asynchronous reads: an event per ticket (ring)
     long long tickets = 0;         // tickets issued
     std::string err;
@@ -283,6 +300,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
     c->d = *d;
+    c->serial = ++g_ctx_serial;
     lbm_default_params(&c->p);
     auto bail = [&](int code) {
         g_create_error = c->err;
@@ -773,15 +791,24 @@ extern "C" int lbm_set_populations(lbm_ctx* c, const double* f, int where) {
     return LBM_OK;
 }
 
-// A snapshot: the current population buffer in the internal layout, then a 256-byte tail with
-// the reference densities of the FP32 deviations and the step counter.
-struct SnapTail {
-    double rho_ref[2];
-    long long step;
-};
+// A snapshot: the current population buffer in the internal layout, then a 256-byte tail (SnapTail).
 static size_t pop_bytes(const lbm_ctx* c) { return (size_t)c->d.n_species * 9 * c->plane * c->esize; }
 
 extern "C" long long lbm_snapshot_bytes(const lbm_ctx* c) { return c ? (long long)(pop_bytes(c) + 256) : -1; }
+
+static SnapTail make_tail(const lbm_ctx* c, unsigned long long tag) {
+    SnapTail t{};
+    t.rho_ref[0] = c->rho_ref[0];
+    t.rho_ref[1] = c->rho_ref[1];
+    t.step = c->step;
+    t.tag = tag;
+    t.nx = c->d.nx;
+    t.nz = c->d.nz;
+    t.ns = c->d.n_species;
+    t.precision = c->d.precision;
+    t.n_inst = (int)c->inst.size();
+    return t;
+}
 
 extern "C" int lbm_snapshot(lbm_ctx* c, void* dst) {
     if (!c) return LBM_EINVAL;
@@ -789,29 +816,23 @@ extern "C" int lbm_snapshot(lbm_ctx* c, void* dst) {
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
     CK(cudaSetDevice(c->d.device));
     CK(cudaMemcpyAsync(dst, c->f[c->cur], pop_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-    const SnapTail t{{c->rho_ref[0], c->rho_ref[1]}, c->step};
+    const SnapTail t = make_tail(c, (unsigned long long)c->serial << 32 | ++c->snap_seq);
     // pageable source: staged before the call returns
     CK(cudaMemcpyAsync(static_cast<char*>(dst) + pop_bytes(c), &t, sizeof t, cudaMemcpyHostToDevice, c->stream));
-    c->snaps[dst] = {{t.rho_ref[0], t.rho_ref[1]}, t.step};  // a restore from here needs no read-back
+    // remembered for lbm_restore_own; the oldest entry goes when the map is full
+    if (c->snaps.find(dst) == c->snaps.end()) {
+        if (c->snap_order.size() >= SNAP_CACHE_MAX) {
+            c->snaps.erase(c->snap_order.front());
+            c->snap_order.erase(c->snap_order.begin());
+        }
+        c->snap_order.push_back(dst);
+    }
+    c->snaps[dst] = t;
     return LBM_OK;
 }
 
-extern "C" int lbm_restore(lbm_ctx* c, const void* src) {
-    if (!c) return LBM_EINVAL;
-    if (!src) return fail(c, LBM_EINVAL, "src is NULL");
-    CK(cudaSetDevice(c->d.device));
-    SnapTail t;
-    const auto known = c->snaps.find(src);
-    const bool async = known != c->snaps.end();
-    if (async) {  // a snapshot this context wrote: its tail is known on the host
-        t.rho_ref[0] = known->second.first[0];
-        t.rho_ref[1] = known->second.first[1];
-        t.step = known->second.second;
-    } else {
-        CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + pop_bytes(c), sizeof t, cudaMemcpyDeviceToHost,
-                           c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-    }
+// Makes the populations at src and the tail t the current state (in stream order).
+static int restore_from(lbm_ctx* c, const void* src, const SnapTail& t, bool check_tag) {
     CK(cudaMemcpyAsync(c->f[0], src, pop_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
     if (t.rho_ref[0] != c->rho_ref[0] || t.rho_ref[1] != c->rho_ref[1]) {
         c->rho_ref[0] = t.rho_ref[0];
@@ -821,13 +842,45 @@ extern "C" int lbm_restore(lbm_ctx* c, const void* src) {
     }
     c->cur = 0;
     CK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    if (check_tag) {
+        CK(launch_snap_check(static_cast<const unsigned long long*>(
+                                 static_cast<const void*>(static_cast<const char*>(src) + pop_bytes(c) +
+                                                          offsetof(SnapTail, tag))),
+                             t.tag, c->flag, c->stream));
+        c->launches += 1;
+    }
     CK(cudaMemsetAsync(c->avg, 0, obs_bytes(c), c->stream));
     c->samples = 0;
     c->pending = false;
-    if (!async) CK(cudaStreamSynchronize(c->stream));
     c->step = t.step;
     c->have_fields = true;
     return LBM_OK;
+}
+
+extern "C" int lbm_restore(lbm_ctx* c, const void* src) {
+    if (!c) return LBM_EINVAL;
+    if (!src) return fail(c, LBM_EINVAL, "src is NULL");
+    CK(cudaSetDevice(c->d.device));
+    SnapTail t;
+    CK(cudaMemcpyAsync(&t, static_cast<const char*>(src) + pop_bytes(c), sizeof t, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (t.nx != c->d.nx || t.nz != c->d.nz || t.ns != c->d.n_species || t.precision != c->d.precision ||
+        t.n_inst != (int)c->inst.size() || (t.tag >> 32) == 0)
+        return fail(c, LBM_EINVAL, "src holds no snapshot of a context of this shape and precision");
+    const int rc = restore_from(c, src, t, false);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+extern "C" int lbm_restore_own(lbm_ctx* c, const void* src) {
+    if (!c) return LBM_EINVAL;
+    if (!src) return fail(c, LBM_EINVAL, "src is NULL");
+    const auto known = c->snaps.find(src);
+    if (known == c->snaps.end()) return lbm_restore(c, src);
+    CK(cudaSetDevice(c->d.device));
+    return restore_from(c, src, known->second, true);
 }
 
 extern "C" int lbm_export_state(lbm_ctx* c, void* f, int precision) {
@@ -1128,6 +1181,9 @@ extern "C" int lbm_synchronize(lbm_ctx* c) {
     CK(cudaStreamSynchronize(c->stream));
     int flag = 0;
     CK(cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 4)
+        return fail(c, LBM_EINVAL, "a snapshot restored by lbm_restore_own had been overwritten since this "
+                                   "context wrote it: the restored state is not valid");
     if (flag & 2) return fail(c, LBM_ETIMEOUT, "a bounded device-side wait for a tile load gave up");
     if (flag & 1) return fail(c, LBM_ENONFINITE, "a step met a density <= 0, NaN or Inf");
     return LBM_OK;

@@ -204,6 +204,10 @@ int reduce_blocks(int nx, int nz);
 // Writes the trailer of an asynchronous read (samples, step, averages, 0: four 8-byte words) at
 // dst, in device memory, in stream order.
 cudaError_t launch_obs_trailer(double* dst, double samples, long long step, long long averages, cudaStream_t st);
+// Sets bit 4 of *flag when the 8-byte tag at `tag` is not `expected` (a snapshot restored from
+// the host's record of it had been overwritten since).
+cudaError_t launch_snap_check(const unsigned long long* tag, unsigned long long expected, int* flag,
+                              cudaStream_t st);
 cudaError_t launch_reduce(int precision_bytes, const ObsPtrs& O, int nxpart, int nzpart, int nx, int nz, int zbc,
                           unsigned* ticket, double* out, double* avg, double* bpart, double* bavg, int accumulate,
                           bool tail, const InstGeom* inst, int ninst, cudaStream_t st);

@@ -204,6 +204,18 @@ cudaError_t launch_obs_trailer(double* dst, double samples, long long step, long
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_snap_check(const unsigned long long* tag, unsigned long long expected, int* flag) {
+    if (*tag != expected) atomicOr(flag, 4);
+}
+}  // namespace
+
+cudaError_t launch_snap_check(const unsigned long long* tag, unsigned long long expected, int* flag,
+                              cudaStream_t st) {
+    k_snap_check<<<1, 1, 0, st>>>(tag, expected, flag);
+    return cudaGetLastError();
+}
+
 int reduce_blocks(int nx, int nz) {
     return (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32) + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
 }

@@ -89,6 +89,7 @@ SIGNATURES = {
     "lbm_snapshot_bytes": (ctypes.c_longlong, [_VP]),
     "lbm_snapshot": (ctypes.c_int, [_VP, _VP]),
     "lbm_restore": (ctypes.c_int, [_VP, _VP]),
+    "lbm_restore_own": (ctypes.c_int, [_VP, _VP]),
     "lbm_export_state": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "lbm_record_states": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
     "lbm_adjoint_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
@@ -299,7 +300,14 @@ def lbm_snapshot(h, dst):
 
 
 def lbm_restore(h, src):
+    """Restores the snapshot in the CUDA tensor src (reads its tail back: synchronises)."""
     _check(load().lbm_restore(h, _dev(src)), h)
+
+
+def lbm_restore_own(h, src):
+    """Asynchronous restore of the snapshot this context last wrote into src; an overwritten
+    src is reported by the next synchronising call."""
+    _check(load().lbm_restore_own(h, _dev(src)), h)
 
 
 def lbm_export_state(h, f):

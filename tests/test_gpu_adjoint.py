@@ -137,6 +137,57 @@ def test_snapshot_restores_exactly(oracle, precision):
     assert np.array_equal(lat.fields()[2], a) and lat.observables()["step"] == step_a
 
 
+@pytest.mark.parametrize("precision", [L.LBM_FP64, L.LBM_FP32])
+def test_restore_after_the_snapshot_buffer_was_reused(precision):
+    """A snapshot buffer that another snapshot overwrote at the same address (as when a freed
+    buffer's memory is handed to a new one): lbm_restore gives the new snapshot's state, step
+    counter and reference densities; lbm_restore_own, which trusts the context's record of what
+    it wrote there, reports the overwrite at the next synchronisation instead of going on."""
+    ns, prm, nx, nz = CASES[0]
+    rho = W.noise_field(nx, nz, seed=72, mean=0.7, amp=0.3, n_species=ns)
+    a = L.Lattice(nx, nz, ns, precision, L.LBM_PERIODIC, **prm)
+    b = L.Lattice(nx, nz, ns, precision, L.LBM_PERIODIC, **prm)
+    a.set_fields(rho)
+    b.set_fields(rho * 1.2)  # FP32: other reference densities
+    a.step(4)
+    b.step(9)
+    snap = torch.empty(L.lbm_snapshot_bytes(a.h), dtype=torch.uint8, device="cuda")
+    L.lbm_snapshot(a.h, snap)
+    a.synchronize()
+    L.lbm_snapshot(b.h, snap)  # same address, another context's snapshot
+    b.synchronize()
+    want = b.fields()[2]
+    L.lbm_restore(a.h, snap)
+    assert a.observables()["step"] == 9
+    assert np.array_equal(a.fields()[2], want)
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.fields()[2], b.fields()[2])
+    # the record-trusting form notices that the tail is not the one this context wrote
+    L.lbm_snapshot(a.h, snap)
+    a.synchronize()
+    L.lbm_snapshot(b.h, snap)
+    b.synchronize()
+    L.lbm_restore_own(a.h, snap)
+    with pytest.raises(L.LbmError) as e:
+        a.synchronize()
+    assert e.value.code == L.LBM_EINVAL
+    # an untouched snapshot of its own restores asynchronously and exactly
+    a.set_fields(rho)
+    a.step(2)
+    L.lbm_snapshot(a.h, snap)
+    f2 = a.fields()[2]
+    a.step(5)
+    L.lbm_restore_own(a.h, snap)
+    a.synchronize()
+    assert np.array_equal(a.fields()[2], f2) and a.observables()["step"] == 2
+    # memory that holds no snapshot of this shape is refused
+    junk = torch.zeros_like(snap)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_restore(a.h, junk)
+    assert e.value.code == L.LBM_EINVAL
+
+
 @pytest.mark.parametrize("ns", [1, 2])
 def test_objective_matches_oracle(oracle, ns):
     nx, nz = 45, 21
