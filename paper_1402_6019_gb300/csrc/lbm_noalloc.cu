@@ -9,6 +9,8 @@
 // in one file-scope device array of fixed size, LBM_NOALLOC_SCRATCH_BYTES, which each GPU
 // that loads the library holds until the process exits.  The caller passes the populations
 // and the output buffer.
+#include <atomic>
+
 #include "lbm.h"
 #include "lbm_consts.h"
 #include "lbm_internal.h"
@@ -22,7 +24,9 @@ namespace {
 static __device__ __align__(256) unsigned char g_scratch[LBM_NOALLOC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-void* g_scratch_ptr[MAX_DEVICES] = {nullptr};  // device address of g_scratch per device
+// device address of g_scratch per device, as last looked up (kept for calls made during a
+// stream capture, when no lookup is made)
+std::atomic<void*> g_scratch_ptr[MAX_DEVICES];
 
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
@@ -46,12 +50,19 @@ extern "C" int lbm_observables_noalloc(const double* f, int nx, int nz, int n_sp
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return LBM_ECUDA;
-    if (!g_scratch_ptr[dev]) {  // set-up, once per device, with that device current
-        void* ptr = nullptr;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The array's device address, looked up with this device current.  It is looked up again on
+    // every call made outside a stream capture, so a device reset (which reloads the module at
+    // another address) is followed; during a capture the address of the last lookup is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return LBM_ECUDA;
+    void* ptr = g_scratch_ptr[dev].load();
+    if (cap == cudaStreamCaptureStatusNone || !ptr) {
+        ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return LBM_ECUDA;
-        g_scratch_ptr[dev] = ptr;
+        g_scratch_ptr[dev].store(ptr);
     }
-    unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    unsigned char* base = static_cast<unsigned char*>(ptr);
     ObsPtrs O;
     O.part_row = base;
     O.part_col = base + b_row;
@@ -64,7 +75,6 @@ extern "C" int lbm_observables_noalloc(const double* f, int nx, int nz, int n_sp
     StepConst<double> C;
     const double rr[2] = {0.0, 0.0};  // plain FP64 populations
     fill_step_const<double>(C, *p, nx, nz, nx, (long long)nx * nz, n_species, z_boundary, rr);
-    const cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: the ticket and the flag must start at zero
     cudaError_t e = cudaMemsetAsync(walls, 0, b_small, st);
     if (e == cudaSuccess) e = launch_tile<double>(n_species, M_OBS, TPZ, f, nullptr, C, O, st);
