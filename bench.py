@@ -84,23 +84,82 @@ def _dist():
     return r.rank, r.world, r.local
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, power, clock event reasons);
+    nothing is set."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake"}
+
+    def __init__(self, index, pci_bus_id=None):
+        import ctypes
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        ok = False
+        if pci_bus_id:
+            ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), ctypes.byref(self.h)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+
+    def sample(self):
+        ct = self.ct
+        clk, pw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) != 0:  # NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(pw))
+        self.reasons_fn(self.h, ct.byref(rs))
+        return (time.perf_counter(), float(clk.value), pw.value / 1000.0, int(rs.value))
+
+
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clocks and clock event reasons during the timed region: NVML read every millisecond by
+    a thread (so a region of a few milliseconds still has samples), plus one read right before
+    and one right after the region; nvidia-smi sampling every 50 ms where NVML cannot be loaded.
+    Read-only: no clock, power or other setting is changed."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    # where the raw samples go (--clocks-csv); by default a temporary file, since the JSON line
-    # carries their summary
+    # where the raw nvidia-smi samples go (--clocks-csv); by default a temporary file
     csv_path = None
 
-    def __init__(self, index):
+    def __init__(self, index, pci_bus_id=None):
         self.index = index
         self.proc = None
+        self.nvml = None
+        self.samples = []
+        self.edges = []
+        try:
+            self.nvml = _Nvml(index, pci_bus_id)
+        except (OSError, AttributeError):
+            self.nvml = None
         self.path = Clocks.csv_path or os.path.join(tempfile.gettempdir(), f"lbm_clocks_{os.getpid()}.csv")
 
+    def _poll(self):
+        while not self.stop.is_set():
+            smp = self.nvml.sample()
+            if smp:
+                self.samples.append(smp)
+            self.stop.wait(0.001)
+
     def __enter__(self):
+        if self.nvml:
+            import threading
+
+            self.edges.append(self.nvml.sample())
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
         try:
             if os.path.dirname(self.path):
                 os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -113,6 +172,11 @@ class Clocks:
         return self
 
     def __exit__(self, *a):
+        if self.nvml:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            self.edges.append(self.nvml.sample())
+            return
         if self.proc:
             self.proc.terminate()
             try:
@@ -122,6 +186,17 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        if self.nvml:
+            rows = [r for r in self.samples if r]
+            edges = [r for r in self.edges if r]
+            allr = rows or edges
+            if not allr:
+                return None
+            reasons = sorted({name for r in allr + edges for bit, name in _Nvml.REASONS.items() if r[3] & bit})
+            return {"sm_mhz": float(np.median([r[1] for r in allr])), "sm_max_mhz": self.nvml.max_mhz,
+                    "reasons": reasons, "samples": len(rows),
+                    "sm_mhz_before_after": [r[1] for r in edges], "power_w_max": max(r[2] for r in allr),
+                    "source": "NVML every 1 ms during the timed region, and once right before and after it"}
         if not self.proc:
             return None
         rows = []
@@ -137,7 +212,17 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
         return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi every 50 ms"}
+
+
+def _pci_bus_id(local):
+    try:
+        import torch
+
+        p = torch.cuda.get_device_properties(local)
+        return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+    except Exception:
+        return None
 
 
 def _peaks():
@@ -182,10 +267,16 @@ def oracle_sample(w, n=256):
     return np.ascontiguousarray(w["rho"][:, :n, :n]), dict(w["params"])
 
 
-def cpu_baseline(w, seconds=12.0):
+def cpu_baseline(w, seconds=12.0, lib_run=None, tol=1e-4, err_steps=1000):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
     whole oracle steps (step + observables, like the GPU step) on a 256 x 256 lattice cut from
-    the same workload, until `seconds` of wall time have passed."""
+    the same workload, until `seconds` of wall time have passed.
+
+    With `lib_run`, the same oracle run then goes on (untimed, without observables) to
+    `err_steps` steps, and the library's run of the same cut over as many steps (observables every
+    step) is compared with it: the state (rho, u) and every observable, each as its largest error
+    relative to the oracle's largest value, and as a fraction of the bound the state contract
+    `tol` allows it (paper_1402_6019_gb300.accuracy)."""
     import oracle
 
     oracle.build()
@@ -203,9 +294,30 @@ def cpu_baseline(w, seconds=12.0):
             break
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(n * rho.shape[1] * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{k} oracle steps (step + observables) on a {n}x{n} cut of the workload, "
-                      f"{dt:.1f} s wall, OpenMP threads={cores}"}
+    out = {"value": round(n * rho.shape[1] * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{k} oracle steps (step + observables) on a {n}x{n} cut of the workload, "
+                     f"{dt:.1f} s wall, OpenMP threads={cores}"}
+    if lib_run is None:
+        return out, None
+    from paper_1402_6019_gb300 import accuracy
+
+    steps = max(err_steps, k)
+    ref.step(steps - k)
+    r_rho, r_u, _ = ref.fields()
+    r_obs = ref.observables()
+    g_rho, g_u, g_obs = lib_run(rho, prm, steps)
+    rel = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    errs = accuracy.observable_errors(g_obs, r_obs, ref.scales(), tol, n, float(np.sum(r_obs["mass"])))
+    errors = {"vs": "FP64 oracle", "sample": f"{n}x{rho.shape[1]} cut of the workload, {steps} steps, "
+                                             "observables every step (the library's launch configuration)",
+              "tol": tol, "rho": rel(g_rho, r_rho), "u": rel(g_u, r_u),
+              "observables": {k_: {"rel": round(e[2], 9), "of_bound": round(e[0] / e[1], 6) if e[1] > 0 else None}
+                              for k_, e in errs.items()},
+              "rel": "largest |library - oracle| / largest |oracle| of each quantity",
+              "of_bound": "largest error / the bound the state contract allows (tol x the magnitude of the "
+                          "terms the observable is formed from)",
+              "within_bounds": not accuracy.check(errs) and rel(g_rho, r_rho) <= tol and rel(g_u, r_u) <= tol}
+    return out, errors
 
 
 def run_reference(a, w):
@@ -369,7 +481,7 @@ def run_adjoint(a, w):
         return float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
 
     launches0 = lat.launches
-    with Clocks(local) as clk:
+    with Clocks(local, _pci_bus_id(local)) as clk:
         grad_ms = timed(False)
     launches = lat.launches - launches0
     # the same gradients again with every step-kernel and adjoint-kernel launch bracketed by
@@ -537,7 +649,7 @@ def main():
 
     launches0 = sum(lt.launches for lt in lats)
     barrier()
-    with Clocks(local) as clk:
+    with Clocks(local, _pci_bus_id(local)) as clk:
         step_ms = timed()
     launches = sum(lt.launches for lt in lats) - launches0
     # the same steps again with CUDA events around every step-kernel launch (which serialises the
@@ -652,7 +764,17 @@ def main():
         "clocks": clk.summary(),
     }
     if world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        def lib_run(rho_cut, prm, steps):
+            lt = L.Lattice(rho_cut.shape[2], rho_cut.shape[1], ns, prec, w["z_boundary"], device=local,
+                           stream=stream.cuda_stream, **prm)
+            lt.set_fields(rho_cut)
+            lt.set_observe(1)
+            lt.step(steps)
+            g_rho, g_u, _ = lt.fields(populations=False)
+            return g_rho, g_u, lt.observables()
+
+        line["cpu_baseline"], errors = cpu_baseline(w, lib_run=lib_run, tol=1e-4 if a.precision == "fp32" else 1e-12)
+        line["errors"] = errors
     print(json.dumps(line))
 
 

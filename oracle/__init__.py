@@ -221,6 +221,19 @@ class RefLattice:
                                            _ptr(out["sxz"])) == 0
         return out
 
+    def scales(self):
+        """Magnitudes the observables of the current state are formed from (for stating errors):
+        rho_max = max rho; u_max = max |u| (barycentric); pop_scale = max over sites of
+        sum_s sum_l |f_l c_l| / sum_s rho_s (the terms a velocity is a difference of);
+        stress_scale = max over sites of |P_xx| + |P_zz| + 2 |P_xz| (Sec. III's tensor: the terms
+        S_xz, p_s and P_xx are sums and differences of)."""
+        rho, u, f = self.fields()
+        P = self.site_fields()["P"]
+        c = np.array([0, 1, 1, 1, 1, 1, 1, 1, 1], float)
+        return dict(rho_max=float(np.abs(rho).max()), u_max=float(np.abs(u).max()),
+                    pop_scale=float(((np.abs(f) * c[None, :, None, None]).sum(axis=(0, 1)) / rho.sum(0)).max()),
+                    stress_scale=float((np.abs(P[0]) + np.abs(P[1]) + 2 * np.abs(P[2])).max()))
+
     def adjoint_step(self, lam_next, grad=None):
         """dJ/df_n from dJ/df_{n+1} at the current state (periodic lattices); adds the
         parameter derivatives to grad (G1 A, B; G2 A, B; G_AB; tau A, B; body_force)."""

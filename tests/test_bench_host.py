@@ -16,6 +16,7 @@ def _clocks_from(tmp_path, lines):
     p = tmp_path / "clocks.csv"
     p.write_text("".join(line + "\n" for line in lines))
     c = bench.Clocks(0)
+    c.nvml = None  # the nvidia-smi path
     c.path = str(p)
     c.proc = object()  # as if nvidia-smi had run
     return c.summary()
@@ -38,6 +39,35 @@ def test_clock_summary_ignores_malformed_lines(tmp_path):
                                 "0, 2070, 2070, 1, 0x0, Not Active, Not Active, Not Active, Not Active"])
     assert s["samples"] == 1 and s["reasons"] == []
     assert _clocks_from(tmp_path, ["garbage"]) is None
+
+
+class _FakeNvml:
+    """Stands in for the NVML reader: replays (time, SM MHz, W, reason bits) samples."""
+    max_mhz = 2070.0
+
+    def __init__(self, rows):
+        self.rows = list(rows)
+
+    def sample(self):
+        return self.rows.pop(0) if self.rows else None
+
+
+def test_nvml_clock_summary_reasons_and_edges():
+    c = bench.Clocks(0)
+    c.nvml = _FakeNvml([(0.0, 2070.0, 300.0, 0x0)])
+    c.edges = [c.nvml.sample()]
+    c.samples = [(0.001, 2055.0, 1200.0, 0x1), (0.002, 2070.0, 1390.0, 0x4), (0.003, 2040.0, 1300.0, 0x0)]
+    c.edges.append((0.004, 2070.0, 400.0, 0x0))
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["samples"] == 3 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]  # GPU-idle (0x1) is not a slowdown
+    assert s["sm_mhz_before_after"] == [2070.0, 2070.0] and s["power_w_max"] == 1390.0
+    c.samples.append((0.005, 1500.0, 700.0, 0x8 | 0x40))
+    assert c.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+    # a region too short for the thread still reports the reads before and after it
+    c.samples = []
+    s = c.summary()
+    assert s["samples"] == 0 and s["sm_mhz"] == 2070.0
 
 
 def test_traffic_only_for_the_same_kernel_source(tmp_path, monkeypatch):
