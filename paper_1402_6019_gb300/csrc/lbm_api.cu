@@ -110,6 +110,7 @@ struct lbm_ctx {
     std::map<const void*, SnapTail> snaps;  // tails of this context's latest snapshots, by address
     std::vector<const void*> snap_order;    // their addresses, oldest first (bounds the map)
     cudaEvent_t tev[64] = {};      // asynchronous reads: an event per ticket (ring)
+    double* rec_dst = nullptr;     // lbm_step_read: where the next launch's folded sample goes
     long long tickets = 0;         // tickets issued
     std::string err;
 };
@@ -525,12 +526,18 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
             Rd.part_row = c->part_row[c->pending_buf];
             Rd.part_col = c->part_col[c->pending_buf];
             Rd.out = c->out;
-            Rd.avg = c->avg;
             Rd.bpart = c->out + ol;
-            Rd.bavg = c->avg + ol;
             Rd.nxpart = (c->d.nx + TPX - 1) / TPX;
             Rd.nzpart = c->ntz_all;
-            Rd.accumulate = c->pending_acc ? 1 : 0;
+            if (c->rec_dst && c->pending_acc) {  // the sample goes into a record of its own
+                Rd.avg = c->rec_dst;
+                Rd.bavg = c->rec_dst + ol;
+                Rd.accumulate = 2;
+            } else {
+                Rd.avg = c->avg;
+                Rd.bavg = c->avg + ol;
+                Rd.accumulate = c->pending_acc ? 1 : 0;
+            }
             Rd.enabled = 1;
             // the reciprocals in the populations' precision, as the reduction kernel takes them
             Rd.inx = c->esize == 4 ? (double)(1.0f / (float)c->d.nx) : 1.0 / c->d.nx;
@@ -1137,18 +1144,59 @@ extern "C" int lbm_observables_enqueue(lbm_ctx* c, void* dst, int averages, int 
     return LBM_OK;
 }
 
+// Where the device can write the host memory at p (pinned or registered): its device address,
+// or null (pageable memory, device memory, unknown pointers).
+static double* host_record_ptr(void* p) {
+    cudaPointerAttributes pa{};
+    const cudaError_t e = cudaPointerGetAttributes(&pa, p);
+    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    if (e != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) return nullptr;
+    return static_cast<double*>(pa.devicePointer);
+}
+
 extern "C" int lbm_step_read(lbm_ctx* c, int nsteps, void* dst, long long stride, int averages, int reset,
                              long long* ticket) {
     if (!c) return LBM_EINVAL;
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
     if (!dst && nsteps > 0) return fail(c, LBM_EINVAL, "dst is NULL");
     if (stride < lbm_observables_bytes(c)) return fail(c, LBM_EINVAL, "stride is below lbm_observables_bytes");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    CK(cudaSetDevice(c->d.device));
+    // Every step samples and every record holds the one completed sample (averages = 2 with
+    // reset): each launch's folded reduction writes the sample it completes straight into that
+    // step's record in pinned host memory, so no copy or reset runs between two step kernels.
+    // The time sums stay cleared and keep only the sample still pending, as the plain path
+    // leaves them.  The first step takes the plain path when the sums hold more than that.
+    double* const dev_dst = (c->pull && averages == 2 && reset && c->observe_every == 1 && !c->profiling)
+                                ? host_record_ptr(dst) : nullptr;
+    const size_t ob = (size_t)obs_bytes(c);
     for (int i = 0; i < nsteps; ++i) {
+        char* const rec = static_cast<char*>(dst) + (long long)i * stride;
+        const bool held = c->pending && c->pending_acc;
+        if (dev_dst && (c->samples == (held ? 1 : 0))) {
+            if (!held) memset(rec, 0, ob);  // no sample completes in this launch
+            const ObsTrailer t{held ? 1.0 : 0.0, c->step + 1, 1, 0};
+            memcpy(rec + ob, &t, sizeof t);
+            c->rec_dst = reinterpret_cast<double*>(reinterpret_cast<char*>(dev_dst) + (long long)i * stride);
+            const cudaError_t e = enqueue_pass(c, c->cur, M_WRITE | M_OBS, true, true, true);
+            c->rec_dst = nullptr;
+            CK(e);
+            c->samples = 1;  // the sample of this step, pending; the one before went into the record
+            c->cur ^= 1;
+            c->step += 1;
+            continue;
+        }
         const int rc = lbm_step(c, 1);
         if (rc != LBM_OK) return rc;
-        const int rr = lbm_observables_enqueue(c, static_cast<char*>(dst) + (long long)i * stride, averages, reset,
-                                               ticket);
+        const int rr = lbm_observables_enqueue(c, rec, averages, reset, ticket);
         if (rr != LBM_OK) return rr;
+    }
+    if (dev_dst && nsteps > 0) {  // one event for the run: its last record
+        cudaEvent_t& e = c->tev[c->tickets % 64];
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaEventRecord(e, c->stream));
+        if (ticket) *ticket = c->tickets;
+        c->tickets += 1;
     }
     return LBM_OK;
 }

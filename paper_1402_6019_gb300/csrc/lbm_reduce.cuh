@@ -70,6 +70,9 @@ template <> struct Red<float> {
 // (gamma) into one partial, stored after the profiles (and added to its own time sum).  The
 // sum over blocks is left to the reader (the host sums the block partials in FP64), except
 // with TAIL, where the last block to finish writes the scalars into `out` on the device.
+// accumulate: 0 = `out` and `bpart` only; 1 = also add the sample to the time sums `avg` and
+// `bavg`; 2 = also write the sample into `avg` and `bavg` in place of what they held (a record
+// of this one sample, with its bad-density flag).
 // Group sums within a row or a column stay in the populations' precision PT; time sums and
 // block partials use the accumulators above.  Fixed summation order: repeatable results.
 // inst / ninst: the lattices of a stacked batch (rows of different lattices are not neighbours);
@@ -94,7 +97,10 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
     if (blk == 0 && t == 0) {  // the step kernels' flag of a bad density
         const bool bad = (flag[0] & 1) != 0;
         R::put(out, O_BAD, R::from(bad ? PT(1) : PT(0)));
-        if (accumulate && bad) R::put(avg, O_BAD, R::from(PT(1)));
+        if (accumulate == 2)
+            R::put(avg, O_BAD, R::from(bad ? PT(1) : PT(0)));
+        else if (accumulate && bad)
+            R::put(avg, O_BAD, R::from(PT(1)));
     }
     if (blk < nrowblocks) {
         const int z = blk * WPB + warp;
@@ -154,8 +160,8 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
                 v[NQR] += prow[((long long)zl * nxpart + p) * NQR + QR_UX];
                 v[NQR + 1] += prow[((long long)zr * nxpart + p) * NQR + QR_UX];
             }
-            const A old = (accumulate && oi >= 0) ? R::get(avg, oi) : R::zero();  // in flight with the sums
-            const A old2 = (accumulate && oi2 >= 0) ? R::get(avg, oi2) : R::zero();
+            const A old = (accumulate == 1 && oi >= 0) ? R::get(avg, oi) : R::zero();  // in flight with the sums
+            const A old2 = (accumulate == 1 && oi2 >= 0) ? R::get(avg, oi2) : R::zero();
 #pragma unroll
             for (int k = 0; k < NQR + 2; ++k) v[k] = warp_sum(v[k]);
             if (lane <= NQR) {
@@ -196,7 +202,7 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
 #pragma unroll
                 for (int k = 0; k < NQC; ++k) v[k] += src[k];
             }
-            const A old = (accumulate && oi >= 0) ? R::get(avg, oi) : R::zero();
+            const A old = (accumulate == 1 && oi >= 0) ? R::get(avg, oi) : R::zero();
 #pragma unroll
             for (int k = 0; k < NQC; ++k) v[k] = warp_sum(v[k]);
             if (oi >= 0) {
@@ -211,7 +217,7 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
     A bsum = R::zero();
     if (t < NSC) {  // this block's share of the scalars, warps in order
         const long long i = (long long)blk * NSC + t;
-        const A old = accumulate ? R::get(bavg, i) : R::zero();
+        const A old = accumulate == 1 ? R::get(bavg, i) : R::zero();
         for (int w = 0; w < WPB; ++w) bsum = R::add(bsum, wsc[w][t]);
         R::put(bpart, i, bsum);
         if (accumulate) R::put(bavg, i, R::add(old, bsum));
