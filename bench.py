@@ -556,6 +556,158 @@ def run_adjoint(a, w):
     print(json.dumps(line))
 
 
+# the 3-D step (D3Q19, two species): the method reads and writes each population once (304 B per
+# site-update in FP32); the collide pass k3_step itself reads the site's populations and the
+# psi / rho pairs and writes the pushed populations (152 + 16 + 152 = 320 B), the density pass
+# reads the populations and writes the pairs (168 B)
+BYTES3 = {"fp32": {"step": 304, "k3_step": 320, "k3_density": 168},
+          "fp64": {"step": 608, "k3_step": 640, "k3_density": 336}}
+
+
+def oracle3_run(w, n, steps):
+    """The 3-D oracle on an n^3 cut of the workload: (RefLattice3D after `steps` steps, seconds)."""
+    from oracle import ref3d
+
+    ref3d.build()
+    rho = np.ascontiguousarray(w["rho"][:, :n, :n, :n])
+    keys = ("tau", "G1", "G2", "G_AB", "rho0", "weight_norm", "body_force", "psi_form", "wall_u")
+    ref = ref3d.RefLattice3D(n, n, n, w["n_species"], zbc=w["z_boundary"],
+                             **{k: w["params"][k] for k in keys if k in w["params"]})
+    ref.set_fields(rho)
+    t0 = time.perf_counter()
+    ref.step(steps)
+    return ref, time.perf_counter() - t0, rho
+
+
+def run_reference_3d(a, w):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    n = 32
+    oracle3_run(w, n, a.warmup)
+    _, dt, _ = oracle3_run(w, n, a.steps)
+    value = n ** 3 * a.steps / dt / 1e6
+    sample = f"{a.steps} timed 3-D oracle steps on a {n}^3 cut of {a.workload} (single thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "sample": f"{n}^3"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_3d(a, w):
+    """The three-dimensional extension: one bench step = lbm3_step(1), a density pass and a collide
+    pass over the whole lattice (128^3 x 2 species: 318 MB of populations per copy, well above
+    L2, so every step reads its input from HBM)."""
+    import torch
+
+    from paper_1402_6019_gb300 import lbm as L
+    from paper_1402_6019_gb300 import replicas
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+
+        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    nx, ny, nz, ns = w["nx"], w["ny"], w["nz"], w["n_species"]
+    sites = nx * ny * nz
+    prec = L.LBM_FP32 if a.precision == "fp32" else L.LBM_FP64
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    lat = L.Lattice3(nx, ny, nz, ns, prec, w["z_boundary"], device=local, stream=stream.cuda_stream, **w["params"])
+    lat.set_fields(w["rho"])
+    lat.step(a.warmup)
+    lat.synchronize()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local, _pci_bus_id(local)) as clk:
+        t0.record(stream)
+        lat.step(a.steps)
+        t1.record(stream)
+        barrier()
+    step_ms = float(t0.elapsed_time(t1))
+    lat.synchronize()
+    # the same number of steps with events around each of the two kernels
+    lat.profile(True)
+    lat.step(a.steps)
+    d_ms, c_ms, nstep = lat.profile_read()
+    lat.profile(False)
+    step_s, job_sites = replicas.aggregate(step_ms * 1e-3, sites, dist=dist, device="cuda")
+    ms_per_step = step_s * 1e3 / a.steps
+    value = job_sites / (ms_per_step * 1e-3) / 1e6
+    peak, peak_kind = _peaks()
+    B = BYTES3[a.precision]
+    kd, kc = d_ms / max(nstep, 1), c_ms / max(nstep, 1)
+    top, kms = ("k3_step", kc) if kc >= kd else ("k3_density", kd)
+    achieved = B[top] * sites / (kms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+                "kernel": f"lbm3::{top}<T, ...>", "kernel_ms": round(kms, 5),
+                "algorithmic_bytes_per_site": B[top],
+                "kernels_ms": {"k3_density": round(kd, 5), "k3_step": round(kc, 5)},
+                "step_frac": round(B["step"] * value * 1e6 / 1e9 / peak, 4),
+                "step_bytes_per_site": B["step"],
+                "timing": "kernel durations from CUDA events around each kernel in a second pass over the same "
+                          "number of steps; step_frac = the method's bytes per site-update x MLUPS / peak"}
+    # end to end: densities uploaded from pinned host memory, then every step followed by a read of
+    # the totals (mass, momentum) to the host
+    e2e = None
+    if a.e2e_steps > 0:
+        rho_pin = torch.from_numpy(np.ascontiguousarray(w["rho"])).pin_memory()
+        nsteps = min(a.e2e_steps, 100)
+        barrier()
+        tt = time.perf_counter()
+        lat.set_fields(rho_pin.numpy())
+        for _ in range(nsteps):
+            lat.step(1)
+            lat.totals()
+        barrier()
+        dt, e2e_sites = replicas.aggregate(time.perf_counter() - tt, sites * nsteps, dist=dist, device="cuda")
+        e2e = {"value": round(e2e_sites / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(rho_pin.numel() * 8 // nsteps), "d2h_bytes_per_step": 8 * (ns + 3),
+               "steps": nsteps, "read": "the densities uploaded from pinned host memory once, then every step "
+                                        "followed by lbm3_totals (mass and momentum read back)"}
+    if rank != 0:
+        return
+    line = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "nx": nx, "ny": ny, "nz": nz, "n_species": ns, "precision": a.precision,
+                   "lattice": "D3Q19", "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": f"one lattice of {2 * 19 * ns * sites * (4 if a.precision == 'fp32' else 8) / 2**20:.0f} "
+                         f"MiB of populations (both copies) > {L2_BYTES / 2**20:.0f} MiB L2; no flush"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk.summary(),
+    }
+    if world == 1 and not a.no_cpu_baseline:
+        n = 32
+        ref, dt, rho = oracle3_run(w, n, 20)
+        line["cpu_baseline"] = {"value": round(n ** 3 * 20 / dt / 1e6, 4), "unit": "MLUPS", "cores": 1,
+                                "kind": "oracle", "sample": f"20 steps of the 3-D oracle on a {n}^3 cut of the "
+                                                            f"workload, {dt:.1f} s, single thread"}
+        g = L.Lattice3(n, n, n, ns, prec, w["z_boundary"], device=local, stream=stream.cuda_stream, **w["params"])
+        g.set_fields(rho)
+        g.step(20)
+        r_rho, r_u, _ = ref.fields()
+        g_rho, g_u, _ = g.fields(populations=False)
+        rel = lambda x, y: float(np.abs(x - y).max() / max(np.abs(y).max(), 1e-300))
+        line["errors"] = {"vs": "FP64 3-D oracle", "sample": f"{n}^3 cut, 20 steps", "rho": rel(g_rho, r_rho),
+                          "u": rel(g_u, r_u)}
+    print(json.dumps(line))
+
+
 def main():
     a = _args()
     Clocks.csv_path = a.clocks_csv
@@ -570,6 +722,8 @@ def main():
                    ("reference", True): 2}[(a.impl, "target_u" in w)]
     if "target_u" in w:  # the calibration workload: gradients of a run
         return run_reference_adjoint(a, w) if a.impl == "reference" else run_adjoint(a, w)
+    if w.get("dim") == 3:  # the three-dimensional extension
+        return run_reference_3d(a, w) if a.impl == "reference" else run_3d(a, w)
     if a.impl == "reference":
         return run_reference(a, w)
 

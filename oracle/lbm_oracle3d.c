@@ -20,7 +20,9 @@
  *  - every interaction weight scaled by weight_norm (1/3: Eq. BULK);
  *  - shifted-velocity BGK of Sec. II with the common velocity u' = sum_s (j_s / tau_s) /
  *    sum_s (rho_s / tau_s), u_s^eq = u' + tau_s F_s / rho_s; body force g along x.
- * Loops run in a fixed order; no FMA contraction (built with -ffp-contract=off).
+ * Loops run in a fixed order; no FMA contraction (built with -ffp-contract=off).  OpenMP splits
+ * only loops whose iterations are independent (per site, or per destination row of the
+ * streaming), so the results are the same for every thread count.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -182,6 +184,7 @@ int lbmref3_set_populations(lbmref3 *L, const double *f) {
 
 static void moments(const lbmref3 *L, double *rho /*[ns][n]*/, double *j /*[ns][3][n]*/) {
     for (int s = 0; s < L->ns; ++s)
+#pragma omp parallel for schedule(static)
         for (long long i = 0; i < L->n; ++i) {
             double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
             for (int l = 0; l < 19; ++l) {
@@ -204,6 +207,7 @@ static void forces(const lbmref3 *L, const double *rho, double *psi, double *F /
     for (int s = 0; s < L->ns; ++s)
         for (long long i = 0; i < L->n; ++i) psi[s * L->n + i] = psi_of(L, s, rho[s * L->n + i]);
     for (int s = 0; s < L->ns; ++s)
+#pragma omp parallel for schedule(static)
         for (int z = 0; z < L->nz; ++z)
             for (int y = 0; y < L->ny; ++y)
                 for (int x = 0; x < L->nx; ++x) {
@@ -276,6 +280,7 @@ static int step1(lbmref3 *L) {
     }
     moments(L, rho, j);
     forces(L, rho, psi, F);
+#pragma omp parallel for schedule(static)
     for (long long i = 0; i < n; ++i) {
         /* common velocity u' = sum_s (j_s / tau_s) / sum_s (rho_s / tau_s) */
         double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
@@ -295,6 +300,7 @@ static int step1(lbmref3 *L) {
     }
     for (int s = 0; s < ns; ++s)
         for (int l = 0; l < 19; ++l)
+#pragma omp parallel for schedule(static)
             for (int z = 0; z < L->nz; ++z)
                 for (int y = 0; y < L->ny; ++y)
                     for (int x = 0; x < L->nx; ++x) {

@@ -1,0 +1,959 @@
+// lbm3d.cu -- the three-dimensional extension of the two-belt Shan-Chen step (D3Q19; Eq. FORCE
+// over the 3-D links of |c|^2 <= 8 with Appendix B's weights solved in three dimensions; the
+// cross repulsion of Sec. IV over the first belt; the shifted-velocity BGK collision of
+// Sec. II), behind the lbm3_* C ABI of include/lbm3d.h.
+//
+// A step is two kernels.
+//  * k3_density reads each site's populations once and writes psi_s and rho_s into two
+//    ghost-padded volumes (4 ghost columns in x, 2 ghost rows in y and z, holding the periodic
+//    images, or beyond a wall the mirror images of the fluid), the two species of a site side
+//    by side, so that a tile with its 2-cell halo is one in-bounds box.
+//  * k3_step: a CTA of 32 x 4 x 2 sites loads the box of both volumes around its tile
+//    (40 x 8 x 6 positions, x from x0 - 4 for 16-byte alignment) with one 4-D
+//    cp.async.bulk.tensor on an mbarrier while every thread loads its own 19 populations per
+//    species from HBM; then the force (46 antipodal link pairs, gathered shell by shell, both
+//    species at once), the cross force, the collision, and the push of the new populations to
+//    x + c_l (periodic in x and y, periodic or halfway bounce-back with Ladd's term in z).
+// HBM traffic per site-update (FP32, two species): 152 B of populations read twice and written
+// once plus the 16 B of the volumes written and read, 488 B; the method's own is 304 B
+// (each population read and written once).  Populations are SoA f[s][l][z][y][x] (rows padded
+// to 32), FP32 deviations f - W_l rho_ref,s or plain FP64.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm3d.h"
+#include "lbm_internal.h"
+
+namespace lbm3 {
+
+// ---- lattice -------------------------------------------------------------------------------
+
+// D3Q19: rest, +-x, +-y, +-z, then the 12 edges; every velocity is followed by its opposite.
+// Each velocity is coded as (cx + 1) + 3 (cy + 1) + 9 (cz + 1).
+__host__ __device__ constexpr int code19(int l) {
+    constexpr int k[19] = {13, 14, 12, 16, 10, 22, 4, 17, 9, 11, 15, 23, 3, 5, 21, 25, 1, 7, 19};
+    return k[l];
+}
+__host__ __device__ constexpr int c3x(int l) { return code19(l) % 3 - 1; }
+__host__ __device__ constexpr int c3y(int l) { return code19(l) / 3 % 3 - 1; }
+__host__ __device__ constexpr int c3z(int l) { return code19(l) / 9 - 1; }
+__host__ __device__ constexpr int opp19(int l) { return l == 0 ? 0 : (l % 2 ? l + 1 : l - 1); }
+template <typename T>
+__host__ __device__ constexpr T w19(int l) {
+    return l == 0 ? T(1) / T(3) : (l <= 6 ? T(1) / T(18) : T(1) / T(36));
+}
+
+// Interaction weights by shell |c|^2 (Appendix B's constraints solved in three dimensions).
+inline double w_att3(int q) {
+    switch (q) {
+        case 1: return 2.0 / 15.0;
+        case 2: return 1.0 / 15.0;
+        case 3: return 1.0 / 60.0;
+        case 4: return 1.0 / 120.0;
+        default: return 0.0;
+    }
+}
+inline double w_rep3(int q) {
+    switch (q) {
+        case 1: return 4.0 / 45.0;
+        case 2: return 1.0 / 21.0;
+        case 3: return 2.0 / 105.0;
+        case 4: return 5.0 / 504.0;
+        case 5: return 1.0 / 315.0;
+        case 6: return 1.0 / 630.0;
+        case 8: return 1.0 / 5040.0;
+        default: return 0.0;
+    }
+}
+inline double w_cross3(int q) { return q == 1 ? 1.0 / 6.0 : (q == 2 ? 1.0 / 12.0 : 0.0); }
+
+// ---- pairs of the two species ----------------------------------------------------------------
+
+// A site's two species side by side: float2 (FP32, packed instructions) or double2.
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using V = float2; };
+template <> struct PairOf<double> { using V = double2; };
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsplat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 vswap(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vsplat(double a) { return make_double2(a, a); }
+__device__ __forceinline__ double2 vswap(double2 a) { return make_double2(a.y, a.x); }
+
+// ---- geometry and constants ----------------------------------------------------------------
+
+constexpr int GX = 4, GY = 2, GZ = 2;         // ghosts of the psi / rho volumes
+constexpr int TX = 32, TY = 4, TZ = 2;        // a CTA's tile (one thread per site)
+constexpr int NT3 = TX * TY * TZ;
+constexpr int BX = TX + 2 * GX, BY = TY + 2 * GY, BZ = TZ + 2 * GZ;  // the box of a tile
+constexpr long long WAIT_LIMIT = 2000000000LL;  // clock cycles of the bounded wait (~1 s)
+
+template <typename T>
+struct Step3 {
+    int nx, ny, nz, ns, zbc, psi_form;
+    int pitch;            // population row length (nx rounded up to 32)
+    int gpitch;           // sites per row of a volume (nx + 2 GX rounded up to 4)
+    long long plane;      // elements of one population volume (nz * ny * pitch)
+    long long gvol;       // pairs in one psi / rho volume (gz * gy * gpitch)
+    int gy, gz;           // rows and layers of a volume (ny + 2 GY, nz + 2 GZ)
+    T omega[2], tau[2], rho_ref[2], inv_rho0[2], rho0[2];
+    T g, wall_u[2];
+    T kq[2][9];           // K_s(q) = weight_norm (G1_s w_att(q) + G2_s w_rep(q)) by shell q
+    T kc[3];              // weight_norm G_AB w_cross(q), q = 1, 2 (zero for one species)
+};
+
+template <typename T>
+__device__ __forceinline__ T psi3(const Step3<T>& C, int s, T rho);
+template <>
+__device__ __forceinline__ float psi3<float>(const Step3<float>& C, int s, float rho) {
+    return C.psi_form == 1 ? rho : 1.0f - __expf(-rho * C.inv_rho0[s]);
+}
+template <>
+__device__ __forceinline__ double psi3<double>(const Step3<double>& C, int s, double rho) {
+    return C.psi_form == 1 ? rho : 1.0 - exp(-rho / C.rho0[s]);
+}
+
+__device__ __forceinline__ int wrap3(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+// reflection about the walls at -1/2 and n - 1/2 (the mirror reading of the ghost rows)
+__device__ __forceinline__ int mirror3(int i, int n) {
+    int m = i % (2 * n);
+    if (m < 0) m += 2 * n;
+    return m >= n ? 2 * n - 1 - m : m;
+}
+
+// ---- k3_density --------------------------------------------------------------------------
+
+// The padded coordinates (own, then ghosts) that hold the value of coordinate v of an axis of
+// n sites with g ghosts on each side: periodic images, or the mirror images with `mirror`.
+__device__ __forceinline__ int ghost_list(int v, int n, int g, bool mirror, int* out) {
+    int k = 0;
+    out[k++] = v + g;
+    if (v >= g && v < n - g) return k;
+    for (int q = -g; q < n + g; ++q) {
+        if (q >= 0 && q < n) {
+            q = n - 1;  // skip the interior
+            continue;
+        }
+        const int src = mirror ? mirror3(q, n) : wrap3(q, n);
+        if (src == v && k < 2 * g + 1) out[k++] = q + g;
+    }
+    return k;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k3_density(const T* __restrict__ f, T* __restrict__ vol, const Step3<T> C) {
+    using V = typename PairOf<T>::V;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= C.nx) return;
+    const long long i = ((long long)z * C.ny + y) * C.pitch + x;
+    T rho[2] = {T(0), T(0)}, psi[2] = {T(0), T(0)};
+    for (int s = 0; s < C.ns; ++s) {
+        T a = T(0);
+#pragma unroll
+        for (int l = 0; l < 19; ++l) a += f[(s * 19 + l) * C.plane + i];
+        rho[s] = C.rho_ref[s] + a;
+        psi[s] = psi3<T>(C, s, rho[s]);
+    }
+    V pv, rv;
+    pv.x = psi[0];
+    pv.y = psi[1];
+    rv.x = rho[0];
+    rv.y = rho[1];
+    int xs[2 * GX + 1], ys[2 * GY + 1], zs[2 * GZ + 1];
+    const int nxl = ghost_list(x, C.nx, GX, false, xs);
+    const int nyl = ghost_list(y, C.ny, GY, false, ys);
+    const int nzl = ghost_list(z, C.nz, GZ, C.zbc != 0, zs);
+    V* const P = reinterpret_cast<V*>(vol);
+    for (int c = 0; c < nzl; ++c)
+        for (int b = 0; b < nyl; ++b)
+            for (int a = 0; a < nxl; ++a) {
+                const long long o = ((long long)zs[c] * C.gy + ys[b]) * C.gpitch + xs[a];
+                P[o] = pv;
+                P[C.gvol + o] = rv;
+            }
+}
+
+// ---- k3_step -----------------------------------------------------------------------------
+
+enum { K3_WRITE = 1, K3_FIELDS = 2 };
+
+template <typename T>
+struct Smem3 {
+    typename PairOf<T>::V box[2][BZ][BY][BX];  // psi, rho pairs of the tile and its halo
+    alignas(8) unsigned long long bar;
+};
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// The links of Eq. FORCE, one of each antipodal pair (first nonzero component positive), by
+// shell |c|^2 = 1, 2, 3, 4, 5, 6, 8.
+#define LBM3_SHELL1(L) L(0, 0, 1) L(0, 1, 0) L(1, 0, 0)
+#define LBM3_SHELL2(L) L(0, 1, -1) L(0, 1, 1) L(1, -1, 0) L(1, 0, -1) L(1, 0, 1) L(1, 1, 0)
+#define LBM3_SHELL3(L) L(1, -1, -1) L(1, -1, 1) L(1, 1, -1) L(1, 1, 1)
+#define LBM3_SHELL4(L) L(0, 0, 2) L(0, 2, 0) L(2, 0, 0)
+#define LBM3_SHELL5(L)                                                                                      \
+    L(0, 1, -2) L(0, 1, 2) L(0, 2, -1) L(0, 2, 1) L(1, -2, 0) L(1, 0, -2) L(1, 0, 2) L(1, 2, 0) L(2, -1, 0) \
+        L(2, 0, -1) L(2, 0, 1) L(2, 1, 0)
+#define LBM3_SHELL6(L)                                                                                    \
+    L(1, -2, -1) L(1, -2, 1) L(1, -1, -2) L(1, -1, 2) L(1, 1, -2) L(1, 1, 2) L(1, 2, -1) L(1, 2, 1)       \
+        L(2, -1, -1) L(2, -1, 1) L(2, 1, -1) L(2, 1, 1)
+#define LBM3_SHELL8(L) L(0, 2, -2) L(0, 2, 2) L(2, -2, 0) L(2, 0, -2) L(2, 0, 2) L(2, 2, 0)
+
+// c * d added into an accumulator for a constant component c in -2..2
+template <int C, typename V>
+__device__ __forceinline__ V addc(V acc, V d) {
+    if constexpr (C == 1) return vadd(acc, d);
+    if constexpr (C == -1) return vsub(acc, d);
+    if constexpr (C == 2 || C == -2) return vfma(vsplat(decltype(d.x)(C)), d, acc);
+    return acc;
+}
+
+template <typename T, int MODE, int NS>
+__global__ void __launch_bounds__(NT3, 2)
+    k3_step(const __grid_constant__ CUtensorMap vmap, const T* __restrict__ fin, T* __restrict__ fout,
+            const Step3<T> C, int* __restrict__ flag, double* __restrict__ fields) {
+    using V = typename PairOf<T>::V;
+    extern __shared__ __align__(1024) unsigned char smem3[];
+    Smem3<T>& S = *reinterpret_cast<Smem3<T>*>(smem3);
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int tid = (tz * TY + ty) * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    const bool live = x < C.nx && y < C.ny && z < C.nz;
+    if (tid == 0) {
+        const unsigned bar = su32(&S.bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        constexpr unsigned bytes = (unsigned)sizeof(S.box);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+        // box origin: padded (x0, y0, z0) = site (x0 - GX, y0 - GY, z0 - GZ); x counts values of T
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+            "%5}], [%6];\n" ::"r"(su32(&S.box[0][0][0][0])),
+            "l"(&vmap), "r"(2 * x0), "r"(y0), "r"(z0), "r"(0), "r"(bar)
+            : "memory");
+    }
+    // own populations from HBM while the box is on its way
+    const long long i = ((long long)z * C.ny + y) * C.pitch + x;
+    T f[NS][19];
+    if (live) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int l = 0; l < 19; ++l) f[s][l] = fin[(s * 19 + l) * C.plane + i];
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    bool ok = true;
+    {
+        const unsigned bar = su32(&S.bar);
+        const long long t0 = clock64();
+        for (;;) {
+            unsigned done;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(bar), "r"(0u)
+                : "memory");
+            if (done) break;
+            if (clock64() - t0 > WAIT_LIMIT) {
+                ok = false;
+                break;
+            }
+        }
+    }
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicOr(flag, 2);
+            // the copy that did not arrive in time is waited for (bounded) before the CTA exits
+            const unsigned bar = su32(&S.bar);
+            const long long t0 = clock64();
+            for (;;) {
+                unsigned done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
+                    "p;\n}\n"
+                    : "=r"(done)
+                    : "r"(bar), "r"(0u)
+                    : "memory");
+                if (done || clock64() - t0 > WAIT_LIMIT) break;
+            }
+        }
+        return;
+    }
+    if (!live) return;
+
+    // ---- force: Eq. FORCE over the 46 antipodal pairs, shell by shell, both species ----
+    const int bx = tx + GX, by = ty + GY, bz = tz + GZ;
+#define PS(dx, dy, dz) S.box[0][bz + (dz)][by + (dy)][bx + (dx)]
+#define RH(dx, dy, dz) S.box[1][bz + (dz)][by + (dy)][bx + (dx)]
+    const V zero = vsplat(T(0));
+    V ax = zero, ay = zero, az = zero;
+#define LBM3_ACC(dx, dy, dz)                                \
+    {                                                       \
+        const V d_ = vsub(PS(dx, dy, dz), PS(-(dx), -(dy), -(dz))); \
+        sx = addc<dx>(sx, d_);                              \
+        sy = addc<dy>(sy, d_);                              \
+        sz = addc<dz>(sz, d_);                              \
+    }
+#define LBM3_SHELL(q, LIST)                          \
+    {                                                \
+        V sx = zero, sy = zero, sz = zero;           \
+        LIST(LBM3_ACC)                               \
+        V kq_;                                       \
+        kq_.x = C.kq[0][q];                          \
+        kq_.y = C.kq[1][q];                          \
+        ax = vfma(kq_, sx, ax);                      \
+        ay = vfma(kq_, sy, ay);                      \
+        az = vfma(kq_, sz, az);                      \
+    }
+    LBM3_SHELL(1, LBM3_SHELL1)
+    LBM3_SHELL(2, LBM3_SHELL2)
+    LBM3_SHELL(3, LBM3_SHELL3)
+    LBM3_SHELL(4, LBM3_SHELL4)
+    LBM3_SHELL(5, LBM3_SHELL5)
+    LBM3_SHELL(6, LBM3_SHELL6)
+    LBM3_SHELL(8, LBM3_SHELL8)
+#undef LBM3_SHELL
+#undef LBM3_ACC
+    const V p0 = PS(0, 0, 0), r0 = RH(0, 0, 0);
+    const V mp = vsub(zero, p0);
+    V Fx = vmul(mp, ax), Fy = vmul(mp, ay), Fz = vmul(mp, az);
+    if constexpr (NS == 2) {
+        // cross repulsion: F_s += -G_AB rho_s(x) sum_l w(|c|^2) rho_s'(x + c_l) c_l over the first belt
+        V bx1 = zero, by1 = zero, bz1 = zero, bx2 = zero, by2 = zero, bz2 = zero;
+#define LBM3_XACC(dx, dy, dz, SX, SY, SZ)                      \
+    {                                                          \
+        const V d_ = vsub(RH(dx, dy, dz), RH(-(dx), -(dy), -(dz)));  \
+        SX = addc<dx>(SX, d_);                                 \
+        SY = addc<dy>(SY, d_);                                 \
+        SZ = addc<dz>(SZ, d_);                                 \
+    }
+#define LBM3_X1(dx, dy, dz) LBM3_XACC(dx, dy, dz, bx1, by1, bz1)
+#define LBM3_X2(dx, dy, dz) LBM3_XACC(dx, dy, dz, bx2, by2, bz2)
+        LBM3_SHELL1(LBM3_X1)
+        LBM3_SHELL2(LBM3_X2)
+#undef LBM3_X1
+#undef LBM3_X2
+#undef LBM3_XACC
+        const V k1 = vsplat(C.kc[1]), k2 = vsplat(C.kc[2]);
+        const V cx_ = vfma(k2, bx2, vmul(k1, bx1)), cy_ = vfma(k2, by2, vmul(k1, by1)),
+                cz_ = vfma(k2, bz2, vmul(k1, bz1));
+        const V mr = vsub(zero, r0);
+        // species A sees the sums over rho_B, species B those over rho_A
+        Fx = vfma(mr, vswap(cx_), Fx);
+        Fy = vfma(mr, vswap(cy_), Fy);
+        Fz = vfma(mr, vswap(cz_), Fz);
+    }
+#undef PS
+#undef RH
+    T F[2][3];
+    F[0][0] = Fx.x;
+    F[0][1] = Fy.x;
+    F[0][2] = Fz.x;
+    F[1][0] = Fx.y;
+    F[1][1] = Fy.y;
+    F[1][2] = Fz.y;
+
+    // ---- moments, body force, common velocity ----
+    T rho[NS], ir[NS], jx[NS], jy[NS], jz[NS], drho[NS];
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        T a = T(0), mx = T(0), my = T(0), mz = T(0);
+#pragma unroll
+        for (int l = 0; l < 19; ++l) {
+            a += f[s][l];
+            if (c3x(l)) mx += T(c3x(l)) * f[s][l];
+            if (c3y(l)) my += T(c3y(l)) * f[s][l];
+            if (c3z(l)) mz += T(c3z(l)) * f[s][l];
+        }
+        drho[s] = a;
+        rho[s] = C.rho_ref[s] + a;
+        if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = true;
+        ir[s] = T(1) / rho[s];
+        jx[s] = mx;
+        jy[s] = my;
+        jz[s] = mz;
+        F[s][0] += rho[s] * C.g;
+    }
+    if (bad) atomicOr(flag, 1);
+    T nxu = T(0), nyu = T(0), nzu = T(0), den = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        nxu += C.omega[s] * jx[s];
+        nyu += C.omega[s] * jy[s];
+        nzu += C.omega[s] * jz[s];
+        den += C.omega[s] * rho[s];
+    }
+    const T iden = T(1) / den;
+    const T upx = nxu * iden, upy = nyu * iden, upz = nzu * iden;
+
+    if constexpr ((MODE & K3_FIELDS) != 0) {
+        // rho_s, the barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s, plain populations
+        const long long n = (long long)C.nx * C.ny * C.nz, k = ((long long)z * C.ny + y) * C.nx + x;
+        T mxs = T(0), mys = T(0), mzs = T(0), rt = T(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            mxs += jx[s] + T(0.5) * F[s][0];
+            mys += jy[s] + T(0.5) * F[s][1];
+            mzs += jz[s] + T(0.5) * F[s][2];
+            rt += rho[s];
+            fields[s * n + k] = (double)rho[s];
+#pragma unroll
+            for (int l = 0; l < 19; ++l)
+                fields[(NS + 3 + s * 19 + l) * n + k] = (double)f[s][l] + w19<double>(l) * (double)C.rho_ref[s];
+        }
+        fields[(NS + 0) * n + k] = (double)(mxs / rt);
+        fields[(NS + 1) * n + k] = (double)(mys / rt);
+        fields[(NS + 2) * n + k] = (double)(mzs / rt);
+    }
+
+    if constexpr ((MODE & K3_WRITE) != 0) {
+        // ---- shifted-velocity BGK (Sec. II) and streaming ----
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const T om = C.omega[s], keep = T(1) - om, tir = C.tau[s] * ir[s];
+            const T ux = upx + F[s][0] * tir, uy = upy + F[s][1] * tir, uz = upz + F[s][2] * tir;
+            const T u15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+            const T b = om * rho[s];
+            const T base = om * drho[s] - b * u15;  // omega (drho - 3/2 rho u^2)
+            T g[19];
+            g[0] = keep * f[s][0] + w19<T>(0) * base;
+#pragma unroll
+            for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
+                const T cu = T(c3x(l)) * ux + T(c3y(l)) * uy + T(c3z(l)) * uz;
+                const T w = w19<T>(l);
+                const T even = w * base + (w * T(4.5)) * b * cu * cu;
+                const T odd = (w * T(3)) * b * cu;
+                g[l] = (keep * f[s][l] + even) + odd;
+                g[l + 1] = (keep * f[s][l + 1] + even) - odd;
+            }
+#pragma unroll
+            for (int l = 0; l < 19; ++l) {
+                int xd = x + c3x(l), yd = y + c3y(l), zd = z + c3z(l);
+                xd = xd < 0 ? xd + C.nx : (xd >= C.nx ? xd - C.nx : xd);
+                yd = yd < 0 ? yd + C.ny : (yd >= C.ny ? yd - C.ny : yd);
+                int ld = l;
+                T v = g[l];
+                if (zd < 0 || zd >= C.nz) {
+                    if (C.zbc) {  // halfway bounce-back into this site with Ladd's term
+                        const T uw = zd < 0 ? C.wall_u[0] : C.wall_u[1];
+                        v = g[l] - T(6) * w19<T>(l) * rho[s] * T(c3x(l)) * uw;
+                        ld = opp19(l);
+                        xd = x;
+                        yd = y;
+                        zd = z;
+                    } else {
+                        zd = zd < 0 ? zd + C.nz : zd - C.nz;
+                    }
+                }
+                fout[(s * 19 + ld) * C.plane + ((long long)zd * C.ny + yd) * C.pitch + xd] = v;
+            }
+        }
+    }
+}
+
+// ---- equilibrium at rest, totals ---------------------------------------------------------------
+
+template <typename T>
+__global__ void k3_init(T* __restrict__ f, const double* __restrict__ rho, const Step3<T> C) {
+    const long long n = (long long)C.nx * C.ny * C.nz;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % C.nx), y = (int)(k / C.nx % C.ny), z = (int)(k / ((long long)C.nx * C.ny));
+        const long long i = ((long long)z * C.ny + y) * C.pitch + x;
+        for (int s = 0; s < C.ns; ++s) {
+            const double d = rho[s * n + k] - (double)C.rho_ref[s];
+            for (int l = 0; l < 19; ++l) f[(s * 19 + l) * C.plane + i] = (T)(w19<double>(l) * d);
+        }
+    }
+}
+
+// Block partials of mass A, mass B and the lattice momentum (x, y, z), FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k3_totals(const T* __restrict__ f, const Step3<T> C, double* __restrict__ part) {
+    const long long n = (long long)C.nx * C.ny * C.nz;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % C.nx), y = (int)(k / C.nx % C.ny), z = (int)(k / ((long long)C.nx * C.ny));
+        const long long i = ((long long)z * C.ny + y) * C.pitch + x;
+        for (int s = 0; s < C.ns; ++s) {
+            double r = (double)C.rho_ref[s];
+            for (int l = 0; l < 19; ++l) {
+                const double v = (double)f[(s * 19 + l) * C.plane + i];
+                r += v;
+                acc[2] += c3x(l) * v;
+                acc[3] += c3y(l) * v;
+                acc[4] += c3z(l) * v;
+            }
+            acc[s] += r;
+        }
+    }
+    __shared__ double red[5][256];
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <typename T, int MODE, int NS>
+cudaError_t launch_step3(const CUtensorMap& map, const T* fin, T* fout, const Step3<T>& C, int* flag, double* fields,
+                         cudaStream_t st) {
+    const size_t smem = sizeof(Smem3<T>);
+    static bool attr = false;  // per template instance
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k3_step<T, MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((C.nx + TX - 1) / TX, (C.ny + TY - 1) / TY, (C.nz + TZ - 1) / TZ);
+    k3_step<T, MODE, NS><<<grid, dim3(TX, TY, TZ), smem, st>>>(map, fin, fout, C, flag, fields);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step3_any(int mode, int ns, const CUtensorMap& map, const T* fin, T* fout, const Step3<T>& C,
+                             int* flag, double* fields, cudaStream_t st) {
+    if (mode == K3_WRITE)
+        return ns == 2 ? launch_step3<T, K3_WRITE, 2>(map, fin, fout, C, flag, fields, st)
+                       : launch_step3<T, K3_WRITE, 1>(map, fin, fout, C, flag, fields, st);
+    return ns == 2 ? launch_step3<T, K3_FIELDS, 2>(map, fin, fout, C, flag, fields, st)
+                   : launch_step3<T, K3_FIELDS, 1>(map, fin, fout, C, flag, fields, st);
+}
+
+}  // namespace lbm3
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+using namespace lbm3;
+
+struct lbm3_ctx {
+    lbm3_desc d{};
+    lbm_params p{};
+    bool have_params = false, have_fields = false;
+    bool own_stream = false;
+    cudaStream_t stream = nullptr;
+    size_t esize = 4;
+    int pitch = 0, gpitch = 0;
+    long long plane = 0, gvol = 0, n = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* vol = nullptr;               // psi and rho volumes: [2][gz][gy][gpitch] pairs
+    alignas(64) unsigned char map[128] = {};  // TMA descriptor of vol
+    int* flag = nullptr;
+    double* staging = nullptr;         // lbm3_get_fields / lbm3_set_fields from the host
+    size_t staging_bytes = 0;
+    double* part = nullptr;            // lbm3_totals block partials
+    int nblk_tot = 0;
+    double rho_ref[2] = {0.0, 0.0};
+    Step3<float> c32{};
+    Step3<double> c64{};
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;       // 4 per timed step
+    size_t ev_used = 0;
+    long long step = 0;
+    std::string err;
+};
+
+static std::string g3_create_error;
+
+static int fail3(lbm3_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g3_create_error = buf;
+    return code;
+}
+
+#define CK3(call)                                                                                            \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess)                                                                               \
+            return fail3(c, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s (%s:%d)", #call, \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);                                        \
+    } while (0)
+
+template <typename T>
+static void fill_step3(const lbm3_ctx* c, Step3<T>& C) {
+    C = Step3<T>{};
+    C.nx = c->d.nx;
+    C.ny = c->d.ny;
+    C.nz = c->d.nz;
+    C.ns = c->d.n_species;
+    C.zbc = c->d.z_boundary;
+    C.psi_form = c->p.psi_form;
+    C.pitch = c->pitch;
+    C.gpitch = c->gpitch;
+    C.plane = c->plane;
+    C.gvol = c->gvol;
+    C.gy = c->d.ny + 2 * GY;
+    C.gz = c->d.nz + 2 * GZ;
+    C.g = (T)c->p.body_force;
+    C.wall_u[0] = (T)c->p.wall_u[0];
+    C.wall_u[1] = (T)c->p.wall_u[1];
+    const double wn = c->p.weight_norm;
+    for (int s = 0; s < 2; ++s) {
+        const bool on = s < c->d.n_species;
+        const int ps = on ? s : 0;
+        C.tau[s] = (T)c->p.tau[ps];
+        C.omega[s] = (T)(1.0 / c->p.tau[ps]);
+        C.rho0[s] = (T)c->p.rho0[ps];
+        C.inv_rho0[s] = (T)(1.0 / c->p.rho0[ps]);
+        C.rho_ref[s] = on ? (T)c->rho_ref[s] : T(0);
+        for (int q = 0; q < 9; ++q)
+            C.kq[s][q] = on ? (T)(wn * (c->p.G1[ps] * w_att3(q) + c->p.G2[ps] * w_rep3(q))) : T(0);
+    }
+    for (int q = 0; q < 3; ++q) C.kc[q] = c->d.n_species == 2 ? (T)(wn * c->p.G_AB * w_cross3(q)) : T(0);
+}
+
+static void refresh3(lbm3_ctx* c) {
+    fill_step3<float>(c, c->c32);
+    fill_step3<double>(c, c->c64);
+}
+
+extern "C" void lbm3_default_desc(lbm3_desc* d) {
+    if (!d) return;
+    *d = lbm3_desc{};
+    d->nx = d->ny = d->nz = 64;
+    d->n_species = 2;
+    d->precision = LBM_FP32;
+    d->z_boundary = LBM_PERIODIC;
+}
+
+static int check3(lbm3_ctx* c, const lbm3_desc* d) {
+    if (!d) return fail3(c, LBM_EINVAL, "desc is NULL");
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx > 65536 || d->ny > 65535 || d->nz > 65535)
+        return fail3(c, LBM_EINVAL, "nx, ny, nz must be >= 1 (nx <= 65536, ny, nz <= 65535)");
+    if ((long long)d->nx * d->ny * d->nz > (1LL << 30)) return fail3(c, LBM_EINVAL, "nx * ny * nz > 2^30");
+    if (d->n_species != 1 && d->n_species != 2) return fail3(c, LBM_EINVAL, "n_species must be 1 or 2");
+    if (d->precision != LBM_FP32 && d->precision != LBM_FP64) return fail3(c, LBM_EINVAL, "bad precision");
+    if (d->z_boundary != LBM_PERIODIC && d->z_boundary != LBM_BOUNCEBACK) return fail3(c, LBM_EINVAL, "bad z_boundary");
+    if (d->device < 0) return fail3(c, LBM_EINVAL, "device < 0");
+    return LBM_OK;
+}
+
+static void release3(lbm3_ctx* c) {
+    for (int b = 0; b < 2; ++b) cudaFree(c->f[b]);
+    cudaFree(c->vol);
+    cudaFree(c->flag);
+    cudaFree(c->staging);
+    cudaFree(c->part);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+static int make_vol_map(lbm3_ctx* c) {
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(lbm::tensor_map_encoder());
+    if (!encode) return 1;
+    const cuuint64_t es = c->esize;
+    // dims: values of T along x (two per site), rows, layers, the two volumes
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * c->gpitch, (cuuint64_t)(c->d.ny + 2 * GY),
+                                (cuuint64_t)(c->d.nz + 2 * GZ), 2};
+    const cuuint64_t strides[3] = {(cuuint64_t)2 * c->gpitch * es, (cuuint64_t)2 * c->gpitch * (c->d.ny + 2 * GY) * es,
+                                   (cuuint64_t)2 * c->gvol * es};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * BX), (cuuint32_t)BY, (cuuint32_t)BZ, 2};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(c->map),
+                              c->esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                              c->vol, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : 2;
+}
+
+extern "C" int lbm3_create(lbm3_ctx** out, const lbm3_desc* d) {
+    if (!out) return fail3(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check3(nullptr, d);
+    if (rc) return rc;
+    lbm3_ctx* c = new (std::nothrow) lbm3_ctx();
+    if (!c) return fail3(nullptr, LBM_ENOMEM, "host allocation failed");
+    c->d = *d;
+    lbm_default_params(&c->p);
+    auto bail = [&](int code) {
+        g3_create_error = c->err;
+        release3(c);
+        delete c;
+        return code;
+    };
+#define CKC3(call)                                                                                       \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return bail(fail3(c, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", #call, \
+                              cudaGetErrorString(e_)));                                                  \
+    } while (0)
+    CKC3(cudaSetDevice(d->device));
+    if (d->stream) {
+        c->stream = static_cast<cudaStream_t>(d->stream);
+    } else {
+        CKC3(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    const int nx = d->nx, ny = d->ny, nz = d->nz, ns = d->n_species;
+    c->esize = d->precision == LBM_FP64 ? 8 : 4;
+    c->pitch = (nx + 31) / 32 * 32;
+    c->plane = (long long)nz * ny * c->pitch;
+    c->gpitch = (nx + 2 * GX + 3) / 4 * 4;
+    c->gvol = (long long)(nz + 2 * GZ) * (ny + 2 * GY) * c->gpitch;
+    c->n = (long long)nx * ny * nz;
+    const size_t fbytes = (size_t)ns * 19 * c->plane * c->esize;
+    for (int b = 0; b < 2; ++b) {
+        CKC3(cudaMalloc(&c->f[b], fbytes));
+        CKC3(cudaMemsetAsync(c->f[b], 0, fbytes, c->stream));
+    }
+    const size_t vbytes = (size_t)2 * c->gvol * 2 * c->esize;
+    CKC3(cudaMalloc(&c->vol, vbytes));
+    CKC3(cudaMemsetAsync(c->vol, 0, vbytes, c->stream));
+    CKC3(cudaMalloc(&c->flag, sizeof(int)));
+    CKC3(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    int nsm = 0;
+    CKC3(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d->device));
+    c->nblk_tot = std::max(1, std::min(4 * nsm, (int)((c->n + 255) / 256)));
+    CKC3(cudaMalloc(&c->part, (size_t)c->nblk_tot * 5 * sizeof(double)));
+    if (make_vol_map(c) != 0) return bail(fail3(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the psi / rho volumes"));
+    CKC3(cudaStreamSynchronize(c->stream));
+#undef CKC3
+    refresh3(c);
+    *out = c;
+    return LBM_OK;
+}
+
+extern "C" void lbm3_destroy(lbm3_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->d.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release3(c);
+    delete c;
+}
+
+extern "C" const char* lbm3_last_error(const lbm3_ctx* c) { return c ? c->err.c_str() : g3_create_error.c_str(); }
+
+extern "C" int lbm3_set_params(lbm3_ctx* c, const lbm_params* p) {
+    if (!c) return LBM_EINVAL;
+    if (!p) return fail3(c, LBM_EINVAL, "params is NULL");
+    if (lbm_validate_params(p, c->d.n_species) != LBM_OK)
+        return fail3(c, LBM_EINVAL, "invalid parameters: %s", lbm_last_error(nullptr));
+    if (p->weight_preset != LBM_WEIGHTS_PAPER) return fail3(c, LBM_EINVAL, "the 3-D step has the paper's weights only");
+    if (p->psi_wall != LBM_WALL_MIRROR) return fail3(c, LBM_EINVAL, "the 3-D step has the mirror wall reading only");
+    c->p = *p;
+    c->have_params = true;
+    refresh3(c);
+    return LBM_OK;
+}
+
+static int staging3(lbm3_ctx* c, size_t bytes) {
+    if (c->staging_bytes >= bytes) return LBM_OK;
+    cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+    CK3(cudaMalloc(&c->staging, bytes));
+    c->staging_bytes = bytes;
+    return LBM_OK;
+}
+
+extern "C" int lbm3_set_fields(lbm3_ctx* c, const double* rho, int where) {
+    if (!c) return LBM_EINVAL;
+    if (!rho) return fail3(c, LBM_EINVAL, "rho is NULL");
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail3(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
+    if (!c->have_params) return fail3(c, LBM_EINVAL, "lbm3_set_params has not been called");
+    CK3(cudaSetDevice(c->d.device));
+    const int ns = c->d.n_species;
+    const long long n = c->n;
+    std::vector<double> h;
+    const double* src = rho;
+    if (where == LBM_DEVICE) {
+        h.resize((size_t)ns * n);
+        CK3(cudaMemcpyAsync(h.data(), rho, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK3(cudaStreamSynchronize(c->stream));
+        src = h.data();
+    }
+    double sum[2] = {0.0, 0.0};
+    for (int s = 0; s < ns; ++s)
+        for (long long k = 0; k < n; ++k) {
+            const double r = src[s * n + k];
+            if (!(r > 0.0) || !std::isfinite(r)) return fail3(c, LBM_EINVAL, "rho must be > 0 and finite");
+            sum[s] += r;
+        }
+    for (int s = 0; s < 2; ++s)
+        c->rho_ref[s] = c->d.precision == LBM_FP64 || s >= ns ? 0.0
+                                                               : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : sum[s] / n);
+    refresh3(c);
+    int rc = staging3(c, (size_t)ns * n * sizeof(double));
+    if (rc) return rc;
+    CK3(cudaMemcpyAsync(c->staging, src, (size_t)ns * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    if (c->d.precision == LBM_FP64)
+        lbm3::k3_init<double><<<blocks, 256, 0, c->stream>>>((double*)c->f[0], c->staging, c->c64);
+    else
+        lbm3::k3_init<float><<<blocks, 256, 0, c->stream>>>((float*)c->f[0], c->staging, c->c32);
+    CK3(cudaGetLastError());
+    CK3(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+    c->cur = 0;
+    c->step = 0;
+    c->have_fields = true;
+    return LBM_OK;
+}
+
+// the density pass over f[cur] into the volumes
+static cudaError_t density3(lbm3_ctx* c) {
+    const dim3 grid((c->d.nx + 127) / 128, c->d.ny, c->d.nz);
+    if (c->d.precision == LBM_FP64)
+        lbm3::k3_density<double><<<grid, 128, 0, c->stream>>>((const double*)c->f[c->cur], (double*)c->vol, c->c64);
+    else
+        lbm3::k3_density<float><<<grid, 128, 0, c->stream>>>((const float*)c->f[c->cur], (float*)c->vol, c->c32);
+    return cudaGetLastError();
+}
+
+static cudaError_t collide3(lbm3_ctx* c, int mode, double* fields) {
+    const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(c->map);
+    if (c->d.precision == LBM_FP64)
+        return launch_step3_any<double>(mode, c->d.n_species, map, (const double*)c->f[c->cur],
+                                        (double*)c->f[c->cur ^ 1], c->c64, c->flag, fields, c->stream);
+    return launch_step3_any<float>(mode, c->d.n_species, map, (const float*)c->f[c->cur], (float*)c->f[c->cur ^ 1],
+                                   c->c32, c->flag, fields, c->stream);
+}
+
+extern "C" int lbm3_step(lbm3_ctx* c, int nsteps) {
+    if (!c || nsteps < 0) return c ? fail3(c, LBM_EINVAL, "nsteps < 0") : LBM_EINVAL;
+    if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
+    CK3(cudaSetDevice(c->d.device));
+    for (int k = 0; k < nsteps; ++k) {
+        cudaEvent_t* e = nullptr;
+        if (c->profiling) {
+            if (c->ev_used + 4 > c->ev.size())
+                for (int q = 0; q < 64; ++q) {
+                    cudaEvent_t ev;
+                    CK3(cudaEventCreate(&ev));
+                    c->ev.push_back(ev);
+                }
+            e = &c->ev[c->ev_used];
+            c->ev_used += 4;
+            CK3(cudaEventRecord(e[0], c->stream));
+        }
+        CK3(density3(c));
+        if (e) {
+            CK3(cudaEventRecord(e[1], c->stream));
+            CK3(cudaEventRecord(e[2], c->stream));
+        }
+        CK3(collide3(c, K3_WRITE, nullptr));
+        if (e) CK3(cudaEventRecord(e[3], c->stream));
+        c->cur ^= 1;
+        c->step += 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm3_synchronize(lbm3_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    CK3(cudaSetDevice(c->d.device));
+    CK3(cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    CK3(cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 2) return fail3(c, LBM_ETIMEOUT, "a bounded device-side wait for a tile load gave up");
+    if (flag & 1) return fail3(c, LBM_ENONFINITE, "a step met a density <= 0, NaN or Inf");
+    return LBM_OK;
+}
+
+extern "C" int lbm3_get_fields(lbm3_ctx* c, double* rho, double* u, double* f, int where) {
+    if (!c) return LBM_EINVAL;
+    if (where != LBM_HOST && where != LBM_DEVICE) return fail3(c, LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
+    if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
+    CK3(cudaSetDevice(c->d.device));
+    const int ns = c->d.n_species;
+    const long long n = c->n;
+    const size_t per = (size_t)(ns + 3 + 19 * ns);
+    int rc = staging3(c, per * n * sizeof(double));
+    if (rc) return rc;
+    CK3(density3(c));
+    CK3(collide3(c, K3_FIELDS, c->staging));
+    const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (rho) CK3(cudaMemcpyAsync(rho, c->staging, (size_t)ns * n * sizeof(double), kind, c->stream));
+    if (u) CK3(cudaMemcpyAsync(u, c->staging + (size_t)ns * n, (size_t)3 * n * sizeof(double), kind, c->stream));
+    if (f)
+        CK3(cudaMemcpyAsync(f, c->staging + (size_t)(ns + 3) * n, (size_t)19 * ns * n * sizeof(double), kind,
+                            c->stream));
+    return lbm3_synchronize(c);
+}
+
+extern "C" int lbm3_totals(lbm3_ctx* c, double* mass, double* momentum) {
+    if (!c) return LBM_EINVAL;
+    if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
+    CK3(cudaSetDevice(c->d.device));
+    if (c->d.precision == LBM_FP64)
+        lbm3::k3_totals<double><<<c->nblk_tot, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->c64, c->part);
+    else
+        lbm3::k3_totals<float><<<c->nblk_tot, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->c32, c->part);
+    CK3(cudaGetLastError());
+    std::vector<double> h((size_t)c->nblk_tot * 5);
+    CK3(cudaMemcpyAsync(h.data(), c->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    const int rc = lbm3_synchronize(c);
+    if (rc) return rc;
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < c->nblk_tot; ++b)
+        for (int q = 0; q < 5; ++q) t[q] += h[(size_t)b * 5 + q];
+    if (mass)
+        for (int s = 0; s < c->d.n_species; ++s) mass[s] = t[s];
+    if (momentum)
+        for (int q = 0; q < 3; ++q) momentum[q] = t[2 + q];
+    return LBM_OK;
+}
+
+extern "C" int lbm3_profile(lbm3_ctx* c, int enable) {
+    if (!c) return LBM_EINVAL;
+    CK3(cudaSetDevice(c->d.device));
+    CK3(cudaStreamSynchronize(c->stream));
+    c->profiling = enable != 0;
+    c->ev_used = 0;
+    return LBM_OK;
+}
+
+extern "C" int lbm3_profile_read(lbm3_ctx* c, double* ms, long long* steps) {
+    if (!c) return LBM_EINVAL;
+    CK3(cudaSetDevice(c->d.device));
+    CK3(cudaStreamSynchronize(c->stream));
+    double t[2] = {0.0, 0.0};
+    for (size_t k = 0; k + 3 < c->ev_used; k += 4)
+        for (int j = 0; j < 2; ++j) {
+            float v = 0.f;
+            CK3(cudaEventElapsedTime(&v, c->ev[k + 2 * j], c->ev[k + 2 * j + 1]));
+            t[j] += v;
+        }
+    if (ms) {
+        ms[0] = t[0];
+        ms[1] = t[1];
+    }
+    if (steps) *steps = (long long)(c->ev_used / 4);
+    return LBM_OK;
+}

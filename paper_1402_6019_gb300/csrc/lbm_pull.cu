@@ -97,6 +97,7 @@ struct PullSmem {
     alignas(8) unsigned long long bar[ST];
     TileInfo<T> ti[NTQ];
     int fold_item;  // the reduction work item thread 0 drew for the CTA
+    unsigned short ring[NT];  // observing builds: ring position of thread tid, rpz << 8 | rpx
 };
 
 // Tile t of the work order; rot > 0 (one periodic lattice): the order starts rot tiles in, at
@@ -302,12 +303,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     const int nfold = Rd.enabled ? nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32) : 0;
 
     // threads with a ring position (ring_position), NRING / PZ = 22 per warp; the observing builds
-    // recompute it per tile instead (one register pair less across the tile, where registers
-    // are short), the others keep it
+    // keep it in shared memory and read it per tile instead (one register pair less across the
+    // tile, where registers are short), the others keep it in registers
     const bool ring = tx < NRING / PZ;
     int rpx0 = 0, rpz0 = 0;
-    if constexpr ((MODE & M_OBS) == 0)
-        if (ring) ring_position(tx, tz, rpx0, rpz0);
+    if (ring) ring_position(tx, tz, rpx0, rpz0);
+    if constexpr ((MODE & M_OBS) != 0) S.ring[tid] = (unsigned short)(rpz0 << 8 | rpx0);
     // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden;
     // ntiles: nothing more to draw
     int upcoming = ntiles;
@@ -416,7 +417,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         }
         if (ring) {
             int rpx = rpx0, rpz = rpz0;
-            if constexpr ((MODE & M_OBS) != 0) ring_position(tx, tz, rpx, rpz);
+            if constexpr ((MODE & M_OBS) != 0) {
+                const unsigned rp = S.ring[tid];
+                rpx = (int)(rp & 255u);
+                rpz = (int)(rp >> 8);
+            }
             side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
         }
         // the only CTA barrier of a tile: psi / rho of the tile and ring complete, box sl read
@@ -630,16 +635,45 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             }
         }
         // new stored values, straight from registers: a warp stores each plane's row of 32
-        // sites as one 128-byte run; with walls the populations leaving through a wall reflected
+        // sites as one 128-byte run; with walls the populations leaving through a wall reflected.
+        // The periodic images of a site -- in the ghost columns when x is within PULL_GX of an
+        // edge, and without walls in the ghost rows when z is within PULL_GZ of one -- take the
+        // same values.  A lattice of at least 2 PULL_GX columns and 2 PULL_GZ rows gives a site at
+        // most one image of each kind and their corner; they are stored here from registers, on
+        // a branch that only warps holding such sites take.  Narrower lattices use write_images.
         T* const dst = fout + (long long)(prow0 + z + PULL_GZ) * C.pitch + (x + PULL_GX);
+        const bool narrow = nx < 2 * PULL_GX || (!WALL && lnz < 2 * PULL_GZ);
+        const int dxi = x < PULL_GX ? nx : (x >= nx - PULL_GX ? -nx : 0);
+        const int dzi = WALL ? 0 : (z < PULL_GZ ? lnz : (z >= lnz - PULL_GZ ? -lnz : 0));
+        const bool img = (MODE & M_WRITE) && collided && !narrow && (dxi != 0 || dzi != 0);
+        const bool img_warp = __any_sync(FULL, img);  // every lane reaches this vote
+        const long long oxi = dxi, ozi = (long long)dzi * C.pitch;
         if (collided) {
             const bool wall_row = WALL && (z == 0 || z == lnz - 1);
             if (!wall_row) {  // warp-uniform
                 if (MODE & M_WRITE) {
+                    if (img_warp) {
 #pragma unroll
-                    for (int s2 = 0; s2 < NS; ++s2)
+                        for (int s2 = 0; s2 < NS; ++s2)
 #pragma unroll
-                        for (int l = 0; l < 9; ++l) dst[(s2 * 9 + l) * C.plane] = f[s2][l];
+                            for (int l = 0; l < 9; ++l) {
+                                T* const p = dst + (s2 * 9 + l) * C.plane;
+                                const T v = f[s2][l];
+                                *p = v;
+                                if (img) {
+                                    if (dxi) p[oxi] = v;
+                                    if (dzi) {
+                                        p[ozi] = v;
+                                        if (dxi) p[oxi + ozi] = v;
+                                    }
+                                }
+                            }
+                    } else {
+#pragma unroll
+                        for (int s2 = 0; s2 < NS; ++s2)
+#pragma unroll
+                            for (int l = 0; l < 9; ++l) dst[(s2 * 9 + l) * C.plane] = f[s2][l];
+                    }
                 }
             } else {
 #pragma unroll
@@ -660,12 +694,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                                     rowq[QR_WALLT] += dm;
                             }
                         }
-                        if (MODE & M_WRITE) dst[(s2 * 9 + l) * C.plane] = v;
+                        if (MODE & M_WRITE) {
+                            T* const p = dst + (s2 * 9 + l) * C.plane;
+                            *p = v;
+                            if (img && dxi) p[oxi] = v;  // walls: column images only
+                        }
                     }
             }
         }
         if (__any_sync(FULL, bad) && tx == 0) atomicOr(O.flag, 1);
-        if ((MODE & M_WRITE) && collided &&
+        if ((MODE & M_WRITE) && collided && narrow &&
             (x < PULL_GX || x >= nx - PULL_GX || (!WALL && (z < PULL_GZ || z >= lnz - PULL_GZ))))
             write_images<T, NS>(C, fout, x, z, lnz, prow0);
         if (MODE & M_OBS) {

@@ -1,6 +1,7 @@
 """Python binding of liblbm.so (argument marshalling only).
 
-The functions below carry the names of the C ABI in include/lbm.h and do nothing but convert
+The functions below carry the names of the C ABI in include/lbm.h and include/lbm3d.h (the
+three-dimensional extension, lbm3_*) and do nothing but convert
 arguments; every step of the method runs in the library's CUDA kernels.  There is no CPU
 fallback: if the library is missing or cannot be loaded, loading raises.
 """
@@ -49,7 +50,13 @@ class lbm_obs(ctypes.Structure):
                 ("pxx_x", _DP)]
 
 
-# Every symbol declared in include/lbm.h: name -> (restype, argtypes)
+class lbm3_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("n_species", ctypes.c_int),
+                ("precision", ctypes.c_int), ("z_boundary", ctypes.c_int), ("device", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+# Every symbol declared in include/lbm.h and include/lbm3d.h: name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 SIGNATURES = {
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(lbm_desc)]),
@@ -96,6 +103,18 @@ SIGNATURES = {
     "lbm_adjoint_steps": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_int]),
     "lbm_adjoint_objective": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int]),
     "lbm_adjoint_initial": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    "lbm3_default_desc": (None, [ctypes.POINTER(lbm3_desc)]),
+    "lbm3_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(lbm3_desc)]),
+    "lbm3_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_params)]),
+    "lbm3_set_fields": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "lbm3_get_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "lbm3_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm3_totals": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "lbm3_synchronize": (ctypes.c_int, [_VP]),
+    "lbm3_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm3_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm3_last_error": (ctypes.c_char_p, [_VP]),
+    "lbm3_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -133,6 +152,12 @@ def load(build_if_missing: bool = True):
 def _check(rc, ctx=None):
     if rc != LBM_OK:
         msg = load().lbm_last_error(ctx)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+def _check3(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = load().lbm3_last_error(ctx)
         raise LbmError(rc, msg.decode() if msg else "")
 
 
@@ -587,3 +612,86 @@ class ObsSeries:
                 res[k] = v[i]
             out.append(res)
         return out
+
+
+# ---- the three-dimensional extension (include/lbm3d.h) ---------------------------------------
+
+def lbm3_default_desc() -> lbm3_desc:
+    d = lbm3_desc()
+    load().lbm3_default_desc(ctypes.byref(d))
+    return d
+
+
+def lbm3_create(d: lbm3_desc):
+    h = ctypes.c_void_p()
+    _check3(load().lbm3_create(ctypes.byref(h), ctypes.byref(d)), None)
+    return h
+
+
+class Lattice3:
+    """One three-dimensional simulation on the GPU (D3Q19, lbm3_*), with numpy I/O: fields are
+    [nz][ny][nx], populations [n_species][19][nz][ny][nx]."""
+
+    def __init__(self, nx, ny, nz, n_species=2, precision=LBM_FP32, z_boundary=LBM_PERIODIC, device=0,
+                 stream=None, **params):
+        d = lbm3_default_desc()
+        d.nx, d.ny, d.nz, d.n_species, d.precision = nx, ny, nz, n_species, precision
+        d.z_boundary, d.device, d.stream = z_boundary, device, stream
+        self.desc = d
+        self.nx, self.ny, self.nz, self.ns = nx, ny, nz, n_species
+        self.h = lbm3_create(d)
+        self.set_params(**params)
+
+    def set_params(self, **params):
+        self.params = make_params(**params)
+        _check3(load().lbm3_set_params(self.h, ctypes.byref(self.params)), self.h)
+
+    def set_fields(self, rho):
+        if hasattr(rho, "data_ptr"):
+            _check3(load().lbm3_set_fields(self.h, ctypes.c_void_p(rho.data_ptr()), LBM_DEVICE), self.h)
+            return
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ns, self.nz, self.ny, self.nx)
+        _check3(load().lbm3_set_fields(self.h, ctypes.c_void_p(rho.ctypes.data), LBM_HOST), self.h)
+
+    def step(self, n=1):
+        _check3(load().lbm3_step(self.h, int(n)), self.h)
+
+    def fields(self, populations=True):
+        """(rho [ns, nz, ny, nx], u [3, nz, ny, nx], f [ns, 19, nz, ny, nx] or None)."""
+        rho = np.zeros((self.ns, self.nz, self.ny, self.nx))
+        u = np.zeros((3, self.nz, self.ny, self.nx))
+        f = np.zeros((self.ns, 19, self.nz, self.ny, self.nx)) if populations else None
+        _check3(load().lbm3_get_fields(self.h, ctypes.c_void_p(rho.ctypes.data), ctypes.c_void_p(u.ctypes.data),
+                                       ctypes.c_void_p(f.ctypes.data) if f is not None else None, LBM_HOST), self.h)
+        return rho, u, f
+
+    def totals(self):
+        """(mass [ns], lattice momentum [3]) of the current state, FP64 sums."""
+        m = (ctypes.c_double * 2)()
+        j = (ctypes.c_double * 3)()
+        _check3(load().lbm3_totals(self.h, m, j), self.h)
+        return np.array(m[:self.ns]), np.array(j[:])
+
+    def synchronize(self):
+        _check3(load().lbm3_synchronize(self.h), self.h)
+
+    def profile(self, enable):
+        _check3(load().lbm3_profile(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self):
+        """(ms of the density pass, ms of the collide pass, steps) since profiling was enabled."""
+        ms = (ctypes.c_double * 2)()
+        n = ctypes.c_longlong(0)
+        _check3(load().lbm3_profile_read(self.h, ms, ctypes.byref(n)), self.h)
+        return ms[0], ms[1], n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -90,6 +90,46 @@ def disk_packing(nx: int, nz: int, fraction: float, seed: int, r_mean: float = 1
     return rho, float(covered.mean())
 
 
+def sphere_packing(nx: int, ny: int, nz: int, fraction: float, seed: int, r_mean: float = 8.0,
+                   r_spread: float = 2.0, rho_in: float = 1.2, rho_out: float = 0.05, periodic_z: bool = True,
+                   max_spheres: int = 1_000_000):
+    """Two-species density fields [2, nz, ny, nx] of a random polydisperse sphere packing, the
+    three-dimensional counterpart of disk_packing: spheres of uniform radius in
+    [r_mean - r_spread, r_mean + r_spread] with uniform centres, overlap allowed, added until the
+    covered volume reaches `fraction`; (rho_A, rho_B) = (rho_in, rho_out) inside, swapped outside.
+    Periodic in x and y; in z periodic or clipped by walls.  Returns (rho, covered fraction)."""
+    if not (0.0 <= fraction < 1.0):
+        raise ValueError("fraction must be in [0, 1)")
+    covered = np.zeros((nz, ny, nx), dtype=bool)
+    target = fraction * nx * ny * nz
+    count = 0
+    k = 0
+    while count < target and k < max_spheres:
+        u = uniform(seed, 4, offset=4 * k)
+        cx, cy, cz = u[0] * nx, u[1] * ny, u[2] * nz
+        r = r_mean + r_spread * (2.0 * u[3] - 1.0)
+        ax = [np.arange(int(np.floor(c - r)), int(np.ceil(c + r)) + 1) for c in (cx, cy, cz)]
+        if not periodic_z:
+            ax[2] = ax[2][(ax[2] >= 0) & (ax[2] < nz)]
+        ix, iy, iz = ax[0] % nx, ax[1] % ny, ax[2] % nz
+        dx = np.minimum(np.abs(ix - cx), nx - np.abs(ix - cx))
+        dy = np.minimum(np.abs(iy - cy), ny - np.abs(iy - cy))
+        dz = np.minimum(np.abs(iz - cz), nz - np.abs(iz - cz)) if periodic_z else np.abs(iz - cz)
+        inside = (dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2) <= r * r
+        xu, fx = np.unique(ix, return_index=True)
+        yu, fy = np.unique(iy, return_index=True)
+        zu, fz = np.unique(iz, return_index=True)
+        inside = inside[np.ix_(fz, fy, fx)]
+        sub = covered[np.ix_(zu, yu, xu)]
+        count += int(np.count_nonzero(inside & ~sub))
+        covered[np.ix_(zu, yu, xu)] = sub | inside
+        k += 1
+    rho = np.empty((2, nz, ny, nx))
+    rho[0] = np.where(covered, rho_in, rho_out)
+    rho[1] = np.where(covered, rho_out, rho_in)
+    return rho, float(covered.mean())
+
+
 # Normalisation of the interaction weights: Appendix B's tables satisfy sum W c c = 1, while
 # Eq. BULK (P_b = c_s^2 rho + c_s^2 (G1 + G2) psi^2 / 2) implies sum W c c = c_s^2.  The paper's
 # couplings only give stable phases near its printed densities under the latter, so every
@@ -157,4 +197,9 @@ def workload(name: str, seed: int = 1402):
                     rho=rho, steps=500, checkpoint=25,
                     target_u=1e-3 * uniform(seed + 1, 256), target_rho=0.3 + 0.6 * uniform(seed + 2, 256),
                     note=f"256x256 periodic disk packing, covered {frac:.3f}, body force 1e-5, 500 steps")
+    if name.startswith("emulsion3d_"):  # emulsion3d_N: an N^3 periodic A/B emulsion (3-D extension)
+        n = int(name.split("_")[1])
+        rho, frac = sphere_packing(n, n, n, 0.5, seed)
+        return dict(nx=n, ny=n, nz=n, n_species=2, z_boundary=0, params=dict(EMULSION_PARAMS), rho=rho, dim=3,
+                    note=f"{n}^3 periodic sphere packing, covered {frac:.3f}, radii 8 +- 2")
     raise KeyError(name)

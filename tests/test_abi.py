@@ -12,9 +12,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    """Every function declared in include/*.h (lbm_* and the three-dimensional lbm3_*)."""
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm3?_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported():
@@ -32,8 +37,8 @@ def test_struct_layouts_match_header(tmp_path):
     """Every field offset of the ctypes mirrors equals the C compiler's layout of include/lbm.h."""
     import subprocess
 
-    structs = {"lbm_desc": L.lbm_desc, "lbm_params": L.lbm_params, "lbm_obs": L.lbm_obs}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
+    structs = {"lbm_desc": L.lbm_desc, "lbm_params": L.lbm_params, "lbm_obs": L.lbm_obs, "lbm3_desc": L.lbm3_desc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', '#include "lbm3d.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
         for fname, _ in cls._fields_:
