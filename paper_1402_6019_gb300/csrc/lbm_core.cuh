@@ -63,28 +63,30 @@ LBM_HD double psi_of(const StepConst<double>& C, int s, double rho) {
 
 // ---------------------------------------------------------------------------------------
 // Eq. FORCE: F = -psi(x) sum_{l=1..24} K(|c_l|^2) psi(x + c_l) c_l, with
-// K = G1 w + G2 p folded into the tables kx/kz.  p[dz+2][dx+2] = psi(x+dx, z+dz).
+// K = G1 w + G2 p folded into the tables kx/kz.  p[dz+2][dx+2] = psi(x+dx, z+dz).  Antipodal
+// links have opposite c, so the sum runs over the 12 differences psi(c) - psi(-c), gathered
+// shell by shell and scaled once per shell: kx at (1,0), (1,1), (2,0), (1,2), (2,2) holds K(1),
+// K(2), 2 K(4), K(5), 2 K(8).
 // ---------------------------------------------------------------------------------------
 template <typename T>
 LBM_HD void intra_force(const StepConst<T>& C, int s, const T (&p)[5][5], T& fx, T& fz) {
-    // one partial sum per stencil row: five independent chains instead of one long one
-    T ax[5], az[5];
-#pragma unroll
-    for (int dz = -2; dz <= 2; ++dz) {
-        ax[dz + 2] = T(0);
-        az[dz + 2] = T(0);
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-            if (dx == 0 && dz == 0) continue;
-            const int i = (dz + 2) * 5 + dx + 2;
-            if (dx != 0) ax[dz + 2] += C.kx[s][i] * p[dz + 2][dx + 2];
-            if (dz != 0) az[dz + 2] += C.kz[s][i] * p[dz + 2][dx + 2];
-        }
-    }
-    const T sx = (ax[0] + ax[4]) + (ax[1] + ax[3]) + ax[2];
-    const T sz = (az[0] + az[4]) + (az[1] + az[3]);
-    fx = -p[2][2] * sx;
-    fz = -p[2][2] * sz;
+#define LBM_Q(dx, dz) p[(dz) + 2][(dx) + 2]
+    const T d10 = LBM_Q(1, 0) - LBM_Q(-1, 0), d01 = LBM_Q(0, 1) - LBM_Q(0, -1);
+    const T d11 = LBM_Q(1, 1) - LBM_Q(-1, -1), e11 = LBM_Q(-1, 1) - LBM_Q(1, -1);
+    const T d20 = LBM_Q(2, 0) - LBM_Q(-2, 0), d02 = LBM_Q(0, 2) - LBM_Q(0, -2);
+    const T d21 = LBM_Q(2, 1) - LBM_Q(-2, -1), e21 = LBM_Q(-2, 1) - LBM_Q(2, -1);
+    const T d12 = LBM_Q(1, 2) - LBM_Q(-1, -2), e12 = LBM_Q(-1, 2) - LBM_Q(1, -2);
+    const T d22 = LBM_Q(2, 2) - LBM_Q(-2, -2), e22 = LBM_Q(-2, 2) - LBM_Q(2, -2);
+    const T* k = C.kx[s];
+    const T k1 = k[13], k2 = k[18], k4 = k[14], k5 = k[23], k8 = k[24];
+    // shell |c|^2 = 5: the links (2,1), (-2,1), (1,2), (-1,2)
+    const T x5 = T(2) * (d21 - e21) + (d12 - e12);
+    const T z5 = T(2) * (d12 + e12) + (d21 + e21);
+    const T sx = ((k1 * d10 + k2 * (d11 - e11)) + (k4 * d20 + k5 * x5)) + k8 * (d22 - e22);
+    const T sz = ((k1 * d01 + k2 * (d11 + e11)) + (k4 * d02 + k5 * z5)) + k8 * (d22 + e22);
+    fx = -LBM_Q(0, 0) * sx;
+    fz = -LBM_Q(0, 0) * sz;
+#undef LBM_Q
 }
 
 // ---------------------------------------------------------------------------------------
@@ -133,26 +135,17 @@ LBM_HD void intra_stress(const StepConst<T>& C, int s, const T (&p)[5][5], T& sx
 // ---------------------------------------------------------------------------------------
 template <typename T>
 LBM_HD void cross_force(const StepConst<T>& C, const T (&ra)[3][3], const T (&rb)[3][3], T (&F)[2][2]) {
-    T ax = T(0), az = T(0), bx = T(0), bz = T(0);
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dz == 0) continue;
-            const int i = (dz + 1) * 3 + dx + 1;
-            if (dx != 0) {
-                ax += C.kcx[i] * rb[dz + 1][dx + 1];
-                bx += C.kcx[i] * ra[dz + 1][dx + 1];
-            }
-            if (dz != 0) {
-                az += C.kcz[i] * rb[dz + 1][dx + 1];
-                bz += C.kcz[i] * ra[dz + 1][dx + 1];
-            }
-        }
-    F[0][0] -= ra[1][1] * ax;
-    F[0][1] -= ra[1][1] * az;
-    F[1][0] -= rb[1][1] * bx;
-    F[1][1] -= rb[1][1] * bz;
+    // over the 4 antipodal differences of the first belt, shell by shell (kcx at (1,0), (1,1):
+    // G_AB w8(1), G_AB w8(2))
+    const T k1 = C.kcx[1 * 3 + 2], k2 = C.kcx[2 * 3 + 2];
+    const T a10 = rb[1][2] - rb[1][0], a01 = rb[2][1] - rb[0][1];
+    const T a11 = rb[2][2] - rb[0][0], b11 = rb[2][0] - rb[0][2];  // (1,1) and (-1,1)
+    const T c10 = ra[1][2] - ra[1][0], c01 = ra[2][1] - ra[0][1];
+    const T c11 = ra[2][2] - ra[0][0], e11 = ra[2][0] - ra[0][2];
+    F[0][0] -= ra[1][1] * (k1 * a10 + k2 * (a11 - b11));
+    F[0][1] -= ra[1][1] * (k1 * a01 + k2 * (a11 + b11));
+    F[1][0] -= rb[1][1] * (k1 * c10 + k2 * (c11 - e11));
+    F[1][1] -= rb[1][1] * (k1 * c01 + k2 * (c11 + e11));
 }
 
 // Cross-species stress, by analogy with App. A's first-belt shells: the pair product
