@@ -38,9 +38,10 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_SITE = {("fp32", 2): 144, ("fp64", 2): 288, ("fp32", 1): 72, ("fp64", 1): 144}
 # The FP64 step (two species, observables every step) is bound by the FP64 pipe: FP64 flops per
-# site-update counted by ncu (331 DFMA, 198 DADD, 101 DMUL; profiles/k_pull_emulsion_1024_fp64.md)
+# site-update counted by ncu (242 DFMA, 244 DADD, 119 DMUL; profiles/k_pull_emulsion_1024_fp64.md)
 # against 2 DFMA per SM per cycle x 152 SMs x 2 flops x 2.07 GHz
-FP64_FLOPS_PER_SITE = 961
+FP64_FLOPS_PER_SITE = 847
+FP64_INSTR_PER_SITE = 605  # the same counts as instructions: each occupies the FP64 pipe once
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 L2_BYTES = 126 << 20          # L2 of a GB300 (nvidia-smi / device properties: 126.5 MiB)
@@ -285,7 +286,8 @@ def cpu_baseline(w, seconds=12.0, lib_run=None, tol=1e-4, err_steps=1000):
     oracle.build()
     n = 256
     rho, prm = oracle_sample(w, n)
-    ref = oracle.RefLattice(n, rho.shape[1], w["n_species"], w["z_boundary"], **prm)
+    cz, cx = rho.shape[1], rho.shape[2]  # the cut (smaller than n x n when the lattice is)
+    ref = oracle.RefLattice(cx, cz, w["n_species"], w["z_boundary"], **prm)
     ref.set_fields(rho)
     t0 = time.perf_counter()
     k = 0
@@ -297,8 +299,8 @@ def cpu_baseline(w, seconds=12.0, lib_run=None, tol=1e-4, err_steps=1000):
             break
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    out = {"value": round(n * rho.shape[1] * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-           "sample": f"{k} oracle steps (step + observables) on a {n}x{n} cut of the workload, "
+    out = {"value": round(cx * cz * k / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{k} oracle steps (step + observables) on a {cx}x{cz} cut of the workload, "
                      f"{dt:.1f} s wall, OpenMP threads={cores}"}
     if lib_run is None:
         return out, None
@@ -310,8 +312,8 @@ def cpu_baseline(w, seconds=12.0, lib_run=None, tol=1e-4, err_steps=1000):
     r_obs = ref.observables()
     g_rho, g_u, g_obs = lib_run(rho, prm, steps)
     rel = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
-    errs = accuracy.observable_errors(g_obs, r_obs, ref.scales(), tol, n, float(np.sum(r_obs["mass"])))
-    errors = {"vs": "FP64 oracle", "sample": f"{n}x{rho.shape[1]} cut of the workload, {steps} steps, "
+    errs = accuracy.observable_errors(g_obs, r_obs, ref.scales(), tol, cx, float(np.sum(r_obs["mass"])))
+    errors = {"vs": "FP64 oracle", "sample": f"{cx}x{cz} cut of the workload, {steps} steps, "
                                              "observables every step (the library's launch configuration)",
               "tol": tol, "rho": rel(g_rho, r_rho), "u": rel(g_u, r_u),
               "observables": {k_: {"rel": float(f"{e[2]:.3g}"),
@@ -339,7 +341,8 @@ def run_reference(a, w):
     oracle.build()
     n = 256
     rho, prm = oracle_sample(w, n)
-    ref = oracle.RefLattice(n, rho.shape[1], w["n_species"], w["z_boundary"], **prm)
+    cz, cx = rho.shape[1], rho.shape[2]
+    ref = oracle.RefLattice(cx, cz, w["n_species"], w["z_boundary"], **prm)
     ref.set_fields(rho)
     for _ in range(a.warmup):
         ref.step(1)
@@ -350,13 +353,13 @@ def run_reference(a, w):
         ref.observables()
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    value = n * rho.shape[1] * a.steps / dt / 1e6
-    sample = f"{a.steps} timed oracle steps (step + observables) on a {n}x{n} cut of {a.workload}"
+    value = cx * cz * a.steps / dt / 1e6
+    sample = f"{a.steps} timed oracle steps (step + observables) on a {cx}x{cz} cut of {a.workload}"
     print(json.dumps({
         "impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": a.workload, "sample": f"{n}x{n}"},
+        "data": "synthetic", "config": {"workload": a.workload, "sample": f"{cx}x{cz}"},
         "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -872,6 +875,8 @@ def main():
                     "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
                     "peak_source": "FP64 pipe: 2 DFMA per SM per cycle (ncu peak), 152 SMs, 2.07 GHz",
                     "flops_per_site": FP64_FLOPS_PER_SITE, "hbm_frac": round(achieved / peak, 4),
+                    "fp64_pipe_frac": round(FP64_INSTR_PER_SITE * sites / (kern_avg_ms * 1e-3) /
+                                            (FP64_PEAK_TFLOPS / 2 * 1e12), 4),
                     "kernel": "lbm::k_pull<double, 2, M_WRITE|M_OBS>", "kernel_ms": round(kern_avg_ms, 5),
                     "kernel_ms_serialised": round(kern_ser_ms, 5)}
     else:
