@@ -637,6 +637,8 @@ def run_3d(a, w):
     torch.cuda.set_stream(stream)
     lat = L.Lattice3(nx, ny, nz, ns, prec, w["z_boundary"], device=local, stream=stream.cuda_stream, **w["params"])
     lat.set_fields(w["rho"])
+    # the collide pass's tile shape, picked by the library's autotuner on this lattice (untimed)
+    shape, tune_ms = lat.autotune(max(a.autotune, 10))
     lat.step(a.warmup)
     lat.synchronize()
     barrier()
@@ -696,6 +698,8 @@ def run_3d(a, w):
         "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": a.workload, "nx": nx, "ny": ny, "nz": nz, "n_species": ns, "precision": a.precision,
                    "lattice": "D3Q19", "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "tile_shape": ["32x4x2", "32x2x4", "32x8x1", "32x4x4"][shape],
+                   "autotune_ms_per_step": [round(t, 5) for t in tune_ms],
                    "l2": f"one lattice of {2 * 19 * ns * sites * (4 if a.precision == 'fp32' else 8) / 2**20:.0f} "
                          f"MiB of populations (both copies) > {L2_BYTES / 2**20:.0f} MiB L2; no flush"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * a.steps, "clocks": clk.summary(),

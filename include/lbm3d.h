@@ -90,6 +90,16 @@ int lbm3_synchronize(lbm3_ctx *c);
 int lbm3_profile(lbm3_ctx *c, int enable);
 int lbm3_profile_read(lbm3_ctx *c, double *ms, long long *steps);
 
+/* Tile shapes of the collide pass: 0 = 32 x 4 x 2 sites (the default), 1 = 32 x 2 x 4,
+   2 = 32 x 8 x 1 (256 threads each), 3 = 32 x 4 x 4 (512 threads).  The shape changes which
+   CTA does which sites and how much of the psi / rho halo each reads, not the arithmetic:
+   results are bit-identical.  lbm3_autotune times `steps` (1 .. 10000) steps of each shape on
+   the context's own lattice, keeps the fastest, and puts the state and step counter back as
+   they were; *chosen (may be NULL) receives the shape, ms[4] (may be NULL) the milliseconds per
+   step of each.  Synchronises.  lbm3_set_shape sets a shape directly (LBM_EINVAL outside 0..3). */
+int lbm3_autotune(lbm3_ctx *c, int steps, int *chosen, double *ms);
+int lbm3_set_shape(lbm3_ctx *c, int shape);
+
 /* One-line description of the last failure on c (or of the last lbm3_create failure when
    c is NULL). */
 const char *lbm3_last_error(const lbm3_ctx *c);

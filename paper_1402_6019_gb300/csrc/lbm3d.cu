@@ -100,10 +100,15 @@ __device__ __forceinline__ double2 vswap(double2 a) { return make_double2(a.y, a
 // ---- geometry and constants ----------------------------------------------------------------
 
 constexpr int GX = 4, GY = 2, GZ = 2;         // ghosts of the psi / rho volumes
-constexpr int TX = 32, TY = 4, TZ = 2;        // a CTA's tile (one thread per site)
-constexpr int NT3 = TX * TY * TZ;
-constexpr int BX = TX + 2 * GX, BY = TY + 2 * GY, BZ = TZ + 2 * GZ;  // the box of a tile
+constexpr int TX = 32;                        // tile width: one warp per tile row
+constexpr int BX = TX + 2 * GX;               // box width (x from x0 - 4: 16-byte aligned)
 constexpr long long WAIT_LIMIT = 2000000000LL;  // clock cycles of the bounded wait (~1 s)
+// The tile shapes (TY x TZ rows of 32 sites, one thread per site) lbm3_autotune chooses from:
+// the halo box of a tile is (TY + 4) x (TZ + 4) rows, so flatter tiles read more halo from L2
+// per site and taller ones hold fewer CTAs per SM.
+constexpr int NSHAPE = 4;
+constexpr int SHAPE_TY[NSHAPE] = {4, 2, 8, 4};
+constexpr int SHAPE_TZ[NSHAPE] = {2, 4, 1, 4};
 
 template <typename T>
 struct Step3 {
@@ -197,8 +202,9 @@ __global__ void __launch_bounds__(128) k3_density(const T* __restrict__ f, T* __
 
 enum { K3_WRITE = 1, K3_FIELDS = 2 };
 
-template <typename T>
+template <typename T, int TY, int TZ>
 struct Smem3 {
+    static constexpr int BY = TY + 2 * GY, BZ = TZ + 2 * GZ;
     typename PairOf<T>::V box[2][BZ][BY][BX];  // psi, rho pairs of the tile and its halo
     alignas(8) unsigned long long bar;
 };
@@ -228,13 +234,13 @@ __device__ __forceinline__ V addc(V acc, V d) {
     return acc;
 }
 
-template <typename T, int MODE, int NS>
-__global__ void __launch_bounds__(NT3, 2)
+template <typename T, int MODE, int NS, int TY, int TZ>
+__global__ void __launch_bounds__(TX* TY* TZ, TX* TY* TZ > 256 ? 1 : 2)
     k3_step(const __grid_constant__ CUtensorMap vmap, const T* __restrict__ fin, T* __restrict__ fout,
             const Step3<T> C, int* __restrict__ flag, double* __restrict__ fields) {
     using V = typename PairOf<T>::V;
     extern __shared__ __align__(1024) unsigned char smem3[];
-    Smem3<T>& S = *reinterpret_cast<Smem3<T>*>(smem3);
+    Smem3<T, TY, TZ>& S = *reinterpret_cast<Smem3<T, TY, TZ>*>(smem3);
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
     const int tid = (tz * TY + ty) * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -519,30 +525,43 @@ __global__ void __launch_bounds__(256) k3_totals(const T* __restrict__ f, const 
     if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-template <typename T, int MODE, int NS>
+template <typename T, int MODE, int NS, int TY, int TZ>
 cudaError_t launch_step3(const CUtensorMap& map, const T* fin, T* fout, const Step3<T>& C, int* flag, double* fields,
                          cudaStream_t st) {
-    const size_t smem = sizeof(Smem3<T>);
+    const size_t smem = sizeof(Smem3<T, TY, TZ>);
     static bool attr = false;  // per template instance
     if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k3_step<T, MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(k3_step<T, MODE, NS, TY, TZ>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const dim3 grid((C.nx + TX - 1) / TX, (C.ny + TY - 1) / TY, (C.nz + TZ - 1) / TZ);
-    k3_step<T, MODE, NS><<<grid, dim3(TX, TY, TZ), smem, st>>>(map, fin, fout, C, flag, fields);
+    k3_step<T, MODE, NS, TY, TZ><<<grid, dim3(TX, TY, TZ), smem, st>>>(map, fin, fout, C, flag, fields);
     return cudaGetLastError();
 }
 
+template <typename T, int MODE, int NS>
+cudaError_t launch_shape(int shape, const CUtensorMap& map, const T* fin, T* fout, const Step3<T>& C, int* flag,
+                         double* fields, cudaStream_t st) {
+    switch (shape) {
+        case 0: return launch_step3<T, MODE, NS, SHAPE_TY[0], SHAPE_TZ[0]>(map, fin, fout, C, flag, fields, st);
+        case 1: return launch_step3<T, MODE, NS, SHAPE_TY[1], SHAPE_TZ[1]>(map, fin, fout, C, flag, fields, st);
+        case 2: return launch_step3<T, MODE, NS, SHAPE_TY[2], SHAPE_TZ[2]>(map, fin, fout, C, flag, fields, st);
+        case 3: return launch_step3<T, MODE, NS, SHAPE_TY[3], SHAPE_TZ[3]>(map, fin, fout, C, flag, fields, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// the step pass in the chosen tile shape; the fields pass (lbm3_get_fields) in shape 0
 template <typename T>
-cudaError_t launch_step3_any(int mode, int ns, const CUtensorMap& map, const T* fin, T* fout, const Step3<T>& C,
-                             int* flag, double* fields, cudaStream_t st) {
+cudaError_t launch_step3_any(int mode, int ns, int shape, const CUtensorMap& map, const T* fin, T* fout,
+                             const Step3<T>& C, int* flag, double* fields, cudaStream_t st) {
     if (mode == K3_WRITE)
-        return ns == 2 ? launch_step3<T, K3_WRITE, 2>(map, fin, fout, C, flag, fields, st)
-                       : launch_step3<T, K3_WRITE, 1>(map, fin, fout, C, flag, fields, st);
-    return ns == 2 ? launch_step3<T, K3_FIELDS, 2>(map, fin, fout, C, flag, fields, st)
-                   : launch_step3<T, K3_FIELDS, 1>(map, fin, fout, C, flag, fields, st);
+        return ns == 2 ? launch_shape<T, K3_WRITE, 2>(shape, map, fin, fout, C, flag, fields, st)
+                       : launch_shape<T, K3_WRITE, 1>(shape, map, fin, fout, C, flag, fields, st);
+    return ns == 2 ? launch_step3<T, K3_FIELDS, 2, SHAPE_TY[0], SHAPE_TZ[0]>(map, fin, fout, C, flag, fields, st)
+                   : launch_step3<T, K3_FIELDS, 1, SHAPE_TY[0], SHAPE_TZ[0]>(map, fin, fout, C, flag, fields, st);
 }
 
 }  // namespace lbm3
@@ -564,7 +583,8 @@ struct lbm3_ctx {
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* vol = nullptr;               // psi and rho volumes: [2][gz][gy][gpitch] pairs
-    alignas(64) unsigned char map[128] = {};  // TMA descriptor of vol
+    alignas(64) unsigned char map[NSHAPE][128] = {};  // TMA descriptors of vol, per tile shape
+    int shape = 0;                     // tile shape of the step pass (lbm3_autotune)
     int* flag = nullptr;
     double* staging = nullptr;         // lbm3_get_fields / lbm3_set_fields from the host
     size_t staging_bytes = 0;
@@ -672,7 +692,7 @@ static void release3(lbm3_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-static int make_vol_map(lbm3_ctx* c) {
+static int make_vol_map(lbm3_ctx* c, int shape) {
     const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(lbm::tensor_map_encoder());
     if (!encode) return 1;
     const cuuint64_t es = c->esize;
@@ -681,9 +701,10 @@ static int make_vol_map(lbm3_ctx* c) {
                                 (cuuint64_t)(c->d.nz + 2 * GZ), 2};
     const cuuint64_t strides[3] = {(cuuint64_t)2 * c->gpitch * es, (cuuint64_t)2 * c->gpitch * (c->d.ny + 2 * GY) * es,
                                    (cuuint64_t)2 * c->gvol * es};
-    const cuuint32_t box[4] = {(cuuint32_t)(2 * BX), (cuuint32_t)BY, (cuuint32_t)BZ, 2};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * BX), (cuuint32_t)(SHAPE_TY[shape] + 2 * GY),
+                               (cuuint32_t)(SHAPE_TZ[shape] + 2 * GZ), 2};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(c->map),
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(c->map[shape]),
                               c->esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                               c->vol, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -741,7 +762,9 @@ extern "C" int lbm3_create(lbm3_ctx** out, const lbm3_desc* d) {
     CKC3(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d->device));
     c->nblk_tot = std::max(1, std::min(4 * nsm, (int)((c->n + 255) / 256)));
     CKC3(cudaMalloc(&c->part, (size_t)c->nblk_tot * 5 * sizeof(double)));
-    if (make_vol_map(c) != 0) return bail(fail3(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the psi / rho volumes"));
+    for (int k = 0; k < NSHAPE; ++k)
+        if (make_vol_map(c, k) != 0)
+            return bail(fail3(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the psi / rho volumes"));
     CKC3(cudaStreamSynchronize(c->stream));
 #undef CKC3
     refresh3(c);
@@ -837,12 +860,13 @@ static cudaError_t density3(lbm3_ctx* c) {
 }
 
 static cudaError_t collide3(lbm3_ctx* c, int mode, double* fields) {
-    const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(c->map);
+    const int shape = mode == K3_WRITE ? c->shape : 0;
+    const CUtensorMap& map = *reinterpret_cast<const CUtensorMap*>(c->map[shape]);
     if (c->d.precision == LBM_FP64)
-        return launch_step3_any<double>(mode, c->d.n_species, map, (const double*)c->f[c->cur],
+        return launch_step3_any<double>(mode, c->d.n_species, shape, map, (const double*)c->f[c->cur],
                                         (double*)c->f[c->cur ^ 1], c->c64, c->flag, fields, c->stream);
-    return launch_step3_any<float>(mode, c->d.n_species, map, (const float*)c->f[c->cur], (float*)c->f[c->cur ^ 1],
-                                   c->c32, c->flag, fields, c->stream);
+    return launch_step3_any<float>(mode, c->d.n_species, shape, map, (const float*)c->f[c->cur],
+                                   (float*)c->f[c->cur ^ 1], c->c32, c->flag, fields, c->stream);
 }
 
 extern "C" int lbm3_step(lbm3_ctx* c, int nsteps) {
@@ -955,5 +979,62 @@ extern "C" int lbm3_profile_read(lbm3_ctx* c, double* ms, long long* steps) {
         ms[1] = t[1];
     }
     if (steps) *steps = (long long)(c->ev_used / 4);
+    return LBM_OK;
+}
+
+extern "C" int lbm3_autotune(lbm3_ctx* c, int steps, int* chosen, double* ms) {
+    if (!c) return LBM_EINVAL;
+    if (steps < 1 || steps > 10000) return fail3(c, LBM_EINVAL, "steps must be in 1 .. 10000");
+    if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
+    CK3(cudaSetDevice(c->d.device));
+    // the state is kept aside and put back: the shapes change the schedule, not the arithmetic
+    const size_t fbytes = (size_t)c->d.n_species * 19 * c->plane * c->esize;
+    void* saved = nullptr;
+    CK3(cudaMalloc(&saved, fbytes));
+    cudaError_t e = cudaMemcpyAsync(saved, c->f[c->cur], fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    const int cur0 = c->cur, shape0 = c->shape;
+    const long long step0 = c->step;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    double t[NSHAPE] = {0.0, 0.0, 0.0, 0.0};
+    int best = 0;
+    for (int k = 0; k < NSHAPE && e == cudaSuccess; ++k) {
+        c->shape = k;
+        e = collide3(c, K3_WRITE, nullptr);  // one untimed pass (module load, caches)
+        if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+        for (int i = 0; i < steps && e == cudaSuccess; ++i) {
+            e = density3(c);
+            if (e == cudaSuccess) e = collide3(c, K3_WRITE, nullptr);
+            c->cur ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float v = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&v, a, b);
+        t[k] = (double)v / steps;
+        if (t[k] < t[best]) best = k;
+        c->cur = cur0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->f[c->cur], saved, fbytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(saved);
+    c->cur = cur0;
+    c->step = step0;
+    c->shape = e == cudaSuccess ? best : shape0;
+    CK3(e);
+    CK3(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    if (chosen) *chosen = best;
+    if (ms)
+        for (int k = 0; k < NSHAPE; ++k) ms[k] = t[k];
+    return LBM_OK;
+}
+
+extern "C" int lbm3_set_shape(lbm3_ctx* c, int shape) {
+    if (!c) return LBM_EINVAL;
+    if (shape < 0 || shape >= NSHAPE) return fail3(c, LBM_EINVAL, "shape must be in 0 .. %d", NSHAPE - 1);
+    c->shape = shape;
     return LBM_OK;
 }

@@ -113,6 +113,8 @@ SIGNATURES = {
     "lbm3_synchronize": (ctypes.c_int, [_VP]),
     "lbm3_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm3_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm3_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "lbm3_set_shape": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm3_last_error": (ctypes.c_char_p, [_VP]),
     "lbm3_destroy": (None, [_VP]),
 }
@@ -674,6 +676,17 @@ class Lattice3:
 
     def synchronize(self):
         _check3(load().lbm3_synchronize(self.h), self.h)
+
+    def autotune(self, steps=10):
+        """Pick the collide pass's tile shape by timing each here; returns (shape, ms per step of
+        each shape).  The state is left as it was."""
+        chosen = ctypes.c_int(0)
+        ms = (ctypes.c_double * 4)()
+        _check3(load().lbm3_autotune(self.h, int(steps), ctypes.byref(chosen), ms), self.h)
+        return chosen.value, tuple(ms[:])
+
+    def set_shape(self, shape):
+        _check3(load().lbm3_set_shape(self.h, int(shape)), self.h)
 
     def profile(self, enable):
         _check3(load().lbm3_profile(self.h, 1 if enable else 0), self.h)

@@ -149,3 +149,33 @@ def test_invalid_input_rejected():
         lat.step(1)  # no fields yet
     with pytest.raises(L.LbmError):
         lat.set_params(**dict(W.EMULSION_PARAMS, weight_preset=1))
+
+
+@pytest.mark.parametrize("precision", [L.LBM_FP64, L.LBM_FP32])
+def test_tile_shapes_are_bit_identical_and_autotune_restores_the_state(precision):
+    """The collide pass's tile shapes change which CTA does which sites, not the arithmetic:
+    every shape gives the same populations bit for bit (a ragged lattice with walls, so every
+    shape has partial tiles); lbm3_autotune leaves the state and step counter as they were."""
+    nx, ny, nz = 45, 18, 13
+    rho, _ = W.sphere_packing(nx, ny, nz, 0.4, seed=43, r_mean=3, r_spread=1, periodic_z=False)
+    prm = dict(W.EMULSION_PARAMS, G_AB=0.587, wall_u=(-0.01, 0.01), body_force=1e-5)
+    got = []
+    for shape in range(4):
+        lat = L.Lattice3(nx, ny, nz, 2, precision, 1, **prm)
+        lat.set_shape(shape)
+        lat.set_fields(rho)
+        lat.step(15)
+        got.append(lat.fields()[2])
+    for g in got[1:]:
+        assert np.array_equal(g, got[0])
+    lat = L.Lattice3(nx, ny, nz, 2, precision, 1, **prm)
+    lat.set_fields(rho)
+    lat.step(5)
+    before = lat.fields()[2]
+    shape, ms = lat.autotune(3)
+    assert 0 <= shape < 4 and min(ms) > 0 and ms[shape] == min(ms)
+    assert np.array_equal(lat.fields()[2], before)
+    lat.step(10)
+    assert np.array_equal(lat.fields()[2], got[0])
+    with pytest.raises(L.LbmError):
+        lat.set_shape(4)
