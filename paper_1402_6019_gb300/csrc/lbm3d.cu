@@ -436,44 +436,103 @@ __global__ void __launch_bounds__(TX* TY* TZ, TX* TY* TZ > 256 ? 1 : 2)
 
     if constexpr ((MODE & K3_WRITE) != 0) {
         // ---- shifted-velocity BGK (Sec. II) and streaming ----
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const T om = C.omega[s], keep = T(1) - om, tir = C.tau[s] * ir[s];
-            const T ux = upx + F[s][0] * tir, uy = upy + F[s][1] * tir, uz = upz + F[s][2] * tir;
-            const T u15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-            const T b = om * rho[s];
-            const T base = om * drho[s] - b * u15;  // omega (drho - 3/2 rho u^2)
-            T g[19];
-            g[0] = keep * f[s][0] + w19<T>(0) * base;
-#pragma unroll
-            for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
-                const T cu = T(c3x(l)) * ux + T(c3y(l)) * uy + T(c3z(l)) * uz;
-                const T w = w19<T>(l);
-                const T even = w * base + (w * T(4.5)) * b * cu * cu;
-                const T odd = (w * T(3)) * b * cu;
-                g[l] = (keep * f[s][l] + even) + odd;
-                g[l + 1] = (keep * f[s][l + 1] + even) - odd;
+        // Destinations: the site's index plus one offset per axis, chosen by the sign of c_l; the
+        // periodic wrap is folded into those offsets once per thread (walls in z are handled by
+        // bounce-back below).
+        const long long row = C.pitch, lay = (long long)C.ny * C.pitch;
+        const bool wall_lo = C.zbc && z == 0, wall_hi = C.zbc && z == C.nz - 1;
+        // FP32: the wrapped offsets of each axis precomputed; FP64 (short of registers): the
+        // destination of each population wrapped where it is stored
+        long long oxm = 0, oxp = 0, oym = 0, oyp = 0, ozm = 0, ozp = 0;
+        if constexpr (sizeof(T) == 4) {
+            oxm = x == 0 ? C.nx - 1 : -1;
+            oxp = x == C.nx - 1 ? -(C.nx - 1) : 1;
+            oym = y == 0 ? (C.ny - 1) * row : -row;
+            oyp = y == C.ny - 1 ? -(C.ny - 1) * row : row;
+            ozm = z == 0 ? (C.nz - 1) * lay : -lay;
+            ozp = z == C.nz - 1 ? -(C.nz - 1) * lay : lay;
+        }
+        auto push = [&](int s, int l, T v) {
+            const int cx_ = c3x(l), cy_ = c3y(l), cz_ = c3z(l);
+            if ((cz_ < 0 && wall_lo) || (cz_ > 0 && wall_hi)) {  // halfway bounce-back with Ladd's term
+                const T uw = cz_ < 0 ? C.wall_u[0] : C.wall_u[1];
+                fout[(s * 19 + opp19(l)) * C.plane + i] = v - T(6) * w19<T>(l) * rho[s] * T(cx_) * uw;
+                return;
             }
-#pragma unroll
-            for (int l = 0; l < 19; ++l) {
-                int xd = x + c3x(l), yd = y + c3y(l), zd = z + c3z(l);
+            if constexpr (sizeof(T) == 4) {
+                const long long o = (cx_ < 0 ? oxm : (cx_ > 0 ? oxp : 0)) + (cy_ < 0 ? oym : (cy_ > 0 ? oyp : 0)) +
+                                    (cz_ < 0 ? ozm : (cz_ > 0 ? ozp : 0));
+                fout[(s * 19 + l) * C.plane + i + o] = v;
+            } else {
+                int xd = x + cx_, yd = y + cy_, zd = z + cz_;
                 xd = xd < 0 ? xd + C.nx : (xd >= C.nx ? xd - C.nx : xd);
                 yd = yd < 0 ? yd + C.ny : (yd >= C.ny ? yd - C.ny : yd);
-                int ld = l;
-                T v = g[l];
-                if (zd < 0 || zd >= C.nz) {
-                    if (C.zbc) {  // halfway bounce-back into this site with Ladd's term
-                        const T uw = zd < 0 ? C.wall_u[0] : C.wall_u[1];
-                        v = g[l] - T(6) * w19<T>(l) * rho[s] * T(c3x(l)) * uw;
-                        ld = opp19(l);
-                        xd = x;
-                        yd = y;
-                        zd = z;
-                    } else {
-                        zd = zd < 0 ? zd + C.nz : zd - C.nz;
-                    }
+                zd = zd < 0 ? zd + C.nz : (zd >= C.nz ? zd - C.nz : zd);
+                fout[(s * 19 + l) * C.plane + ((long long)zd * C.ny + yd) * C.pitch + xd] = v;
+            }
+        };
+        if constexpr (NS == 2 && sizeof(T) == 4) {
+            // both species in lockstep, (A, B) pairs of packed FP32 instructions
+            V fp[19];
+#pragma unroll
+            for (int l = 0; l < 19; ++l) {
+                fp[l].x = f[0][l];
+                fp[l].y = f[1][l];
+            }
+            V rh, drh, om, tau, fx, fy, fz;
+            rh.x = rho[0], rh.y = rho[1];
+            drh.x = drho[0], drh.y = drho[1];
+            om.x = C.omega[0], om.y = C.omega[1];
+            tau.x = C.tau[0] * ir[0], tau.y = C.tau[1] * ir[1];
+            fx.x = F[0][0], fx.y = F[1][0];
+            fy.x = F[0][1], fy.y = F[1][1];
+            fz.x = F[0][2], fz.y = F[1][2];
+            const V keep = vsub(vsplat(T(1)), om);
+            const V ux = vfma(fx, tau, vsplat(upx)), uy = vfma(fy, tau, vsplat(upy)), uz = vfma(fz, tau, vsplat(upz));
+            const V u15 = vmul(vsplat(T(1.5)), vfma(ux, ux, vfma(uy, uy, vmul(uz, uz))));
+            const V b = vmul(om, rh);
+            const V base = vsub(vmul(om, drh), vmul(b, u15));  // omega (drho - 3/2 rho u^2)
+            push(0, 0, vfma(keep, fp[0], vmul(vsplat(w19<T>(0)), base)).x);
+            push(1, 0, vfma(keep, fp[0], vmul(vsplat(w19<T>(0)), base)).y);
+#pragma unroll
+            for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
+                // c_l . u with the components +-1 or 0 of this l (the branches fold away unrolled)
+                V cu = vsplat(T(0));
+                if (c3x(l) > 0) cu = vadd(cu, ux);
+                if (c3x(l) < 0) cu = vsub(cu, ux);
+                if (c3y(l) > 0) cu = vadd(cu, uy);
+                if (c3y(l) < 0) cu = vsub(cu, uy);
+                if (c3z(l) > 0) cu = vadd(cu, uz);
+                if (c3z(l) < 0) cu = vsub(cu, uz);
+                const T w = w19<T>(l);
+                const V wb = vmul(vsplat(w), b);
+                const V even = vfma(vmul(vsplat(T(4.5)), wb), vmul(cu, cu), vmul(vsplat(w), base));
+                const V odd = vmul(vmul(vsplat(T(3)), wb), cu);
+                const V gp = vadd(vfma(keep, fp[l], even), odd);
+                const V gm = vsub(vfma(keep, fp[l + 1], even), odd);
+                push(0, l, gp.x);
+                push(1, l, gp.y);
+                push(0, l + 1, gm.x);
+                push(1, l + 1, gm.y);
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const T om = C.omega[s], keep = T(1) - om, tir = C.tau[s] * ir[s];
+                const T ux = upx + F[s][0] * tir, uy = upy + F[s][1] * tir, uz = upz + F[s][2] * tir;
+                const T u15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+                const T b = om * rho[s];
+                const T base = om * drho[s] - b * u15;  // omega (drho - 3/2 rho u^2)
+                push(s, 0, keep * f[s][0] + w19<T>(0) * base);
+#pragma unroll
+                for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
+                    const T cu = T(c3x(l)) * ux + T(c3y(l)) * uy + T(c3z(l)) * uz;
+                    const T w = w19<T>(l);
+                    const T even = w * base + (w * T(4.5)) * b * cu * cu;
+                    const T odd = (w * T(3)) * b * cu;
+                    push(s, l, (keep * f[s][l] + even) + odd);
+                    push(s, l + 1, (keep * f[s][l + 1] + even) - odd);
                 }
-                fout[(s * 19 + ld) * C.plane + ((long long)zd * C.ny + yd) * C.pitch + xd] = v;
             }
         }
     }
