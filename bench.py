@@ -254,12 +254,17 @@ def _traffic(kernel_src_hash, workload, precision, kernel):
     return e.get("dram_bytes_per_launch")
 
 
-KERNEL_SOURCE = {"pull": "lbm_pull.cu", "fused": "lbm_tile.cu", "twopass": "lbm_twopass.cu", "sweep": "lbm_fused.cu"}
+_CORE = ("lbm_core.cuh", "lbm_pair.cuh", "lbm_reduce.cuh")
+KERNEL_SOURCE = {"pull": ("lbm_pull.cu",) + _CORE, "fused": ("lbm_tile.cu",) + _CORE,
+                 "twopass": ("lbm_twopass.cu",) + _CORE, "sweep": ("lbm_fused.cu",) + _CORE,
+                 "k3_step": ("lbm3d.cu",), "k3_density": ("lbm3d.cu",)}
 
 
 def kernel_source_hash(kernel):
+    """SHA-1 of the sources a kernel is compiled from: a committed DRAM-traffic figure holds
+    only for the source it was captured on."""
     h = hashlib.sha1()
-    for f in (KERNEL_SOURCE[kernel], "lbm_core.cuh", "lbm_pair.cuh"):
+    for f in KERNEL_SOURCE[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1402_6019_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -663,8 +668,11 @@ def run_3d(a, w):
     kd, kc = d_ms / max(nstep, 1), c_ms / max(nstep, 1)
     top, kms = ("k3_step", kc) if kc >= kd else ("k3_density", kd)
     achieved = B[top] * sites / (kms * 1e-3) / 1e9
+    traffic = _traffic(kernel_source_hash(top), a.workload, a.precision, top)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+                "frac": round(achieved / peak, 4),
+                "traffic": traffic,
+                "peak_source": peak_kind,
                 "kernel": f"lbm3::{top}<T, ...>", "kernel_ms": round(kms, 5),
                 "algorithmic_bytes_per_site": B[top],
                 "kernels_ms": {"k3_density": round(kd, 5), "k3_step": round(kc, 5)},
