@@ -813,18 +813,37 @@ def main():
 
     timing_mode = {"graph": None}
 
+    def graph_events():
+        """Timing events that a graph capture records as nodes of the graph, or None where this
+        PyTorch has none."""
+        try:
+            return (torch.cuda.Event(enable_timing=True, external=True),
+                    torch.cuda.Event(enable_timing=True, external=True))
+        except TypeError:
+            return None
+
     def capture():
         """The step launches of the timed region, captured (untimed) into one CUDA graph that the
-        region replays once, so the host's launch rate cannot starve the GPU; None when refused."""
+        region replays once, so the host's launch rate cannot starve the GPU; None when refused.
+        The graph's first and last nodes record timing events: the device time of exactly the K
+        steps, without the host's submission of the replay to a stream that the synchronisation
+        before the region left idle."""
+        ev = graph_events()
         try:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream):
+                if ev:
+                    ev[0].record(stream)
                 for k in range(a.steps):
                     lats[k % n_rot].step(1)
+                if ev:
+                    ev[1].record(stream)
             timing_mode["graph"] = True
+            timing_mode["events"] = ev
             return g
         except Exception as ex:
             timing_mode["graph"] = f"graph capture failed ({type(ex).__name__}); one library call per step"
+            timing_mode["events"] = None
             for lt in lats:
                 lt.synchronize()
             return None
@@ -849,7 +868,12 @@ def main():
                 lats[k % n_rot].step(1)
         t1.record(stream)
         barrier()
-        return float(t0.elapsed_time(t1))
+        outer = float(t0.elapsed_time(t1))
+        ev = timing_mode.get("events") if graph is not None else None
+        if ev:
+            timing_mode["outer_ms"] = outer
+            return float(ev[0].elapsed_time(ev[1]))
+        return outer
 
     launches0 = sum(lt.launches for lt in lats)
     graph = capture() if a.graph and flush is None else None
@@ -964,6 +988,10 @@ def main():
                    "timed_launches": ("one CUDA graph replay of the captured step launches"
                                       if timing_mode["graph"] is True else timing_mode["graph"] or
                                       "one library call per step"),
+                   **({"timed_region": "events recorded by the graph's first and last nodes (the K steps "
+                                       "on the device); the events around the replay on the stream: "
+                                       f"{timing_mode['outer_ms']:.4f} ms"}
+                      if timing_mode.get("outer_ms") is not None else {}),
                    "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel,
                    **({"instances": len(w["instances"])} if "instances" in w else {}),
                    **({"pipeline_depth": depth, "autotune_ms": [round(t, 5) for t in tune_ms]}
