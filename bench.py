@@ -70,8 +70,8 @@ def _args():
                          "was evicted from L2 by the others' traffic (no flush); flush: one lattice, a 256 MiB "
                          "write then a 256 MiB read between timed steps")
     ap.add_argument("--autotune", type=int, default=0, metavar="STEPS",
-                    help="before timing, let the library pick the pull kernel's launch shape by timing STEPS "
-                         "steps of each (0 = the default shape)")
+                    help="before timing, let the library pick the pull kernel's tile width and pipeline depth by "
+                         "timing STEPS steps of each (lbm_autotune_tiles; 0 = the default shape)")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: the timed region replays the captured step launches as one CUDA graph (the rotating "
                          "lattices only); 0: one library call per step inside the region")
@@ -791,9 +791,9 @@ def main():
     lat = lats[0]
     depth = None
     tune_ms = None
-    if a.autotune > 0:
+    if a.autotune > 0 and a.kernel == "pull":
         for lt in lats:
-            depth, tune_ms = lt.autotune(a.autotune)
+            (width, depth), tune_ms = lt.autotune_tiles(a.autotune)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
     flush_src = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if a.l2 == "flush" else None
 
@@ -994,7 +994,9 @@ def main():
                       if timing_mode.get("outer_ms") is not None else {}),
                    "rows_per_warp": lat.desc.rows_per_warp, "tile_rows": lat.desc.tile_rows, "kernel": a.kernel,
                    **({"instances": len(w["instances"])} if "instances" in w else {}),
-                   **({"pipeline_depth": depth, "autotune_ms": [round(t, 5) for t in tune_ms]}
+                   **({"tile": f"{width}x8", "pipeline_depth": depth,
+                       "autotune_ms_per_step": {"32x8 depth 1": round(tune_ms[0], 5), "32x8 depth 2": round(tune_ms[1], 5),
+                                                "64x8 depth 1": round(tune_ms[2], 5), "64x8 depth 2": round(tune_ms[3], 5)}}
                       if depth is not None else {})},
         "roofline": roofline,
         "e2e": e2e,

@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 4
+#define LBM_ABI_VERSION 5
 
 /* status codes */
 enum {
@@ -271,6 +271,23 @@ int lbm_instance_observables(lbm_ctx *c, int i, lbm_obs *out, int averages);
    kernels, which have nothing to choose), ms_per_step[2] (may be NULL) the measured step times.
    Synchronises. */
 int lbm_autotune(lbm_ctx *c, int steps, int *chosen, double *ms_per_step);
+
+/* Tile shapes of the PULL kernel's step passes (no counterpart in the paper; they serve the
+   batched sweeps of Sec. V).  A step pass runs tiles of 32 x 8 sites (one warp per tile row) or,
+   in FP32, 64 x 8 (two warps per tile row: one CTA of 512 threads per SM, a halo of 304 instead
+   of 2 x 176 psi/rho positions per 512 sites), at pipeline depth 1 or 2 (boxes in flight per
+   CTA).  The shape changes which CTA does which sites and how much halo it reads, not the
+   arithmetic: row sums stay per 32 columns and column sums per 8 rows, so states and observables
+   are bit-identical across shapes.  lbm_autotune_tiles times `steps` (1..10000) steps of each
+   (width, depth) in (32, 1), (32, 2), (64, 1), (64, 2) on the context's own lattices with the
+   current sampling, keeps the fastest for that kind of pass (sampling on or off), and puts the
+   state, time sums and step count back; *width and *depth (may be NULL) receive the choice,
+   ms_per_step[4] (may be NULL) the milliseconds per step of the four (0 for width 64 in FP64,
+   which has none).  Synchronises.  lbm_set_tile_shape sets a shape for both kinds of pass.  Both
+   return LBM_EINVAL for the other kernels, and lbm_set_tile_shape for a width other than 32 / 64,
+   a depth other than 1 / 2, or width 64 in FP64. */
+int lbm_autotune_tiles(lbm_ctx *c, int steps, int *width, int *depth, double *ms_per_step);
+int lbm_set_tile_shape(lbm_ctx *c, int width, int depth);
 
 /* Self-test of failure detection (no counterpart in the paper).  The step kernels' only
    device-side waits are bounded waits on TMA copies; an expired wait sets a flag that the next

@@ -74,13 +74,17 @@ struct lbm_ctx {
     void* gfield = nullptr;     // two-pass ghost fields
     alignas(64) unsigned char tmap[128] = {};  // two-pass: TMA descriptor of gfield
     bool pull = false;                          // pull layout (LBM_KERNEL_PULL)
-    alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1]
-    int pull_grid[32][2] = {};                        // pull: resident CTAs per mode and depth
+    alignas(64) unsigned char pmap_in[2][128] = {};   // pull: load descriptors of f[0], f[1] (tile width 32)
+    alignas(64) unsigned char pmap_wide[2][128] = {}; // pull, FP32: the same for tiles of width 64
+    int pull_grid[32][2][2] = {};                     // pull: resident CTAs per mode, depth and width (32, 64)
     void* rec = nullptr;                              // pull, M_RECORD pass: where the input state goes
     // pull: boxes in flight per CTA (1 or 2) for passes without [0] and with [1] observables; FP32
     // defaults from measurements on GB300: FP32 depth 1 (3 CTAs per SM within 80 registers) with
     // and without observables; FP64 depth 2
     int stages[2] = {2, 2};
+    // pull: tile width (32 or 64 columns) of the step passes without [0] and with [1] observables;
+    // 64 only in FP32; chosen by lbm_autotune_tiles
+    int width[2] = {32, 32};
     // the lattices of a batch (one entry for a single lattice): host and device copies
     std::vector<InstGeom> inst;
     InstGeom* inst_d = nullptr;
@@ -336,7 +340,6 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     c->pull = c->kernel == LBM_KERNEL_PULL;
     {  // the lattices: rows stacked in order, each with its own ghost rows in the planes
         const int ni = d->n_instances > 1 ? d->n_instances : 1;
-        const int ntx = (nx + 31) / 32;
         c->inst.assign(ni, InstGeom{});
         c->drive_set.assign(ni, 0);
         int zrow = 0, prow = 0, trow = 0;
@@ -345,7 +348,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
             g.nz = ni > 1 ? d->inst_nz[i] : nz;
             g.zrow0 = zrow;
             g.prow0 = prow;
-            g.tile0 = trow * ntx;
+            g.trow0 = trow;
             g.ntz = (g.nz + 7) / 8;
             zrow += g.nz;
             prow += g.nz + 2 * PULL_GZ;
@@ -414,17 +417,26 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
             return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the two-pass field planes"));
     }
     if (c->pull) {
-        for (int b = 0; b < 2; ++b)
-            if (make_pop_tmap(c->pmap_in[b], c->f[b], (int)c->esize, ns, c->prows, c->pitch, c->plane) != 0)
+        for (int b = 0; b < 2; ++b) {
+            if (make_pop_tmap(c->pmap_in[b], c->f[b], (int)c->esize, ns, c->prows, c->pitch, c->plane, 32) != 0)
                 return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
+            if (d->precision == LBM_FP32 &&
+                make_pop_tmap(c->pmap_wide[b], c->f[b], (int)c->esize, ns, c->prows, c->pitch, c->plane, 64) != 0)
+                return bail(fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the population buffers"));
+        }
         const int per = d->z_boundary == LBM_PERIODIC ? M_PERIODIC : 0;
         const int modes[5] = {M_WRITE, M_WRITE | M_OBS | per, M_OBS | per, M_FIELDS, M_WRITE | M_RECORD};
         for (int m : modes)
             for (int st = 1; st <= 2; ++st) {
-                const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m, st)
-                                                        : pull_blocks_per_sm<float>(ns, m, st);
+                const int nb = d->precision == LBM_FP64 ? pull_blocks_per_sm<double>(ns, m, st, 32)
+                                                        : pull_blocks_per_sm<float>(ns, m, st, 32);
                 if (nb < 1) return bail(fail(c, LBM_ECUDA, "occupancy query of the pull kernel failed"));
-                c->pull_grid[m][st - 1] = nb * c->nsm;
+                c->pull_grid[m][st - 1][0] = nb * c->nsm;
+                if (d->precision == LBM_FP32 && (m == M_WRITE || m == (M_WRITE | M_OBS | per))) {
+                    const int nw = pull_blocks_per_sm<float>(ns, m, st, 64);
+                    if (nw < 1) return bail(fail(c, LBM_ECUDA, "occupancy query of the pull kernel failed"));
+                    c->pull_grid[m][st - 1][1] = nw * c->nsm;
+                }
             }
     }
     refresh_const(c);
@@ -579,21 +591,23 @@ static cudaError_t enqueue_pass(lbm_ctx* c, int cur, int mode, bool reduce, bool
         }
         c->launches += 1;
     } else if (c->pull) {
-        const void* tin = c->pmap_in[cur];
         const Batch B = batch(c);
         // observing passes on periodic lattices run the build without wall logic (fewer
         // instructions and registers); the others run the general build, which fits the
         // depth-1 register budget without spills
         const int pm = mode | (c->d.z_boundary == LBM_PERIODIC && (mode & M_OBS) ? M_PERIODIC : 0);
-        const int stg = c->stages[(mode & M_OBS) ? 1 : 0];
+        const int cls = (mode & M_OBS) ? 1 : 0;
+        const int stg = c->stages[cls];
+        // the tuned width applies to the step passes (write, observing or not); other passes run 32
+        const bool wide = c->width[cls] == 64 && c->d.precision == LBM_FP32 && c->pull_grid[pm][stg - 1][1] > 0;
+        const void* tin = wide ? c->pmap_wide[cur] : c->pmap_in[cur];
+        const int grid = c->pull_grid[pm][stg - 1][wide ? 1 : 0];
         if (c->d.precision == LBM_FP64)
-            e = launch_pull<double>(c->d.n_species, pm, stg, tin, (double*)c->f[cur ^ 1], c->c64, O,
-                                    Rd, c->sched, c->sched_set, B, c->pull_grid[pm][stg - 1], c->stream,
-                                    (double*)c->rec);
+            e = launch_pull<double>(c->d.n_species, pm, stg, 32, tin, (double*)c->f[cur ^ 1], c->c64, O,
+                                    Rd, c->sched, c->sched_set, B, grid, c->stream, (double*)c->rec);
         else
-            e = launch_pull<float>(c->d.n_species, pm, stg, tin, (float*)c->f[cur ^ 1], c->c32, O,
-                                   Rd, c->sched, c->sched_set, B, c->pull_grid[pm][stg - 1], c->stream,
-                                   (float*)c->rec);
+            e = launch_pull<float>(c->d.n_species, pm, stg, wide ? 64 : 32, tin, (float*)c->f[cur ^ 1], c->c32, O,
+                                   Rd, c->sched, c->sched_set, B, grid, c->stream, (float*)c->rec);
         if (e == cudaSuccess) c->sched_set ^= 1;
     } else if (c->kernel == LBM_KERNEL_SWEEP) {
         const SweepGeom& G = (mode & M_OBS) ? c->geom_obs : c->geom;
@@ -1303,19 +1317,15 @@ extern "C" int lbm_selftest_wait(lbm_ctx* c, long long cycles) {
     return LBM_OK;
 }
 
-// Autotuner of the pull kernel's launch shape: every candidate (pipeline depth 1 with 3 CTAs per
-// SM, depth 2 with 2) steps the context's own lattices `steps` times with the current sampling,
-// timed by events; the fastest is kept.  The state, the time sums and the step count are put
-// back afterwards, so tuning does not advance the simulation.
-extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_step) {
-    if (!c) return LBM_EINVAL;
+// Autotuner of the pull kernel's launch shapes: every candidate (pipeline depth, tile width) steps
+// the context's own lattices `steps` times with the current sampling, timed by events; the
+// fastest is kept for the kind of pass tuned (with or without observables).  The state, the time
+// sums and the step count are put back afterwards, so tuning does not advance the simulation.
+// ms[i]: milliseconds per step of candidate i, 0 for a shape the context does not have.
+static int autotune_shapes(lbm_ctx* c, int steps, const int (*cand)[2], int ncand, int* pick, double* ms) {
     if (steps < 1 || steps > 10000) return fail(c, LBM_EINVAL, "steps must be in [1, 10000]");
     if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
     CK(cudaSetDevice(c->d.device));
-    if (!c->pull) {  // nothing to choose for the other kernels
-        if (chosen) *chosen = 0;
-        return LBM_OK;
-    }
     CK(flush_pending(c));
     const size_t fbytes = (size_t)c->d.n_species * 9 * c->plane * c->esize;
     void* save = nullptr;
@@ -1327,20 +1337,25 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sv + 2 * fbytes + obs_bytes(c), c->flag, sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
     const int cls = c->observe_every > 0 ? 1 : 0;  // the pass kind tuned: with or without observables
-    const int cur = c->cur, saved_stages = c->stages[cls];
+    const bool ob = c->observe_every > 0;
+    const int cur = c->cur, saved_stages = c->stages[cls], saved_width = c->width[cls];
     const long long step = c->step, samples = c->samples, launches = c->launches;
     const bool prof = c->profiling;
     c->profiling = false;
-    double best = 1e300, ms[2] = {0.0, 0.0};
-    int pick = saved_stages;
+    double best = 1e300;
+    int best_i = -1;
     cudaEvent_t a = nullptr, b = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    for (int st = 1; st <= 2 && e == cudaSuccess; ++st) {
+    const int pm = M_WRITE | (ob ? M_OBS | (c->d.z_boundary == LBM_PERIODIC ? M_PERIODIC : 0) : 0);
+    for (int i = 0; i < ncand && e == cudaSuccess; ++i) {
+        ms[i] = 0.0;
+        const int st = cand[i][0], w = cand[i][1];
+        if (w == 64 && c->pull_grid[pm][st - 1][1] < 1) continue;  // not built for this context
         c->stages[cls] = st;
+        c->width[cls] = w;
         for (int k = 0; k < 2 + steps && e == cudaSuccess; ++k) {  // two warm-up steps, then the timed ones
             if (k == 2) e = cudaEventRecord(a, c->stream);
-            const bool ob = c->observe_every > 0;
             if (e == cudaSuccess) e = enqueue_pass(c, c->cur, M_WRITE | (ob ? M_OBS : 0), ob, ob, true);
             c->cur ^= 1;
         }
@@ -1348,10 +1363,10 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
         if (e == cudaSuccess) e = cudaEventSynchronize(b);
         float t = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
-        ms[st - 1] = (double)t / steps;
-        if (e == cudaSuccess && ms[st - 1] < best) {
-            best = ms[st - 1];
-            pick = st;
+        ms[i] = (double)t / steps;
+        if (e == cudaSuccess && ms[i] < best) {
+            best = ms[i];
+            best_i = i;
         }
     }
     // put the state back
@@ -1370,14 +1385,64 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_s
     c->samples = samples;
     c->launches = launches;
     c->profiling = prof;
-    c->stages[cls] = e == cudaSuccess ? pick : saved_stages;
+    const bool ok = e == cudaSuccess && best_i >= 0;
+    c->stages[cls] = ok ? cand[best_i][0] : saved_stages;
+    c->width[cls] = ok ? cand[best_i][1] : saved_width;
     drop_graphs(c);
     CK(e);
-    if (chosen) *chosen = pick;
+    *pick = best_i;
+    return LBM_OK;
+}
+
+extern "C" int lbm_autotune(lbm_ctx* c, int steps, int* chosen, double* ms_per_step) {
+    if (!c) return LBM_EINVAL;
+    if (steps < 1 || steps > 10000) return fail(c, LBM_EINVAL, "steps must be in [1, 10000]");
+    if (!c->have_fields) return fail(c, LBM_EINVAL, "lbm_set_fields has not been called");
+    if (!c->pull) {  // nothing to choose for the other kernels
+        if (chosen) *chosen = 0;
+        return LBM_OK;
+    }
+    const int w = c->width[c->observe_every > 0 ? 1 : 0];
+    const int cand[2][2] = {{1, w}, {2, w}};
+    double ms[2] = {0.0, 0.0};
+    int pick = -1;
+    const int rc = autotune_shapes(c, steps, cand, 2, &pick, ms);
+    if (rc != LBM_OK) return rc;
+    if (chosen) *chosen = cand[pick][0];
     if (ms_per_step) {
         ms_per_step[0] = ms[0];
         ms_per_step[1] = ms[1];
     }
+    return LBM_OK;
+}
+
+extern "C" int lbm_autotune_tiles(lbm_ctx* c, int steps, int* width, int* depth, double* ms_per_step) {
+    if (!c) return LBM_EINVAL;
+    if (!c->pull) return fail(c, LBM_EINVAL, "tile shapes are the PULL kernel's");
+    const int cand[4][2] = {{1, 32}, {2, 32}, {1, 64}, {2, 64}};
+    double ms[4] = {0.0, 0.0, 0.0, 0.0};
+    int pick = -1;
+    const int rc = autotune_shapes(c, steps, cand, 4, &pick, ms);
+    if (rc != LBM_OK) return rc;
+    if (depth) *depth = cand[pick][0];
+    if (width) *width = cand[pick][1];
+    if (ms_per_step)
+        for (int i = 0; i < 4; ++i) ms_per_step[i] = ms[i];
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_tile_shape(lbm_ctx* c, int width, int depth) {
+    if (!c) return LBM_EINVAL;
+    if (!c->pull) return fail(c, LBM_EINVAL, "tile shapes are the PULL kernel's");
+    if ((width != 32 && width != 64) || (depth != 1 && depth != 2))
+        return fail(c, LBM_EINVAL, "width must be 32 or 64 and depth 1 or 2");
+    if (width == 64 && c->d.precision != LBM_FP32) return fail(c, LBM_EINVAL, "width 64 is built for FP32 only");
+    CK(cudaSetDevice(c->d.device));
+    for (int k = 0; k < 2; ++k) {
+        c->stages[k] = depth;
+        c->width[k] = width;
+    }
+    drop_graphs(c);
     return LBM_OK;
 }
 

@@ -55,7 +55,7 @@ struct InstGeom {
     int nz;       // rows of the lattice
     int zrow0;    // its row 0 among the compact rows of the batch
     int prow0;    // padded plane row of its row -PULL_GZ (its row z sits at prow0 + PULL_GZ + z)
-    int tile0;    // its first tile in the pull kernel's numbering (ntx tiles per tile row)
+    int trow0;    // its first tile row in the pull kernel's numbering (tiles of PZ = 8 rows)
     int ntz;      // its tile rows
     float g_f;           // g in FP32 (set with g: the FP32 kernels issue no FP64 conversion)
     double g;            // body acceleration along x
@@ -89,7 +89,7 @@ struct Batch {
     int ntz;
 };
 
-// The lattice holding compact row zg, or tile t (binary search over ascending starts).
+// The lattice holding compact row zg, or tile row tr (binary search over ascending starts).
 LBM_HD int inst_of_row(const InstGeom* I, int n, int zg) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -101,11 +101,11 @@ LBM_HD int inst_of_row(const InstGeom* I, int n, int zg) {
     }
     return lo;
 }
-LBM_HD int inst_of_tile(const InstGeom* I, int n, int t) {
+LBM_HD int inst_of_tile(const InstGeom* I, int n, int tr) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (I[mid].tile0 <= t)
+        if (I[mid].trow0 <= tr)
             lo = mid;
         else
             hi = mid - 1;
@@ -159,14 +159,16 @@ struct Fold {
 constexpr int PULL_GX = 4, PULL_GZ = 3;
 
 // Pull-layout kernel: the TMA descriptor (CUtensorMap, 128 bytes at in_map) of one population
-// buffer f ([9 ns][prows][pitch] values) for loading the box of a tile and its 3-cell ring.
-// Returns 0 on success.
-int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int pitch, long long plane);
-// CTAs of the pull kernel resident per SM for a mode and a pipeline depth (stages = boxes in
-// flight per CTA, 1 or 2; sets the kernel's shared-memory limit on the current device); 0 on
-// failure.
+// buffer f ([9 ns][prows][pitch] values) for loading the box of a tile of `width` (32 or 64)
+// columns and its 3-cell ring.  Returns 0 on success.
+int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int pitch, long long plane,
+                  int width);
+// CTAs of the pull kernel resident per SM for a mode, a pipeline depth (stages = boxes in flight
+// per CTA, 1 or 2) and a tile width (32, or 64 for the FP32 step passes M_WRITE, M_WRITE | M_OBS,
+// M_PERIODIC | M_WRITE | M_OBS); sets the kernel's shared-memory limit on the current device; 0
+// on failure or for a width the mode is not built at.
 template <typename T>
-int pull_blocks_per_sm(int ns, int mode, int stages);
+int pull_blocks_per_sm(int ns, int mode, int stages, int width);
 // One pass of the pull kernel: loads through tin (a buffer's in_map) and stores the new values
 // into fout, the other buffer (their periodic images too).  fold: a pending reduction run by the same launch.  sched: two
 // pairs of work-item counters (tiles, reduction items); consecutive launches of a context
@@ -174,7 +176,7 @@ int pull_blocks_per_sm(int ns, int mode, int stages);
 // zeroes the other pair for the next.
 // grid_max: resident CTAs on the device.
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
+cudaError_t launch_pull(int ns, int mode, int stages, int width, const void* tin, T* fout,
                         const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, int set,
                         const Batch& B, int grid_max, cudaStream_t st, T* rec = nullptr);
 // One thread waits `cycles` clock cycles on a barrier nothing completes, then sets bit 1 of *flag.

@@ -231,8 +231,10 @@ __device__ __forceinline__ void cross_stress2(const StepConst<float>& C, const f
     sxz += C.sc[2] * (d - a);
 }
 
+// In sum9's order (lbm_core.cuh): a site's density is the same number whether the tile that holds
+// it forms it (here) or a neighbouring tile forms it for its halo (per species, sum9).
 __device__ __forceinline__ f2 sum9_2(const f2 (&f)[9]) {
-    return add2(add2(add2(f[0], f[1]), add2(f[2], f[3])), add2(add2(add2(f[4], f[5]), add2(f[6], f[7])), f[8]));
+    return add2(add2(add2(add2(f[0], f[1]), add2(f[2], f[3])), add2(add2(f[4], f[5]), add2(f[6], f[7]))), f[8]);
 }
 __device__ __forceinline__ void momentum9_2(const f2 (&f)[9], f2& jx, f2& jz) {
     jx = add2(add2(sub2(f[1], f[3]), sub2(f[5], f[6])), sub2(f[8], f[7]));

@@ -12,7 +12,7 @@
 // periodic images of the lattice (rows only without walls); the kernel that writes a boundary
 // site also writes its images, so every tile's read is one in-bounds rectangle.
 //
-// Work.  A CTA of PX x PZ threads (one warp per tile row) loops over tiles.  The populations of
+// Work.  A CTA of TW x PZ threads (one or two warps per tile row; Shape) loops over tiles.  The populations of
 // the tile and of a 3-cell ring around it (2 cells for the psi stencil of Eq. FORCE, 1 more for
 // the gather, x rounded to a 16-byte boundary) arrive in shared memory with one 3-D
 // cp.async.bulk.tensor load; each warp stores the new populations of its row of 32 sites straight
@@ -43,15 +43,26 @@ namespace lbm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int PX = 32, PZ = 8, NT = PX * PZ;
-constexpr int BX = PX + 8;                // box columns: x0 - 4 .. x0 + PX + 3 (padded x0 .. x0 + PX + 7)
-constexpr int BZ = PZ + 6;                // box rows:    z0 - 3 .. z0 + PZ + 2 (padded z0 .. z0 + PZ + 5)
-constexpr int HW = PX + 4, HH = PZ + 4;   // psi/rho tile: x0 - 2 .. x0 + PX + 1, z0 - 2 .. z0 + PZ + 1
-constexpr int NRING = HW * HH - PX * PZ;  // psi/rho tile positions outside the tile
-// ST (template parameter): boxes in flight per CTA.  2: tiles are loaded two ahead, 2 CTAs per
-// SM in FP32; 1: one ahead, 3 CTAs per SM with fewer registers each.  Chosen by lbm_autotune.
-static_assert(NRING % PZ == 0 && NRING / PZ <= PX, "the ring shared evenly over the warps");
-static_assert(NT == RB_THREADS, "a CTA runs the reduction's work items");
+constexpr int PZ = 8;   // tile rows
+constexpr int BZ = PZ + 6;  // box rows: z0 - 3 .. z0 + PZ + 2 (padded z0 .. z0 + PZ + 5)
+constexpr int HH = PZ + 4;  // psi/rho tile rows: z0 - 2 .. z0 + PZ + 1
+// Tile shape: TW columns by PZ rows, one thread per site, TW = 32 (a warp per tile row) or 64 (two
+// warps per tile row).  Row sums are formed per warp, over 32 columns, and column sums over the
+// PZ rows, whatever the width: the partial sums, and so every result, do not depend on the shape.
+template <int TW>
+struct Shape {
+    static constexpr int NT = TW * PZ;               // threads
+    static constexpr int NW = NT / 32;               // warps
+    static constexpr int BX = TW + 8;                // box columns: x0 - 4 .. x0 + TW + 3
+    static constexpr int HW = TW + 4;                // psi/rho tile columns: x0 - 2 .. x0 + TW + 1
+    static constexpr int NRING = HW * HH - TW * PZ;  // psi/rho tile positions outside the tile
+    static constexpr int RPW = NRING / NW;           // ring positions per warp
+    static_assert(NRING % NW == 0 && RPW <= 32, "the ring shared evenly over the warps");
+    static_assert(NT % RB_THREADS == 0, "a CTA runs the reduction's work items");
+};
+// ST (template parameter): boxes in flight per CTA.  Width 32: 2, tiles loaded two ahead, 2 CTAs
+// per SM in FP32; 1, one ahead, 3 CTAs per SM with fewer registers each.  Width 64: one CTA of 16
+// warps per SM.  Chosen by lbm_autotune / lbm_autotune_tiles.
 static_assert(PULL_GX == 4 && PULL_GZ == 3, "the box starts at padded (x0, z0)");
 
 // Two species in FP32: the species go through the per-site arithmetic in lockstep (lbm_pair.cuh).
@@ -59,15 +70,15 @@ template <typename T, int NS>
 constexpr bool kPair = sizeof(T) == 4 && NS == 2;
 
 // psi and rho of the tile and its 2-cell ring: per species, or (species A, B) pairs
-template <typename T, int NS, bool PAIR = kPair<T, NS>>
+template <typename T, int NS, int TW, bool PAIR = kPair<T, NS>>
 struct PsiTile {
-    T ps[NS][HH][HW];
-    T rh[NS][HH][HW];
+    T ps[NS][HH][Shape<TW>::HW];
+    T rh[NS][HH][Shape<TW>::HW];
 };
-template <>
-struct PsiTile<float, 2, true> {
-    f2 ps[HH][HW];
-    f2 rh[HH][HW];
+template <int TW>
+struct PsiTile<float, 2, TW, true> {
+    f2 ps[HH][Shape<TW>::HW];
+    f2 rh[HH][Shape<TW>::HW];
 };
 
 // Per-iteration ring of the tiles to work on: iteration k works on the tile described by
@@ -88,33 +99,33 @@ struct TileInfo {
     T g, wall[2];   // its lattice's drive
 };
 
-template <typename T, int NS, int ST>
+template <typename T, int NS, int ST, int TW>
 struct PullSmem {
-    T box[ST][9 * NS][BZ][BX];  // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
-    PsiTile<T, NS> q[2];        // by iteration parity: tile k + 1 fills one while tile k reads the other
-    T colsum[2][PZ][NQC][PX];   // by iteration parity: summed over the tile's rows one tile later
-    typename Red<T>::A wsc[RB_THREADS / 32][NSC];  // folded reduction: per-warp scalars
+    T box[ST][9 * NS][BZ][Shape<TW>::BX];  // TMA destinations (column bx = x - x0 + 4, row bz = z - z0 + 3)
+    PsiTile<T, NS, TW> q[2];    // by iteration parity: tile k + 1 fills one while tile k reads the other
+    T colsum[2][PZ][NQC][TW];   // by iteration parity: summed over the tile's rows one tile later
+    typename Red<T>::A wsc[Shape<TW>::NW][NSC];  // folded reduction: per-warp scalars
     alignas(8) unsigned long long bar[ST];
     TileInfo<T> ti[NTQ];
     int fold_item;  // the reduction work item thread 0 drew for the CTA
-    unsigned short ring[NT];  // observing builds: ring position of thread tid, rpz << 8 | rpx
+    unsigned short ring[Shape<TW>::NT];  // observing builds: ring position of thread tid, rpz << 8 | rpx
 };
 
 // Tile t of the work order; rot > 0 (one periodic lattice): the order starts rot tiles in, at
 // the last tile row, so the two rows whose sites also write the periodic row images come first
 // and the last tiles of a launch are plain ones.
-template <typename T>
+template <typename T, int TW>
 __device__ __forceinline__ void describe(TileInfo<T>& D, int t, int ntiles, const InstGeom* __restrict__ inst,
                                          int ninst, int ntx, int rot) {
     D.t = t;
     if (t >= ntiles) return;
-    const InstGeom& I = inst[ninst > 1 ? inst_of_tile(inst, ninst, t) : 0];
-    int tl = t - I.tile0;
+    const InstGeom& I = inst[ninst > 1 ? inst_of_tile(inst, ninst, t / ntx) : 0];
+    int tl = t - I.trow0 * ntx;
     if (rot > 0) tl = tl < ntiles - rot ? tl + rot : tl - (ntiles - rot);
     const int j = tl / ntx;
-    D.x0 = (tl - j * ntx) * PX;
+    D.x0 = (tl - j * ntx) * TW;
     D.z0 = j * PZ;
-    D.jg = I.tile0 / ntx + j;
+    D.jg = I.trow0 + j;
     D.lnz = I.nz;
     D.zrow0 = I.zrow0;
     D.prow0 = I.prow0;
@@ -125,9 +136,9 @@ __device__ __forceinline__ void describe(TileInfo<T>& D, int t, int ntiles, cons
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-template <typename T, int NS, int ST>
-__device__ __forceinline__ void issue_load(PullSmem<T, NS, ST>& S, const CUtensorMap* map, int x, int z, int sl) {
-    constexpr unsigned bytes = (unsigned)(sizeof(T) * 9 * NS * BZ * BX);
+template <typename T, int NS, int ST, int TW>
+__device__ __forceinline__ void issue_load(PullSmem<T, NS, ST, TW>& S, const CUtensorMap* map, int x, int z, int sl) {
+    constexpr unsigned bytes = (unsigned)(sizeof(T) * 9 * NS * BZ * Shape<TW>::BX);
     const unsigned bar = smem_u32(&S.bar[sl]);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile(
@@ -166,15 +177,15 @@ __global__ void k_wait_selftest(int* flag, long long limit) {
 // Post-streaming populations at box position (bx, bz): the gather of the pull layout.  lo / hi:
 // the site is the bottom / top row next to a wall, where populations coming from beyond the
 // wall are the site's own reflected values.
-template <typename T, int NS, int ST>
-__device__ __forceinline__ void gather(const PullSmem<T, NS, ST>& S, int sl, int bx, int bz, T (&f)[NS][9]) {
+template <typename T, int NS, int ST, int TW>
+__device__ __forceinline__ void gather(const PullSmem<T, NS, ST, TW>& S, int sl, int bx, int bz, T (&f)[NS][9]) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int l = 0; l < 9; ++l) f[s][l] = S.box[sl][s * 9 + l][bz - cz(l)][bx - cx(l)];
 }
-template <typename T, int NS, int ST>
-__device__ __forceinline__ void gather_wall(const PullSmem<T, NS, ST>& S, int sl, int bx, int bz, bool lo, bool hi,
+template <typename T, int NS, int ST, int TW>
+__device__ __forceinline__ void gather_wall(const PullSmem<T, NS, ST, TW>& S, int sl, int bx, int bz, bool lo, bool hi,
                                             T (&f)[NS][9]) {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -189,8 +200,8 @@ __device__ __forceinline__ void gather_wall(const PullSmem<T, NS, ST>& S, int sl
 // tile: the ring, and the padding of ragged tiles.  With walls, rows beyond a wall take the
 // mirror image (or zero, Sec. IV's two readings of the ghost rows).  Positions that no live
 // site reads (far padding of ragged tiles) are set to zero.
-template <typename T, int NS, int ST>
-__device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, int qb, const StepConst<T>& C,
+template <typename T, int NS, int ST, int TW>
+__device__ __forceinline__ void side_density(PullSmem<T, NS, ST, TW>& S, int sl, int qb, const StepConst<T>& C,
                                              const PairConst& K, int px, int pz, int z0, int nz, bool WALL) {
     const int Z = z0 - 2 + pz;
     int Zs = Z;
@@ -210,9 +221,9 @@ __device__ __forceinline__ void side_density(PullSmem<T, NS, ST>& S, int sl, int
         T g[NS][9];
         const bool lo = WALL && Zs == 0, hi = WALL && Zs == nz - 1;
         if (WALL && (lo || hi))
-            gather_wall<T, NS, ST>(S, sl, bx, bz, lo, hi, g);
+            gather_wall<T, NS, ST, TW>(S, sl, bx, bz, lo, hi, g);
         else
-            gather<T, NS, ST>(S, sl, bx, bz, g);
+            gather<T, NS, ST, TW>(S, sl, bx, bz, g);
 #pragma unroll
         for (int s = 0; s < NS; ++s) sum[s] = sum9(g[s]);
     }
@@ -263,11 +274,13 @@ __device__ __noinline__ void write_images(const StepConst<T>& C, T* __restrict__
         }
 }
 
-// Ring position (psi/rho tile coordinates) of a thread with tx < NRING / PZ: 22 per warp, so that
-// every warp has the same phase-A work; in ring order the top two rows, the bottom two rows, then
-// two columns on each side of the tile rows.
-__device__ __forceinline__ void ring_position(int tx, int tz, int& rpx, int& rpz) {
-    const int k = tz * (NRING / PZ) + tx;
+// Ring position (psi/rho tile coordinates) of lane `lane` < RPW of warp `warp`: every warp has the
+// same phase-A work (22 positions per warp at width 32, 19 at width 64); in ring order the top two
+// rows, the bottom two rows, then two columns on each side of the tile rows.
+template <int TW>
+__device__ __forceinline__ void ring_position(int lane, int warp, int& rpx, int& rpz) {
+    constexpr int HW = Shape<TW>::HW;
+    const int k = warp * Shape<TW>::RPW + lane;
     if (k < 2 * HW) {
         rpz = k / HW;
         rpx = k % HW;
@@ -282,8 +295,8 @@ __device__ __forceinline__ void ring_position(int tx, int tz, int& rpx, int& rpz
     }
 }
 
-template <typename T, int NS, int MODE, int ST>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
+template <typename T, int NS, int MODE, int ST, int TW>
+__global__ void __launch_bounds__(Shape<TW>::NT, TW == 64 ? 1 : (sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1))
     k_pull(const __grid_constant__ CUtensorMap tin, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ ctr,
            unsigned* __restrict__ ctr_next, const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz,
@@ -291,8 +304,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     // walls in z: never in the periodic build, else as the step constants say
     const bool WALL = (MODE & M_PERIODIC) ? false : C.zbc != 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    PullSmem<T, NS, ST>& S = *reinterpret_cast<PullSmem<T, NS, ST>*>(smem_raw);
-    const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * PX + tx;
+    using SH = Shape<TW>;
+    PullSmem<T, NS, ST, TW>& S = *reinterpret_cast<PullSmem<T, NS, ST, TW>*>(smem_raw);
+    const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TW + tx;
     const int nx = C.nx, nz = C.nz;
     const int ntiles = ntx * ntz;  // nz: rows of all lattices; ntz: their tile rows
     // tiles 0 .. nstat - 1 are owned by CTA (tile mod grid), the rest come from ctr[0]
@@ -302,12 +316,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     const int nrb = (nz + RB_THREADS / 32 - 1) / (RB_THREADS / 32);
     const int nfold = Rd.enabled ? nrb + (nx + RB_THREADS / 32 - 1) / (RB_THREADS / 32) : 0;
 
-    // threads with a ring position (ring_position), NRING / PZ = 22 per warp; the observing builds
-    // keep it in shared memory and read it per tile instead (one register pair less across the
-    // tile, where registers are short), the others keep it in registers
-    const bool ring = tx < NRING / PZ;
+    // threads with a ring position (ring_position), RPW per warp; the observing builds keep it in
+    // shared memory and read it per tile instead (one register pair less across the tile, where
+    // registers are short), the others keep it in registers
+    const bool ring = (tid & 31) < SH::RPW;
     int rpx0 = 0, rpz0 = 0;
-    if (ring) ring_position(tx, tz, rpx0, rpz0);
+    if (ring) ring_position<TW>(tid & 31, tid >> 5, rpx0, rpz0);
     if constexpr ((MODE & M_OBS) != 0) S.ring[tid] = (unsigned short)(rpz0 << 8 | rpx0);
     // thread 0 draws tiles one ahead of their loads, so the counter's latency is hidden;
     // ntiles: nothing more to draw
@@ -321,7 +335,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tin) : "memory");
         for (int sl = 0; sl < ST; ++sl) {
             const int t = (int)blockIdx.x + sl * (int)gridDim.x;
-            if (t < nstat) describe<T>(S.ti[sl], t, ntiles, inst, ninst, ntx, rot);
+            if (t < nstat) describe<T, TW>(S.ti[sl], t, ntiles, inst, ninst, ntx, rot);
         }
     }
     // Programmatic dependent launch: the next step's CTAs may be scheduled as soon as this grid's
@@ -342,7 +356,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             if (!more) break;  // the slots after the CTA's first non-tile item stay unused
             const int t = (int)blockIdx.x + sl * (int)gridDim.x;
             if (t >= nstat)
-                describe<T>(S.ti[sl], min(nstat + (int)atomicAdd(ctr, 1u), ntiles), ntiles, inst, ninst, ntx,
+                describe<T, TW>(S.ti[sl], min(nstat + (int)atomicAdd(ctr, 1u), ntiles), ntiles, inst, ninst, ntx,
                             rot);
             more = S.ti[sl].t < ntiles;
             if (more && sl == 0) issue_load(S, &tin, S.ti[0].x0, S.ti[0].prow0 + S.ti[0].z0, 0);
@@ -362,7 +376,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         const TileInfo<T> D = S.ti[k % NTQ];
         if (D.t >= ntiles) break;
         if (tid == 0)  // publish the tile of iteration k + ST, one barrier ahead of its readers
-            describe<T>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot);
+            describe<T, TW>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot);
         // this tile: first column and row (rows of its lattice), tile row among all lattices; its
         // lattice: rows, first compact row, first padded row (the observing builds read them again
         // from shared memory after the tile barrier, so that they hold no registers across it)
@@ -383,9 +397,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         if (live) {
             const bool lo = WALL && z == 0, hi = WALL && z == lnz - 1;
             if (WALL && (lo || hi))
-                gather_wall<T, NS, ST>(S, sl, tx + 4, tz + 3, lo, hi, f);
+                gather_wall<T, NS, ST, TW>(S, sl, tx + 4, tz + 3, lo, hi, f);
             else
-                gather<T, NS, ST>(S, sl, tx + 4, tz + 3, f);
+                gather<T, NS, ST, TW>(S, sl, tx + 4, tz + 3, f);
             if constexpr ((MODE & M_RECORD) != 0) {  // the input state, as plain values (one lattice)
                 const long long n = (long long)nx * nz, i = (long long)z * nx + x;
 #pragma unroll
@@ -413,7 +427,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 }
             }
         } else {
-            side_density<T, NS, ST>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz, WALL);
+            side_density<T, NS, ST, TW>(S, sl, qb, C, K, tx + 2, tz + 2, z0, lnz, WALL);
         }
         if (ring) {
             int rpx = rpx0, rpz = rpz0;
@@ -422,7 +436,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
                 rpx = (int)(rp & 255u);
                 rpz = (int)(rp >> 8);
             }
-            side_density<T, NS, ST>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
+            side_density<T, NS, ST, TW>(S, sl, qb, C, K, rpx, rpz, z0, lnz, WALL);
         }
         // the only CTA barrier of a tile: psi / rho of the tile and ring complete, box sl read
         // by all, the previous tile's column sums written
@@ -442,7 +456,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             z = z0 + tz;
             live = x < nx && z < lnz;
         }
-        const int s = x0 / PX;  // tile column
+        const int s = (x0 + (tx & ~31)) >> 5;  // this warp's group of 32 columns (row sums)
         // box sl is free: start the load of the tile ST ahead (published at the top of this
         // iteration) and draw the one after it; past the last tile, look at the reduction's
         // counter instead (its value is only used after the loop)
@@ -469,7 +483,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
         }
 
         // ---- phase B: interaction, collision, new stored values, observables ----
-        const PsiTile<T, NS>& Q = S.q[qb];
+        const PsiTile<T, NS, TW>& Q = S.q[qb];
         T rowq[NQR];
 #pragma unroll
         for (int q = 0; q < NQR; ++q) rowq[q] = T(0);
@@ -482,7 +496,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             float sxx = 0.f, szz = 0.f, sxz = 0.f;
             if constexpr ((MODE & M_OBS) != 0) {
                 f2 a2, b2, c2;
-                force_stress2<HW>(K, &Q.ps[tz][tx], Fx, Fz, a2, b2, c2);
+                force_stress2<SH::HW>(K, &Q.ps[tz][tx], Fx, Fz, a2, b2, c2);
                 sxx = a2.x + a2.y;
                 szz = b2.x + b2.y;
                 sxz = c2.x + c2.y;
@@ -727,9 +741,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             }
             v1 += __shfl_xor_sync(FULL, v1, 2);
             v1 += __shfl_xor_sync(FULL, v1, 1);
-            if ((tx & 3) == 0 && z < lnz) {
+            if ((tx & 3) == 0 && z < lnz && (TW == 32 || (s << 5) < nx)) {  // a wide tile's warp may lie past nx
                 const int q = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-                static_cast<T*>(O.part_row)[((long long)(zrow0 + z) * ntx + s) * NQR + q] = v1;
+                static_cast<T*>(O.part_row)[((long long)(zrow0 + z) * ((nx + 31) >> 5) + s) * NQR + q] = v1;
             }
             S.colsum[qb][tz][QC_PS][tx] = cps;
             S.colsum[qb][tz][QC_PXX][tx] = cpx;
@@ -752,7 +766,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
             __syncthreads();
             const int b = S.fold_item;
             if (b >= nfold) break;  // uniform: every thread read the same item
-            reduce_block<T>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
+            reduce_block<T, (TW > 32)>(b, Rd.part_row, Rd.part_col, O.flag, Rd.nxpart, Rd.nzpart, nx, nz, C.zbc, nrb, Rd.out,
                             Rd.avg, Rd.bpart, Rd.bavg, Rd.accumulate, T(Rd.inx), T(Rd.inz), S.wsc,
                             ninst > 1 ? inst : nullptr, ninst);  // ends with a CTA barrier
         }
@@ -768,22 +782,24 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (ST == 2 ? 2 : 3) : 1)
     }
 }
 
-template <typename T, int NS, int MODE, int ST>
+template <typename T, int NS, int MODE, int ST, int TW>
 int pull_occupancy() {
-    const size_t smem = sizeof(PullSmem<T, NS, ST>);
-    if (cudaFuncSetAttribute(k_pull<T, NS, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const size_t smem = sizeof(PullSmem<T, NS, ST, TW>);
+    if (cudaFuncSetAttribute(k_pull<T, NS, MODE, ST, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pull<T, NS, MODE, ST>, NT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pull<T, NS, MODE, ST, TW>, Shape<TW>::NT, smem) !=
+        cudaSuccess)
+        return 0;
     return nb;
 }
 
-template <typename T, int NS, int MODE, int ST>
+template <typename T, int NS, int MODE, int ST, int TW>
 cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const ObsPtrs& O,
                         const Fold& Rd, unsigned* sched, int set, const Batch& B, int grid_max, cudaStream_t st,
                         T* rec) {
-    const int ntx = (C.nx + PX - 1) / PX;
+    const int ntx = (C.nx + TW - 1) / TW;
     const long long ntiles = (long long)ntx * B.ntz;
     int grid = (int)(ntiles < grid_max ? ntiles : grid_max);
     if (Rd.enabled && grid < 1) grid = 1;
@@ -793,33 +809,50 @@ cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const O
     // on the stream drains, and waits for it in its prologue (griddepcontrol.wait)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(PX, PZ);
-    cfg.dynamicSmemBytes = sizeof(PullSmem<T, NS, ST>);
+    cfg.blockDim = dim3(TW, PZ);
+    cfg.dynamicSmemBytes = sizeof(PullSmem<T, NS, ST, TW>);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST>, *static_cast<const CUtensorMap*>(tin), fout, C, K, O,
-                              Rd, sched + 2 * set, sched + 2 * (set ^ 1), B.inst, B.ninst, ntx, B.ntz, rec);
+    return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST, TW>, *static_cast<const CUtensorMap*>(tin), fout, C, K,
+                              O, Rd, sched + 2 * set, sched + 2 * (set ^ 1), B.inst, B.ninst, ntx, B.ntz, rec);
 }
 
-template <typename T, int NS, int ST>
+// The passes built at width 64 as well: the FP32 step passes (lbm_step); all others run width 32.
+template <typename T>
+bool wide_pass(int mode) {
+    return sizeof(T) == 4 && (mode == M_WRITE || mode == (M_WRITE | M_OBS) || mode == (M_PERIODIC | M_WRITE | M_OBS));
+}
+
+template <typename T, int NS, int ST, int TW>
 cudaError_t launch_ns(int mode, const void* tin, T* fout, const StepConst<T>& C,
                       const ObsPtrs& O, const Fold& Rd, unsigned* sched, int set, const Batch& B, int grid_max,
                       cudaStream_t st, T* rec) {
 #define LBM_PULL_CASE(m) \
-    case m: return launch_mode<T, NS, m, ST>(tin, fout, C, O, Rd, sched, set, B, grid_max, st, rec);
-    switch (mode) {
-        LBM_PULL_CASE(M_WRITE)
-        LBM_PULL_CASE(M_WRITE | M_OBS)
-        LBM_PULL_CASE(M_OBS)
-        LBM_PULL_CASE(M_FIELDS)
-        LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
-        LBM_PULL_CASE(M_PERIODIC | M_OBS)
-        LBM_PULL_CASE(M_WRITE | M_RECORD)
-        default: return cudaErrorInvalidValue;
+    case m: return launch_mode<T, NS, m, ST, TW>(tin, fout, C, O, Rd, sched, set, B, grid_max, st, rec);
+    if constexpr (TW == 32) {
+        switch (mode) {
+            LBM_PULL_CASE(M_WRITE)
+            LBM_PULL_CASE(M_WRITE | M_OBS)
+            LBM_PULL_CASE(M_OBS)
+            LBM_PULL_CASE(M_FIELDS)
+            LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
+            LBM_PULL_CASE(M_PERIODIC | M_OBS)
+            LBM_PULL_CASE(M_WRITE | M_RECORD)
+            default: return cudaErrorInvalidValue;
+        }
+    } else if constexpr (sizeof(T) == 4) {
+        switch (mode) {
+            LBM_PULL_CASE(M_WRITE)
+            LBM_PULL_CASE(M_WRITE | M_OBS)
+            LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
     }
 #undef LBM_PULL_CASE
 }
@@ -856,44 +889,67 @@ __global__ void k_images(int ns, T* __restrict__ f, const StepConst<T> C, const 
 
 }  // namespace
 
-template <typename T, int NS, int ST>
+template <typename T, int NS, int ST, int TW>
 int blocks_per_sm_ns(int mode) {
 #define LBM_PULL_CASE(m) \
-    case m: return pull_occupancy<T, NS, m, ST>();
-    switch (mode) {
-        LBM_PULL_CASE(M_WRITE)
-        LBM_PULL_CASE(M_WRITE | M_OBS)
-        LBM_PULL_CASE(M_OBS)
-        LBM_PULL_CASE(M_FIELDS)
-        LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
-        LBM_PULL_CASE(M_PERIODIC | M_OBS)
-        LBM_PULL_CASE(M_WRITE | M_RECORD)
-        default: return 0;
+    case m: return pull_occupancy<T, NS, m, ST, TW>();
+    if constexpr (TW == 32) {
+        switch (mode) {
+            LBM_PULL_CASE(M_WRITE)
+            LBM_PULL_CASE(M_WRITE | M_OBS)
+            LBM_PULL_CASE(M_OBS)
+            LBM_PULL_CASE(M_FIELDS)
+            LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
+            LBM_PULL_CASE(M_PERIODIC | M_OBS)
+            LBM_PULL_CASE(M_WRITE | M_RECORD)
+            default: return 0;
+        }
+    } else if constexpr (sizeof(T) == 4) {
+        switch (mode) {
+            LBM_PULL_CASE(M_WRITE)
+            LBM_PULL_CASE(M_WRITE | M_OBS)
+            LBM_PULL_CASE(M_PERIODIC | M_WRITE | M_OBS)
+            default: return 0;
+        }
+    } else {
+        return 0;
     }
 #undef LBM_PULL_CASE
 }
 
-template <typename T, int ST>
+template <typename T, int ST, int TW>
 int blocks_per_sm(int ns, int mode) {
-    return ns == 1 ? blocks_per_sm_ns<T, 1, ST>(mode) : blocks_per_sm_ns<T, 2, ST>(mode);
+    return ns == 1 ? blocks_per_sm_ns<T, 1, ST, TW>(mode) : blocks_per_sm_ns<T, 2, ST, TW>(mode);
 }
 
 template <typename T>
-int pull_blocks_per_sm(int ns, int mode, int stages) {
-    return stages == 1 ? blocks_per_sm<T, 1>(ns, mode) : blocks_per_sm<T, 2>(ns, mode);
+int pull_blocks_per_sm(int ns, int mode, int stages, int width) {
+    if (width == 64) {
+        if (!wide_pass<T>(mode)) return 0;
+        return stages == 1 ? blocks_per_sm<T, 1, 64>(ns, mode) : blocks_per_sm<T, 2, 64>(ns, mode);
+    }
+    return stages == 1 ? blocks_per_sm<T, 1, 32>(ns, mode) : blocks_per_sm<T, 2, 32>(ns, mode);
 }
 
 template <typename T>
-cudaError_t launch_pull(int ns, int mode, int stages, const void* tin, T* fout,
+cudaError_t launch_pull(int ns, int mode, int stages, int width, const void* tin, T* fout,
                         const StepConst<T>& C, const ObsPtrs& O, const Fold& fold, unsigned* sched, int set,
                         const Batch& B, int grid_max, cudaStream_t st, T* rec) {
     if (set & ~1) return cudaErrorInvalidValue;
     if (grid_max < 1) return cudaErrorInvalidConfiguration;
+    if (width == 64) {
+        if (!wide_pass<T>(mode)) return cudaErrorInvalidValue;
+        if (stages == 1)
+            return ns == 1 ? launch_ns<T, 1, 1, 64>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
+                           : launch_ns<T, 2, 1, 64>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
+        return ns == 1 ? launch_ns<T, 1, 2, 64>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
+                       : launch_ns<T, 2, 2, 64>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
+    }
     if (stages == 1)
-        return ns == 1 ? launch_ns<T, 1, 1>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
-                       : launch_ns<T, 2, 1>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
-    return ns == 1 ? launch_ns<T, 1, 2>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
-                   : launch_ns<T, 2, 2>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
+        return ns == 1 ? launch_ns<T, 1, 1, 32>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
+                       : launch_ns<T, 2, 1, 32>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
+    return ns == 1 ? launch_ns<T, 1, 2, 32>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec)
+                   : launch_ns<T, 2, 2, 32>(mode, tin, fout, C, O, fold, sched, set, B, grid_max, st, rec);
 }
 
 cudaError_t launch_wait_selftest(int* flag, long long cycles, cudaStream_t st) {
@@ -907,13 +963,14 @@ cudaError_t launch_pull_images(int ns, T* f, const StepConst<T>& C, const Batch&
     return cudaGetLastError();
 }
 
-int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int pitch, long long plane) {
+int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int pitch, long long plane, int width) {
     const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!encode) return 1;
     // the whole padded plane (prows rows), boxes of a tile and its 3-cell ring
     const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)prows, (cuuint64_t)(9 * ns)};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
-    const cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
+    if (width != 32 && width != 64) return 3;
+    const cuuint32_t box[3] = {(cuuint32_t)(width + 8), (cuuint32_t)BZ, (cuuint32_t)(9 * ns)};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     const CUresult r = encode(static_cast<CUtensorMap*>(in_map), dt, 3, const_cast<void*>(f), dims, strides, box, estr,
@@ -922,12 +979,12 @@ int make_pop_tmap(void* in_map, const void* f, int esize, int ns, int prows, int
     return r == CUDA_SUCCESS ? 0 : 2;
 }
 
-template int pull_blocks_per_sm<float>(int, int, int);
-template int pull_blocks_per_sm<double>(int, int, int);
-template cudaError_t launch_pull<float>(int, int, int, const void*, float*, const StepConst<float>&,
+template int pull_blocks_per_sm<float>(int, int, int, int);
+template int pull_blocks_per_sm<double>(int, int, int, int);
+template cudaError_t launch_pull<float>(int, int, int, int, const void*, float*, const StepConst<float>&,
                                         const ObsPtrs&, const Fold&, unsigned*, int, const Batch&, int, cudaStream_t,
                                         float*);
-template cudaError_t launch_pull<double>(int, int, int, const void*, double*, const StepConst<double>&,
+template cudaError_t launch_pull<double>(int, int, int, int, const void*, double*, const StepConst<double>&,
                                          const ObsPtrs&, const Fold&, unsigned*, int, const Batch&, int, cudaStream_t,
                                          double*);
 template cudaError_t launch_pull_images<float>(int, float*, const StepConst<float>&, const Batch&, cudaStream_t);

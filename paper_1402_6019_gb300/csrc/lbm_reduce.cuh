@@ -62,7 +62,9 @@ template <> struct Red<float> {
     __device__ static bool nonzero(A a) { return a.x != 0.f || a.y != 0.f; }
 };
 
-// Work item blk, run by a block of RB_THREADS threads (all of which call this).  One warp per
+// Work item blk, run by a block of RB_THREADS threads (all of which call this), or with WIDE by a
+// block of a multiple of them, whose warps past the first RB_THREADS / 32 take part in the
+// barriers only.  One warp per
 // row: the row's totals over its column groups, its profile entries (x-averages), its fluidity (Eq. fluidity: shear rate = central difference of ux_z, one-sided
 // at wall rows, wrapped when periodic, over the shear stress), its wall momenta and, when
 // sampling, its time sums.  One warp per column: the z-averages of P_xx - P_zz and P_xx.  Each
@@ -77,7 +79,7 @@ template <> struct Red<float> {
 // block partials use the accumulators above.  Fixed summation order: repeatable results.
 // inst / ninst: the lattices of a stacked batch (rows of different lattices are not neighbours);
 // null for a single lattice of nz rows.
-template <typename PT>
+template <typename PT, bool WIDE = false>
 __device__ __forceinline__ void reduce_block(int blk, const void* part_row, const void* part_col, const int* flag,
                                              int nxpart, int nzpart, int nx, int nz, int zbc, int nrowblocks,
                                              void* __restrict__ out, void* __restrict__ avg,
@@ -102,7 +104,9 @@ __device__ __forceinline__ void reduce_block(int blk, const void* part_row, cons
         else if (accumulate && bad)
             R::put(avg, O_BAD, R::from(PT(1)));
     }
-    if (blk < nrowblocks) {
+    if (WIDE && warp >= WPB) {
+        // idle in this work item
+    } else if (blk < nrowblocks) {
         const int z = blk * WPB + warp;
         if (z < nz) {
             // this row's lattice: its first compact row and height

@@ -84,6 +84,9 @@ SIGNATURES = {
     "lbm_set_instance_drive": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "lbm_instance_observables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_obs), ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "lbm_autotune_tiles": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "lbm_set_tile_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_set_populations": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "lbm_observables_bytes": (ctypes.c_longlong, [_VP]),
     "lbm_observables_enqueue": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
@@ -412,6 +415,18 @@ class Lattice:
         ms = (ctypes.c_double * 2)()
         _check(load().lbm_autotune(self.h, steps, ctypes.byref(chosen), ms), self.h)
         return chosen.value, (ms[0], ms[1])
+
+    def autotune_tiles(self, steps=20):
+        """Pick the pull kernel's tile width and depth by timing them here; returns
+        ((width, depth), ms per step of (32, 1), (32, 2), (64, 1), (64, 2)).  The state is left as
+        it was."""
+        width, depth = ctypes.c_int(0), ctypes.c_int(0)
+        ms = (ctypes.c_double * 4)()
+        _check(load().lbm_autotune_tiles(self.h, int(steps), ctypes.byref(width), ctypes.byref(depth), ms), self.h)
+        return (width.value, depth.value), tuple(ms[:])
+
+    def set_tile_shape(self, width, depth):
+        _check(load().lbm_set_tile_shape(self.h, int(width), int(depth)), self.h)
 
     def set_instance_drive(self, i, body_force=0.0, wall_u=(0.0, 0.0)):
         _check(load().lbm_set_instance_drive(self.h, i, body_force, wall_u[0], wall_u[1]), self.h)

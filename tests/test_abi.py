@@ -30,7 +30,7 @@ def test_every_declared_symbol_is_exported():
         assert hasattr(lib, n), n
         assert n in L.SIGNATURES, n
     assert set(L.SIGNATURES) == set(names)
-    assert L.lbm_abi_version() == 4
+    assert L.lbm_abi_version() == 5
 
 
 def test_struct_layouts_match_header(tmp_path):
