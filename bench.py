@@ -979,7 +979,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": a.workload, "nx": nx, "nz": nz, "n_species": ns,
                    "precision": a.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": (f"{n_rot} lattices of the workload stepped in turn, back to back "
+                   "l2": ((f"{n_rot} lattices of the workload stepped in turn, back to back " if n_rot > 1 else
+                           "one lattice ") +
                           f"({n_rot * lattice_bytes / 2**20:.0f} MiB of populations > {L2_BYTES / 2**20:.0f} MiB L2); "
                           "no flush" if flush is None else
                           "one lattice; a 256 MiB write then a 256 MiB read between timed steps"),
