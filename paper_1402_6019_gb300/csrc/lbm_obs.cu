@@ -8,6 +8,9 @@ namespace {
 // Slot of population l of site (x, z) of the lattice whose row -PULL_GZ is padded row prow0 (nz
 // rows) in the pull layout: where its gather reads it, at x - c_l, or at (x, opp(l)) when
 // x - c_l lies beyond a wall.  Returns the offset within a plane and sets ls to the plane.
+// Index i in -n .. 2n - 1 wrapped into 0 .. n - 1 (a neighbour one cell across an edge).
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 template <typename T>
 __device__ long long pull_slot(const StepConst<T>& C, int x, int z, int nz, int prow0, int l, int& ls) {
     const int zs = z - cz(l);
@@ -16,7 +19,7 @@ __device__ long long pull_slot(const StepConst<T>& C, int x, int z, int nz, int 
         return (long long)(prow0 + z + PULL_GZ) * C.pitch + x + PULL_GX;
     }
     ls = l;
-    return (long long)(prow0 + wrap_index(zs, nz) + PULL_GZ) * C.pitch + wrap_index(x - cx(l), C.nx) + PULL_GX;
+    return (long long)(prow0 + wrap1(zs, nz) + PULL_GZ) * C.pitch + wrap1(x - cx(l), C.nx) + PULL_GX;
 }
 
 // Populations at the equilibrium of Sec. II for given rho, u (stored as deviations from
@@ -24,23 +27,28 @@ __device__ long long pull_slot(const StepConst<T>& C, int x, int z, int nz, int 
 // (inst null): the value of (x, l) sits at (x, l).  Pull layout: it sits where the gather of
 // (x, l) reads it (pull_slot); every slot is written once.  z runs over the compact rows of all
 // lattices of a batch.
+// A thread per column x of a row, the rows strided over gridDim.y.  At rest (u null) the
+// equilibrium is W_l (rho - rho_ref) exactly, which takes one FP64 product per population.
 template <typename T>
 __global__ void k_init(int ns, T* __restrict__ f, const double* __restrict__ rho, const double* __restrict__ u,
                        const StepConst<T> C, const InstGeom* __restrict__ inst, int ninst) {
     const long long n = (long long)C.nx * C.nz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % C.nx), zg = (int)(i / C.nx);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= C.nx) return;
+    for (int zg = blockIdx.y; zg < C.nz; zg += gridDim.y) {
+        const long long i = (long long)zg * C.nx + x;
         const double ux = u ? u[i] : 0.0, uz = u ? u[n + i] : 0.0;
         int k = 0;
         if (inst && ninst > 1) k = inst_of_row(inst, ninst, zg);
         for (int s = 0; s < ns; ++s) {
             const double r = rho[s * n + i];
             const double dr = r - (double)C.rho_ref[s];
+#pragma unroll
             for (int l = 0; l < 9; ++l) {
                 long long o = (long long)zg * C.pitch + x;
                 int ls = l;
                 if (inst) o = pull_slot(C, x, zg - inst[k].zrow0, inst[k].nz, inst[k].prow0, l, ls);
-                f[(s * 9 + ls) * C.plane + o] = (T)feq_dev<double>(l, dr, r, ux, uz);
+                f[(s * 9 + ls) * C.plane + o] = (T)(u ? feq_dev<double>(l, dr, r, ux, uz) : wlb<double>(l) * dr);
             }
         }
     }
@@ -169,9 +177,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, const Batch* B,
                         cudaStream_t st) {
-    const long long n = (long long)C.nx * C.nz;
-    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_init<T><<<blocks, 256, 0, st>>>(ns, f, rho, u, C, B ? B->inst : nullptr, B ? B->ninst : 0);
+    const dim3 grid((C.nx + 127) / 128, C.nz < 65535 ? C.nz : 65535);
+    k_init<T><<<grid, 128, 0, st>>>(ns, f, rho, u, C, B ? B->inst : nullptr, B ? B->ninst : 0);
     return cudaGetLastError();
 }
 
