@@ -944,21 +944,21 @@ def main():
     if a.e2e_steps > 0:
         rho_pin = torch.from_numpy(np.ascontiguousarray(w["rho"])).pin_memory()
         rho_np = rho_pin.numpy()
-        series = lat.series(chunk=E2E_RUN, depth=2)
+        series = lat.series(chunk=E2E_RUN, depth=3)
         reader = lat.reader(depth=1)
         barrier()
         t0 = time.perf_counter()
         lat.set_fields(rho_np)
         lat.set_observe(1)
-        pending, left = None, a.e2e_steps
+        pending, left = [], a.e2e_steps
         while left > 0:
             n = min(E2E_RUN, left)
-            ticket = series.run(n)  # each record: the step before's sample (its reduction runs in the next launch)
+            pending.append(series.run(n))  # each record: the step before's sample (its reduction runs in the next launch)
             left -= n
-            if pending is not None:
-                series.results(pending)
-            pending = ticket
-        series.results(pending)
+            if len(pending) > 2:  # two runs in flight while the oldest is unpacked
+                series.results(pending.pop(0))
+        for ticket in pending:
+            series.results(ticket)
         reader.result(reader.enqueue(averages=True, reset=True))  # the last step's
         barrier()
         dt, e2e_sites = replicas.aggregate(time.perf_counter() - t0, sites * a.e2e_steps, dist=dist,
@@ -968,7 +968,7 @@ def main():
                "d2h_bytes_per_step": int(L.load().lbm_observables_bytes(lat.h)), "steps": a.e2e_steps,
                "read": f"every step's observables (time sums of one sample) copied into pinned host memory "
                        f"by lbm_step_read in runs of {E2E_RUN} steps, each run's records unpacked on the "
-                       f"host while the next run executes"}
+                       f"host while the next two runs execute"}
 
     if rank != 0:
         return
