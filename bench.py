@@ -65,10 +65,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--clocks-csv", default=None, help="keep the raw nvidia-smi clock samples in this file")
-    ap.add_argument("--l2", choices=["rotate", "flush"], default="rotate",
+    ap.add_argument("--l2", choices=["rotate", "flush", "none"], default="rotate",
                     help="rotate: step several lattices of the workload in turn, so that each step's input "
                          "was evicted from L2 by the others' traffic (no flush); flush: one lattice, a 256 MiB "
-                         "write then a 256 MiB read between timed steps")
+                         "write then a 256 MiB read between timed steps; none: one lattice stepped back to back "
+                         "(a step's input is what the step before wrote)")
     ap.add_argument("--autotune", type=int, default=0, metavar="STEPS",
                     help="before timing, let the library pick the pull kernel's tile width and pipeline depth by "
                          "timing STEPS steps of each (lbm_autotune_tiles; 0 = the default shape)")
@@ -786,7 +787,7 @@ def main():
 
     esize = 4 if a.precision == "fp32" else 8
     lattice_bytes = 2 * 9 * ns * sites * esize  # both population buffers
-    n_rot = 1 if a.l2 == "flush" else max(1, min(8, -(-ROTATE_BYTES // lattice_bytes)))
+    n_rot = 1 if a.l2 in ("flush", "none") else max(1, min(8, -(-ROTATE_BYTES // lattice_bytes)))
     lats = [make_lattice() for _ in range(n_rot)]
     lat = lats[0]
     depth = None

@@ -113,15 +113,24 @@ struct PullSmem {
 
 // Tile t of the work order; rot > 0 (one periodic lattice): the order starts rot tiles in, at
 // the last tile row, so the two rows whose sites also write the periodic row images come first
-// and the last tiles of a launch are plain ones.
+// and the last tiles of a launch are plain ones.  rev (one lattice, alternate launches): the tile
+// rows in the opposite direction -- rows 0, ntz - 1, ntz - 2, ..., 1 when periodic (the image rows
+// still first), ntz - 1 .. 0 between walls -- so that a launch starts on the rows the launch
+// before wrote last, which may still be in L2.
 template <typename T, int TW>
 __device__ __forceinline__ void describe(TileInfo<T>& D, int t, int ntiles, const InstGeom* __restrict__ inst,
-                                         int ninst, int ntx, int rot) {
+                                         int ninst, int ntx, int rot, int rev) {
     D.t = t;
     if (t >= ntiles) return;
     const InstGeom& I = inst[ninst > 1 ? inst_of_tile(inst, ninst, t / ntx) : 0];
     int tl = t - I.trow0 * ntx;
-    if (rot > 0) tl = tl < ntiles - rot ? tl + rot : tl - (ntiles - rot);
+    if (rev && ninst == 1) {
+        const int rp = tl / ntx, ntz = ntiles / ntx;
+        const int row = rot > 0 ? (rp == 0 ? 0 : ntz - rp) : ntz - 1 - rp;
+        tl = row * ntx + (tl - rp * ntx);
+    } else if (rot > 0) {
+        tl = tl < ntiles - rot ? tl + rot : tl - (ntiles - rot);
+    }
     const int j = tl / ntx;
     D.x0 = (tl - j * ntx) * TW;
     D.z0 = j * PZ;
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(Shape<TW>::NT, TW == 64 ? 1 : (sizeof(T) == 4 
     k_pull(const __grid_constant__ CUtensorMap tin, T* __restrict__ fout,
            const StepConst<T> C, const PairConst K, const ObsPtrs O, const Fold Rd, unsigned* __restrict__ ctr,
            unsigned* __restrict__ ctr_next, const InstGeom* __restrict__ inst, int ninst, int ntx, int ntz,
-           T* __restrict__ rec) {
+           T* __restrict__ rec, int rev) {
     // walls in z: never in the periodic build, else as the step constants say
     const bool WALL = (MODE & M_PERIODIC) ? false : C.zbc != 0;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(Shape<TW>::NT, TW == 64 ? 1 : (sizeof(T) == 4 
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tin) : "memory");
         for (int sl = 0; sl < ST; ++sl) {
             const int t = (int)blockIdx.x + sl * (int)gridDim.x;
-            if (t < nstat) describe<T, TW>(S.ti[sl], t, ntiles, inst, ninst, ntx, rot);
+            if (t < nstat) describe<T, TW>(S.ti[sl], t, ntiles, inst, ninst, ntx, rot, rev);
         }
     }
     // Programmatic dependent launch: the next step's CTAs may be scheduled as soon as this grid's
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(Shape<TW>::NT, TW == 64 ? 1 : (sizeof(T) == 4 
             const int t = (int)blockIdx.x + sl * (int)gridDim.x;
             if (t >= nstat)
                 describe<T, TW>(S.ti[sl], min(nstat + (int)atomicAdd(ctr, 1u), ntiles), ntiles, inst, ninst, ntx,
-                            rot);
+                                rot, rev);
             more = S.ti[sl].t < ntiles;
             if (more && sl == 0) issue_load(S, &tin, S.ti[0].x0, S.ti[0].prow0 + S.ti[0].z0, 0);
         }
@@ -376,7 +385,7 @@ __global__ void __launch_bounds__(Shape<TW>::NT, TW == 64 ? 1 : (sizeof(T) == 4 
         const TileInfo<T> D = S.ti[k % NTQ];
         if (D.t >= ntiles) break;
         if (tid == 0)  // publish the tile of iteration k + ST, one barrier ahead of its readers
-            describe<T, TW>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot);
+            describe<T, TW>(S.ti[(k + ST) % NTQ], upcoming, ntiles, inst, ninst, ntx, rot, rev);
         // this tile: first column and row (rows of its lattice), tile row among all lattices; its
         // lattice: rows, first compact row, first padded row (the observing builds read them again
         // from shared memory after the tile barrier, so that they hold no registers across it)
@@ -818,7 +827,8 @@ cudaError_t launch_mode(const void* tin, T* fout, const StepConst<T>& C, const O
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_pull<T, NS, MODE, ST, TW>, *static_cast<const CUtensorMap*>(tin), fout, C, K,
-                              O, Rd, sched + 2 * set, sched + 2 * (set ^ 1), B.inst, B.ninst, ntx, B.ntz, rec);
+                              O, Rd, sched + 2 * set, sched + 2 * (set ^ 1), B.inst, B.ninst, ntx, B.ntz, rec,
+                              set & 1);
 }
 
 // The passes built at width 64 as well: the FP32 step passes (lbm_step); all others run width 32.
