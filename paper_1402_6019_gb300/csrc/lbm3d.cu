@@ -97,6 +97,14 @@ __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
 __device__ __forceinline__ double2 vsplat(double a) { return make_double2(a, a); }
 __device__ __forceinline__ double2 vswap(double2 a) { return make_double2(a.y, a.x); }
 
+// Scalar operations whose rounding is fixed (the compiler neither contracts nor reorders them).
+__device__ __forceinline__ float smul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double smul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double sfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ---- geometry and constants ----------------------------------------------------------------
 
 constexpr int GX = 4, GY = 2, GZ = 2;         // ghosts of the psi / rho volumes
@@ -234,6 +242,255 @@ __device__ __forceinline__ V addc(V acc, V d) {
     return acc;
 }
 
+// Eq. FORCE over the 46 antipodal link pairs, shell by shell, both species at once, and the cross
+// repulsion of Sec. IV over the first belt: F[s][axis] of the site whose psi and rho pairs at the
+// offset (dx, dy, dz) are ps(dx, dy, dz) and rh(dx, dy, dz).
+template <typename T, int NS, typename PSF, typename RHF>
+__device__ __forceinline__ void force3(const Step3<T>& C, const PSF& ps, const RHF& rh, T (&F)[2][3]) {
+    using V = typename PairOf<T>::V;
+#define PS(dx, dy, dz) ps(dx, dy, dz)
+#define RH(dx, dy, dz) rh(dx, dy, dz)
+    const V zero = vsplat(T(0));
+    V ax = zero, ay = zero, az = zero;
+#define LBM3_ACC(dx, dy, dz)                                \
+    {                                                       \
+        const V d_ = vsub(PS(dx, dy, dz), PS(-(dx), -(dy), -(dz))); \
+        sx = addc<dx>(sx, d_);                              \
+        sy = addc<dy>(sy, d_);                              \
+        sz = addc<dz>(sz, d_);                              \
+    }
+#define LBM3_SHELL(q, LIST)                          \
+    {                                                \
+        V sx = zero, sy = zero, sz = zero;           \
+        LIST(LBM3_ACC)                               \
+        V kq_;                                       \
+        kq_.x = C.kq[0][q];                          \
+        kq_.y = C.kq[1][q];                          \
+        ax = vfma(kq_, sx, ax);                      \
+        ay = vfma(kq_, sy, ay);                      \
+        az = vfma(kq_, sz, az);                      \
+    }
+    LBM3_SHELL(1, LBM3_SHELL1)
+    LBM3_SHELL(2, LBM3_SHELL2)
+    LBM3_SHELL(3, LBM3_SHELL3)
+    LBM3_SHELL(4, LBM3_SHELL4)
+    LBM3_SHELL(5, LBM3_SHELL5)
+    LBM3_SHELL(6, LBM3_SHELL6)
+    LBM3_SHELL(8, LBM3_SHELL8)
+#undef LBM3_SHELL
+#undef LBM3_ACC
+    const V p0 = PS(0, 0, 0), r0 = RH(0, 0, 0);
+    const V mp = vsub(zero, p0);
+    V Fx = vmul(mp, ax), Fy = vmul(mp, ay), Fz = vmul(mp, az);
+    if constexpr (NS == 2) {
+        // cross repulsion: F_s += -G_AB rho_s(x) sum_l w(|c|^2) rho_s'(x + c_l) c_l over the first belt
+        V bx1 = zero, by1 = zero, bz1 = zero, bx2 = zero, by2 = zero, bz2 = zero;
+#define LBM3_XACC(dx, dy, dz, SX, SY, SZ)                      \
+    {                                                          \
+        const V d_ = vsub(RH(dx, dy, dz), RH(-(dx), -(dy), -(dz)));  \
+        SX = addc<dx>(SX, d_);                                 \
+        SY = addc<dy>(SY, d_);                                 \
+        SZ = addc<dz>(SZ, d_);                                 \
+    }
+#define LBM3_X1(dx, dy, dz) LBM3_XACC(dx, dy, dz, bx1, by1, bz1)
+#define LBM3_X2(dx, dy, dz) LBM3_XACC(dx, dy, dz, bx2, by2, bz2)
+        LBM3_SHELL1(LBM3_X1)
+        LBM3_SHELL2(LBM3_X2)
+#undef LBM3_X1
+#undef LBM3_X2
+#undef LBM3_XACC
+        const V k1 = vsplat(C.kc[1]), k2 = vsplat(C.kc[2]);
+        const V cx_ = vfma(k2, bx2, vmul(k1, bx1)), cy_ = vfma(k2, by2, vmul(k1, by1)),
+                cz_ = vfma(k2, bz2, vmul(k1, bz1));
+        const V mr = vsub(zero, r0);
+        // species A sees the sums over rho_B, species B those over rho_A
+        Fx = vfma(mr, vswap(cx_), Fx);
+        Fy = vfma(mr, vswap(cy_), Fy);
+        Fz = vfma(mr, vswap(cz_), Fz);
+    }
+    F[0][0] = Fx.x;
+    F[0][1] = Fy.x;
+    F[0][2] = Fz.x;
+    F[1][0] = Fx.y;
+    F[1][1] = Fy.y;
+    F[1][2] = Fz.y;
+#undef PS
+#undef RH
+}
+
+// The moments of the site's populations f, the body force along x, the common velocity of R5;
+// then (K3_FIELDS) rho_s, u and the plain populations into `fields`, or (K3_WRITE) the
+// shifted-velocity BGK of Sec. II and the push of the new populations to x + c_l.  Every scalar
+// operation has its rounding fixed (smul, sadd, sfma), so a kernel that inlines this computes the
+// same bits whatever the code around it.
+template <typename T, int NS, int MODE>
+__device__ __forceinline__ void site3(const Step3<T>& C, const T (&f)[NS][19], T (&F)[2][3], int x, int y, int z,
+                                      long long i, T* __restrict__ fout, int* __restrict__ flag,
+                                      double* __restrict__ fields) {
+    using V = typename PairOf<T>::V;
+    // ---- moments, body force, common velocity ----
+    T rho[NS], ir[NS], jx[NS], jy[NS], jz[NS], drho[NS];
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        T a = T(0), mx = T(0), my = T(0), mz = T(0);
+#pragma unroll
+        for (int l = 0; l < 19; ++l) {
+            a = sadd(a, f[s][l]);
+            if (c3x(l)) mx = sadd(mx, c3x(l) > 0 ? f[s][l] : -f[s][l]);
+            if (c3y(l)) my = sadd(my, c3y(l) > 0 ? f[s][l] : -f[s][l]);
+            if (c3z(l)) mz = sadd(mz, c3z(l) > 0 ? f[s][l] : -f[s][l]);
+        }
+        drho[s] = a;
+        rho[s] = sadd(C.rho_ref[s], a);
+        if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = true;
+        ir[s] = T(1) / rho[s];
+        jx[s] = mx;
+        jy[s] = my;
+        jz[s] = mz;
+        F[s][0] = sfma(rho[s], C.g, F[s][0]);
+    }
+    if (bad) atomicOr(flag, 1);
+    T nxu = T(0), nyu = T(0), nzu = T(0), den = T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        nxu = sfma(C.omega[s], jx[s], nxu);
+        nyu = sfma(C.omega[s], jy[s], nyu);
+        nzu = sfma(C.omega[s], jz[s], nzu);
+        den = sfma(C.omega[s], rho[s], den);
+    }
+    const T iden = T(1) / den;
+    const T upx = smul(nxu, iden), upy = smul(nyu, iden), upz = smul(nzu, iden);
+
+    if constexpr ((MODE & K3_FIELDS) != 0) {
+        // rho_s, the barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s, plain populations
+        const long long n = (long long)C.nx * C.ny * C.nz, k = ((long long)z * C.ny + y) * C.nx + x;
+        T mxs = T(0), mys = T(0), mzs = T(0), rt = T(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            mxs += jx[s] + T(0.5) * F[s][0];
+            mys += jy[s] + T(0.5) * F[s][1];
+            mzs += jz[s] + T(0.5) * F[s][2];
+            rt += rho[s];
+            fields[s * n + k] = (double)rho[s];
+#pragma unroll
+            for (int l = 0; l < 19; ++l)
+                fields[(NS + 3 + s * 19 + l) * n + k] = (double)f[s][l] + w19<double>(l) * (double)C.rho_ref[s];
+        }
+        fields[(NS + 0) * n + k] = (double)(mxs / rt);
+        fields[(NS + 1) * n + k] = (double)(mys / rt);
+        fields[(NS + 2) * n + k] = (double)(mzs / rt);
+    }
+
+    if constexpr ((MODE & K3_WRITE) != 0) {
+        // ---- shifted-velocity BGK (Sec. II) and streaming ----
+        // Destinations: the site's index plus one offset per axis, chosen by the sign of c_l; the
+        // periodic wrap is folded into those offsets once per thread (walls in z are handled by
+        // bounce-back below).
+        const long long row = C.pitch, lay = (long long)C.ny * C.pitch;
+        const bool wall_lo = C.zbc && z == 0, wall_hi = C.zbc && z == C.nz - 1;
+        // FP32: the wrapped offsets of each axis precomputed; FP64 (short of registers): the
+        // destination of each population wrapped where it is stored
+        long long oxm = 0, oxp = 0, oym = 0, oyp = 0, ozm = 0, ozp = 0;
+        if constexpr (sizeof(T) == 4) {
+            oxm = x == 0 ? C.nx - 1 : -1;
+            oxp = x == C.nx - 1 ? -(C.nx - 1) : 1;
+            oym = y == 0 ? (C.ny - 1) * row : -row;
+            oyp = y == C.ny - 1 ? -(C.ny - 1) * row : row;
+            ozm = z == 0 ? (C.nz - 1) * lay : -lay;
+            ozp = z == C.nz - 1 ? -(C.nz - 1) * lay : lay;
+        }
+        auto push = [&](int s, int l, T v) {
+            const int cx_ = c3x(l), cy_ = c3y(l), cz_ = c3z(l);
+            if ((cz_ < 0 && wall_lo) || (cz_ > 0 && wall_hi)) {  // halfway bounce-back with Ladd's term
+                const T uw = cz_ < 0 ? C.wall_u[0] : C.wall_u[1];
+                fout[(s * 19 + opp19(l)) * C.plane + i] = sadd(v, -smul(smul(T(6 * cx_) * w19<T>(l), rho[s]), uw));
+                return;
+            }
+            if constexpr (sizeof(T) == 4) {
+                const long long o = (cx_ < 0 ? oxm : (cx_ > 0 ? oxp : 0)) + (cy_ < 0 ? oym : (cy_ > 0 ? oyp : 0)) +
+                                    (cz_ < 0 ? ozm : (cz_ > 0 ? ozp : 0));
+                fout[(s * 19 + l) * C.plane + i + o] = v;
+            } else {
+                int xd = x + cx_, yd = y + cy_, zd = z + cz_;
+                xd = xd < 0 ? xd + C.nx : (xd >= C.nx ? xd - C.nx : xd);
+                yd = yd < 0 ? yd + C.ny : (yd >= C.ny ? yd - C.ny : yd);
+                zd = zd < 0 ? zd + C.nz : (zd >= C.nz ? zd - C.nz : zd);
+                fout[(s * 19 + l) * C.plane + ((long long)zd * C.ny + yd) * C.pitch + xd] = v;
+            }
+        };
+        if constexpr (NS == 2 && sizeof(T) == 4) {
+            // both species in lockstep, (A, B) pairs of packed FP32 instructions
+            V fp[19];
+#pragma unroll
+            for (int l = 0; l < 19; ++l) {
+                fp[l].x = f[0][l];
+                fp[l].y = f[1][l];
+            }
+            V rh, drh, om, tau, fx, fy, fz;
+            rh.x = rho[0], rh.y = rho[1];
+            drh.x = drho[0], drh.y = drho[1];
+            om.x = C.omega[0], om.y = C.omega[1];
+            tau.x = smul(C.tau[0], ir[0]), tau.y = smul(C.tau[1], ir[1]);
+            fx.x = F[0][0], fx.y = F[1][0];
+            fy.x = F[0][1], fy.y = F[1][1];
+            fz.x = F[0][2], fz.y = F[1][2];
+            const V keep = vsub(vsplat(T(1)), om);
+            const V ux = vfma(fx, tau, vsplat(upx)), uy = vfma(fy, tau, vsplat(upy)), uz = vfma(fz, tau, vsplat(upz));
+            const V u15 = vmul(vsplat(T(1.5)), vfma(ux, ux, vfma(uy, uy, vmul(uz, uz))));
+            const V b = vmul(om, rh);
+            const V base = vsub(vmul(om, drh), vmul(b, u15));  // omega (drho - 3/2 rho u^2)
+            push(0, 0, vfma(keep, fp[0], vmul(vsplat(w19<T>(0)), base)).x);
+            push(1, 0, vfma(keep, fp[0], vmul(vsplat(w19<T>(0)), base)).y);
+#pragma unroll
+            for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
+                // c_l . u with the components +-1 or 0 of this l (the branches fold away unrolled)
+                V cu = vsplat(T(0));
+                if (c3x(l) > 0) cu = vadd(cu, ux);
+                if (c3x(l) < 0) cu = vsub(cu, ux);
+                if (c3y(l) > 0) cu = vadd(cu, uy);
+                if (c3y(l) < 0) cu = vsub(cu, uy);
+                if (c3z(l) > 0) cu = vadd(cu, uz);
+                if (c3z(l) < 0) cu = vsub(cu, uz);
+                const T w = w19<T>(l);
+                const V wb = vmul(vsplat(w), b);
+                const V even = vfma(vmul(vsplat(T(4.5)), wb), vmul(cu, cu), vmul(vsplat(w), base));
+                const V odd = vmul(vmul(vsplat(T(3)), wb), cu);
+                const V gp = vadd(vfma(keep, fp[l], even), odd);
+                const V gm = vsub(vfma(keep, fp[l + 1], even), odd);
+                push(0, l, gp.x);
+                push(1, l, gp.y);
+                push(0, l + 1, gm.x);
+                push(1, l + 1, gm.y);
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                // the operations of the packed path, one species at a time
+                const T om = C.omega[s], keep = T(1) - om, tir = smul(C.tau[s], ir[s]);
+                const T ux = sfma(F[s][0], tir, upx), uy = sfma(F[s][1], tir, upy), uz = sfma(F[s][2], tir, upz);
+                const T u15 = smul(T(1.5), sfma(ux, ux, sfma(uy, uy, smul(uz, uz))));
+                const T b = smul(om, rho[s]);
+                const T base = sadd(smul(om, drho[s]), -smul(b, u15));  // omega (drho - 3/2 rho u^2)
+                push(s, 0, sfma(keep, f[s][0], smul(w19<T>(0), base)));
+#pragma unroll
+                for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
+                    T cu = T(0);
+                    if (c3x(l)) cu = sadd(cu, c3x(l) > 0 ? ux : -ux);
+                    if (c3y(l)) cu = sadd(cu, c3y(l) > 0 ? uy : -uy);
+                    if (c3z(l)) cu = sadd(cu, c3z(l) > 0 ? uz : -uz);
+                    const T w = w19<T>(l);
+                    const T wb = smul(w, b);
+                    const T even = sfma(smul(T(4.5), wb), smul(cu, cu), smul(w, base));
+                    const T odd = smul(smul(T(3), wb), cu);
+                    push(s, l, sadd(sfma(keep, f[s][l], even), odd));
+                    push(s, l + 1, sadd(sfma(keep, f[s][l + 1], even), -odd));
+                }
+            }
+        }
+    }
+}
+
 // FP32 tiles of 256 threads: 3 CTAs per SM (80 registers, 16 bytes of spills), measured faster than
 // 2 CTAs at 110 registers without spills -- the kernel waits on memory and more warps hide it.
 template <typename T, int MODE, int NS, int TY, int TZ>
@@ -310,234 +567,12 @@ __global__ void __launch_bounds__(TX* TY* TZ, TX* TY* TZ > 256 ? 1 : (sizeof(T) 
     }
     if (!live) return;
 
-    // ---- force: Eq. FORCE over the 46 antipodal pairs, shell by shell, both species ----
     const int bx = tx + GX, by = ty + GY, bz = tz + GZ;
-#define PS(dx, dy, dz) S.box[0][bz + (dz)][by + (dy)][bx + (dx)]
-#define RH(dx, dy, dz) S.box[1][bz + (dz)][by + (dy)][bx + (dx)]
-    const V zero = vsplat(T(0));
-    V ax = zero, ay = zero, az = zero;
-#define LBM3_ACC(dx, dy, dz)                                \
-    {                                                       \
-        const V d_ = vsub(PS(dx, dy, dz), PS(-(dx), -(dy), -(dz))); \
-        sx = addc<dx>(sx, d_);                              \
-        sy = addc<dy>(sy, d_);                              \
-        sz = addc<dz>(sz, d_);                              \
-    }
-#define LBM3_SHELL(q, LIST)                          \
-    {                                                \
-        V sx = zero, sy = zero, sz = zero;           \
-        LIST(LBM3_ACC)                               \
-        V kq_;                                       \
-        kq_.x = C.kq[0][q];                          \
-        kq_.y = C.kq[1][q];                          \
-        ax = vfma(kq_, sx, ax);                      \
-        ay = vfma(kq_, sy, ay);                      \
-        az = vfma(kq_, sz, az);                      \
-    }
-    LBM3_SHELL(1, LBM3_SHELL1)
-    LBM3_SHELL(2, LBM3_SHELL2)
-    LBM3_SHELL(3, LBM3_SHELL3)
-    LBM3_SHELL(4, LBM3_SHELL4)
-    LBM3_SHELL(5, LBM3_SHELL5)
-    LBM3_SHELL(6, LBM3_SHELL6)
-    LBM3_SHELL(8, LBM3_SHELL8)
-#undef LBM3_SHELL
-#undef LBM3_ACC
-    const V p0 = PS(0, 0, 0), r0 = RH(0, 0, 0);
-    const V mp = vsub(zero, p0);
-    V Fx = vmul(mp, ax), Fy = vmul(mp, ay), Fz = vmul(mp, az);
-    if constexpr (NS == 2) {
-        // cross repulsion: F_s += -G_AB rho_s(x) sum_l w(|c|^2) rho_s'(x + c_l) c_l over the first belt
-        V bx1 = zero, by1 = zero, bz1 = zero, bx2 = zero, by2 = zero, bz2 = zero;
-#define LBM3_XACC(dx, dy, dz, SX, SY, SZ)                      \
-    {                                                          \
-        const V d_ = vsub(RH(dx, dy, dz), RH(-(dx), -(dy), -(dz)));  \
-        SX = addc<dx>(SX, d_);                                 \
-        SY = addc<dy>(SY, d_);                                 \
-        SZ = addc<dz>(SZ, d_);                                 \
-    }
-#define LBM3_X1(dx, dy, dz) LBM3_XACC(dx, dy, dz, bx1, by1, bz1)
-#define LBM3_X2(dx, dy, dz) LBM3_XACC(dx, dy, dz, bx2, by2, bz2)
-        LBM3_SHELL1(LBM3_X1)
-        LBM3_SHELL2(LBM3_X2)
-#undef LBM3_X1
-#undef LBM3_X2
-#undef LBM3_XACC
-        const V k1 = vsplat(C.kc[1]), k2 = vsplat(C.kc[2]);
-        const V cx_ = vfma(k2, bx2, vmul(k1, bx1)), cy_ = vfma(k2, by2, vmul(k1, by1)),
-                cz_ = vfma(k2, bz2, vmul(k1, bz1));
-        const V mr = vsub(zero, r0);
-        // species A sees the sums over rho_B, species B those over rho_A
-        Fx = vfma(mr, vswap(cx_), Fx);
-        Fy = vfma(mr, vswap(cy_), Fy);
-        Fz = vfma(mr, vswap(cz_), Fz);
-    }
-#undef PS
-#undef RH
     T F[2][3];
-    F[0][0] = Fx.x;
-    F[0][1] = Fy.x;
-    F[0][2] = Fz.x;
-    F[1][0] = Fx.y;
-    F[1][1] = Fy.y;
-    F[1][2] = Fz.y;
-
-    // ---- moments, body force, common velocity ----
-    T rho[NS], ir[NS], jx[NS], jy[NS], jz[NS], drho[NS];
-    bool bad = false;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        T a = T(0), mx = T(0), my = T(0), mz = T(0);
-#pragma unroll
-        for (int l = 0; l < 19; ++l) {
-            a += f[s][l];
-            if (c3x(l)) mx += T(c3x(l)) * f[s][l];
-            if (c3y(l)) my += T(c3y(l)) * f[s][l];
-            if (c3z(l)) mz += T(c3z(l)) * f[s][l];
-        }
-        drho[s] = a;
-        rho[s] = C.rho_ref[s] + a;
-        if (!(rho[s] > T(0)) || !(rho[s] < T(1e30))) bad = true;
-        ir[s] = T(1) / rho[s];
-        jx[s] = mx;
-        jy[s] = my;
-        jz[s] = mz;
-        F[s][0] += rho[s] * C.g;
-    }
-    if (bad) atomicOr(flag, 1);
-    T nxu = T(0), nyu = T(0), nzu = T(0), den = T(0);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        nxu += C.omega[s] * jx[s];
-        nyu += C.omega[s] * jy[s];
-        nzu += C.omega[s] * jz[s];
-        den += C.omega[s] * rho[s];
-    }
-    const T iden = T(1) / den;
-    const T upx = nxu * iden, upy = nyu * iden, upz = nzu * iden;
-
-    if constexpr ((MODE & K3_FIELDS) != 0) {
-        // rho_s, the barycentric velocity (sum_s j_s + F_s / 2) / sum_s rho_s, plain populations
-        const long long n = (long long)C.nx * C.ny * C.nz, k = ((long long)z * C.ny + y) * C.nx + x;
-        T mxs = T(0), mys = T(0), mzs = T(0), rt = T(0);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            mxs += jx[s] + T(0.5) * F[s][0];
-            mys += jy[s] + T(0.5) * F[s][1];
-            mzs += jz[s] + T(0.5) * F[s][2];
-            rt += rho[s];
-            fields[s * n + k] = (double)rho[s];
-#pragma unroll
-            for (int l = 0; l < 19; ++l)
-                fields[(NS + 3 + s * 19 + l) * n + k] = (double)f[s][l] + w19<double>(l) * (double)C.rho_ref[s];
-        }
-        fields[(NS + 0) * n + k] = (double)(mxs / rt);
-        fields[(NS + 1) * n + k] = (double)(mys / rt);
-        fields[(NS + 2) * n + k] = (double)(mzs / rt);
-    }
-
-    if constexpr ((MODE & K3_WRITE) != 0) {
-        // ---- shifted-velocity BGK (Sec. II) and streaming ----
-        // Destinations: the site's index plus one offset per axis, chosen by the sign of c_l; the
-        // periodic wrap is folded into those offsets once per thread (walls in z are handled by
-        // bounce-back below).
-        const long long row = C.pitch, lay = (long long)C.ny * C.pitch;
-        const bool wall_lo = C.zbc && z == 0, wall_hi = C.zbc && z == C.nz - 1;
-        // FP32: the wrapped offsets of each axis precomputed; FP64 (short of registers): the
-        // destination of each population wrapped where it is stored
-        long long oxm = 0, oxp = 0, oym = 0, oyp = 0, ozm = 0, ozp = 0;
-        if constexpr (sizeof(T) == 4) {
-            oxm = x == 0 ? C.nx - 1 : -1;
-            oxp = x == C.nx - 1 ? -(C.nx - 1) : 1;
-            oym = y == 0 ? (C.ny - 1) * row : -row;
-            oyp = y == C.ny - 1 ? -(C.ny - 1) * row : row;
-            ozm = z == 0 ? (C.nz - 1) * lay : -lay;
-            ozp = z == C.nz - 1 ? -(C.nz - 1) * lay : lay;
-        }
-        auto push = [&](int s, int l, T v) {
-            const int cx_ = c3x(l), cy_ = c3y(l), cz_ = c3z(l);
-            if ((cz_ < 0 && wall_lo) || (cz_ > 0 && wall_hi)) {  // halfway bounce-back with Ladd's term
-                const T uw = cz_ < 0 ? C.wall_u[0] : C.wall_u[1];
-                fout[(s * 19 + opp19(l)) * C.plane + i] = v - T(6) * w19<T>(l) * rho[s] * T(cx_) * uw;
-                return;
-            }
-            if constexpr (sizeof(T) == 4) {
-                const long long o = (cx_ < 0 ? oxm : (cx_ > 0 ? oxp : 0)) + (cy_ < 0 ? oym : (cy_ > 0 ? oyp : 0)) +
-                                    (cz_ < 0 ? ozm : (cz_ > 0 ? ozp : 0));
-                fout[(s * 19 + l) * C.plane + i + o] = v;
-            } else {
-                int xd = x + cx_, yd = y + cy_, zd = z + cz_;
-                xd = xd < 0 ? xd + C.nx : (xd >= C.nx ? xd - C.nx : xd);
-                yd = yd < 0 ? yd + C.ny : (yd >= C.ny ? yd - C.ny : yd);
-                zd = zd < 0 ? zd + C.nz : (zd >= C.nz ? zd - C.nz : zd);
-                fout[(s * 19 + l) * C.plane + ((long long)zd * C.ny + yd) * C.pitch + xd] = v;
-            }
-        };
-        if constexpr (NS == 2 && sizeof(T) == 4) {
-            // both species in lockstep, (A, B) pairs of packed FP32 instructions
-            V fp[19];
-#pragma unroll
-            for (int l = 0; l < 19; ++l) {
-                fp[l].x = f[0][l];
-                fp[l].y = f[1][l];
-            }
-            V rh, drh, om, tau, fx, fy, fz;
-            rh.x = rho[0], rh.y = rho[1];
-            drh.x = drho[0], drh.y = drho[1];
-            om.x = C.omega[0], om.y = C.omega[1];
-            tau.x = C.tau[0] * ir[0], tau.y = C.tau[1] * ir[1];
-            fx.x = F[0][0], fx.y = F[1][0];
-            fy.x = F[0][1], fy.y = F[1][1];
-            fz.x = F[0][2], fz.y = F[1][2];
-            const V keep = vsub(vsplat(T(1)), om);
-            const V ux = vfma(fx, tau, vsplat(upx)), uy = vfma(fy, tau, vsplat(upy)), uz = vfma(fz, tau, vsplat(upz));
-            const V u15 = vmul(vsplat(T(1.5)), vfma(ux, ux, vfma(uy, uy, vmul(uz, uz))));
-            const V b = vmul(om, rh);
-            const V base = vsub(vmul(om, drh), vmul(b, u15));  // omega (drho - 3/2 rho u^2)
-            push(0, 0, vfma(keep, fp[0], vmul(vsplat(w19<T>(0)), base)).x);
-            push(1, 0, vfma(keep, fp[0], vmul(vsplat(w19<T>(0)), base)).y);
-#pragma unroll
-            for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
-                // c_l . u with the components +-1 or 0 of this l (the branches fold away unrolled)
-                V cu = vsplat(T(0));
-                if (c3x(l) > 0) cu = vadd(cu, ux);
-                if (c3x(l) < 0) cu = vsub(cu, ux);
-                if (c3y(l) > 0) cu = vadd(cu, uy);
-                if (c3y(l) < 0) cu = vsub(cu, uy);
-                if (c3z(l) > 0) cu = vadd(cu, uz);
-                if (c3z(l) < 0) cu = vsub(cu, uz);
-                const T w = w19<T>(l);
-                const V wb = vmul(vsplat(w), b);
-                const V even = vfma(vmul(vsplat(T(4.5)), wb), vmul(cu, cu), vmul(vsplat(w), base));
-                const V odd = vmul(vmul(vsplat(T(3)), wb), cu);
-                const V gp = vadd(vfma(keep, fp[l], even), odd);
-                const V gm = vsub(vfma(keep, fp[l + 1], even), odd);
-                push(0, l, gp.x);
-                push(1, l, gp.y);
-                push(0, l + 1, gm.x);
-                push(1, l + 1, gm.y);
-            }
-        } else {
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                const T om = C.omega[s], keep = T(1) - om, tir = C.tau[s] * ir[s];
-                const T ux = upx + F[s][0] * tir, uy = upy + F[s][1] * tir, uz = upz + F[s][2] * tir;
-                const T u15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-                const T b = om * rho[s];
-                const T base = om * drho[s] - b * u15;  // omega (drho - 3/2 rho u^2)
-                push(s, 0, keep * f[s][0] + w19<T>(0) * base);
-#pragma unroll
-                for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
-                    const T cu = T(c3x(l)) * ux + T(c3y(l)) * uy + T(c3z(l)) * uz;
-                    const T w = w19<T>(l);
-                    const T even = w * base + (w * T(4.5)) * b * cu * cu;
-                    const T odd = (w * T(3)) * b * cu;
-                    push(s, l, (keep * f[s][l] + even) + odd);
-                    push(s, l + 1, (keep * f[s][l + 1] + even) - odd);
-                }
-            }
-        }
-    }
+    force3<T, NS>(
+        C, [&](int dx, int dy, int dz) { return S.box[0][bz + dz][by + dy][bx + dx]; },
+        [&](int dx, int dy, int dz) { return S.box[1][bz + dz][by + dy][bx + dx]; }, F);
+    site3<T, NS, MODE>(C, f, F, x, y, z, i, fout, flag, fields);
 }
 
 // ---- equilibrium at rest, totals ---------------------------------------------------------------
