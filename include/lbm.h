@@ -148,7 +148,14 @@ int lbm_get_fields(lbm_ctx *c, double *rho, double *u, double *f, int where);
 /* Advance nsteps >= 0 time steps (Eq. LB with the force of Eq. FORCE applied by the shifted
    velocity of Sec. II, then streaming with the walls of Sec. IV).  Asynchronous.  While
    sampling is on (lbm_set_observe), every k-th step also accumulates the observables of
-   the state it collides into FP64 time sums on the device. */
+   the state it collides into FP64 time sums on the device.
+   Captured into a caller's CUDA graph (stream capture on the context's stream), the launches
+   are recorded with their arguments and the context's host-side state advances as if they had
+   run: the step counter, the pending observables pass, and the pair of work counters that
+   consecutive launches alternate.  Replay such a graph once per capture.  A second replay
+   would start from a state the context has moved past (with an odd number of steps captured,
+   its first launch would also find a work counter it expects to be zero still holding the last
+   count). */
 int lbm_step(lbm_ctx *c, int nsteps);
 
 /* Sampling of time averages: every k >= 1 steps, or 0 = off.  Resets the sums. */
