@@ -77,8 +77,24 @@ int lbm3_get_fields(lbm3_ctx *c, double *rho, double *u, double *f, int where);
 int lbm3_step(lbm3_ctx *c, int nsteps);
 
 /* Totals of the current state: mass[s] = sum of rho_s (n_species entries), momentum[3] =
-   the lattice momentum sum_s sum_l c_l f_l,s.  FP64 sums.  Synchronises. */
+   the lattice momentum sum_s sum_l c_l f_l,s.  A site's sums over its 19 populations are formed
+   in the context's precision (FP32 deviations: the sums the step forms rho with), the sums over
+   the sites in FP64.  Synchronises. */
 int lbm3_totals(lbm3_ctx *c, double *mass, double *momentum);
+
+/* Advance nsteps >= 0 steps and, after each, write the totals of the new state into record i,
+   the 5 doubles at (char *)dst + i * stride: mass A, mass B (zero for one species), the lattice
+   momentum x, y, z.  They are the values lbm3_totals returns, summed in the same order, so the
+   same bits.  dst is device memory or pinned host memory (cudaHostAlloc or registered); stride is
+   a multiple of 8 bytes, at least 40.  The records are written by kernels on the context's
+   stream: asynchronous, no host copy.  *ticket (may be NULL) receives the ticket of the run's last
+   record; lbm3_wait(c, ticket) waits until it and every record before it are written (an event;
+   for one of the last 64 tickets, else the whole stream).  A failed step (density <= 0, NaN or
+   Inf, a tile load that did not arrive) is reported by lbm3_synchronize, not here.  The next
+   step's density pass forms each record along with its own work, so the populations are read once
+   per step for both; lbm3_profile does not time these steps. */
+int lbm3_step_totals(lbm3_ctx *c, int nsteps, double *dst, long long stride, long long *ticket);
+int lbm3_wait(lbm3_ctx *c, long long ticket);
 
 /* Wait for the context's stream; LBM_ENONFINITE if a step met a density <= 0, NaN or Inf,
    LBM_ETIMEOUT if a bounded device-side wait for a tile load gave up. */

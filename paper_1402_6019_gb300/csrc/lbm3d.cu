@@ -154,6 +154,29 @@ __device__ __forceinline__ int mirror3(int i, int n) {
     return m >= n ? 2 * n - 1 - m : m;
 }
 
+// The step's two kernels are launched with programmatic dependent launch: the next kernel's CTAs
+// may be scheduled while this grid drains, and every thread waits for the previous grid in the
+// stream (and the visibility of its writes) before its first global access.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 // ---- k3_density --------------------------------------------------------------------------
 
 // The padded coordinates (own, then ghosts) that hold the value of coordinate v of an axis of
@@ -173,37 +196,113 @@ __device__ __forceinline__ int ghost_list(int v, int n, int g, bool mirror, int*
     return k;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) k3_density(const T* __restrict__ f, T* __restrict__ vol, const Step3<T> C) {
+// The density pass: each site's sums over its 19 populations per species give rho_s and psi_s,
+// written with their ghost images into the two volumes.  One thread per site: x from the block
+// (128 sites of a row), y and z from the grid, looping when the grid is smaller than the lattice
+// (the plain pass launches one block per row segment, so each loop runs once).  TOT: the block's
+// FP64 partials of the totals of the state go to part[block] as well -- the sums over its sites of
+// each species' density deviation sum_l f_l and of the lattice momentum: a site's sums (its two
+// species' momenta added) in the context's precision, the sums over the sites in FP64 (the
+// FP64 pipe is the scarce one), in a fixed order.
+// 16 CTAs per SM for the plain FP32 pass (32 registers, as it ran fastest); 8 with the totals,
+// whose FP64 accumulators need up to 64 registers, and in FP64, so that neither spills
+template <typename T, bool TOT>
+__global__ void __launch_bounds__(128, TOT || sizeof(T) == 8 ? 8 : 16)
+    k3_density(const T* __restrict__ f, T* __restrict__ vol, const Step3<T> C, double* __restrict__ part) {
     using V = typename PairOf<T>::V;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-    if (x >= C.nx) return;
-    const long long i = ((long long)z * C.ny + y) * C.pitch + x;
-    T rho[2] = {T(0), T(0)}, psi[2] = {T(0), T(0)};
-    for (int s = 0; s < C.ns; ++s) {
-        T a = T(0);
-#pragma unroll
-        for (int l = 0; l < 19; ++l) a += f[(s * 19 + l) * C.plane + i];
-        rho[s] = C.rho_ref[s] + a;
-        psi[s] = psi3<T>(C, s, rho[s]);
-    }
-    V pv, rv;
-    pv.x = psi[0];
-    pv.y = psi[1];
-    rv.x = rho[0];
-    rv.y = rho[1];
-    int xs[2 * GX + 1], ys[2 * GY + 1], zs[2 * GZ + 1];
-    const int nxl = ghost_list(x, C.nx, GX, false, xs);
-    const int nyl = ghost_list(y, C.ny, GY, false, ys);
-    const int nzl = ghost_list(z, C.nz, GZ, C.zbc != 0, zs);
+    pdl_enter();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    double mass0 = 0.0, mass1 = 0.0, momx = 0.0, momy = 0.0, momz = 0.0;
     V* const P = reinterpret_cast<V*>(vol);
-    for (int c = 0; c < nzl; ++c)
-        for (int b = 0; b < nyl; ++b)
-            for (int a = 0; a < nxl; ++a) {
-                const long long o = ((long long)zs[c] * C.gy + ys[b]) * C.gpitch + xs[a];
-                P[o] = pv;
-                P[C.gvol + o] = rv;
+    for (int z = blockIdx.z; z < C.nz; z += gridDim.z)
+        for (int y = blockIdx.y; y < C.ny; y += gridDim.y) {
+            if (x >= C.nx) continue;
+            const long long i = ((long long)z * C.ny + y) * C.pitch + x;
+            T rho[2] = {T(0), T(0)}, psi[2] = {T(0), T(0)};
+            T mx = T(0), my = T(0), mz = T(0);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {  // unrolled, so that the per-species values stay in registers
+                if (s >= C.ns) break;
+                T a = T(0);
+#pragma unroll
+                for (int l = 0; l < 19; ++l) {
+                    const T v = f[(s * 19 + l) * C.plane + i];
+                    a += v;
+                    if constexpr (TOT) {
+                        if (c3x(l)) mx += c3x(l) > 0 ? v : -v;
+                        if (c3y(l)) my += c3y(l) > 0 ? v : -v;
+                        if (c3z(l)) mz += c3z(l) > 0 ? v : -v;
+                    }
+                }
+                rho[s] = C.rho_ref[s] + a;
+                psi[s] = psi3<T>(C, s, rho[s]);
+                if constexpr (TOT) {
+                    if (s == 0)
+                        mass0 += (double)a;
+                    else
+                        mass1 += (double)a;
+                }
             }
+            if constexpr (TOT) {
+                momx += (double)mx;
+                momy += (double)my;
+                momz += (double)mz;
+            }
+            V pv, rv;
+            pv.x = psi[0];
+            pv.y = psi[1];
+            rv.x = rho[0];
+            rv.y = rho[1];
+            int xs[2 * GX + 1], ys[2 * GY + 1], zs[2 * GZ + 1];
+            const int nxl = ghost_list(x, C.nx, GX, false, xs);
+            const int nyl = ghost_list(y, C.ny, GY, false, ys);
+            const int nzl = ghost_list(z, C.nz, GZ, C.zbc != 0, zs);
+            for (int c = 0; c < nzl; ++c)
+                for (int b = 0; b < nyl; ++b)
+                    for (int a = 0; a < nxl; ++a) {
+                        const long long o = ((long long)zs[c] * C.gy + ys[b]) * C.gpitch + xs[a];
+                        P[o] = pv;
+                        P[C.gvol + o] = rv;
+                    }
+        }
+    if constexpr (TOT) {
+        __shared__ double red[5][128];
+        red[0][threadIdx.x] = mass0;
+        red[1][threadIdx.x] = mass1;
+        red[2][threadIdx.x] = momx;
+        red[3][threadIdx.x] = momy;
+        red[4][threadIdx.x] = momz;
+        __syncthreads();
+        for (int h = 64; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h)
+                for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+            __syncthreads();
+        }
+        const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        if (threadIdx.x < 5) part[blk * 5 + threadIdx.x] = red[threadIdx.x][0];
+    }
+}
+
+// out = mass A, mass B, momentum x, y, z: the sum of part[b][q] over the nblk blocks (thread t adds
+// blocks t, t + 256, ... in order, then a fixed tree over the threads; FP64, the same bits on every
+// call), plus base[q] (the sites times rho_ref,s for the masses).
+__global__ void __launch_bounds__(256)
+    k3_totals_sum(const double* __restrict__ part, int nblk, double base0, double base1, double* __restrict__ out) {
+    __shared__ double red[5][256];
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += 256)
+        for (int q = 0; q < 5; ++q) a[q] += part[b * 5 + q];
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) {
+        const double base = threadIdx.x == 0 ? base0 : (threadIdx.x == 1 ? base1 : 0.0);
+        out[threadIdx.x] = red[threadIdx.x][0] + base;
+    }
 }
 
 // ---- k3_step -----------------------------------------------------------------------------
@@ -505,6 +604,7 @@ __global__ void __launch_bounds__(TX* TY* TZ, TX* TY* TZ > 256 ? 1 : (sizeof(T) 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
     const bool live = x < C.nx && y < C.ny && z < C.nz;
+    pdl_enter();
     if (tid == 0) {
         const unsigned bar = su32(&S.bar);
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
@@ -590,37 +690,6 @@ __global__ void k3_init(T* __restrict__ f, const double* __restrict__ rho, const
     }
 }
 
-// Block partials of mass A, mass B and the lattice momentum (x, y, z), FP64.
-template <typename T>
-__global__ void __launch_bounds__(256) k3_totals(const T* __restrict__ f, const Step3<T> C, double* __restrict__ part) {
-    const long long n = (long long)C.nx * C.ny * C.nz;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(k % C.nx), y = (int)(k / C.nx % C.ny), z = (int)(k / ((long long)C.nx * C.ny));
-        const long long i = ((long long)z * C.ny + y) * C.pitch + x;
-        for (int s = 0; s < C.ns; ++s) {
-            double r = (double)C.rho_ref[s];
-            for (int l = 0; l < 19; ++l) {
-                const double v = (double)f[(s * 19 + l) * C.plane + i];
-                r += v;
-                acc[2] += c3x(l) * v;
-                acc[3] += c3y(l) * v;
-                acc[4] += c3z(l) * v;
-            }
-            acc[s] += r;
-        }
-    }
-    __shared__ double red[5][256];
-    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = acc[q];
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h)
-            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
-}
-
 template <typename T, int MODE, int NS, int TY, int TZ>
 cudaError_t launch_step3(const CUtensorMap& map, const T* fin, T* fout, const Step3<T>& C, int* flag, double* fields,
                          cudaStream_t st) {
@@ -633,8 +702,7 @@ cudaError_t launch_step3(const CUtensorMap& map, const T* fin, T* fout, const St
         attr = true;
     }
     const dim3 grid((C.nx + TX - 1) / TX, (C.ny + TY - 1) / TY, (C.nz + TZ - 1) / TZ);
-    k3_step<T, MODE, NS, TY, TZ><<<grid, dim3(TX, TY, TZ), smem, st>>>(map, fin, fout, C, flag, fields);
-    return cudaGetLastError();
+    return launch_pdl(k3_step<T, MODE, NS, TY, TZ>, grid, dim3(TX, TY, TZ), smem, st, map, fin, fout, C, flag, fields);
 }
 
 template <typename T, int MODE, int NS>
@@ -684,8 +752,10 @@ struct lbm3_ctx {
     int* flag = nullptr;
     double* staging = nullptr;         // lbm3_get_fields / lbm3_set_fields from the host
     size_t staging_bytes = 0;
-    double* part = nullptr;            // lbm3_totals block partials
-    int nblk_tot = 0;
+    double* part = nullptr;            // the density pass's block partials of the totals
+    double* tot = nullptr;             // lbm3_totals: the 5 totals on the device
+    int nblk_den = 0;                  // blocks of the density pass with totals
+    int tot_grid[3] = {1, 1, 1};       // its grid
     double rho_ref[2] = {0.0, 0.0};
     Step3<float> c32{};
     Step3<double> c64{};
@@ -693,6 +763,8 @@ struct lbm3_ctx {
     std::vector<cudaEvent_t> ev;       // 4 per timed step
     size_t ev_used = 0;
     long long step = 0;
+    cudaEvent_t tev[64] = {};          // lbm3_step_totals: an event per ticket (ring)
+    long long tickets = 0;             // tickets issued
     std::string err;
 };
 
@@ -784,7 +856,10 @@ static void release3(lbm3_ctx* c) {
     cudaFree(c->flag);
     cudaFree(c->staging);
     cudaFree(c->part);
+    cudaFree(c->tot);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tev)
+        if (e) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -856,8 +931,17 @@ extern "C" int lbm3_create(lbm3_ctx** out, const lbm3_desc* d) {
     CKC3(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
     int nsm = 0;
     CKC3(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d->device));
-    c->nblk_tot = std::max(1, std::min(4 * nsm, (int)((c->n + 255) / 256)));
-    CKC3(cudaMalloc(&c->part, (size_t)c->nblk_tot * 5 * sizeof(double)));
+    {  // the density pass with totals: about 8 CTAs per SM, each looping over its rows
+        const int gx = (nx + 127) / 128, target = 8 * nsm;
+        const int gy = std::max(1, std::min(ny, target / gx));
+        const int gz = std::max(1, std::min(nz, target / (gx * gy)));
+        c->tot_grid[0] = gx;
+        c->tot_grid[1] = gy;
+        c->tot_grid[2] = gz;
+        c->nblk_den = gx * gy * gz;
+    }
+    CKC3(cudaMalloc(&c->part, (size_t)c->nblk_den * 5 * sizeof(double)));
+    CKC3(cudaMalloc(&c->tot, 5 * sizeof(double)));
     for (int k = 0; k < NSHAPE; ++k)
         if (make_vol_map(c, k) != 0)
             return bail(fail3(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the psi / rho volumes"));
@@ -918,12 +1002,12 @@ extern "C" int lbm3_set_fields(lbm3_ctx* c, const double* rho, int where) {
         src = h.data();
     }
     double sum[2] = {0.0, 0.0};
-    for (int s = 0; s < ns; ++s)
-        for (long long k = 0; k < n; ++k) {
-            const double r = src[s * n + k];
-            if (!(r > 0.0) || !std::isfinite(r)) return fail3(c, LBM_EINVAL, "rho must be > 0 and finite");
-            sum[s] += r;
-        }
+    for (int s = 0; s < ns; ++s) {
+        long long bad = -1;
+        sum[s] = lbm::density_sum(src + s * n, n, &bad);
+        if (bad >= 0)
+            return fail3(c, LBM_EINVAL, "rho must be > 0 and finite (rho[%d][%lld] = %g)", s, bad, src[s * n + bad]);
+    }
     for (int s = 0; s < 2; ++s)
         c->rho_ref[s] = c->d.precision == LBM_FP64 || s >= ns ? 0.0
                                                                : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : sum[s] / n);
@@ -945,13 +1029,30 @@ extern "C" int lbm3_set_fields(lbm3_ctx* c, const double* rho, int where) {
     return LBM_OK;
 }
 
-// the density pass over f[cur] into the volumes
-static cudaError_t density3(lbm3_ctx* c) {
-    const dim3 grid((c->d.nx + 127) / 128, c->d.ny, c->d.nz);
+// the density pass over f[cur] into the volumes; totals: its block partials of the totals of
+// f[cur] summed into out (5 doubles, device memory) as well
+static cudaError_t density3(lbm3_ctx* c, double* totals = nullptr) {
+    const dim3 grid = totals ? dim3(c->tot_grid[0], c->tot_grid[1], c->tot_grid[2])
+                             : dim3((c->d.nx + 127) / 128, c->d.ny, c->d.nz);
+    const dim3 block(128);
+    cudaError_t e;
     if (c->d.precision == LBM_FP64)
-        lbm3::k3_density<double><<<grid, 128, 0, c->stream>>>((const double*)c->f[c->cur], (double*)c->vol, c->c64);
+        e = totals ? launch_pdl(lbm3::k3_density<double, true>, grid, block, 0, c->stream, (const double*)c->f[c->cur],
+                                (double*)c->vol, c->c64, c->part)
+                   : launch_pdl(lbm3::k3_density<double, false>, grid, block, 0, c->stream,
+                                (const double*)c->f[c->cur], (double*)c->vol, c->c64, (double*)nullptr);
     else
-        lbm3::k3_density<float><<<grid, 128, 0, c->stream>>>((const float*)c->f[c->cur], (float*)c->vol, c->c32);
+        e = totals ? launch_pdl(lbm3::k3_density<float, true>, grid, block, 0, c->stream, (const float*)c->f[c->cur],
+                                (float*)c->vol, c->c32, c->part)
+                   : launch_pdl(lbm3::k3_density<float, false>, grid, block, 0, c->stream, (const float*)c->f[c->cur],
+                                (float*)c->vol, c->c32, (double*)nullptr);
+    if (e != cudaSuccess || !totals) return e;
+    // the reference densities the FP32 deviations are taken from (zero in FP64, and for an absent
+    // species), once per site
+    const double n = (double)c->n;
+    const double r0 = c->d.precision == LBM_FP64 ? 0.0 : (double)c->c32.rho_ref[0];
+    const double r1 = c->d.precision == LBM_FP64 ? 0.0 : (double)c->c32.rho_ref[1];
+    lbm3::k3_totals_sum<<<1, 256, 0, c->stream>>>(c->part, c->nblk_den, n * r0, n * r1, totals);
     return cudaGetLastError();
 }
 
@@ -965,33 +1066,92 @@ static cudaError_t collide3(lbm3_ctx* c, int mode, double* fields) {
                                    (float*)c->f[c->cur ^ 1], c->c32, c->flag, fields, c->stream);
 }
 
+// one step: the density pass and the collide pass (bracketed by events while profiling)
+static int one_step3(lbm3_ctx* c) {
+    cudaEvent_t* e = nullptr;
+    if (c->profiling) {
+        if (c->ev_used + 4 > c->ev.size())
+            for (int q = 0; q < 64; ++q) {
+                cudaEvent_t ev;
+                CK3(cudaEventCreate(&ev));
+                c->ev.push_back(ev);
+            }
+        e = &c->ev[c->ev_used];
+        c->ev_used += 4;
+        CK3(cudaEventRecord(e[0], c->stream));
+    }
+    CK3(density3(c));
+    if (e) {
+        CK3(cudaEventRecord(e[1], c->stream));
+        CK3(cudaEventRecord(e[2], c->stream));
+    }
+    CK3(collide3(c, K3_WRITE, nullptr));
+    if (e) CK3(cudaEventRecord(e[3], c->stream));
+    c->cur ^= 1;
+    c->step += 1;
+    return LBM_OK;
+}
+
 extern "C" int lbm3_step(lbm3_ctx* c, int nsteps) {
     if (!c || nsteps < 0) return c ? fail3(c, LBM_EINVAL, "nsteps < 0") : LBM_EINVAL;
     if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
     CK3(cudaSetDevice(c->d.device));
     for (int k = 0; k < nsteps; ++k) {
-        cudaEvent_t* e = nullptr;
-        if (c->profiling) {
-            if (c->ev_used + 4 > c->ev.size())
-                for (int q = 0; q < 64; ++q) {
-                    cudaEvent_t ev;
-                    CK3(cudaEventCreate(&ev));
-                    c->ev.push_back(ev);
-                }
-            e = &c->ev[c->ev_used];
-            c->ev_used += 4;
-            CK3(cudaEventRecord(e[0], c->stream));
-        }
-        CK3(density3(c));
-        if (e) {
-            CK3(cudaEventRecord(e[1], c->stream));
-            CK3(cudaEventRecord(e[2], c->stream));
-        }
+        const int rc = one_step3(c);
+        if (rc != LBM_OK) return rc;
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm3_step_totals(lbm3_ctx* c, int nsteps, double* dst, long long stride, long long* ticket) {
+    if (!c) return LBM_EINVAL;
+    if (nsteps < 0) return fail3(c, LBM_EINVAL, "nsteps < 0");
+    if (!dst && nsteps > 0) return fail3(c, LBM_EINVAL, "dst is NULL");
+    if (stride < 5 * (long long)sizeof(double) || stride % (long long)sizeof(double))
+        return fail3(c, LBM_EINVAL, "stride must be a multiple of 8 bytes and at least 40");
+    if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
+    CK3(cudaSetDevice(c->d.device));
+    // the kernels write the records themselves: device memory, or pinned host memory through its
+    // device address
+    double* out = nullptr;
+    if (nsteps > 0) {
+        cudaPointerAttributes pa{};
+        const cudaError_t e = cudaPointerGetAttributes(&pa, dst);
+        cudaGetLastError();  // an unregistered pointer may leave an error behind
+        if (e == cudaSuccess && pa.type == cudaMemoryTypeDevice)
+            out = dst;
+        else if (e == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            out = static_cast<double*>(pa.devicePointer);
+        else
+            return fail3(c, LBM_EINVAL, "dst must be device memory or pinned host memory");
+    }
+    // after each collide pass, the density pass of the next step forms the totals of the new state
+    // too (so the populations are read once per step for both); the first step needs its own
+    for (int k = 0; k < nsteps; ++k) {
+        if (k == 0) CK3(density3(c));
         CK3(collide3(c, K3_WRITE, nullptr));
-        if (e) CK3(cudaEventRecord(e[3], c->stream));
         c->cur ^= 1;
         c->step += 1;
+        CK3(density3(c, out + (long long)k * (stride / (long long)sizeof(double))));
     }
+    if (nsteps > 0) {  // one event for the run: its last record
+        cudaEvent_t& e = c->tev[c->tickets % 64];
+        if (!e) CK3(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK3(cudaEventRecord(e, c->stream));
+        if (ticket) *ticket = c->tickets;
+        c->tickets += 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm3_wait(lbm3_ctx* c, long long ticket) {
+    if (!c) return LBM_EINVAL;
+    if (ticket < 0 || ticket >= c->tickets) return fail3(c, LBM_EINVAL, "ticket %lld was not issued", ticket);
+    CK3(cudaSetDevice(c->d.device));
+    if (ticket < c->tickets - 64)
+        CK3(cudaStreamSynchronize(c->stream));  // its event was reused: wait for everything
+    else
+        CK3(cudaEventSynchronize(c->tev[ticket % 64]));
     return LBM_OK;
 }
 
@@ -1031,18 +1191,11 @@ extern "C" int lbm3_totals(lbm3_ctx* c, double* mass, double* momentum) {
     if (!c) return LBM_EINVAL;
     if (!c->have_fields) return fail3(c, LBM_EINVAL, "lbm3_set_fields has not been called");
     CK3(cudaSetDevice(c->d.device));
-    if (c->d.precision == LBM_FP64)
-        lbm3::k3_totals<double><<<c->nblk_tot, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->c64, c->part);
-    else
-        lbm3::k3_totals<float><<<c->nblk_tot, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->c32, c->part);
-    CK3(cudaGetLastError());
-    std::vector<double> h((size_t)c->nblk_tot * 5);
-    CK3(cudaMemcpyAsync(h.data(), c->part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK3(density3(c, c->tot));  // the density pass with the totals of f[cur]
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    CK3(cudaMemcpyAsync(t, c->tot, sizeof t, cudaMemcpyDeviceToHost, c->stream));
     const int rc = lbm3_synchronize(c);
     if (rc) return rc;
-    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = 0; b < c->nblk_tot; ++b)
-        for (int q = 0; q < 5; ++q) t[q] += h[(size_t)b * 5 + q];
     if (mass)
         for (int s = 0; s < c->d.n_species; ++s) mass[s] = t[s];
     if (momentum)

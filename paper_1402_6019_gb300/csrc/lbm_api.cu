@@ -736,12 +736,9 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
         hr = h.data();
     }
     for (int s = 0; s < ns; ++s) {
-        double sum = 0.0;
-        for (long long i = 0; i < n; ++i) {
-            const double v = hr[s * n + i];
-            if (!(v > 0.0) || !std::isfinite(v)) return fail(c, LBM_EINVAL, "rho[%d][%lld] = %g is not > 0", s, i, v);
-            sum += v;
-        }
+        long long bad = -1;
+        const double sum = density_sum(hr + s * n, n, &bad);
+        if (bad >= 0) return fail(c, LBM_EINVAL, "rho[%d][%lld] = %g is not > 0", s, bad, hr[s * n + bad]);
         c->rho_ref[s] = c->d.precision == LBM_FP64 ? 0.0 : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : sum / n);
     }
     const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;

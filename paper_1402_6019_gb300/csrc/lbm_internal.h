@@ -6,6 +6,8 @@
 #include "lbm.h"
 #include "lbm_core.cuh"
 
+#include <cfloat>
+
 namespace lbm {
 
 // Kernel modes (bit set).  M_PERIODIC (pull kernel only): compiled for periodic z, with no wall
@@ -73,6 +75,34 @@ LBM_HD T inst_wall_u(const InstGeom& I, int w) {
     if constexpr (sizeof(T) == 4) return I.wall_u_f[w]; else return I.wall_u[w];
 }
 // Sets a lattice's drive (both precisions).
+// Sum of the n densities r[0 .. n) and the first index whose value is not > 0 and finite (or -1):
+// eight running sums, independent chains of FP64 adds combined in a fixed order, so that the host
+// is not held up by one chain of dependent adds; the same result on every call.
+inline double density_sum(const double* r, long long n, long long* first_bad) {
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool ok = true;
+    long long i = 0;
+    for (; i + 8 <= n; i += 8)
+        for (int k = 0; k < 8; ++k) {
+            const double v = r[i + k];
+            ok &= (v > 0.0) & (v <= DBL_MAX);  // NaN fails the first, +inf the second
+            a[k] += v;
+        }
+    for (int k = 0; i < n; ++i, ++k) {
+        const double v = r[i];
+        ok &= (v > 0.0) & (v <= DBL_MAX);
+        a[k] += v;
+    }
+    *first_bad = -1;
+    if (!ok)
+        for (long long k = 0; k < n; ++k)
+            if (!(r[k] > 0.0) || !(r[k] <= DBL_MAX)) {
+                *first_bad = k;
+                break;
+            }
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 inline void set_inst_drive(InstGeom& I, double g, double wb, double wt) {
     I.g = g;
     I.g_f = (float)g;

@@ -116,6 +116,8 @@ SIGNATURES = {
     "lbm3_synchronize": (ctypes.c_int, [_VP]),
     "lbm3_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm3_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm3_step_totals": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    "lbm3_wait": (ctypes.c_int, [_VP, ctypes.c_longlong]),
     "lbm3_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "lbm3_set_shape": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm3_last_error": (ctypes.c_char_p, [_VP]),
@@ -691,6 +693,18 @@ class Lattice3:
 
     def synchronize(self):
         _check3(load().lbm3_synchronize(self.h), self.h)
+
+    def step_totals(self, n, out, stride=40):
+        """Advance n steps, writing each new state's totals (mass A, mass B, momentum x, y, z) as 5
+        doubles every `stride` bytes from `out` (a pinned CPU or CUDA float64 tensor, or a device
+        or pinned address); asynchronous, returns the ticket of the last record (wait() on it)."""
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else int(out)
+        t = ctypes.c_longlong(-1)
+        _check3(load().lbm3_step_totals(self.h, int(n), ctypes.c_void_p(ptr), int(stride), ctypes.byref(t)), self.h)
+        return t.value
+
+    def wait(self, ticket):
+        _check3(load().lbm3_wait(self.h, int(ticket)), self.h)
 
     def autotune(self, steps=10):
         """Pick the collide pass's tile shape by timing each here; returns (shape, ms per step of

@@ -201,3 +201,47 @@ def test_tile_shapes_bit_identical_on_small_lattices(nx, ny, nz, ns, zbc, precis
     for g in out[1:]:
         assert np.array_equal(g, out[0])
 
+
+@pytest.mark.parametrize("precision,ns", [(L.LBM_FP32, 2), (L.LBM_FP64, 2), (L.LBM_FP32, 1)])
+def test_step_totals_records_are_the_totals(precision, ns):
+    """lbm3_step_totals writes, after every step, the totals lbm3_totals returns (the same sums in
+    the same order, so the same bits) into pinned host or device records; bad arguments are
+    refused."""
+    import torch
+
+    nx, ny, nz = 37, 13, 9
+    rho, _ = W.sphere_packing(nx, ny, nz, 0.45, seed=31, r_mean=3, r_spread=1)
+    if ns == 1:
+        rho = rho[:1]
+    prm = dict(W.EMULSION_PARAMS if ns == 2 else W.SINGLE_PARAMS, body_force=2e-5)
+    ref = L.Lattice3(nx, ny, nz, ns, precision, 0, **prm)
+    ref.set_fields(rho)
+    expected = []
+    for _ in range(7):
+        ref.step(1)
+        m, j = ref.totals()
+        expected.append(np.concatenate([m, np.zeros(2 - ns), j]))
+    expected = np.array(expected)
+    host = torch.zeros((7, 6), dtype=torch.float64).pin_memory()  # stride 48 bytes
+    dev = torch.zeros((7, 5), dtype=torch.float64, device="cuda")
+    for out, stride in ((host, 48), (dev, 40)):
+        lat = L.Lattice3(nx, ny, nz, ns, precision, 0, **prm)
+        lat.set_fields(rho)
+        t1 = lat.step_totals(3, out, stride=stride)
+        t2 = lat.step_totals(4, out[3:], stride=stride)
+        assert t2 == t1 + 1
+        lat.wait(t2)
+        got = out[:, :5].cpu().numpy()
+        assert np.array_equal(got, expected)
+        lat.synchronize()
+    lat = L.Lattice3(nx, ny, nz, ns, precision, 0, **prm)
+    lat.set_fields(rho)
+    with pytest.raises(L.LbmError):
+        lat.step_totals(2, np.zeros((2, 5)).ctypes.data, stride=40)  # pageable host memory
+    with pytest.raises(L.LbmError):
+        lat.step_totals(2, dev, stride=32)
+    with pytest.raises(L.LbmError):
+        lat.step_totals(-1, dev)
+    with pytest.raises(L.LbmError):
+        lat.wait(0)  # no ticket issued yet
+
