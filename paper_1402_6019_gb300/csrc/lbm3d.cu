@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <new>
 #include <string>
 #include <vector>
@@ -754,6 +755,7 @@ struct lbm3_ctx {
     size_t staging_bytes = 0;
     double* part = nullptr;            // the density pass's block partials of the totals
     double* tot = nullptr;             // lbm3_totals: the 5 totals on the device
+    double* dcheck = nullptr;          // lbm3_set_fields: DCHECK_DOUBLES doubles (launch_density_check)
     int nblk_den = 0;                  // blocks of the density pass with totals
     int tot_grid[3] = {1, 1, 1};       // its grid
     double rho_ref[2] = {0.0, 0.0};
@@ -857,6 +859,7 @@ static void release3(lbm3_ctx* c) {
     cudaFree(c->staging);
     cudaFree(c->part);
     cudaFree(c->tot);
+    cudaFree(c->dcheck);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->tev)
         if (e) cudaEventDestroy(e);
@@ -942,6 +945,7 @@ extern "C" int lbm3_create(lbm3_ctx** out, const lbm3_desc* d) {
     }
     CKC3(cudaMalloc(&c->part, (size_t)c->nblk_den * 5 * sizeof(double)));
     CKC3(cudaMalloc(&c->tot, 5 * sizeof(double)));
+    CKC3(cudaMalloc(&c->dcheck, lbm::DCHECK_DOUBLES * sizeof(double)));
     for (int k = 0; k < NSHAPE; ++k)
         if (make_vol_map(c, k) != 0)
             return bail(fail3(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed for the psi / rho volumes"));
@@ -993,28 +997,28 @@ extern "C" int lbm3_set_fields(lbm3_ctx* c, const double* rho, int where) {
     CK3(cudaSetDevice(c->d.device));
     const int ns = c->d.n_species;
     const long long n = c->n;
-    std::vector<double> h;
-    const double* src = rho;
-    if (where == LBM_DEVICE) {
-        h.resize((size_t)ns * n);
-        CK3(cudaMemcpyAsync(h.data(), rho, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK3(cudaStreamSynchronize(c->stream));
-        src = h.data();
-    }
-    double sum[2] = {0.0, 0.0};
-    for (int s = 0; s < ns; ++s) {
-        long long bad = -1;
-        sum[s] = lbm::density_sum(src + s * n, n, &bad);
-        if (bad >= 0)
-            return fail3(c, LBM_EINVAL, "rho must be > 0 and finite (rho[%d][%lld] = %g)", s, bad, src[s * n + bad]);
+    int rc = staging3(c, (size_t)ns * n * sizeof(double));
+    if (rc) return rc;
+    // the densities into the staging buffer, checked and summed there (the reference densities
+    // need the sums on the host: one small read-back)
+    CK3(cudaMemcpyAsync(c->staging, rho, (size_t)ns * n * sizeof(double),
+                        where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    CK3(lbm::launch_density_check(c->staging, n, ns, c->dcheck, c->stream));
+    double chk[3];
+    CK3(cudaMemcpyAsync(chk, c->dcheck, sizeof chk, cudaMemcpyDeviceToHost, c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+    unsigned long long bad;
+    memcpy(&bad, &chk[2], sizeof bad);
+    if (bad != ~0ull) {
+        double v = 0.0;
+        CK3(cudaMemcpy(&v, c->staging + bad, sizeof v, cudaMemcpyDeviceToHost));
+        return fail3(c, LBM_EINVAL, "rho must be > 0 and finite (rho[%d][%lld] = %g)", (int)(bad / n),
+                     (long long)(bad % n), v);
     }
     for (int s = 0; s < 2; ++s)
         c->rho_ref[s] = c->d.precision == LBM_FP64 || s >= ns ? 0.0
-                                                               : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : sum[s] / n);
+                                                               : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : chk[s] / n);
     refresh3(c);
-    int rc = staging3(c, (size_t)ns * n * sizeof(double));
-    if (rc) return rc;
-    CK3(cudaMemcpyAsync(c->staging, src, (size_t)ns * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
     if (c->d.precision == LBM_FP64)
         lbm3::k3_init<double><<<blocks, 256, 0, c->stream>>>((double*)c->f[0], c->staging, c->c64);

@@ -68,6 +68,7 @@ struct lbm_ctx {
     double* out = nullptr;
     double* avg = nullptr;
     double* staging = nullptr;  // (ns + 2) * n doubles
+    double* dcheck = nullptr;   // lbm_set_fields: DCHECK_DOUBLES doubles (launch_density_check)
     double* fexport = nullptr;  // ns * 9 * n doubles
     void* adj_scratch = nullptr;  // adjoint: adjoint_scratch_bytes(nx, nz, ns)
     void* adj_lam = nullptr;      // adjoint: second lam buffer, ns * 9 * n doubles
@@ -270,7 +271,7 @@ static void release(lbm_ctx* c) {
     void* ptrs[] = {c->f_raw[0],   c->f_raw[1], c->part_row[0], c->part_row[1], c->part_col[0],
                     c->part_col[1], c->sched,   c->ticket,      c->flag,        c->out,
                     c->avg,         c->staging, c->fexport,     c->gfield,      c->inst_d,
-                    c->adj_scratch, c->adj_lam};
+                    c->adj_scratch, c->adj_lam,    c->dcheck};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_out) cudaFreeHost(c->host_out);
@@ -404,6 +405,7 @@ extern "C" int lbm_create(lbm_ctx** out, const lbm_desc* d) {
     CKC(cudaMalloc(&c->out, olen + 64));
     CKC(cudaMalloc(&c->avg, olen + 64));
     CKC(cudaMalloc(&c->staging, (size_t)(ns + 2) * nx * nz * sizeof(double)));
+    CKC(cudaMalloc(&c->dcheck, DCHECK_DOUBLES * sizeof(double)));
     CKC(cudaMallocHost(&c->host_out, olen));
     CKC(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned), c->stream));
     CKC(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
@@ -726,23 +728,23 @@ extern "C" int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u, in
     const Batch B = batch(c);
     const int ns = c->d.n_species;
     const long long n = (long long)c->d.nx * c->d.nz;
-    // validation and the reference densities need the values on the host
-    std::vector<double> h;
-    const double* hr = rho;
-    if (where == LBM_DEVICE) {
-        h.resize((size_t)ns * n);
-        CK(cudaMemcpyAsync(h.data(), rho, (size_t)ns * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        hr = h.data();
-    }
-    for (int s = 0; s < ns; ++s) {
-        long long bad = -1;
-        const double sum = density_sum(hr + s * n, n, &bad);
-        if (bad >= 0) return fail(c, LBM_EINVAL, "rho[%d][%lld] = %g is not > 0", s, bad, hr[s * n + bad]);
-        c->rho_ref[s] = c->d.precision == LBM_FP64 ? 0.0 : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : sum / n);
-    }
+    // the densities into the staging buffer, checked and summed there (the reference densities
+    // need the sums on the host: one small read-back)
     const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(c->staging, rho, (size_t)ns * n * sizeof(double), kind, c->stream));
+    CK(launch_density_check(c->staging, n, ns, c->dcheck, c->stream));
+    double chk[3];
+    CK(cudaMemcpyAsync(chk, c->dcheck, sizeof chk, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned long long bad;
+    memcpy(&bad, &chk[2], sizeof bad);
+    if (bad != ~0ull) {
+        double v = 0.0;
+        CK(cudaMemcpy(&v, c->staging + bad, sizeof v, cudaMemcpyDeviceToHost));
+        return fail(c, LBM_EINVAL, "rho[%d][%lld] = %g is not > 0", (int)(bad / n), (long long)(bad % n), v);
+    }
+    for (int s = 0; s < ns; ++s)
+        c->rho_ref[s] = c->d.precision == LBM_FP64 ? 0.0 : (c->p.rho_ref[s] >= 0.0 ? c->p.rho_ref[s] : chk[s] / n);
     const double* du = nullptr;
     if (u) {
         CK(cudaMemcpyAsync(c->staging + ns * n, u, (size_t)2 * n * sizeof(double), kind, c->stream));

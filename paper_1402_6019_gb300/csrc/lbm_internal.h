@@ -6,8 +6,6 @@
 #include "lbm.h"
 #include "lbm_core.cuh"
 
-#include <cfloat>
-
 namespace lbm {
 
 // Kernel modes (bit set).  M_PERIODIC (pull kernel only): compiled for periodic z, with no wall
@@ -75,33 +73,14 @@ LBM_HD T inst_wall_u(const InstGeom& I, int w) {
     if constexpr (sizeof(T) == 4) return I.wall_u_f[w]; else return I.wall_u[w];
 }
 // Sets a lattice's drive (both precisions).
-// Sum of the n densities r[0 .. n) and the first index whose value is not > 0 and finite (or -1):
-// eight running sums, independent chains of FP64 adds combined in a fixed order, so that the host
-// is not held up by one chain of dependent adds; the same result on every call.
-inline double density_sum(const double* r, long long n, long long* first_bad) {
-    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    bool ok = true;
-    long long i = 0;
-    for (; i + 8 <= n; i += 8)
-        for (int k = 0; k < 8; ++k) {
-            const double v = r[i + k];
-            ok &= (v > 0.0) & (v <= DBL_MAX);  // NaN fails the first, +inf the second
-            a[k] += v;
-        }
-    for (int k = 0; i < n; ++i, ++k) {
-        const double v = r[i];
-        ok &= (v > 0.0) & (v <= DBL_MAX);
-        a[k] += v;
-    }
-    *first_bad = -1;
-    if (!ok)
-        for (long long k = 0; k < n; ++k)
-            if (!(r[k] > 0.0) || !(r[k] <= DBL_MAX)) {
-                *first_bad = k;
-                break;
-            }
-    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-}
+// The densities of lbm_set_fields checked and summed on the device.  rho [ns][n] (device memory);
+// scratch: DCHECK_DOUBLES doubles of device memory.  The kernels leave in scratch: [0], [1] the
+// sums over each species' n values (a fixed order, the same bits on every call); [2], as an
+// unsigned 64-bit integer, the first index s n + i of a value that is not > 0 and finite, or all
+// ones.  Enqueued on st; the caller reads the three values back.
+constexpr int DCHECK_BLOCKS = 256;
+constexpr int DCHECK_DOUBLES = 3 + 2 * DCHECK_BLOCKS;
+cudaError_t launch_density_check(const double* rho, long long n, int ns, double* scratch, cudaStream_t st);
 
 inline void set_inst_drive(InstGeom& I, double g, double wb, double wt) {
     I.g = g;

@@ -1,3 +1,4 @@
+#include <cfloat>
 // lbm_obs.cu -- initial state, state export and the FP64 reduction of the observables.
 #include "lbm_reduce.cuh"
 
@@ -173,6 +174,59 @@ __global__ void __launch_bounds__(RB_THREADS) k_reduce(const ObsPtrs O, int nxpa
 
 
 }  // namespace
+
+// ---- the densities of lbm_set_fields: check and sums -----------------------------------------
+
+// Block b of species blockIdx.y: the values b 256 + t + k 256 DCHECK_BLOCKS, summed per thread in
+// that order, then a fixed tree over the block; the first invalid index by atomicMin.
+__global__ void __launch_bounds__(256) k_density_check(const double* __restrict__ rho, long long n,
+                                                       double* __restrict__ scratch) {
+    const int s = blockIdx.y;
+    const double* r = rho + s * n;
+    double a = 0.0;
+    unsigned long long first = ~0ull;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x) {
+        const double v = r[i];
+        if (!(v > 0.0) || !(v <= DBL_MAX)) first = min(first, (unsigned long long)(s * n + i));  // NaN, <= 0, inf
+        a += v;
+    }
+    if (first != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(scratch + 2), first);
+    __shared__ double red[256];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scratch[3 + s * gridDim.x + blockIdx.x] = red[0];
+}
+
+// scratch[s] = the sum of species s's block sums: thread t adds blocks t, t + 256, ... (one here),
+// then a fixed tree.
+__global__ void __launch_bounds__(256) k_density_total(int ns, double* __restrict__ scratch) {
+    __shared__ double red[256];
+    for (int s = 0; s < ns; ++s) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < DCHECK_BLOCKS; b += 256) a += scratch[3 + s * DCHECK_BLOCKS + b];
+        red[threadIdx.x] = a;
+        __syncthreads();
+        for (int h = 128; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) scratch[s] = red[0];
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_density_check(const double* rho, long long n, int ns, double* scratch, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch + 2, 0xff, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_density_check<<<dim3(DCHECK_BLOCKS, ns), 256, 0, st>>>(rho, n, scratch);
+    k_density_total<<<1, 256, 0, st>>>(ns, scratch);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_init(int ns, T* f, const double* rho, const double* u, const StepConst<T>& C, const Batch* B,
