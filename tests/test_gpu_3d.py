@@ -139,12 +139,19 @@ def test_fp32_full_size_bench_workload_against_oracle(ref3d):
 
 
 def test_invalid_input_rejected():
+    import torch
+
     lat = L.Lattice3(8, 8, 8, 2, L.LBM_FP32, 0, **W.EMULSION_PARAMS)
     rho = np.ones((2, 8, 8, 8))
     rho[1, 2, 3, 4] = -1.0
+    rho[1, 5, 0, 0] = np.nan
     with pytest.raises(L.LbmError) as e:
         lat.set_fields(rho)
     assert e.value.code == L.LBM_EINVAL
+    assert "rho[1][156] = -1" in str(e.value)  # the first of the two: (2 * 8 + 3) * 8 + 4
+    rho[1, 2, 3, 4] = np.inf
+    with pytest.raises(L.LbmError):
+        lat.set_fields(torch.from_numpy(rho).cuda())
     with pytest.raises(L.LbmError):
         lat.step(1)  # no fields yet
     with pytest.raises(L.LbmError):

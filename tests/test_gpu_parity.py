@@ -357,19 +357,32 @@ def test_time_averages_match_oracle_mean(oracle, kernel):
 
 
 def test_invalid_fields_rejected():
+    """lbm_set_fields checks the densities on the device: a value <= 0, NaN or inf is refused,
+    from host or device memory, and the first invalid one is named; a refused call changes
+    nothing, and a valid one after it works."""
+    import torch
+
     lat = L.Lattice(8, 8, 2, L.LBM_FP32, 0, **W.EMULSION_PARAMS)
     rho = np.ones((2, 8, 8))
+    rho[1, 5, 6] = -2.0
     rho[1, 3, 4] = 0.0
     with pytest.raises(L.LbmError) as e:
         lat.set_fields(rho)
     assert e.value.code == L.LBM_EINVAL
-    rho[1, 3, 4] = np.nan
-    with pytest.raises(L.LbmError):
-        lat.set_fields(rho)
+    assert "rho[1][28] = 0 " in str(e.value)  # the first of the two, at 3 * 8 + 4
+    for bad in (np.nan, np.inf):
+        rho[1, 3, 4] = bad
+        with pytest.raises(L.LbmError):
+            lat.set_fields(rho)
+        with pytest.raises(L.LbmError):
+            lat.set_fields(torch.from_numpy(rho).cuda())
     with pytest.raises(L.LbmError):
         lat.step(1)  # no fields yet
     with pytest.raises(L.LbmError):
         lat.set_params(tau=0.5)
+    lat.set_fields(np.ones((2, 8, 8)))
+    lat.step(2)
+    assert np.allclose(lat.fields()[0], 1.0)
 
 
 def test_nonfinite_state_is_reported():
