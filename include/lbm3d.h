@@ -88,7 +88,7 @@ int lbm3_totals(lbm3_ctx *c, double *mass, double *momentum);
    same bits.  dst is device memory or pinned host memory (cudaHostAlloc or registered); stride is
    a multiple of 8 bytes, at least 40.  The records are written by kernels on the context's
    stream: asynchronous, no host copy.  *ticket (may be NULL) receives the ticket of the run's last
-   record; lbm3_wait(c, ticket) waits until it and every record before it are written (an event;
+   record (left as it is when nsteps is 0); lbm3_wait(c, ticket) waits until it and every record before it are written (an event;
    for one of the last 64 tickets, else the whole stream).  A failed step (density <= 0, NaN or
    Inf, a tile load that did not arrive) is reported by lbm3_synchronize, not here.  The next
    step's density pass forms each record along with its own work, so the populations are read once
