@@ -252,3 +252,24 @@ def test_step_totals_records_are_the_totals(precision, ns):
     with pytest.raises(L.LbmError):
         lat.wait(0)  # no ticket issued yet
 
+
+@pytest.mark.parametrize("precision,tol", [(L.LBM_FP64, 1e-12), (L.LBM_FP32, 1e-6)])
+def test_totals_equal_sums_of_the_exported_state(precision, tol):
+    """lbm3_totals (the density pass's FP64 block partials, on a 40^3 lattice whose grid of the
+    totals loops over the planes) against the mass and lattice momentum summed on the host from
+    the exported densities and populations."""
+    n = 40
+    rho, _ = W.sphere_packing(n, n, n, 0.45, seed=51, r_mean=4, r_spread=1)
+    lat = L.Lattice3(n, n, n, 2, precision, 1, **dict(W.EMULSION_PARAMS, body_force=1e-5, wall_u=(0.01, -0.01)))
+    lat.set_fields(rho)
+    lat.step(7)
+    m, j = lat.totals()
+    r, _, f = lat.fields()
+    c = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 0],
+                  [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1], [-1, 0, 1], [0, 1, 1],
+                  [0, -1, -1], [0, 1, -1], [0, -1, 1]], float)
+    mass = r.sum(axis=(1, 2, 3))
+    mom = np.einsum("slzyx,lk->k", f, c)
+    assert np.abs(m - mass).max() <= tol * mass.max()
+    assert np.abs(j - mom).max() <= tol * mass.sum() * 1e-2
+
