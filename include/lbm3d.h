@@ -73,7 +73,9 @@ int lbm3_set_fields(lbm3_ctx *c, const double *rho, int where);
 int lbm3_get_fields(lbm3_ctx *c, double *rho, double *u, double *f, int where);
 
 /* nsteps (>= 0) time steps: a density pass (rho and psi into ghost-padded volumes), then the
-   force, collision and streaming pass.  Asynchronous. */
+   force, collision and streaming pass.  Asynchronous.  Captured into a caller's CUDA graph, the
+   launches are recorded with their buffers and the context's host-side state (step counter, the
+   current population buffer) advances as if they had run: replay such a graph once per capture. */
 int lbm3_step(lbm3_ctx *c, int nsteps);
 
 /* Totals of the current state: mass[s] = sum of rho_s (n_species entries), momentum[3] =
