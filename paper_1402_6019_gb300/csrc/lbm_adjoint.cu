@@ -118,23 +118,29 @@ __device__ void block_sum(const T (&v)[NPAR], typename Acc<T>::A* part, int accu
     }
 }
 
-// grad[k] += sum over the nb blocks of part[b][k]: one block, FP64, fixed order.
+// grad[k] += sum over the nb blocks of part[b][k]: one block, FP64, fixed order (per parameter:
+// each thread's blocks in order, a butterfly over the warp, the warps in order); the eight
+// parameters side by side, so their loads and reductions overlap.
 template <typename T>
 __global__ void __launch_bounds__(AT) k_adj_sum(const typename Acc<T>::A* __restrict__ part, long long nb,
                                                 double* __restrict__ grad) {
-    __shared__ double red[AT / 32];
+    __shared__ double red[AT / 32][NPAR];
+    double t[NPAR];
+#pragma unroll
+    for (int k = 0; k < NPAR; ++k) t[k] = 0.0;
+    for (long long b = threadIdx.x; b < nb; b += AT)
+#pragma unroll
+        for (int k = 0; k < NPAR; ++k) t[k] += Acc<T>::wide(part[b * NPAR + k]);
+#pragma unroll
     for (int k = 0; k < NPAR; ++k) {
-        double t = 0.0;
-        for (long long b = threadIdx.x; b < nb; b += AT) t += Acc<T>::wide(part[b * NPAR + k]);
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0;
-            for (int w = 0; w < AT / 32; ++w) a += red[w];
-            grad[k] += a;
-        }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = t[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < NPAR) {
+        double a = 0.0;
+        for (int w = 0; w < AT / 32; ++w) a += red[w][threadIdx.x];
+        grad[threadIdx.x] += a;
     }
 }
 
