@@ -251,6 +251,13 @@ def test_step_totals_records_are_the_totals(precision, ns):
         lat.step_totals(-1, dev)
     with pytest.raises(L.LbmError):
         lat.wait(0)  # no ticket issued yet
+    # more runs than the 64 events kept: waiting on an old ticket waits for the whole stream
+    tickets = [lat.step_totals(1, dev[k % 7:], stride=40) for k in range(66)]
+    assert tickets == list(range(66))
+    lat.wait(0)
+    lat.wait(65)
+    with pytest.raises(L.LbmError):
+        lat.wait(66)
 
 
 @pytest.mark.parametrize("precision,tol", [(L.LBM_FP64, 1e-12), (L.LBM_FP32, 1e-6)])
