@@ -109,6 +109,22 @@ def test_fp32_emulsion_against_oracle(ref3d):
     check3(ref, lat, TOL32, pops=False)
 
 
+@pytest.mark.parametrize("ns", [1, 2])
+def test_fp32_walls_and_drives_against_oracle(ref3d, ns):
+    """FP32 deviations between moving walls with a body force (halfway bounce-back with Ladd's
+    term, the mirror images of the densities beyond the walls), 200 steps, against the FP64
+    oracle at the FP32 bound; two species with unequal relaxation times."""
+    nx, ny, nz = 40, 12, 18
+    rho, _ = W.sphere_packing(nx, ny, nz, 0.4, seed=57, r_mean=3, r_spread=1, periodic_z=False)
+    if ns == 1:
+        rho = (0.8 + 0.3 * (rho[0] - rho[0].mean()))[None]
+        prm = dict(W.SINGLE_PARAMS, wall_u=(-0.02, 0.02), body_force=1e-5)
+    else:
+        prm = dict(W.EMULSION_PARAMS, tau=(1.0, 1.2), G_AB=0.587, wall_u=(-0.02, 0.02), body_force=1e-5)
+    ref, lat = pair3(ref3d, nx, ny, nz, ns, 1, L.LBM_FP32, rho, 200, **prm)
+    check3(ref, lat, TOL32, pops=False)
+
+
 def test_fp64_conservation_and_body_force():
     """Eq. LB conserves each species' mass; the interaction forces are pairwise antisymmetric,
     so on a periodic lattice the lattice momentum grows by exactly g sum(rho) per step."""
