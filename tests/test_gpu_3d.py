@@ -92,14 +92,17 @@ def test_fp64_unequal_tau_rho_pseudopotential(ref3d):
     check3(ref, lat, TOL64)
 
 
+@pytest.mark.parametrize("precision,tol", [(L.LBM_FP64, TOL64), (L.LBM_FP32, TOL32)])
 @pytest.mark.parametrize("nx,ny,nz,ns,zbc", [(1, 1, 1, 1, 0), (3, 2, 5, 2, 1), (5, 7, 3, 2, 0), (2, 9, 4, 1, 1),
                                               (33, 1, 1, 2, 0), (4, 3, 1, 2, 1)])
-def test_fp64_tiny_and_degenerate(ref3d, nx, ny, nz, ns, zbc):
+def test_tiny_and_degenerate(ref3d, nx, ny, nz, ns, zbc, precision, tol):
+    """Lattices narrower than the halo in some direction (every neighbour an image, several
+    times over), with walls or periodic, in FP64 and in the FP32 packed form."""
     rho = 0.8 + 0.2 * (2.0 * W.uniform(nx * 100 + ny * 10 + nz, ns * nx * ny * nz) - 1.0)
     rho = rho.reshape(ns, nz, ny, nx)
     prm = dict(W.EMULSION_PARAMS if ns == 2 else W.SINGLE_PARAMS, wall_u=(0.01, -0.02), body_force=2e-5)
-    ref, lat = pair3(ref3d, nx, ny, nz, ns, zbc, L.LBM_FP64, rho, 20, **prm)
-    check3(ref, lat, TOL64)
+    ref, lat = pair3(ref3d, nx, ny, nz, ns, zbc, precision, rho, 20, **prm)
+    check3(ref, lat, tol, pops=precision == L.LBM_FP64)
 
 
 def test_fp32_emulsion_against_oracle(ref3d):
