@@ -141,6 +141,19 @@ def test_fp64_tiny_and_degenerate(oracle, nx, nz, ns, zbc, kernel):
     check_obs(ref, lat, TOL64)
 
 
+@pytest.mark.parametrize("nx,nz,ns,zbc", [(1, 1, 1, 0), (5, 7, 2, 0), (3, 1, 1, 1), (29, 5, 2, 1),
+                                           (30, 2, 1, 0), (57, 3, 2, 0), (2, 9, 2, 1)])
+def test_fp32_tiny_and_degenerate(oracle, nx, nz, ns, zbc):
+    """The same narrow lattices in FP32 deviations through the default step kernel (the packed
+    two-species form where there are two): fields and observables at the FP32 bound."""
+    rho = W.noise_field(nx, nz, seed=nx * 100 + nz, mean=0.8, amp=0.2, n_species=ns)
+    u = 0.01 * W.noise_field(nx, nz, seed=7, mean=0.0, amp=1.0, n_species=2)
+    prm = dict(W.EMULSION_PARAMS if ns == 2 else W.SINGLE_PARAMS, wall_u=(0.01, -0.02), body_force=2e-5)
+    ref, lat = pair(oracle, nx, nz, ns, zbc, L.LBM_FP32, rho, 60, u=u, **prm)
+    check_fields(ref, lat, TOL32, pops=False)
+    check_obs(ref, lat, TOL32)
+
+
 @pytest.mark.parametrize("rpw", [1, 3, 200])
 def test_fp64_sweep_row_chunking(oracle, rpw):
     nx, nz = 64, 50
