@@ -47,6 +47,21 @@ __host__ __device__ constexpr int c3x(int l) { return code19(l) % 3 - 1; }
 __host__ __device__ constexpr int c3y(int l) { return code19(l) / 3 % 3 - 1; }
 __host__ __device__ constexpr int c3z(int l) { return code19(l) / 9 - 1; }
 __host__ __device__ constexpr int opp19(int l) { return l == 0 ? 0 : (l % 2 ? l + 1 : l - 1); }
+// The first velocity with a nonzero component along an axis (0: x, 1: y, 2: z).
+__host__ __device__ constexpr int first19(int axis) {
+    for (int l = 1; l < 19; ++l)
+        if ((axis == 0 ? c3x(l) : (axis == 1 ? c3y(l) : c3z(l))) != 0) return l;
+    return 0;
+}
+// Every odd velocity's first nonzero component is +1, so c_l . u can start from that component.
+__host__ __device__ constexpr bool odd_velocities_lead_positive() {
+    for (int l = 1; l < 19; l += 2)
+        if ((c3x(l) ? c3x(l) : (c3y(l) ? c3y(l) : c3z(l))) != 1) return false;
+    return true;
+}
+static_assert(odd_velocities_lead_positive(), "c_l . u of an odd velocity starts from a +1 component");
+static_assert(c3x(first19(0)) == 1 && c3y(first19(1)) == 1 && c3z(first19(2)) == 1,
+              "the momentum sums start from a +1 component");
 template <typename T>
 __host__ __device__ constexpr T w19(int l) {
     return l == 0 ? T(1) / T(3) : (l <= 6 ? T(1) / T(18) : T(1) / T(36));
@@ -433,13 +448,14 @@ __device__ __forceinline__ void site3(const Step3<T>& C, const T (&f)[NS][19], T
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        T a = T(0), mx = T(0), my = T(0), mz = T(0);
+        // each sum starts from its first term (no add of zero)
+        T a = f[s][0], mx = f[s][first19(0)], my = f[s][first19(1)], mz = f[s][first19(2)];
 #pragma unroll
-        for (int l = 0; l < 19; ++l) {
+        for (int l = 1; l < 19; ++l) {
             a = sadd(a, f[s][l]);
-            if (c3x(l)) mx = sadd(mx, c3x(l) > 0 ? f[s][l] : -f[s][l]);
-            if (c3y(l)) my = sadd(my, c3y(l) > 0 ? f[s][l] : -f[s][l]);
-            if (c3z(l)) mz = sadd(mz, c3z(l) > 0 ? f[s][l] : -f[s][l]);
+            if (c3x(l) && l != first19(0)) mx = sadd(mx, c3x(l) > 0 ? f[s][l] : -f[s][l]);
+            if (c3y(l) && l != first19(1)) my = sadd(my, c3y(l) > 0 ? f[s][l] : -f[s][l]);
+            if (c3z(l) && l != first19(2)) mz = sadd(mz, c3z(l) > 0 ? f[s][l] : -f[s][l]);
         }
         drho[s] = a;
         rho[s] = sadd(C.rho_ref[s], a);
@@ -545,6 +561,8 @@ __device__ __forceinline__ void site3(const Step3<T>& C, const T (&f)[NS][19], T
 #pragma unroll
             for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
                 // c_l . u with the components +-1 or 0 of this l (the branches fold away unrolled)
+                // from zero: starting from the first component, as the scalar path does, saves an
+                // add but changed the register allocation of this build for the worse (measured)
                 V cu = vsplat(T(0));
                 if (c3x(l) > 0) cu = vadd(cu, ux);
                 if (c3x(l) < 0) cu = vsub(cu, ux);
@@ -575,10 +593,10 @@ __device__ __forceinline__ void site3(const Step3<T>& C, const T (&f)[NS][19], T
                 push(s, 0, sfma(keep, f[s][0], smul(w19<T>(0), base)));
 #pragma unroll
                 for (int l = 1; l < 19; l += 2) {  // l and its opposite l + 1
-                    T cu = T(0);
-                    if (c3x(l)) cu = sadd(cu, c3x(l) > 0 ? ux : -ux);
-                    if (c3y(l)) cu = sadd(cu, c3y(l) > 0 ? uy : -uy);
-                    if (c3z(l)) cu = sadd(cu, c3z(l) > 0 ? uz : -uz);
+                    // starting from the first, +1, component (no add of zero)
+                    T cu = c3x(l) ? ux : (c3y(l) ? uy : uz);
+                    if (c3x(l) && c3y(l)) cu = sadd(cu, c3y(l) > 0 ? uy : -uy);
+                    if ((c3x(l) || c3y(l)) && c3z(l)) cu = sadd(cu, c3z(l) > 0 ? uz : -uz);
                     const T w = w19<T>(l);
                     const T wb = smul(w, b);
                     const T even = sfma(smul(T(4.5), wb), smul(cu, cu), smul(w, base));
