@@ -84,12 +84,15 @@ def test_fp64_walls_and_drives(ref3d, ns):
     check3(ref, lat, TOL64)
 
 
-def test_fp64_unequal_tau_rho_pseudopotential(ref3d):
+@pytest.mark.parametrize("precision,tol", [(L.LBM_FP64, TOL64), (L.LBM_FP32, TOL32)])
+def test_unequal_tau_rho_pseudopotential(ref3d, precision, tol):
+    """Unequal relaxation times and psi = rho, in FP64 and in the FP32 packed form (the two
+    species then differ in every term of the pair collision)."""
     nx, ny, nz = 20, 9, 12
     rho, _ = W.sphere_packing(nx, ny, nz, 0.4, seed=35, r_mean=3, r_spread=1)
     prm = dict(W.EMULSION_PARAMS, tau=(0.8, 1.3), psi_form=1, G_AB=0.3, G1=(-1.0, -0.8), G2=(0.6, 0.5))
-    ref, lat = pair3(ref3d, nx, ny, nz, 2, 0, L.LBM_FP64, rho, 50, **prm)
-    check3(ref, lat, TOL64)
+    ref, lat = pair3(ref3d, nx, ny, nz, 2, 0, precision, rho, 50, **prm)
+    check3(ref, lat, tol, pops=precision == L.LBM_FP64)
 
 
 @pytest.mark.parametrize("precision,tol", [(L.LBM_FP64, TOL64), (L.LBM_FP32, TOL32)])

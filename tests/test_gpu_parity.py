@@ -129,6 +129,20 @@ def test_fp64_unequal_tau_chem09_rho_psi(oracle):
     check_fields(ref, lat, TOL64)
 
 
+@pytest.mark.parametrize("zbc", [0, 1], ids=["periodic", "walls"])
+def test_fp32_unequal_tau_chem09_rho_psi(oracle, zbc):
+    """Unequal relaxation times, the second weight set and psi = rho in FP32 deviations (the
+    species then differ in every term of the packed collision): fields and observables at the
+    FP32 bound."""
+    nx, nz = 45, 33
+    rho, _ = W.disk_packing(nx, nz, 0.6, seed=8, r_mean=5, r_spread=1, periodic_z=not zbc)
+    prm = dict(W.EMULSION_PARAMS, tau=(0.8, 1.3), weight_preset=1, psi_form=1, G_AB=0.3,
+               G1=(-1.0, -0.8), G2=(0.6, 0.5), wall_u=(-0.01, 0.01), body_force=1e-5)
+    ref, lat = pair(oracle, nx, nz, 2, zbc, L.LBM_FP32, rho, 200, **prm)
+    check_fields(ref, lat, TOL32, pops=False)
+    check_obs(ref, lat, TOL32)
+
+
 @KERNELS
 @pytest.mark.parametrize("nx,nz,ns,zbc", [(1, 1, 1, 0), (5, 7, 2, 0), (3, 1, 1, 1), (29, 5, 2, 1),
                                            (30, 2, 1, 0), (57, 3, 2, 0), (2, 9, 2, 1)])
