@@ -178,6 +178,9 @@ def test_invalid_input_rejected():
         lat.step(1)  # no fields yet
     with pytest.raises(L.LbmError):
         lat.set_params(**dict(W.EMULSION_PARAMS, weight_preset=1))
+    with pytest.raises(L.LbmError) as e:
+        lat.set_params(**dict(W.EMULSION_PARAMS, psi_wall=L.LBM_WALL_ZERO))
+    assert e.value.code == L.LBM_EINVAL and "mirror" in str(e.value)
 
 
 @pytest.mark.parametrize("precision", [L.LBM_FP64, L.LBM_FP32])
