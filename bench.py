@@ -939,8 +939,11 @@ def main():
     kern_avg_ms = step_ms / a.steps if one_launch else kern_ser_ms
     achieved = bps * sites / (kern_avg_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
+    # the committed records are of the build that observes every step; without observables (or
+    # observing every k-th step) another build runs, whose traffic has no record
     traffic = _traffic(kernel_source_hash(a.kernel), a.workload, a.precision,
-                       a.kernel if a.tile_rows in (0, 8) else f"{a.kernel}{a.tile_rows}")
+                       (a.kernel if a.tile_rows in (0, 8) else f"{a.kernel}{a.tile_rows}")
+                       + ("" if a.observe_every == 1 else f"/observe_every_{a.observe_every}"))
     if a.precision == "fp64" and ns == 2 and a.observe_every == 1 and a.kernel == "pull":
         tf = FP64_FLOPS_PER_SITE * sites / (kern_avg_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),

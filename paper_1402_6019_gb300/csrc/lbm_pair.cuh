@@ -57,12 +57,23 @@ inline void fill_pair_const(PairConst& K, const StepConst<float>& C) {
     K.hom = make_float2(0.5f * C.omega[0], 0.5f * C.omega[1]);
 }
 
+// 2^a by the hardware approximation with subnormal results flushed to zero
+__device__ __forceinline__ float ex2_ftz(float a) {
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+#else
+    return exp2f(a);
+#endif
+}
+
 // Pseudopotential of Sec. IV for both species: psi = 1 - exp(-rho / rho0) (hardware exp2), or
 // psi = rho.
 __device__ __forceinline__ f2 psi2(const StepConst<float>& C, const PairConst& K, f2 rho) {
     if (C.psi_form == 1) return rho;
     const f2 a = mul2(rho, K.nexp);
-    return p2(1.0f - exp2f(a.x), 1.0f - exp2f(a.y));
+    return p2(1.0f - ex2_ftz(a.x), 1.0f - ex2_ftz(a.y));
 }
 
 // Eq. FORCE for both species: F = -psi(x) sum_l K(|c_l|^2) psi(x + c_l) c_l.  The 24 links come
